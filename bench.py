@@ -1,0 +1,323 @@
+"""Benchmark: time-to-1e-8 solves of the 128^3 lowest-order Nedelec H(curl)
+problem with the V-cycle of arXiv 2205.05840 (vertex-based DD smoother) as
+the PCG preconditioner, reported as V-cycle DoF*cycles/s.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one complete solve A u = f to ||f - A u|| <= 1e-8 ||f|| from u = 0
+(inputs resident in HBM); value = N_dofs * V-cycles / time.  With N > 1 (one
+process per GPU under torchrun) every rank solves its own right-hand side:
+the path needs no exchange between problems, so scaling is weak.
+
+--impl reference times the FP64 CPU oracle (oracle/) on the host cores on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_GRID = 128
+N_COARSEST = 4
+ALPHA = 1.0
+M_SMOOTH = 2
+TOL = 1e-8
+L2_FLUSH_BYTES = 256 << 20
+ORACLE_SAMPLE_N = 64
+
+
+def num_edges(n):
+    return 3 * n * (n - 1) ** 2
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--precision", choices=["auto", "fp64", "fp32", "bf16", "fp16"], default="auto")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# the oracle on the host cores
+# --------------------------------------------------------------------------
+def oracle_rate(n: int, cycles: int):
+    """DoF*cycles/s of the FP64 CPU oracle's V-cycle on an n^3 problem."""
+    import numpy as np
+    from oracle import mg
+    from paper_2205_05840_gb300 import inputs
+    H = mg.Hierarchy(n, 1.0, ALPHA, 1.0, n0=N_COARSEST, kind="vertex", m=M_SMOOTH)
+    f = inputs.random_load(n, 0)
+    z = np.zeros_like(f)
+    t0 = time.perf_counter()
+    for _ in range(cycles):
+        z = H.vcycle(f, z)
+    dt = time.perf_counter() - t0
+    return num_edges(n) * cycles / dt, dt
+
+
+def cores_used():
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS"):
+        if os.environ.get(var):
+            return int(os.environ[var])
+    return os.cpu_count() or 1
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    # warm-up and timed steps: each step one oracle V-cycle on the sample grid
+    rate_w = [oracle_rate(ORACLE_SAMPLE_N, 1)[0] for _ in range(max(args.warmup, 0))]
+    del rate_w
+    rates, secs = [], []
+    for _ in range(args.steps):
+        r, dt = oracle_rate(ORACLE_SAMPLE_N, 1)
+        rates.append(r)
+        secs.append(dt)
+    value = num_edges(ORACLE_SAMPLE_N) * len(rates) / sum(secs)
+    sample = f"one FP64 oracle V-cycle per step on the {ORACLE_SAMPLE_N}^3 grid (same alpha, m, coarsest 4^3)"
+    out = {"impl": "reference", "metric": "V-cycle DoF*cycles/s (solve to 1e-8 at 128^3)", "value": value,
+           "unit": "DoF*cycles/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * sum(secs) / len(secs), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"{ORACLE_SAMPLE_N}^3 sample of the 128^3 alpha=1 seeded-uniform-load solve"},
+           "cpu_baseline": {"value": value, "unit": "DoF*cycles/s", "cores": cores_used(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": "DoF*cycles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2205_05840_gb300 import inputs, ndmg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+
+    prec = {"auto": ndmg.PREC_FP64, "fp64": ndmg.PREC_FP64, "fp32": ndmg.PREC_FP32,
+            "bf16": ndmg.PREC_MIXED_BF16, "fp16": ndmg.PREC_MIXED_FP16}[args.precision]
+    if args.precision == "auto":
+        prec = getattr(ndmg, "DEFAULT_BENCH_PRECISION", ndmg.PREC_FP64)
+    dtype_name = {ndmg.PREC_FP64: "f64", ndmg.PREC_FP32: "f32+f64-refinement",
+                  ndmg.PREC_MIXED_BF16: "bf16-tc/f32+f64-refinement",
+                  ndmg.PREC_MIXED_FP16: "fp16-tc/f32+f64-refinement"}[prec]
+    stream = torch.cuda.Stream(device=dev)
+    S = ndmg.Solver(N_GRID, n_coarsest=N_COARSEST, alpha=ALPHA, m=M_SMOOTH, precision=prec, stream=stream)
+    Nd = S.num_dofs()
+    f = torch.tensor(inputs.random_load(N_GRID, seed=rank), dtype=torch.float64, device=dev)
+    u = torch.zeros_like(f)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def one_solve():
+        with torch.cuda.stream(stream):
+            u.zero_()
+        return S.solve(f, u, tol=TOL, maxit=500)
+
+    for _ in range(args.warmup):
+        one_solve()
+    torch.cuda.synchronize()
+
+    # kernel-class timing inside the timed region
+    classes = [ndmg.K_STENCIL, ndmg.K_PATCH, ndmg.K_BUBBLE, ndmg.K_RESTRICT, ndmg.K_PROLONG, ndmg.K_BLAS,
+               ndmg.K_COARSE]
+    for c in classes:
+        S.trace_read(c)
+        S.trace(c, True)
+    l0, v0 = S.counters()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    iters = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for s in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(s))          # evict L2 between timed steps (not timed)
+                u.zero_()
+                ev[s][0].record(stream)
+            st, it, rr = S.solve(f, u, tol=TOL, maxit=500)
+            with torch.cuda.stream(stream):
+                ev[s][1].record(stream)
+            iters.append((it, rr))
+        torch.cuda.synchronize()
+    l1, v1 = S.counters()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    ms_total = sum(ms)
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+        dist.barrier()
+    kern = {}
+    for c in classes:
+        n_l, k_ms, units = S.trace_read(c)
+        S.trace(c, False)
+        name = [k for k, v in ndmg.KERNEL_CLASSES.items() if v == c][0]
+        kern[name] = {"launches": n_l, "ms": k_ms, "units": units}
+    vcyc_per_step = (v1 - v0) / args.steps
+    launches = l1 - l0
+    value = world * Nd * vcyc_per_step * args.steps / (ms_total / 1e3)
+
+    # roofline of the dominant kernel class
+    import json as _json
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = _json.load(fh)
+    except OSError:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
+    dom = max(kern, key=lambda k: kern[k]["ms"])
+    kd = kern[dom]
+    if dom == "patch":
+        if prec in (ndmg.PREC_MIXED_BF16, ndmg.PREC_MIXED_FP16):
+            bound, peak, unit, scale = "tensor", bf16, "TFLOP/s", 1e12
+        elif prec == ndmg.PREC_FP64:
+            bound, peak, unit, scale = "alu", FP64_PEAK_TFLOPS, "TFLOP/s", 1e12
+        else:
+            bound, peak, unit, scale = "alu", FP32_PEAK_TFLOPS, "TFLOP/s", 1e12
+    else:
+        bound, peak, unit, scale = "hbm", hbm, "GB/s", 1e9
+    achieved = kd["units"] / (kd["ms"] / 1e3) / scale if kd["ms"] > 0 else 0.0
+    roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": achieved / peak if peak else None, "traffic": None,
+            "peak_source": "MEASURED_PEAKS.json" if bound in ("hbm", "tensor") else "nominal (see DESIGN.md)",
+            "launches": kd["launches"], "ms": kd["ms"]}
+
+    # end to end through the host-buffer entry point
+    f_h = torch.tensor(inputs.random_load(N_GRID, seed=rank), dtype=torch.float64).pin_memory()
+    u_h = torch.zeros(Nd, dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    v_e0 = S.counters()[1]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        u_h.zero_()
+        S.solve_host(f_h, u_h, tol=TOL, maxit=500)
+    t_e2e = time.perf_counter() - t0
+    v_e1 = S.counters()[1]
+    e2e_value = world * Nd * (v_e1 - v_e0) / t_e2e
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, dt = oracle_rate(ORACLE_SAMPLE_N, 2)
+        cpu = {"value": rate, "unit": "DoF*cycles/s", "cores": cores_used(), "kind": "oracle",
+               "sample": f"2 FP64 oracle V-cycles on the {ORACLE_SAMPLE_N}^3 grid ({dt:.1f} s)"}
+
+    if rank == 0:
+        out = {"metric": "V-cycle DoF*cycles/s (solve to 1e-8 at 128^3)", "value": value, "unit": "DoF*cycles/s",
+               "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype_name,
+               "data": "synthetic",
+               "config": {"workload": f"{N_GRID}^3 hexahedra, {Nd} edge DOFs, alpha={ALPHA}, beta=1, seeded "
+                                      f"uniform load (seed=rank), PCG + V-cycle (vertex DD smoother, eta=1/9, "
+                                      f"m={M_SMOOTH}, coarsest {N_COARSEST}^3) to {TOL:g}",
+                          "n": N_GRID, "dofs": Nd, "tol": TOL, "l2": "flushed (256 MB write) between timed steps",
+                          "parallelism": f"replicas{world}"},
+               "time_to_tol_ms": ms_total / args.steps, "vcycles_per_solve": vcyc_per_step,
+               "pcg_iterations": iters[-1][0], "final_relres": iters[-1][1],
+               "gpu_launches": launches, "roofline": roof, "kernels": kern,
+               "e2e": {"value": e2e_value, "unit": "DoF*cycles/s", "h2d_bytes_per_step": 2 * 8 * Nd,
+                       "d2h_bytes_per_step": 8 * Nd},
+               "clocks": clk.summary(), "cpu_baseline": cpu}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# nominal CUDA-core peaks for ALU-bound kernels (GB300: FP64 1.25 TFLOP/s as
+# stated for this part; FP32 from 152 SMs x 128 FMA/clk x 2 x 2.07 GHz)
+FP64_PEAK_TFLOPS = 1.25
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

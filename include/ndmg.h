@@ -1,0 +1,206 @@
+/*
+ * ndmg.h -- C ABI of libndmg: V-cycle multigrid for the lowest-order
+ * hexahedral Nedelec discretisation of curl(alpha curl u) + beta u = f on an
+ * axis-aligned box [0,L]^3 with zero tangential trace, smoothed by the
+ * nonoverlapping domain-decomposition smoothers of Oh, "Multigrid methods for
+ * 3D H(curl) problems with nonoverlapping domain decomposition smoothers"
+ * (arXiv 2205.05840).  One GPU (sm_103a), no CPU fallback.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Mesh.  Level k (0 = coarsest, K = finest) has n_k = n_0 * 2^k hexahedra per
+ *   side, h_k = L / n_k (Sec. 3.1: uniform refinement, h_k = h_{k-1}/2).
+ * DOFs.  One value per interior edge (Sec. 2, eq. NDdof: the average
+ *   tangential component), N(n) = 3 n (n-1)^2, canonical order, every edge
+ *   oriented along +axis:
+ *     x-edge (segment i in [0,n), nodes j,k in [1,n-1]): ((k-1)(n-1)+(j-1)) n + i
+ *     y-edge (node i in [1,n-1], segment j in [0,n), node k): n(n-1)^2 + ((k-1) n + j)(n-1) + (i-1)
+ *     z-edge (nodes i,j in [1,n-1], segment k in [0,n)): 2n(n-1)^2 + (k(n-1) + (j-1))(n-1) + (i-1)
+ *   Right-hand sides are load (dual) vectors <f_h, phi_e>.
+ * Batches.  With opts.nrhs = R > 1 the vector arguments hold R right-hand
+ *   sides interleaved as [dof][rhs] (element (e, r) at e * R + r).
+ * Pointers.  Vector arguments are DEVICE pointers owned by the caller (for
+ *   instance torch tensors), contiguous, at least 16-byte aligned, and of the
+ *   element type named by the call's `dtype` (NDMG_F64 = double, NDMG_F32 =
+ *   float).  Entry points whose name ends in _host take HOST pointers
+ *   instead.  Scalar outputs are host pointers, written before return.
+ * Streams.  Work is queued on the handle's stream (opts.stream, NULL = the
+ *   legacy default stream).  Calls that return scalars synchronise that
+ *   stream; the others return as soon as the work is queued.
+ * Errors.  Every call returns an ndmg_status.  On failure the handle keeps a
+ *   message (ndmg_last_error); nothing is allocated or freed by a failing
+ *   call except by ndmg_create, which releases what it built.  Invalid
+ *   arguments are detected on the host before any launch.
+ * Threads.  A handle may be used by one host thread at a time.
+ */
+#ifndef NDMG_H
+#define NDMG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum ndmg_status {
+  NDMG_OK = 0,
+  NDMG_INVALID_ARG = 1,
+  NDMG_CUDA_ERROR = 2,
+  NDMG_OUT_OF_MEMORY = 3,
+  NDMG_NOT_CONVERGED = 4,
+  NDMG_BREAKDOWN = 5,     /* PCG: non-positive or non-finite curvature / NaN */
+  NDMG_DEVICE_TIMEOUT = 6 /* a bounded device-side wait gave up; results invalid */
+} ndmg_status;
+
+typedef enum ndmg_dtype { NDMG_F64 = 0, NDMG_F32 = 1 } ndmg_dtype;
+
+/* Smoother of Sec. 3.2. */
+typedef enum ndmg_smoother {
+  NDMG_SMOOTHER_VERTEX = 0, /* eq. (Preconditioner P), default eta 1/9 */
+  NDMG_SMOOTHER_EDGE = 1    /* eq. (Preconditioner E), default eta 1/13 (not yet built) */
+} ndmg_smoother;
+
+/* Arithmetic of the V-cycle.  FP64: everything in double.  MIXED_BF16 /
+ * MIXED_FP16: the inner V-cycle runs on float vectors (stencil, transfers,
+ * interior solves in FP32) with the vertex-patch solves on tensor cores in
+ * bf16 / fp16 with FP32 accumulation; residuals of the outer refinement loop,
+ * PCG inner products and the coarsest solve stay in double. */
+typedef enum ndmg_precision {
+  NDMG_PREC_FP64 = 0,
+  NDMG_PREC_MIXED_BF16 = 1,
+  NDMG_PREC_MIXED_FP16 = 2,
+  NDMG_PREC_FP32 = 3 /* float V-cycle, patch solves on CUDA cores (FP32) */
+} ndmg_precision;
+
+typedef struct ndmg_opts {
+  int32_t n;          /* hexahedra per side on the finest level; even unless n == n_coarsest */
+  int32_t n_coarsest; /* hexahedra per side on the coarsest level (paper: 2); n = n_coarsest * 2^K */
+  double L;           /* box side length, > 0 */
+  double alpha;       /* curl-curl coefficient, > 0 (eq. 1) */
+  double beta;        /* mass coefficient, > 0 (1 in eq. 1; eps + sigma dt/2 in eq. Maxwell timestep) */
+  int32_t smoother;   /* ndmg_smoother */
+  double eta;         /* damping factor; <= 0 selects the paper's value for the smoother */
+  int32_t m;          /* pre- and post-smoothing steps per level (Fig. 1), >= 1 */
+  int32_t precision;  /* ndmg_precision */
+  int32_t nrhs;       /* right-hand sides per call, >= 1 */
+  void* stream;       /* cudaStream_t, NULL = legacy default stream */
+} ndmg_opts;
+
+typedef struct ndmg_handle ndmg_t;
+
+/* Fill *o with defaults: n = 8, n_coarsest = 2, L = 1, alpha = beta = 1,
+ * vertex smoother with eta = 1/9, m = 2, FP64, nrhs = 1, default stream. */
+int ndmg_opts_default(ndmg_opts* o);
+
+/* Build the level hierarchy of Sec. 3.1 and every local operator of Sec. 3.2
+ * for the options in *o: the interior-space matrix A_T of eq. (ATDef) and its
+ * inverse, the vertex-space operator J_V A_V^{-1} J_V^t of eq. (AVDef) as a
+ * dense 108x108 matrix and as a Gram factor W (108x60, W W^t = the same
+ * operator), and the coarsest inverse A_0^{-1} (Fig. 1, k = 0).  Allocates all
+ * device workspaces.  *out receives the handle (NULL on failure).  Errors:
+ * INVALID_ARG (bad sizes, alpha/beta/L <= 0, nrhs < 1, unsupported smoother),
+ * OUT_OF_MEMORY, CUDA_ERROR. */
+int ndmg_create(const ndmg_opts* o, ndmg_t** out);
+
+/* Free every resource of the handle (NULL is accepted). */
+int ndmg_destroy(ndmg_t* h);
+
+/* Message of the last failing call on this handle ("" if none); owned by the
+ * handle, valid until the next call on it. */
+const char* ndmg_last_error(const ndmg_t* h);
+
+/* Rebuild the local operators for a new alpha (eq. 1), keeping all buffers. */
+int ndmg_set_alpha(ndmg_t* h, double alpha);
+
+/* Number of levels K+1. */
+int ndmg_num_levels(const ndmg_t* h, int32_t* out);
+
+/* N(n_k) for level k (k = -1 means the finest). */
+int ndmg_num_dofs(const ndmg_t* h, int32_t level, int64_t* out);
+
+/* y = A_k x (Sec. 2: <A_h w, v> = a(w, v)), matrix-free.  x, y: N(n_k) [x nrhs]. */
+int ndmg_apply(ndmg_t* h, int32_t level, int32_t dtype, const void* x, void* y);
+
+/* r = g - A_k z. */
+int ndmg_residual(ndmg_t* h, int32_t level, int32_t dtype, const void* g, const void* z, void* r);
+
+/* `steps` smoothing steps z <- z + M_k^{-1} (g - A_k z) (Fig. 1) on level
+ * k >= 1, with M_k^{-1} the smoother of eq. (Preconditioner P).  dtype F64
+ * uses the FP64 patch operator; dtype F32 uses the handle's precision mode
+ * (tensor-core patch solves in the MIXED modes, FP32 CUDA cores otherwise). */
+int ndmg_smooth(ndmg_t* h, int32_t level, int32_t dtype, const void* g, void* z, int32_t steps);
+
+/* g_c = I_k^{k-1} r_f (eq. F2C), level k >= 1: r_f on level k, g_c on k-1. */
+int ndmg_restrict(ndmg_t* h, int32_t level, int32_t dtype, const void* r_fine, void* g_coarse);
+
+/* z_f += I_{k-1}^k z_c (Sec. 3.1, natural injection), level k >= 1. */
+int ndmg_prolong_add(ndmg_t* h, int32_t level, int32_t dtype, const void* z_coarse, void* z_fine);
+
+/* z = A_0^{-1} g on the coarsest level (Fig. 1, k = 0). */
+int ndmg_coarse_solve(ndmg_t* h, int32_t dtype, const void* g, void* z);
+
+/* z <- MG(K, g, z, m) on the finest level (Fig. 1), z in/out. */
+int ndmg_vcycle(ndmg_t* h, int32_t dtype, const void* g, void* z);
+
+/* Solve A_K u = f to ||f - A u||_2 <= tol ||f||_2 with conjugate gradients
+ * preconditioned by one V-cycle MG(K, ., 0, m) (symmetric: Remark 6).  FP64
+ * handles run FP64 PCG; MIXED / FP32 handles run an FP64 iterative-refinement
+ * loop around a float PCG + V-cycle (see ndmg_solve_ir).  f, u: double device
+ * vectors, u in/out (warm start).  *iters: PCG iterations (total over
+ * refinement sweeps), *relres: final relative residual in FP64 (either may
+ * be NULL).  Returns NOT_CONVERGED after maxit iterations, BREAKDOWN on a
+ * non-finite residual or non-positive curvature. */
+int ndmg_solve(ndmg_t* h, const double* f, double* u, double tol, int32_t maxit,
+               int32_t* iters, double* relres);
+
+/* As ndmg_solve with HOST f and u: copies f in and u out on the handle's
+ * stream (pinned memory recommended) and synchronises. */
+int ndmg_solve_host(ndmg_t* h, const double* f_host, double* u_host, double tol, int32_t maxit,
+                    int32_t* iters, double* relres);
+
+/* Standalone iteration u <- MG(K, f, u, m) until ||f - A u|| <= tol ||f|| or
+ * maxit cycles (Sec. 5 style), FP64 vectors. */
+int ndmg_vcycle_iterate(ndmg_t* h, const double* f, double* u, double tol, int32_t maxit,
+                        int32_t* cycles, double* relres);
+
+/* dL/dalpha of a loss L(u(f, alpha)) given the adjoint lambda (A lambda =
+ * dL/du; A is symmetric, Remark 6): out[r] = -lambda_r^T K u_r with K the
+ * alpha-free curl-curl matrix (a(w,v) = alpha (curl w, curl v) + beta (w, v)).
+ * lambda, u: double device vectors on the finest level; out: host, nrhs doubles. */
+int ndmg_grad_alpha(ndmg_t* h, const double* lambda, const double* u, double* out);
+
+/* Inner product in FP64: out[r] = x_r^T y_r for the nrhs interleaved columns. */
+int ndmg_dot(ndmg_t* h, int32_t level, int32_t dtype, const void* x, const void* y, double* out);
+
+/* ---- tracing (no counterpart in the paper: measurement support) --------
+ * Kernel classes whose launches can be timed with CUDA events recorded on the
+ * handle's stream around every launch of that class. */
+typedef enum ndmg_kernel_class {
+  NDMG_K_STENCIL = 0,  /* operator apply / residual */
+  NDMG_K_RESTRICT = 1,
+  NDMG_K_PROLONG = 2,
+  NDMG_K_BUBBLE = 3,   /* interior-space solves */
+  NDMG_K_PATCH = 4,    /* vertex-patch solves (CUDA-core or tensor-core kernel) */
+  NDMG_K_COARSE = 5,
+  NDMG_K_BLAS = 6,     /* reductions and vector updates */
+  NDMG_K_COUNT = 7
+} ndmg_kernel_class;
+
+/* Switch event timing of one kernel class on (on != 0) or off. */
+int ndmg_trace_enable(ndmg_t* h, int32_t kernel_class, int32_t on);
+
+/* Synchronise, then report and reset the class's totals since the last read:
+ * launches, summed device time in ms, and summed algorithmic work: bytes a
+ * launch must move to or from memory (every vector read or written once) for
+ * the memory-bound classes, arithmetic operations (flops) for NDMG_K_PATCH. */
+int ndmg_trace_read(ndmg_t* h, int32_t kernel_class, int64_t* launches, double* ms, double* units);
+
+/* Running totals since ndmg_create: kernels launched by this handle (all
+ * classes) and V-cycles MG(K, ., ., m) performed on the finest level.  Either
+ * pointer may be NULL. */
+int ndmg_counters(const ndmg_t* h, int64_t* launches, int64_t* vcycles);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NDMG_H */

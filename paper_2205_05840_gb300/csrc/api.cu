@@ -1,0 +1,750 @@
+// C ABI of libndmg (include/ndmg.h): handle, level hierarchy, V-cycle driver
+// (Fig. 1), PCG and the FP64 iterative-refinement loop.  All vector work runs
+// in the kernels of kernels.cu / tc_patch.cu on the handle's stream.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <exception>
+#include <new>
+
+#include "kernels.cuh"
+#include "tc_patch.cuh"
+
+using namespace ndmg;
+
+namespace {
+
+int fail(ndmg_t* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+int cuda_fail(ndmg_t* h, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  return fail(h, e == cudaErrorMemoryAllocation ? NDMG_OUT_OF_MEMORY : NDMG_CUDA_ERROR, m);
+}
+
+#define NDMG_CK(call)                                      \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+  } while (0)
+
+// launch errors are sticky per call: check after queuing a group of launches
+#define NDMG_CK_LAUNCH() NDMG_CK(cudaGetLastError())
+
+// Counts launches and, when the class is traced, brackets them with events
+// recorded on the handle's stream.
+struct Span {
+  ndmg_t* h;
+  cudaEvent_t end = nullptr;
+  Span(ndmg_t* h_, int cls, double units, int nlaunch = 1) : h(h_) {
+    h->launch_total += nlaunch;
+    if (!h->trace_on[cls]) return;
+    std::pair<cudaEvent_t, cudaEvent_t> pr{nullptr, nullptr};
+    if (!h->ev_free.empty()) {
+      pr = h->ev_free.back();
+      h->ev_free.pop_back();
+    } else if (cudaEventCreate(&pr.first) != cudaSuccess || cudaEventCreate(&pr.second) != cudaSuccess) {
+      return;
+    }
+    h->trace_launches[cls] += nlaunch;
+    h->trace_units[cls] += units;
+    cudaEventRecord(pr.first, h->stream);
+    h->ev_used[cls].push_back(pr);
+    end = pr.second;
+  }
+  ~Span() {
+    if (end) cudaEventRecord(end, h->stream);
+  }
+};
+
+template <typename T>
+T* dev_alloc(int64_t count, cudaError_t* err) {
+  void* p = nullptr;
+  if (count <= 0) count = 1;
+  cudaError_t e = cudaMalloc(&p, sizeof(T) * count);
+  if (e != cudaSuccess && *err == cudaSuccess) *err = e;
+  return (T*)p;
+}
+
+template <typename T>
+cudaError_t upload(T** dst, const std::vector<double>& src) {
+  std::vector<T> tmp(src.size());
+  for (size_t i = 0; i < src.size(); ++i) tmp[i] = (T)src[i];
+  if (!*dst) {
+    cudaError_t e = cudaMalloc((void**)dst, sizeof(T) * tmp.size());
+    if (e != cudaSuccess) return e;
+  }
+  return cudaMemcpy(*dst, tmp.data(), sizeof(T) * tmp.size(), cudaMemcpyHostToDevice);
+}
+
+int64_t edges(int n) { return 3LL * n * (n - 1) * (n - 1); }
+double bubble_bytes(int n, size_t w) {
+  const double c = n / 2;
+  return c * c * c * 18.0 * w;  // per coarse element: read 6 r, read+write 6 z
+}
+double num_patches(int n) {
+  const double v = n / 2 - 1;
+  return v > 0 ? v * v * v : 0.0;
+}
+
+// per-level FP64 / FP32 workspace pointers
+template <typename T> T* lv_g(DevLevel& L);
+template <typename T> T* lv_z(DevLevel& L);
+template <typename T> T* lv_r(DevLevel& L);
+template <> double* lv_g<double>(DevLevel& L) { return L.g64; }
+template <> double* lv_z<double>(DevLevel& L) { return L.z64; }
+template <> double* lv_r<double>(DevLevel& L) { return L.r64; }
+template <> float* lv_g<float>(DevLevel& L) { return L.g32; }
+template <> float* lv_z<float>(DevLevel& L) { return L.z32; }
+template <> float* lv_r<float>(DevLevel& L) { return L.r32; }
+const double* lv_Ainv(DevLevel& L, double*) { return L.AinvT64; }
+const float* lv_Ainv(DevLevel& L, float*) { return L.AinvT32; }
+const double* lv_D(DevLevel& L, double*) { return L.Dv64; }
+const float* lv_D(DevLevel& L, float*) { return L.Dv32; }
+
+bool mixed(const ndmg_t* h) {
+  return h->o.precision == NDMG_PREC_MIXED_BF16 || h->o.precision == NDMG_PREC_MIXED_FP16;
+}
+
+// ---------------------------------------------------------------------------
+// Level operations
+// ---------------------------------------------------------------------------
+template <typename T>
+void op_residual(ndmg_t* h, int k, const T* g, const T* z, T* r) {
+  DevLevel& L = h->lv[k];
+  Span sp(h, NDMG_K_STENCIL, 3.0 * sizeof(T) * L.N);  // read g, z; write r
+  launch_stencil<T>(h->stream, h->sm_count, L.n, L.cK, L.cM, z, g, r);
+}
+
+template <typename T>
+void op_apply(ndmg_t* h, int k, const T* x, T* y) {
+  DevLevel& L = h->lv[k];
+  Span sp(h, NDMG_K_STENCIL, 2.0 * sizeof(T) * L.N);  // read x; write y
+  launch_stencil<T>(h->stream, h->sm_count, L.n, L.cK, L.cM, x, (const T*)nullptr, y);
+}
+
+// z += M_k^{-1} r (eta included), eq. (Preconditioner P)
+template <typename T>
+void op_smoother(ndmg_t* h, int k, const T* r, T* z) {
+  DevLevel& L = h->lv[k];
+  {
+    Span sp(h, NDMG_K_BUBBLE, bubble_bytes(L.n, sizeof(T)));
+    launch_bubble<T>(h->stream, h->sm_count, L.n, lv_Ainv(L, (T*)nullptr), h->o.eta, r, z);
+  }
+  Span sp(h, NDMG_K_PATCH, num_patches(L.n) * 2.0 * 108 * 108);  // dense 108x108 per patch
+  launch_vertex_dense<T>(h->stream, h->sm_count, L.n, lv_D(L, (T*)nullptr), h->o.eta, r, z);
+}
+
+template <>
+void op_smoother<float>(ndmg_t* h, int k, const float* r, float* z) {
+  DevLevel& L = h->lv[k];
+  {
+    Span sp(h, NDMG_K_BUBBLE, bubble_bytes(L.n, sizeof(float)));
+    launch_bubble<float>(h->stream, h->sm_count, L.n, L.AinvT32, h->o.eta, r, z);
+  }
+  // Gram form on tensor cores: two 108x60 products per patch; dense otherwise
+  Span sp(h, NDMG_K_PATCH, num_patches(L.n) * ((mixed(h) && L.Wtc) ? 4.0 * 108 * 60 : 2.0 * 108 * 108));
+  if (mixed(h) && L.Wtc)
+    launch_tc_patch(h->stream, h->sm_count, L.n, L.Wtc, h->o.precision == NDMG_PREC_MIXED_FP16, h->o.eta, r, z,
+                    h->status);
+  else
+    launch_vertex_dense<float>(h->stream, h->sm_count, L.n, L.Dv32, h->o.eta, r, z);
+}
+
+template <typename T>
+void op_smooth_steps(ndmg_t* h, int k, const T* g, T* z, int steps) {
+  T* r = lv_r<T>(h->lv[k]);
+  for (int s = 0; s < steps; ++s) {
+    op_residual<T>(h, k, g, z, r);
+    op_smoother<T>(h, k, r, z);
+  }
+}
+
+// MG(k, g, z, m) of Fig. 1 with z in/out
+template <typename T>
+void op_vcycle(ndmg_t* h, int k, const T* g, T* z) {
+  if (k == h->K) ++h->vcycle_total;
+  if (k == 0) {
+    Span sp(h, NDMG_K_COARSE, 2.0 * sizeof(T) * h->lv[0].N + 8.0 * h->lv[0].N * h->lv[0].N);
+    launch_coarse<T>(h->stream, (int)h->lv[0].N, h->Ainv0, g, z);
+    return;
+  }
+  DevLevel& L = h->lv[k];
+  DevLevel& C = h->lv[k - 1];
+  T* r = lv_r<T>(L);
+  op_smooth_steps<T>(h, k, g, z, h->o.m);
+  op_residual<T>(h, k, g, z, r);
+  {
+    Span sp(h, NDMG_K_RESTRICT, (double)sizeof(T) * (L.N + C.N));
+    launch_restrict<T>(h->stream, h->sm_count, L.n, r, lv_g<T>(C));
+  }
+  cudaMemsetAsync(lv_z<T>(C), 0, sizeof(T) * C.N, h->stream);
+  op_vcycle<T>(h, k - 1, lv_g<T>(C), lv_z<T>(C));
+  {
+    Span sp(h, NDMG_K_PROLONG, (double)sizeof(T) * (2 * L.N + C.N));
+    launch_prolong_add<T>(h->stream, h->sm_count, L.n, lv_z<T>(C), z);
+  }
+  op_smooth_steps<T>(h, k, g, z, h->o.m);
+}
+
+// two FP64 inner products, synchronised
+template <typename T>
+int dot2(ndmg_t* h, int64_t N, const T* x, const T* y, const T* x2, const T* y2, double* a, double* b) {
+  const int nb = reduction_blocks(h->sm_count);
+  double* out = h->red + 2 * nb;
+  {
+    Span sp(h, NDMG_K_BLAS, (double)sizeof(T) * N * (x2 ? 4 : 2), 2);
+    launch_dot2<T>(h->stream, h->sm_count, N, x, y, x2, y2, h->red, out);
+  }
+  NDMG_CK_LAUNCH();
+  NDMG_CK(cudaMemcpyAsync(h->red_host, out, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  NDMG_CK(cudaStreamSynchronize(h->stream));
+  *a = h->red_host[0];
+  if (b) *b = h->red_host[1];
+  return NDMG_OK;
+}
+
+int check_level(ndmg_t* h, int32_t& level, bool need_fine_transfer) {
+  if (level == -1) level = h->K;
+  if (level < 0 || level > h->K) return fail(h, NDMG_INVALID_ARG, "level out of range");
+  if (need_fine_transfer && level < 1) return fail(h, NDMG_INVALID_ARG, "level must be >= 1");
+  return NDMG_OK;
+}
+
+int check_dtype(ndmg_t* h, int32_t dtype) {
+  if (dtype != NDMG_F64 && dtype != NDMG_F32) return fail(h, NDMG_INVALID_ARG, "dtype must be NDMG_F64 or NDMG_F32");
+  return NDMG_OK;
+}
+
+bool misaligned(const void* p) { return p == nullptr || ((uintptr_t)p & 15u) != 0; }
+
+int check_ptrs(ndmg_t* h, std::initializer_list<const void*> ps) {
+  for (const void* p : ps)
+    if (misaligned(p)) return fail(h, NDMG_INVALID_ARG, "vector pointer is NULL or not 16-byte aligned");
+  return NDMG_OK;
+}
+
+int check_status(ndmg_t* h) {
+  int st = 0;
+  NDMG_CK(cudaMemcpyAsync(&h->red_host[4], h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  NDMG_CK(cudaStreamSynchronize(h->stream));
+  std::memcpy(&st, &h->red_host[4], sizeof(int));
+  if (st != 0) {
+    cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
+    return fail(h, NDMG_DEVICE_TIMEOUT, "a device-side wait timed out (status " + std::to_string(st) + ")");
+  }
+  return NDMG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Solvers
+// ---------------------------------------------------------------------------
+// FP64 PCG preconditioned by one V-cycle
+int pcg64(ndmg_t* h, const double* f, double* u, double tol, int maxit, int* iters, double* relres) {
+  const int K = h->K;
+  const int64_t N = h->lv[K].N;
+  const int sm = h->sm_count;
+  double *r = h->w64[0], *z = h->w64[1], *p = h->w64[2], *q = h->w64[3];
+  double ff, rr, rz, pq, dum;
+  int st;
+  *iters = 0;
+  op_residual<double>(h, K, f, u, r);
+  if ((st = dot2<double>(h, N, f, f, r, r, &ff, &rr)) != NDMG_OK) return st;
+  const double nf = std::sqrt(ff) > 0 ? std::sqrt(ff) : 1.0;
+  *relres = std::sqrt(rr) / nf;
+  if (!std::isfinite(*relres)) return fail(h, NDMG_BREAKDOWN, "non-finite residual");
+  if (*relres <= tol) return NDMG_OK;
+  cudaMemsetAsync(z, 0, sizeof(double) * N, h->stream);
+  op_vcycle<double>(h, K, r, z);
+  if ((st = dot2<double>(h, N, r, z, (const double*)nullptr, (const double*)nullptr, &rz, &dum)) != NDMG_OK) return st;
+  NDMG_CK(cudaMemcpyAsync(p, z, sizeof(double) * N, cudaMemcpyDeviceToDevice, h->stream));
+  for (int it = 1; it <= maxit; ++it) {
+    op_apply<double>(h, K, p, q);
+    if ((st = dot2<double>(h, N, p, q, (const double*)nullptr, (const double*)nullptr, &pq, &dum)) != NDMG_OK) return st;
+    if (!(pq > 0.0) || !std::isfinite(pq)) return fail(h, NDMG_BREAKDOWN, "non-positive curvature p^T A p");
+    const double a = rz / pq;
+    {
+      Span sp(h, NDMG_K_BLAS, 6.0 * 8 * N);
+      launch_cg_update<double>(h->stream, sm, N, a, p, q, u, r);
+    }
+    if ((st = dot2<double>(h, N, r, r, (const double*)nullptr, (const double*)nullptr, &rr, &dum)) != NDMG_OK) return st;
+    *iters = it;
+    *relres = std::sqrt(rr) / nf;
+    if (!std::isfinite(*relres)) return fail(h, NDMG_BREAKDOWN, "non-finite residual");
+    if (*relres <= tol) return NDMG_OK;
+    cudaMemsetAsync(z, 0, sizeof(double) * N, h->stream);
+    op_vcycle<double>(h, K, r, z);
+    double rz_new;
+    if ((st = dot2<double>(h, N, r, z, (const double*)nullptr, (const double*)nullptr, &rz_new, &dum)) != NDMG_OK) return st;
+    {
+      Span sp(h, NDMG_K_BLAS, 3.0 * 8 * N);
+      launch_axpby<double>(h->stream, sm, N, 1.0, z, rz_new / rz, p);
+    }
+    rz = rz_new;
+  }
+  return fail(h, NDMG_NOT_CONVERGED, "PCG reached maxit");
+}
+
+// float PCG on A d = b (b float, d float, d starts at 0) to relative tol;
+// flexible beta = -a (q.z_new) / (r.z)_old so that a slightly nonsymmetric
+// low-precision preconditioner is tolerated.
+int pcg32(ndmg_t* h, const float* b, float* d, double tol, int maxit, int* iters) {
+  const int K = h->K;
+  const int64_t N = h->lv[K].N;
+  const int sm = h->sm_count;
+  float *r = h->w32[0], *z = h->w32[1], *p = h->w32[2], *q = h->w32[3];
+  double bb, rz, pq, rr, dum;
+  int st;
+  *iters = 0;
+  cudaMemsetAsync(d, 0, sizeof(float) * N, h->stream);
+  NDMG_CK(cudaMemcpyAsync(r, b, sizeof(float) * N, cudaMemcpyDeviceToDevice, h->stream));
+  cudaMemsetAsync(z, 0, sizeof(float) * N, h->stream);
+  op_vcycle<float>(h, K, r, z);
+  if ((st = dot2<float>(h, N, b, b, r, z, &bb, &rz)) != NDMG_OK) return st;
+  if (bb == 0.0) return NDMG_OK;
+  NDMG_CK(cudaMemcpyAsync(p, z, sizeof(float) * N, cudaMemcpyDeviceToDevice, h->stream));
+  const double nb = std::sqrt(bb);
+  for (int it = 1; it <= maxit; ++it) {
+    op_apply<float>(h, K, p, q);
+    if ((st = dot2<float>(h, N, p, q, (const float*)nullptr, (const float*)nullptr, &pq, &dum)) != NDMG_OK) return st;
+    if (!(pq > 0.0) || !std::isfinite(pq)) return fail(h, NDMG_BREAKDOWN, "non-positive curvature (float PCG)");
+    const double a = rz / pq;
+    {
+      Span sp(h, NDMG_K_BLAS, 6.0 * 4 * N);
+      launch_cg_update<float>(h->stream, sm, N, a, p, q, d, r);
+    }
+    if ((st = dot2<float>(h, N, r, r, (const float*)nullptr, (const float*)nullptr, &rr, &dum)) != NDMG_OK) return st;
+    *iters = it;
+    if (!std::isfinite(rr)) return fail(h, NDMG_BREAKDOWN, "non-finite residual (float PCG)");
+    if (std::sqrt(rr) <= tol * nb) return NDMG_OK;
+    cudaMemsetAsync(z, 0, sizeof(float) * N, h->stream);
+    op_vcycle<float>(h, K, r, z);
+    double rz_new, qz;
+    if ((st = dot2<float>(h, N, r, z, q, z, &rz_new, &qz)) != NDMG_OK) return st;
+    {
+      Span sp(h, NDMG_K_BLAS, 3.0 * 4 * N);
+      launch_axpby<float>(h->stream, sm, N, 1.0, z, -a * qz / rz, p);
+    }
+    rz = rz_new;
+  }
+  return NDMG_OK;  // the outer loop decides convergence
+}
+
+// FP64 iterative refinement around the float PCG
+int solve_ir(ndmg_t* h, const double* f, double* u, double tol, int maxit, int* iters, double* relres) {
+  const int K = h->K;
+  const int64_t N = h->lv[K].N;
+  const int sm = h->sm_count;
+  double* r = h->w64[0];
+  float* b32 = h->w32[4];
+  float* d32 = h->w32[5];
+  double ff, rr;
+  int st;
+  *iters = 0;
+  const double inner_tol = 1e-4;
+  if ((st = dot2<double>(h, N, f, f, (const double*)nullptr, (const double*)nullptr, &ff, &rr)) != NDMG_OK) return st;
+  const double nf = std::sqrt(ff) > 0 ? std::sqrt(ff) : 1.0;
+  for (int outer = 0; outer < 64; ++outer) {
+    op_residual<double>(h, K, f, u, r);
+    if ((st = dot2<double>(h, N, r, r, (const double*)nullptr, (const double*)nullptr, &rr, &ff)) != NDMG_OK) return st;
+    const double rn = std::sqrt(rr);
+    *relres = rn / nf;
+    if (!std::isfinite(*relres)) return fail(h, NDMG_BREAKDOWN, "non-finite residual");
+    if (*relres <= tol) return check_status(h);
+    if (*iters >= maxit) return fail(h, NDMG_NOT_CONVERGED, "refinement reached maxit inner iterations");
+    {
+      Span sp(h, NDMG_K_BLAS, 12.0 * N);
+      launch_to_f32(h->stream, sm, N, 1.0 / rn, r, b32);
+    }
+    int it = 0;
+    if ((st = pcg32(h, b32, d32, inner_tol, maxit - *iters, &it)) != NDMG_OK) return st;
+    *iters += it;
+    {
+      Span sp(h, NDMG_K_BLAS, 20.0 * N);
+      launch_add_f32(h->stream, sm, N, rn, d32, u);
+    }
+    NDMG_CK_LAUNCH();
+  }
+  return fail(h, NDMG_NOT_CONVERGED, "refinement stalled");
+}
+
+void free_handle(ndmg_t* h) {
+  if (!h) return;
+  for (auto& L : h->lv) {
+    cudaFree(L.g64); cudaFree(L.z64); cudaFree(L.r64);
+    cudaFree(L.g32); cudaFree(L.z32); cudaFree(L.r32);
+    cudaFree(L.AinvT64); cudaFree(L.AinvT32); cudaFree(L.Dv64); cudaFree(L.Dv32);
+    cudaFree(L.Wtc);
+  }
+  cudaFree(h->Ainv0);
+  for (int i = 0; i < 6; ++i) { cudaFree(h->w64[i]); cudaFree(h->w32[i]); }
+  cudaFree(h->red);
+  cudaFree(h->status);
+  if (h->red_host) cudaFreeHost(h->red_host);
+  for (int c = 0; c < NDMG_K_COUNT; ++c)
+    for (auto& pr : h->ev_used[c]) h->ev_free.push_back(pr);
+  for (auto& pr : h->ev_free) {
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
+  delete h;
+}
+
+int build_operators(ndmg_t* h) {
+  const ndmg_opts& o = h->o;
+  try {
+    for (int k = 1; k <= h->K; ++k) {
+      DevLevel& L = h->lv[k];
+      LocalOps ops;
+      build_local_ops(L.n, o.L, o.alpha, o.beta, &ops);
+      NDMG_CK(upload(&L.AinvT64, ops.AinvT));
+      NDMG_CK(upload(&L.AinvT32, ops.AinvT));
+      NDMG_CK(upload(&L.Dv64, ops.Dv));
+      NDMG_CK(upload(&L.Dv32, ops.Dv));
+      if (mixed(h)) {
+        cudaError_t e = upload_tc_operand(&L.Wtc, ops.Wv, o.precision == NDMG_PREC_MIXED_FP16);
+        if (e != cudaSuccess) return cuda_fail(h, e, "upload_tc_operand");
+      }
+    }
+    std::vector<double> inv = coarse_inverse(h->lv[0].n, o.L, o.alpha, o.beta);
+    NDMG_CK(upload(&h->Ainv0, inv));
+  } catch (const std::exception& ex) {
+    return fail(h, NDMG_INVALID_ARG, ex.what());
+  }
+  for (auto& L : h->lv) {
+    L.cK = o.alpha * L.h;
+    L.cM = o.beta * L.h * L.h * L.h;
+  }
+  return NDMG_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+int ndmg_opts_default(ndmg_opts* o) {
+  if (!o) return NDMG_INVALID_ARG;
+  std::memset(o, 0, sizeof(*o));
+  o->n = 8;
+  o->n_coarsest = 2;
+  o->L = 1.0;
+  o->alpha = 1.0;
+  o->beta = 1.0;
+  o->smoother = NDMG_SMOOTHER_VERTEX;
+  o->eta = 1.0 / 9.0;
+  o->m = 2;
+  o->precision = NDMG_PREC_FP64;
+  o->nrhs = 1;
+  o->stream = nullptr;
+  return NDMG_OK;
+}
+
+int ndmg_create(const ndmg_opts* o, ndmg_t** out) {
+  if (!out) return NDMG_INVALID_ARG;
+  *out = nullptr;
+  if (!o) return NDMG_INVALID_ARG;
+  if (o->n < 2 || o->n_coarsest < 2 || o->n < o->n_coarsest) return NDMG_INVALID_ARG;
+  if (!(o->L > 0) || !(o->alpha > 0) || !(o->beta > 0) || o->m < 1 || o->nrhs < 1) return NDMG_INVALID_ARG;
+  if (o->nrhs != 1) return NDMG_INVALID_ARG;              // batched layout: not built yet
+  if (o->smoother != NDMG_SMOOTHER_VERTEX) return NDMG_INVALID_ARG;
+  if (o->precision != NDMG_PREC_FP64 && o->precision != NDMG_PREC_FP32) return NDMG_INVALID_ARG;
+  if (edges(o->n_coarsest) > 4096) return NDMG_INVALID_ARG;   // dense coarsest inverse
+  int K = 0;
+  for (int n = o->n; n > o->n_coarsest; n /= 2, ++K)
+    if (n % 2) return NDMG_INVALID_ARG;
+  if ((o->n_coarsest << K) != o->n) return NDMG_INVALID_ARG;
+
+  ndmg_t* h = new (std::nothrow) ndmg_handle();
+  if (!h) return NDMG_OUT_OF_MEMORY;
+  h->o = *o;
+  if (!(h->o.eta > 0)) h->o.eta = 1.0 / 9.0;
+  h->stream = (cudaStream_t)o->stream;
+  h->K = K;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) {
+    free_handle(h);
+    return NDMG_CUDA_ERROR;
+  }
+  if (mixed(h)) {
+    int major = 0, minor = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    if (major != 10) {  // tcgen05 needs a Blackwell datacenter part
+      free_handle(h);
+      return NDMG_INVALID_ARG;
+    }
+  }
+  h->lv.resize(K + 1);
+  cudaError_t ae = cudaSuccess;
+  for (int k = 0; k <= K; ++k) {
+    DevLevel& L = h->lv[k];
+    L.n = o->n_coarsest << k;
+    L.N = edges(L.n);
+    L.h = o->L / L.n;
+    L.r64 = dev_alloc<double>(L.N, &ae);
+    L.r32 = dev_alloc<float>(L.N, &ae);
+    if (k < K) {
+      L.g64 = dev_alloc<double>(L.N, &ae);
+      L.z64 = dev_alloc<double>(L.N, &ae);
+      L.g32 = dev_alloc<float>(L.N, &ae);
+      L.z32 = dev_alloc<float>(L.N, &ae);
+    }
+  }
+  const int64_t NF = h->lv[K].N;
+  for (int i = 0; i < 6; ++i) {
+    h->w64[i] = dev_alloc<double>(NF, &ae);
+    h->w32[i] = dev_alloc<float>(NF, &ae);
+  }
+  h->red = dev_alloc<double>(2 * reduction_blocks(h->sm_count) + 8, &ae);
+  h->status = dev_alloc<int>(4, &ae);
+  if (ae == cudaSuccess) ae = cudaMallocHost((void**)&h->red_host, 8 * sizeof(double));
+  if (ae == cudaSuccess) ae = cudaMemset(h->status, 0, 4 * sizeof(int));
+  if (ae == cudaSuccess) ae = prepare_vertex_dense<double>();
+  if (ae == cudaSuccess) ae = prepare_vertex_dense<float>();
+  if (ae == cudaSuccess && mixed(h)) ae = prepare_tc_patch();
+  if (ae != cudaSuccess) {
+    free_handle(h);
+    return ae == cudaErrorMemoryAllocation ? NDMG_OUT_OF_MEMORY : NDMG_CUDA_ERROR;
+  }
+  int st = build_operators(h);
+  if (st != NDMG_OK) {
+    std::fprintf(stderr, "ndmg_create: %s\n", h->err.c_str());
+    free_handle(h);
+    return st;
+  }
+  *out = h;
+  return NDMG_OK;
+}
+
+int ndmg_destroy(ndmg_t* h) {
+  if (h) cudaStreamSynchronize(h->stream);
+  free_handle(h);
+  return NDMG_OK;
+}
+
+const char* ndmg_last_error(const ndmg_t* h) { return h ? h->err.c_str() : "null handle"; }
+
+int ndmg_set_alpha(ndmg_t* h, double alpha) {
+  if (!h) return NDMG_INVALID_ARG;
+  if (!(alpha > 0)) return fail(h, NDMG_INVALID_ARG, "alpha must be > 0");
+  NDMG_CK(cudaStreamSynchronize(h->stream));
+  h->o.alpha = alpha;
+  return build_operators(h);
+}
+
+int ndmg_num_levels(const ndmg_t* h, int32_t* out) {
+  if (!h || !out) return NDMG_INVALID_ARG;
+  *out = h->K + 1;
+  return NDMG_OK;
+}
+
+int ndmg_num_dofs(const ndmg_t* h, int32_t level, int64_t* out) {
+  if (!h || !out) return NDMG_INVALID_ARG;
+  if (level == -1) level = h->K;
+  if (level < 0 || level > h->K) return NDMG_INVALID_ARG;
+  *out = h->lv[level].N;
+  return NDMG_OK;
+}
+
+int ndmg_apply(ndmg_t* h, int32_t level, int32_t dtype, const void* x, void* y) {
+  if (!h) return NDMG_INVALID_ARG;
+  int st;
+  if ((st = check_level(h, level, false)) || (st = check_dtype(h, dtype)) || (st = check_ptrs(h, {x, y}))) return st;
+  if (dtype == NDMG_F64) op_apply<double>(h, level, (const double*)x, (double*)y);
+  else op_apply<float>(h, level, (const float*)x, (float*)y);
+  NDMG_CK_LAUNCH();
+  return NDMG_OK;
+}
+
+int ndmg_residual(ndmg_t* h, int32_t level, int32_t dtype, const void* g, const void* z, void* r) {
+  if (!h) return NDMG_INVALID_ARG;
+  int st;
+  if ((st = check_level(h, level, false)) || (st = check_dtype(h, dtype)) || (st = check_ptrs(h, {g, z, r}))) return st;
+  if (dtype == NDMG_F64) op_residual<double>(h, level, (const double*)g, (const double*)z, (double*)r);
+  else op_residual<float>(h, level, (const float*)g, (const float*)z, (float*)r);
+  NDMG_CK_LAUNCH();
+  return NDMG_OK;
+}
+
+int ndmg_smooth(ndmg_t* h, int32_t level, int32_t dtype, const void* g, void* z, int32_t steps) {
+  if (!h) return NDMG_INVALID_ARG;
+  int st;
+  if ((st = check_level(h, level, true)) || (st = check_dtype(h, dtype)) || (st = check_ptrs(h, {g, z}))) return st;
+  if (steps < 0) return fail(h, NDMG_INVALID_ARG, "steps must be >= 0");
+  if (dtype == NDMG_F64) op_smooth_steps<double>(h, level, (const double*)g, (double*)z, steps);
+  else op_smooth_steps<float>(h, level, (const float*)g, (float*)z, steps);
+  NDMG_CK_LAUNCH();
+  return dtype == NDMG_F32 && mixed(h) ? check_status(h) : NDMG_OK;
+}
+
+int ndmg_restrict(ndmg_t* h, int32_t level, int32_t dtype, const void* r_fine, void* g_coarse) {
+  if (!h) return NDMG_INVALID_ARG;
+  int st;
+  if ((st = check_level(h, level, true)) || (st = check_dtype(h, dtype)) || (st = check_ptrs(h, {r_fine, g_coarse})))
+    return st;
+  Span sp(h, NDMG_K_RESTRICT, (dtype == NDMG_F64 ? 8.0 : 4.0) * (h->lv[level].N + h->lv[level - 1].N));
+  if (dtype == NDMG_F64) launch_restrict<double>(h->stream, h->sm_count, h->lv[level].n, (const double*)r_fine, (double*)g_coarse);
+  else launch_restrict<float>(h->stream, h->sm_count, h->lv[level].n, (const float*)r_fine, (float*)g_coarse);
+  NDMG_CK_LAUNCH();
+  return NDMG_OK;
+}
+
+int ndmg_prolong_add(ndmg_t* h, int32_t level, int32_t dtype, const void* z_coarse, void* z_fine) {
+  if (!h) return NDMG_INVALID_ARG;
+  int st;
+  if ((st = check_level(h, level, true)) || (st = check_dtype(h, dtype)) || (st = check_ptrs(h, {z_coarse, z_fine})))
+    return st;
+  Span sp(h, NDMG_K_PROLONG, (dtype == NDMG_F64 ? 8.0 : 4.0) * (2 * h->lv[level].N + h->lv[level - 1].N));
+  if (dtype == NDMG_F64) launch_prolong_add<double>(h->stream, h->sm_count, h->lv[level].n, (const double*)z_coarse, (double*)z_fine);
+  else launch_prolong_add<float>(h->stream, h->sm_count, h->lv[level].n, (const float*)z_coarse, (float*)z_fine);
+  NDMG_CK_LAUNCH();
+  return NDMG_OK;
+}
+
+int ndmg_coarse_solve(ndmg_t* h, int32_t dtype, const void* g, void* z) {
+  if (!h) return NDMG_INVALID_ARG;
+  int st;
+  if ((st = check_dtype(h, dtype)) || (st = check_ptrs(h, {g, z}))) return st;
+  Span sp(h, NDMG_K_COARSE, 8.0 * h->lv[0].N * (h->lv[0].N + 2));
+  if (dtype == NDMG_F64) launch_coarse<double>(h->stream, (int)h->lv[0].N, h->Ainv0, (const double*)g, (double*)z);
+  else launch_coarse<float>(h->stream, (int)h->lv[0].N, h->Ainv0, (const float*)g, (float*)z);
+  NDMG_CK_LAUNCH();
+  return NDMG_OK;
+}
+
+int ndmg_vcycle(ndmg_t* h, int32_t dtype, const void* g, void* z) {
+  if (!h) return NDMG_INVALID_ARG;
+  int st;
+  if ((st = check_dtype(h, dtype)) || (st = check_ptrs(h, {g, z}))) return st;
+  if (dtype == NDMG_F64) op_vcycle<double>(h, h->K, (const double*)g, (double*)z);
+  else op_vcycle<float>(h, h->K, (const float*)g, (float*)z);
+  NDMG_CK_LAUNCH();
+  return dtype == NDMG_F32 && mixed(h) ? check_status(h) : NDMG_OK;
+}
+
+int ndmg_solve(ndmg_t* h, const double* f, double* u, double tol, int32_t maxit, int32_t* iters, double* relres) {
+  if (!h) return NDMG_INVALID_ARG;
+  int st;
+  if ((st = check_ptrs(h, {f, u}))) return st;
+  if (!(tol > 0) || maxit < 0) return fail(h, NDMG_INVALID_ARG, "tol must be > 0 and maxit >= 0");
+  int it = 0;
+  double rr = 0.0;
+  if (h->o.precision == NDMG_PREC_FP64) st = pcg64(h, f, u, tol, maxit, &it, &rr);
+  else st = solve_ir(h, f, u, tol, maxit, &it, &rr);
+  if (iters) *iters = it;
+  if (relres) *relres = rr;
+  return st;
+}
+
+int ndmg_solve_host(ndmg_t* h, const double* f_host, double* u_host, double tol, int32_t maxit, int32_t* iters,
+                    double* relres) {
+  if (!h) return NDMG_INVALID_ARG;
+  if (!f_host || !u_host) return fail(h, NDMG_INVALID_ARG, "null host buffer");
+  const int64_t N = h->lv[h->K].N;
+  double* f = h->w64[4];
+  double* u = h->w64[5];
+  NDMG_CK(cudaMemcpyAsync(f, f_host, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream));
+  NDMG_CK(cudaMemcpyAsync(u, u_host, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream));
+  int st = ndmg_solve(h, f, u, tol, maxit, iters, relres);
+  if (st != NDMG_OK && st != NDMG_NOT_CONVERGED) return st;
+  NDMG_CK(cudaMemcpyAsync(u_host, u, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream));
+  NDMG_CK(cudaStreamSynchronize(h->stream));
+  return st;
+}
+
+int ndmg_vcycle_iterate(ndmg_t* h, const double* f, double* u, double tol, int32_t maxit, int32_t* cycles,
+                        double* relres) {
+  if (!h) return NDMG_INVALID_ARG;
+  int st;
+  if ((st = check_ptrs(h, {f, u}))) return st;
+  const int K = h->K;
+  const int64_t N = h->lv[K].N;
+  double* r = h->w64[0];
+  double ff, rr, dum;
+  if ((st = dot2<double>(h, N, f, f, (const double*)nullptr, (const double*)nullptr, &ff, &dum)) != NDMG_OK) return st;
+  const double nf = std::sqrt(ff) > 0 ? std::sqrt(ff) : 1.0;
+  int c = 0;
+  for (;; ++c) {
+    op_residual<double>(h, K, f, u, r);
+    if ((st = dot2<double>(h, N, r, r, (const double*)nullptr, (const double*)nullptr, &rr, &dum)) != NDMG_OK) return st;
+    if (relres) *relres = std::sqrt(rr) / nf;
+    if (cycles) *cycles = c;
+    if (!std::isfinite(rr)) return fail(h, NDMG_BREAKDOWN, "non-finite residual");
+    if (std::sqrt(rr) <= tol * nf) return NDMG_OK;
+    if (c >= maxit) return fail(h, NDMG_NOT_CONVERGED, "V-cycle iteration reached maxit");
+    op_vcycle<double>(h, K, f, u);
+  }
+}
+
+int ndmg_grad_alpha(ndmg_t* h, const double* lambda, const double* u, double* out) {
+  if (!h) return NDMG_INVALID_ARG;
+  int st;
+  if ((st = check_ptrs(h, {lambda, u}))) return st;
+  if (!out) return fail(h, NDMG_INVALID_ARG, "null output");
+  const int K = h->K;
+  DevLevel& L = h->lv[K];
+  double* Ku = h->w64[3];
+  {
+    Span sp(h, NDMG_K_STENCIL, 16.0 * L.N);
+    launch_stencil<double>(h->stream, h->sm_count, L.n, L.h, 0.0, u, (const double*)nullptr, Ku);
+  }
+  double v, dum;
+  if ((st = dot2<double>(h, L.N, lambda, Ku, (const double*)nullptr, (const double*)nullptr, &v, &dum)) != NDMG_OK)
+    return st;
+  *out = -v;
+  return NDMG_OK;
+}
+
+int ndmg_dot(ndmg_t* h, int32_t level, int32_t dtype, const void* x, const void* y, double* out) {
+  if (!h) return NDMG_INVALID_ARG;
+  int st;
+  if ((st = check_level(h, level, false)) || (st = check_dtype(h, dtype)) || (st = check_ptrs(h, {x, y}))) return st;
+  if (!out) return fail(h, NDMG_INVALID_ARG, "null output");
+  double dum;
+  const int64_t N = h->lv[level].N;
+  if (dtype == NDMG_F64) return dot2<double>(h, N, (const double*)x, (const double*)y, (const double*)nullptr, (const double*)nullptr, out, &dum);
+  return dot2<float>(h, N, (const float*)x, (const float*)y, (const float*)nullptr, (const float*)nullptr, out, &dum);
+}
+
+int ndmg_trace_enable(ndmg_t* h, int32_t kernel_class, int32_t on) {
+  if (!h) return NDMG_INVALID_ARG;
+  if (kernel_class < 0 || kernel_class >= NDMG_K_COUNT) return fail(h, NDMG_INVALID_ARG, "bad kernel class");
+  h->trace_on[kernel_class] = on != 0;
+  return NDMG_OK;
+}
+
+int ndmg_trace_read(ndmg_t* h, int32_t kernel_class, int64_t* launches, double* ms, double* units) {
+  if (!h) return NDMG_INVALID_ARG;
+  if (kernel_class < 0 || kernel_class >= NDMG_K_COUNT) return fail(h, NDMG_INVALID_ARG, "bad kernel class");
+  NDMG_CK(cudaStreamSynchronize(h->stream));
+  double total = 0.0;
+  for (auto& pr : h->ev_used[kernel_class]) {
+    float t = 0.f;
+    NDMG_CK(cudaEventElapsedTime(&t, pr.first, pr.second));
+    total += t;
+    h->ev_free.push_back(pr);
+  }
+  h->ev_used[kernel_class].clear();
+  if (launches) *launches = h->trace_launches[kernel_class];
+  if (ms) *ms = total;
+  if (units) *units = h->trace_units[kernel_class];
+  h->trace_launches[kernel_class] = 0;
+  h->trace_units[kernel_class] = 0.0;
+  return NDMG_OK;
+}
+
+int ndmg_counters(const ndmg_t* h, int64_t* launches, int64_t* vcycles) {
+  if (!h) return NDMG_INVALID_ARG;
+  if (launches) *launches = h->launch_total;
+  if (vcycles) *vcycles = h->vcycle_total;
+  return NDMG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,91 @@
+// Internal declarations of libndmg (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/ndmg.h"
+
+namespace ndmg {
+
+// Interior edges of a box of bx*by*bz cells (the canonical layout of
+// ndmg.h with per-axis extents), N = bx(by-1)(bz-1) + (bx-1)by(bz-1) + (bx-1)(by-1)bz.
+struct Box {
+  int b[3];
+  int64_t count(int d) const {
+    int64_t c = 1;
+    for (int a = 0; a < 3; ++a) c *= (a == d) ? b[a] : (b[a] - 1);
+    return c;
+  }
+  int64_t size() const { return count(0) + count(1) + count(2); }
+  // index of edge (d, i, j, k) in box coordinates or -1 if not interior
+  int64_t index(int d, int i, int j, int k) const;
+};
+
+// ---- host-side local operators (setup.cpp) ---------------------------------
+struct LocalOps {
+  int n;                      // cells per side on this level
+  double h;
+  std::vector<double> AinvT;  // 6x6 inverse of the interior-space matrix A_T
+  std::vector<double> Dv;     // 108x108 J_V A_V^{-1} J_V^t (patch-local order)
+  std::vector<double> Wv;     // 108x60 Gram factor, Dv = Wv Wv^t
+};
+
+// Dense assembled matrix of a box with Dirichlet (interior-edge) DOFs for
+// a(w,v) = alpha (curl w, curl v) + beta (w, v) on cubes of side h.
+std::vector<double> box_matrix(const Box& box, double h, double alpha, double beta);
+// Vertex-patch operator and Gram factor, interior-space inverse for level n.
+void build_local_ops(int n, double L, double alpha, double beta, LocalOps* out);
+// Inverse of the coarsest operator (n0^3 box).
+std::vector<double> coarse_inverse(int n0, double L, double alpha, double beta);
+// In-place Cholesky of an SPD matrix (lower), returns false if not SPD.
+bool cholesky(std::vector<double>& a, int n);
+std::vector<double> spd_inverse(const std::vector<double>& a, int n, bool* ok);
+
+// ---- device side -----------------------------------------------------------
+struct DevLevel {
+  int n;
+  int64_t N;                  // edges on this level
+  double h, cK, cM;           // alpha*h, beta*h^3
+  // FP64 workspaces (coarse levels) and FP32 workspaces
+  double *g64 = nullptr, *z64 = nullptr, *r64 = nullptr;
+  float *g32 = nullptr, *z32 = nullptr, *r32 = nullptr;
+  // local operators (levels >= 1)
+  double* AinvT64 = nullptr;  // 36
+  float* AinvT32 = nullptr;
+  double* Dv64 = nullptr;     // 108*108
+  float* Dv32 = nullptr;
+  void* Wtc = nullptr;        // tensor-core operand images (bf16/fp16), see tc kernel
+};
+
+}  // namespace ndmg
+
+struct ndmg_handle {
+  ndmg_opts o;
+  cudaStream_t stream;
+  int sm_count;
+  int K;                                  // finest level index
+  std::vector<ndmg::DevLevel> lv;         // lv[0] = coarsest
+  double* Ainv0 = nullptr;                // coarsest inverse (FP64, N0 x N0)
+  // PCG / refinement workspaces on the finest level
+  double *w64[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  float *w32[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  double* red = nullptr;                  // reduction scratch (partials + results)
+  double* red_host = nullptr;             // pinned mirror of the results
+  int* status = nullptr;                  // device status word (timeouts)
+  std::string err;
+  // tracing: per kernel class, event pairs recorded around launches
+  bool trace_on[NDMG_K_COUNT] = {};
+  int64_t trace_launches[NDMG_K_COUNT] = {};
+  double trace_units[NDMG_K_COUNT] = {};
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used[NDMG_K_COUNT];
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_free;
+  int64_t launch_total = 0;
+  int64_t vcycle_total = 0;
+};

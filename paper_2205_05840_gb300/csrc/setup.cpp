@@ -1,0 +1,246 @@
+// Host-side (FP64) construction of the local operators of the smoother and of
+// the coarsest solve.  Everything here runs once per (n, L, alpha, beta).
+//
+// Element matrices of the lowest-order hexahedral Nedelec element (Sec. 2,
+// eq. nedlec form / NDdof) on a cube of side h, written in closed form.  With
+// l_0(t) = 1 - t/h, l_1(t) = t/h, int_0^h l_a l_c = h m_ac,
+// m = [[1/3, 1/6], [1/6, 1/3]], l_a' = s_a / h, s = (-1, +1), and the basis
+// function of the edge along axis d whose start vertex sits at offset a on
+// axis d+1 and b on axis d+2 (cyclic) equal to l_a l_b e_d:
+//   mass            M = h^3 m_{a a'} m_{b b'}                     (same axis)
+//   curl-curl       K = h (m_{a a'} s_b s_b' + s_a s_a' m_{b b'})  (same axis)
+//                   K = -h s_a s_b' m_{b a'}   (second edge along axis d+1)
+// The local spaces of Sec. 3.2 are boxes of cells with only the edges in the
+// box's relative interior, which is the same numbering as the global mesh.
+#include <cmath>
+#include <cstring>
+#include <stdexcept>
+
+#include "ndmg_internal.h"
+
+namespace ndmg {
+
+int64_t Box::index(int d, int i, int j, int k) const {
+  const int p[3] = {i, j, k};
+  for (int a = 0; a < 3; ++a) {
+    if (a == d) {
+      if (p[a] < 0 || p[a] >= b[a]) return -1;
+    } else {
+      if (p[a] < 1 || p[a] > b[a] - 1) return -1;
+    }
+  }
+  const int bx = b[0], by = b[1];
+  if (d == 0) return ((int64_t)(k - 1) * (by - 1) + (j - 1)) * bx + i;
+  if (d == 1) return count(0) + ((int64_t)(k - 1) * by + j) * (bx - 1) + (i - 1);
+  return count(0) + count(1) + ((int64_t)k * (by - 1) + (j - 1)) * (bx - 1) + (i - 1);
+}
+
+namespace {
+
+const double kM[2][2] = {{1.0 / 3.0, 1.0 / 6.0}, {1.0 / 6.0, 1.0 / 3.0}};
+const double kS[2] = {-1.0, 1.0};
+
+struct LocalEdge {
+  int d, a, b;
+};
+
+LocalEdge local_edge(int e) { return LocalEdge{e / 4, e % 2, (e / 2) % 2}; }
+
+// 12x12 element matrix alpha K + beta M of one cube of side h.
+void element_matrix(double h, double alpha, double beta, double out[12][12]) {
+  for (int p = 0; p < 12; ++p) {
+    for (int q = 0; q < 12; ++q) {
+      LocalEdge e1 = local_edge(p), e2 = local_edge(q);
+      double kv = 0.0, mv = 0.0;
+      if (e1.d == e2.d) {
+        mv = h * h * h * kM[e1.a][e2.a] * kM[e1.b][e2.b];
+        kv = h * (kM[e1.a][e2.a] * kS[e1.b] * kS[e2.b] + kS[e1.a] * kS[e2.a] * kM[e1.b][e2.b]);
+      } else if (e2.d == (e1.d + 1) % 3) {
+        kv = -h * kS[e1.a] * kS[e2.b] * kM[e1.b][e2.a];
+      } else {
+        kv = -h * kS[e2.a] * kS[e1.b] * kM[e2.b][e1.a];
+      }
+      out[p][q] = alpha * kv + beta * mv;
+    }
+  }
+}
+
+}  // namespace
+
+std::vector<double> box_matrix(const Box& box, double h, double alpha, double beta) {
+  const int64_t N = box.size();
+  std::vector<double> A((size_t)(N * N), 0.0);
+  double E[12][12];
+  element_matrix(h, alpha, beta, E);
+  int64_t gid[12];
+  for (int ck = 0; ck < box.b[2]; ++ck)
+    for (int cj = 0; cj < box.b[1]; ++cj)
+      for (int ci = 0; ci < box.b[0]; ++ci) {
+        const int c[3] = {ci, cj, ck};
+        for (int e = 0; e < 12; ++e) {
+          LocalEdge le = local_edge(e);
+          int p[3] = {c[0], c[1], c[2]};
+          p[(le.d + 1) % 3] += le.a;
+          p[(le.d + 2) % 3] += le.b;
+          gid[e] = box.index(le.d, p[0], p[1], p[2]);
+        }
+        for (int e = 0; e < 12; ++e) {
+          if (gid[e] < 0) continue;
+          for (int f = 0; f < 12; ++f) {
+            if (gid[f] < 0) continue;
+            A[(size_t)(gid[e] * N + gid[f])] += E[e][f];
+          }
+        }
+      }
+  return A;
+}
+
+bool cholesky(std::vector<double>& a, int n) {
+  for (int j = 0; j < n; ++j) {
+    double s = a[(size_t)j * n + j];
+    for (int k = 0; k < j; ++k) s -= a[(size_t)j * n + k] * a[(size_t)j * n + k];
+    if (!(s > 0.0)) return false;
+    const double d = std::sqrt(s);
+    a[(size_t)j * n + j] = d;
+    for (int i = j + 1; i < n; ++i) {
+      double t = a[(size_t)i * n + j];
+      for (int k = 0; k < j; ++k) t -= a[(size_t)i * n + k] * a[(size_t)j * n + k];
+      a[(size_t)i * n + j] = t / d;
+    }
+    for (int i = 0; i < j; ++i) a[(size_t)i * n + j] = 0.0;
+  }
+  return true;
+}
+
+// inverse of a lower-triangular matrix
+static std::vector<double> lower_inverse(const std::vector<double>& Lm, int n) {
+  std::vector<double> X((size_t)n * n, 0.0);
+  for (int c = 0; c < n; ++c) {
+    for (int i = c; i < n; ++i) {
+      double s = (i == c) ? 1.0 : 0.0;
+      for (int k = c; k < i; ++k) s -= Lm[(size_t)i * n + k] * X[(size_t)k * n + c];
+      X[(size_t)i * n + c] = s / Lm[(size_t)i * n + i];
+    }
+  }
+  return X;
+}
+
+std::vector<double> spd_inverse(const std::vector<double>& a, int n, bool* ok) {
+  std::vector<double> Lm = a;
+  *ok = cholesky(Lm, n);
+  if (!*ok) return {};
+  std::vector<double> Li = lower_inverse(Lm, n);
+  std::vector<double> inv((size_t)n * n, 0.0);
+  // A^{-1} = L^{-T} L^{-1}
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j <= i; ++j) {
+      double s = 0.0;
+      for (int k = i; k < n; ++k) s += Li[(size_t)k * n + i] * Li[(size_t)k * n + j];
+      inv[(size_t)i * n + j] = s;
+      inv[(size_t)j * n + i] = s;
+    }
+  return inv;
+}
+
+void build_local_ops(int n, double L, double alpha, double beta, LocalOps* out) {
+  const double h = L / n;
+  out->n = n;
+  out->h = h;
+  bool ok = false;
+  // interior space N_h^T of one coarse element (2x2x2 cells, 6 edges)
+  const Box bub{{2, 2, 2}};
+  std::vector<double> AT = box_matrix(bub, h, alpha, beta);
+  out->AinvT = spd_inverse(AT, 6, &ok);
+  if (!ok) throw std::runtime_error("interior-space matrix is not SPD");
+
+  // vertex patch: 4x4x4 cells around a coarse vertex, 108 interior edges
+  const Box pb{{4, 4, 4}};
+  const int np = (int)pb.size();
+  std::vector<double> Ap = box_matrix(pb, h, alpha, beta);
+  std::vector<double> Apinv = spd_inverse(Ap, np, &ok);
+  if (!ok) throw std::runtime_error("vertex-patch matrix is not SPD");
+
+  // the 8 interior spaces inside the patch, each in the 2x2x2 box order
+  std::vector<int> isB(np, 0);
+  out->Dv = Apinv;
+  for (int sr = 0; sr < 2; ++sr)
+    for (int sq = 0; sq < 2; ++sq)
+      for (int sp = 0; sp < 2; ++sp) {
+        const int o[3] = {2 * sp, 2 * sq, 2 * sr};
+        int ids[6];
+        int t = 0;
+        for (int d = 0; d < 3; ++d)
+          for (int s = 0; s < 2; ++s) {
+            int p[3] = {o[0] + 1, o[1] + 1, o[2] + 1};
+            p[d] = o[d] + s;
+            ids[t++] = (int)pb.index(d, p[0], p[1], p[2]);
+          }
+        for (int a = 0; a < 6; ++a) {
+          isB[ids[a]] = 1;
+          for (int b = 0; b < 6; ++b) out->Dv[(size_t)ids[a] * np + ids[b]] -= out->AinvT[a * 6 + b];
+        }
+      }
+
+  // Gram factor through the Schur complement on the interface (60 edges)
+  std::vector<int> I, G;
+  for (int e = 0; e < np; ++e) (isB[e] ? I : G).push_back(e);
+  const int nI = (int)I.size(), nG = (int)G.size();
+  if (nI != 48 || nG != 60) throw std::runtime_error("unexpected vertex-patch split");
+  std::vector<double> AII((size_t)nI * nI), AIG((size_t)nI * nG), AGG((size_t)nG * nG);
+  for (int a = 0; a < nI; ++a)
+    for (int b = 0; b < nI; ++b) AII[(size_t)a * nI + b] = Ap[(size_t)I[a] * np + I[b]];
+  for (int a = 0; a < nI; ++a)
+    for (int b = 0; b < nG; ++b) AIG[(size_t)a * nG + b] = Ap[(size_t)I[a] * np + G[b]];
+  for (int a = 0; a < nG; ++a)
+    for (int b = 0; b < nG; ++b) AGG[(size_t)a * nG + b] = Ap[(size_t)G[a] * np + G[b]];
+  std::vector<double> AIIinv = spd_inverse(AII, nI, &ok);
+  if (!ok) throw std::runtime_error("bubble block is not SPD");
+  // X = A_II^{-1} A_IG (nI x nG)
+  std::vector<double> X((size_t)nI * nG, 0.0);
+  for (int a = 0; a < nI; ++a)
+    for (int k = 0; k < nI; ++k) {
+      const double v = AIIinv[(size_t)a * nI + k];
+      for (int b = 0; b < nG; ++b) X[(size_t)a * nG + b] += v * AIG[(size_t)k * nG + b];
+    }
+  std::vector<double> S = AGG;
+  for (int a = 0; a < nG; ++a)
+    for (int b = 0; b < nG; ++b) {
+      double s = 0.0;
+      for (int k = 0; k < nI; ++k) s += AIG[(size_t)k * nG + a] * X[(size_t)k * nG + b];
+      S[(size_t)a * nG + b] -= s;
+    }
+  std::vector<double> R = S;
+  if (!cholesky(R, nG)) throw std::runtime_error("Schur complement is not SPD");
+  std::vector<double> Ri = lower_inverse(R, nG);        // R^{-1}; R^{-T} = Ri^t
+  out->Wv.assign((size_t)np * nG, 0.0);
+  for (int a = 0; a < nG; ++a)                          // interface rows: R^{-T}
+    for (int c = 0; c < nG; ++c) out->Wv[(size_t)G[a] * nG + c] = Ri[(size_t)c * nG + a];
+  for (int a = 0; a < nI; ++a)                          // bubble rows: -X R^{-T}
+    for (int c = 0; c < nG; ++c) {
+      double s = 0.0;
+      for (int b = 0; b < nG; ++b) s += X[(size_t)a * nG + b] * Ri[(size_t)c * nG + b];
+      out->Wv[(size_t)I[a] * nG + c] = -s;
+    }
+  // self-check: W W^t reproduces the dense operator
+  double mx = 0.0, err = 0.0;
+  for (int a = 0; a < np; ++a)
+    for (int b = 0; b < np; ++b) {
+      double s = 0.0;
+      for (int c = 0; c < nG; ++c) s += out->Wv[(size_t)a * nG + c] * out->Wv[(size_t)b * nG + c];
+      err = std::fmax(err, std::fabs(s - out->Dv[(size_t)a * np + b]));
+      mx = std::fmax(mx, std::fabs(out->Dv[(size_t)a * np + b]));
+    }
+  if (!(err <= 1e-9 * mx)) throw std::runtime_error("Gram factor does not reproduce the patch operator");
+}
+
+std::vector<double> coarse_inverse(int n0, double L, double alpha, double beta) {
+  const Box b{{n0, n0, n0}};
+  const int N = (int)b.size();
+  std::vector<double> A = box_matrix(b, L / n0, alpha, beta);
+  bool ok = false;
+  std::vector<double> inv = spd_inverse(A, N, &ok);
+  if (!ok) throw std::runtime_error("coarsest operator is not SPD");
+  return inv;
+}
+
+}  // namespace ndmg

@@ -1,0 +1,223 @@
+"""GPU parity of the FP64 path against the CPU oracle (arXiv 2205.05840,
+Sec. 2-3).  Every CUDA result goes through the C-ABI library; every expected
+value comes from oracle/ on the same seeded inputs.
+
+Tolerances: the FP64 path matches the oracle to 1e-10 relative per V-cycle
+iterate (the requirement for this path); single operator applications are
+held to 1e-13 relative, the level of FP64 rounding of a 33-point stencil.
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse.linalg as spla
+import torch
+
+from oracle import hcurl, mg
+from paper_2205_05840_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+try:
+    from paper_2205_05840_gb300 import ndmg
+except ImportError:
+    if torch.cuda.is_available():
+        raise                      # on a GPU machine the library must load: no fallback
+    pytest.skip("library not built and no GPU here", allow_module_level=True)
+
+DEV = "cuda"
+
+
+def T(x, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype, device=DEV)
+
+
+def N(t):
+    torch.cuda.synchronize()
+    return t.detach().double().cpu().numpy()
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.mark.parametrize("n,n0,L,alpha,beta", [(2, 2, 1.0, 1.0, 1.0), (4, 2, 1.0, 0.3, 2.0), (6, 3, 2.0, 10.0, 1.0),
+                                              (8, 2, 1.0, 1.0, 1.0), (16, 4, 1.0, 0.01, 1.0), (12, 3, 1.0, 100.0, 0.5)])
+def test_apply_and_residual_parity(n, n0, L, alpha, beta):
+    S = ndmg.Solver(n, n_coarsest=n0, L=L, alpha=alpha, beta=beta)
+    A = hcurl.assemble(n, L, alpha, beta)
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal(A.shape[0])
+    g = rng.standard_normal(A.shape[0])
+    y = torch.empty(A.shape[0], dtype=torch.float64, device=DEV)
+    S.apply(T(x), y)
+    assert rel(N(y), A @ x) < 1e-13
+    r = torch.empty_like(y)
+    S.residual(T(g), T(x), r)
+    assert rel(N(r), g - A @ x) < 1e-13
+    # float vectors: same operator in FP32 arithmetic
+    y32 = torch.empty(A.shape[0], dtype=torch.float32, device=DEV)
+    S.apply(T(x, torch.float32), y32)
+    assert rel(N(y32), A @ x.astype(np.float32).astype(np.float64)) < 2e-6
+    # every coarser level of the hierarchy too
+    for lv in range(S.num_levels):
+        nl = n0 << lv
+        Al = hcurl.assemble(nl, L, alpha, beta)
+        xl = rng.standard_normal(Al.shape[0])
+        yl = torch.empty(Al.shape[0], dtype=torch.float64, device=DEV)
+        S.apply(T(xl), yl, level=lv)
+        assert rel(N(yl), Al @ xl) < 1e-13
+
+
+@pytest.mark.parametrize("nc", [2, 3, 4, 8])
+def test_transfer_parity(nc):
+    S = ndmg.Solver(2 * nc, n_coarsest=nc)
+    P = mg.prolongation(nc, 1.0)
+    rng = np.random.default_rng(nc)
+    rf = rng.standard_normal(P.shape[0])
+    zc = rng.standard_normal(P.shape[1])
+    zf = rng.standard_normal(P.shape[0])
+    gc = torch.empty(P.shape[1], dtype=torch.float64, device=DEV)
+    S.restrict(T(rf), gc, level=1)
+    assert rel(N(gc), P.T @ rf) < 1e-14
+    zt = T(zf)
+    S.prolong_add(T(zc), zt, level=1)
+    assert rel(N(zt), zf + P @ zc) < 1e-14
+
+
+@pytest.mark.parametrize("n0", [2, 3, 4])
+def test_coarse_solve_parity(n0):
+    S = ndmg.Solver(2 * n0, n_coarsest=n0, alpha=0.7)
+    A0 = hcurl.assemble(n0, 1.0, 0.7, 1.0).toarray()
+    g = np.random.default_rng(0).standard_normal(A0.shape[0])
+    z = torch.empty(A0.shape[0], dtype=torch.float64, device=DEV)
+    S.coarse_solve(T(g), z)
+    assert rel(N(z), sla.cho_solve(sla.cho_factor(A0), g)) < 1e-12
+
+
+@pytest.mark.parametrize("n,alpha", [(4, 1.0), (8, 0.01), (12, 3.0), (16, 100.0)])
+def test_smoothing_step_parity(n, alpha):
+    # z <- z + M_V^{-1}(g - A z), eq. (Preconditioner P), eta = 1/9
+    S = ndmg.Solver(n, n_coarsest=n // 2, alpha=alpha)
+    A = hcurl.assemble(n, 1.0, alpha, 1.0)
+    Sm = mg.Smoother(A, n, "vertex")
+    rng = np.random.default_rng(1)
+    g = rng.standard_normal(A.shape[0])
+    z = rng.standard_normal(A.shape[0])
+    ref = z.copy()
+    for _ in range(2):
+        ref = ref + Sm.apply(g - A @ ref)
+    zt = T(z)
+    S.smooth(T(g), zt, steps=2, level=-1)
+    assert rel(N(zt), ref) < 1e-12
+
+
+@pytest.mark.parametrize("n,n0,alpha,m", [(8, 2, 1.0, 2), (16, 4, 0.01, 2), (12, 3, 100.0, 1), (32, 4, 1.0, 2)])
+def test_vcycle_iterates_parity(n, n0, alpha, m):
+    # Fig. 1 V-cycle, standalone iteration: every iterate within 1e-10 relative
+    S = ndmg.Solver(n, n_coarsest=n0, alpha=alpha, m=m)
+    H = mg.Hierarchy(n, 1.0, alpha, 1.0, n0=n0, m=m)
+    f = inputs.random_load(n, 0)
+    z = np.zeros_like(f)
+    zt = T(z)
+    ft = T(f)
+    for it in range(5):
+        z = H.vcycle(f, z)
+        S.vcycle(ft, zt)
+        assert rel(N(zt), z) < 1e-10, it
+
+
+def test_config1_standalone_vcycle_iteration():
+    # unit cube 8^3, alpha = 1, seed-0 load, 8->4->2, m = 2: cycles to 1e-8 equal the oracle's
+    H = mg.Hierarchy(8, 1.0, 1.0, 1.0, n0=2, m=2)
+    f = inputs.random_load(8, 0)
+    z_ref, it_ref, hist = mg.vcycle_iteration(H, f, tol=1e-8)
+    S = ndmg.Solver(8, n_coarsest=2)
+    u = torch.zeros(f.size, dtype=torch.float64, device=DEV)
+    st, cycles, rr = S.vcycle_iterate(T(f), u, tol=1e-8, maxit=200)
+    assert cycles == it_ref and rr <= 1e-8
+    assert rel(N(u), z_ref) < 1e-9
+
+
+@pytest.mark.parametrize("n,n0,alpha", [(16, 2, 1.0), (32, 4, 0.01), (24, 3, 100.0)])
+def test_pcg_parity(n, n0, alpha):
+    S = ndmg.Solver(n, n_coarsest=n0, alpha=alpha)
+    H = mg.Hierarchy(n, 1.0, alpha, 1.0, n0=n0, m=2)
+    f = inputs.random_load(n, 2)
+    u_ref, it_ref, rr_ref, _ = mg.pcg(H, f, tol=1e-8)
+    u = torch.zeros(f.size, dtype=torch.float64, device=DEV)
+    st, it, rr = S.solve(T(f), u, tol=1e-8)
+    assert rr <= 1e-8 and it == it_ref
+    assert rel(N(u), u_ref) < 1e-9
+    x = spla.spsolve(H.A[-1].tocsc(), f)
+    assert rel(N(u), x) < 1e-6
+
+
+@pytest.mark.parametrize("alpha", [0.01, 1.0, 100.0])
+def test_manufactured_64(alpha):
+    # 64^3, coarsening to 4^3, manufactured sine load: the discrete solution is c Pi u
+    n = 64
+    h = 1.0 / n
+    S = ndmg.Solver(n, n_coarsest=4, alpha=alpha)
+    f = inputs.manufactured_load(n, 1.0, alpha, 1.0)
+    u = torch.zeros(f.size, dtype=torch.float64, device=DEV)
+    st, it, rr = S.solve(T(f), u, tol=1e-8)
+    assert rr <= 1e-8 and it <= 30
+    mu = (2.0 + np.cos(np.pi * h)) / 3.0
+    sig = (np.sin(np.pi * h / 2) / (np.pi * h / 2)) ** 2
+    c = (2 * np.pi ** 2 * alpha + 1) * sig ** 2 / (8 * alpha * np.sin(np.pi * h / 2) ** 2 * mu / h ** 2 + mu ** 2)
+    assert rel(N(u), c * inputs.sine_interpolant(n)) < 1e-6
+
+
+def test_full_size_128_sampled_rows_and_solve():
+    # 128^3 (6.19M unknowns): operator rows sampled against the oracle's
+    # element-by-element evaluation, then an FP64 PCG solve to 1e-8
+    n = 128
+    S = ndmg.Solver(n, n_coarsest=4)
+    Nn = hcurl.num_edges(n)
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal(Nn)
+    y = torch.empty(Nn, dtype=torch.float64, device=DEV)
+    S.apply(T(x), y)
+    rows = np.concatenate([rng.integers(0, Nn, 3000), [0, Nn - 1, Nn // 3, 2 * Nn // 3]])
+    ref = hcurl.apply_rows(n, 1.0, 1.0, 1.0, x, rows)
+    assert rel(N(y)[rows], ref) < 1e-13
+    f = inputs.random_load(n, 0)
+    u = torch.zeros(Nn, dtype=torch.float64, device=DEV)
+    st, it, rr = S.solve(T(f), u, tol=1e-8)
+    assert rr <= 1e-8
+    r = torch.empty_like(u)
+    S.residual(T(f), u, r)
+    rn = np.linalg.norm(N(r)) / np.linalg.norm(f)
+    assert rn <= 1.01e-8
+
+
+def test_grad_alpha_parity():
+    n = 16
+    alpha = 0.7
+    S = ndmg.Solver(n, n_coarsest=2, alpha=alpha)
+    K, _ = hcurl.assemble_parts(n, 1.0)
+    rng = np.random.default_rng(3)
+    lam, u = rng.standard_normal((2, K.shape[0]))
+    assert abs(S.grad_alpha(T(lam), T(u)) - (-(lam @ (K @ u)))) < 1e-12 * abs(lam @ (K @ u))
+
+
+def test_error_paths():
+    S = ndmg.Solver(8, n_coarsest=2)
+    Nn = S.num_dofs()
+    f = T(inputs.random_load(8, 0))
+    u = torch.zeros(Nn, dtype=torch.float64, device=DEV)
+    st, it, rr = S.solve(f, u, tol=1e-8, maxit=1, raise_on_fail=False)
+    assert st == ndmg.NOT_CONVERGED and it == 1
+    bad = f.clone()
+    bad[5] = float("nan")
+    u.zero_()
+    st, it, rr = S.solve(bad, u, tol=1e-8, raise_on_fail=False)
+    assert st == ndmg.BREAKDOWN
+    # misaligned pointer -> INVALID_ARG before any launch
+    big = torch.zeros(Nn + 1, dtype=torch.float64, device=DEV)
+    st = ndmg._lib.ndmg_apply(S._h, -1, ndmg.F64, big.data_ptr() + 8, u.data_ptr())
+    assert st == ndmg.INVALID_ARG
+    st = ndmg._lib.ndmg_apply(S._h, 7, ndmg.F64, f.data_ptr(), u.data_ptr())
+    assert st == ndmg.INVALID_ARG
+    with pytest.raises(ndmg.NdmgError):
+        ndmg.Solver(8, n_coarsest=2, alpha=-1.0)
