@@ -302,6 +302,7 @@ int pcg32(ndmg_t* h, const float* b, float* d, double tol, int maxit, int* iters
   NDMG_CK(cudaMemcpyAsync(r, b, sizeof(float) * N, cudaMemcpyDeviceToDevice, h->stream));
   cudaMemsetAsync(z, 0, sizeof(float) * N, h->stream);
   op_vcycle<float>(h, K, r, z);
+  if (mixed(h) && (st = check_status(h)) != NDMG_OK) return st;
   if ((st = dot2<float>(h, N, b, b, r, z, &bb, &rz)) != NDMG_OK) return st;
   if (bb == 0.0) return NDMG_OK;
   NDMG_CK(cudaMemcpyAsync(p, z, sizeof(float) * N, cudaMemcpyDeviceToDevice, h->stream));
@@ -321,6 +322,7 @@ int pcg32(ndmg_t* h, const float* b, float* d, double tol, int maxit, int* iters
     if (std::sqrt(rr) <= tol * nb) return NDMG_OK;
     cudaMemsetAsync(z, 0, sizeof(float) * N, h->stream);
     op_vcycle<float>(h, K, r, z);
+    if (mixed(h) && (st = check_status(h)) != NDMG_OK) return st;
     double rz_new, qz;
     if ((st = dot2<float>(h, N, r, z, q, z, &rz_new, &qz)) != NDMG_OK) return st;
     {
@@ -452,7 +454,7 @@ int ndmg_create(const ndmg_opts* o, ndmg_t** out) {
   if (!(o->L > 0) || !(o->alpha > 0) || !(o->beta > 0) || o->m < 1 || o->nrhs < 1) return NDMG_INVALID_ARG;
   if (o->nrhs != 1) return NDMG_INVALID_ARG;              // batched layout: not built yet
   if (o->smoother != NDMG_SMOOTHER_VERTEX) return NDMG_INVALID_ARG;
-  if (o->precision != NDMG_PREC_FP64 && o->precision != NDMG_PREC_FP32) return NDMG_INVALID_ARG;
+  if (o->precision < NDMG_PREC_FP64 || o->precision > NDMG_PREC_FP32) return NDMG_INVALID_ARG;
   if (edges(o->n_coarsest) > 4096) return NDMG_INVALID_ARG;   // dense coarsest inverse
   int K = 0;
   for (int n = o->n; n > o->n_coarsest; n /= 2, ++K)

@@ -1,11 +1,457 @@
-// Tensor-core vertex-patch kernel (tcgen05): not built yet; ndmg_create
-// rejects the mixed precision modes until it is.
+// Vertex-patch term of the smoother, eq. (Preconditioner P), on the 5th-gen
+// tensor cores (tcgen05, sm_103a):
+//
+//     z += eta * sum_V J_V A_V^{-1} J_V^t r,   J_V A_V^{-1} J_V^t = W W^t,
+//
+// with W the 108x60 Gram factor of the vertex-space operator (the same matrix
+// for every patch: constant alpha on a uniform grid).  One CTA owns a brick of
+// 8x8x8 fine cells (4x4x4 coarse elements) and computes every patch that
+// touches its edges: the (4+1)^3 = 125 patches around the brick's coarse
+// vertices, one 128-row MMA tile.  Per CTA:
+//   1. stage r on the 12x12x12-cell region the patches cover (FP32, smem);
+//   2. gather the 125 patch vectors into A1 (128 x 112, bf16/fp16, K-major);
+//   3. D1 = A1 W           (tcgen05.mma M=128 N=64  K=112, FP32 in TMEM);
+//   4. A2 = lowp(D1)       (tcgen05.ld -> registers -> smem);
+//   5. D2 = A2 W^t         (tcgen05.mma M=128 N=112 K=64, FP32 in TMEM);
+//   6. add each patch's 108 outputs that land on owned edges into an smem
+//      accumulator (shared atomics: up to 8 patches share an edge);
+//   7. z[owned] += scale * acc.
+// Every edge is written by exactly one CTA, so no global atomics are needed.
+// Neighbouring CTAs recompute the patches on their common boundary.
+//
+// Operand layout (SWIZZLE_NONE, K-major canonical layout): 8x16-byte "core
+// matrices" (8 rows x 8 elements) stored contiguously; core matrix (g, c) of
+// an R x K operand (g = row / 8, c = k / 8) sits at byte (g * K/8 + c) * 128.
+// Descriptor: leading byte offset (next core matrix along K) = 128, stride
+// byte offset (next 8-row group) = K/8 * 128.
+#include <cmath>
+#include <cstring>
+
 #include "tc_patch.cuh"
 
 namespace ndmg {
+namespace {
 
-cudaError_t upload_tc_operand(void**, const std::vector<double>&, bool) { return cudaErrorNotSupported; }
-cudaError_t prepare_tc_patch() { return cudaErrorNotSupported; }
-void launch_tc_patch(cudaStream_t, int, int, const void*, bool, double, const float*, float*, int*) {}
+constexpr int kB = 4;                      // coarse vertices per brick side
+constexpr int kM = 128;                    // MMA rows (125 patches + 3 empty)
+constexpr int kK1 = 112, kN1 = 64;         // A1: 128 x 112, W: 112 x 64
+constexpr int kK2 = 64, kN2 = 112;         // A2: 128 x 64,  W^t: 64 x 112
+constexpr int kRE = 2 * kB + 4;            // region: 12 cells per side
+constexpr int kRN = kRE - 1;               // 11 interior node lines
+constexpr int kRegion = kRE * kRN * kRN;   // staged edges per direction
+constexpr int kOwn = 2 * kB;               // owned cells per side
+constexpr int kOwn3 = kOwn * kOwn * kOwn;  // owned edges per direction
+constexpr int kThreads = 128;
+constexpr uint32_t kTmemCols = 256;        // D1: cols [0,64), D2: cols [64,176)
+
+constexpr int OFF_A1 = 0;
+constexpr int OFF_B1 = OFF_A1 + kM * kK1 * 2;
+constexpr int OFF_A2 = OFF_B1 + kN1 * kK1 * 2;
+constexpr int OFF_B2 = OFF_A2 + kM * kK2 * 2;
+constexpr int OFF_R = OFF_B2 + kN2 * kK2 * 2;
+constexpr int OFF_ACC = OFF_R + 3 * kRegion * 4;
+constexpr int OFF_BAR = OFF_ACC + 3 * kOwn3 * 4;
+constexpr int OFF_TM = OFF_BAR + 16;
+constexpr int OFF_RED = OFF_TM + 16;
+constexpr int kSmem = OFF_RED + 16;
+static_assert(OFF_BAR % 8 == 0, "mbarrier alignment");
+static_assert(kSmem <= 110 * 1024, "two CTAs per SM");
+
+constexpr int kImgBytes = (kN1 * kK1 + kN2 * kK2) * 2;  // both W images
+constexpr int kTimeout = 1;                              // status code
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// byte offset of element (row, k) in a K-major no-swizzle operand of width K
+__host__ __device__ constexpr int core_off(int row, int k, int K) {
+  return ((row >> 3) * (K >> 3) + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo & 0x3FFFFu) >> 4) << 16;
+  d |= (uint64_t)((sbo & 0x3FFFFu) >> 4) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version of the tcgen05 family
+  return d;                // base offset 0, absolute LBO mode, no swizzle
+}
+
+// instruction descriptor, kind::f16: D f32, A/B bf16 (or f16), both K-major
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N, bool fp16) {
+  return (1u << 4) | ((fp16 ? 0u : 1u) << 7) | ((fp16 ? 0u : 1u) << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.b32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait: gives up after 2^20 polls or ~5e8 cycles (~0.25 s)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  for (int it = 0; it < (1 << 20); ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if (clock64() - t0 > 500000000LL) break;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 16 consecutive FP32 columns of this warp's 32 TMEM lanes (one row per thread)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+template <bool FP16>
+__device__ __forceinline__ uint32_t pack2(float a, float b) {
+  if constexpr (FP16) {
+    __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+  } else {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+  }
+}
+
+// patch-local edge l in [0,108) -> (direction, region coordinates) for the
+// patch at brick-relative vertex (a,b,c); the 4x4x4 box numbering of the
+// library (x: 4 segments x 3 x 3 nodes, then y, then z)
+__device__ __forceinline__ int region_index(int l, int a, int b, int c) {
+  int d, i, j, k;
+  if (l < 36) {
+    d = 0; i = l % 4; j = (l / 4) % 3; k = l / 12;
+  } else if (l < 72) {
+    l -= 36; d = 1; i = l % 3; j = (l / 3) % 4; k = l / 12;
+  } else {
+    l -= 72; d = 2; i = l % 3; j = (l / 3) % 3; k = l / 9;
+  }
+  i += 2 * a; j += 2 * b; k += 2 * c;
+  // region extents per direction: along-axis 12 segments, 11 node lines
+  if (d == 0) return (k * kRN + j) * kRE + i;
+  if (d == 1) return kRegion + (k * kRE + j) * kRN + i;
+  return 2 * kRegion + (k * kRN + j) * kRN + i;
+}
+
+// patch-local edge -> owned-accumulator slot (or -1 if not owned by the brick)
+__device__ __forceinline__ int owned_index(int l, int a, int b, int c) {
+  int d, i, j, k;
+  if (l < 36) {
+    d = 0; i = l % 4; j = (l / 4) % 3 + 1; k = l / 12 + 1;
+  } else if (l < 72) {
+    l -= 36; d = 1; i = l % 3 + 1; j = (l / 3) % 4; k = l / 12 + 1;
+  } else {
+    l -= 72; d = 2; i = l % 3 + 1; j = (l / 3) % 3 + 1; k = l / 9;
+  }
+  // global coordinate minus brick origin 2*(I0,J0,K0): patch origin is 2(a,b,c) - 2
+  i += 2 * a - 2; j += 2 * b - 2; k += 2 * c - 2;
+  if ((unsigned)i >= (unsigned)kOwn || (unsigned)j >= (unsigned)kOwn || (unsigned)k >= (unsigned)kOwn) return -1;
+  return d * kOwn3 + (k * kOwn + j) * kOwn + i;
+}
+
+__device__ __forceinline__ int64_t gidx(int n, int d, int i, int j, int k) {
+  const int64_t N3 = (int64_t)n * (n - 1) * (n - 1);
+  if (d == 0) return ((int64_t)(k - 1) * (n - 1) + (j - 1)) * n + i;
+  if (d == 1) return N3 + ((int64_t)(k - 1) * n + j) * (n - 1) + (i - 1);
+  return 2 * N3 + ((int64_t)k * (n - 1) + (j - 1)) * (n - 1) + (i - 1);
+}
+
+// is (i,j,k) an interior edge of direction d on an n^3 mesh?
+__device__ __forceinline__ bool interior(int n, int d, int i, int j, int k) {
+  const int p[3] = {i, j, k};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (a == d) {
+      if (p[a] < 0 || p[a] >= n) return false;
+    } else if (p[a] < 1 || p[a] > n - 1) {
+      return false;
+    }
+  }
+  return true;
+}
+
+template <bool FP16>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_tc_patch(int n, const uint8_t* __restrict__ img, float eta, const float* __restrict__ r, float* __restrict__ z,
+               int* __restrict__ status) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nc = n / 2;
+  const int nbr = (nc + kB - 1) / kB;
+  const int bx = blockIdx.x % nbr, by = (blockIdx.x / nbr) % nbr, bz = blockIdx.x / (nbr * nbr);
+  const int I0 = bx * kB, J0 = by * kB, K0 = bz * kB;
+
+  // a CTA of an earlier launch gave up on a wait: do nothing until the host
+  // has read and cleared the status word
+  if (*reinterpret_cast<volatile int*>(status) != 0) return;
+
+  float* R = reinterpret_cast<float*>(smem + OFF_R);
+  float* ACC = reinterpret_cast<float*>(smem + OFF_ACC);
+  const uint32_t bar0 = smem_u32(smem + OFF_BAR), bar1 = bar0 + 8;
+  uint32_t* tm_slot = reinterpret_cast<uint32_t*>(smem + OFF_TM);
+  float* red = reinterpret_cast<float*>(smem + OFF_RED);
+
+  // ---- set-up: TMEM, barriers, both W images ---------------------------------
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tm_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar0), "r"(1) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar1), "r"(1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(img);
+    uint4* dst = reinterpret_cast<uint4*>(smem + OFF_B1);   // B1 and B2 are contiguous
+    for (int q = tid; q < kImgBytes / 16; q += kThreads) dst[q] = __ldg(src + q);
+  }
+  const float wscale = __ldg(reinterpret_cast<const float*>(img + kImgBytes));  // 1 / s_w^2
+
+  // ---- 1. stage r on the region, zero the accumulator -------------------------
+  // region origins (global): x-edges (2I0-2, 2J0-1, 2K0-1), y-edges (2I0-1,
+  // 2J0-2, 2K0-1), z-edges (2I0-1, 2J0-1, 2K0-2)
+  float amax = 0.f;
+  for (int q = tid; q < 3 * kRegion; q += kThreads) {
+    const int d = q / kRegion, e = q - d * kRegion;
+    int i, j, k;
+    if (d == 0) { i = e % kRE; j = (e / kRE) % kRN; k = e / (kRE * kRN); }
+    else if (d == 1) { i = e % kRN; j = (e / kRN) % kRE; k = e / (kRN * kRE); }
+    else { i = e % kRN; j = (e / kRN) % kRN; k = e / (kRN * kRN); }
+    const int gi = 2 * I0 + i - (d == 0 ? 2 : 1);
+    const int gj = 2 * J0 + j - (d == 1 ? 2 : 1);
+    const int gk = 2 * K0 + k - (d == 2 ? 2 : 1);
+    float v = 0.f;
+    if (interior(n, d, gi, gj, gk)) v = __ldg(r + gidx(n, d, gi, gj, gk));
+    R[q] = v;
+    amax = fmaxf(amax, fabsf(v));
+  }
+  for (int q = tid; q < 3 * kOwn3; q += kThreads) ACC[q] = 0.f;
+  // fp16 operands: scale r by a power of two so that max |r| <= 1 on the region
+  float rscale = 1.f;
+  if constexpr (FP16) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if (lane == 0) red[warp] = amax;
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tm_slot;
+  if constexpr (FP16) {
+    const float m = fmaxf(fmaxf(red[0], red[1]), fmaxf(red[2], red[3]));
+    if (m > 0.f) rscale = exp2f(-ceilf(log2f(m)));
+  }
+
+  // ---- 2. gather the patch vectors into A1 ------------------------------------
+  {
+    const int p = tid;  // one patch row per thread
+    const int a = p % 5, b = (p / 5) % 5, c = p / 25;
+    const bool live = p < 125 && (I0 + a) >= 1 && (I0 + a) <= nc - 1 && (J0 + b) >= 1 && (J0 + b) <= nc - 1 &&
+                      (K0 + c) >= 1 && (K0 + c) <= nc - 1;
+    uint8_t* A1 = smem + OFF_A1;
+#pragma unroll 1
+    for (int ch = 0; ch < kK1 / 8; ++ch) {
+      float v[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int l = ch * 8 + t;
+        v[t] = (live && l < 108) ? R[region_index(l, a, b, c)] * rscale : 0.f;
+      }
+      uint4 w;
+      w.x = pack2<FP16>(v[0], v[1]);
+      w.y = pack2<FP16>(v[2], v[3]);
+      w.z = pack2<FP16>(v[4], v[5]);
+      w.w = pack2<FP16>(v[6], v[7]);
+      *reinterpret_cast<uint4*>(A1 + core_off(p, ch * 8, kK1)) = w;
+    }
+  }
+  fence_async_smem();
+  __syncthreads();
+
+  // ---- 3. D1 = A1 W ---------------------------------------------------------
+  bool ok = true;
+  if (tid == 0) {
+    fence_after();
+    const uint32_t a0 = smem_u32(smem + OFF_A1), b0 = smem_u32(smem + OFF_B1);
+    const uint32_t idesc = instr_desc(kM, kN1, FP16);
+#pragma unroll
+    for (int kk = 0; kk < kK1 / 16; ++kk)
+      mma_f16(tmem, smem_desc(a0 + kk * 256, 128, (kK1 / 8) * 128), smem_desc(b0 + kk * 256, 128, (kK1 / 8) * 128),
+              idesc, kk > 0);
+    mma_commit(bar0);
+  }
+  ok = mbar_wait(bar0, 0);
+  fence_after();
+
+  // ---- 4. A2 = low-precision copy of D1 ----------------------------------------
+  if (ok) {
+    const int p = warp * 32 + lane;
+    uint8_t* A2 = smem + OFF_A2;
+#pragma unroll 1
+    for (int cb = 0; cb < kN1; cb += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + cb, v);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        uint4 w;
+        w.x = pack2<FP16>(v[8 * h + 0], v[8 * h + 1]);
+        w.y = pack2<FP16>(v[8 * h + 2], v[8 * h + 3]);
+        w.z = pack2<FP16>(v[8 * h + 4], v[8 * h + 5]);
+        w.w = pack2<FP16>(v[8 * h + 6], v[8 * h + 7]);
+        *reinterpret_cast<uint4*>(A2 + core_off(p, cb + 8 * h, kK2)) = w;
+      }
+    }
+  }
+  fence_async_smem();
+  fence_before();
+  __syncthreads();
+
+  // ---- 5. D2 = A2 W^t -------------------------------------------------------
+  if (tid == 0 && ok) {
+    fence_after();
+    const uint32_t a0 = smem_u32(smem + OFF_A2), b0 = smem_u32(smem + OFF_B2);
+    const uint32_t idesc = instr_desc(kM, kN2, FP16);
+#pragma unroll
+    for (int kk = 0; kk < kK2 / 16; ++kk)
+      mma_f16(tmem + kN1, smem_desc(a0 + kk * 256, 128, (kK2 / 8) * 128),
+              smem_desc(b0 + kk * 256, 128, (kK2 / 8) * 128), idesc, kk > 0);
+    mma_commit(bar1);
+  }
+  if (ok) ok = mbar_wait(bar1, 0);
+  fence_after();
+
+  // ---- 6. accumulate owned outputs --------------------------------------------
+  if (ok) {
+    const int p = warp * 32 + lane;
+    const int a = p % 5, b = (p / 5) % 5, c = p / 25;
+    const bool live = p < 125 && (I0 + a) >= 1 && (I0 + a) <= nc - 1 && (J0 + b) >= 1 && (J0 + b) <= nc - 1 &&
+                      (K0 + c) >= 1 && (K0 + c) <= nc - 1;
+#pragma unroll 1
+    for (int cb = 0; cb < kN2; cb += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + kN1 + cb, v);
+      if (live) {
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+          const int l = cb + t;
+          if (l < 108) {
+            const int s = owned_index(l, a, b, c);
+            if (s >= 0) atomicAdd(ACC + s, v[t]);
+          }
+        }
+      }
+    }
+  } else if (tid == 0) {
+    atomicExch(status, kTimeout);
+  }
+  fence_before();
+  __syncthreads();
+
+  // ---- 7. z[owned] += eta * acc / (s_w^2 s_r) ---------------------------------
+  if (ok) {
+    const float sc = eta * wscale / rscale;
+    for (int q = tid; q < 3 * kOwn3; q += kThreads) {
+      const int d = q / kOwn3, e = q - d * kOwn3;
+      const int i = 2 * I0 + e % kOwn, j = 2 * J0 + (e / kOwn) % kOwn, k = 2 * K0 + e / (kOwn * kOwn);
+      if (interior(n, d, i, j, k)) {
+        const int64_t g = gidx(n, d, i, j, k);
+        z[g] += sc * ACC[q];
+      }
+    }
+  }
+  if (warp == 0) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+}  // namespace
+
+cudaError_t upload_tc_operand(void** dst, const std::vector<double>& W, bool fp16) {
+  // W: 108 x 60 row-major.  Scale by a power of two so that max |W| <= 1.
+  double mx = 0.0;
+  for (double v : W) mx = std::fmax(mx, std::fabs(v));
+  const double sw = mx > 0 ? std::exp2(-std::ceil(std::log2(mx))) : 1.0;
+  std::vector<uint8_t> img(kImgBytes + 16, 0);
+  auto put = [&](uint8_t* base, int row, int k, int K, double v) {
+    uint16_t bits;
+    if (fp16) {
+      __half hv = __double2half(v);
+      bits = *reinterpret_cast<uint16_t*>(&hv);
+    } else {
+      __nv_bfloat16 bv = __double2bfloat16(v);
+      bits = *reinterpret_cast<uint16_t*>(&bv);
+    }
+    *reinterpret_cast<uint16_t*>(base + core_off(row, k, K)) = bits;
+  };
+  uint8_t* b1 = img.data();                    // B1[n][k] = W[k][n]: N = 64, K = 112
+  uint8_t* b2 = img.data() + kN1 * kK1 * 2;    // B2[n][k] = W[n][k]: N = 112, K = 64
+  for (int l = 0; l < 108; ++l)
+    for (int c = 0; c < 60; ++c) {
+      const double v = W[(size_t)l * 60 + c] * sw;
+      put(b1, c, l, kK1, v);
+      put(b2, l, c, kK2, v);
+    }
+  const float inv = (float)(1.0 / (sw * sw));
+  std::memcpy(img.data() + kImgBytes, &inv, sizeof(float));
+  if (!*dst) {
+    cudaError_t e = cudaMalloc(dst, img.size());
+    if (e != cudaSuccess) return e;
+  }
+  return cudaMemcpy(*dst, img.data(), img.size(), cudaMemcpyHostToDevice);
+}
+
+cudaError_t prepare_tc_patch() {
+  cudaError_t e = cudaFuncSetAttribute(k_tc_patch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_patch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+  return e;
+}
+
+void launch_tc_patch(cudaStream_t s, int, int n, const void* Wimg, bool fp16, double eta, const float* r, float* z,
+                     int* status) {
+  const int nc = n / 2;
+  if (nc < 2) return;
+  const int nbr = (nc + kB - 1) / kB;
+  const int grid = nbr * nbr * nbr;
+  if (fp16)
+    k_tc_patch<true><<<grid, kThreads, kSmem, s>>>(n, (const uint8_t*)Wimg, (float)eta, r, z, status);
+  else
+    k_tc_patch<false><<<grid, kThreads, kSmem, s>>>(n, (const uint8_t*)Wimg, (float)eta, r, z, status);
+}
 
 }  // namespace ndmg

@@ -1,0 +1,155 @@
+"""GPU checks of the mixed-precision path: FP32 vectors, vertex-patch solves
+on tensor cores (tcgen05) in bf16 / fp16 with FP32 accumulation, FP64
+iterative refinement outside (arXiv 2205.05840, eq. Preconditioner P, Fig. 1).
+
+Tolerances are derived from the operand precision: a patch output is a sum
+over 108 (then 60) products of rounded operands, each carrying a relative
+rounding error of at most u = 2^-8 (bf16) or 2^-11 (fp16) per rounding and
+two roundings in sequence (r, then W^t r); measured against the largest
+entry, the error stays below 8u.  FP32 stencil / transfer results are held to
+2e-6 relative.  Refined solves must reach the FP64 tolerance 1e-8 exactly as
+the FP64 path does.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import hcurl, mg
+from paper_2205_05840_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+try:
+    from paper_2205_05840_gb300 import ndmg
+except ImportError:
+    if torch.cuda.is_available():
+        raise
+    pytest.skip("library not built and no GPU here", allow_module_level=True)
+
+DEV = "cuda"
+U = {"bf16": 2.0 ** -8, "fp16": 2.0 ** -11}
+
+
+def prec_code(p):
+    return {"bf16": ndmg.PREC_MIXED_BF16, "fp16": ndmg.PREC_MIXED_FP16}[p]
+
+
+def T(x, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype, device=DEV)
+
+
+def N(t):
+    torch.cuda.synchronize()
+    return t.detach().double().cpu().numpy()
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+@pytest.mark.parametrize("n,alpha", [(4, 1.0), (8, 1.0), (12, 0.01), (20, 100.0), (32, 1.0)])
+def test_tc_smoothing_step(prec, n, alpha):
+    # one smoothing step z <- z + M_V^{-1}(g - A z) on float vectors, patch
+    # solves on tensor cores, against the FP64 oracle
+    S = ndmg.Solver(n, n_coarsest=n // 2, alpha=alpha, precision=prec_code(prec))
+    A = hcurl.assemble(n, 1.0, alpha, 1.0)
+    Sm = mg.Smoother(A, n, "vertex")
+    rng = np.random.default_rng(n)
+    g = rng.standard_normal(A.shape[0]).astype(np.float32).astype(np.float64)
+    z = rng.standard_normal(A.shape[0]).astype(np.float32).astype(np.float64)
+    corr = Sm.apply(g - A @ z)
+    zt = T(z)
+    S.smooth(T(g), zt, steps=1, level=-1)
+    got = N(zt) - z
+    assert rel(got, corr) < 8 * U[prec]
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_tc_patch_columns(prec):
+    # a unit residual on single edges: the correction is one column of the
+    # smoother (every patch index must land on the right edge)
+    n = 12
+    S = ndmg.Solver(n, n_coarsest=6, precision=prec_code(prec))
+    A = hcurl.assemble(n, 1.0, 1.0, 1.0)
+    Sm = mg.Smoother(A, n, "vertex")
+    Nn = A.shape[0]
+    # g = A z + e_j  =>  residual = e_j exactly (FP32 stencil on z = 0)
+    for j in (0, 17, Nn // 3, Nn // 2 + 5, Nn - 1, hcurl.edge_index(n, 1, 5, 6, 7), hcurl.edge_index(n, 2, 6, 6, 6)):
+        g = np.zeros(Nn)
+        g[j] = 1.0
+        zt = torch.zeros(Nn, dtype=torch.float32, device=DEV)
+        S.smooth(T(g), zt, steps=1)
+        col = Sm.apply(g)
+        got = N(zt)
+        assert rel(got, col) < 8 * U[prec], j
+        assert set(np.nonzero(np.abs(got) > 1e-3 * np.abs(col).max())[0]) <= set(np.nonzero(col)[0])
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+@pytest.mark.parametrize("n,n0", [(16, 2), (32, 4), (24, 3)])
+def test_mixed_vcycle_close_to_oracle(prec, n, n0):
+    S = ndmg.Solver(n, n_coarsest=n0, precision=prec_code(prec))
+    H = mg.Hierarchy(n, 1.0, 1.0, 1.0, n0=n0, m=2)
+    f = inputs.random_load(n, 0)
+    ref = H.vcycle(f, np.zeros_like(f))
+    zt = torch.zeros(f.size, dtype=torch.float32, device=DEV)
+    S.vcycle(T(f), zt)
+    # one V-cycle is a product of ~(4m+1)*levels rounded operators; the
+    # deviation from the FP64 cycle stays within 16u of the result's size
+    assert rel(N(zt), ref) < 16 * U[prec]
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16", "fp32"])
+@pytest.mark.parametrize("n,n0,alpha", [(32, 4, 1.0), (64, 4, 0.01), (48, 3, 100.0)])
+def test_mixed_refined_solve_reaches_fp64_tolerance(prec, n, n0, alpha):
+    code = ndmg.PREC_FP32 if prec == "fp32" else prec_code(prec)
+    S = ndmg.Solver(n, n_coarsest=n0, alpha=alpha, precision=code)
+    f = inputs.random_load(n, 4)
+    u = torch.zeros(f.size, dtype=torch.float64, device=DEV)
+    st, it, rr = S.solve(T(f, torch.float64), u, tol=1e-8, maxit=300)
+    assert rr <= 1e-8
+    # independent FP64 check of the residual, then against the FP64 GPU solve
+    S64 = ndmg.Solver(n, n_coarsest=n0, alpha=alpha)
+    r = torch.empty_like(u)
+    S64.residual(T(f, torch.float64), u, r)
+    assert np.linalg.norm(N(r)) / np.linalg.norm(f) <= 1.01e-8
+    u64 = torch.zeros_like(u)
+    S64.solve(T(f, torch.float64), u64, tol=1e-10)
+    assert rel(N(u), N(u64)) < 1e-6
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_mixed_128_full_size(prec):
+    # the benchmark configuration: 128^3, alpha = 1, seed-0 load, coarsest 4^3
+    n = 128
+    S = ndmg.Solver(n, n_coarsest=4, precision=prec_code(prec))
+    f = inputs.random_load(n, 0)
+    ft = T(f, torch.float64)
+    u = torch.zeros(f.size, dtype=torch.float64, device=DEV)
+    st, it, rr = S.solve(ft, u, tol=1e-8, maxit=300)
+    assert rr <= 1e-8 and it < 60
+    S64 = ndmg.Solver(n, n_coarsest=4)
+    r = torch.empty_like(u)
+    S64.residual(ft, u, r)
+    assert np.linalg.norm(N(r)) / np.linalg.norm(f) <= 1.01e-8
+    # sampled rows of the operator in FP32 against the oracle
+    x = np.random.default_rng(3).standard_normal(f.size).astype(np.float32)
+    y = torch.empty(f.size, dtype=torch.float32, device=DEV)
+    S.apply(T(x), y)
+    rows = np.random.default_rng(4).integers(0, f.size, 2000)
+    ref = hcurl.apply_rows(n, 1.0, 1.0, 1.0, x.astype(np.float64), rows)
+    assert rel(N(y)[rows], ref) < 2e-6
+
+
+def test_mixed_manufactured_64():
+    n, alpha = 64, 1.0
+    h = 1.0 / n
+    S = ndmg.Solver(n, n_coarsest=4, alpha=alpha, precision=ndmg.PREC_MIXED_BF16)
+    f = inputs.manufactured_load(n, 1.0, alpha, 1.0)
+    u = torch.zeros(f.size, dtype=torch.float64, device=DEV)
+    st, it, rr = S.solve(T(f, torch.float64), u, tol=1e-8)
+    mu = (2.0 + np.cos(np.pi * h)) / 3.0
+    sig = (np.sin(np.pi * h / 2) / (np.pi * h / 2)) ** 2
+    c = (2 * np.pi ** 2 * alpha + 1) * sig ** 2 / (8 * alpha * np.sin(np.pi * h / 2) ** 2 * mu / h ** 2 + mu ** 2)
+    assert rr <= 1e-8 and rel(N(u), c * inputs.sine_interpolant(n)) < 1e-6
