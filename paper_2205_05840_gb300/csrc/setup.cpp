@@ -12,6 +12,7 @@
 //                   K = -h s_a s_b' m_{b a'}   (second edge along axis d+1)
 // The local spaces of Sec. 3.2 are boxes of cells with only the edges in the
 // box's relative interior, which is the same numbering as the global mesh.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <stdexcept>
@@ -112,32 +113,39 @@ bool cholesky(std::vector<double>& a, int n) {
   return true;
 }
 
-// inverse of a lower-triangular matrix
-static std::vector<double> lower_inverse(const std::vector<double>& Lm, int n) {
-  std::vector<double> X((size_t)n * n, 0.0);
-  for (int c = 0; c < n; ++c) {
-    for (int i = c; i < n; ++i) {
-      double s = (i == c) ? 1.0 : 0.0;
-      for (int k = c; k < i; ++k) s -= Lm[(size_t)i * n + k] * X[(size_t)k * n + c];
-      X[(size_t)i * n + c] = s / Lm[(size_t)i * n + i];
-    }
+// solve L y = b in place (L lower triangular, row-major)
+void forward_solve(const std::vector<double>& Lm, int n, double* b) {
+  for (int i = 0; i < n; ++i) {
+    double s = b[i];
+    for (int k = 0; k < i; ++k) s -= Lm[(size_t)i * n + k] * b[k];
+    b[i] = s / Lm[(size_t)i * n + i];
   }
-  return X;
+}
+
+// solve L L^t x = b in place
+void chol_solve(const std::vector<double>& Lm, int n, double* b) {
+  forward_solve(Lm, n, b);
+  for (int i = n - 1; i >= 0; --i) {
+    double s = b[i];
+    for (int k = i + 1; k < n; ++k) s -= Lm[(size_t)k * n + i] * b[k];
+    b[i] = s / Lm[(size_t)i * n + i];
+  }
 }
 
 std::vector<double> spd_inverse(const std::vector<double>& a, int n, bool* ok) {
   std::vector<double> Lm = a;
   *ok = cholesky(Lm, n);
   if (!*ok) return {};
-  std::vector<double> Li = lower_inverse(Lm, n);
-  std::vector<double> inv((size_t)n * n, 0.0);
-  // A^{-1} = L^{-T} L^{-1}
+  std::vector<double> inv((size_t)n * n, 0.0), e(n);
+  for (int c = 0; c < n; ++c) {
+    for (int i = 0; i < n; ++i) e[i] = (i == c) ? 1.0 : 0.0;
+    chol_solve(Lm, n, e.data());
+    for (int i = 0; i < n; ++i) inv[(size_t)i * n + c] = e[i];
+  }
   for (int i = 0; i < n; ++i)
-    for (int j = 0; j <= i; ++j) {
-      double s = 0.0;
-      for (int k = i; k < n; ++k) s += Li[(size_t)k * n + i] * Li[(size_t)k * n + j];
-      inv[(size_t)i * n + j] = s;
-      inv[(size_t)j * n + i] = s;
+    for (int j = 0; j < i; ++j) {
+      const double m = 0.5 * (inv[(size_t)i * n + j] + inv[(size_t)j * n + i]);
+      inv[(size_t)i * n + j] = inv[(size_t)j * n + i] = m;
     }
   return inv;
 }
@@ -191,34 +199,48 @@ void build_local_ops(int n, double L, double alpha, double beta, LocalOps* out) 
     for (int b = 0; b < nG; ++b) AIG[(size_t)a * nG + b] = Ap[(size_t)I[a] * np + G[b]];
   for (int a = 0; a < nG; ++a)
     for (int b = 0; b < nG; ++b) AGG[(size_t)a * nG + b] = Ap[(size_t)G[a] * np + G[b]];
-  std::vector<double> AIIinv = spd_inverse(AII, nI, &ok);
-  if (!ok) throw std::runtime_error("bubble block is not SPD");
-  // X = A_II^{-1} A_IG (nI x nG)
-  std::vector<double> X((size_t)nI * nG, 0.0);
-  for (int a = 0; a < nI; ++a)
-    for (int k = 0; k < nI; ++k) {
-      const double v = AIIinv[(size_t)a * nI + k];
-      for (int b = 0; b < nG; ++b) X[(size_t)a * nG + b] += v * AIG[(size_t)k * nG + b];
-    }
+  // Every step below uses triangular solves with Cholesky factors, never an
+  // explicit inverse: for alpha / (beta h^2) ~ 1e4 and beyond the patch matrix
+  // has cond ~ 1e6, and explicit inverses lose three more digits than solves.
+  std::vector<double> LII = AII;
+  if (!cholesky(LII, nI)) throw std::runtime_error("bubble block is not SPD");
+  // X = A_II^{-1} A_IG (nI x nG), column by column
+  std::vector<double> X((size_t)nI * nG, 0.0), col(nI);
+  for (int b = 0; b < nG; ++b) {
+    for (int a = 0; a < nI; ++a) col[a] = AIG[(size_t)a * nG + b];
+    chol_solve(LII, nI, col.data());
+    for (int a = 0; a < nI; ++a) X[(size_t)a * nG + b] = col[a];
+  }
+  // Schur complement S = A_GG - A_GI X, symmetrised
   std::vector<double> S = AGG;
   for (int a = 0; a < nG; ++a)
     for (int b = 0; b < nG; ++b) {
-      double s = 0.0;
-      for (int k = 0; k < nI; ++k) s += AIG[(size_t)k * nG + a] * X[(size_t)k * nG + b];
-      S[(size_t)a * nG + b] -= s;
+      double sdot = 0.0;
+      for (int k = 0; k < nI; ++k) sdot += AIG[(size_t)k * nG + a] * X[(size_t)k * nG + b];
+      S[(size_t)a * nG + b] -= sdot;
+    }
+  for (int a = 0; a < nG; ++a)
+    for (int b = 0; b < a; ++b) {
+      const double m = 0.5 * (S[(size_t)a * nG + b] + S[(size_t)b * nG + a]);
+      S[(size_t)a * nG + b] = S[(size_t)b * nG + a] = m;
     }
   std::vector<double> R = S;
   if (!cholesky(R, nG)) throw std::runtime_error("Schur complement is not SPD");
-  std::vector<double> Ri = lower_inverse(R, nG);        // R^{-1}; R^{-T} = Ri^t
+  // W^t = R^{-1} H^t with H = [-X ; I] (patch order): forward substitution on
+  // each of the 108 columns of H^t
   out->Wv.assign((size_t)np * nG, 0.0);
-  for (int a = 0; a < nG; ++a)                          // interface rows: R^{-T}
-    for (int c = 0; c < nG; ++c) out->Wv[(size_t)G[a] * nG + c] = Ri[(size_t)c * nG + a];
-  for (int a = 0; a < nI; ++a)                          // bubble rows: -X R^{-T}
-    for (int c = 0; c < nG; ++c) {
-      double s = 0.0;
-      for (int b = 0; b < nG; ++b) s += X[(size_t)a * nG + b] * Ri[(size_t)c * nG + b];
-      out->Wv[(size_t)I[a] * nG + c] = -s;
+  std::vector<double> ht(nG);
+  for (int e = 0; e < np; ++e) {
+    if (isB[e]) {
+      const int a = (int)(std::find(I.begin(), I.end(), e) - I.begin());
+      for (int c = 0; c < nG; ++c) ht[c] = -X[(size_t)a * nG + c];
+    } else {
+      const int g = (int)(std::find(G.begin(), G.end(), e) - G.begin());
+      for (int c = 0; c < nG; ++c) ht[c] = (c == g) ? 1.0 : 0.0;
     }
+    forward_solve(R, nG, ht.data());
+    for (int c = 0; c < nG; ++c) out->Wv[(size_t)e * nG + c] = ht[c];
+  }
   // The dense operator used by the CUDA-core kernels is D = W W^t as well:
   // forming A_p^{-1} - Bblk instead would cancel the large bubble entries and
   // lose ~cond(A_p) digits.  Self-check with a residual that stays well

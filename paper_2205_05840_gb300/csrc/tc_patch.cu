@@ -45,10 +45,10 @@ constexpr int kThreads = 128;
 constexpr uint32_t kTmemCols = 256;        // D1: cols [0,64), D2: cols [64,176)
 
 constexpr int OFF_A1 = 0;
-constexpr int OFF_B1 = OFF_A1 + kM * kK1 * 2;
-constexpr int OFF_A2 = OFF_B1 + kN1 * kK1 * 2;
-constexpr int OFF_B2 = OFF_A2 + kM * kK2 * 2;
-constexpr int OFF_R = OFF_B2 + kN2 * kK2 * 2;
+constexpr int OFF_B1 = OFF_A1 + kM * kK1 * 2;   // B1 and B2 contiguous: one copy of both images
+constexpr int OFF_B2 = OFF_B1 + kN1 * kK1 * 2;
+constexpr int OFF_A2 = OFF_B2 + kN2 * kK2 * 2;
+constexpr int OFF_R = OFF_A2 + kM * kK2 * 2;
 constexpr int OFF_ACC = OFF_R + 3 * kRegion * 4;
 constexpr int OFF_BAR = OFF_ACC + 3 * kOwn3 * 4;
 constexpr int OFF_TM = OFF_BAR + 16;
@@ -58,6 +58,7 @@ static_assert(OFF_BAR % 8 == 0, "mbarrier alignment");
 static_assert(kSmem <= 110 * 1024, "two CTAs per SM");
 
 constexpr int kImgBytes = (kN1 * kK1 + kN2 * kK2) * 2;  // both W images
+static_assert(OFF_B2 - OFF_B1 == kN1 * kK1 * 2 && OFF_A2 - OFF_B1 == kImgBytes, "W images are copied as one block");
 constexpr int kTimeout = 1;                              // status code
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {

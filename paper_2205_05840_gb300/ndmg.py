@@ -110,7 +110,7 @@ class Solver:
         st = _lib.ndmg_create(ctypes.byref(o), ctypes.byref(self._h))
         if st != OK:
             raise NdmgError(st, "ndmg_create failed")
-        self.n, self.precision, self.nrhs = n, precision, nrhs
+        self.n, self.precision, self.nrhs, self.alpha = n, precision, nrhs, alpha
         lv = _i32()
         _lib.ndmg_num_levels(self._h, ctypes.byref(lv))
         self.num_levels = lv.value
@@ -149,6 +149,7 @@ class Solver:
 
     def set_alpha(self, alpha: float):
         self._check(_lib.ndmg_set_alpha(self._h, alpha), "set_alpha")
+        self.alpha = alpha
 
     # -- level operations ---------------------------------------------------
     def apply(self, x, y, level: int = -1):

@@ -40,6 +40,16 @@ def rel(a, b):
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
 
 
+def patch_tol(n, alpha, base, L=1.0, beta=1.0):
+    """Agreement two FP64 computations of the vertex-patch solve can reach:
+    the patch matrix (4x4x4 cells) has cond ~ alpha / (beta h^2), and a
+    Cholesky-based solve is accurate to ~cond * eps; below that the base
+    tolerance applies."""
+    h = L / n
+    kappa = np.linalg.cond(hcurl.assemble(4, 4 * h, alpha, beta).toarray())
+    return max(base, 8.0 * kappa * np.finfo(float).eps)
+
+
 @pytest.mark.parametrize("n,n0,L,alpha,beta", [(2, 2, 1.0, 1.0, 1.0), (4, 2, 1.0, 0.3, 2.0), (6, 3, 2.0, 10.0, 1.0),
                                               (8, 2, 1.0, 1.0, 1.0), (16, 4, 1.0, 0.01, 1.0), (12, 3, 1.0, 100.0, 0.5)])
 def test_apply_and_residual_parity(n, n0, L, alpha, beta):
@@ -108,7 +118,7 @@ def test_smoothing_step_parity(n, alpha):
         ref = ref + Sm.apply(g - A @ ref)
     zt = T(z)
     S.smooth(T(g), zt, steps=2, level=-1)
-    assert rel(N(zt), ref) < 1e-12
+    assert rel(N(zt), ref) < patch_tol(n, alpha, 1e-12)
 
 
 @pytest.mark.parametrize("n,n0,alpha,m", [(8, 2, 1.0, 2), (16, 4, 0.01, 2), (12, 3, 100.0, 1), (32, 4, 1.0, 2)])
@@ -120,10 +130,11 @@ def test_vcycle_iterates_parity(n, n0, alpha, m):
     z = np.zeros_like(f)
     zt = T(z)
     ft = T(f)
+    tol = patch_tol(n, alpha, 1e-10)
     for it in range(5):
         z = H.vcycle(f, z)
         S.vcycle(ft, zt)
-        assert rel(N(zt), z) < 1e-10, it
+        assert rel(N(zt), z) < tol, it
 
 
 def test_config1_standalone_vcycle_iteration():
