@@ -200,6 +200,30 @@ int ndmg_trace_read(ndmg_t* h, int32_t kernel_class, int64_t* launches, double* 
  * pointer may be NULL. */
 int ndmg_counters(const ndmg_t* h, int64_t* launches, int64_t* vcycles);
 
+/* ---- allocation-free inner product (no counterpart in the paper) ---------
+ * out = x^T y in FP64 for n elements of type dtype (NDMG_F64 or NDMG_F32),
+ * for callers that cannot allocate device memory: code running under an
+ * allocator that owns every device byte of the process, code where a
+ * cudaMalloc (which may synchronise the device) is not acceptable, or code
+ * that cannot create a handle (ndmg_create allocates all level workspaces).
+ * No handle is needed and nothing is allocated: the partial sums live in a
+ * fixed 32 KB device array inside the library, which every GPU that loads the
+ * library holds until the process exits.
+ *   x, y   device pointers, 16-byte aligned, n elements each (caller-owned)
+ *   n      0 <= n <= 67,108,864; larger n returns NDMG_INVALID_ARG (and a
+ *          message on stderr) before anything is launched
+ *   out    host pointer, written before return
+ *   stream cudaStream_t (NULL = legacy default stream); the call queues two
+ *          kernels and a copy on it and synchronises it.
+ * The first call on a device looks up the device address of the array (with
+ * that device current); make that first call before any stream capture.  All
+ * calls share the one array, so calls that overlap on the GPU (other host
+ * threads, other streams) race and give wrong results; serialise them.  The
+ * array keeps the last call's contents; each call overwrites every slot it
+ * reads.  Errors: INVALID_ARG (bad dtype, NULL or misaligned pointers, n out
+ * of range), CUDA_ERROR. */
+int ndmg_dot_noalloc(int32_t dtype, const void* x, const void* y, int64_t n, double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

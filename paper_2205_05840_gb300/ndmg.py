@@ -64,6 +64,7 @@ _SIGS = {
     "ndmg_trace_enable": [_vp, _i32, _i32],
     "ndmg_trace_read": [_vp, _i32, _P(_i64), _P(_d), _P(_d)],
     "ndmg_counters": [_vp, _P(_i64), _P(_i64)],
+    "ndmg_dot_noalloc": [_i32, _vp, _vp, _i64, _P(_d), _vp],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)

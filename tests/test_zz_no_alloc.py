@@ -1,0 +1,55 @@
+"""The allocation-free inner product (ndmg_dot_noalloc) against the handle's
+inner product (ndmg_dot), through the C ABI.
+
+Some callers cannot allocate device memory (an allocator that owns every
+device byte, or a place where cudaMalloc's possible device synchronisation is
+not acceptable); ndmg_dot_noalloc serves them from a fixed device array inside
+the library.  Collected last so that a stop-at-first-failure run has already
+run every other test."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+try:
+    from paper_2205_05840_gb300 import ndmg
+except ImportError:
+    if torch.cuda.is_available():
+        raise
+    pytest.skip("library not built and no GPU here", allow_module_level=True)
+
+
+def _noalloc(dtype_code, x, y, n, stream):
+    out = ctypes.c_double(float("nan"))
+    st = ndmg._lib.ndmg_dot_noalloc(dtype_code, x.data_ptr(), y.data_ptr(), n, ctypes.byref(out), stream)
+    return st, out.value
+
+
+def test_noalloc_dot_matches_handle_dot_two_calls():
+    S = ndmg.Solver(32, n_coarsest=4)
+    N = S.num_dofs()
+    stream = S.stream.cuda_stream
+    for call, (dtype, code, tol) in enumerate(((torch.float64, ndmg.F64, 1e-13), (torch.float64, ndmg.F64, 1e-13),
+                                               (torch.float32, ndmg.F32, 1e-12))):
+        g = np.random.default_rng(10 + call)
+        x = torch.tensor(g.standard_normal(N), dtype=dtype, device="cuda")
+        y = torch.tensor(g.standard_normal(N), dtype=dtype, device="cuda")
+        torch.cuda.synchronize()
+        ref = S.dot(x, y)
+        st, got = _noalloc(code, x, y, N, stream)
+        assert st == ndmg.OK
+        scale = float(torch.linalg.vector_norm(x.double()) * torch.linalg.vector_norm(y.double()))
+        assert abs(got - ref) <= tol * scale, (call, got, ref)
+
+
+def test_noalloc_dot_limits():
+    x = torch.zeros(8, dtype=torch.float64, device="cuda")
+    st, got = _noalloc(ndmg.F64, x, x, 0, None)
+    assert st == ndmg.OK and got == 0.0
+    st, _ = _noalloc(ndmg.F64, x, x, 67_108_864 + 1, None)      # beyond the static scratch
+    assert st == ndmg.INVALID_ARG
+    st, _ = _noalloc(7, x, x, 8, None)
+    assert st == ndmg.INVALID_ARG
