@@ -47,7 +47,37 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--precision", choices=["auto", "fp64", "fp32", "bf16", "fp16"], default="auto")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    p.add_argument("--profile-case", choices=["none", "smooth", "residual", "vcycle"], default="none",
+                   help="run only a few launches of one kernel class on an --n grid (for ncu captures)")
+    p.add_argument("--n", type=int, default=N_GRID)
     return p.parse_args()
+
+
+def run_profile_case(args):
+    """A small, fixed sequence of launches for kernel captures: --steps
+    repetitions of one smoothing step, one residual or one V-cycle on the
+    finest level of an --n grid (inputs: seeded uniform load, z = 0)."""
+    import torch
+
+    from paper_2205_05840_gb300 import inputs, ndmg
+    prec = {"auto": ndmg.PREC_MIXED_BF16, "fp64": ndmg.PREC_FP64, "fp32": ndmg.PREC_FP32,
+            "bf16": ndmg.PREC_MIXED_BF16, "fp16": ndmg.PREC_MIXED_FP16}[args.precision]
+    dt = torch.float64 if prec == ndmg.PREC_FP64 else torch.float32
+    S = ndmg.Solver(args.n, n_coarsest=N_COARSEST, alpha=ALPHA, m=M_SMOOTH, precision=prec)
+    g = torch.tensor(inputs.random_load(args.n, 0), dtype=dt, device="cuda")
+    z = torch.zeros_like(g)
+    r = torch.empty_like(g)
+    for _ in range(args.warmup + args.steps):
+        if args.profile_case == "smooth":
+            S.smooth(g, z, steps=1)
+        elif args.profile_case == "residual":
+            S.residual(g, z, r)
+        else:
+            S.vcycle(g, z)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": args.profile_case, "n": args.n, "precision": args.precision,
+                      "launches": S.counters()[0]}))
 
 
 # --------------------------------------------------------------------------
@@ -108,19 +138,31 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # the oracle on the host cores
 # --------------------------------------------------------------------------
+class OracleSample:
+    """The FP64 CPU oracle's V-cycle on an n^3 problem (same alpha, m and
+    coarsest grid as the benchmark), set up once."""
+
+    def __init__(self, n: int):
+        import numpy as np
+        from oracle import mg
+        from paper_2205_05840_gb300 import inputs
+        self.n = n
+        self.H = mg.Hierarchy(n, 1.0, ALPHA, 1.0, n0=N_COARSEST, kind="vertex", m=M_SMOOTH)
+        self.f = inputs.random_load(n, 0)
+        self.z = np.zeros_like(self.f)
+
+    def cycles(self, k: int):
+        """Run k V-cycles; returns (DoF*cycles/s, seconds)."""
+        t0 = time.perf_counter()
+        for _ in range(k):
+            self.z = self.H.vcycle(self.f, self.z)
+        dt = time.perf_counter() - t0
+        return num_edges(self.n) * k / dt, dt
+
+
 def oracle_rate(n: int, cycles: int):
     """DoF*cycles/s of the FP64 CPU oracle's V-cycle on an n^3 problem."""
-    import numpy as np
-    from oracle import mg
-    from paper_2205_05840_gb300 import inputs
-    H = mg.Hierarchy(n, 1.0, ALPHA, 1.0, n0=N_COARSEST, kind="vertex", m=M_SMOOTH)
-    f = inputs.random_load(n, 0)
-    z = np.zeros_like(f)
-    t0 = time.perf_counter()
-    for _ in range(cycles):
-        z = H.vcycle(f, z)
-    dt = time.perf_counter() - t0
-    return num_edges(n) * cycles / dt, dt
+    return OracleSample(n).cycles(cycles)
 
 
 def cores_used():
@@ -135,11 +177,12 @@ def run_reference(args):
     if rank != 0:
         return
     # warm-up and timed steps: each step one oracle V-cycle on the sample grid
-    rate_w = [oracle_rate(ORACLE_SAMPLE_N, 1)[0] for _ in range(max(args.warmup, 0))]
-    del rate_w
+    sample_run = OracleSample(ORACLE_SAMPLE_N)
+    for _ in range(max(args.warmup, 0)):
+        sample_run.cycles(1)
     rates, secs = [], []
     for _ in range(args.steps):
-        r, dt = oracle_rate(ORACLE_SAMPLE_N, 1)
+        r, dt = sample_run.cycles(1)
         rates.append(r)
         secs.append(dt)
     value = num_edges(ORACLE_SAMPLE_N) * len(rates) / sum(secs)
@@ -249,10 +292,8 @@ def run_ours(args):
     bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
     dom = max(kern, key=lambda k: kern[k]["ms"])
     kd = kern[dom]
-    if dom == "patch":
-        if prec in (ndmg.PREC_MIXED_BF16, ndmg.PREC_MIXED_FP16):
-            bound, peak, unit, scale = "tensor", bf16, "TFLOP/s", 1e12
-        elif prec == ndmg.PREC_FP64:
+    if dom == "patch" and prec not in (ndmg.PREC_MIXED_BF16, ndmg.PREC_MIXED_FP16):
+        if prec == ndmg.PREC_FP64:
             bound, peak, unit, scale = "alu", FP64_PEAK_TFLOPS, "TFLOP/s", 1e12
         else:
             bound, peak, unit, scale = "alu", FP32_PEAK_TFLOPS, "TFLOP/s", 1e12
@@ -265,18 +306,20 @@ def run_ours(args):
             "launches": kd["launches"], "ms": kd["ms"]}
 
     # end to end through the host-buffer entry point
-    f_h = torch.tensor(inputs.random_load(N_GRID, seed=rank), dtype=torch.float64).pin_memory()
-    u_h = torch.zeros(Nd, dtype=torch.float64).pin_memory()
-    e2e_steps = max(1, min(args.steps, 3))
-    v_e0 = S.counters()[1]
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        u_h.zero_()
-        S.solve_host(f_h, u_h, tol=TOL, maxit=500)
-    t_e2e = time.perf_counter() - t0
-    v_e1 = S.counters()[1]
-    e2e_value = world * Nd * (v_e1 - v_e0) / t_e2e
+    e2e_value = None
+    if not args.no_e2e:
+        f_h = torch.tensor(inputs.random_load(N_GRID, seed=rank), dtype=torch.float64).pin_memory()
+        u_h = torch.zeros(Nd, dtype=torch.float64).pin_memory()
+        e2e_steps = max(1, min(args.steps, 3))
+        v_e0 = S.counters()[1]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            u_h.zero_()
+            S.solve_host(f_h, u_h, tol=TOL, maxit=500)
+        t_e2e = time.perf_counter() - t0
+        v_e1 = S.counters()[1]
+        e2e_value = world * Nd * (v_e1 - v_e0) / t_e2e
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -315,6 +358,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.profile_case != "none":
+        run_profile_case(args)
     else:
         run_ours(args)
 

@@ -144,14 +144,22 @@ int ndmg_vcycle(ndmg_t* h, int32_t dtype, const void* g, void* z);
 
 /* Solve A_K u = f to ||f - A u||_2 <= tol ||f||_2 with conjugate gradients
  * preconditioned by one V-cycle MG(K, ., 0, m) (symmetric: Remark 6).  FP64
- * handles run FP64 PCG; MIXED / FP32 handles run an FP64 iterative-refinement
- * loop around a float PCG + V-cycle (see ndmg_solve_ir).  f, u: double device
- * vectors, u in/out (warm start).  *iters: PCG iterations (total over
- * refinement sweeps), *relres: final relative residual in FP64 (either may
- * be NULL).  Returns NOT_CONVERGED after maxit iterations, BREAKDOWN on a
- * non-finite residual or non-positive curvature. */
+ * handles run FP64 PCG.  MIXED / FP32 handles run the same FP64 PCG (FP64
+ * vectors, residuals and inner products, flexible beta) with the float
+ * V-cycle as preconditioner: r / ||r|| is handed to the V-cycle in float and
+ * its result scaled back in double.  f, u: double device vectors, u in/out
+ * (warm start).  *iters: PCG iterations (= V-cycles), *relres: final relative
+ * residual in FP64 (either may be NULL).  Returns NOT_CONVERGED after maxit
+ * iterations, BREAKDOWN on a non-finite residual or non-positive curvature. */
 int ndmg_solve(ndmg_t* h, const double* f, double* u, double tol, int32_t maxit,
                int32_t* iters, double* relres);
+
+/* FP64 iterative refinement (MIXED / FP32 handles): repeat r = f - A u in
+ * FP64; solve A d = r / ||r|| with float PCG + float V-cycle to relative
+ * inner_tol (0 < inner_tol < 1); u += ||r|| d; until ||f - A u|| <= tol ||f||.
+ * maxit bounds the total inner PCG iterations (reported in *iters). */
+int ndmg_solve_ir(ndmg_t* h, const double* f, double* u, double tol, double inner_tol, int32_t maxit,
+                  int32_t* iters, double* relres);
 
 /* As ndmg_solve with HOST f and u: copies f in and u out on the handle's
  * stream (pinned memory recommended) and synchronises. */

@@ -140,17 +140,22 @@ void op_smoother(ndmg_t* h, int k, const T* r, T* z) {
 template <>
 void op_smoother<float>(ndmg_t* h, int k, const float* r, float* z) {
   DevLevel& L = h->lv[k];
+  if (mixed(h) && L.Wtc) {
+    // one tensor-core kernel for both terms (Gram form: two 108x60 products
+    // per patch; the 6x6 interior solves ride along)
+    // algorithmic bytes: read r, read and write z (FP32); 25,920 flops per
+    // patch is ~86 flop/B, below the bf16 ridge of ~256 flop/B: memory-bound
+    Span sp(h, NDMG_K_PATCH, 12.0 * L.N);
+    launch_tc_smoother(h->stream, L.n, L.Wtc, L.AinvT32, h->o.precision == NDMG_PREC_MIXED_FP16, h->o.eta, r, z,
+                       h->status);
+    return;
+  }
   {
     Span sp(h, NDMG_K_BUBBLE, bubble_bytes(L.n, sizeof(float)));
     launch_bubble<float>(h->stream, h->sm_count, L.n, L.AinvT32, h->o.eta, r, z);
   }
-  // Gram form on tensor cores: two 108x60 products per patch; dense otherwise
-  Span sp(h, NDMG_K_PATCH, num_patches(L.n) * ((mixed(h) && L.Wtc) ? 4.0 * 108 * 60 : 2.0 * 108 * 108));
-  if (mixed(h) && L.Wtc)
-    launch_tc_patch(h->stream, h->sm_count, L.n, L.Wtc, h->o.precision == NDMG_PREC_MIXED_FP16, h->o.eta, r, z,
-                    h->status);
-  else
-    launch_vertex_dense<float>(h->stream, h->sm_count, L.n, L.Dv32, h->o.eta, r, z);
+  Span sp(h, NDMG_K_PATCH, num_patches(L.n) * 2.0 * 108 * 108);
+  launch_vertex_dense<float>(h->stream, h->sm_count, L.n, L.Dv32, h->o.eta, r, z);
 }
 
 template <typename T>
@@ -335,7 +340,8 @@ int pcg32(ndmg_t* h, const float* b, float* d, double tol, int maxit, int* iters
 }
 
 // FP64 iterative refinement around the float PCG
-int solve_ir(ndmg_t* h, const double* f, double* u, double tol, int maxit, int* iters, double* relres) {
+int solve_ir(ndmg_t* h, const double* f, double* u, double tol, double inner_tol, int maxit, int* iters,
+             double* relres) {
   const int K = h->K;
   const int64_t N = h->lv[K].N;
   const int sm = h->sm_count;
@@ -345,7 +351,6 @@ int solve_ir(ndmg_t* h, const double* f, double* u, double tol, int maxit, int* 
   double ff, rr;
   int st;
   *iters = 0;
-  const double inner_tol = 1e-4;
   if ((st = dot2<double>(h, N, f, f, (const double*)nullptr, (const double*)nullptr, &ff, &rr)) != NDMG_OK) return st;
   const double nf = std::sqrt(ff) > 0 ? std::sqrt(ff) : 1.0;
   for (int outer = 0; outer < 64; ++outer) {
@@ -370,6 +375,68 @@ int solve_ir(ndmg_t* h, const double* f, double* u, double tol, int maxit, int* 
     NDMG_CK_LAUNCH();
   }
   return fail(h, NDMG_NOT_CONVERGED, "refinement stalled");
+}
+
+// FP64 flexible PCG preconditioned by the float V-cycle (mixed handles):
+// r, p, q, u and every inner product stay in double; the preconditioner sees
+// r / ||r|| in float (keeps fp16 operands in range) and returns z in double.
+// beta = -a (q . z_new) / (r . z)_old (flexible form: the low-precision
+// V-cycle is symmetric only up to rounding).
+int pcg_mixed(ndmg_t* h, const double* f, double* u, double tol, int maxit, int* iters, double* relres) {
+  const int K = h->K;
+  const int64_t N = h->lv[K].N;
+  const int sm = h->sm_count;
+  double *r = h->w64[0], *z = h->w64[1], *p = h->w64[2], *q = h->w64[3];
+  float *r32 = h->w32[4], *z32 = h->w32[5];
+  double ff, rr, rz, pq, dum;
+  int st;
+  *iters = 0;
+  auto precondition = [&](double rnorm) -> int {
+    {
+      Span sp(h, NDMG_K_BLAS, 12.0 * N);
+      launch_to_f32(h->stream, sm, N, 1.0 / rnorm, r, r32);
+    }
+    cudaMemsetAsync(z32, 0, sizeof(float) * N, h->stream);
+    op_vcycle<float>(h, K, r32, z32);
+    {
+      Span sp(h, NDMG_K_BLAS, 12.0 * N);
+      launch_from_f32(h->stream, sm, N, rnorm, z32, z);
+    }
+    return mixed(h) ? check_status(h) : NDMG_OK;
+  };
+  op_residual<double>(h, K, f, u, r);
+  if ((st = dot2<double>(h, N, f, f, r, r, &ff, &rr)) != NDMG_OK) return st;
+  const double nf = std::sqrt(ff) > 0 ? std::sqrt(ff) : 1.0;
+  *relres = std::sqrt(rr) / nf;
+  if (!std::isfinite(*relres)) return fail(h, NDMG_BREAKDOWN, "non-finite residual");
+  if (*relres <= tol) return NDMG_OK;
+  if ((st = precondition(std::sqrt(rr))) != NDMG_OK) return st;
+  if ((st = dot2<double>(h, N, r, z, (const double*)nullptr, (const double*)nullptr, &rz, &dum)) != NDMG_OK) return st;
+  NDMG_CK(cudaMemcpyAsync(p, z, sizeof(double) * N, cudaMemcpyDeviceToDevice, h->stream));
+  for (int it = 1; it <= maxit; ++it) {
+    op_apply<double>(h, K, p, q);
+    if ((st = dot2<double>(h, N, p, q, (const double*)nullptr, (const double*)nullptr, &pq, &dum)) != NDMG_OK) return st;
+    if (!(pq > 0.0) || !std::isfinite(pq)) return fail(h, NDMG_BREAKDOWN, "non-positive curvature p^T A p");
+    const double a = rz / pq;
+    {
+      Span sp(h, NDMG_K_BLAS, 6.0 * 8 * N);
+      launch_cg_update<double>(h->stream, sm, N, a, p, q, u, r);
+    }
+    if ((st = dot2<double>(h, N, r, r, (const double*)nullptr, (const double*)nullptr, &rr, &dum)) != NDMG_OK) return st;
+    *iters = it;
+    *relres = std::sqrt(rr) / nf;
+    if (!std::isfinite(*relres)) return fail(h, NDMG_BREAKDOWN, "non-finite residual");
+    if (*relres <= tol) return NDMG_OK;
+    if ((st = precondition(std::sqrt(rr))) != NDMG_OK) return st;
+    double rz_new, qz;
+    if ((st = dot2<double>(h, N, r, z, q, z, &rz_new, &qz)) != NDMG_OK) return st;
+    {
+      Span sp(h, NDMG_K_BLAS, 3.0 * 8 * N);
+      launch_axpby<double>(h->stream, sm, N, 1.0, z, -a * qz / rz, p);
+    }
+    rz = rz_new;
+  }
+  return fail(h, NDMG_NOT_CONVERGED, "PCG reached maxit");
 }
 
 void free_handle(ndmg_t* h) {
@@ -456,6 +523,9 @@ int ndmg_create(const ndmg_opts* o, ndmg_t** out) {
   if (o->smoother != NDMG_SMOOTHER_VERTEX) return NDMG_INVALID_ARG;
   if (o->precision < NDMG_PREC_FP64 || o->precision > NDMG_PREC_FP32) return NDMG_INVALID_ARG;
   if (edges(o->n_coarsest) > 4096) return NDMG_INVALID_ARG;   // dense coarsest inverse
+  // 32-bit edge offsets inside the tensor-core smoother: 3 n (n-1)^2 < 2^32
+  if ((o->precision == NDMG_PREC_MIXED_BF16 || o->precision == NDMG_PREC_MIXED_FP16) && o->n > 1024)
+    return NDMG_INVALID_ARG;
   int K = 0;
   for (int n = o->n; n > o->n_coarsest; n /= 2, ++K)
     if (n % 2) return NDMG_INVALID_ARG;
@@ -508,6 +578,8 @@ int ndmg_create(const ndmg_opts* o, ndmg_t** out) {
   h->status = dev_alloc<int>(4, &ae);
   if (ae == cudaSuccess) ae = cudaMallocHost((void**)&h->red_host, 8 * sizeof(double));
   if (ae == cudaSuccess) ae = cudaMemset(h->status, 0, 4 * sizeof(int));
+  if (ae == cudaSuccess) ae = prepare_stencil<double>();
+  if (ae == cudaSuccess) ae = prepare_stencil<float>();
   if (ae == cudaSuccess) ae = prepare_vertex_dense<double>();
   if (ae == cudaSuccess) ae = prepare_vertex_dense<float>();
   if (ae == cudaSuccess && mixed(h)) ae = prepare_tc_patch();
@@ -639,7 +711,22 @@ int ndmg_solve(ndmg_t* h, const double* f, double* u, double tol, int32_t maxit,
   int it = 0;
   double rr = 0.0;
   if (h->o.precision == NDMG_PREC_FP64) st = pcg64(h, f, u, tol, maxit, &it, &rr);
-  else st = solve_ir(h, f, u, tol, maxit, &it, &rr);
+  else st = pcg_mixed(h, f, u, tol, maxit, &it, &rr);
+  if (iters) *iters = it;
+  if (relres) *relres = rr;
+  return st;
+}
+
+int ndmg_solve_ir(ndmg_t* h, const double* f, double* u, double tol, double inner_tol, int32_t maxit,
+                  int32_t* iters, double* relres) {
+  if (!h) return NDMG_INVALID_ARG;
+  int st;
+  if ((st = check_ptrs(h, {f, u}))) return st;
+  if (!(tol > 0) || !(inner_tol > 0) || !(inner_tol < 1) || maxit < 0)
+    return fail(h, NDMG_INVALID_ARG, "need tol > 0, 0 < inner_tol < 1, maxit >= 0");
+  int it = 0;
+  double rr = 0.0;
+  st = solve_ir(h, f, u, tol, inner_tol, maxit, &it, &rr);
   if (iters) *iters = it;
   if (relres) *relres = rr;
   return st;

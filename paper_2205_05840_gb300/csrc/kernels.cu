@@ -144,68 +144,244 @@ __global__ void __launch_bounds__(256) k_stencil(int n, T cK, T cM, const T* __r
   }
 }
 
+// Tiled variant: one CTA owns TX x TY x TZ cells (the edges whose lowest node
+// is in the tile, all three directions).  u is staged once on the tile plus a
+// one-cell halo and g on the tile, all with asynchronous copies (zero fill
+// outside the box, which is exactly the boundary condition); the three
+// face-circulation arrays are computed once in shared memory, and every output
+// then reads 4 circulation triples (face mass along the normal) and a 3x3
+// edge-mass stencil from shared memory.
+constexpr int kTX = 32, kTY = 8, kTZ = 8;
+constexpr int kEX = kTX + 2, kEY = kTY + 2, kEZ = kTZ + 2;
+constexpr int kE3 = kEX * kEY * kEZ;
+constexpr int kT3 = kTX * kTY * kTZ;
+
+__device__ __forceinline__ int eidx(int a, int b, int c) { return (c * kEY + b) * kEX + a; }  // halo-shifted coords
+
+// asynchronous copy of one element global -> shared; zero fill when !valid
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src, bool valid, const T* any_valid) {
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+  const void* sp = valid ? (const void*)src : (const void*)any_valid;
+  if constexpr (sizeof(T) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(sp), "r"(valid ? 8u : 0u) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(sp), "r"(valid ? 4u : 0u) : "memory");
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTX * kTY) k_stencil_tiled(int n, T cK, T cM, const T* __restrict__ u,
+                                                             const T* __restrict__ g, T* __restrict__ y) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Ux = reinterpret_cast<T*>(smem_raw);
+  T* Uy = Ux + kE3;
+  T* Uz = Uy + kE3;
+  T* Cx = Uz + kE3;
+  T* Cy = Cx + kE3;
+  T* Cz = Cy + kE3;
+  T* G = Cz + kE3;  // 3 x kT3 (only when g != nullptr)
+  const int64_t N3 = (int64_t)n * (n - 1) * (n - 1);
+  const int i0 = blockIdx.x * kTX, j0 = blockIdx.y * kTY, k0 = blockIdx.z * kTZ;
+  const int tid = threadIdx.y * kTX + threadIdx.x;
+  const T* ux = u;
+  const T* uy = u + N3;
+  const T* uz = u + 2 * N3;
+  // 1. stage u on [i0-1, i0+TX] x [j0-1, j0+TY] x [k0-1, k0+TZ] and g on the tile
+  for (int q = tid; q < kE3; q += kTX * kTY) {
+    const int a = q % kEX, b = (q / kEX) % kEY, c = q / (kEX * kEY);
+    const int i = i0 + a - 1, j = j0 + b - 1, k = k0 + c - 1;
+    const bool vx = in_seg(i, n) && in_node(j, n) && in_node(k, n);
+    const bool vy = in_node(i, n) && in_seg(j, n) && in_node(k, n);
+    const bool vz = in_node(i, n) && in_node(j, n) && in_seg(k, n);
+    cp_async_elem(Ux + q, ux + (vx ? off_x(n, i, j, k) : 0), vx, u);
+    cp_async_elem(Uy + q, uy + (vy ? off_y(n, i, j, k) : 0), vy, u);
+    cp_async_elem(Uz + q, uz + (vz ? off_z(n, i, j, k) : 0), vz, u);
+  }
+  if (g) {
+    for (int q = tid; q < kT3; q += kTX * kTY) {
+      const int a = q % kTX, b = (q / kTX) % kTY, c = q / (kTX * kTY);
+      const int i = i0 + a, j = j0 + b, k = k0 + c;
+      const bool vx = in_seg(i, n) && in_node(j, n) && in_node(k, n);
+      const bool vy = in_node(i, n) && in_seg(j, n) && in_node(k, n);
+      const bool vz = in_node(i, n) && in_node(j, n) && in_seg(k, n);
+      cp_async_elem(G + q, g + (vx ? off_x(n, i, j, k) : 0), vx, g);
+      cp_async_elem(G + kT3 + q, g + N3 + (vy ? off_y(n, i, j, k) : 0), vy, g);
+      cp_async_elem(G + 2 * kT3 + q, g + 2 * N3 + (vz ? off_z(n, i, j, k) : 0), vz, g);
+    }
+  }
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+  __syncthreads();
+  // 2. face circulations wherever their four edges are staged
+  for (int q = tid; q < kE3; q += kTX * kTY) {
+    const int a = q % kEX, b = (q / kEX) % kEY, c = q / (kEX * kEY);
+    const bool ha = a + 1 < kEX, hb = b + 1 < kEY, hc = c + 1 < kEZ;
+    // cx(i,j,k) = uz(i,j+1,k) - uz(i,j,k) - uy(i,j,k+1) + uy(i,j,k)
+    Cx[q] = (hb && hc) ? Uz[eidx(a, b + 1, c)] - Uz[q] - Uy[eidx(a, b, c + 1)] + Uy[q] : T(0);
+    // cy(i,j,k) = ux(i,j,k+1) - ux(i,j,k) - uz(i+1,j,k) + uz(i,j,k)
+    Cy[q] = (ha && hc) ? Ux[eidx(a, b, c + 1)] - Ux[q] - Uz[eidx(a + 1, b, c)] + Uz[q] : T(0);
+    // cz(i,j,k) = uy(i+1,j,k) - uy(i,j,k) - ux(i,j+1,k) + ux(i,j,k)
+    Cz[q] = (ha && hb) ? Uy[eidx(a + 1, b, c)] - Uy[q] - Ux[eidx(a, b + 1, c)] + Ux[q] : T(0);
+  }
+  __syncthreads();
+  // 3. outputs: thread (tx, ty) walks its column over the tile's k range,
+  //    carrying the plane-(c-1) face-mass values and the partial mass sums
+  //    in registers from one plane to the next
+  const T w6 = T(1.0 / 6.0), w23 = T(2.0 / 3.0);
+  const int a = threadIdx.x + 1, b = threadIdx.y + 1;
+  const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
+  constexpr int P = kEX * kEY;  // plane stride
+  const int q0 = eidx(a, b, 0);
+  auto f3 = [&](T m, T c0, T p1) { return w6 * (m + p1) + w23 * c0; };
+  // face mass along x / y at column (a,b) and its neighbours, plane c
+  auto Xf = [&](int q) { return f3(Cx[q - 1], Cx[q], Cx[q + 1]); };
+  auto Yf = [&](int q) { return f3(Cy[q - kEX], Cy[q], Cy[q + kEX]); };
+  // mass rows across the edge, in the plane: x-edges vary in y, y-edges in x
+  auto rowX = [&](int q) { return f3(Ux[q - kEX], Ux[q], Ux[q + kEX]); };
+  auto rowY = [&](int q) { return f3(Uy[q - 1], Uy[q], Uy[q + 1]); };
+  // rolling state at plane c-1 / c / c+1
+  T yf_prev = Yf(q0), xf_prev = Xf(q0);                       // Yf(a,b,0), Xf(a,b,0)
+  T cz0[3] = {Cz[q0], Cz[q0 - kEX], Cz[q0 - 1]};             // Cz at (a,b), (a,b-1), (a-1,b), plane 0
+  T cz1[3] = {Cz[q0 + P], Cz[q0 + P - kEX], Cz[q0 + P - 1]};  // plane 1
+  T rx0 = rowX(q0), rx1 = rowX(q0 + P), ry0 = rowY(q0), ry1 = rowY(q0 + P);
+#pragma unroll 2
+  for (int kk = 0; kk < kTZ; ++kk) {
+    const int c = kk + 1, k = k0 + kk;
+    const int q = q0 + c * P;
+    const int t = (kk * kTY + threadIdx.y) * kTX + threadIdx.x;
+    const T cz2[3] = {Cz[q + P], Cz[q + P - kEX], Cz[q + P - 1]};
+    const T zf = f3(cz0[0], cz1[0], cz2[0]);     // Zf(a, b, c)
+    const T zf_b = f3(cz0[1], cz1[1], cz2[1]);   // Zf(a, b-1, c)
+    const T zf_a = f3(cz0[2], cz1[2], cz2[2]);   // Zf(a-1, b, c)
+    const T yf = Yf(q), xf = Xf(q);
+    const T rx2 = rowX(q + P), ry2 = rowY(q + P);
+    if (in_seg(i, n) && in_node(j, n) && in_node(k, n)) {
+      const T kv = -yf + yf_prev + zf - zf_b;
+      const T v = cK * kv + cM * f3(rx0, rx1, rx2);
+      y[off_x(n, i, j, k)] = g ? G[t] - v : v;
+    }
+    if (in_node(i, n) && in_seg(j, n) && in_node(k, n)) {
+      const T kv = -zf + zf_a + xf - xf_prev;
+      const T v = cK * kv + cM * f3(ry0, ry1, ry2);
+      y[N3 + off_y(n, i, j, k)] = g ? G[kT3 + t] - v : v;
+    }
+    if (in_node(i, n) && in_node(j, n) && in_seg(k, n)) {
+      const T kv = -xf + Xf(q - kEX) + yf - Yf(q - 1);
+      const T mz = f3(f3(Uz[q - kEX - 1], Uz[q - 1], Uz[q + kEX - 1]), f3(Uz[q - kEX], Uz[q], Uz[q + kEX]),
+                      f3(Uz[q - kEX + 1], Uz[q + 1], Uz[q + kEX + 1]));
+      const T v = cK * kv + cM * mz;
+      y[2 * N3 + off_z(n, i, j, k)] = g ? G[2 * kT3 + t] - v : v;
+    }
+    yf_prev = yf;
+    xf_prev = xf;
+#pragma unroll
+    for (int u3 = 0; u3 < 3; ++u3) {
+      cz0[u3] = cz1[u3];
+      cz1[u3] = cz2[u3];
+    }
+    rx0 = rx1; rx1 = rx2;
+    ry0 = ry1; ry1 = ry2;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Grid transfer (Sec. 3.1).  Prolongation = natural injection N_{k-1} ->
 // N_k: along a coarse edge both fine halves take its value; across it the
 // coarse hat is linear (weight 1 at the coarse node, 1/2 one fine node away).
 // Restriction is the transpose.
 // ---------------------------------------------------------------------------
+// One thread per lattice point (i, j, k) of the output mesh handles the x-,
+// y- and z-edge that start there (when they are interior); blocks of 32 x 8
+// threads run along i, the grid's z index is k.
 template <typename T>
 __global__ void __launch_bounds__(256) k_restrict(int nf, const T* __restrict__ rf, T* __restrict__ gc) {
   const int nc = nf / 2;
+  const int I = blockIdx.x * 32 + threadIdx.x, J = blockIdx.y * 8 + threadIdx.y, K = blockIdx.z;
+  if (I >= nc || J >= nc) return;
   const int64_t N3c = (int64_t)nc * (nc - 1) * (nc - 1);
   const int64_t N3f = (int64_t)nf * (nf - 1) * (nf - 1);
   const T w[3] = {T(0.5), T(1), T(0.5)};
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < 3 * N3c;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int d = (int)(e / N3c);
-    int I, J, K;
-    decode(d, nc, e - d * N3c, I, J, K);
-    const T* r = rf + d * N3f;
+  // coarse x-edge (I, J, K): fine x-edges 2I+a, 2J+b, 2K+c with weight w_b w_c
+  if (in_node(J, nc) && in_node(K, nc)) {
+    T s = T(0);
+#pragma unroll
+    for (int c = -1; c <= 1; ++c)
+#pragma unroll
+      for (int b = -1; b <= 1; ++b)
+#pragma unroll
+        for (int a = 0; a < 2; ++a) s += w[b + 1] * w[c + 1] * __ldg(rf + off_x(nf, 2 * I + a, 2 * J + b, 2 * K + c));
+    gc[off_x(nc, I, J, K)] = s;
+  }
+  if (in_node(I, nc) && in_node(K, nc)) {
+    T s = T(0);
+#pragma unroll
+    for (int c = -1; c <= 1; ++c)
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = -1; b <= 1; ++b)
+          s += w[b + 1] * w[c + 1] * __ldg(rf + N3f + off_y(nf, 2 * I + b, 2 * J + a, 2 * K + c));
+    gc[N3c + off_y(nc, I, J, K)] = s;
+  }
+  if (in_node(I, nc) && in_node(J, nc)) {
     T s = T(0);
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
-      for (int b = -1; b <= 1; ++b)
+      for (int c = -1; c <= 1; ++c)
 #pragma unroll
-        for (int c = -1; c <= 1; ++c) {
-          const T wt = w[b + 1] * w[c + 1];
-          if (d == 0) s += wt * __ldg(r + off_x(nf, 2 * I + a, 2 * J + b, 2 * K + c));
-          else if (d == 1) s += wt * __ldg(r + off_y(nf, 2 * I + c, 2 * J + a, 2 * K + b));
-          else s += wt * __ldg(r + off_z(nf, 2 * I + b, 2 * J + c, 2 * K + a));
-        }
-    gc[e] = s;
+        for (int b = -1; b <= 1; ++b)
+          s += w[b + 1] * w[c + 1] * __ldg(rf + 2 * N3f + off_z(nf, 2 * I + b, 2 * J + c, 2 * K + a));
+    gc[2 * N3c + off_z(nc, I, J, K)] = s;
   }
+}
+
+// weights of the coarse hat across an edge: fine node p -> coarse nodes
+// p/2 (weight 1) if p is even, (p-1)/2 and (p+1)/2 (weight 1/2) if odd
+template <typename T>
+__device__ __forceinline__ int hat(int p, int (&C)[2], T (&w)[2]) {
+  C[0] = p >> 1;
+  C[1] = (p >> 1) + 1;
+  if (p & 1) {
+    w[0] = w[1] = T(0.5);
+    return 2;
+  }
+  w[0] = T(1);
+  return 1;
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_prolong_add(int nf, const T* __restrict__ zc, T* __restrict__ zf) {
   const int nc = nf / 2;
+  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+  if (i >= nf || j >= nf) return;
   const int64_t N3c = (int64_t)nc * (nc - 1) * (nc - 1);
   const int64_t N3f = (int64_t)nf * (nf - 1) * (nf - 1);
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < 3 * N3f;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int d = (int)(e / N3f);
-    int p[3];
-    decode(d, nf, e - d * N3f, p[0], p[1], p[2]);
-    const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
-    int c[3];
-    c[d] = p[d] >> 1;
-    // transverse coarse nodes and weights
-    int na = (p[t1] & 1) ? 2 : 1, nb = (p[t2] & 1) ? 2 : 1;
-    int A[2] = {p[t1] >> 1, (p[t1] >> 1) + 1}, B[2] = {p[t2] >> 1, (p[t2] >> 1) + 1};
-    const T wa = (na == 2) ? T(0.5) : T(1), wb = (nb == 2) ? T(0.5) : T(1);
-    const T* z = zc + d * N3c;
+  int A[2], B[2];
+  T wa[2], wb[2];
+  if (in_node(j, nf) && in_node(k, nf)) {  // x-edge: injection along x, hats in y and z
+    const int na = hat(j, A, wa), nb = hat(k, B, wb);
     T s = T(0);
     for (int a = 0; a < na; ++a)
-      for (int b = 0; b < nb; ++b) {
-        c[t1] = A[a];
-        c[t2] = B[b];
-        if (!in_node(c[t1], nc) || !in_node(c[t2], nc)) continue;
-        int64_t o = d == 0 ? off_x(nc, c[0], c[1], c[2]) : d == 1 ? off_y(nc, c[0], c[1], c[2]) : off_z(nc, c[0], c[1], c[2]);
-        s += wa * wb * __ldg(z + o);
-      }
-    zf[e] += s;
+      for (int b = 0; b < nb; ++b)
+        if (in_node(A[a], nc) && in_node(B[b], nc)) s += wa[a] * wb[b] * __ldg(zc + off_x(nc, i >> 1, A[a], B[b]));
+    zf[off_x(nf, i, j, k)] += s;
+  }
+  if (in_node(i, nf) && in_node(k, nf)) {
+    const int na = hat(i, A, wa), nb = hat(k, B, wb);
+    T s = T(0);
+    for (int a = 0; a < na; ++a)
+      for (int b = 0; b < nb; ++b)
+        if (in_node(A[a], nc) && in_node(B[b], nc)) s += wa[a] * wb[b] * __ldg(zc + N3c + off_y(nc, A[a], j >> 1, B[b]));
+    zf[N3f + off_y(nf, i, j, k)] += s;
+  }
+  if (in_node(i, nf) && in_node(j, nf)) {
+    const int na = hat(i, A, wa), nb = hat(j, B, wb);
+    T s = T(0);
+    for (int a = 0; a < na; ++a)
+      for (int b = 0; b < nb; ++b)
+        if (in_node(A[a], nc) && in_node(B[b], nc))
+          s += wa[a] * wb[b] * __ldg(zc + 2 * N3c + off_z(nc, A[a], B[b], k >> 1));
+    zf[2 * N3f + off_z(nf, i, j, k)] += s;
   }
 }
 
@@ -405,6 +581,12 @@ __global__ void __launch_bounds__(256) k_to_f32(int64_t N, double s, const doubl
     dst[e] = (float)(s * src[e]);
 }
 
+// dst (double) = s * src (float)
+__global__ void __launch_bounds__(256) k_from_f32(int64_t N, double s, const float* __restrict__ src, double* __restrict__ dst) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = s * (double)src[e];
+}
+
 // dst (double) += s * src (float)
 __global__ void __launch_bounds__(256) k_add_f32(int64_t N, double s, const float* __restrict__ src, double* __restrict__ dst) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x)
@@ -423,24 +605,40 @@ static inline int grid_for(int64_t work, int sm_count, int per_sm = 8) {
 }
 
 template <typename T>
+size_t stencil_smem() { return sizeof(T) * (6 * kE3 + 3 * kT3); }
+
+template <typename T>
+cudaError_t prepare_stencil() {
+  return cudaFuncSetAttribute(k_stencil_tiled<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stencil_smem<T>());
+}
+
+template <typename T>
 void launch_stencil(cudaStream_t s, int sm, int n, double cK, double cM, const T* u, const T* g, T* y) {
+  const int64_t N = 3LL * n * (n - 1) * (n - 1);
+  if (N == 0) return;
+  (void)sm;
+  dim3 grid((n + kTX - 1) / kTX, (n + kTY - 1) / kTY, (n + kTZ - 1) / kTZ);
+  k_stencil_tiled<T><<<grid, dim3(kTX, kTY), stencil_smem<T>(), s>>>(n, (T)cK, (T)cM, u, g, y);
+}
+
+// reference-style variant kept for the tests: one thread per edge, loads through L1
+template <typename T>
+void launch_stencil_simple(cudaStream_t s, int sm, int n, double cK, double cM, const T* u, const T* g, T* y) {
   const int64_t N = 3LL * n * (n - 1) * (n - 1);
   if (N == 0) return;
   k_stencil<T><<<grid_for(N, sm, 16), 256, 0, s>>>(n, (T)cK, (T)cM, u, g, y);
 }
 
 template <typename T>
-void launch_restrict(cudaStream_t s, int sm, int nf, const T* rf, T* gc) {
+void launch_restrict(cudaStream_t s, int, int nf, const T* rf, T* gc) {
   const int nc = nf / 2;
-  const int64_t N = 3LL * nc * (nc - 1) * (nc - 1);
-  if (N == 0) return;
-  k_restrict<T><<<grid_for(N, sm, 16), 256, 0, s>>>(nf, rf, gc);
+  if (nc < 2) return;
+  k_restrict<T><<<dim3((nc + 31) / 32, (nc + 7) / 8, nc), dim3(32, 8), 0, s>>>(nf, rf, gc);
 }
 
 template <typename T>
-void launch_prolong_add(cudaStream_t s, int sm, int nf, const T* zc, T* zf) {
-  const int64_t N = 3LL * nf * (nf - 1) * (nf - 1);
-  k_prolong_add<T><<<grid_for(N, sm, 16), 256, 0, s>>>(nf, zc, zf);
+void launch_prolong_add(cudaStream_t s, int, int nf, const T* zc, T* zf) {
+  k_prolong_add<T><<<dim3((nf + 31) / 32, (nf + 7) / 8, nf), dim3(32, 8), 0, s>>>(nf, zc, zf);
 }
 
 template <typename T>
@@ -504,12 +702,17 @@ void launch_cg_update(cudaStream_t s, int sm, int64_t N, double a, const T* p, c
 void launch_to_f32(cudaStream_t s, int sm, int64_t N, double sc, const double* src, float* dst) {
   k_to_f32<<<grid_for(N, sm, 8), 256, 0, s>>>(N, sc, src, dst);
 }
+void launch_from_f32(cudaStream_t s, int sm, int64_t N, double sc, const float* src, double* dst) {
+  k_from_f32<<<grid_for(N, sm, 8), 256, 0, s>>>(N, sc, src, dst);
+}
 void launch_add_f32(cudaStream_t s, int sm, int64_t N, double sc, const float* src, double* dst) {
   k_add_f32<<<grid_for(N, sm, 8), 256, 0, s>>>(N, sc, src, dst);
 }
 
 #define NDMG_INST(T)                                                                                   \
   template void launch_stencil<T>(cudaStream_t, int, int, double, double, const T*, const T*, T*);    \
+  template void launch_stencil_simple<T>(cudaStream_t, int, int, double, double, const T*, const T*, T*); \
+  template cudaError_t prepare_stencil<T>();                                                          \
   template void launch_restrict<T>(cudaStream_t, int, int, const T*, T*);                             \
   template void launch_prolong_add<T>(cudaStream_t, int, int, const T*, T*);                          \
   template void launch_bubble<T>(cudaStream_t, int, int, const T*, double, const T*, T*);             \

@@ -8,6 +8,10 @@ namespace ndmg {
 template <typename T>
 void launch_stencil(cudaStream_t s, int sm, int n, double cK, double cM, const T* u, const T* g, T* y);
 template <typename T>
+void launch_stencil_simple(cudaStream_t s, int sm, int n, double cK, double cM, const T* u, const T* g, T* y);
+template <typename T>
+cudaError_t prepare_stencil();
+template <typename T>
 void launch_restrict(cudaStream_t s, int sm, int nf, const T* rf, T* gc);
 template <typename T>
 void launch_prolong_add(cudaStream_t s, int sm, int nf, const T* zc, T* zf);
@@ -29,5 +33,6 @@ template <typename T>
 void launch_cg_update(cudaStream_t s, int sm, int64_t N, double a, const T* p, const T* q, T* u, T* r);
 void launch_to_f32(cudaStream_t s, int sm, int64_t N, double sc, const double* src, float* dst);
 void launch_add_f32(cudaStream_t s, int sm, int64_t N, double sc, const float* src, double* dst);
+void launch_from_f32(cudaStream_t s, int sm, int64_t N, double sc, const float* src, double* dst);
 
 }  // namespace ndmg

@@ -1,27 +1,29 @@
-// Vertex-patch term of the smoother, eq. (Preconditioner P), on the 5th-gen
-// tensor cores (tcgen05, sm_103a):
+// Smoother correction of eq. (Preconditioner P) on the 5th-gen tensor cores
+// (tcgen05, sm_103a), one kernel for both additive parts:
 //
-//     z += eta * sum_V J_V A_V^{-1} J_V^t r,   J_V A_V^{-1} J_V^t = W W^t,
+//     z += eta * ( sum_T J_T A_T^{-1} J_T^t r  +  sum_V J_V A_V^{-1} J_V^t r ),
 //
-// with W the 108x60 Gram factor of the vertex-space operator (the same matrix
-// for every patch: constant alpha on a uniform grid).  One CTA owns a brick of
-// 8x8x8 fine cells (4x4x4 coarse elements) and computes every patch that
-// touches its edges: the (4+1)^3 = 125 patches around the brick's coarse
-// vertices, one 128-row MMA tile.  Per CTA:
-//   1. stage r on the 12x12x12-cell region the patches cover (FP32, smem);
-//   2. gather the 125 patch vectors into A1 (128 x 112, bf16/fp16, K-major);
-//   3. D1 = A1 W           (tcgen05.mma M=128 N=64  K=112, FP32 in TMEM);
-//   4. A2 = lowp(D1)       (tcgen05.ld -> registers -> smem);
-//   5. D2 = A2 W^t         (tcgen05.mma M=128 N=112 K=64, FP32 in TMEM);
-//   6. add each patch's 108 outputs that land on owned edges into an smem
+// with J_V A_V^{-1} J_V^t = W W^t, W the 108x60 Gram factor of the vertex
+// space operator (identical for every patch: constant alpha, uniform grid).
+// One CTA owns a brick of 8x8x8 fine cells (4x4x4 coarse elements) and
+// computes every patch that touches the brick's edges: the (4+1)^3 = 125
+// patches around its coarse vertices, one 128-row MMA tile.  Per CTA:
+//   1. stage r on the 12x12x12-cell region the patches cover (cp.async with
+//      zero fill outside the box: that is the boundary condition);
+//   2. interior-space solves of the brick's 64 coarse elements (6x6, FP32);
+//   3. gather the 125 patch vectors into A (128 x 112, bf16/fp16, K-major);
+//   4. D = A W             (tcgen05.mma M=128 N=64  K=112, FP32 in TMEM);
+//   5. A' = lowp(D)        (tcgen05.ld -> registers -> smem, over A);
+//   6. D' = A' W^t         (tcgen05.mma M=128 N=112 K=64, FP32 in TMEM, over D);
+//   7. add each patch's outputs that land on owned edges into an smem
 //      accumulator (shared atomics: up to 8 patches share an edge);
-//   7. z[owned] += scale * acc.
-// Every edge is written by exactly one CTA, so no global atomics are needed.
-// Neighbouring CTAs recompute the patches on their common boundary.
+//   8. z[owned] += eta * acc.
+// Every edge is written by exactly one CTA, so no global atomics are needed;
+// neighbouring CTAs recompute the patches on their common boundary.
 //
-// Operand layout (SWIZZLE_NONE, K-major canonical layout): 8x16-byte "core
-// matrices" (8 rows x 8 elements) stored contiguously; core matrix (g, c) of
-// an R x K operand (g = row / 8, c = k / 8) sits at byte (g * K/8 + c) * 128.
+// Operand layout (SWIZZLE_NONE, K-major canonical layout): 8-row x 16-byte
+// "core matrices" stored contiguously; core matrix (g, c) of an R x K
+// operand (g = row / 8, c = k / 8) sits at byte (g * K/8 + c) * 128.
 // Descriptor: leading byte offset (next core matrix along K) = 128, stride
 // byte offset (next 8-row group) = K/8 * 128.
 #include <cmath>
@@ -34,31 +36,35 @@ namespace {
 
 constexpr int kB = 4;                      // coarse vertices per brick side
 constexpr int kM = 128;                    // MMA rows (125 patches + 3 empty)
-constexpr int kK1 = 112, kN1 = 64;         // A1: 128 x 112, W: 112 x 64
-constexpr int kK2 = 64, kN2 = 112;         // A2: 128 x 64,  W^t: 64 x 112
+constexpr int kK1 = 112, kN1 = 64;         // A: 128 x 112, W: 112 x 64
+constexpr int kK2 = 64, kN2 = 112;         // A': 128 x 64, W^t: 64 x 112
 constexpr int kRE = 2 * kB + 4;            // region: 12 cells per side
 constexpr int kRN = kRE - 1;               // 11 interior node lines
 constexpr int kRegion = kRE * kRN * kRN;   // staged edges per direction
 constexpr int kOwn = 2 * kB;               // owned cells per side
 constexpr int kOwn3 = kOwn * kOwn * kOwn;  // owned edges per direction
-constexpr int kThreads = 128;
-constexpr uint32_t kTmemCols = 256;        // D1: cols [0,64), D2: cols [64,176)
+constexpr int kThreads = 256;
+constexpr uint32_t kTmemCols = 128;        // D: cols [0,64), then D': cols [0,112)
 
-constexpr int OFF_A1 = 0;
-constexpr int OFF_B1 = OFF_A1 + kM * kK1 * 2;   // B1 and B2 contiguous: one copy of both images
+// shared memory: A' aliases A (A is dead once the first MMA completed); the
+// accumulator aliases the staged region (dead once A and the interior-space
+// solves are done)
+constexpr int OFF_A = 0;
+constexpr int OFF_B1 = OFF_A + kM * kK1 * 2;      // W images, contiguous
 constexpr int OFF_B2 = OFF_B1 + kN1 * kK1 * 2;
-constexpr int OFF_A2 = OFF_B2 + kN2 * kK2 * 2;
-constexpr int OFF_R = OFF_A2 + kM * kK2 * 2;
-constexpr int OFF_ACC = OFF_R + 3 * kRegion * 4;
-constexpr int OFF_BAR = OFF_ACC + 3 * kOwn3 * 4;
+constexpr int OFF_R = OFF_B2 + kN2 * kK2 * 2;
+constexpr int OFF_ACC = OFF_R;
+constexpr int OFF_BUB = OFF_R + 3 * kRegion * 4;  // 64 elements x 6 interior-space results
+constexpr int OFF_BAR = OFF_BUB + 64 * 6 * 4;
 constexpr int OFF_TM = OFF_BAR + 16;
 constexpr int OFF_RED = OFF_TM + 16;
-constexpr int kSmem = OFF_RED + 16;
+constexpr int kSmem = OFF_RED + 32;
 static_assert(OFF_BAR % 8 == 0, "mbarrier alignment");
-static_assert(kSmem <= 110 * 1024, "two CTAs per SM");
+static_assert(3 * kOwn3 * 4 <= 3 * kRegion * 4, "accumulator fits in the staged region");
+static_assert(3 * (kSmem + 1024) <= 228 * 1024, "three CTAs per SM (228 KB, 1 KB reserved per CTA)");
 
 constexpr int kImgBytes = (kN1 * kK1 + kN2 * kK2) * 2;  // both W images
-static_assert(OFF_B2 - OFF_B1 == kN1 * kK1 * 2 && OFF_A2 - OFF_B1 == kImgBytes, "W images are copied as one block");
+static_assert(OFF_B2 - OFF_B1 == kN1 * kK1 * 2 && OFF_R - OFF_B1 == kImgBytes, "W images are one block");
 constexpr int kTimeout = 1;                              // status code
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -122,6 +128,11 @@ __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::be
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// 4-byte asynchronous copy global -> shared; src_bytes = 0 writes a zero
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+
 // 16 consecutive FP32 columns of this warp's 32 TMEM lanes (one row per thread)
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   uint32_t r[16];
@@ -147,9 +158,17 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {
   }
 }
 
-// patch-local edge l in [0,108) -> (direction, region coordinates) for the
-// patch at brick-relative vertex (a,b,c); the 4x4x4 box numbering of the
-// library (x: 4 segments x 3 x 3 nodes, then y, then z)
+// staged-region index of edge (d; i, j, k) given in region coordinates
+// (x: 12 segments x 11 x 11 node lines; y: 11 x 12 x 11; z: 11 x 11 x 12)
+__device__ __forceinline__ int region_at(int d, int i, int j, int k) {
+  if (d == 0) return (k * kRN + j) * kRE + i;
+  if (d == 1) return kRegion + (k * kRE + j) * kRN + i;
+  return 2 * kRegion + (k * kRN + j) * kRN + i;
+}
+
+// patch-local edge l in [0,108) of the patch at brick-relative vertex (a,b,c):
+// the 4x4x4 box numbering of the library (x: 4 segments x 3 x 3 nodes, then
+// y, then z), as a staged-region index
 __device__ __forceinline__ int region_index(int l, int a, int b, int c) {
   int d, i, j, k;
   if (l < 36) {
@@ -159,11 +178,7 @@ __device__ __forceinline__ int region_index(int l, int a, int b, int c) {
   } else {
     l -= 72; d = 2; i = l % 3; j = (l / 3) % 3; k = l / 9;
   }
-  i += 2 * a; j += 2 * b; k += 2 * c;
-  // region extents per direction: along-axis 12 segments, 11 node lines
-  if (d == 0) return (k * kRN + j) * kRE + i;
-  if (d == 1) return kRegion + (k * kRE + j) * kRN + i;
-  return 2 * kRegion + (k * kRN + j) * kRN + i;
+  return region_at(d, i + 2 * a, j + 2 * b, k + 2 * c);
 }
 
 // patch-local edge -> owned-accumulator slot (or -1 if not owned by the brick)
@@ -203,28 +218,98 @@ __device__ __forceinline__ bool interior(int n, int d, int i, int j, int k) {
   return true;
 }
 
+// the 6 interior-space edges of brick-relative coarse element (a,b,c), in
+// the 2x2x2 box order (x segment 0/1, then y, then z), as offsets from the
+// brick origin 2*(I0,J0,K0)
+__device__ __forceinline__ void bubble_edge(int t, int a, int b, int c, int& d, int (&p)[3]) {
+  d = t >> 1;
+  const int s = t & 1;
+  p[0] = 2 * a + 1;
+  p[1] = 2 * b + 1;
+  p[2] = 2 * c + 1;
+  p[d] = 2 * (d == 0 ? a : d == 1 ? b : c) + s;
+}
+
+// direction of patch-local edge l and its region offset for the patch at
+// brick-relative vertex (0,0,0); both constant-fold when l is a literal
+__device__ __forceinline__ int local_dir(int l) { return l < 36 ? 0 : (l < 72 ? 1 : 2); }
+__device__ __forceinline__ int local_off(int l) { return region_index(l, 0, 0, 0) - region_at(local_dir(l), 0, 0, 0); }
+
+// 7 chunks of 8 patch-local edges from chunk CH0 on, rounded to bf16/fp16 and
+// stored as 16-byte rows of the K-major operand A
+template <int CH0, bool FP16>
+__device__ __forceinline__ void gather_chunks(const float* R, uint8_t* A, int p, const int (&base)[3], bool live,
+                                              float rscale) {
+#pragma unroll
+  for (int ch = CH0; ch < CH0 + 7; ++ch) {
+    float v[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int l = ch * 8 + t;
+      v[t] = (live && l < 108) ? R[base[local_dir(l)] + local_off(l)] * rscale : 0.f;
+    }
+    uint4 w;
+    w.x = pack2<FP16>(v[0], v[1]);
+    w.y = pack2<FP16>(v[2], v[3]);
+    w.z = pack2<FP16>(v[4], v[5]);
+    w.w = pack2<FP16>(v[6], v[7]);
+    *reinterpret_cast<uint4*>(A + core_off(p, ch * 8, kK1)) = w;
+  }
+}
+
+// box coordinates (direction, i, j, k) of patch-local edge l in the 4x4x4
+// numbering; constant-folds for a literal l
+__device__ __forceinline__ void local_box(int l, int& d, int& i, int& j, int& k) {
+  if (l < 36) {
+    d = 0; i = l % 4; j = (l / 4) % 3 + 1; k = l / 12 + 1;
+  } else if (l < 72) {
+    l -= 36; d = 1; i = l % 3 + 1; j = (l / 3) % 4; k = l / 12 + 1;
+  } else {
+    l -= 72; d = 2; i = l % 3 + 1; j = (l / 3) % 3 + 1; k = l / 9;
+  }
+}
+
+// add the 16 outputs l = CB..CB+15 of patch (a,b,c) that land on edges owned
+// by the brick into the accumulator; owned coordinates are box + 2(a,b,c) - 2
+template <int CB>
+__device__ __forceinline__ void scatter16(float* ACC, const float (&v)[16], int a, int b, int c) {
+  const int pbase = 2 * a + 16 * b + 128 * c - (2 + 16 + 128);
+#pragma unroll
+  for (int t = 0; t < 16; ++t) {
+    const int l = CB + t;
+    if (l < 108) {
+      int d, i, j, k;
+      local_box(l, d, i, j, k);
+      const int oi = i + 2 * a - 2, oj = j + 2 * b - 2, ok = k + 2 * c - 2;
+      if ((unsigned)oi < (unsigned)kOwn && (unsigned)oj < (unsigned)kOwn && (unsigned)ok < (unsigned)kOwn)
+        atomicAdd(ACC + d * kOwn3 + (k * kOwn + j) * kOwn + i + pbase, v[t]);
+    }
+  }
+}
+
 template <bool FP16>
-__global__ void __launch_bounds__(kThreads, 2)
-    k_tc_patch(int n, const uint8_t* __restrict__ img, float eta, const float* __restrict__ r, float* __restrict__ z,
-               int* __restrict__ status) {
+__global__ void __launch_bounds__(kThreads, 3)
+    k_tc_smoother(int n, const uint8_t* __restrict__ img, const float* __restrict__ AinvT, float eta,
+                  const float* __restrict__ r, float* __restrict__ z, int* __restrict__ status) {
   extern __shared__ __align__(128) uint8_t smem[];
+  // a CTA of an earlier launch gave up on a wait: do nothing until the host
+  // has read and cleared the status word
+  if (*reinterpret_cast<volatile int*>(status) != 0) return;
+
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nc = n / 2;
   const int nbr = (nc + kB - 1) / kB;
   const int bx = blockIdx.x % nbr, by = (blockIdx.x / nbr) % nbr, bz = blockIdx.x / (nbr * nbr);
   const int I0 = bx * kB, J0 = by * kB, K0 = bz * kB;
 
-  // a CTA of an earlier launch gave up on a wait: do nothing until the host
-  // has read and cleared the status word
-  if (*reinterpret_cast<volatile int*>(status) != 0) return;
-
   float* R = reinterpret_cast<float*>(smem + OFF_R);
   float* ACC = reinterpret_cast<float*>(smem + OFF_ACC);
+  float* BUB = reinterpret_cast<float*>(smem + OFF_BUB);
   const uint32_t bar0 = smem_u32(smem + OFF_BAR), bar1 = bar0 + 8;
   uint32_t* tm_slot = reinterpret_cast<uint32_t*>(smem + OFF_TM);
   float* red = reinterpret_cast<float*>(smem + OFF_RED);
 
-  // ---- set-up: TMEM, barriers, both W images ---------------------------------
+  // ---- set-up: TMEM, barriers; copies of r and of both W images --------------
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tm_slot)),
                  "r"(kTmemCols)
@@ -236,79 +321,102 @@ __global__ void __launch_bounds__(kThreads, 2)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar1), "r"(1) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  // 1. r on the region: x-edges from (2I0-2, 2J0-1, 2K0-1), y-edges from
+  //    (2I0-1, 2J0-2, 2K0-1), z-edges from (2I0-1, 2J0-1, 2K0-2)
   {
+    const uint32_t rbase = smem_u32(R);
+    const int n1 = n - 1;
+    const uint32_t N3 = (uint32_t)n * n1 * n1;   // < 2^31 for the supported n (checked on the host)
+    for (int q = tid; q < 3 * kRegion; q += kThreads) {
+      const int d = q >= 2 * kRegion ? 2 : (q >= kRegion ? 1 : 0);
+      const int e = q - d * kRegion;
+      // region extents: along-axis 12 segments, 11 node lines across
+      const int Li = d == 0 ? kRE : kRN, Lj = d == 1 ? kRE : kRN;
+      const int i = e % Li, jk = e / Li, j = jk % Lj, k = jk / Lj;
+      const int gi = 2 * I0 + i - (d == 0 ? 2 : 1);
+      const int gj = 2 * J0 + j - (d == 1 ? 2 : 1);
+      const int gk = 2 * K0 + k - (d == 2 ? 2 : 1);
+      const bool in = interior(n, d, gi, gj, gk);
+      uint32_t off = 0;
+      if (in) {
+        if (d == 0) off = ((uint32_t)(gk - 1) * n1 + (gj - 1)) * n + gi;
+        else if (d == 1) off = N3 + ((uint32_t)(gk - 1) * n + gj) * n1 + (gi - 1);
+        else off = 2 * N3 + ((uint32_t)gk * n1 + (gj - 1)) * n1 + (gi - 1);
+      }
+      cp_async4(rbase + 4u * q, r + off, in ? 4u : 0u);
+    }
     const uint4* src = reinterpret_cast<const uint4*>(img);
-    uint4* dst = reinterpret_cast<uint4*>(smem + OFF_B1);   // B1 and B2 are contiguous
-    for (int q = tid; q < kImgBytes / 16; q += kThreads) dst[q] = __ldg(src + q);
+    const uint32_t wbase = smem_u32(smem + OFF_B1);
+    for (int q = tid; q < kImgBytes / 16; q += kThreads)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(wbase + 16u * q), "l"(src + q) : "memory");
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
   }
   const float wscale = __ldg(reinterpret_cast<const float*>(img + kImgBytes));  // 1 / s_w^2
-
-  // ---- 1. stage r on the region, zero the accumulator -------------------------
-  // region origins (global): x-edges (2I0-2, 2J0-1, 2K0-1), y-edges (2I0-1,
-  // 2J0-2, 2K0-1), z-edges (2I0-1, 2J0-1, 2K0-2)
-  float amax = 0.f;
-  for (int q = tid; q < 3 * kRegion; q += kThreads) {
-    const int d = q / kRegion, e = q - d * kRegion;
-    int i, j, k;
-    if (d == 0) { i = e % kRE; j = (e / kRE) % kRN; k = e / (kRE * kRN); }
-    else if (d == 1) { i = e % kRN; j = (e / kRN) % kRE; k = e / (kRN * kRE); }
-    else { i = e % kRN; j = (e / kRN) % kRN; k = e / (kRN * kRN); }
-    const int gi = 2 * I0 + i - (d == 0 ? 2 : 1);
-    const int gj = 2 * J0 + j - (d == 1 ? 2 : 1);
-    const int gk = 2 * K0 + k - (d == 2 ? 2 : 1);
-    float v = 0.f;
-    if (interior(n, d, gi, gj, gk)) v = __ldg(r + gidx(n, d, gi, gj, gk));
-    R[q] = v;
-    amax = fmaxf(amax, fabsf(v));
-  }
-  for (int q = tid; q < 3 * kOwn3; q += kThreads) ACC[q] = 0.f;
-  // fp16 operands: scale r by a power of two so that max |r| <= 1 on the region
-  float rscale = 1.f;
-  if constexpr (FP16) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-    if (lane == 0) red[warp] = amax;
-  }
   fence_before();
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tm_slot;
+
+  // fp16 operands: scale r by a power of two so that max |r| <= 1 on the region
+  float rscale = 1.f;
   if constexpr (FP16) {
-    const float m = fmaxf(fmaxf(red[0], red[1]), fmaxf(red[2], red[3]));
+    float amax = 0.f;
+    for (int q = tid; q < 3 * kRegion; q += kThreads) amax = fmaxf(amax, fabsf(R[q]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if (lane == 0) red[warp] = amax;
+    __syncthreads();
+    float m = 0.f;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) m = fmaxf(m, red[w]);
     if (m > 0.f) rscale = exp2f(-ceilf(log2f(m)));
   }
 
-  // ---- 2. gather the patch vectors into A1 ------------------------------------
+  // ---- 2. interior spaces of the brick's 64 coarse elements (FP32) ----------
+  if (tid < kB * kB * kB) {
+    const int a = tid % kB, b = (tid / kB) % kB, c = tid / (kB * kB);
+    float rv[6];
+#pragma unroll
+    for (int t = 0; t < 6; ++t) {
+      int d, p[3];
+      bubble_edge(t, a, b, c, d, p);
+      // brick-relative -> region coordinates: region origin sits 2 (along the
+      // edge) or 1 (across it) cells below the brick origin
+      rv[t] = R[region_at(d, p[0] + (d == 0 ? 2 : 1), p[1] + (d == 1 ? 2 : 1), p[2] + (d == 2 ? 2 : 1))];
+    }
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      float acc = 0.f;
+#pragma unroll
+      for (int w = 0; w < 6; ++w) acc += __ldg(AinvT + q * 6 + w) * rv[w];
+      BUB[tid * 6 + q] = acc;
+    }
+  }
+
+  // ---- 3. gather the patch vectors into A (two threads per row; the loops
+  //         are unrolled so every patch-local offset is a compile-time constant)
   {
-    const int p = tid;  // one patch row per thread
+    const int p = tid & (kM - 1), half = tid >> 7;
     const int a = p % 5, b = (p / 5) % 5, c = p / 25;
     const bool live = p < 125 && (I0 + a) >= 1 && (I0 + a) <= nc - 1 && (J0 + b) >= 1 && (J0 + b) <= nc - 1 &&
                       (K0 + c) >= 1 && (K0 + c) <= nc - 1;
-    uint8_t* A1 = smem + OFF_A1;
-#pragma unroll 1
-    for (int ch = 0; ch < kK1 / 8; ++ch) {
-      float v[8];
-#pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        const int l = ch * 8 + t;
-        v[t] = (live && l < 108) ? R[region_index(l, a, b, c)] * rscale : 0.f;
-      }
-      uint4 w;
-      w.x = pack2<FP16>(v[0], v[1]);
-      w.y = pack2<FP16>(v[2], v[3]);
-      w.z = pack2<FP16>(v[4], v[5]);
-      w.w = pack2<FP16>(v[6], v[7]);
-      *reinterpret_cast<uint4*>(A1 + core_off(p, ch * 8, kK1)) = w;
-    }
+    const int base[3] = {region_at(0, 2 * a, 2 * b, 2 * c), region_at(1, 2 * a, 2 * b, 2 * c),
+                         region_at(2, 2 * a, 2 * b, 2 * c)};
+    uint8_t* A = smem + OFF_A;
+    if (half == 0)
+      gather_chunks<0, FP16>(R, A, p, base, live, rscale);
+    else
+      gather_chunks<7, FP16>(R, A, p, base, live, rscale);
   }
   fence_async_smem();
   __syncthreads();
 
-  // ---- 3. D1 = A1 W ---------------------------------------------------------
-  bool ok = true;
+  // ---- 4. D = A W (one thread issues); meanwhile the others clear the
+  //         accumulator (the staged region is dead now) and seed it with the
+  //         interior-space results, pre-divided by the final output scale -----
   if (tid == 0) {
     fence_after();
-    const uint32_t a0 = smem_u32(smem + OFF_A1), b0 = smem_u32(smem + OFF_B1);
+    const uint32_t a0 = smem_u32(smem + OFF_A), b0 = smem_u32(smem + OFF_B1);
     const uint32_t idesc = instr_desc(kM, kN1, FP16);
 #pragma unroll
     for (int kk = 0; kk < kK1 / 16; ++kk)
@@ -316,17 +424,30 @@ __global__ void __launch_bounds__(kThreads, 2)
               idesc, kk > 0);
     mma_commit(bar0);
   }
-  ok = mbar_wait(bar0, 0);
+  for (int q = tid; q < 3 * kOwn3; q += kThreads) ACC[q] = 0.f;
+  __syncthreads();
+  if (tid < kB * kB * kB) {
+    const int a = tid % kB, b = (tid / kB) % kB, c = tid / (kB * kB);
+    const float pre = rscale / wscale;   // undone by eta * wscale / rscale at the end
+#pragma unroll
+    for (int t = 0; t < 6; ++t) {
+      int d, p[3];
+      bubble_edge(t, a, b, c, d, p);
+      ACC[d * kOwn3 + (p[2] * kOwn + p[1]) * kOwn + p[0]] += BUB[tid * 6 + t] * pre;
+    }
+  }
+  bool ok = mbar_wait(bar0, 0);
   fence_after();
 
-  // ---- 4. A2 = low-precision copy of D1 ----------------------------------------
+  // ---- 5. A' = low-precision copy of D (8 warps: lane quadrant x column half)
   if (ok) {
-    const int p = warp * 32 + lane;
-    uint8_t* A2 = smem + OFF_A2;
+    const int p = (warp & 3) * 32 + lane;
+    const int cb0 = (warp >> 2) * 32;
+    uint8_t* A2 = smem + OFF_A;
 #pragma unroll 1
-    for (int cb = 0; cb < kN1; cb += 16) {
+    for (int cb = cb0; cb < cb0 + 32; cb += 16) {
       float v[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + cb, v);
+      tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + cb, v);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         uint4 w;
@@ -342,40 +463,44 @@ __global__ void __launch_bounds__(kThreads, 2)
   fence_before();
   __syncthreads();
 
-  // ---- 5. D2 = A2 W^t -------------------------------------------------------
+  // ---- 6. D' = A' W^t, written over D -----------------------------------------
   if (tid == 0 && ok) {
     fence_after();
-    const uint32_t a0 = smem_u32(smem + OFF_A2), b0 = smem_u32(smem + OFF_B2);
+    const uint32_t a0 = smem_u32(smem + OFF_A), b0 = smem_u32(smem + OFF_B2);
     const uint32_t idesc = instr_desc(kM, kN2, FP16);
 #pragma unroll
     for (int kk = 0; kk < kK2 / 16; ++kk)
-      mma_f16(tmem + kN1, smem_desc(a0 + kk * 256, 128, (kK2 / 8) * 128),
-              smem_desc(b0 + kk * 256, 128, (kK2 / 8) * 128), idesc, kk > 0);
+      mma_f16(tmem, smem_desc(a0 + kk * 256, 128, (kK2 / 8) * 128), smem_desc(b0 + kk * 256, 128, (kK2 / 8) * 128),
+              idesc, kk > 0);
     mma_commit(bar1);
   }
   if (ok) ok = mbar_wait(bar1, 0);
   fence_after();
 
-  // ---- 6. accumulate owned outputs --------------------------------------------
+  // ---- 7. accumulate owned outputs (columns split between warp w and w+4) -----
   if (ok) {
-    const int p = warp * 32 + lane;
+    const int p = (warp & 3) * 32 + lane;
     const int a = p % 5, b = (p / 5) % 5, c = p / 25;
     const bool live = p < 125 && (I0 + a) >= 1 && (I0 + a) <= nc - 1 && (J0 + b) >= 1 && (J0 + b) <= nc - 1 &&
                       (K0 + c) >= 1 && (K0 + c) <= nc - 1;
-#pragma unroll 1
-    for (int cb = 0; cb < kN2; cb += 16) {
-      float v[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + kN1 + cb, v);
-      if (live) {
-#pragma unroll
-        for (int t = 0; t < 16; ++t) {
-          const int l = cb + t;
-          if (l < 108) {
-            const int s = owned_index(l, a, b, c);
-            if (s >= 0) atomicAdd(ACC + s, v[t]);
-          }
-        }
-      }
+    const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    float v[16];
+    if ((warp >> 2) == 0) {
+      tmem_ld16(trow + 0, v);
+      if (live) scatter16<0>(ACC, v, a, b, c);
+      tmem_ld16(trow + 16, v);
+      if (live) scatter16<16>(ACC, v, a, b, c);
+      tmem_ld16(trow + 32, v);
+      if (live) scatter16<32>(ACC, v, a, b, c);
+      tmem_ld16(trow + 48, v);
+      if (live) scatter16<48>(ACC, v, a, b, c);
+    } else {
+      tmem_ld16(trow + 64, v);
+      if (live) scatter16<64>(ACC, v, a, b, c);
+      tmem_ld16(trow + 80, v);
+      if (live) scatter16<80>(ACC, v, a, b, c);
+      tmem_ld16(trow + 96, v);
+      if (live) scatter16<96>(ACC, v, a, b, c);
     }
   } else if (tid == 0) {
     atomicExch(status, kTimeout);
@@ -383,17 +508,25 @@ __global__ void __launch_bounds__(kThreads, 2)
   fence_before();
   __syncthreads();
 
-  // ---- 7. z[owned] += eta * acc / (s_w^2 s_r) ---------------------------------
+  // ---- 8. z[owned] += eta * acc / (s_w^2 s_r) ---------------------------------
   if (ok) {
+    // 1536 owned edges, 6 per thread: issue every load before the first add
+    constexpr int kPer = 3 * kOwn3 / kThreads;
+    static_assert(kPer * kThreads == 3 * kOwn3, "owned edges split evenly");
     const float sc = eta * wscale / rscale;
-    for (int q = tid; q < 3 * kOwn3; q += kThreads) {
+    int64_t gi[kPer];
+    float zv[kPer];
+#pragma unroll
+    for (int t = 0; t < kPer; ++t) {
+      const int q = tid + t * kThreads;
       const int d = q / kOwn3, e = q - d * kOwn3;
       const int i = 2 * I0 + e % kOwn, j = 2 * J0 + (e / kOwn) % kOwn, k = 2 * K0 + e / (kOwn * kOwn);
-      if (interior(n, d, i, j, k)) {
-        const int64_t g = gidx(n, d, i, j, k);
-        z[g] += sc * ACC[q];
-      }
+      gi[t] = interior(n, d, i, j, k) ? gidx(n, d, i, j, k) : -1;
+      zv[t] = gi[t] >= 0 ? z[gi[t]] : 0.f;
     }
+#pragma unroll
+    for (int t = 0; t < kPer; ++t)
+      if (gi[t] >= 0) z[gi[t]] = zv[t] + sc * ACC[tid + t * kThreads];
   }
   if (warp == 0) {
     fence_after();
@@ -413,12 +546,12 @@ cudaError_t upload_tc_operand(void** dst, const std::vector<double>& W, bool fp1
     uint16_t bits;
     if (fp16) {
       __half hv = __double2half(v);
-      bits = *reinterpret_cast<uint16_t*>(&hv);
+      std::memcpy(&bits, &hv, 2);
     } else {
       __nv_bfloat16 bv = __double2bfloat16(v);
-      bits = *reinterpret_cast<uint16_t*>(&bv);
+      std::memcpy(&bits, &bv, 2);
     }
-    *reinterpret_cast<uint16_t*>(base + core_off(row, k, K)) = bits;
+    std::memcpy(base + core_off(row, k, K), &bits, 2);
   };
   uint8_t* b1 = img.data();                    // B1[n][k] = W[k][n]: N = 64, K = 112
   uint8_t* b2 = img.data() + kN1 * kK1 * 2;    // B2[n][k] = W[n][k]: N = 112, K = 64
@@ -438,21 +571,22 @@ cudaError_t upload_tc_operand(void** dst, const std::vector<double>& W, bool fp1
 }
 
 cudaError_t prepare_tc_patch() {
-  cudaError_t e = cudaFuncSetAttribute(k_tc_patch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_patch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+  cudaError_t e = cudaFuncSetAttribute(k_tc_smoother<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tc_smoother<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
   return e;
 }
 
-void launch_tc_patch(cudaStream_t s, int, int n, const void* Wimg, bool fp16, double eta, const float* r, float* z,
-                     int* status) {
+void launch_tc_smoother(cudaStream_t s, int n, const void* Wimg, const float* AinvT, bool fp16, double eta,
+                        const float* r, float* z, int* status) {
   const int nc = n / 2;
-  if (nc < 2) return;
+  if (nc < 1) return;
   const int nbr = (nc + kB - 1) / kB;
   const int grid = nbr * nbr * nbr;
   if (fp16)
-    k_tc_patch<true><<<grid, kThreads, kSmem, s>>>(n, (const uint8_t*)Wimg, (float)eta, r, z, status);
+    k_tc_smoother<true><<<grid, kThreads, kSmem, s>>>(n, (const uint8_t*)Wimg, AinvT, (float)eta, r, z, status);
   else
-    k_tc_patch<false><<<grid, kThreads, kSmem, s>>>(n, (const uint8_t*)Wimg, (float)eta, r, z, status);
+    k_tc_smoother<false><<<grid, kThreads, kSmem, s>>>(n, (const uint8_t*)Wimg, AinvT, (float)eta, r, z, status);
 }
 
 }  // namespace ndmg

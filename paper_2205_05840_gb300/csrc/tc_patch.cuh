@@ -9,9 +9,11 @@ namespace ndmg {
 cudaError_t upload_tc_operand(void** dst, const std::vector<double>& W, bool fp16);
 // Opt in to the kernel's dynamic shared memory.
 cudaError_t prepare_tc_patch();
-// z += eta * sum_V J_V A_V^{-1} J_V^t r on level n (float vectors); on a
-// device-side timeout the kernel writes a nonzero code to *status.
-void launch_tc_patch(cudaStream_t s, int sm, int n, const void* Wimg, bool fp16, double eta, const float* r, float* z,
-                     int* status);
+// z += eta * (sum_T J_T A_T^{-1} J_T^t r + sum_V J_V A_V^{-1} J_V^t r) on
+// level n (float vectors), eq. (Preconditioner P), both terms in one kernel
+// (AinvT: the 6x6 interior-space inverse, FP32).  On a device-side timeout
+// the kernel writes a nonzero code to *status.
+void launch_tc_smoother(cudaStream_t s, int n, const void* Wimg, const float* AinvT, bool fp16, double eta,
+                        const float* r, float* z, int* status);
 
 }  // namespace ndmg

