@@ -17,8 +17,11 @@
  *     y-edge (node i in [1,n-1], segment j in [0,n), node k): n(n-1)^2 + ((k-1) n + j)(n-1) + (i-1)
  *     z-edge (nodes i,j in [1,n-1], segment k in [0,n)): 2n(n-1)^2 + (k(n-1) + (j-1))(n-1) + (i-1)
  *   Right-hand sides are load (dual) vectors <f_h, phi_e>.
- * Batches.  With opts.nrhs = R > 1 the vector arguments hold R right-hand
- *   sides interleaved as [dof][rhs] (element (e, r) at e * R + r).
+ * Batches.  With opts.nrhs = R > 1 every vector argument holds R right-hand
+ *   sides one after the other: right-hand side r is the canonical vector at
+ *   offset r * N(n_k).  All R are processed by the same launches (the batch is
+ *   a grid dimension of every kernel); solvers iterate them in lockstep with
+ *   per-right-hand-side scalars, and scalar outputs become arrays of R.
  * Pointers.  Vector arguments are DEVICE pointers owned by the caller (for
  *   instance torch tensors), contiguous, at least 16-byte aligned, and of the
  *   element type named by the call's `dtype` (NDMG_F64 = double, NDMG_F32 =
@@ -177,7 +180,8 @@ int ndmg_vcycle_iterate(ndmg_t* h, const double* f, double* u, double tol, int32
  * lambda, u: double device vectors on the finest level; out: host, nrhs doubles. */
 int ndmg_grad_alpha(ndmg_t* h, const double* lambda, const double* u, double* out);
 
-/* Inner product in FP64: out[r] = x_r^T y_r for the nrhs interleaved columns. */
+/* Inner product in FP64: out[r] = x_r^T y_r for each of the nrhs right-hand
+ * sides (out: host, nrhs doubles). */
 int ndmg_dot(ndmg_t* h, int32_t level, int32_t dtype, const void* x, const void* y, double* out);
 
 /* ---- tracing (no counterpart in the paper: measurement support) --------

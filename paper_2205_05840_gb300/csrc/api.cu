@@ -109,53 +109,57 @@ bool mixed(const ndmg_t* h) {
 }
 
 // ---------------------------------------------------------------------------
-// Level operations
+// Level operations (every launch covers the R = nrhs right-hand sides)
 // ---------------------------------------------------------------------------
+int nrhs(const ndmg_t* h) { return h->o.nrhs; }
+
 template <typename T>
 void op_residual(ndmg_t* h, int k, const T* g, const T* z, T* r) {
   DevLevel& L = h->lv[k];
-  Span sp(h, NDMG_K_STENCIL, 3.0 * sizeof(T) * L.N);  // read g, z; write r
-  launch_stencil<T>(h->stream, h->sm_count, L.n, L.cK, L.cM, z, g, r);
+  Span sp(h, NDMG_K_STENCIL, 3.0 * sizeof(T) * L.N * nrhs(h));  // read g, z; write r
+  launch_stencil<T>(h->stream, h->sm_count, L.n, L.cK, L.cM, z, g, r, nrhs(h));
 }
 
 template <typename T>
 void op_apply(ndmg_t* h, int k, const T* x, T* y) {
   DevLevel& L = h->lv[k];
-  Span sp(h, NDMG_K_STENCIL, 2.0 * sizeof(T) * L.N);  // read x; write y
-  launch_stencil<T>(h->stream, h->sm_count, L.n, L.cK, L.cM, x, (const T*)nullptr, y);
+  Span sp(h, NDMG_K_STENCIL, 2.0 * sizeof(T) * L.N * nrhs(h));  // read x; write y
+  launch_stencil<T>(h->stream, h->sm_count, L.n, L.cK, L.cM, x, (const T*)nullptr, y, nrhs(h));
 }
 
 // z += M_k^{-1} r (eta included), eq. (Preconditioner P)
 template <typename T>
 void op_smoother(ndmg_t* h, int k, const T* r, T* z) {
   DevLevel& L = h->lv[k];
+  const int R = nrhs(h);
   {
-    Span sp(h, NDMG_K_BUBBLE, bubble_bytes(L.n, sizeof(T)));
-    launch_bubble<T>(h->stream, h->sm_count, L.n, lv_Ainv(L, (T*)nullptr), h->o.eta, r, z);
+    Span sp(h, NDMG_K_BUBBLE, bubble_bytes(L.n, sizeof(T)) * R);
+    launch_bubble<T>(h->stream, h->sm_count, L.n, lv_Ainv(L, (T*)nullptr), h->o.eta, r, z, R);
   }
-  Span sp(h, NDMG_K_PATCH, num_patches(L.n) * 2.0 * 108 * 108);  // dense 108x108 per patch
-  launch_vertex_dense<T>(h->stream, h->sm_count, L.n, lv_D(L, (T*)nullptr), h->o.eta, r, z);
+  Span sp(h, NDMG_K_PATCH, num_patches(L.n) * 2.0 * 108 * 108 * R);  // dense 108x108 per patch
+  launch_vertex_dense<T>(h->stream, h->sm_count, L.n, lv_D(L, (T*)nullptr), h->o.eta, r, z, R);
 }
 
 template <>
 void op_smoother<float>(ndmg_t* h, int k, const float* r, float* z) {
   DevLevel& L = h->lv[k];
+  const int R = nrhs(h);
   if (mixed(h) && L.Wtc) {
     // one tensor-core kernel for both terms (Gram form: two 108x60 products
-    // per patch; the 6x6 interior solves ride along)
-    // algorithmic bytes: read r, read and write z (FP32); 25,920 flops per
-    // patch is ~86 flop/B, below the bf16 ridge of ~256 flop/B: memory-bound
-    Span sp(h, NDMG_K_PATCH, 12.0 * L.N);
+    // per patch; the 6x6 interior solves ride along).  Algorithmic bytes:
+    // read r, read and write z (FP32); 25,920 flops per patch is ~86 flop/B,
+    // below the bf16 ridge of ~256 flop/B, so the kernel is memory-bound.
+    Span sp(h, NDMG_K_PATCH, 12.0 * L.N * R);
     launch_tc_smoother(h->stream, L.n, L.Wtc, L.AinvT32, h->o.precision == NDMG_PREC_MIXED_FP16, h->o.eta, r, z,
-                       h->status);
+                       h->status, R);
     return;
   }
   {
-    Span sp(h, NDMG_K_BUBBLE, bubble_bytes(L.n, sizeof(float)));
-    launch_bubble<float>(h->stream, h->sm_count, L.n, L.AinvT32, h->o.eta, r, z);
+    Span sp(h, NDMG_K_BUBBLE, bubble_bytes(L.n, sizeof(float)) * R);
+    launch_bubble<float>(h->stream, h->sm_count, L.n, L.AinvT32, h->o.eta, r, z, R);
   }
-  Span sp(h, NDMG_K_PATCH, num_patches(L.n) * 2.0 * 108 * 108);
-  launch_vertex_dense<float>(h->stream, h->sm_count, L.n, L.Dv32, h->o.eta, r, z);
+  Span sp(h, NDMG_K_PATCH, num_patches(L.n) * 2.0 * 108 * 108 * R);
+  launch_vertex_dense<float>(h->stream, h->sm_count, L.n, L.Dv32, h->o.eta, r, z, R);
 }
 
 template <typename T>
@@ -170,10 +174,12 @@ void op_smooth_steps(ndmg_t* h, int k, const T* g, T* z, int steps) {
 // MG(k, g, z, m) of Fig. 1 with z in/out
 template <typename T>
 void op_vcycle(ndmg_t* h, int k, const T* g, T* z) {
+  const int R = nrhs(h);
   if (k == h->K) ++h->vcycle_total;
   if (k == 0) {
-    Span sp(h, NDMG_K_COARSE, 2.0 * sizeof(T) * h->lv[0].N + 8.0 * h->lv[0].N * h->lv[0].N);
-    launch_coarse<T>(h->stream, (int)h->lv[0].N, h->Ainv0, g, z);
+    const double N0 = (double)h->lv[0].N;
+    Span sp(h, NDMG_K_COARSE, (2.0 * sizeof(T) * N0 + 8.0 * N0 * N0) * R);
+    launch_coarse<T>(h->stream, (int)h->lv[0].N, h->Ainv0, g, z, R);
     return;
   }
   DevLevel& L = h->lv[k];
@@ -182,33 +188,53 @@ void op_vcycle(ndmg_t* h, int k, const T* g, T* z) {
   op_smooth_steps<T>(h, k, g, z, h->o.m);
   op_residual<T>(h, k, g, z, r);
   {
-    Span sp(h, NDMG_K_RESTRICT, (double)sizeof(T) * (L.N + C.N));
-    launch_restrict<T>(h->stream, h->sm_count, L.n, r, lv_g<T>(C));
+    Span sp(h, NDMG_K_RESTRICT, (double)sizeof(T) * (L.N + C.N) * R);
+    launch_restrict<T>(h->stream, h->sm_count, L.n, r, lv_g<T>(C), R);
   }
-  cudaMemsetAsync(lv_z<T>(C), 0, sizeof(T) * C.N, h->stream);
+  cudaMemsetAsync(lv_z<T>(C), 0, sizeof(T) * C.N * R, h->stream);
   op_vcycle<T>(h, k - 1, lv_g<T>(C), lv_z<T>(C));
   {
-    Span sp(h, NDMG_K_PROLONG, (double)sizeof(T) * (2 * L.N + C.N));
-    launch_prolong_add<T>(h->stream, h->sm_count, L.n, lv_z<T>(C), z);
+    Span sp(h, NDMG_K_PROLONG, (double)sizeof(T) * (2 * L.N + C.N) * R);
+    launch_prolong_add<T>(h->stream, h->sm_count, L.n, lv_z<T>(C), z, R);
   }
   op_smooth_steps<T>(h, k, g, z, h->o.m);
 }
 
-// two FP64 inner products, synchronised
+// per-right-hand-side FP64 inner products x_r.y_r (and x2_r.y2_r), synchronised
 template <typename T>
-int dot2(ndmg_t* h, int64_t N, const T* x, const T* y, const T* x2, const T* y2, double* a, double* b) {
+int dot2(ndmg_t* h, int64_t N, const T* x, const T* y, const T* x2, const T* y2, std::vector<double>& a,
+         std::vector<double>* b) {
+  const int R = nrhs(h);
   const int nb = reduction_blocks(h->sm_count);
-  double* out = h->red + 2 * nb;
+  double* out = h->red + 2 * (int64_t)nb * R;
   {
-    Span sp(h, NDMG_K_BLAS, (double)sizeof(T) * N * (x2 ? 4 : 2), 2);
-    launch_dot2<T>(h->stream, h->sm_count, N, x, y, x2, y2, h->red, out);
+    Span sp(h, NDMG_K_BLAS, (double)sizeof(T) * N * (x2 ? 4 : 2) * R, 2);
+    launch_dot2<T>(h->stream, h->sm_count, N, x, y, x2, y2, h->red, out, R);
   }
   NDMG_CK_LAUNCH();
-  NDMG_CK(cudaMemcpyAsync(h->red_host, out, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  NDMG_CK(cudaMemcpyAsync(h->red_host, out, 2 * sizeof(double) * R, cudaMemcpyDeviceToHost, h->stream));
   NDMG_CK(cudaStreamSynchronize(h->stream));
-  *a = h->red_host[0];
-  if (b) *b = h->red_host[1];
+  a.resize(R);
+  if (b) b->resize(R);
+  for (int i = 0; i < R; ++i) {
+    a[i] = h->red_host[2 * i];
+    if (b) (*b)[i] = h->red_host[2 * i + 1];
+  }
   return NDMG_OK;
+}
+
+// per-right-hand-side scalars for the BLAS kernels: each purpose has its own
+// pinned and device slot, rewritten only after a synchronisation that
+// follows its previous use
+enum CoefSlot { SLOT_ALPHA = 0, SLOT_AB = 1, SLOT_TO = 2, SLOT_FROM = 3, SLOT_COUNT = 4 };
+
+const double* push_coef(ndmg_t* h, int slot, const std::vector<double>& v) {
+  const int R = nrhs(h);
+  double* hp = h->coef_host + (size_t)slot * 2 * R;
+  double* dp = h->coef + (size_t)slot * 2 * R;
+  std::memcpy(hp, v.data(), sizeof(double) * v.size());
+  cudaMemcpyAsync(dp, hp, sizeof(double) * v.size(), cudaMemcpyHostToDevice, h->stream);
+  return dp;
 }
 
 int check_level(ndmg_t* h, int32_t& level, bool need_fine_transfer) {
@@ -232,10 +258,9 @@ int check_ptrs(ndmg_t* h, std::initializer_list<const void*> ps) {
 }
 
 int check_status(ndmg_t* h) {
-  int st = 0;
-  NDMG_CK(cudaMemcpyAsync(&h->red_host[4], h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  NDMG_CK(cudaMemcpyAsync(h->status_host, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   NDMG_CK(cudaStreamSynchronize(h->stream));
-  std::memcpy(&st, &h->red_host[4], sizeof(int));
+  const int st = *h->status_host;
   if (st != 0) {
     cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
     return fail(h, NDMG_DEVICE_TIMEOUT, "a device-side wait timed out (status " + std::to_string(st) + ")");
@@ -243,138 +268,135 @@ int check_status(ndmg_t* h) {
   return NDMG_OK;
 }
 
+double max_of(const std::vector<double>& v) {
+  double m = 0.0;
+  for (double x : v) m = std::isfinite(x) ? std::fmax(m, x) : x;
+  return m;
+}
+
 // ---------------------------------------------------------------------------
-// Solvers
+// Solvers.  All right-hand sides iterate in lockstep, each with its own
+// scalars; a right-hand side that has converged is frozen (alpha = beta = 0)
+// while the others continue.
 // ---------------------------------------------------------------------------
-// FP64 PCG preconditioned by one V-cycle
+struct CGState {
+  std::vector<double> nf, rz, relres;
+  std::vector<char> done;
+};
+
+// one CG scalar update for every right-hand side; returns BREAKDOWN on a
+// non-positive or non-finite curvature of a live right-hand side
+int cg_alpha(ndmg_t* h, CGState& S, const std::vector<double>& pq, std::vector<double>& a) {
+  const int R = nrhs(h);
+  a.assign(R, 0.0);
+  for (int i = 0; i < R; ++i) {
+    if (S.done[i]) continue;
+    if (!(pq[i] > 0.0) || !std::isfinite(pq[i])) return fail(h, NDMG_BREAKDOWN, "non-positive curvature p^T A p");
+    a[i] = S.rz[i] / pq[i];
+  }
+  return NDMG_OK;
+}
+
+// relative residuals from ||r||^2; marks converged right-hand sides
+int cg_check(ndmg_t* h, CGState& S, const std::vector<double>& rr, double tol, bool* all_done) {
+  const int R = nrhs(h);
+  *all_done = true;
+  for (int i = 0; i < R; ++i) {
+    S.relres[i] = std::sqrt(rr[i]) / S.nf[i];
+    if (!std::isfinite(S.relres[i])) return fail(h, NDMG_BREAKDOWN, "non-finite residual");
+    if (S.relres[i] <= tol) S.done[i] = 1;
+    *all_done = *all_done && S.done[i];
+  }
+  return NDMG_OK;
+}
+
+int cg_init(ndmg_t* h, CGState& S, const std::vector<double>& ff, const std::vector<double>& rr, double tol,
+            bool* all_done) {
+  const int R = nrhs(h);
+  S.nf.resize(R);
+  S.rz.assign(R, 0.0);
+  S.relres.assign(R, 0.0);
+  S.done.assign(R, 0);
+  for (int i = 0; i < R; ++i) S.nf[i] = std::sqrt(ff[i]) > 0 ? std::sqrt(ff[i]) : 1.0;
+  return cg_check(h, S, rr, tol, all_done);
+}
+
+// FP64 PCG preconditioned by one FP64 V-cycle
 int pcg64(ndmg_t* h, const double* f, double* u, double tol, int maxit, int* iters, double* relres) {
-  const int K = h->K;
+  const int K = h->K, R = nrhs(h);
   const int64_t N = h->lv[K].N;
   const int sm = h->sm_count;
   double *r = h->w64[0], *z = h->w64[1], *p = h->w64[2], *q = h->w64[3];
-  double ff, rr, rz, pq, dum;
+  std::vector<double> ff, rr, pq, rz_new, a, ab(2 * R);
+  CGState S;
+  bool all_done = false;
   int st;
   *iters = 0;
   op_residual<double>(h, K, f, u, r);
-  if ((st = dot2<double>(h, N, f, f, r, r, &ff, &rr)) != NDMG_OK) return st;
-  const double nf = std::sqrt(ff) > 0 ? std::sqrt(ff) : 1.0;
-  *relres = std::sqrt(rr) / nf;
-  if (!std::isfinite(*relres)) return fail(h, NDMG_BREAKDOWN, "non-finite residual");
-  if (*relres <= tol) return NDMG_OK;
-  cudaMemsetAsync(z, 0, sizeof(double) * N, h->stream);
+  if ((st = dot2<double>(h, N, f, f, r, r, ff, &rr)) != NDMG_OK) return st;
+  if ((st = cg_init(h, S, ff, rr, tol, &all_done)) != NDMG_OK) return st;
+  *relres = max_of(S.relres);
+  if (all_done) return NDMG_OK;
+  cudaMemsetAsync(z, 0, sizeof(double) * N * R, h->stream);
   op_vcycle<double>(h, K, r, z);
-  if ((st = dot2<double>(h, N, r, z, (const double*)nullptr, (const double*)nullptr, &rz, &dum)) != NDMG_OK) return st;
-  NDMG_CK(cudaMemcpyAsync(p, z, sizeof(double) * N, cudaMemcpyDeviceToDevice, h->stream));
+  if ((st = dot2<double>(h, N, r, z, (const double*)nullptr, (const double*)nullptr, S.rz, nullptr)) != NDMG_OK)
+    return st;
+  NDMG_CK(cudaMemcpyAsync(p, z, sizeof(double) * N * R, cudaMemcpyDeviceToDevice, h->stream));
   for (int it = 1; it <= maxit; ++it) {
     op_apply<double>(h, K, p, q);
-    if ((st = dot2<double>(h, N, p, q, (const double*)nullptr, (const double*)nullptr, &pq, &dum)) != NDMG_OK) return st;
-    if (!(pq > 0.0) || !std::isfinite(pq)) return fail(h, NDMG_BREAKDOWN, "non-positive curvature p^T A p");
-    const double a = rz / pq;
+    if ((st = dot2<double>(h, N, p, q, (const double*)nullptr, (const double*)nullptr, pq, nullptr)) != NDMG_OK)
+      return st;
+    if ((st = cg_alpha(h, S, pq, a)) != NDMG_OK) return st;
     {
-      Span sp(h, NDMG_K_BLAS, 6.0 * 8 * N);
-      launch_cg_update<double>(h->stream, sm, N, a, p, q, u, r);
+      const double* da = push_coef(h, SLOT_ALPHA, a);
+      Span sp(h, NDMG_K_BLAS, 6.0 * 8 * N * R);
+      launch_cg_update<double>(h->stream, sm, N, da, p, q, u, r, R);
     }
-    if ((st = dot2<double>(h, N, r, r, (const double*)nullptr, (const double*)nullptr, &rr, &dum)) != NDMG_OK) return st;
+    if ((st = dot2<double>(h, N, r, r, (const double*)nullptr, (const double*)nullptr, rr, nullptr)) != NDMG_OK)
+      return st;
     *iters = it;
-    *relres = std::sqrt(rr) / nf;
-    if (!std::isfinite(*relres)) return fail(h, NDMG_BREAKDOWN, "non-finite residual");
-    if (*relres <= tol) return NDMG_OK;
-    cudaMemsetAsync(z, 0, sizeof(double) * N, h->stream);
+    if ((st = cg_check(h, S, rr, tol, &all_done)) != NDMG_OK) return st;
+    *relres = max_of(S.relres);
+    if (all_done) return NDMG_OK;
+    cudaMemsetAsync(z, 0, sizeof(double) * N * R, h->stream);
     op_vcycle<double>(h, K, r, z);
-    double rz_new;
-    if ((st = dot2<double>(h, N, r, z, (const double*)nullptr, (const double*)nullptr, &rz_new, &dum)) != NDMG_OK) return st;
-    {
-      Span sp(h, NDMG_K_BLAS, 3.0 * 8 * N);
-      launch_axpby<double>(h->stream, sm, N, 1.0, z, rz_new / rz, p);
+    if ((st = dot2<double>(h, N, r, z, (const double*)nullptr, (const double*)nullptr, rz_new, nullptr)) != NDMG_OK)
+      return st;
+    for (int i = 0; i < R; ++i) {
+      ab[2 * i] = 1.0;
+      ab[2 * i + 1] = (S.done[i] || S.rz[i] == 0.0) ? 0.0 : rz_new[i] / S.rz[i];
+      S.rz[i] = rz_new[i];
     }
-    rz = rz_new;
+    {
+      const double* dab = push_coef(h, SLOT_AB, ab);
+      Span sp(h, NDMG_K_BLAS, 3.0 * 8 * N * R);
+      launch_axpby<double>(h->stream, sm, N, dab, z, p, R);
+    }
   }
   return fail(h, NDMG_NOT_CONVERGED, "PCG reached maxit");
 }
 
-// float PCG on A d = b (b float, d float, d starts at 0) to relative tol;
-// flexible beta = -a (q.z_new) / (r.z)_old so that a slightly nonsymmetric
-// low-precision preconditioner is tolerated.
-int pcg32(ndmg_t* h, const float* b, float* d, double tol, int maxit, int* iters) {
-  const int K = h->K;
+// the float V-cycle as preconditioner of FP64 vectors: z = ||r|| MG(r / ||r||)
+int precondition_mixed(ndmg_t* h, const double* r, double* z, const std::vector<double>& rnorm) {
+  const int K = h->K, R = nrhs(h);
   const int64_t N = h->lv[K].N;
   const int sm = h->sm_count;
-  float *r = h->w32[0], *z = h->w32[1], *p = h->w32[2], *q = h->w32[3];
-  double bb, rz, pq, rr, dum;
-  int st;
-  *iters = 0;
-  cudaMemsetAsync(d, 0, sizeof(float) * N, h->stream);
-  NDMG_CK(cudaMemcpyAsync(r, b, sizeof(float) * N, cudaMemcpyDeviceToDevice, h->stream));
-  cudaMemsetAsync(z, 0, sizeof(float) * N, h->stream);
-  op_vcycle<float>(h, K, r, z);
-  if (mixed(h) && (st = check_status(h)) != NDMG_OK) return st;
-  if ((st = dot2<float>(h, N, b, b, r, z, &bb, &rz)) != NDMG_OK) return st;
-  if (bb == 0.0) return NDMG_OK;
-  NDMG_CK(cudaMemcpyAsync(p, z, sizeof(float) * N, cudaMemcpyDeviceToDevice, h->stream));
-  const double nb = std::sqrt(bb);
-  for (int it = 1; it <= maxit; ++it) {
-    op_apply<float>(h, K, p, q);
-    if ((st = dot2<float>(h, N, p, q, (const float*)nullptr, (const float*)nullptr, &pq, &dum)) != NDMG_OK) return st;
-    if (!(pq > 0.0) || !std::isfinite(pq)) return fail(h, NDMG_BREAKDOWN, "non-positive curvature (float PCG)");
-    const double a = rz / pq;
-    {
-      Span sp(h, NDMG_K_BLAS, 6.0 * 4 * N);
-      launch_cg_update<float>(h->stream, sm, N, a, p, q, d, r);
-    }
-    if ((st = dot2<float>(h, N, r, r, (const float*)nullptr, (const float*)nullptr, &rr, &dum)) != NDMG_OK) return st;
-    *iters = it;
-    if (!std::isfinite(rr)) return fail(h, NDMG_BREAKDOWN, "non-finite residual (float PCG)");
-    if (std::sqrt(rr) <= tol * nb) return NDMG_OK;
-    cudaMemsetAsync(z, 0, sizeof(float) * N, h->stream);
-    op_vcycle<float>(h, K, r, z);
-    if (mixed(h) && (st = check_status(h)) != NDMG_OK) return st;
-    double rz_new, qz;
-    if ((st = dot2<float>(h, N, r, z, q, z, &rz_new, &qz)) != NDMG_OK) return st;
-    {
-      Span sp(h, NDMG_K_BLAS, 3.0 * 4 * N);
-      launch_axpby<float>(h->stream, sm, N, 1.0, z, -a * qz / rz, p);
-    }
-    rz = rz_new;
+  float *r32 = h->w32[4], *z32 = h->w32[5];
+  std::vector<double> inv(R);
+  for (int i = 0; i < R; ++i) inv[i] = rnorm[i] > 0 ? 1.0 / rnorm[i] : 0.0;
+  {
+    const double* d = push_coef(h, SLOT_TO, inv);
+    Span sp(h, NDMG_K_BLAS, 12.0 * N * R);
+    launch_to_f32(h->stream, sm, N, d, r, r32, R);
   }
-  return NDMG_OK;  // the outer loop decides convergence
-}
-
-// FP64 iterative refinement around the float PCG
-int solve_ir(ndmg_t* h, const double* f, double* u, double tol, double inner_tol, int maxit, int* iters,
-             double* relres) {
-  const int K = h->K;
-  const int64_t N = h->lv[K].N;
-  const int sm = h->sm_count;
-  double* r = h->w64[0];
-  float* b32 = h->w32[4];
-  float* d32 = h->w32[5];
-  double ff, rr;
-  int st;
-  *iters = 0;
-  if ((st = dot2<double>(h, N, f, f, (const double*)nullptr, (const double*)nullptr, &ff, &rr)) != NDMG_OK) return st;
-  const double nf = std::sqrt(ff) > 0 ? std::sqrt(ff) : 1.0;
-  for (int outer = 0; outer < 64; ++outer) {
-    op_residual<double>(h, K, f, u, r);
-    if ((st = dot2<double>(h, N, r, r, (const double*)nullptr, (const double*)nullptr, &rr, &ff)) != NDMG_OK) return st;
-    const double rn = std::sqrt(rr);
-    *relres = rn / nf;
-    if (!std::isfinite(*relres)) return fail(h, NDMG_BREAKDOWN, "non-finite residual");
-    if (*relres <= tol) return check_status(h);
-    if (*iters >= maxit) return fail(h, NDMG_NOT_CONVERGED, "refinement reached maxit inner iterations");
-    {
-      Span sp(h, NDMG_K_BLAS, 12.0 * N);
-      launch_to_f32(h->stream, sm, N, 1.0 / rn, r, b32);
-    }
-    int it = 0;
-    if ((st = pcg32(h, b32, d32, inner_tol, maxit - *iters, &it)) != NDMG_OK) return st;
-    *iters += it;
-    {
-      Span sp(h, NDMG_K_BLAS, 20.0 * N);
-      launch_add_f32(h->stream, sm, N, rn, d32, u);
-    }
-    NDMG_CK_LAUNCH();
+  cudaMemsetAsync(z32, 0, sizeof(float) * N * R, h->stream);
+  op_vcycle<float>(h, K, r32, z32);
+  {
+    const double* d = push_coef(h, SLOT_FROM, rnorm);
+    Span sp(h, NDMG_K_BLAS, 12.0 * N * R);
+    launch_from_f32(h->stream, sm, N, d, z32, z, R);
   }
-  return fail(h, NDMG_NOT_CONVERGED, "refinement stalled");
+  return mixed(h) ? check_status(h) : NDMG_OK;
 }
 
 // FP64 flexible PCG preconditioned by the float V-cycle (mixed handles):
@@ -383,60 +405,164 @@ int solve_ir(ndmg_t* h, const double* f, double* u, double tol, double inner_tol
 // beta = -a (q . z_new) / (r . z)_old (flexible form: the low-precision
 // V-cycle is symmetric only up to rounding).
 int pcg_mixed(ndmg_t* h, const double* f, double* u, double tol, int maxit, int* iters, double* relres) {
-  const int K = h->K;
+  const int K = h->K, R = nrhs(h);
   const int64_t N = h->lv[K].N;
   const int sm = h->sm_count;
   double *r = h->w64[0], *z = h->w64[1], *p = h->w64[2], *q = h->w64[3];
-  float *r32 = h->w32[4], *z32 = h->w32[5];
-  double ff, rr, rz, pq, dum;
+  std::vector<double> ff, rr, pq, rz_new, qz, a, ab(2 * R), rn(R);
+  CGState S;
+  bool all_done = false;
   int st;
   *iters = 0;
-  auto precondition = [&](double rnorm) -> int {
-    {
-      Span sp(h, NDMG_K_BLAS, 12.0 * N);
-      launch_to_f32(h->stream, sm, N, 1.0 / rnorm, r, r32);
-    }
-    cudaMemsetAsync(z32, 0, sizeof(float) * N, h->stream);
-    op_vcycle<float>(h, K, r32, z32);
-    {
-      Span sp(h, NDMG_K_BLAS, 12.0 * N);
-      launch_from_f32(h->stream, sm, N, rnorm, z32, z);
-    }
-    return mixed(h) ? check_status(h) : NDMG_OK;
-  };
   op_residual<double>(h, K, f, u, r);
-  if ((st = dot2<double>(h, N, f, f, r, r, &ff, &rr)) != NDMG_OK) return st;
-  const double nf = std::sqrt(ff) > 0 ? std::sqrt(ff) : 1.0;
-  *relres = std::sqrt(rr) / nf;
-  if (!std::isfinite(*relres)) return fail(h, NDMG_BREAKDOWN, "non-finite residual");
-  if (*relres <= tol) return NDMG_OK;
-  if ((st = precondition(std::sqrt(rr))) != NDMG_OK) return st;
-  if ((st = dot2<double>(h, N, r, z, (const double*)nullptr, (const double*)nullptr, &rz, &dum)) != NDMG_OK) return st;
-  NDMG_CK(cudaMemcpyAsync(p, z, sizeof(double) * N, cudaMemcpyDeviceToDevice, h->stream));
+  if ((st = dot2<double>(h, N, f, f, r, r, ff, &rr)) != NDMG_OK) return st;
+  if ((st = cg_init(h, S, ff, rr, tol, &all_done)) != NDMG_OK) return st;
+  *relres = max_of(S.relres);
+  if (all_done) return NDMG_OK;
+  for (int i = 0; i < R; ++i) rn[i] = std::sqrt(rr[i]);
+  if ((st = precondition_mixed(h, r, z, rn)) != NDMG_OK) return st;
+  if ((st = dot2<double>(h, N, r, z, (const double*)nullptr, (const double*)nullptr, S.rz, nullptr)) != NDMG_OK)
+    return st;
+  NDMG_CK(cudaMemcpyAsync(p, z, sizeof(double) * N * R, cudaMemcpyDeviceToDevice, h->stream));
   for (int it = 1; it <= maxit; ++it) {
     op_apply<double>(h, K, p, q);
-    if ((st = dot2<double>(h, N, p, q, (const double*)nullptr, (const double*)nullptr, &pq, &dum)) != NDMG_OK) return st;
-    if (!(pq > 0.0) || !std::isfinite(pq)) return fail(h, NDMG_BREAKDOWN, "non-positive curvature p^T A p");
-    const double a = rz / pq;
+    if ((st = dot2<double>(h, N, p, q, (const double*)nullptr, (const double*)nullptr, pq, nullptr)) != NDMG_OK)
+      return st;
+    if ((st = cg_alpha(h, S, pq, a)) != NDMG_OK) return st;
     {
-      Span sp(h, NDMG_K_BLAS, 6.0 * 8 * N);
-      launch_cg_update<double>(h->stream, sm, N, a, p, q, u, r);
+      const double* da = push_coef(h, SLOT_ALPHA, a);
+      Span sp(h, NDMG_K_BLAS, 6.0 * 8 * N * R);
+      launch_cg_update<double>(h->stream, sm, N, da, p, q, u, r, R);
     }
-    if ((st = dot2<double>(h, N, r, r, (const double*)nullptr, (const double*)nullptr, &rr, &dum)) != NDMG_OK) return st;
+    if ((st = dot2<double>(h, N, r, r, (const double*)nullptr, (const double*)nullptr, rr, nullptr)) != NDMG_OK)
+      return st;
     *iters = it;
-    *relres = std::sqrt(rr) / nf;
-    if (!std::isfinite(*relres)) return fail(h, NDMG_BREAKDOWN, "non-finite residual");
-    if (*relres <= tol) return NDMG_OK;
-    if ((st = precondition(std::sqrt(rr))) != NDMG_OK) return st;
-    double rz_new, qz;
-    if ((st = dot2<double>(h, N, r, z, q, z, &rz_new, &qz)) != NDMG_OK) return st;
-    {
-      Span sp(h, NDMG_K_BLAS, 3.0 * 8 * N);
-      launch_axpby<double>(h->stream, sm, N, 1.0, z, -a * qz / rz, p);
+    if ((st = cg_check(h, S, rr, tol, &all_done)) != NDMG_OK) return st;
+    *relres = max_of(S.relres);
+    if (all_done) return NDMG_OK;
+    for (int i = 0; i < R; ++i) rn[i] = std::sqrt(rr[i]);
+    if ((st = precondition_mixed(h, r, z, rn)) != NDMG_OK) return st;
+    if ((st = dot2<double>(h, N, r, z, q, z, rz_new, &qz)) != NDMG_OK) return st;
+    for (int i = 0; i < R; ++i) {
+      ab[2 * i] = 1.0;
+      ab[2 * i + 1] = (S.done[i] || S.rz[i] == 0.0) ? 0.0 : -a[i] * qz[i] / S.rz[i];
+      S.rz[i] = rz_new[i];
     }
-    rz = rz_new;
+    {
+      const double* dab = push_coef(h, SLOT_AB, ab);
+      Span sp(h, NDMG_K_BLAS, 3.0 * 8 * N * R);
+      launch_axpby<double>(h->stream, sm, N, dab, z, p, R);
+    }
   }
   return fail(h, NDMG_NOT_CONVERGED, "PCG reached maxit");
+}
+
+// float PCG on A d = b (b float, d float, d starts at 0) to relative tol;
+// flexible beta.  Returns OK also when maxit is reached: the outer
+// refinement loop judges convergence.
+int pcg32(ndmg_t* h, const float* b, float* d, double tol, int maxit, int* iters) {
+  const int K = h->K, R = nrhs(h);
+  const int64_t N = h->lv[K].N;
+  const int sm = h->sm_count;
+  float *r = h->w32[0], *z = h->w32[1], *p = h->w32[2], *q = h->w32[3];
+  std::vector<double> bb, rr, pq, rz_new, qz, a, ab(2 * R);
+  CGState S;
+  bool all_done = false;
+  int st;
+  *iters = 0;
+  cudaMemsetAsync(d, 0, sizeof(float) * N * R, h->stream);
+  NDMG_CK(cudaMemcpyAsync(r, b, sizeof(float) * N * R, cudaMemcpyDeviceToDevice, h->stream));
+  cudaMemsetAsync(z, 0, sizeof(float) * N * R, h->stream);
+  op_vcycle<float>(h, K, r, z);
+  if (mixed(h) && (st = check_status(h)) != NDMG_OK) return st;
+  if ((st = dot2<float>(h, N, b, b, r, z, bb, &S.rz)) != NDMG_OK) return st;
+  std::vector<double> rz0 = S.rz;
+  if ((st = cg_init(h, S, bb, bb, 2.0, &all_done)) != NDMG_OK) return st;   // relres = 1 < 2: none done
+  S.rz = rz0;
+  for (int i = 0; i < R; ++i) S.done[i] = bb[i] == 0.0;
+  NDMG_CK(cudaMemcpyAsync(p, z, sizeof(float) * N * R, cudaMemcpyDeviceToDevice, h->stream));
+  for (int it = 1; it <= maxit; ++it) {
+    op_apply<float>(h, K, p, q);
+    if ((st = dot2<float>(h, N, p, q, (const float*)nullptr, (const float*)nullptr, pq, nullptr)) != NDMG_OK)
+      return st;
+    if ((st = cg_alpha(h, S, pq, a)) != NDMG_OK) return st;
+    {
+      const double* da = push_coef(h, SLOT_ALPHA, a);
+      Span sp(h, NDMG_K_BLAS, 6.0 * 4 * N * R);
+      launch_cg_update<float>(h->stream, sm, N, da, p, q, d, r, R);
+    }
+    if ((st = dot2<float>(h, N, r, r, (const float*)nullptr, (const float*)nullptr, rr, nullptr)) != NDMG_OK)
+      return st;
+    *iters = it;
+    if ((st = cg_check(h, S, rr, tol, &all_done)) != NDMG_OK) return st;
+    if (all_done) return NDMG_OK;
+    cudaMemsetAsync(z, 0, sizeof(float) * N * R, h->stream);
+    op_vcycle<float>(h, K, r, z);
+    if (mixed(h) && (st = check_status(h)) != NDMG_OK) return st;
+    if ((st = dot2<float>(h, N, r, z, q, z, rz_new, &qz)) != NDMG_OK) return st;
+    for (int i = 0; i < R; ++i) {
+      ab[2 * i] = 1.0;
+      ab[2 * i + 1] = (S.done[i] || S.rz[i] == 0.0) ? 0.0 : -a[i] * qz[i] / S.rz[i];
+      S.rz[i] = rz_new[i];
+    }
+    {
+      const double* dab = push_coef(h, SLOT_AB, ab);
+      Span sp(h, NDMG_K_BLAS, 3.0 * 4 * N * R);
+      launch_axpby<float>(h->stream, sm, N, dab, z, p, R);
+    }
+  }
+  return NDMG_OK;
+}
+
+// FP64 iterative refinement around the float PCG
+int solve_ir(ndmg_t* h, const double* f, double* u, double tol, double inner_tol, int maxit, int* iters,
+             double* relres) {
+  const int K = h->K, R = nrhs(h);
+  const int64_t N = h->lv[K].N;
+  const int sm = h->sm_count;
+  double* r = h->w64[0];
+  float* b32 = h->w32[4];
+  float* d32 = h->w32[5];
+  std::vector<double> ff, rr, inv(R), rn(R);
+  int st;
+  *iters = 0;
+  if ((st = dot2<double>(h, N, f, f, (const double*)nullptr, (const double*)nullptr, ff, nullptr)) != NDMG_OK)
+    return st;
+  for (int outer = 0; outer < 64; ++outer) {
+    op_residual<double>(h, K, f, u, r);
+    if ((st = dot2<double>(h, N, r, r, (const double*)nullptr, (const double*)nullptr, rr, nullptr)) != NDMG_OK)
+      return st;
+    bool all_done = true;
+    double worst = 0.0;
+    for (int i = 0; i < R; ++i) {
+      const double nf = std::sqrt(ff[i]) > 0 ? std::sqrt(ff[i]) : 1.0;
+      const double rel = std::sqrt(rr[i]) / nf;
+      if (!std::isfinite(rel)) return fail(h, NDMG_BREAKDOWN, "non-finite residual");
+      worst = std::fmax(worst, rel);
+      const bool done = rel <= tol;
+      all_done = all_done && done;
+      rn[i] = done ? 0.0 : std::sqrt(rr[i]);            // converged columns get a zero correction
+      inv[i] = rn[i] > 0 ? 1.0 / rn[i] : 0.0;
+    }
+    *relres = worst;
+    if (all_done) return check_status(h);
+    if (*iters >= maxit) return fail(h, NDMG_NOT_CONVERGED, "refinement reached maxit inner iterations");
+    {
+      const double* d = push_coef(h, SLOT_TO, inv);
+      Span sp(h, NDMG_K_BLAS, 12.0 * N * R);
+      launch_to_f32(h->stream, sm, N, d, r, b32, R);
+    }
+    int it = 0;
+    if ((st = pcg32(h, b32, d32, inner_tol, maxit - *iters, &it)) != NDMG_OK) return st;
+    *iters += it;
+    {
+      const double* d = push_coef(h, SLOT_FROM, rn);
+      Span sp(h, NDMG_K_BLAS, 20.0 * N * R);
+      launch_add_f32(h->stream, sm, N, d, d32, u, R);
+    }
+    NDMG_CK_LAUNCH();
+  }
+  return fail(h, NDMG_NOT_CONVERGED, "refinement stalled");
 }
 
 void free_handle(ndmg_t* h) {
@@ -450,8 +576,11 @@ void free_handle(ndmg_t* h) {
   cudaFree(h->Ainv0);
   for (int i = 0; i < 6; ++i) { cudaFree(h->w64[i]); cudaFree(h->w32[i]); }
   cudaFree(h->red);
+  cudaFree(h->coef);
   cudaFree(h->status);
   if (h->red_host) cudaFreeHost(h->red_host);
+  if (h->coef_host) cudaFreeHost(h->coef_host);
+  if (h->status_host) cudaFreeHost(h->status_host);
   for (int c = 0; c < NDMG_K_COUNT; ++c)
     for (auto& pr : h->ev_used[c]) h->ev_free.push_back(pr);
   for (auto& pr : h->ev_free) {
@@ -519,7 +648,7 @@ int ndmg_create(const ndmg_opts* o, ndmg_t** out) {
   if (!o) return NDMG_INVALID_ARG;
   if (o->n < 2 || o->n_coarsest < 2 || o->n < o->n_coarsest) return NDMG_INVALID_ARG;
   if (!(o->L > 0) || !(o->alpha > 0) || !(o->beta > 0) || o->m < 1 || o->nrhs < 1) return NDMG_INVALID_ARG;
-  if (o->nrhs != 1) return NDMG_INVALID_ARG;              // batched layout: not built yet
+  if (o->nrhs > 4096) return NDMG_INVALID_ARG;
   if (o->smoother != NDMG_SMOOTHER_VERTEX) return NDMG_INVALID_ARG;
   if (o->precision < NDMG_PREC_FP64 || o->precision > NDMG_PREC_FP32) return NDMG_INVALID_ARG;
   if (edges(o->n_coarsest) > 4096) return NDMG_INVALID_ARG;   // dense coarsest inverse
@@ -555,28 +684,32 @@ int ndmg_create(const ndmg_opts* o, ndmg_t** out) {
   }
   h->lv.resize(K + 1);
   cudaError_t ae = cudaSuccess;
+  const int64_t R = o->nrhs;
   for (int k = 0; k <= K; ++k) {
     DevLevel& L = h->lv[k];
     L.n = o->n_coarsest << k;
     L.N = edges(L.n);
     L.h = o->L / L.n;
-    L.r64 = dev_alloc<double>(L.N, &ae);
-    L.r32 = dev_alloc<float>(L.N, &ae);
+    L.r64 = dev_alloc<double>(L.N * R, &ae);
+    L.r32 = dev_alloc<float>(L.N * R, &ae);
     if (k < K) {
-      L.g64 = dev_alloc<double>(L.N, &ae);
-      L.z64 = dev_alloc<double>(L.N, &ae);
-      L.g32 = dev_alloc<float>(L.N, &ae);
-      L.z32 = dev_alloc<float>(L.N, &ae);
+      L.g64 = dev_alloc<double>(L.N * R, &ae);
+      L.z64 = dev_alloc<double>(L.N * R, &ae);
+      L.g32 = dev_alloc<float>(L.N * R, &ae);
+      L.z32 = dev_alloc<float>(L.N * R, &ae);
     }
   }
-  const int64_t NF = h->lv[K].N;
+  const int64_t NF = h->lv[K].N * R;
   for (int i = 0; i < 6; ++i) {
     h->w64[i] = dev_alloc<double>(NF, &ae);
     h->w32[i] = dev_alloc<float>(NF, &ae);
   }
-  h->red = dev_alloc<double>(2 * reduction_blocks(h->sm_count) + 8, &ae);
+  h->red = dev_alloc<double>(2 * (int64_t)reduction_blocks(h->sm_count) * R + 2 * R + 8, &ae);
+  h->coef = dev_alloc<double>(4 * 2 * R, &ae);
   h->status = dev_alloc<int>(4, &ae);
-  if (ae == cudaSuccess) ae = cudaMallocHost((void**)&h->red_host, 8 * sizeof(double));
+  if (ae == cudaSuccess) ae = cudaMallocHost((void**)&h->red_host, (2 * R + 8) * sizeof(double));
+  if (ae == cudaSuccess) ae = cudaMallocHost((void**)&h->coef_host, 4 * 2 * R * sizeof(double));
+  if (ae == cudaSuccess) ae = cudaMallocHost((void**)&h->status_host, 4 * sizeof(int));
   if (ae == cudaSuccess) ae = cudaMemset(h->status, 0, 4 * sizeof(int));
   if (ae == cudaSuccess) ae = prepare_stencil<double>();
   if (ae == cudaSuccess) ae = prepare_stencil<float>();
@@ -663,9 +796,11 @@ int ndmg_restrict(ndmg_t* h, int32_t level, int32_t dtype, const void* r_fine, v
   int st;
   if ((st = check_level(h, level, true)) || (st = check_dtype(h, dtype)) || (st = check_ptrs(h, {r_fine, g_coarse})))
     return st;
-  Span sp(h, NDMG_K_RESTRICT, (dtype == NDMG_F64 ? 8.0 : 4.0) * (h->lv[level].N + h->lv[level - 1].N));
-  if (dtype == NDMG_F64) launch_restrict<double>(h->stream, h->sm_count, h->lv[level].n, (const double*)r_fine, (double*)g_coarse);
-  else launch_restrict<float>(h->stream, h->sm_count, h->lv[level].n, (const float*)r_fine, (float*)g_coarse);
+  Span sp(h, NDMG_K_RESTRICT, (dtype == NDMG_F64 ? 8.0 : 4.0) * (h->lv[level].N + h->lv[level - 1].N) * nrhs(h));
+  if (dtype == NDMG_F64)
+    launch_restrict<double>(h->stream, h->sm_count, h->lv[level].n, (const double*)r_fine, (double*)g_coarse, nrhs(h));
+  else
+    launch_restrict<float>(h->stream, h->sm_count, h->lv[level].n, (const float*)r_fine, (float*)g_coarse, nrhs(h));
   NDMG_CK_LAUNCH();
   return NDMG_OK;
 }
@@ -675,9 +810,13 @@ int ndmg_prolong_add(ndmg_t* h, int32_t level, int32_t dtype, const void* z_coar
   int st;
   if ((st = check_level(h, level, true)) || (st = check_dtype(h, dtype)) || (st = check_ptrs(h, {z_coarse, z_fine})))
     return st;
-  Span sp(h, NDMG_K_PROLONG, (dtype == NDMG_F64 ? 8.0 : 4.0) * (2 * h->lv[level].N + h->lv[level - 1].N));
-  if (dtype == NDMG_F64) launch_prolong_add<double>(h->stream, h->sm_count, h->lv[level].n, (const double*)z_coarse, (double*)z_fine);
-  else launch_prolong_add<float>(h->stream, h->sm_count, h->lv[level].n, (const float*)z_coarse, (float*)z_fine);
+  Span sp(h, NDMG_K_PROLONG, (dtype == NDMG_F64 ? 8.0 : 4.0) * (2 * h->lv[level].N + h->lv[level - 1].N) * nrhs(h));
+  if (dtype == NDMG_F64)
+    launch_prolong_add<double>(h->stream, h->sm_count, h->lv[level].n, (const double*)z_coarse, (double*)z_fine,
+                               nrhs(h));
+  else
+    launch_prolong_add<float>(h->stream, h->sm_count, h->lv[level].n, (const float*)z_coarse, (float*)z_fine,
+                              nrhs(h));
   NDMG_CK_LAUNCH();
   return NDMG_OK;
 }
@@ -686,9 +825,11 @@ int ndmg_coarse_solve(ndmg_t* h, int32_t dtype, const void* g, void* z) {
   if (!h) return NDMG_INVALID_ARG;
   int st;
   if ((st = check_dtype(h, dtype)) || (st = check_ptrs(h, {g, z}))) return st;
-  Span sp(h, NDMG_K_COARSE, 8.0 * h->lv[0].N * (h->lv[0].N + 2));
-  if (dtype == NDMG_F64) launch_coarse<double>(h->stream, (int)h->lv[0].N, h->Ainv0, (const double*)g, (double*)z);
-  else launch_coarse<float>(h->stream, (int)h->lv[0].N, h->Ainv0, (const float*)g, (float*)z);
+  Span sp(h, NDMG_K_COARSE, 8.0 * h->lv[0].N * (h->lv[0].N + 2) * nrhs(h));
+  if (dtype == NDMG_F64)
+    launch_coarse<double>(h->stream, (int)h->lv[0].N, h->Ainv0, (const double*)g, (double*)z, nrhs(h));
+  else
+    launch_coarse<float>(h->stream, (int)h->lv[0].N, h->Ainv0, (const float*)g, (float*)z, nrhs(h));
   NDMG_CK_LAUNCH();
   return NDMG_OK;
 }
@@ -736,7 +877,7 @@ int ndmg_solve_host(ndmg_t* h, const double* f_host, double* u_host, double tol,
                     double* relres) {
   if (!h) return NDMG_INVALID_ARG;
   if (!f_host || !u_host) return fail(h, NDMG_INVALID_ARG, "null host buffer");
-  const int64_t N = h->lv[h->K].N;
+  const int64_t N = h->lv[h->K].N * nrhs(h);
   double* f = h->w64[4];
   double* u = h->w64[5];
   NDMG_CK(cudaMemcpyAsync(f, f_host, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream));
@@ -753,20 +894,26 @@ int ndmg_vcycle_iterate(ndmg_t* h, const double* f, double* u, double tol, int32
   if (!h) return NDMG_INVALID_ARG;
   int st;
   if ((st = check_ptrs(h, {f, u}))) return st;
-  const int K = h->K;
+  const int K = h->K, R = nrhs(h);
   const int64_t N = h->lv[K].N;
   double* r = h->w64[0];
-  double ff, rr, dum;
-  if ((st = dot2<double>(h, N, f, f, (const double*)nullptr, (const double*)nullptr, &ff, &dum)) != NDMG_OK) return st;
-  const double nf = std::sqrt(ff) > 0 ? std::sqrt(ff) : 1.0;
-  int c = 0;
-  for (;; ++c) {
+  std::vector<double> ff, rr;
+  if ((st = dot2<double>(h, N, f, f, (const double*)nullptr, (const double*)nullptr, ff, nullptr)) != NDMG_OK)
+    return st;
+  for (int c = 0;; ++c) {
     op_residual<double>(h, K, f, u, r);
-    if ((st = dot2<double>(h, N, r, r, (const double*)nullptr, (const double*)nullptr, &rr, &dum)) != NDMG_OK) return st;
-    if (relres) *relres = std::sqrt(rr) / nf;
+    if ((st = dot2<double>(h, N, r, r, (const double*)nullptr, (const double*)nullptr, rr, nullptr)) != NDMG_OK)
+      return st;
+    double worst = 0.0;
+    for (int i = 0; i < R; ++i) {
+      const double nf = std::sqrt(ff[i]) > 0 ? std::sqrt(ff[i]) : 1.0;
+      const double rel = std::sqrt(rr[i]) / nf;
+      if (!std::isfinite(rel)) return fail(h, NDMG_BREAKDOWN, "non-finite residual");
+      worst = std::fmax(worst, rel);
+    }
+    if (relres) *relres = worst;
     if (cycles) *cycles = c;
-    if (!std::isfinite(rr)) return fail(h, NDMG_BREAKDOWN, "non-finite residual");
-    if (std::sqrt(rr) <= tol * nf) return NDMG_OK;
+    if (worst <= tol) return NDMG_OK;
     if (c >= maxit) return fail(h, NDMG_NOT_CONVERGED, "V-cycle iteration reached maxit");
     op_vcycle<double>(h, K, f, u);
   }
@@ -777,17 +924,17 @@ int ndmg_grad_alpha(ndmg_t* h, const double* lambda, const double* u, double* ou
   int st;
   if ((st = check_ptrs(h, {lambda, u}))) return st;
   if (!out) return fail(h, NDMG_INVALID_ARG, "null output");
-  const int K = h->K;
+  const int K = h->K, R = nrhs(h);
   DevLevel& L = h->lv[K];
   double* Ku = h->w64[3];
   {
-    Span sp(h, NDMG_K_STENCIL, 16.0 * L.N);
-    launch_stencil<double>(h->stream, h->sm_count, L.n, L.h, 0.0, u, (const double*)nullptr, Ku);
+    Span sp(h, NDMG_K_STENCIL, 16.0 * L.N * R);
+    launch_stencil<double>(h->stream, h->sm_count, L.n, L.h, 0.0, u, (const double*)nullptr, Ku, R);
   }
-  double v, dum;
-  if ((st = dot2<double>(h, L.N, lambda, Ku, (const double*)nullptr, (const double*)nullptr, &v, &dum)) != NDMG_OK)
+  std::vector<double> v;
+  if ((st = dot2<double>(h, L.N, lambda, Ku, (const double*)nullptr, (const double*)nullptr, v, nullptr)) != NDMG_OK)
     return st;
-  *out = -v;
+  for (int i = 0; i < R; ++i) out[i] = -v[i];
   return NDMG_OK;
 }
 
@@ -796,10 +943,16 @@ int ndmg_dot(ndmg_t* h, int32_t level, int32_t dtype, const void* x, const void*
   int st;
   if ((st = check_level(h, level, false)) || (st = check_dtype(h, dtype)) || (st = check_ptrs(h, {x, y}))) return st;
   if (!out) return fail(h, NDMG_INVALID_ARG, "null output");
-  double dum;
   const int64_t N = h->lv[level].N;
-  if (dtype == NDMG_F64) return dot2<double>(h, N, (const double*)x, (const double*)y, (const double*)nullptr, (const double*)nullptr, out, &dum);
-  return dot2<float>(h, N, (const float*)x, (const float*)y, (const float*)nullptr, (const float*)nullptr, out, &dum);
+  std::vector<double> v;
+  if (dtype == NDMG_F64)
+    st = dot2<double>(h, N, (const double*)x, (const double*)y, (const double*)nullptr, (const double*)nullptr, v,
+                      nullptr);
+  else
+    st = dot2<float>(h, N, (const float*)x, (const float*)y, (const float*)nullptr, (const float*)nullptr, v, nullptr);
+  if (st != NDMG_OK) return st;
+  for (int i = 0; i < nrhs(h); ++i) out[i] = v[i];
+  return NDMG_OK;
 }
 
 int ndmg_trace_enable(ndmg_t* h, int32_t kernel_class, int32_t on) {

@@ -21,41 +21,6 @@ __device__ __forceinline__ int64_t off_z(int n, int i, int j, int k) {
 __device__ __forceinline__ bool in_seg(int p, int n) { return (unsigned)p < (unsigned)n; }
 __device__ __forceinline__ bool in_node(int p, int n) { return (unsigned)(p - 1) < (unsigned)(n - 1); }
 
-// value of an edge, zero on the boundary and outside the box
-template <typename T>
-__device__ __forceinline__ T UX(const T* __restrict__ u, int n, int i, int j, int k) {
-  return (in_seg(i, n) && in_node(j, n) && in_node(k, n)) ? __ldg(u + off_x(n, i, j, k)) : T(0);
-}
-template <typename T>
-__device__ __forceinline__ T UY(const T* __restrict__ u, int n, int i, int j, int k) {
-  return (in_node(i, n) && in_seg(j, n) && in_node(k, n)) ? __ldg(u + off_y(n, i, j, k)) : T(0);
-}
-template <typename T>
-__device__ __forceinline__ T UZ(const T* __restrict__ u, int n, int i, int j, int k) {
-  return (in_node(i, n) && in_node(j, n) && in_seg(k, n)) ? __ldg(u + off_z(n, i, j, k)) : T(0);
-}
-
-// decode a per-direction offset into lattice coordinates
-__device__ __forceinline__ void decode(int d, int n, int64_t loc, int& i, int& j, int& k) {
-  const int n1 = n - 1;
-  if (d == 0) {
-    i = (int)(loc % n);
-    int64_t t = loc / n;
-    j = (int)(t % n1) + 1;
-    k = (int)(t / n1) + 1;
-  } else if (d == 1) {
-    i = (int)(loc % n1) + 1;
-    int64_t t = loc / n1;
-    j = (int)(t % n);
-    k = (int)(t / n) + 1;
-  } else {
-    i = (int)(loc % n1) + 1;
-    int64_t t = loc / n1;
-    j = (int)(t % n1) + 1;
-    k = (int)(t / n1);
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Operator apply.  A = alpha K + beta M with K = h C^t Mf C: C is the integer
 // edge->face circulation matrix, Mf the face mass along the face normal
@@ -67,83 +32,6 @@ __device__ __forceinline__ void decode(int d, int n, int64_t loc, int& i, int& j
 //   cy(i,j,k) = ux(i,j,k+1) - ux(i,j,k) - uz(i+1,j,k) + uz(i,j,k)
 //   cz(i,j,k) = uy(i+1,j,k) - uy(i,j,k) - ux(i,j+1,k) + ux(i,j,k)
 // ---------------------------------------------------------------------------
-template <typename T>
-struct Fields {
-  const T* __restrict__ ux;
-  const T* __restrict__ uy;
-  const T* __restrict__ uz;
-  int n;
-  __device__ __forceinline__ T cx(int i, int j, int k) const {
-    return UZ(uz, n, i, j + 1, k) - UZ(uz, n, i, j, k) - UY(uy, n, i, j, k + 1) + UY(uy, n, i, j, k);
-  }
-  __device__ __forceinline__ T cy(int i, int j, int k) const {
-    return UX(ux, n, i, j, k + 1) - UX(ux, n, i, j, k) - UZ(uz, n, i + 1, j, k) + UZ(uz, n, i, j, k);
-  }
-  __device__ __forceinline__ T cz(int i, int j, int k) const {
-    return UY(uy, n, i + 1, j, k) - UY(uy, n, i, j, k) - UX(ux, n, i, j + 1, k) + UX(ux, n, i, j, k);
-  }
-  // face mass along the normal
-  __device__ __forceinline__ T Xf(int i, int j, int k) const {
-    return T(1.0 / 6.0) * (cx(i - 1, j, k) + cx(i + 1, j, k)) + T(2.0 / 3.0) * cx(i, j, k);
-  }
-  __device__ __forceinline__ T Yf(int i, int j, int k) const {
-    return T(1.0 / 6.0) * (cy(i, j - 1, k) + cy(i, j + 1, k)) + T(2.0 / 3.0) * cy(i, j, k);
-  }
-  __device__ __forceinline__ T Zf(int i, int j, int k) const {
-    return T(1.0 / 6.0) * (cz(i, j, k - 1) + cz(i, j, k + 1)) + T(2.0 / 3.0) * cz(i, j, k);
-  }
-};
-
-template <typename T>
-__device__ __forceinline__ T mass3x3(T m1, T c, T p1) {
-  return T(1.0 / 6.0) * (m1 + p1) + T(2.0 / 3.0) * c;
-}
-
-template <typename T>
-__device__ __forceinline__ T apply_edge(const Fields<T>& F, int d, int i, int j, int k, T cK, T cM) {
-  const int n = F.n;
-  T kv, mv;
-  if (d == 0) {
-    kv = -F.Yf(i, j, k) + F.Yf(i, j, k - 1) + F.Zf(i, j, k) - F.Zf(i, j - 1, k);
-    T r[3];
-#pragma unroll
-    for (int b = -1; b <= 1; ++b)
-      r[b + 1] = mass3x3(UX(F.ux, n, i, j - 1, k + b), UX(F.ux, n, i, j, k + b), UX(F.ux, n, i, j + 1, k + b));
-    mv = mass3x3(r[0], r[1], r[2]);
-  } else if (d == 1) {
-    kv = -F.Zf(i, j, k) + F.Zf(i - 1, j, k) + F.Xf(i, j, k) - F.Xf(i, j, k - 1);
-    T r[3];
-#pragma unroll
-    for (int b = -1; b <= 1; ++b)
-      r[b + 1] = mass3x3(UY(F.uy, n, i - 1, j, k + b), UY(F.uy, n, i, j, k + b), UY(F.uy, n, i + 1, j, k + b));
-    mv = mass3x3(r[0], r[1], r[2]);
-  } else {
-    kv = -F.Xf(i, j, k) + F.Xf(i, j - 1, k) + F.Yf(i, j, k) - F.Yf(i - 1, j, k);
-    T r[3];
-#pragma unroll
-    for (int b = -1; b <= 1; ++b)
-      r[b + 1] = mass3x3(UZ(F.uz, n, i - 1, j + b, k), UZ(F.uz, n, i, j + b, k), UZ(F.uz, n, i + 1, j + b, k));
-    mv = mass3x3(r[0], r[1], r[2]);
-  }
-  return cK * kv + cM * mv;
-}
-
-// y = A u (g == nullptr) or y = g - A u
-template <typename T>
-__global__ void __launch_bounds__(256) k_stencil(int n, T cK, T cM, const T* __restrict__ u,
-                                                 const T* __restrict__ g, T* __restrict__ y) {
-  const int64_t N3 = (int64_t)n * (n - 1) * (n - 1);
-  Fields<T> F{u, u + N3, u + 2 * N3, n};
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < 3 * N3;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int d = (int)(e / N3);
-    int i, j, k;
-    decode(d, n, e - d * N3, i, j, k);
-    const T v = apply_edge(F, d, i, j, k, cK, cM);
-    y[e] = g ? g[e] - v : v;
-  }
-}
-
 // Tiled variant: one CTA owns TX x TY x TZ cells (the edges whose lowest node
 // is in the tile, all three directions).  u is staged once on the tile plus a
 // one-cell halo and g on the tile, all with asynchronous copies (zero fill
@@ -181,46 +69,75 @@ __global__ void __launch_bounds__(kTX * kTY) k_stencil_tiled(int n, T cK, T cM, 
   T* Cz = Cy + kE3;
   T* G = Cz + kE3;  // 3 x kT3 (only when g != nullptr)
   const int64_t N3 = (int64_t)n * (n - 1) * (n - 1);
-  const int i0 = blockIdx.x * kTX, j0 = blockIdx.y * kTY, k0 = blockIdx.z * kTZ;
+  // grid z = (k tiles) x (right-hand sides); each right-hand side is a
+  // contiguous canonical vector
+  const int nzt = (n + kTZ - 1) / kTZ;
+  const int rhs = blockIdx.z / nzt;
+  u += (int64_t)rhs * 3 * N3;
+  y += (int64_t)rhs * 3 * N3;
+  if (g) g += (int64_t)rhs * 3 * N3;
+  const int i0 = blockIdx.x * kTX, j0 = blockIdx.y * kTY, k0 = (blockIdx.z - rhs * nzt) * kTZ;
   const int tid = threadIdx.y * kTX + threadIdx.x;
   const T* ux = u;
   const T* uy = u + N3;
   const T* uz = u + 2 * N3;
-  // 1. stage u on [i0-1, i0+TX] x [j0-1, j0+TY] x [k0-1, k0+TZ] and g on the tile
-  for (int q = tid; q < kE3; q += kTX * kTY) {
-    const int a = q % kEX, b = (q / kEX) % kEY, c = q / (kEX * kEY);
-    const int i = i0 + a - 1, j = j0 + b - 1, k = k0 + c - 1;
-    const bool vx = in_seg(i, n) && in_node(j, n) && in_node(k, n);
-    const bool vy = in_node(i, n) && in_seg(j, n) && in_node(k, n);
-    const bool vz = in_node(i, n) && in_node(j, n) && in_seg(k, n);
-    cp_async_elem(Ux + q, ux + (vx ? off_x(n, i, j, k) : 0), vx, u);
-    cp_async_elem(Uy + q, uy + (vy ? off_y(n, i, j, k) : 0), vy, u);
-    cp_async_elem(Uz + q, uz + (vz ? off_z(n, i, j, k) : 0), vz, u);
+  // 1. stage u on [i0-1, i0+TX] x [j0-1, j0+TY] x [k0-1, k0+TZ] and g on the
+  //    tile, one warp per row along i (row offsets computed once per row;
+  //    offsets within one direction fit in 32 bits for n <= 1290)
+  const int warp = tid >> 5, lane = tid & 31;
+  const int n1 = n - 1;
+  for (int row = warp; row < kEY * kEZ; row += kTY) {
+    const int b = row % kEY, c = row / kEY;
+    const int j = j0 + b - 1, k = k0 + c - 1;
+    const bool jn = in_node(j, n), js = in_seg(j, n), kn = in_node(k, n), ks = in_seg(k, n);
+    const uint32_t rx = ((uint32_t)(k - 1) * n1 + (j - 1)) * n;      // + i
+    const uint32_t ry = ((uint32_t)(k - 1) * n + j) * n1 - 1;        // + i
+    const uint32_t rz = ((uint32_t)k * n1 + (j - 1)) * n1 - 1;       // + i
+    for (int a = lane; a < kEX; a += 32) {
+      const int i = i0 + a - 1;
+      const int q = row * kEX + a;
+      const bool vx = in_seg(i, n) && jn && kn;
+      const bool vy = in_node(i, n) && js && kn;
+      const bool vz = in_node(i, n) && jn && ks;
+      cp_async_elem(Ux + q, ux + (vx ? rx + i : 0), vx, u);
+      cp_async_elem(Uy + q, uy + (vy ? ry + i : 0), vy, u);
+      cp_async_elem(Uz + q, uz + (vz ? rz + i : 0), vz, u);
+    }
   }
   if (g) {
-    for (int q = tid; q < kT3; q += kTX * kTY) {
-      const int a = q % kTX, b = (q / kTX) % kTY, c = q / (kTX * kTY);
-      const int i = i0 + a, j = j0 + b, k = k0 + c;
-      const bool vx = in_seg(i, n) && in_node(j, n) && in_node(k, n);
-      const bool vy = in_node(i, n) && in_seg(j, n) && in_node(k, n);
-      const bool vz = in_node(i, n) && in_node(j, n) && in_seg(k, n);
-      cp_async_elem(G + q, g + (vx ? off_x(n, i, j, k) : 0), vx, g);
-      cp_async_elem(G + kT3 + q, g + N3 + (vy ? off_y(n, i, j, k) : 0), vy, g);
-      cp_async_elem(G + 2 * kT3 + q, g + 2 * N3 + (vz ? off_z(n, i, j, k) : 0), vz, g);
+    for (int row = warp; row < kTY * kTZ; row += kTY) {
+      const int b = row % kTY, c = row / kTY;
+      const int j = j0 + b, k = k0 + c;
+      const int i = i0 + lane;
+      const int q = row * kTX + lane;
+      const bool jn = in_node(j, n), js = in_seg(j, n), kn = in_node(k, n), ks = in_seg(k, n);
+      const bool vx = in_seg(i, n) && jn && kn;
+      const bool vy = in_node(i, n) && js && kn;
+      const bool vz = in_node(i, n) && jn && ks;
+      const uint32_t ox = vx ? ((uint32_t)(k - 1) * n1 + (j - 1)) * n + i : 0;
+      const uint32_t oy = vy ? ((uint32_t)(k - 1) * n + j) * n1 + i - 1 : 0;
+      const uint32_t oz = vz ? ((uint32_t)k * n1 + (j - 1)) * n1 + i - 1 : 0;
+      cp_async_elem(G + q, g + ox, vx, g);
+      cp_async_elem(G + kT3 + q, g + N3 + oy, vy, g);
+      cp_async_elem(G + 2 * kT3 + q, g + 2 * N3 + oz, vz, g);
     }
   }
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
   __syncthreads();
-  // 2. face circulations wherever their four edges are staged
-  for (int q = tid; q < kE3; q += kTX * kTY) {
-    const int a = q % kEX, b = (q / kEX) % kEY, c = q / (kEX * kEY);
-    const bool ha = a + 1 < kEX, hb = b + 1 < kEY, hc = c + 1 < kEZ;
-    // cx(i,j,k) = uz(i,j+1,k) - uz(i,j,k) - uy(i,j,k+1) + uy(i,j,k)
-    Cx[q] = (hb && hc) ? Uz[eidx(a, b + 1, c)] - Uz[q] - Uy[eidx(a, b, c + 1)] + Uy[q] : T(0);
-    // cy(i,j,k) = ux(i,j,k+1) - ux(i,j,k) - uz(i+1,j,k) + uz(i,j,k)
-    Cy[q] = (ha && hc) ? Ux[eidx(a, b, c + 1)] - Ux[q] - Uz[eidx(a + 1, b, c)] + Uz[q] : T(0);
-    // cz(i,j,k) = uy(i+1,j,k) - uy(i,j,k) - ux(i,j+1,k) + ux(i,j,k)
-    Cz[q] = (ha && hb) ? Uy[eidx(a + 1, b, c)] - Uy[q] - Ux[eidx(a, b + 1, c)] + Ux[q] : T(0);
+  // 2. face circulations wherever their four edges are staged (row-wise)
+  for (int row = warp; row < kEY * kEZ; row += kTY) {
+    const int b = row % kEY, c = row / kEY;
+    const bool hb = b + 1 < kEY, hc = c + 1 < kEZ;
+    for (int a = lane; a < kEX; a += 32) {
+      const int q = row * kEX + a;
+      const bool ha = a + 1 < kEX;
+      // cx(i,j,k) = uz(i,j+1,k) - uz(i,j,k) - uy(i,j,k+1) + uy(i,j,k)
+      Cx[q] = (hb && hc) ? Uz[q + kEX] - Uz[q] - Uy[q + kEX * kEY] + Uy[q] : T(0);
+      // cy(i,j,k) = ux(i,j,k+1) - ux(i,j,k) - uz(i+1,j,k) + uz(i,j,k)
+      Cy[q] = (ha && hc) ? Ux[q + kEX * kEY] - Ux[q] - Uz[q + 1] + Uz[q] : T(0);
+      // cz(i,j,k) = uy(i+1,j,k) - uy(i,j,k) - ux(i,j+1,k) + ux(i,j,k)
+      Cz[q] = (ha && hb) ? Uy[q + 1] - Uy[q] - Ux[q + kEX] + Ux[q] : T(0);
+    }
   }
   __syncthreads();
   // 3. outputs: thread (tx, ty) walks its column over the tile's k range,
@@ -295,10 +212,13 @@ __global__ void __launch_bounds__(kTX * kTY) k_stencil_tiled(int n, T cK, T cM, 
 template <typename T>
 __global__ void __launch_bounds__(256) k_restrict(int nf, const T* __restrict__ rf, T* __restrict__ gc) {
   const int nc = nf / 2;
-  const int I = blockIdx.x * 32 + threadIdx.x, J = blockIdx.y * 8 + threadIdx.y, K = blockIdx.z;
+  const int rhs = blockIdx.z / nc;
+  const int I = blockIdx.x * 32 + threadIdx.x, J = blockIdx.y * 8 + threadIdx.y, K = blockIdx.z - rhs * nc;
   if (I >= nc || J >= nc) return;
   const int64_t N3c = (int64_t)nc * (nc - 1) * (nc - 1);
   const int64_t N3f = (int64_t)nf * (nf - 1) * (nf - 1);
+  rf += (int64_t)rhs * 3 * N3f;
+  gc += (int64_t)rhs * 3 * N3c;
   const T w[3] = {T(0.5), T(1), T(0.5)};
   // coarse x-edge (I, J, K): fine x-edges 2I+a, 2J+b, 2K+c with weight w_b w_c
   if (in_node(J, nc) && in_node(K, nc)) {
@@ -352,10 +272,13 @@ __device__ __forceinline__ int hat(int p, int (&C)[2], T (&w)[2]) {
 template <typename T>
 __global__ void __launch_bounds__(256) k_prolong_add(int nf, const T* __restrict__ zc, T* __restrict__ zf) {
   const int nc = nf / 2;
-  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+  const int rhs = blockIdx.z / nf;
+  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z - rhs * nf;
   if (i >= nf || j >= nf) return;
   const int64_t N3c = (int64_t)nc * (nc - 1) * (nc - 1);
   const int64_t N3f = (int64_t)nf * (nf - 1) * (nf - 1);
+  zc += (int64_t)rhs * 3 * N3c;
+  zf += (int64_t)rhs * 3 * N3f;
   int A[2], B[2];
   T wa[2], wb[2];
   if (in_node(j, nf) && in_node(k, nf)) {  // x-edge: injection along x, hats in y and z
@@ -402,6 +325,9 @@ __global__ void __launch_bounds__(256) k_bubble(int n, const T* __restrict__ Ain
                                                 T* __restrict__ z) {
   const int nc = n / 2;
   const int64_t NT = (int64_t)nc * nc * nc;
+  const int64_t N3 = (int64_t)n * (n - 1) * (n - 1);
+  r += (int64_t)blockIdx.y * 3 * N3;
+  z += (int64_t)blockIdx.y * 3 * N3;
   __shared__ T As[36];
   if (threadIdx.x < 36) As[threadIdx.x] = Ainv[threadIdx.x];
   __syncthreads();
@@ -453,6 +379,9 @@ __global__ void __launch_bounds__(128) k_vertex_dense(int n, const T* __restrict
   T* Rs = Ds + 108 * 108;                          // 108*PB
   const int nc = n / 2, nv = nc - 1;
   const int64_t NP = (int64_t)nv * nv * nv;
+  const int64_t N3 = (int64_t)n * (n - 1) * (n - 1);
+  r += (int64_t)blockIdx.y * 3 * N3;
+  z += (int64_t)blockIdx.y * 3 * N3;
   for (int q = threadIdx.x; q < 108 * 108; q += blockDim.x) Ds[q] = D[q];
   for (int64_t base = (int64_t)blockIdx.x * PB; base < NP; base += (int64_t)gridDim.x * PB) {
     __syncthreads();
@@ -496,6 +425,8 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_coarse(int N0, const double* __restrict__ Ainv, const T* __restrict__ g,
                                                 T* __restrict__ z) {
   extern __shared__ double gs[];
+  g += (int64_t)blockIdx.x * N0;
+  z += (int64_t)blockIdx.x * N0;
   for (int i = threadIdx.x; i < N0; i += blockDim.x) gs[i] = (double)g[i];
   __syncthreads();
   for (int i = threadIdx.x; i < N0; i += blockDim.x) {
@@ -536,61 +467,80 @@ __device__ __forceinline__ void block_sum_store(double (&v)[NV], double* out) {
   }
 }
 
-// partial[b*2 + {0,1}] = block sums of x.y and (optionally) x2.y2
+// Batched BLAS-1: grid y (or x for the finishing kernel) is the right-hand
+// side; every right-hand side is a contiguous vector of N entries; scalars
+// come from per-right-hand-side device arrays.
+// partial[(rhs * gridDim.x + b) * 2 + {0,1}] = block sums of x.y and x2.y2
 template <typename T>
 __global__ void __launch_bounds__(256) k_dot2(int64_t N, const T* __restrict__ x, const T* __restrict__ y,
                                               const T* __restrict__ x2, const T* __restrict__ y2,
                                               double* __restrict__ partial) {
+  const int64_t off = (int64_t)blockIdx.y * N;
   double v[2] = {0.0, 0.0};
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
-    v[0] += (double)x[e] * (double)y[e];
-    if (x2) v[1] += (double)x2[e] * (double)y2[e];
+    v[0] += (double)x[off + e] * (double)y[off + e];
+    if (x2) v[1] += (double)x2[off + e] * (double)y2[off + e];
   }
-  block_sum_store<2>(v, partial + 2 * blockIdx.x);
+  block_sum_store<2>(v, partial + 2 * ((int64_t)blockIdx.y * gridDim.x + blockIdx.x));
 }
 
 __global__ void k_finish2(int nb, const double* __restrict__ partial, double* __restrict__ out) {
+  partial += 2 * (int64_t)blockIdx.x * nb;
   double v[2] = {0.0, 0.0};
   for (int b = threadIdx.x; b < nb; b += blockDim.x) {
     v[0] += partial[2 * b];
     v[1] += partial[2 * b + 1];
   }
-  block_sum_store<2>(v, out);
+  block_sum_store<2>(v, out + 2 * blockIdx.x);
 }
 
-// y = a x + b y
+// y = a x + b y with (a, b) = ab[2 rhs], ab[2 rhs + 1]
 template <typename T>
-__global__ void __launch_bounds__(256) k_axpby(int64_t N, double a, const T* __restrict__ x, double b, T* __restrict__ y) {
+__global__ void __launch_bounds__(256) k_axpby(int64_t N, const double* __restrict__ ab, const T* __restrict__ x,
+                                               T* __restrict__ y) {
+  const int64_t off = (int64_t)blockIdx.y * N;
+  const double a = ab[2 * blockIdx.y], b = ab[2 * blockIdx.y + 1];
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x)
-    y[e] = (T)(a * (double)x[e] + b * (double)y[e]);
+    y[off + e] = (T)(a * (double)x[off + e] + b * (double)y[off + e]);
 }
 
-// u += a p ; r -= a q
+// u += a p ; r -= a q with a = alpha[rhs]
 template <typename T>
-__global__ void __launch_bounds__(256) k_cg_update(int64_t N, double a, const T* __restrict__ p, const T* __restrict__ q,
-                                                   T* __restrict__ u, T* __restrict__ r) {
+__global__ void __launch_bounds__(256) k_cg_update(int64_t N, const double* __restrict__ alpha, const T* __restrict__ p,
+                                                   const T* __restrict__ q, T* __restrict__ u, T* __restrict__ r) {
+  const int64_t off = (int64_t)blockIdx.y * N;
+  const double a = alpha[blockIdx.y];
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
-    u[e] = (T)((double)u[e] + a * (double)p[e]);
-    r[e] = (T)((double)r[e] - a * (double)q[e]);
+    u[off + e] = (T)((double)u[off + e] + a * (double)p[off + e]);
+    r[off + e] = (T)((double)r[off + e] - a * (double)q[off + e]);
   }
 }
 
-// dst (float) = s * src (double)
-__global__ void __launch_bounds__(256) k_to_f32(int64_t N, double s, const double* __restrict__ src, float* __restrict__ dst) {
+// dst (float) = s * src (double), s = sc[rhs]
+__global__ void __launch_bounds__(256) k_to_f32(int64_t N, const double* __restrict__ sc, const double* __restrict__ src,
+                                                float* __restrict__ dst) {
+  const int64_t off = (int64_t)blockIdx.y * N;
+  const double s = sc[blockIdx.y];
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x)
-    dst[e] = (float)(s * src[e]);
+    dst[off + e] = (float)(s * src[off + e]);
 }
 
 // dst (double) = s * src (float)
-__global__ void __launch_bounds__(256) k_from_f32(int64_t N, double s, const float* __restrict__ src, double* __restrict__ dst) {
+__global__ void __launch_bounds__(256) k_from_f32(int64_t N, const double* __restrict__ sc, const float* __restrict__ src,
+                                                  double* __restrict__ dst) {
+  const int64_t off = (int64_t)blockIdx.y * N;
+  const double s = sc[blockIdx.y];
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x)
-    dst[e] = s * (double)src[e];
+    dst[off + e] = s * (double)src[off + e];
 }
 
 // dst (double) += s * src (float)
-__global__ void __launch_bounds__(256) k_add_f32(int64_t N, double s, const float* __restrict__ src, double* __restrict__ dst) {
+__global__ void __launch_bounds__(256) k_add_f32(int64_t N, const double* __restrict__ sc, const float* __restrict__ src,
+                                                 double* __restrict__ dst) {
+  const int64_t off = (int64_t)blockIdx.y * N;
+  const double s = sc[blockIdx.y];
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x)
-    dst[e] += s * (double)src[e];
+    dst[off + e] += s * (double)src[off + e];
 }
 
 // ---------------------------------------------------------------------------
@@ -613,38 +563,30 @@ cudaError_t prepare_stencil() {
 }
 
 template <typename T>
-void launch_stencil(cudaStream_t s, int sm, int n, double cK, double cM, const T* u, const T* g, T* y) {
+void launch_stencil(cudaStream_t s, int sm, int n, double cK, double cM, const T* u, const T* g, T* y, int R) {
   const int64_t N = 3LL * n * (n - 1) * (n - 1);
   if (N == 0) return;
   (void)sm;
-  dim3 grid((n + kTX - 1) / kTX, (n + kTY - 1) / kTY, (n + kTZ - 1) / kTZ);
+  dim3 grid((n + kTX - 1) / kTX, (n + kTY - 1) / kTY, ((n + kTZ - 1) / kTZ) * R);
   k_stencil_tiled<T><<<grid, dim3(kTX, kTY), stencil_smem<T>(), s>>>(n, (T)cK, (T)cM, u, g, y);
 }
 
-// reference-style variant kept for the tests: one thread per edge, loads through L1
 template <typename T>
-void launch_stencil_simple(cudaStream_t s, int sm, int n, double cK, double cM, const T* u, const T* g, T* y) {
-  const int64_t N = 3LL * n * (n - 1) * (n - 1);
-  if (N == 0) return;
-  k_stencil<T><<<grid_for(N, sm, 16), 256, 0, s>>>(n, (T)cK, (T)cM, u, g, y);
-}
-
-template <typename T>
-void launch_restrict(cudaStream_t s, int, int nf, const T* rf, T* gc) {
+void launch_restrict(cudaStream_t s, int, int nf, const T* rf, T* gc, int R) {
   const int nc = nf / 2;
   if (nc < 2) return;
-  k_restrict<T><<<dim3((nc + 31) / 32, (nc + 7) / 8, nc), dim3(32, 8), 0, s>>>(nf, rf, gc);
+  k_restrict<T><<<dim3((nc + 31) / 32, (nc + 7) / 8, nc * R), dim3(32, 8), 0, s>>>(nf, rf, gc);
 }
 
 template <typename T>
-void launch_prolong_add(cudaStream_t s, int, int nf, const T* zc, T* zf) {
-  k_prolong_add<T><<<dim3((nf + 31) / 32, (nf + 7) / 8, nf), dim3(32, 8), 0, s>>>(nf, zc, zf);
+void launch_prolong_add(cudaStream_t s, int, int nf, const T* zc, T* zf, int R) {
+  k_prolong_add<T><<<dim3((nf + 31) / 32, (nf + 7) / 8, nf * R), dim3(32, 8), 0, s>>>(nf, zc, zf);
 }
 
 template <typename T>
-void launch_bubble(cudaStream_t s, int sm, int n, const T* Ainv, double eta, const T* r, T* z) {
+void launch_bubble(cudaStream_t s, int sm, int n, const T* Ainv, double eta, const T* r, T* z, int R) {
   const int64_t nc = n / 2;
-  k_bubble<T><<<grid_for(nc * nc * nc, sm, 16), 256, 0, s>>>(n, Ainv, (T)eta, r, z);
+  k_bubble<T><<<dim3(grid_for(nc * nc * nc, sm, 16), R), 256, 0, s>>>(n, Ainv, (T)eta, r, z);
 }
 
 constexpr int kPB64 = 8;
@@ -663,7 +605,7 @@ cudaError_t prepare_vertex_dense() {
 }
 
 template <typename T>
-void launch_vertex_dense(cudaStream_t s, int sm, int n, const T* D, double eta, const T* r, T* z) {
+void launch_vertex_dense(cudaStream_t s, int sm, int n, const T* D, double eta, const T* r, T* z, int R) {
   const int64_t nv = n / 2 - 1;
   const int64_t NP = nv * nv * nv;
   if (NP <= 0) return;
@@ -671,58 +613,62 @@ void launch_vertex_dense(cudaStream_t s, int sm, int n, const T* D, double eta, 
   int64_t blocks = (NP + PB - 1) / PB;
   const int64_t cap = (int64_t)sm * 2;
   if (blocks > cap) blocks = cap;
-  k_vertex_dense<T, PB><<<(int)blocks, 128, vertex_dense_smem<T>(), s>>>(n, D, (T)eta, r, z);
+  k_vertex_dense<T, PB><<<dim3((int)blocks, R), 128, vertex_dense_smem<T>(), s>>>(n, D, (T)eta, r, z);
 }
 
 template <typename T>
-void launch_coarse(cudaStream_t s, int N0, const double* Ainv, const T* g, T* z) {
-  k_coarse<T><<<1, 256, sizeof(double) * N0, s>>>(N0, Ainv, g, z);
+void launch_coarse(cudaStream_t s, int N0, const double* Ainv, const T* g, T* z, int R) {
+  k_coarse<T><<<R, 256, sizeof(double) * N0, s>>>(N0, Ainv, g, z);
 }
 
 int reduction_blocks(int sm) { return sm * 4; }
 
 template <typename T>
 void launch_dot2(cudaStream_t s, int sm, int64_t N, const T* x, const T* y, const T* x2, const T* y2, double* partial,
-                 double* out) {
+                 double* out, int R) {
   const int nb = reduction_blocks(sm);
-  k_dot2<T><<<nb, 256, 0, s>>>(N, x, y, x2, y2, partial);
-  k_finish2<<<1, 256, 0, s>>>(nb, partial, out);
+  k_dot2<T><<<dim3(nb, R), 256, 0, s>>>(N, x, y, x2, y2, partial);
+  k_finish2<<<R, 256, 0, s>>>(nb, partial, out);
+}
+
+static inline dim3 blas_grid(int64_t N, int sm, int R) {
+  const int per = R > 1 ? 2 : 8;
+  return dim3(grid_for(N, sm, per), R);
 }
 
 template <typename T>
-void launch_axpby(cudaStream_t s, int sm, int64_t N, double a, const T* x, double b, T* y) {
-  k_axpby<T><<<grid_for(N, sm, 8), 256, 0, s>>>(N, a, x, b, y);
+void launch_axpby(cudaStream_t s, int sm, int64_t N, const double* ab, const T* x, T* y, int R) {
+  k_axpby<T><<<blas_grid(N, sm, R), 256, 0, s>>>(N, ab, x, y);
 }
 
 template <typename T>
-void launch_cg_update(cudaStream_t s, int sm, int64_t N, double a, const T* p, const T* q, T* u, T* r) {
-  k_cg_update<T><<<grid_for(N, sm, 8), 256, 0, s>>>(N, a, p, q, u, r);
+void launch_cg_update(cudaStream_t s, int sm, int64_t N, const double* alpha, const T* p, const T* q, T* u, T* r, int R) {
+  k_cg_update<T><<<blas_grid(N, sm, R), 256, 0, s>>>(N, alpha, p, q, u, r);
 }
 
-void launch_to_f32(cudaStream_t s, int sm, int64_t N, double sc, const double* src, float* dst) {
-  k_to_f32<<<grid_for(N, sm, 8), 256, 0, s>>>(N, sc, src, dst);
+void launch_to_f32(cudaStream_t s, int sm, int64_t N, const double* sc, const double* src, float* dst, int R) {
+  k_to_f32<<<blas_grid(N, sm, R), 256, 0, s>>>(N, sc, src, dst);
 }
-void launch_from_f32(cudaStream_t s, int sm, int64_t N, double sc, const float* src, double* dst) {
-  k_from_f32<<<grid_for(N, sm, 8), 256, 0, s>>>(N, sc, src, dst);
+void launch_from_f32(cudaStream_t s, int sm, int64_t N, const double* sc, const float* src, double* dst, int R) {
+  k_from_f32<<<blas_grid(N, sm, R), 256, 0, s>>>(N, sc, src, dst);
 }
-void launch_add_f32(cudaStream_t s, int sm, int64_t N, double sc, const float* src, double* dst) {
-  k_add_f32<<<grid_for(N, sm, 8), 256, 0, s>>>(N, sc, src, dst);
+void launch_add_f32(cudaStream_t s, int sm, int64_t N, const double* sc, const float* src, double* dst, int R) {
+  k_add_f32<<<blas_grid(N, sm, R), 256, 0, s>>>(N, sc, src, dst);
 }
 
 #define NDMG_INST(T)                                                                                   \
-  template void launch_stencil<T>(cudaStream_t, int, int, double, double, const T*, const T*, T*);    \
-  template void launch_stencil_simple<T>(cudaStream_t, int, int, double, double, const T*, const T*, T*); \
+  template void launch_stencil<T>(cudaStream_t, int, int, double, double, const T*, const T*, T*, int); \
   template cudaError_t prepare_stencil<T>();                                                          \
-  template void launch_restrict<T>(cudaStream_t, int, int, const T*, T*);                             \
-  template void launch_prolong_add<T>(cudaStream_t, int, int, const T*, T*);                          \
-  template void launch_bubble<T>(cudaStream_t, int, int, const T*, double, const T*, T*);             \
+  template void launch_restrict<T>(cudaStream_t, int, int, const T*, T*, int);                        \
+  template void launch_prolong_add<T>(cudaStream_t, int, int, const T*, T*, int);                     \
+  template void launch_bubble<T>(cudaStream_t, int, int, const T*, double, const T*, T*, int);        \
   template cudaError_t prepare_vertex_dense<T>();                                                     \
-  template void launch_vertex_dense<T>(cudaStream_t, int, int, const T*, double, const T*, T*);       \
-  template void launch_coarse<T>(cudaStream_t, int, const double*, const T*, T*);                     \
+  template void launch_vertex_dense<T>(cudaStream_t, int, int, const T*, double, const T*, T*, int);  \
+  template void launch_coarse<T>(cudaStream_t, int, const double*, const T*, T*, int);                \
   template void launch_dot2<T>(cudaStream_t, int, int64_t, const T*, const T*, const T*, const T*,    \
-                               double*, double*);                                                     \
-  template void launch_axpby<T>(cudaStream_t, int, int64_t, double, const T*, double, T*);            \
-  template void launch_cg_update<T>(cudaStream_t, int, int64_t, double, const T*, const T*, T*, T*);
+                               double*, double*, int);                                                \
+  template void launch_axpby<T>(cudaStream_t, int, int64_t, const double*, const T*, T*, int);         \
+  template void launch_cg_update<T>(cudaStream_t, int, int64_t, const double*, const T*, const T*, T*, T*, int);
 NDMG_INST(double)
 NDMG_INST(float)
 

@@ -1,38 +1,37 @@
-// Launchers of the CUDA-core kernels (kernels.cu) and the tensor-core
-// vertex-patch kernel (tc_patch.cu).
+// Launchers of the CUDA-core kernels (kernels.cu).  R = right-hand sides in
+// the batch; every right-hand side is a contiguous canonical vector.
 #pragma once
 #include "ndmg_internal.h"
 
 namespace ndmg {
 
 template <typename T>
-void launch_stencil(cudaStream_t s, int sm, int n, double cK, double cM, const T* u, const T* g, T* y);
-template <typename T>
-void launch_stencil_simple(cudaStream_t s, int sm, int n, double cK, double cM, const T* u, const T* g, T* y);
+void launch_stencil(cudaStream_t s, int sm, int n, double cK, double cM, const T* u, const T* g, T* y, int R);
 template <typename T>
 cudaError_t prepare_stencil();
 template <typename T>
-void launch_restrict(cudaStream_t s, int sm, int nf, const T* rf, T* gc);
+void launch_restrict(cudaStream_t s, int sm, int nf, const T* rf, T* gc, int R);
 template <typename T>
-void launch_prolong_add(cudaStream_t s, int sm, int nf, const T* zc, T* zf);
+void launch_prolong_add(cudaStream_t s, int sm, int nf, const T* zc, T* zf, int R);
 template <typename T>
-void launch_bubble(cudaStream_t s, int sm, int n, const T* Ainv, double eta, const T* r, T* z);
+void launch_bubble(cudaStream_t s, int sm, int n, const T* Ainv, double eta, const T* r, T* z, int R);
 template <typename T>
 cudaError_t prepare_vertex_dense();
 template <typename T>
-void launch_vertex_dense(cudaStream_t s, int sm, int n, const T* D, double eta, const T* r, T* z);
+void launch_vertex_dense(cudaStream_t s, int sm, int n, const T* D, double eta, const T* r, T* z, int R);
 template <typename T>
-void launch_coarse(cudaStream_t s, int N0, const double* Ainv, const T* g, T* z);
+void launch_coarse(cudaStream_t s, int N0, const double* Ainv, const T* g, T* z, int R);
 int reduction_blocks(int sm);
 template <typename T>
 void launch_dot2(cudaStream_t s, int sm, int64_t N, const T* x, const T* y, const T* x2, const T* y2,
-                 double* partial, double* out);
+                 double* partial, double* out, int R);
 template <typename T>
-void launch_axpby(cudaStream_t s, int sm, int64_t N, double a, const T* x, double b, T* y);
+void launch_axpby(cudaStream_t s, int sm, int64_t N, const double* ab, const T* x, T* y, int R);
 template <typename T>
-void launch_cg_update(cudaStream_t s, int sm, int64_t N, double a, const T* p, const T* q, T* u, T* r);
-void launch_to_f32(cudaStream_t s, int sm, int64_t N, double sc, const double* src, float* dst);
-void launch_add_f32(cudaStream_t s, int sm, int64_t N, double sc, const float* src, double* dst);
-void launch_from_f32(cudaStream_t s, int sm, int64_t N, double sc, const float* src, double* dst);
+void launch_cg_update(cudaStream_t s, int sm, int64_t N, const double* alpha, const T* p, const T* q, T* u, T* r,
+                      int R);
+void launch_to_f32(cudaStream_t s, int sm, int64_t N, const double* sc, const double* src, float* dst, int R);
+void launch_from_f32(cudaStream_t s, int sm, int64_t N, const double* sc, const float* src, double* dst, int R);
+void launch_add_f32(cudaStream_t s, int sm, int64_t N, const double* sc, const float* src, double* dst, int R);
 
 }  // namespace ndmg

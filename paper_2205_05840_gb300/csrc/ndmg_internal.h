@@ -77,8 +77,11 @@ struct ndmg_handle {
   double *w64[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   float *w32[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   double* red = nullptr;                  // reduction scratch (partials + results)
-  double* red_host = nullptr;             // pinned mirror of the results
+  double* red_host = nullptr;             // pinned mirror of the results (2 per right-hand side)
+  double* coef = nullptr;                 // per-right-hand-side BLAS scalars (4 slots x 2R)
+  double* coef_host = nullptr;            // pinned staging of those scalars
   int* status = nullptr;                  // device status word (timeouts)
+  int* status_host = nullptr;             // pinned mirror of the status word
   std::string err;
   // tracing: per kernel class, event pairs recorded around launches
   bool trace_on[NDMG_K_COUNT] = {};

@@ -43,6 +43,10 @@ constexpr int kRN = kRE - 1;               // 11 interior node lines
 constexpr int kRegion = kRE * kRN * kRN;   // staged edges per direction
 constexpr int kOwn = 2 * kB;               // owned cells per side
 constexpr int kOwn3 = kOwn * kOwn * kOwn;  // owned edges per direction
+// accumulator layout (padded against shared-memory bank conflicts of the
+// patch scatter): slot(d, i, j, k) = d * kAccD + k * kAccK + j * kOwn + i
+constexpr int kAccK = 68, kAccD = 544;
+constexpr int kAccSize = 3 * kAccD;
 constexpr int kThreads = 256;
 constexpr uint32_t kTmemCols = 128;        // D: cols [0,64), then D': cols [0,112)
 
@@ -60,7 +64,8 @@ constexpr int OFF_TM = OFF_BAR + 16;
 constexpr int OFF_RED = OFF_TM + 16;
 constexpr int kSmem = OFF_RED + 32;
 static_assert(OFF_BAR % 8 == 0, "mbarrier alignment");
-static_assert(3 * kOwn3 * 4 <= 3 * kRegion * 4, "accumulator fits in the staged region");
+static_assert(kAccSize * 4 <= 3 * kRegion * 4 && kAccK >= kOwn * kOwn && kAccD >= kOwn * kAccK,
+              "accumulator fits in the staged region");
 static_assert(3 * (kSmem + 1024) <= 228 * 1024, "three CTAs per SM (228 KB, 1 KB reserved per CTA)");
 
 constexpr int kImgBytes = (kN1 * kK1 + kN2 * kK2) * 2;  // both W images
@@ -273,7 +278,7 @@ __device__ __forceinline__ void local_box(int l, int& d, int& i, int& j, int& k)
 // by the brick into the accumulator; owned coordinates are box + 2(a,b,c) - 2
 template <int CB>
 __device__ __forceinline__ void scatter16(float* ACC, const float (&v)[16], int a, int b, int c) {
-  const int pbase = 2 * a + 16 * b + 128 * c - (2 + 16 + 128);
+  const int pbase = 2 * a + 2 * kOwn * b + 2 * kAccK * c - (2 + 2 * kOwn + 2 * kAccK);
 #pragma unroll
   for (int t = 0; t < 16; ++t) {
     const int l = CB + t;
@@ -282,7 +287,7 @@ __device__ __forceinline__ void scatter16(float* ACC, const float (&v)[16], int 
       local_box(l, d, i, j, k);
       const int oi = i + 2 * a - 2, oj = j + 2 * b - 2, ok = k + 2 * c - 2;
       if ((unsigned)oi < (unsigned)kOwn && (unsigned)oj < (unsigned)kOwn && (unsigned)ok < (unsigned)kOwn)
-        atomicAdd(ACC + d * kOwn3 + (k * kOwn + j) * kOwn + i + pbase, v[t]);
+        atomicAdd(ACC + d * kAccD + k * kAccK + j * kOwn + i + pbase, v[t]);
     }
   }
 }
@@ -299,7 +304,15 @@ __global__ void __launch_bounds__(kThreads, 3)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nc = n / 2;
   const int nbr = (nc + kB - 1) / kB;
-  const int bx = blockIdx.x % nbr, by = (blockIdx.x / nbr) % nbr, bz = blockIdx.x / (nbr * nbr);
+  // grid = bricks x right-hand sides (each a contiguous canonical vector)
+  const int rhs = blockIdx.x / (nbr * nbr * nbr);
+  const int brick = blockIdx.x - rhs * nbr * nbr * nbr;
+  const int bx = brick % nbr, by = (brick / nbr) % nbr, bz = brick / (nbr * nbr);
+  {
+    const int64_t off = (int64_t)rhs * 3 * (int64_t)n * (n - 1) * (n - 1);
+    r += off;
+    z += off;
+  }
   const int I0 = bx * kB, J0 = by * kB, K0 = bz * kB;
 
   float* R = reinterpret_cast<float*>(smem + OFF_R);
@@ -424,7 +437,7 @@ __global__ void __launch_bounds__(kThreads, 3)
               idesc, kk > 0);
     mma_commit(bar0);
   }
-  for (int q = tid; q < 3 * kOwn3; q += kThreads) ACC[q] = 0.f;
+  for (int q = tid; q < kAccSize; q += kThreads) ACC[q] = 0.f;
   __syncthreads();
   if (tid < kB * kB * kB) {
     const int a = tid % kB, b = (tid / kB) % kB, c = tid / (kB * kB);
@@ -433,7 +446,7 @@ __global__ void __launch_bounds__(kThreads, 3)
     for (int t = 0; t < 6; ++t) {
       int d, p[3];
       bubble_edge(t, a, b, c, d, p);
-      ACC[d * kOwn3 + (p[2] * kOwn + p[1]) * kOwn + p[0]] += BUB[tid * 6 + t] * pre;
+      ACC[d * kAccD + p[2] * kAccK + p[1] * kOwn + p[0]] += BUB[tid * 6 + t] * pre;
     }
   }
   bool ok = mbar_wait(bar0, 0);
@@ -525,8 +538,12 @@ __global__ void __launch_bounds__(kThreads, 3)
       zv[t] = gi[t] >= 0 ? z[gi[t]] : 0.f;
     }
 #pragma unroll
-    for (int t = 0; t < kPer; ++t)
-      if (gi[t] >= 0) z[gi[t]] = zv[t] + sc * ACC[tid + t * kThreads];
+    for (int t = 0; t < kPer; ++t) {
+      const int q = tid + t * kThreads;
+      const int d = q / kOwn3, e = q - d * kOwn3;
+      const int slot = d * kAccD + (e / (kOwn * kOwn)) * kAccK + e % (kOwn * kOwn);
+      if (gi[t] >= 0) z[gi[t]] = zv[t] + sc * ACC[slot];
+    }
   }
   if (warp == 0) {
     fence_after();
@@ -578,11 +595,11 @@ cudaError_t prepare_tc_patch() {
 }
 
 void launch_tc_smoother(cudaStream_t s, int n, const void* Wimg, const float* AinvT, bool fp16, double eta,
-                        const float* r, float* z, int* status) {
+                        const float* r, float* z, int* status, int R) {
   const int nc = n / 2;
   if (nc < 1) return;
   const int nbr = (nc + kB - 1) / kB;
-  const int grid = nbr * nbr * nbr;
+  const int grid = nbr * nbr * nbr * R;
   if (fp16)
     k_tc_smoother<true><<<grid, kThreads, kSmem, s>>>(n, (const uint8_t*)Wimg, AinvT, (float)eta, r, z, status);
   else

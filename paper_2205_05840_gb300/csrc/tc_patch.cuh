@@ -14,6 +14,6 @@ cudaError_t prepare_tc_patch();
 // (AinvT: the 6x6 interior-space inverse, FP32).  On a device-side timeout
 // the kernel writes a nonzero code to *status.
 void launch_tc_smoother(cudaStream_t s, int n, const void* Wimg, const float* AinvT, bool fp16, double eta,
-                        const float* r, float* z, int* status);
+                        const float* r, float* z, int* status, int R);
 
 }  // namespace ndmg

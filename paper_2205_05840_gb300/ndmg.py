@@ -184,11 +184,12 @@ class Solver:
     def vcycle(self, g, z):
         self._check(_lib.ndmg_vcycle(self._h, _dtype_code(g), self._vec(g, -1), self._vec(z, -1, g.dtype)), "vcycle")
 
-    def dot(self, x, y, level: int = -1) -> float:
-        out = _d()
+    def dot(self, x, y, level: int = -1):
+        """x_r . y_r in FP64 (a float, or a list of nrhs floats for batches)."""
+        out = (_d * self.nrhs)()
         self._check(_lib.ndmg_dot(self._h, level, _dtype_code(x), self._vec(x, level), self._vec(y, level, x.dtype),
-                                  ctypes.byref(out)), "dot")
-        return out.value
+                                  out), "dot")
+        return out[0] if self.nrhs == 1 else list(out)
 
     # -- solvers ------------------------------------------------------------
     def solve(self, f, u, tol: float = 1e-8, maxit: int = 200, raise_on_fail: bool = True):
@@ -227,11 +228,12 @@ class Solver:
         self._check(st, "vcycle_iterate")
         return st, c.value, rr.value
 
-    def grad_alpha(self, lam, u) -> float:
-        out = _d()
+    def grad_alpha(self, lam, u):
+        """-lambda_r^T K u_r (a float, or a list of nrhs floats for batches)."""
+        out = (_d * self.nrhs)()
         self._check(_lib.ndmg_grad_alpha(self._h, self._vec(lam, -1, torch.float64), self._vec(u, -1, torch.float64),
-                                         ctypes.byref(out)), "grad_alpha")
-        return out.value
+                                         out), "grad_alpha")
+        return out[0] if self.nrhs == 1 else list(out)
 
     # -- tracing ------------------------------------------------------------
     def trace(self, kernel_class: int, on: bool = True):
