@@ -202,6 +202,24 @@ def run_reference(args):
 # --------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------
+def max_over_ranks(ms_total: float, world: int, device) -> float:
+    """Barrier, then the slowest rank's time (every rank gets it)."""
+    if world <= 1:
+        return ms_total
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms_total], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def whole_job_value(world: int, dofs: int, vcycles_per_step: float, steps: int, ms_total: float) -> float:
+    """DoF*cycles/s summed over all ranks: every rank solves its own
+    right-hand side, timed by the slowest rank."""
+    return world * dofs * vcycles_per_step * steps / (ms_total / 1e3)
+
+
 BATCH_RHS = 32
 BATCH_ALPHA = 1e-2 ** 2 / 4.0
 
@@ -309,12 +327,7 @@ def run_ours(args):
         torch.cuda.synchronize()
     l1, v1 = S.counters()
     ms = [a.elapsed_time(b) for a, b in ev]
-    ms_total = sum(ms)
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
-        dist.barrier()
+    ms_total = max_over_ranks(sum(ms), world, dev)
     kern = {}
     for c in classes:
         n_l, k_ms, units = S.trace_read(c)
@@ -323,7 +336,7 @@ def run_ours(args):
         kern[name] = {"launches": n_l, "ms": k_ms, "units": units}
     vcyc_per_step = (v1 - v0) / args.steps
     launches = l1 - l0
-    value = world * Nd * vcyc_per_step * args.steps / (ms_total / 1e3)
+    value = whole_job_value(world, Nd, vcyc_per_step, args.steps, ms_total)
 
     # roofline of the dominant kernel class
     import json as _json

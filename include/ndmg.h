@@ -60,7 +60,7 @@ typedef enum ndmg_dtype { NDMG_F64 = 0, NDMG_F32 = 1 } ndmg_dtype;
 /* Smoother of Sec. 3.2. */
 typedef enum ndmg_smoother {
   NDMG_SMOOTHER_VERTEX = 0, /* eq. (Preconditioner P), default eta 1/9 */
-  NDMG_SMOOTHER_EDGE = 1    /* eq. (Preconditioner E), default eta 1/13 (not yet built) */
+  NDMG_SMOOTHER_EDGE = 1    /* eq. (Preconditioner E), default eta 1/13; CUDA cores in every precision mode */
 } ndmg_smoother;
 
 /* Arithmetic of the V-cycle.  FP64: everything in double.  MIXED_BF16 /
@@ -82,7 +82,7 @@ typedef struct ndmg_opts {
   double alpha;       /* curl-curl coefficient, > 0 (eq. 1) */
   double beta;        /* mass coefficient, > 0 (1 in eq. 1; eps + sigma dt/2 in eq. Maxwell timestep) */
   int32_t smoother;   /* ndmg_smoother */
-  double eta;         /* damping factor; <= 0 selects the paper's value for the smoother */
+  double eta;         /* damping factor; <= 0 selects the paper's value (1/9 vertex, 1/13 edge) */
   int32_t m;          /* pre- and post-smoothing steps per level (Fig. 1), >= 1 */
   int32_t precision;  /* ndmg_precision */
   int32_t nrhs;       /* right-hand sides per call, >= 1 */

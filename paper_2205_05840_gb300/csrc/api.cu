@@ -103,6 +103,8 @@ const double* lv_Ainv(DevLevel& L, double*) { return L.AinvT64; }
 const float* lv_Ainv(DevLevel& L, float*) { return L.AinvT32; }
 const double* lv_D(DevLevel& L, double*) { return L.Dv64; }
 const float* lv_D(DevLevel& L, float*) { return L.Dv32; }
+const double* lv_De(DevLevel& L, double*) { return L.De64; }
+const float* lv_De(DevLevel& L, float*) { return L.De32; }
 
 bool mixed(const ndmg_t* h) {
   return h->o.precision == NDMG_PREC_MIXED_BF16 || h->o.precision == NDMG_PREC_MIXED_FP16;
@@ -127,7 +129,22 @@ void op_apply(ndmg_t* h, int k, const T* x, T* y) {
   launch_stencil<T>(h->stream, h->sm_count, L.n, L.cK, L.cM, x, (const T*)nullptr, y, nrhs(h));
 }
 
-// z += M_k^{-1} r (eta included), eq. (Preconditioner P)
+bool edge_smoother(const ndmg_t* h) { return h->o.smoother == NDMG_SMOOTHER_EDGE; }
+
+// sum_E J_E A_E^{-1} J_E^t r of eq. (Preconditioner E): one launch per
+// coarse-edge direction, each with its 42x42 operator
+template <typename T>
+void op_edge_terms(ndmg_t* h, int k, const T* De, const T* r, T* z) {
+  DevLevel& L = h->lv[k];
+  const int R = nrhs(h);
+  for (int d = 0; d < 3; ++d) {
+    const PatchFamily fam = edge_family(L.n, d);
+    Span sp(h, NDMG_K_PATCH, (double)fam.np[0] * fam.np[1] * fam.np[2] * 2.0 * 42 * 42 * R);
+    launch_patch_dense<T>(h->stream, h->sm_count, L.n, fam, De + d * 42 * 42, h->o.eta, r, z, R);
+  }
+}
+
+// z += M_k^{-1} r (eta included), eq. (Preconditioner P) or (Preconditioner E)
 template <typename T>
 void op_smoother(ndmg_t* h, int k, const T* r, T* z) {
   DevLevel& L = h->lv[k];
@@ -135,6 +152,10 @@ void op_smoother(ndmg_t* h, int k, const T* r, T* z) {
   {
     Span sp(h, NDMG_K_BUBBLE, bubble_bytes(L.n, sizeof(T)) * R);
     launch_bubble<T>(h->stream, h->sm_count, L.n, lv_Ainv(L, (T*)nullptr), h->o.eta, r, z, R);
+  }
+  if (edge_smoother(h)) {
+    op_edge_terms<T>(h, k, lv_De(L, (T*)nullptr), r, z);
+    return;
   }
   Span sp(h, NDMG_K_PATCH, num_patches(L.n) * 2.0 * 108 * 108 * R);  // dense 108x108 per patch
   launch_vertex_dense<T>(h->stream, h->sm_count, L.n, lv_D(L, (T*)nullptr), h->o.eta, r, z, R);
@@ -144,6 +165,14 @@ template <>
 void op_smoother<float>(ndmg_t* h, int k, const float* r, float* z) {
   DevLevel& L = h->lv[k];
   const int R = nrhs(h);
+  if (edge_smoother(h)) {  // the edge-based smoother runs on CUDA cores in every precision mode
+    {
+      Span sp(h, NDMG_K_BUBBLE, bubble_bytes(L.n, sizeof(float)) * R);
+      launch_bubble<float>(h->stream, h->sm_count, L.n, L.AinvT32, h->o.eta, r, z, R);
+    }
+    op_edge_terms<float>(h, k, L.De32, r, z);
+    return;
+  }
   if (mixed(h) && L.Wtc) {
     // one tensor-core kernel for both terms (Gram form: two 108x60 products
     // per patch; the 6x6 interior solves ride along).  Algorithmic bytes:
@@ -571,6 +600,7 @@ void free_handle(ndmg_t* h) {
     cudaFree(L.g64); cudaFree(L.z64); cudaFree(L.r64);
     cudaFree(L.g32); cudaFree(L.z32); cudaFree(L.r32);
     cudaFree(L.AinvT64); cudaFree(L.AinvT32); cudaFree(L.Dv64); cudaFree(L.Dv32);
+    cudaFree(L.De64); cudaFree(L.De32);
     cudaFree(L.Wtc);
   }
   cudaFree(h->Ainv0);
@@ -601,6 +631,10 @@ int build_operators(ndmg_t* h) {
       NDMG_CK(upload(&L.AinvT32, ops.AinvT));
       NDMG_CK(upload(&L.Dv64, ops.Dv));
       NDMG_CK(upload(&L.Dv32, ops.Dv));
+      std::vector<double> de;
+      for (int d = 0; d < 3; ++d) de.insert(de.end(), ops.De[d].begin(), ops.De[d].end());
+      NDMG_CK(upload(&L.De64, de));
+      NDMG_CK(upload(&L.De32, de));
       if (mixed(h)) {
         cudaError_t e = upload_tc_operand(&L.Wtc, ops.Wv, o.precision == NDMG_PREC_MIXED_FP16);
         if (e != cudaSuccess) return cuda_fail(h, e, "upload_tc_operand");
@@ -649,7 +683,7 @@ int ndmg_create(const ndmg_opts* o, ndmg_t** out) {
   if (o->n < 2 || o->n_coarsest < 2 || o->n < o->n_coarsest) return NDMG_INVALID_ARG;
   if (!(o->L > 0) || !(o->alpha > 0) || !(o->beta > 0) || o->m < 1 || o->nrhs < 1) return NDMG_INVALID_ARG;
   if (o->nrhs > 4096) return NDMG_INVALID_ARG;
-  if (o->smoother != NDMG_SMOOTHER_VERTEX) return NDMG_INVALID_ARG;
+  if (o->smoother != NDMG_SMOOTHER_VERTEX && o->smoother != NDMG_SMOOTHER_EDGE) return NDMG_INVALID_ARG;
   if (o->precision < NDMG_PREC_FP64 || o->precision > NDMG_PREC_FP32) return NDMG_INVALID_ARG;
   if (edges(o->n_coarsest) > 4096) return NDMG_INVALID_ARG;   // dense coarsest inverse
   // 32-bit edge offsets inside the tensor-core smoother: 3 n (n-1)^2 < 2^32
@@ -663,7 +697,7 @@ int ndmg_create(const ndmg_opts* o, ndmg_t** out) {
   ndmg_t* h = new (std::nothrow) ndmg_handle();
   if (!h) return NDMG_OUT_OF_MEMORY;
   h->o = *o;
-  if (!(h->o.eta > 0)) h->o.eta = 1.0 / 9.0;
+  if (!(h->o.eta > 0)) h->o.eta = h->o.smoother == NDMG_SMOOTHER_EDGE ? 1.0 / 13.0 : 1.0 / 9.0;
   h->stream = (cudaStream_t)o->stream;
   h->K = K;
   int dev = 0;

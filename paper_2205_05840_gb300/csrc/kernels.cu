@@ -354,65 +354,68 @@ __global__ void __launch_bounds__(256) k_bubble(int n, const T* __restrict__ Ain
   }
 }
 
-// Vertex patch local index l in [0,108) -> global edge, patch at coarse
-// vertex (I,J,K): the 4x4x4 box numbering with origin (2I-2, 2J-2, 2K-2).
-__device__ __forceinline__ int64_t patch_gidx(int n, int I, int J, int K, int l) {
-  int d, i, j, k;
-  if (l < 36) {
-    d = 0; i = l % 4; j = (l / 4) % 3 + 1; k = l / 12 + 1;
-  } else if (l < 72) {
-    l -= 36; d = 1; i = l % 3 + 1; j = (l / 3) % 4; k = l / 12 + 1;
-  } else {
-    l -= 72; d = 2; i = l % 3 + 1; j = (l / 3) % 3 + 1; k = l / 9;
-  }
-  return edge_gidx(n, d, 2 * I - 2 + i, 2 * J - 2 + j, 2 * K - 2 + k);
-}
-
-// Dense vertex-patch solve on CUDA cores: z += eta * D r_p per patch, D =
-// J_V A_V^{-1} J_V^t (108x108, symmetric) staged in shared memory, PB patches
-// per pass; overlapping patches accumulate with atomics.
+// Dense patch solves on CUDA cores: z += eta * D r_p for every patch of one
+// family, D = J_D A_D^{-1} J_D^t (nloc x nloc, symmetric) staged in shared
+// memory, PB patches per pass; overlapping patches accumulate with atomics.
+// A family is a lattice of boxes of cells (vertex patches: 4x4x4 around each
+// interior coarse vertex; edge patches: 2 cells along a coarse edge x 4 x 4
+// across); patch (pa, pb, pc) has its box origin at 2 (pa, pb, pc) - shift,
+// and its local edges follow the canonical numbering of that box.
 template <typename T, int PB>
-__global__ void __launch_bounds__(128) k_vertex_dense(int n, const T* __restrict__ D, T eta, const T* __restrict__ r,
-                                                      T* __restrict__ z) {
+__global__ void __launch_bounds__(128) k_patch_dense(int n, PatchFamily fam, const T* __restrict__ D, T eta,
+                                                     const T* __restrict__ r, T* __restrict__ z) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* Ds = reinterpret_cast<T*>(smem_raw);          // 108*108
-  T* Rs = Ds + 108 * 108;                          // 108*PB
-  const int nc = n / 2, nv = nc - 1;
-  const int64_t NP = (int64_t)nv * nv * nv;
+  const int nl = fam.nloc;
+  T* Ds = reinterpret_cast<T*>(smem_raw);          // nl * nl
+  T* Rs = Ds + nl * nl;                            // nl * PB
+  int* loc = reinterpret_cast<int*>(Rs + nl * PB); // packed (d, i, j, k) of each local edge
+  const int64_t NP = (int64_t)fam.np[0] * fam.np[1] * fam.np[2];
   const int64_t N3 = (int64_t)n * (n - 1) * (n - 1);
   r += (int64_t)blockIdx.y * 3 * N3;
   z += (int64_t)blockIdx.y * 3 * N3;
-  for (int q = threadIdx.x; q < 108 * 108; q += blockDim.x) Ds[q] = D[q];
+  for (int q = threadIdx.x; q < nl * nl; q += blockDim.x) Ds[q] = D[q];
+  const int bx = fam.b[0], by = fam.b[1], bz = fam.b[2];
+  const int cx = bx * (by - 1) * (bz - 1), cy = (bx - 1) * by * (bz - 1);
+  for (int l = threadIdx.x; l < nl; l += blockDim.x) {
+    int d, i, j, k, e = l;
+    if (e < cx) {
+      d = 0; i = e % bx; j = (e / bx) % (by - 1) + 1; k = e / (bx * (by - 1)) + 1;
+    } else if ((e -= cx) < cy) {
+      d = 1; i = e % (bx - 1) + 1; j = (e / (bx - 1)) % by; k = e / ((bx - 1) * by) + 1;
+    } else {
+      e -= cy;
+      d = 2; i = e % (bx - 1) + 1; j = (e / (bx - 1)) % (by - 1) + 1; k = e / ((bx - 1) * (by - 1));
+    }
+    loc[l] = (((d * 16 + i) * 16 + j) * 16) + k;
+  }
+  auto gidx_of = [&](int64_t P, int l) {
+    const int pa = (int)(P % fam.np[0]) + fam.p0[0];
+    const int pb = (int)((P / fam.np[0]) % fam.np[1]) + fam.p0[1];
+    const int pc = (int)(P / ((int64_t)fam.np[0] * fam.np[1])) + fam.p0[2];
+    const int c = loc[l];
+    const int d = c >> 12, i = (c >> 8) & 15, j = (c >> 4) & 15, k = c & 15;
+    return edge_gidx(n, d, 2 * pa - fam.shift[0] + i, 2 * pb - fam.shift[1] + j, 2 * pc - fam.shift[2] + k);
+  };
   for (int64_t base = (int64_t)blockIdx.x * PB; base < NP; base += (int64_t)gridDim.x * PB) {
     __syncthreads();
-    for (int q = threadIdx.x; q < 108 * PB; q += blockDim.x) {
-      const int p = q / 108, l = q % 108;
+    for (int q = threadIdx.x; q < nl * PB; q += blockDim.x) {
+      const int p = q / nl, l = q % nl;
       const int64_t P = base + p;
-      T v = T(0);
-      if (P < NP) {
-        const int I = (int)(P % nv) + 1, J = (int)((P / nv) % nv) + 1, K = (int)(P / ((int64_t)nv * nv)) + 1;
-        v = __ldg(r + patch_gidx(n, I, J, K, l));
-      }
-      Rs[l * PB + p] = v;
+      Rs[l * PB + p] = P < NP ? __ldg(r + gidx_of(P, l)) : T(0);
     }
     __syncthreads();
-    for (int row = threadIdx.x; row < 108; row += blockDim.x) {
+    for (int row = threadIdx.x; row < nl; row += blockDim.x) {
       T acc[PB];
 #pragma unroll
       for (int p = 0; p < PB; ++p) acc[p] = T(0);
-      for (int c = 0; c < 108; ++c) {
-        const T dv = Ds[c * 108 + row];
+      for (int c = 0; c < nl; ++c) {
+        const T dv = Ds[c * nl + row];
 #pragma unroll
         for (int p = 0; p < PB; ++p) acc[p] += dv * Rs[c * PB + p];
       }
 #pragma unroll
-      for (int p = 0; p < PB; ++p) {
-        const int64_t P = base + p;
-        if (P < NP) {
-          const int I = (int)(P % nv) + 1, J = (int)((P / nv) % nv) + 1, K = (int)(P / ((int64_t)nv * nv)) + 1;
-          atomicAdd(z + patch_gidx(n, I, J, K, row), eta * acc[p]);
-        }
-      }
+      for (int p = 0; p < PB; ++p)
+        if (base + p < NP) atomicAdd(z + gidx_of(base + p, row), eta * acc[p]);
     }
   }
 }
@@ -596,24 +599,44 @@ template <typename T>
 static constexpr int pb_for() { return sizeof(T) == 8 ? kPB64 : kPB32; }
 
 template <typename T>
-size_t vertex_dense_smem() { return sizeof(T) * (108 * 108 + 108 * pb_for<T>()); }
+size_t patch_dense_smem(int nloc) { return sizeof(T) * (nloc * nloc + nloc * pb_for<T>()) + sizeof(int) * nloc; }
 
 template <typename T>
 cudaError_t prepare_vertex_dense() {
-  return cudaFuncSetAttribute(k_vertex_dense<T, pb_for<T>()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)vertex_dense_smem<T>());
+  return cudaFuncSetAttribute(k_patch_dense<T, pb_for<T>()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)patch_dense_smem<T>(108));
 }
 
 template <typename T>
-void launch_vertex_dense(cudaStream_t s, int sm, int n, const T* D, double eta, const T* r, T* z, int R) {
-  const int64_t nv = n / 2 - 1;
-  const int64_t NP = nv * nv * nv;
+void launch_patch_dense(cudaStream_t s, int sm, int n, const PatchFamily& fam, const T* D, double eta, const T* r,
+                        T* z, int R) {
+  const int64_t NP = (int64_t)fam.np[0] * fam.np[1] * fam.np[2];
   if (NP <= 0) return;
   constexpr int PB = pb_for<T>();
   int64_t blocks = (NP + PB - 1) / PB;
   const int64_t cap = (int64_t)sm * 2;
   if (blocks > cap) blocks = cap;
-  k_vertex_dense<T, PB><<<dim3((int)blocks, R), 128, vertex_dense_smem<T>(), s>>>(n, D, (T)eta, r, z);
+  k_patch_dense<T, PB><<<dim3((int)blocks, R), 128, patch_dense_smem<T>(fam.nloc), s>>>(n, fam, D, (T)eta, r, z);
+}
+
+PatchFamily vertex_family(int n) {
+  const int nv = n / 2 - 1;
+  return PatchFamily{108, {4, 4, 4}, {nv, nv, nv}, {1, 1, 1}, {2, 2, 2}};
+}
+
+PatchFamily edge_family(int n, int d) {
+  const int nc = n / 2;
+  PatchFamily f{42, {4, 4, 4}, {nc - 1, nc - 1, nc - 1}, {1, 1, 1}, {2, 2, 2}};
+  f.b[d] = 2;
+  f.np[d] = nc;
+  f.p0[d] = 0;
+  f.shift[d] = 0;
+  return f;
+}
+
+template <typename T>
+void launch_vertex_dense(cudaStream_t s, int sm, int n, const T* D, double eta, const T* r, T* z, int R) {
+  launch_patch_dense<T>(s, sm, n, vertex_family(n), D, eta, r, z, R);
 }
 
 template <typename T>
@@ -664,6 +687,7 @@ void launch_add_f32(cudaStream_t s, int sm, int64_t N, const double* sc, const f
   template void launch_bubble<T>(cudaStream_t, int, int, const T*, double, const T*, T*, int);        \
   template cudaError_t prepare_vertex_dense<T>();                                                     \
   template void launch_vertex_dense<T>(cudaStream_t, int, int, const T*, double, const T*, T*, int);  \
+  template void launch_patch_dense<T>(cudaStream_t, int, int, const PatchFamily&, const T*, double, const T*, T*, int); \
   template void launch_coarse<T>(cudaStream_t, int, const double*, const T*, T*, int);                \
   template void launch_dot2<T>(cudaStream_t, int, int64_t, const T*, const T*, const T*, const T*,    \
                                double*, double*, int);                                                \

@@ -19,6 +19,19 @@ template <typename T>
 cudaError_t prepare_vertex_dense();
 template <typename T>
 void launch_vertex_dense(cudaStream_t s, int sm, int n, const T* D, double eta, const T* r, T* z, int R);
+// A lattice of box-shaped patches (see k_patch_dense in kernels.cu).
+struct PatchFamily {
+  int nloc;      // interior edges of one box
+  int b[3];      // box extents in cells
+  int np[3];     // patches per axis
+  int p0[3];     // first patch index per axis
+  int shift[3];  // box origin = 2 * patch index - shift
+};
+PatchFamily vertex_family(int n);
+PatchFamily edge_family(int n, int d);
+template <typename T>
+void launch_patch_dense(cudaStream_t s, int sm, int n, const PatchFamily& fam, const T* D, double eta, const T* r,
+                        T* z, int R);
 template <typename T>
 void launch_coarse(cudaStream_t s, int N0, const double* Ainv, const T* g, T* z, int R);
 int reduction_blocks(int sm);

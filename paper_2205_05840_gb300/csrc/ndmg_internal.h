@@ -35,6 +35,7 @@ struct LocalOps {
   std::vector<double> AinvT;  // 6x6 inverse of the interior-space matrix A_T
   std::vector<double> Dv;     // 108x108 J_V A_V^{-1} J_V^t (patch-local order)
   std::vector<double> Wv;     // 108x60 Gram factor, Dv = Wv Wv^t
+  std::vector<double> De[3];  // 42x42 J_E A_E^{-1} J_E^t for coarse edges along x, y, z
 };
 
 // Dense assembled matrix of a box with Dirichlet (interior-edge) DOFs for
@@ -61,6 +62,8 @@ struct DevLevel {
   float* AinvT32 = nullptr;
   double* Dv64 = nullptr;     // 108*108
   float* Dv32 = nullptr;
+  double* De64 = nullptr;     // 3 * 42*42 (edge-based smoother)
+  float* De32 = nullptr;
   void* Wtc = nullptr;        // tensor-core operand images (bf16/fp16), see tc kernel
 };
 

@@ -150,28 +150,23 @@ std::vector<double> spd_inverse(const std::vector<double>& a, int n, bool* ok) {
   return inv;
 }
 
-void build_local_ops(int n, double L, double alpha, double beta, LocalOps* out) {
-  const double h = L / n;
-  out->n = n;
-  out->h = h;
-  bool ok = false;
-  // interior space N_h^T of one coarse element (2x2x2 cells, 6 edges)
-  const Box bub{{2, 2, 2}};
-  std::vector<double> AT = box_matrix(bub, h, alpha, beta);
-  out->AinvT = spd_inverse(AT, 6, &ok);
-  if (!ok) throw std::runtime_error("interior-space matrix is not SPD");
-
-  // vertex patch: 4x4x4 cells around a coarse vertex, 108 interior edges
-  const Box pb{{4, 4, 4}};
+// J_D A_D^{-1} J_D^t for the discrete-harmonic patch space of a box of
+// cells (Sec. 3.2, eq. vertex space / edge space): the box's edges split into
+// the interiors of its 2x2x2 coarse elements (I) and the rest (G); with
+// S = A_GG - A_GI A_II^{-1} A_IG = R R^t and H = [-A_II^{-1} A_IG ; I],
+// W = H R^{-t} and D = W W^t (= A_p^{-1} - sum_T J_T A_T^{-1} J_T^t).
+// AinvT: the 6x6 interior-space inverse (for the self-check).
+static void patch_operator(const Box& pb, double h, double alpha, double beta, const std::vector<double>& AinvT,
+                           std::vector<double>* D, std::vector<double>* W, int* n_interface) {
   const int np = (int)pb.size();
   std::vector<double> Ap = box_matrix(pb, h, alpha, beta);
-  // the 8 interior spaces inside the patch, each in the 2x2x2 box order;
-  // Bblk = sum_T J_T A_T^{-1} J_T^t restricted to the patch
+  // the interior spaces of the coarse elements inside the box, each in the
+  // 2x2x2 box order; Bblk = sum_T J_T A_T^{-1} J_T^t restricted to the box
   std::vector<int> isB(np, 0);
   std::vector<double> Bblk((size_t)np * np, 0.0);
-  for (int sr = 0; sr < 2; ++sr)
-    for (int sq = 0; sq < 2; ++sq)
-      for (int sp = 0; sp < 2; ++sp) {
+  for (int sr = 0; sr < pb.b[2] / 2; ++sr)
+    for (int sq = 0; sq < pb.b[1] / 2; ++sq)
+      for (int sp = 0; sp < pb.b[0] / 2; ++sp) {
         const int o[3] = {2 * sp, 2 * sq, 2 * sr};
         int ids[6];
         int t = 0;
@@ -183,15 +178,15 @@ void build_local_ops(int n, double L, double alpha, double beta, LocalOps* out) 
           }
         for (int a = 0; a < 6; ++a) {
           isB[ids[a]] = 1;
-          for (int b = 0; b < 6; ++b) Bblk[(size_t)ids[a] * np + ids[b]] = out->AinvT[a * 6 + b];
+          for (int b = 0; b < 6; ++b) Bblk[(size_t)ids[a] * np + ids[b]] = AinvT[a * 6 + b];
         }
       }
 
-  // Gram factor through the Schur complement on the interface (60 edges)
+  // Gram factor through the Schur complement on the interface edges
   std::vector<int> I, G;
   for (int e = 0; e < np; ++e) (isB[e] ? I : G).push_back(e);
   const int nI = (int)I.size(), nG = (int)G.size();
-  if (nI != 48 || nG != 60) throw std::runtime_error("unexpected vertex-patch split");
+  *n_interface = nG;
   std::vector<double> AII((size_t)nI * nI), AIG((size_t)nI * nG), AGG((size_t)nG * nG);
   for (int a = 0; a < nI; ++a)
     for (int b = 0; b < nI; ++b) AII[(size_t)a * nI + b] = Ap[(size_t)I[a] * np + I[b]];
@@ -228,7 +223,7 @@ void build_local_ops(int n, double L, double alpha, double beta, LocalOps* out) 
   if (!cholesky(R, nG)) throw std::runtime_error("Schur complement is not SPD");
   // W^t = R^{-1} H^t with H = [-X ; I] (patch order): forward substitution on
   // each of the 108 columns of H^t
-  out->Wv.assign((size_t)np * nG, 0.0);
+  (*W).assign((size_t)np * nG, 0.0);
   std::vector<double> ht(nG);
   for (int e = 0; e < np; ++e) {
     if (isB[e]) {
@@ -239,31 +234,58 @@ void build_local_ops(int n, double L, double alpha, double beta, LocalOps* out) 
       for (int c = 0; c < nG; ++c) ht[c] = (c == g) ? 1.0 : 0.0;
     }
     forward_solve(R, nG, ht.data());
-    for (int c = 0; c < nG; ++c) out->Wv[(size_t)e * nG + c] = ht[c];
+    for (int c = 0; c < nG; ++c) (*W)[(size_t)e * nG + c] = ht[c];
   }
   // The dense operator used by the CUDA-core kernels is D = W W^t as well:
   // forming A_p^{-1} - Bblk instead would cancel the large bubble entries and
   // lose ~cond(A_p) digits.  Self-check with a residual that stays well
   // scaled: A_p (D + Bblk) = I (Sec. 3.2: the patch space is the direct sum of
   // the 8 interior spaces and the a-orthogonal vertex space).
-  out->Dv.assign((size_t)np * np, 0.0);
+  (*D).assign((size_t)np * np, 0.0);
   for (int a = 0; a < np; ++a)
     for (int b = 0; b < np; ++b) {
       double sdot = 0.0;
-      for (int c = 0; c < nG; ++c) sdot += out->Wv[(size_t)a * nG + c] * out->Wv[(size_t)b * nG + c];
-      out->Dv[(size_t)a * np + b] = sdot;
+      for (int c = 0; c < nG; ++c) sdot += (*W)[(size_t)a * nG + c] * (*W)[(size_t)b * nG + c];
+      (*D)[(size_t)a * np + b] = sdot;
     }
   double err = 0.0;
   for (int a = 0; a < np; ++a)
     for (int b = 0; b < np; ++b) {
       double sdot = 0.0;
       for (int c = 0; c < np; ++c)
-        sdot += Ap[(size_t)a * np + c] * (out->Dv[(size_t)c * np + b] + Bblk[(size_t)c * np + b]);
+        sdot += Ap[(size_t)a * np + c] * ((*D)[(size_t)c * np + b] + Bblk[(size_t)c * np + b]);
       err = std::fmax(err, std::fabs(sdot - (a == b ? 1.0 : 0.0)));
     }
   // rounding grows like cond(A_p)^2 eps here (cond ~ alpha / (beta h^2));
   // an indexing mistake gives O(1), so 1e-3 separates the two up to n ~ 1000
   if (!(err <= 1e-3)) throw std::runtime_error("Gram factor does not reproduce the patch operator");
+}
+
+
+void build_local_ops(int n, double L, double alpha, double beta, LocalOps* out) {
+  const double h = L / n;
+  out->n = n;
+  out->h = h;
+  bool ok = false;
+  // interior space N_h^T of one coarse element (2x2x2 cells, 6 edges)
+  const Box bub{{2, 2, 2}};
+  std::vector<double> AT = box_matrix(bub, h, alpha, beta);
+  out->AinvT = spd_inverse(AT, 6, &ok);
+  if (!ok) throw std::runtime_error("interior-space matrix is not SPD");
+  // vertex patch: 4x4x4 cells around a coarse vertex, 108 interior edges,
+  // 60 of them on the interface (eq. vertex space)
+  int nG = 0;
+  patch_operator(Box{{4, 4, 4}}, h, alpha, beta, out->AinvT, &out->Dv, &out->Wv, &nG);
+  if (nG != 60) throw std::runtime_error("unexpected vertex-patch split");
+  // edge patches: 2 cells along the coarse edge, 4 x 4 across, 42 interior
+  // edges, 18 on the interface (eq. edge space); one operator per direction
+  for (int d = 0; d < 3; ++d) {
+    Box eb{{4, 4, 4}};
+    eb.b[d] = 2;
+    std::vector<double> We;
+    patch_operator(eb, h, alpha, beta, out->AinvT, &out->De[d], &We, &nG);
+    if (nG != 18) throw std::runtime_error("unexpected edge-patch split");
+  }
 }
 
 std::vector<double> coarse_inverse(int n0, double L, double alpha, double beta) {

@@ -163,12 +163,43 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {
   }
 }
 
-// staged-region index of edge (d; i, j, k) given in region coordinates
-// (x: 12 segments x 11 x 11 node lines; y: 11 x 12 x 11; z: 11 x 11 x 12)
+// Staged region: per direction a 12 x 11 x 11 box (12 along the edges, 11
+// node lines across: x: 12x11x11, y: 11x12x11, z: 11x11x12), stored split by
+// the parity of (i, j, k) into 8 octant sub-boxes.  Patches sit two cells
+// apart, so in a plain layout the 32 patches of a warp read words an even
+// distance apart and hit only 16 banks; in the octant layout neighbouring
+// patches read neighbouring words (about half the shared-memory wavefronts).
+__host__ __device__ constexpr int dir_len(int d, int axis) { return axis == d ? kRE : kRN; }
+__host__ __device__ constexpr int oct_len(int L, int par) { return (L + 1 - par) / 2; }
+__host__ __device__ constexpr int oct_size(int d, int o) {
+  return oct_len(dir_len(d, 0), o & 1) * oct_len(dir_len(d, 1), (o >> 1) & 1) * oct_len(dir_len(d, 2), (o >> 2) & 1);
+}
+__host__ __device__ constexpr int oct_base(int d, int o) {
+  int base = d * kRegion;
+  for (int q = 0; q < o; ++q) base += oct_size(d, q);
+  return base;
+}
+__constant__ int kOctBase[24] = {
+    oct_base(0, 0), oct_base(0, 1), oct_base(0, 2), oct_base(0, 3), oct_base(0, 4), oct_base(0, 5), oct_base(0, 6),
+    oct_base(0, 7), oct_base(1, 0), oct_base(1, 1), oct_base(1, 2), oct_base(1, 3), oct_base(1, 4), oct_base(1, 5),
+    oct_base(1, 6), oct_base(1, 7), oct_base(2, 0), oct_base(2, 1), oct_base(2, 2), oct_base(2, 3), oct_base(2, 4),
+    oct_base(2, 5), oct_base(2, 6), oct_base(2, 7)};
+static_assert(oct_base(2, 7) + oct_size(2, 7) == 3 * kRegion, "octants tile the region");
+
+// staged-region index of edge (d; i, j, k) in region coordinates; with
+// literal arguments everything but the final sum constant-folds
+__host__ __device__ constexpr int region_at_c(int d, int i, int j, int k) {
+  const int o = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
+  const int PI = oct_len(dir_len(d, 0), i & 1);
+  const int PJ = PI * oct_len(dir_len(d, 1), j & 1);
+  return oct_base(d, o) + (k >> 1) * PJ + (j >> 1) * PI + (i >> 1);
+}
+// same, for run-time arguments (octant bases from a constant table)
 __device__ __forceinline__ int region_at(int d, int i, int j, int k) {
-  if (d == 0) return (k * kRN + j) * kRE + i;
-  if (d == 1) return kRegion + (k * kRE + j) * kRN + i;
-  return 2 * kRegion + (k * kRN + j) * kRN + i;
+  const int o = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
+  const int PI = oct_len(dir_len(d, 0), i & 1);
+  const int PJ = PI * oct_len(dir_len(d, 1), j & 1);
+  return kOctBase[d * 8 + o] + (k >> 1) * PJ + (j >> 1) * PI + (i >> 1);
 }
 
 // patch-local edge l in [0,108) of the patch at brick-relative vertex (a,b,c):
@@ -183,7 +214,7 @@ __device__ __forceinline__ int region_index(int l, int a, int b, int c) {
   } else {
     l -= 72; d = 2; i = l % 3; j = (l / 3) % 3; k = l / 9;
   }
-  return region_at(d, i + 2 * a, j + 2 * b, k + 2 * c);
+  return region_at_c(d, i + 2 * a, j + 2 * b, k + 2 * c);
 }
 
 // patch-local edge -> owned-accumulator slot (or -1 if not owned by the brick)
@@ -235,15 +266,29 @@ __device__ __forceinline__ void bubble_edge(int t, int a, int b, int c, int& d, 
   p[d] = 2 * (d == 0 ? a : d == 1 ? b : c) + s;
 }
 
-// direction of patch-local edge l and its region offset for the patch at
-// brick-relative vertex (0,0,0); both constant-fold when l is a literal
-__device__ __forceinline__ int local_dir(int l) { return l < 36 ? 0 : (l < 72 ? 1 : 2); }
-__device__ __forceinline__ int local_off(int l) { return region_index(l, 0, 0, 0) - region_at(local_dir(l), 0, 0, 0); }
+// region coordinates of patch-local edge l for the patch at brick-relative
+// vertex (0,0,0) (the 4x4x4 box numbering: x: 4 segments x 3 x 3 nodes, then
+// y, then z); constant-folds for a literal l
+__host__ __device__ constexpr int local_dir(int l) { return l < 36 ? 0 : (l < 72 ? 1 : 2); }
+__host__ __device__ constexpr int local_ri(int l) { return l < 36 ? l % 4 : (l < 72 ? (l - 36) % 3 : (l - 72) % 3); }
+__host__ __device__ constexpr int local_rj(int l) {
+  return l < 36 ? (l / 4) % 3 : (l < 72 ? ((l - 36) / 3) % 4 : ((l - 72) / 3) % 3);
+}
+__host__ __device__ constexpr int local_rk(int l) { return l < 36 ? l / 12 : (l < 72 ? (l - 36) / 12 : (l - 72) / 9); }
+
+// staged-region index of patch-local edge l of the patch at (a,b,c): the
+// patch moves by 2 cells per vertex, i.e. by one entry of its octant
+__device__ __forceinline__ int patch_elem(int l, int a, int b, int c) {
+  const int d = local_dir(l), i = local_ri(l), j = local_rj(l), k = local_rk(l);
+  const int PI = oct_len(dir_len(d, 0), i & 1);
+  const int PJ = PI * oct_len(dir_len(d, 1), j & 1);
+  return region_at_c(d, i, j, k) + c * PJ + b * PI + a;
+}
 
 // 7 chunks of 8 patch-local edges from chunk CH0 on, rounded to bf16/fp16 and
 // stored as 16-byte rows of the K-major operand A
 template <int CH0, bool FP16>
-__device__ __forceinline__ void gather_chunks(const float* R, uint8_t* A, int p, const int (&base)[3], bool live,
+__device__ __forceinline__ void gather_chunks(const float* R, uint8_t* A, int p, int a, int b, int c, bool live,
                                               float rscale) {
 #pragma unroll
   for (int ch = CH0; ch < CH0 + 7; ++ch) {
@@ -251,7 +296,7 @@ __device__ __forceinline__ void gather_chunks(const float* R, uint8_t* A, int p,
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
       const int l = ch * 8 + t;
-      v[t] = (live && l < 108) ? R[base[local_dir(l)] + local_off(l)] * rscale : 0.f;
+      v[t] = (live && l < 108) ? R[patch_elem(l, a, b, c)] * rscale : 0.f;
     }
     uint4 w;
     w.x = pack2<FP16>(v[0], v[1]);
@@ -356,7 +401,7 @@ __global__ void __launch_bounds__(kThreads, 3)
         else if (d == 1) off = N3 + ((uint32_t)(gk - 1) * n + gj) * n1 + (gi - 1);
         else off = 2 * N3 + ((uint32_t)gk * n1 + (gj - 1)) * n1 + (gi - 1);
       }
-      cp_async4(rbase + 4u * q, r + off, in ? 4u : 0u);
+      cp_async4(rbase + 4u * region_at(d, i, j, k), r + off, in ? 4u : 0u);
     }
     const uint4* src = reinterpret_cast<const uint4*>(img);
     const uint32_t wbase = smem_u32(smem + OFF_B1);
@@ -413,13 +458,11 @@ __global__ void __launch_bounds__(kThreads, 3)
     const int a = p % 5, b = (p / 5) % 5, c = p / 25;
     const bool live = p < 125 && (I0 + a) >= 1 && (I0 + a) <= nc - 1 && (J0 + b) >= 1 && (J0 + b) <= nc - 1 &&
                       (K0 + c) >= 1 && (K0 + c) <= nc - 1;
-    const int base[3] = {region_at(0, 2 * a, 2 * b, 2 * c), region_at(1, 2 * a, 2 * b, 2 * c),
-                         region_at(2, 2 * a, 2 * b, 2 * c)};
     uint8_t* A = smem + OFF_A;
     if (half == 0)
-      gather_chunks<0, FP16>(R, A, p, base, live, rscale);
+      gather_chunks<0, FP16>(R, A, p, a, b, c, live, rscale);
     else
-      gather_chunks<7, FP16>(R, A, p, base, live, rscale);
+      gather_chunks<7, FP16>(R, A, p, a, b, c, live, rscale);
   }
   fence_async_smem();
   __syncthreads();
