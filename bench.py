@@ -52,7 +52,47 @@ def parse():
     p.add_argument("--profile-case", choices=["none", "smooth", "residual", "vcycle"], default="none",
                    help="run only a few launches of one kernel class on an --n grid (for ncu captures)")
     p.add_argument("--n", type=int, default=N_GRID)
+    p.add_argument("--grad-sweep", action="store_true",
+                   help="forward + adjoint solve throughput for 32^3 .. 256^3 (one JSON line per size)")
     return p.parse_args()
+
+
+def run_grad_sweep(args):
+    """Differentiable solve: u = A(alpha)^{-1} f forward, lambda = A^{-1}(u - u_t)
+    and dL/dalpha = -lambda^T K u backward, for n in 32, 64, 96, 128, 192, 256
+    (coarsest 4^3, or 3^3 when n is a multiple of 3); bf16 tensor-core
+    V-cycle inside FP64 PCG, tolerance 1e-8; times of --steps fwd+bwd passes."""
+    import torch
+
+    from paper_2205_05840_gb300 import autograd, inputs, ndmg
+    for n in (32, 64, 96, 128, 192, 256):
+        n0 = 3 if n % 3 == 0 else 4
+        S = ndmg.Solver(n, n_coarsest=n0, alpha=1.0, precision=ndmg.PREC_MIXED_BF16)
+        f = torch.tensor(inputs.random_load(n, 0), device="cuda", requires_grad=True)
+        ut = torch.tensor(1e-3 * inputs.random_target(n, 1), device="cuda")
+        a = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+        times = []
+        for s in range(args.warmup + args.steps):
+            f.grad = None
+            a.grad = None
+            v0 = S.counters()[1]
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            u = autograd.solve(f, a, S, tol=TOL)
+            loss = 0.5 * ((u - ut) ** 2).sum()
+            loss.backward()
+            e1.record()
+            torch.cuda.synchronize()
+            if s >= args.warmup:
+                times.append((e0.elapsed_time(e1), S.counters()[1] - v0))
+        ms = sum(t for t, _ in times) / len(times)
+        vc = sum(c for _, c in times) / len(times)
+        print(json.dumps({"case": "fwd+bwd", "n": n, "dofs": S.num_dofs(), "ms": ms, "vcycles": vc,
+                          "dof_cycles_per_s": S.num_dofs() * vc / (ms / 1e3), "dL_dalpha": float(a.grad)}),
+              flush=True)
+        del S, f, ut, u
+        torch.cuda.empty_cache()
 
 
 def run_profile_case(args):
@@ -220,6 +260,33 @@ def whole_job_value(world: int, dofs: int, vcycles_per_step: float, steps: int, 
     return world * dofs * vcycles_per_step * steps / (ms_total / 1e3)
 
 
+# DRAM traffic per finest-level launch (dram__bytes_read.sum +
+# dram__bytes_write.sum, one ncu capture at 128^3, profiles/), valid only for
+# the kernel source it was measured on (sha256 prefix of the file)
+PROFILED_TRAFFIC = {
+    "patch": {"bytes": 49.626880e6 + 0.648704e6, "algorithmic": 12.0 * 6193536,
+              "source": "paper_2205_05840_gb300/csrc/tc_patch.cu", "sha256": "ddfbce46620c54b8"},
+    "stencil": {"bytes": 49.562624e6 + 1.336064e6, "algorithmic": 12.0 * 6193536,
+                "source": "paper_2205_05840_gb300/csrc/kernels.cu", "sha256": "e934fffa53a0fa72"},
+}
+
+
+def profiled_traffic(kernel: str):
+    """(traffic, algorithmic bytes) of one 128^3 launch, or (None, None) when
+    the kernel source changed since the counters were taken."""
+    import hashlib
+    t = PROFILED_TRAFFIC.get(kernel)
+    if not t:
+        return None, None
+    try:
+        with open(os.path.join(ROOT, t["source"]), "rb") as fh:
+            if hashlib.sha256(fh.read()).hexdigest()[:16] != t["sha256"]:
+                return None, None
+    except OSError:
+        return None, None
+    return t["bytes"], t["algorithmic"]
+
+
 BATCH_RHS = 32
 BATCH_ALPHA = 1e-2 ** 2 / 4.0
 
@@ -358,8 +425,11 @@ def run_ours(args):
     else:
         bound, peak, unit, scale = "hbm", hbm, "GB/s", 1e9
     achieved = kd["units"] / (kd["ms"] / 1e3) / scale if kd["ms"] > 0 else 0.0
+    traffic, traffic_alg = profiled_traffic(dom)
     roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": achieved / peak if peak else None, "traffic": None,
+            "frac": achieved / peak if peak else None, "traffic": traffic,
+            "traffic_note": "DRAM bytes of one finest-level (128^3) launch from ncu; algorithmic bytes of that "
+                            f"launch: {traffic_alg}" if traffic else "no capture of the current kernel source",
             "peak_source": "MEASURED_PEAKS.json" if bound in ("hbm", "tensor") else "nominal (see DESIGN.md)",
             "launches": kd["launches"], "ms": kd["ms"]}
 
@@ -428,6 +498,8 @@ def main():
         run_reference(args)
     elif args.profile_case != "none":
         run_profile_case(args)
+    elif args.grad_sweep:
+        run_grad_sweep(args)
     else:
         run_ours(args)
 

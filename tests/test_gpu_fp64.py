@@ -159,8 +159,9 @@ def test_pcg_parity(n, n0, alpha):
     st, it, rr = S.solve(T(f), u, tol=1e-8)
     assert rr <= 1e-8 and it == it_ref
     assert rel(N(u), u_ref) < 1e-9
-    x = spla.spsolve(H.A[-1].tocsc(), f)
-    assert rel(N(u), x) < 1e-6
+    if f.size < 50000:   # sparse direct solves of 3D meshes fill in quickly; keep them small
+        x = spla.spsolve(H.A[-1].tocsc(), f)
+        assert rel(N(u), x) < 1e-6
 
 
 @pytest.mark.parametrize("alpha", [0.01, 1.0, 100.0])

@@ -56,3 +56,29 @@ def test_gradient_matches_oracle_and_fd(prec):
         Lm = 0.5 * float(((autograd.solve(f.detach() - t * v, torch.tensor(alpha0, dtype=torch.float64), S, 1e-10) - ut) ** 2).sum())
     fdf = (Lp - Lm) / (2 * t)
     assert abs(float((f.grad * v).sum()) - fdf) < 1e-5 * abs(fdf)
+
+
+def test_gradient_96_cubed_directional_fd():
+    # the differentiable-solve configuration: 96^3 (coarsest 3^3), loss
+    # 0.5 ||u(f, alpha) - u_t||^2 with u_t from seed 1; the adjoint gradient
+    # agrees with central differences along alpha and along a random f-direction
+    n, alpha0 = 96, 1.0
+    S = ndmg.Solver(n, n_coarsest=3, alpha=alpha0, precision=ndmg.PREC_MIXED_BF16)
+    f = torch.tensor(inputs.random_load(n, 0), device="cuda", requires_grad=True)
+    ut = torch.tensor(1e-3 * inputs.random_target(n, 1), device="cuda")
+    a = torch.tensor(alpha0, dtype=torch.float64, requires_grad=True)
+    u = autograd.solve(f, a, S, tol=1e-10)
+    loss = 0.5 * ((u - ut) ** 2).sum()
+    loss.backward()
+
+    def L(al, ff):
+        with torch.no_grad():
+            uu = autograd.solve(ff, torch.tensor(al, dtype=torch.float64), S, tol=1e-10)
+            return 0.5 * float(((uu - ut) ** 2).sum())
+    eps = 1e-4 * alpha0
+    fd = (L(alpha0 + eps, f.detach()) - L(alpha0 - eps, f.detach())) / (2 * eps)
+    assert abs(float(a.grad) - fd) < 1e-5 * abs(fd)
+    v = torch.tensor(np.random.default_rng(3).standard_normal(f.numel()), device="cuda")
+    t = 1e-3
+    fdf = (L(alpha0, f.detach() + t * v) - L(alpha0, f.detach() - t * v)) / (2 * t)
+    assert abs(float((f.grad * v).sum()) - fdf) < 1e-5 * abs(fdf)
