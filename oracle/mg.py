@@ -422,6 +422,42 @@ def contraction_power(H: Hierarchy, m: int | None = None, iters=60, seed=0) -> f
     return lam
 
 
+def contraction_lanczos(H: Hierarchy, m: int | None = None, steps=40, z0=None, seed=0) -> float:
+    """||E_K||_a by the Lanczos process in the a-inner product.
+
+    E_K is a-self-adjoint and a-positive semidefinite (Remark 6), so the
+    Krylov space of E_K from z0, orthonormalised in (x, y)_a = x^T A y, gives
+    a tridiagonal T whose largest eigenvalue approaches ||E_K||_a from below
+    (much faster than the power iteration when the top eigenvalues cluster).
+    Every new basis vector is orthogonalised against all previous ones."""
+    A = H.A[-1]
+    if z0 is None:
+        z0 = np.random.default_rng(seed).standard_normal(A.shape[0])
+    zero = np.zeros(A.shape[0])
+    V, AV = [], []
+    diag, off = [], []
+    Az = A @ z0
+    nrm = np.sqrt(z0 @ Az)
+    v, Av = z0 / nrm, Az / nrm
+    for j in range(steps):
+        V.append(v)
+        AV.append(Av)
+        w = H.mg(H.K, zero, v, m)                  # w = E_K v
+        diag.append(float(w @ Av))
+        for vi, Avi in zip(V, AV):                  # (w, v_i)_a = w^T (A v_i)
+            w = w - (w @ Avi) * vi
+        for vi, Avi in zip(V, AV):                  # second pass: orthogonality to rounding
+            w = w - (w @ Avi) * vi
+        Aw = A @ w
+        b = np.sqrt(max(float(w @ Aw), 0.0))
+        if j == steps - 1 or b < 1e-14 * abs(diag[0]):
+            break
+        off.append(b)
+        v, Av = w / b, Aw / b
+    T = np.diag(diag) + np.diag(off[:len(diag) - 1], 1) + np.diag(off[:len(diag) - 1], -1)
+    return float(np.max(np.abs(np.linalg.eigvalsh(T))))
+
+
 # --------------------------------------------------------------------------
 # Adjoint gradient of L = 0.5 ||u(f, alpha) - u_t||^2
 # --------------------------------------------------------------------------

@@ -291,6 +291,14 @@ def test_table2_k2_approximate():
         assert rho >= (8 / 9) ** (2 * m) - 1e-12      # interior eigenmode lower bound
 
 
+@pytest.mark.parametrize("alpha,k,m", [(0.01, 1, 3), (100.0, 2, 1), (1.0, 2, 2)])
+def test_lanczos_contraction_equals_dense(alpha, k, m):
+    # the Lanczos estimate used at k >= 3 (where the dense E_k is out of reach)
+    # reproduces the exact ||E_k||_a of the dense error operator
+    H = mg.Hierarchy(2 ** (k + 1), 2.0, alpha, 1.0, n0=2, kind="vertex", m=m)
+    assert abs(mg.contraction_lanczos(H, steps=150) - mg.contraction_dense(H)) < 1e-10
+
+
 def test_vcycle_error_operator_spsd_and_contractive():
     # Remark 6: E_k is a-symmetric positive semidefinite; Theorem 10: ||E_k||_a < 1
     H = mg.Hierarchy(8, 1.0, 1.0, 1.0, n0=2, m=1)
