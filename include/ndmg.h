@@ -124,6 +124,23 @@ int ndmg_num_dofs(const ndmg_t* h, int32_t level, int64_t* out);
 /* y = A_k x (Sec. 2: <A_h w, v> = a(w, v)), matrix-free.  x, y: N(n_k) [x nrhs]. */
 int ndmg_apply(ndmg_t* h, int32_t level, int32_t dtype, const void* x, void* y);
 
+/* y = g + (a K_k + b M_k) x: any member of the pencil whose (alpha, beta)
+ * member is A_k (eq. 1: a(w,v) = alpha (curl w, curl v) + beta (w, v)), with
+ * K_k the alpha-free curl-curl matrix and M_k the mass matrix of level k.
+ * An implicit Maxwell step (Sec. 1, eq. (Maxwell timestep)) forms its
+ * right-hand side from the two previous time levels with two such calls.
+ * g may be NULL (then y = (a K_k + b M_k) x).  x, g, y: N(n_k) [x nrhs]
+ * vectors of dtype, caller-owned device memory, 16-byte aligned; y may alias
+ * g but not x.  Asynchronous on the handle's stream.  Errors: INVALID_ARG
+ * (level, dtype, pointers, aliasing, non-finite a or b), CUDA_ERROR. */
+int ndmg_pencil(ndmg_t* h, int32_t level, int32_t dtype, double a, double b, const void* g, const void* x, void* y);
+
+/* y = a x + b y elementwise over all nrhs right-hand sides of level k (y is
+ * not read when b = 0).  No counterpart in the paper: the vector update that
+ * time-stepping drivers need between solves (warm-start extrapolation).
+ * Pointers as for ndmg_pencil; x may alias y.  Errors: INVALID_ARG, CUDA_ERROR. */
+int ndmg_axpby(ndmg_t* h, int32_t level, int32_t dtype, double a, const void* x, double b, void* y);
+
 /* r = g - A_k z. */
 int ndmg_residual(ndmg_t* h, int32_t level, int32_t dtype, const void* g, const void* z, void* r);
 

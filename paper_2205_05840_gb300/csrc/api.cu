@@ -129,6 +129,17 @@ void op_apply(ndmg_t* h, int k, const T* x, T* y) {
   launch_stencil<T>(h->stream, h->sm_count, L.n, L.cK, L.cM, x, (const T*)nullptr, y, nrhs(h));
 }
 
+// y = g + (a K + b M) x (or (a K + b M) x when g is null): the stencil in
+// residual form with the pencil's coefficients negated
+template <typename T>
+void op_pencil(ndmg_t* h, int k, double a, double b, const T* g, const T* x, T* y) {
+  DevLevel& L = h->lv[k];
+  const double hk = L.h, h3 = hk * hk * hk;
+  Span sp(h, NDMG_K_STENCIL, (g ? 3.0 : 2.0) * sizeof(T) * L.N * nrhs(h));
+  if (g) launch_stencil<T>(h->stream, h->sm_count, L.n, -a * hk, -b * h3, x, g, y, nrhs(h));
+  else launch_stencil<T>(h->stream, h->sm_count, L.n, a * hk, b * h3, x, (const T*)nullptr, y, nrhs(h));
+}
+
 bool edge_smoother(const ndmg_t* h) { return h->o.smoother == NDMG_SMOOTHER_EDGE; }
 
 // sum_E J_E A_E^{-1} J_E^t r of eq. (Preconditioner E): one launch per
@@ -174,13 +185,14 @@ void op_smoother<float>(ndmg_t* h, int k, const float* r, float* z) {
     return;
   }
   if (mixed(h) && L.Wtc) {
-    // one tensor-core kernel for both terms (Gram form: two 108x60 products
-    // per patch; the 6x6 interior solves ride along).  Algorithmic bytes:
-    // read r, read and write z (FP32); 25,920 flops per patch is ~86 flop/B,
-    // below the bf16 ridge of ~256 flop/B, so the kernel is memory-bound.
-    Span sp(h, NDMG_K_PATCH, 12.0 * L.N * R);
-    launch_tc_smoother(h->stream, L.n, L.Wtc, L.AinvT32, h->o.precision == NDMG_PREC_MIXED_FP16, h->o.eta, r, z,
-                       h->status, R);
+    // vertex patches on tensor cores (Gram form: two 108x60 products per
+    // patch), then one gather per edge that also adds the interior 6x6
+    // solves.  Algorithmic bytes of the pair: read r, read and write z
+    // (FP32); 25,920 flops per patch is ~86 flop/B, below the bf16 ridge of
+    // ~256 flop/B, so the work is memory-bound.
+    Span sp(h, NDMG_K_PATCH, 12.0 * L.N * R, 2);
+    launch_tc_patches(h->stream, L.n, L.Wtc, h->o.precision == NDMG_PREC_MIXED_FP16, r, L.ypatch, h->status, R);
+    launch_vertex_gather(h->stream, L.n, L.ypatch, L.AinvT32, h->o.eta, r, z, R);
     return;
   }
   {
@@ -602,6 +614,7 @@ void free_handle(ndmg_t* h) {
     cudaFree(L.AinvT64); cudaFree(L.AinvT32); cudaFree(L.Dv64); cudaFree(L.Dv32);
     cudaFree(L.De64); cudaFree(L.De32);
     cudaFree(L.Wtc);
+    cudaFree(L.ypatch);
   }
   cudaFree(h->Ainv0);
   for (int i = 0; i < 6; ++i) { cudaFree(h->w64[i]); cudaFree(h->w32[i]); }
@@ -638,6 +651,11 @@ int build_operators(ndmg_t* h) {
       if (mixed(h)) {
         cudaError_t e = upload_tc_operand(&L.Wtc, ops.Wv, o.precision == NDMG_PREC_MIXED_FP16);
         if (e != cudaSuccess) return cuda_fail(h, e, "upload_tc_operand");
+        if (!L.ypatch) {
+          const int64_t ny = tc_patch_buffer_floats(L.n) * o.nrhs;
+          e = cudaMalloc((void**)&L.ypatch, sizeof(float) * (ny > 0 ? ny : 1));
+          if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc(ypatch)");
+        }
       }
     }
     std::vector<double> inv = coarse_inverse(h->lv[0].n, o.L, o.alpha, o.beta);
@@ -810,6 +828,34 @@ int ndmg_residual(ndmg_t* h, int32_t level, int32_t dtype, const void* g, const 
   if ((st = check_level(h, level, false)) || (st = check_dtype(h, dtype)) || (st = check_ptrs(h, {g, z, r}))) return st;
   if (dtype == NDMG_F64) op_residual<double>(h, level, (const double*)g, (const double*)z, (double*)r);
   else op_residual<float>(h, level, (const float*)g, (const float*)z, (float*)r);
+  NDMG_CK_LAUNCH();
+  return NDMG_OK;
+}
+
+int ndmg_pencil(ndmg_t* h, int32_t level, int32_t dtype, double a, double b, const void* g, const void* x, void* y) {
+  if (!h) return NDMG_INVALID_ARG;
+  int st;
+  if ((st = check_level(h, level, false)) || (st = check_dtype(h, dtype)) || (st = check_ptrs(h, {x, y}))) return st;
+  if (g && (st = check_ptrs(h, {g}))) return st;
+  if (x == y) return fail(h, NDMG_INVALID_ARG, "y must not alias x");
+  if (!std::isfinite(a) || !std::isfinite(b)) return fail(h, NDMG_INVALID_ARG, "a and b must be finite");
+  if (dtype == NDMG_F64) op_pencil<double>(h, level, a, b, (const double*)g, (const double*)x, (double*)y);
+  else op_pencil<float>(h, level, a, b, (const float*)g, (const float*)x, (float*)y);
+  NDMG_CK_LAUNCH();
+  return NDMG_OK;
+}
+
+int ndmg_axpby(ndmg_t* h, int32_t level, int32_t dtype, double a, const void* x, double b, void* y) {
+  if (!h) return NDMG_INVALID_ARG;
+  int st;
+  if ((st = check_level(h, level, false)) || (st = check_dtype(h, dtype)) || (st = check_ptrs(h, {x, y}))) return st;
+  if (!std::isfinite(a) || !std::isfinite(b)) return fail(h, NDMG_INVALID_ARG, "a and b must be finite");
+  const int64_t N = h->lv[level].N * nrhs(h);
+  {
+    Span sp(h, NDMG_K_BLAS, (b == 0.0 ? 2.0 : 3.0) * (dtype == NDMG_F64 ? 8 : 4) * N);
+    if (dtype == NDMG_F64) launch_axpby_scalar<double>(h->stream, h->sm_count, N, a, (const double*)x, b, (double*)y);
+    else launch_axpby_scalar<float>(h->stream, h->sm_count, N, a, (const float*)x, b, (float*)y);
+  }
   NDMG_CK_LAUNCH();
   return NDMG_OK;
 }

@@ -32,19 +32,19 @@ __device__ __forceinline__ bool in_node(int p, int n) { return (unsigned)(p - 1)
 //   cy(i,j,k) = ux(i,j,k+1) - ux(i,j,k) - uz(i+1,j,k) + uz(i,j,k)
 //   cz(i,j,k) = uy(i+1,j,k) - uy(i,j,k) - ux(i,j+1,k) + ux(i,j,k)
 // ---------------------------------------------------------------------------
-// Tiled variant: one CTA owns TX x TY x TZ cells (the edges whose lowest node
-// is in the tile, all three directions).  u is staged once on the tile plus a
-// one-cell halo and g on the tile, all with asynchronous copies (zero fill
-// outside the box, which is exactly the boundary condition); the three
-// face-circulation arrays are computed once in shared memory, and every output
-// then reads 4 circulation triples (face mass along the normal) and a 3x3
-// edge-mass stencil from shared memory.
-constexpr int kTX = 32, kTY = 8, kTZ = 8;
-constexpr int kEX = kTX + 2, kEY = kTY + 2, kEZ = kTZ + 2;
-constexpr int kE3 = kEX * kEY * kEZ;
-constexpr int kT3 = kTX * kTY * kTZ;
-
-__device__ __forceinline__ int eidx(int a, int b, int c) { return (c * kEY + b) * kEX + a; }  // halo-shifted coords
+// Streaming variant: one CTA owns a column of TX x TY cells and walks a chunk
+// of KZ planes along z (the edges whose lowest node is in the column).  Per
+// plane it needs u on that plane and the next one (tile plus a one-cell halo
+// in x and y), so u sits in a ring of three shared-memory planes and the next
+// plane is staged with asynchronous copies (zero fill outside the box, which
+// is exactly the boundary condition) while the current one is consumed; g is
+// staged one plane ahead as well.  The three face-circulation planes are
+// formed once per step in shared memory; the face mass along z and the edge
+// mass across x- and y-edges, which span three planes, are carried in
+// registers from one plane to the next.
+constexpr int kTX = 32, kTY = 8;
+constexpr int kPX = kTX + 2, kPY = kTY + 2, kP = kPX * kPY;  // one staged plane
+constexpr int kTP = kTX * kTY;                               // outputs per plane
 
 // asynchronous copy of one element global -> shared; zero fill when !valid
 template <typename T>
@@ -58,146 +58,148 @@ __device__ __forceinline__ void cp_async_elem(T* dst, const T* src, bool valid, 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kTX * kTY) k_stencil_tiled(int n, T cK, T cM, const T* __restrict__ u,
-                                                             const T* __restrict__ g, T* __restrict__ y) {
+__global__ void __launch_bounds__(kTX * kTY) k_stencil_stream(int n, int KZ, T cK, T cM, const T* __restrict__ u,
+                                                              const T* __restrict__ g, T* __restrict__ y) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* Ux = reinterpret_cast<T*>(smem_raw);
-  T* Uy = Ux + kE3;
-  T* Uz = Uy + kE3;
-  T* Cx = Uz + kE3;
-  T* Cy = Cx + kE3;
-  T* Cz = Cy + kE3;
-  T* G = Cz + kE3;  // 3 x kT3 (only when g != nullptr)
+  T* Ur = reinterpret_cast<T*>(smem_raw);  // [3 ring slots][x, y, z][kP]
+  T* Cx = Ur + 9 * kP;                     // circulations of the current step
+  T* Cy = Cx + kP;
+  T* Cz = Cy + kP;
+  T* Gr = Cz + kP;                         // [2 ring slots][x, y, z][kTP]
   const int64_t N3 = (int64_t)n * (n - 1) * (n - 1);
-  // grid z = (k tiles) x (right-hand sides); each right-hand side is a
+  // grid z = (z chunks) x (right-hand sides); each right-hand side is a
   // contiguous canonical vector
-  const int nzt = (n + kTZ - 1) / kTZ;
-  const int rhs = blockIdx.z / nzt;
+  const int nzc = (n + KZ - 1) / KZ;
+  const int rhs = blockIdx.z / nzc;
   u += (int64_t)rhs * 3 * N3;
   y += (int64_t)rhs * 3 * N3;
   if (g) g += (int64_t)rhs * 3 * N3;
-  const int i0 = blockIdx.x * kTX, j0 = blockIdx.y * kTY, k0 = (blockIdx.z - rhs * nzt) * kTZ;
+  const int i0 = blockIdx.x * kTX, j0 = blockIdx.y * kTY, k0 = (blockIdx.z - rhs * nzc) * KZ;
+  const int T_out = min(KZ, n - k0);  // output planes k0 .. k0 + T_out - 1
   const int tid = threadIdx.y * kTX + threadIdx.x;
-  const T* ux = u;
-  const T* uy = u + N3;
-  const T* uz = u + 2 * N3;
-  // 1. stage u on [i0-1, i0+TX] x [j0-1, j0+TY] x [k0-1, k0+TZ] and g on the
-  //    tile, one warp per row along i (row offsets computed once per row;
-  //    offsets within one direction fit in 32 bits for n <= 1290)
   const int warp = tid >> 5, lane = tid & 31;
   const int n1 = n - 1;
-  for (int row = warp; row < kEY * kEZ; row += kTY) {
-    const int b = row % kEY, c = row / kEY;
-    const int j = j0 + b - 1, k = k0 + c - 1;
+  // stage u on plane k, [i0-1, i0+TX] x [j0-1, j0+TY], into ring slot `slot`
+  // (one warp per row along i; offsets within one direction fit in 32 bits
+  // for n <= 1290)
+  auto stage_u = [&](int k, int slot) {
+    T* Sx = Ur + slot * 3 * kP;
+    const bool kn = in_node(k, n), ks = in_seg(k, n);
+    for (int b = warp; b < kPY; b += kTY) {
+      const int j = j0 + b - 1;
+      const bool jn = in_node(j, n), js = in_seg(j, n);
+      const uint32_t rx = ((uint32_t)(k - 1) * n1 + (j - 1)) * n;  // + i
+      const uint32_t ry = ((uint32_t)(k - 1) * n + j) * n1 - 1;    // + i
+      const uint32_t rz = ((uint32_t)k * n1 + (j - 1)) * n1 - 1;   // + i
+      for (int a = lane; a < kPX; a += 32) {
+        const int i = i0 + a - 1;
+        const int q = b * kPX + a;
+        const bool vx = in_seg(i, n) && jn && kn;
+        const bool vy = in_node(i, n) && js && kn;
+        const bool vz = in_node(i, n) && jn && ks;
+        cp_async_elem(Sx + q, u + (vx ? rx + i : 0), vx, u);
+        cp_async_elem(Sx + kP + q, u + N3 + (vy ? ry + i : 0), vy, u);
+        cp_async_elem(Sx + 2 * kP + q, u + 2 * N3 + (vz ? rz + i : 0), vz, u);
+      }
+    }
+  };
+  // stage g on plane k of the tile into ring slot `slot` (row = warp)
+  auto stage_g = [&](int k, int slot) {
+    T* Sg = Gr + slot * 3 * kTP;
+    const int j = j0 + warp, i = i0 + lane;
     const bool jn = in_node(j, n), js = in_seg(j, n), kn = in_node(k, n), ks = in_seg(k, n);
-    const uint32_t rx = ((uint32_t)(k - 1) * n1 + (j - 1)) * n;      // + i
-    const uint32_t ry = ((uint32_t)(k - 1) * n + j) * n1 - 1;        // + i
-    const uint32_t rz = ((uint32_t)k * n1 + (j - 1)) * n1 - 1;       // + i
-    for (int a = lane; a < kEX; a += 32) {
-      const int i = i0 + a - 1;
-      const int q = row * kEX + a;
-      const bool vx = in_seg(i, n) && jn && kn;
-      const bool vy = in_node(i, n) && js && kn;
-      const bool vz = in_node(i, n) && jn && ks;
-      cp_async_elem(Ux + q, ux + (vx ? rx + i : 0), vx, u);
-      cp_async_elem(Uy + q, uy + (vy ? ry + i : 0), vy, u);
-      cp_async_elem(Uz + q, uz + (vz ? rz + i : 0), vz, u);
-    }
-  }
-  if (g) {
-    for (int row = warp; row < kTY * kTZ; row += kTY) {
-      const int b = row % kTY, c = row / kTY;
-      const int j = j0 + b, k = k0 + c;
-      const int i = i0 + lane;
-      const int q = row * kTX + lane;
-      const bool jn = in_node(j, n), js = in_seg(j, n), kn = in_node(k, n), ks = in_seg(k, n);
-      const bool vx = in_seg(i, n) && jn && kn;
-      const bool vy = in_node(i, n) && js && kn;
-      const bool vz = in_node(i, n) && jn && ks;
-      const uint32_t ox = vx ? ((uint32_t)(k - 1) * n1 + (j - 1)) * n + i : 0;
-      const uint32_t oy = vy ? ((uint32_t)(k - 1) * n + j) * n1 + i - 1 : 0;
-      const uint32_t oz = vz ? ((uint32_t)k * n1 + (j - 1)) * n1 + i - 1 : 0;
-      cp_async_elem(G + q, g + ox, vx, g);
-      cp_async_elem(G + kT3 + q, g + N3 + oy, vy, g);
-      cp_async_elem(G + 2 * kT3 + q, g + 2 * N3 + oz, vz, g);
-    }
-  }
-  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
-  __syncthreads();
-  // 2. face circulations wherever their four edges are staged (row-wise)
-  for (int row = warp; row < kEY * kEZ; row += kTY) {
-    const int b = row % kEY, c = row / kEY;
-    const bool hb = b + 1 < kEY, hc = c + 1 < kEZ;
-    for (int a = lane; a < kEX; a += 32) {
-      const int q = row * kEX + a;
-      const bool ha = a + 1 < kEX;
-      // cx(i,j,k) = uz(i,j+1,k) - uz(i,j,k) - uy(i,j,k+1) + uy(i,j,k)
-      Cx[q] = (hb && hc) ? Uz[q + kEX] - Uz[q] - Uy[q + kEX * kEY] + Uy[q] : T(0);
-      // cy(i,j,k) = ux(i,j,k+1) - ux(i,j,k) - uz(i+1,j,k) + uz(i,j,k)
-      Cy[q] = (ha && hc) ? Ux[q + kEX * kEY] - Ux[q] - Uz[q + 1] + Uz[q] : T(0);
-      // cz(i,j,k) = uy(i+1,j,k) - uy(i,j,k) - ux(i,j+1,k) + ux(i,j,k)
-      Cz[q] = (ha && hb) ? Uy[q + 1] - Uy[q] - Ux[q + kEX] + Ux[q] : T(0);
-    }
-  }
-  __syncthreads();
-  // 3. outputs: thread (tx, ty) walks its column over the tile's k range,
-  //    carrying the plane-(c-1) face-mass values and the partial mass sums
-  //    in registers from one plane to the next
+    const bool vx = in_seg(i, n) && jn && kn;
+    const bool vy = in_node(i, n) && js && kn;
+    const bool vz = in_node(i, n) && jn && ks;
+    const uint32_t ox = vx ? ((uint32_t)(k - 1) * n1 + (j - 1)) * n + i : 0;
+    const uint32_t oy = vy ? ((uint32_t)(k - 1) * n + j) * n1 + i - 1 : 0;
+    const uint32_t oz = vz ? ((uint32_t)k * n1 + (j - 1)) * n1 + i - 1 : 0;
+    cp_async_elem(Sg + tid, g + ox, vx, g);
+    cp_async_elem(Sg + kTP + tid, g + N3 + oy, vy, g);
+    cp_async_elem(Sg + 2 * kTP + tid, g + 2 * N3 + oz, vz, g);
+  };
+  // u plane p of the chunk is z = k0 - 1 + p, held in ring slot p % 3
+  stage_u(k0 - 1, 0);
+  asm volatile("cp.async.commit_group;" ::: "memory");
+
   const T w6 = T(1.0 / 6.0), w23 = T(2.0 / 3.0);
   const int a = threadIdx.x + 1, b = threadIdx.y + 1;
   const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
-  constexpr int P = kEX * kEY;  // plane stride
-  const int q0 = eidx(a, b, 0);
+  const int q = b * kPX + a;
   auto f3 = [&](T m, T c0, T p1) { return w6 * (m + p1) + w23 * c0; };
-  // face mass along x / y at column (a,b) and its neighbours, plane c
-  auto Xf = [&](int q) { return f3(Cx[q - 1], Cx[q], Cx[q + 1]); };
-  auto Yf = [&](int q) { return f3(Cy[q - kEX], Cy[q], Cy[q + kEX]); };
-  // mass rows across the edge, in the plane: x-edges vary in y, y-edges in x
-  auto rowX = [&](int q) { return f3(Ux[q - kEX], Ux[q], Ux[q + kEX]); };
-  auto rowY = [&](int q) { return f3(Uy[q - 1], Uy[q], Uy[q + 1]); };
-  // rolling state at plane c-1 / c / c+1
-  T yf_prev = Yf(q0), xf_prev = Xf(q0);                       // Yf(a,b,0), Xf(a,b,0)
-  T cz0[3] = {Cz[q0], Cz[q0 - kEX], Cz[q0 - 1]};             // Cz at (a,b), (a,b-1), (a-1,b), plane 0
-  T cz1[3] = {Cz[q0 + P], Cz[q0 + P - kEX], Cz[q0 + P - 1]};  // plane 1
-  T rx0 = rowX(q0), rx1 = rowX(q0 + P), ry0 = rowY(q0), ry1 = rowY(q0 + P);
-#pragma unroll 2
-  for (int kk = 0; kk < kTZ; ++kk) {
-    const int c = kk + 1, k = k0 + kk;
-    const int q = q0 + c * P;
-    const int t = (kk * kTY + threadIdx.y) * kTX + threadIdx.x;
-    const T cz2[3] = {Cz[q + P], Cz[q + P - kEX], Cz[q + P - 1]};
-    const T zf = f3(cz0[0], cz1[0], cz2[0]);     // Zf(a, b, c)
-    const T zf_b = f3(cz0[1], cz1[1], cz2[1]);   // Zf(a, b-1, c)
-    const T zf_a = f3(cz0[2], cz1[2], cz2[2]);   // Zf(a-1, b, c)
-    const T yf = Yf(q), xf = Xf(q);
-    const T rx2 = rowX(q + P), ry2 = rowY(q + P);
-    if (in_seg(i, n) && in_node(j, n) && in_node(k, n)) {
-      const T kv = -yf + yf_prev + zf - zf_b;
-      const T v = cK * kv + cM * f3(rx0, rx1, rx2);
-      y[off_x(n, i, j, k)] = g ? G[t] - v : v;
+  // face mass along x / y of the current plane at (a,b) and its neighbours
+  auto Xf = [&](int r) { return f3(Cx[r - 1], Cx[r], Cx[r + 1]); };
+  auto Yf = [&](int r) { return f3(Cy[r - kPX], Cy[r], Cy[r + kPX]); };
+  // rolling state: Cz at (a,b), (a,b-1), (a-1,b) and the in-plane edge-mass
+  // rows of x- and y-edges, for planes k-1 (0) and k (1); Xf, Yf of plane k-1
+  T cz0[3] = {T(0), T(0), T(0)}, cz1[3] = {T(0), T(0), T(0)};
+  T rx0 = T(0), rx1 = T(0), ry0 = T(0), ry1 = T(0), yf_prev = T(0), xf_prev = T(0);
+  // step t forms the circulations of the current plane k0 + t (x- and
+  // y-normal faces, t >= -1), those of the z-normal faces on the next plane
+  // k0 + t + 1 and the next plane's edge-mass rows; outputs for t >= 0
+  for (int t = -2; t < T_out; ++t) {
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();  // plane t+2 and g(t) landed; step t-1 is done with the ring
+    if (t + 2 <= T_out) stage_u(k0 + t + 2, (t + 3) % 3);
+    if (g && t + 1 >= 0 && t + 1 < T_out) stage_g(k0 + t + 1, (t + 1) & 1);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    const T* Uc = Ur + ((t + 4) % 3) * 3 * kP;  // plane k0 + t
+    const T* Un = Ur + ((t + 2) % 3) * 3 * kP;  // plane k0 + t + 1
+    for (int r = tid; r < kP; r += kTP) {
+      const int ra = r % kPX, rb = r / kPX;
+      const bool ha = ra + 1 < kPX, hb = rb + 1 < kPY;
+      if (t >= -1) {
+        // cx(i,j,k) = uz(i,j+1,k) - uz(i,j,k) - uy(i,j,k+1) + uy(i,j,k)
+        Cx[r] = hb ? Uc[2 * kP + r + kPX] - Uc[2 * kP + r] - Un[kP + r] + Uc[kP + r] : T(0);
+        // cy(i,j,k) = ux(i,j,k+1) - ux(i,j,k) - uz(i+1,j,k) + uz(i,j,k)
+        Cy[r] = ha ? Un[r] - Uc[r] - Uc[2 * kP + r + 1] + Uc[2 * kP + r] : T(0);
+      }
+      // cz(i,j,k+1) = uy(i+1,j,k+1) - uy(i,j,k+1) - ux(i,j+1,k+1) + ux(i,j,k+1)
+      Cz[r] = (ha && hb) ? Un[kP + r + 1] - Un[kP + r] - Un[r + kPX] + Un[r] : T(0);
     }
-    if (in_node(i, n) && in_seg(j, n) && in_node(k, n)) {
-      const T kv = -zf + zf_a + xf - xf_prev;
-      const T v = cK * kv + cM * f3(ry0, ry1, ry2);
-      y[N3 + off_y(n, i, j, k)] = g ? G[kT3 + t] - v : v;
+    __syncthreads();
+    const T cz2[3] = {Cz[q], Cz[q - kPX], Cz[q - 1]};
+    const T rx2 = f3(Un[q - kPX], Un[q], Un[q + kPX]);               // x-edges vary in y
+    const T ry2 = f3(Un[kP + q - 1], Un[kP + q], Un[kP + q + 1]);    // y-edges vary in x
+    if (t >= -1) {
+      const T yf = Yf(q), xf = Xf(q);
+      if (t >= 0) {
+        const int k = k0 + t;
+        const T* G = Gr + (t & 1) * 3 * kTP;
+        const T zf = f3(cz0[0], cz1[0], cz2[0]);    // Zf(a, b, k)
+        const T zf_b = f3(cz0[1], cz1[1], cz2[1]);  // Zf(a, b-1, k)
+        const T zf_a = f3(cz0[2], cz1[2], cz2[2]);  // Zf(a-1, b, k)
+        if (in_seg(i, n) && in_node(j, n) && in_node(k, n)) {
+          const T kv = -yf + yf_prev + zf - zf_b;
+          const T v = cK * kv + cM * f3(rx0, rx1, rx2);
+          y[off_x(n, i, j, k)] = g ? G[tid] - v : v;
+        }
+        if (in_node(i, n) && in_seg(j, n) && in_node(k, n)) {
+          const T kv = -zf + zf_a + xf - xf_prev;
+          const T v = cK * kv + cM * f3(ry0, ry1, ry2);
+          y[N3 + off_y(n, i, j, k)] = g ? G[kTP + tid] - v : v;
+        }
+        if (in_node(i, n) && in_node(j, n) && in_seg(k, n)) {
+          const T* Uz = Uc + 2 * kP;
+          const T kv = -xf + Xf(q - kPX) + yf - Yf(q - 1);
+          const T mz = f3(f3(Uz[q - kPX - 1], Uz[q - 1], Uz[q + kPX - 1]), f3(Uz[q - kPX], Uz[q], Uz[q + kPX]),
+                          f3(Uz[q - kPX + 1], Uz[q + 1], Uz[q + kPX + 1]));
+          const T v = cK * kv + cM * mz;
+          y[2 * N3 + off_z(n, i, j, k)] = g ? G[2 * kTP + tid] - v : v;
+        }
+      }
+      yf_prev = yf;
+      xf_prev = xf;
     }
-    if (in_node(i, n) && in_node(j, n) && in_seg(k, n)) {
-      const T kv = -xf + Xf(q - kEX) + yf - Yf(q - 1);
-      const T mz = f3(f3(Uz[q - kEX - 1], Uz[q - 1], Uz[q + kEX - 1]), f3(Uz[q - kEX], Uz[q], Uz[q + kEX]),
-                      f3(Uz[q - kEX + 1], Uz[q + 1], Uz[q + kEX + 1]));
-      const T v = cK * kv + cM * mz;
-      y[2 * N3 + off_z(n, i, j, k)] = g ? G[2 * kT3 + t] - v : v;
-    }
-    yf_prev = yf;
-    xf_prev = xf;
 #pragma unroll
-    for (int u3 = 0; u3 < 3; ++u3) {
-      cz0[u3] = cz1[u3];
-      cz1[u3] = cz2[u3];
+    for (int c = 0; c < 3; ++c) {
+      cz0[c] = cz1[c];
+      cz1[c] = cz2[c];
     }
     rx0 = rx1; rx1 = rx2;
     ry0 = ry1; ry1 = ry2;
   }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -507,6 +509,14 @@ __global__ void __launch_bounds__(256) k_axpby(int64_t N, const double* __restri
     y[off + e] = (T)(a * (double)x[off + e] + b * (double)y[off + e]);
 }
 
+// y = a x + b y with host scalars over a whole batch (y is not read when b = 0)
+template <typename T>
+__global__ void __launch_bounds__(256) k_axpby_scalar(int64_t N, double a, const T* __restrict__ x, double b,
+                                                      T* __restrict__ y) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x)
+    y[e] = b == 0.0 ? (T)(a * (double)x[e]) : (T)(a * (double)x[e] + b * (double)y[e]);
+}
+
 // u += a p ; r -= a q with a = alpha[rhs]
 template <typename T>
 __global__ void __launch_bounds__(256) k_cg_update(int64_t N, const double* __restrict__ alpha, const T* __restrict__ p,
@@ -558,20 +568,24 @@ static inline int grid_for(int64_t work, int sm_count, int per_sm = 8) {
 }
 
 template <typename T>
-size_t stencil_smem() { return sizeof(T) * (6 * kE3 + 3 * kT3); }
+size_t stencil_smem() { return sizeof(T) * (12 * kP + 6 * kTP); }
 
 template <typename T>
 cudaError_t prepare_stencil() {
-  return cudaFuncSetAttribute(k_stencil_tiled<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stencil_smem<T>());
+  return cudaFuncSetAttribute(k_stencil_stream<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stencil_smem<T>());
 }
 
 template <typename T>
 void launch_stencil(cudaStream_t s, int sm, int n, double cK, double cM, const T* u, const T* g, T* y, int R) {
   const int64_t N = 3LL * n * (n - 1) * (n - 1);
   if (N == 0) return;
-  (void)sm;
-  dim3 grid((n + kTX - 1) / kTX, (n + kTY - 1) / kTY, ((n + kTZ - 1) / kTZ) * R);
-  k_stencil_tiled<T><<<grid, dim3(kTX, kTY), stencil_smem<T>(), s>>>(n, (T)cK, (T)cM, u, g, y);
+  // z chunk: the longest (fewest halo planes) that still gives about four
+  // CTAs per SM
+  const int64_t cols = (int64_t)((n + kTX - 1) / kTX) * ((n + kTY - 1) / kTY) * R;
+  int KZ = n;
+  while (KZ > 4 && cols * ((n + KZ - 1) / KZ) < 4LL * sm) KZ = (KZ + 1) / 2;
+  dim3 grid((n + kTX - 1) / kTX, (n + kTY - 1) / kTY, ((n + KZ - 1) / KZ) * R);
+  k_stencil_stream<T><<<grid, dim3(kTX, kTY), stencil_smem<T>(), s>>>(n, KZ, (T)cK, (T)cM, u, g, y);
 }
 
 template <typename T>
@@ -665,6 +679,12 @@ void launch_axpby(cudaStream_t s, int sm, int64_t N, const double* ab, const T* 
 }
 
 template <typename T>
+void launch_axpby_scalar(cudaStream_t s, int sm, int64_t N, double a, const T* x, double b, T* y) {
+  if (N <= 0) return;
+  k_axpby_scalar<T><<<grid_for(N, sm, 8), 256, 0, s>>>(N, a, x, b, y);
+}
+
+template <typename T>
 void launch_cg_update(cudaStream_t s, int sm, int64_t N, const double* alpha, const T* p, const T* q, T* u, T* r, int R) {
   k_cg_update<T><<<blas_grid(N, sm, R), 256, 0, s>>>(N, alpha, p, q, u, r);
 }
@@ -692,6 +712,7 @@ void launch_add_f32(cudaStream_t s, int sm, int64_t N, const double* sc, const f
   template void launch_dot2<T>(cudaStream_t, int, int64_t, const T*, const T*, const T*, const T*,    \
                                double*, double*, int);                                                \
   template void launch_axpby<T>(cudaStream_t, int, int64_t, const double*, const T*, T*, int);         \
+  template void launch_axpby_scalar<T>(cudaStream_t, int, int64_t, double, const T*, double, T*);      \
   template void launch_cg_update<T>(cudaStream_t, int, int64_t, const double*, const T*, const T*, T*, T*, int);
 NDMG_INST(double)
 NDMG_INST(float)

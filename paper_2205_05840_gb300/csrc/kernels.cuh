@@ -41,6 +41,8 @@ void launch_dot2(cudaStream_t s, int sm, int64_t N, const T* x, const T* y, cons
 template <typename T>
 void launch_axpby(cudaStream_t s, int sm, int64_t N, const double* ab, const T* x, T* y, int R);
 template <typename T>
+void launch_axpby_scalar(cudaStream_t s, int sm, int64_t N, double a, const T* x, double b, T* y);
+template <typename T>
 void launch_cg_update(cudaStream_t s, int sm, int64_t N, const double* alpha, const T* p, const T* q, T* u, T* r,
                       int R);
 void launch_to_f32(cudaStream_t s, int sm, int64_t N, const double* sc, const double* src, float* dst, int R);

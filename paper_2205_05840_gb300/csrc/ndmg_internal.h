@@ -65,6 +65,7 @@ struct DevLevel {
   double* De64 = nullptr;     // 3 * 42*42 (edge-based smoother)
   float* De32 = nullptr;
   void* Wtc = nullptr;        // tensor-core operand images (bf16/fp16), see tc kernel
+  float* ypatch = nullptr;    // per-patch outputs of the tensor-core smoother (108 x patches x R)
 };
 
 }  // namespace ndmg

@@ -1,25 +1,28 @@
-// Smoother correction of eq. (Preconditioner P) on the 5th-gen tensor cores
-// (tcgen05, sm_103a), one kernel for both additive parts:
+// Smoother correction of eq. (Preconditioner P) with the vertex-space solves
+// on the 5th-gen tensor cores (tcgen05, sm_103a):
 //
 //     z += eta * ( sum_T J_T A_T^{-1} J_T^t r  +  sum_V J_V A_V^{-1} J_V^t r ),
 //
 // with J_V A_V^{-1} J_V^t = W W^t, W the 108x60 Gram factor of the vertex
 // space operator (identical for every patch: constant alpha, uniform grid).
-// One CTA owns a brick of 8x8x8 fine cells (4x4x4 coarse elements) and
-// computes every patch that touches the brick's edges: the (4+1)^3 = 125
-// patches around its coarse vertices, one 128-row MMA tile.  Per CTA:
-//   1. stage r on the 12x12x12-cell region the patches cover (cp.async with
-//      zero fill outside the box: that is the boundary condition);
-//   2. interior-space solves of the brick's 64 coarse elements (6x6, FP32);
-//   3. gather the 125 patch vectors into A (128 x 112, bf16/fp16, K-major);
-//   4. D = A W             (tcgen05.mma M=128 N=64  K=112, FP32 in TMEM);
-//   5. A' = lowp(D)        (tcgen05.ld -> registers -> smem, over A);
-//   6. D' = A' W^t         (tcgen05.mma M=128 N=112 K=64, FP32 in TMEM, over D);
-//   7. add each patch's outputs that land on owned edges into an smem
-//      accumulator (shared atomics: up to 8 patches share an edge);
-//   8. z[owned] += eta * acc.
-// Every edge is written by exactly one CTA, so no global atomics are needed;
-// neighbouring CTAs recompute the patches on their common boundary.
+// Two kernels:
+//   k_tc_patches: every vertex patch exactly once.  One CTA takes a brick of
+//     8 x 4 x 4 interior coarse vertices (one 128-row MMA tile, neighbouring
+//     rows are neighbouring vertices along x; the brick shape keeps the staged
+//     region small enough for three CTAs per SM) and
+//       1. stages r on the cells the brick's patches cover (cp.async, zero
+//          fill outside the box = the boundary condition), split by the parity
+//          of the cell coordinates so that neighbouring patches read
+//          neighbouring words;
+//       2. gathers the 128 patch vectors into A (128 x 112, bf16/fp16, K-major);
+//       3. D = A W             (tcgen05.mma M=128 N=64  K=112, FP32 in TMEM);
+//       4. A' = lowp(D)        (tcgen05.ld -> registers -> smem, over A);
+//       5. D' = A' W^t         (tcgen05.mma M=128 N=112 K=64, FP32 in TMEM, over D);
+//       6. stores the 108 outputs of every patch to y[l][p] (coalesced along p).
+//   k_vertex_gather: one thread per lattice point and edge direction sums the
+//     (up to 8) patch outputs that belong to its edge, adds its row of the
+//     interior-space solve A_T^{-1} r_T (edges inside a coarse element) and
+//     updates z once.  No atomics, no recomputed patches.
 //
 // Operand layout (SWIZZLE_NONE, K-major canonical layout): 8-row x 16-byte
 // "core matrices" stored contiguously; core matrix (g, c) of an R x K
@@ -34,38 +37,65 @@
 namespace ndmg {
 namespace {
 
-constexpr int kB = 4;                      // coarse vertices per brick side
-constexpr int kM = 128;                    // MMA rows (125 patches + 3 empty)
+constexpr int kBX = 8, kBY = 4, kBZ = 4;   // coarse vertices per brick
+constexpr int kM = 128;                    // MMA rows = kBX * kBY * kBZ patches
+static_assert(kBX * kBY * kBZ == kM, "one MMA tile per brick");
 constexpr int kK1 = 112, kN1 = 64;         // A: 128 x 112, W: 112 x 64
 constexpr int kK2 = 64, kN2 = 112;         // A': 128 x 64, W^t: 64 x 112
-constexpr int kRE = 2 * kB + 4;            // region: 12 cells per side
-constexpr int kRN = kRE - 1;               // 11 interior node lines
-constexpr int kRegion = kRE * kRN * kRN;   // staged edges per direction
-constexpr int kOwn = 2 * kB;               // owned cells per side
-constexpr int kOwn3 = kOwn * kOwn * kOwn;  // owned edges per direction
-// accumulator layout (padded against shared-memory bank conflicts of the
-// patch scatter): slot(d, i, j, k) = d * kAccD + k * kAccK + j * kOwn + i
-constexpr int kAccK = 68, kAccD = 544;
-constexpr int kAccSize = 3 * kAccD;
 constexpr int kThreads = 256;
 constexpr uint32_t kTmemCols = 128;        // D: cols [0,64), then D': cols [0,112)
 
-// shared memory: A' aliases A (A is dead once the first MMA completed); the
-// accumulator aliases the staged region (dead once A and the interior-space
-// solves are done)
+// staged region: cells [2V0 - 2, 2(V0 + B - 1) + 2] per axis, i.e. 2B + 2
+// cells; per direction the along-axis extent counts segments (2B + 2) and
+// the across extents count node lines (2B + 1)
+constexpr int kCX = 2 * kBX + 2, kCY = 2 * kBY + 2, kCZ = 2 * kBZ + 2;
+__host__ __device__ constexpr int dir_len(int d, int axis) {
+  return (axis == 0 ? kCX : axis == 1 ? kCY : kCZ) - (axis == d ? 0 : 1);
+}
+__host__ __device__ constexpr int dir_size(int d) { return dir_len(d, 0) * dir_len(d, 1) * dir_len(d, 2); }
+constexpr int kRegionAll = dir_size(0) + dir_size(1) + dir_size(2);
+
+// octant (parity-split) layout of the staged region
+__host__ __device__ constexpr int oct_len(int L, int par) { return (L + 1 - par) / 2; }
+__host__ __device__ constexpr int oct_size(int d, int o) {
+  return oct_len(dir_len(d, 0), o & 1) * oct_len(dir_len(d, 1), (o >> 1) & 1) * oct_len(dir_len(d, 2), (o >> 2) & 1);
+}
+__host__ __device__ constexpr int oct_base(int d, int o) {
+  int base = 0;
+  for (int q = 0; q < d; ++q) base += dir_size(q);
+  for (int q = 0; q < o; ++q) base += oct_size(d, q);
+  return base;
+}
+__constant__ int kOctBase[24] = {
+    oct_base(0, 0), oct_base(0, 1), oct_base(0, 2), oct_base(0, 3), oct_base(0, 4), oct_base(0, 5), oct_base(0, 6),
+    oct_base(0, 7), oct_base(1, 0), oct_base(1, 1), oct_base(1, 2), oct_base(1, 3), oct_base(1, 4), oct_base(1, 5),
+    oct_base(1, 6), oct_base(1, 7), oct_base(2, 0), oct_base(2, 1), oct_base(2, 2), oct_base(2, 3), oct_base(2, 4),
+    oct_base(2, 5), oct_base(2, 6), oct_base(2, 7)};
+static_assert(oct_base(2, 7) + oct_size(2, 7) == kRegionAll, "octants tile the region");
+
+__host__ __device__ constexpr int region_at_c(int d, int i, int j, int k) {
+  const int o = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
+  const int PI = oct_len(dir_len(d, 0), i & 1);
+  const int PJ = PI * oct_len(dir_len(d, 1), j & 1);
+  return oct_base(d, o) + (k >> 1) * PJ + (j >> 1) * PI + (i >> 1);
+}
+__device__ __forceinline__ int region_at(int d, int i, int j, int k) {
+  const int o = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
+  const int PI = oct_len(dir_len(d, 0), i & 1);
+  const int PJ = PI * oct_len(dir_len(d, 1), j & 1);
+  return kOctBase[d * 8 + o] + (k >> 1) * PJ + (j >> 1) * PI + (i >> 1);
+}
+
+// shared memory: A' aliases A (A is dead once the first MMA completed)
 constexpr int OFF_A = 0;
-constexpr int OFF_B1 = OFF_A + kM * kK1 * 2;      // W images, contiguous
+constexpr int OFF_B1 = OFF_A + kM * kK1 * 2;  // W images, contiguous
 constexpr int OFF_B2 = OFF_B1 + kN1 * kK1 * 2;
 constexpr int OFF_R = OFF_B2 + kN2 * kK2 * 2;
-constexpr int OFF_ACC = OFF_R;
-constexpr int OFF_BUB = OFF_R + 3 * kRegion * 4;  // 64 elements x 6 interior-space results
-constexpr int OFF_BAR = OFF_BUB + 64 * 6 * 4;
+constexpr int OFF_BAR = OFF_R + ((kRegionAll * 4 + 15) / 16) * 16;
 constexpr int OFF_TM = OFF_BAR + 16;
 constexpr int OFF_RED = OFF_TM + 16;
 constexpr int kSmem = OFF_RED + 32;
 static_assert(OFF_BAR % 8 == 0, "mbarrier alignment");
-static_assert(kAccSize * 4 <= 3 * kRegion * 4 && kAccK >= kOwn * kOwn && kAccD >= kOwn * kAccK,
-              "accumulator fits in the staged region");
 static_assert(3 * (kSmem + 1024) <= 228 * 1024, "three CTAs per SM (228 KB, 1 KB reserved per CTA)");
 
 constexpr int kImgBytes = (kN1 * kK1 + kN2 * kK2) * 2;  // both W images
@@ -163,112 +193,11 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {
   }
 }
 
-// Staged region: per direction a 12 x 11 x 11 box (12 along the edges, 11
-// node lines across: x: 12x11x11, y: 11x12x11, z: 11x11x12), stored split by
-// the parity of (i, j, k) into 8 octant sub-boxes.  Patches sit two cells
-// apart, so in a plain layout the 32 patches of a warp read words an even
-// distance apart and hit only 16 banks; in the octant layout neighbouring
-// patches read neighbouring words (about half the shared-memory wavefronts).
-__host__ __device__ constexpr int dir_len(int d, int axis) { return axis == d ? kRE : kRN; }
-__host__ __device__ constexpr int oct_len(int L, int par) { return (L + 1 - par) / 2; }
-__host__ __device__ constexpr int oct_size(int d, int o) {
-  return oct_len(dir_len(d, 0), o & 1) * oct_len(dir_len(d, 1), (o >> 1) & 1) * oct_len(dir_len(d, 2), (o >> 2) & 1);
-}
-__host__ __device__ constexpr int oct_base(int d, int o) {
-  int base = d * kRegion;
-  for (int q = 0; q < o; ++q) base += oct_size(d, q);
-  return base;
-}
-__constant__ int kOctBase[24] = {
-    oct_base(0, 0), oct_base(0, 1), oct_base(0, 2), oct_base(0, 3), oct_base(0, 4), oct_base(0, 5), oct_base(0, 6),
-    oct_base(0, 7), oct_base(1, 0), oct_base(1, 1), oct_base(1, 2), oct_base(1, 3), oct_base(1, 4), oct_base(1, 5),
-    oct_base(1, 6), oct_base(1, 7), oct_base(2, 0), oct_base(2, 1), oct_base(2, 2), oct_base(2, 3), oct_base(2, 4),
-    oct_base(2, 5), oct_base(2, 6), oct_base(2, 7)};
-static_assert(oct_base(2, 7) + oct_size(2, 7) == 3 * kRegion, "octants tile the region");
-
-// staged-region index of edge (d; i, j, k) in region coordinates; with
-// literal arguments everything but the final sum constant-folds
-__host__ __device__ constexpr int region_at_c(int d, int i, int j, int k) {
-  const int o = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
-  const int PI = oct_len(dir_len(d, 0), i & 1);
-  const int PJ = PI * oct_len(dir_len(d, 1), j & 1);
-  return oct_base(d, o) + (k >> 1) * PJ + (j >> 1) * PI + (i >> 1);
-}
-// same, for run-time arguments (octant bases from a constant table)
-__device__ __forceinline__ int region_at(int d, int i, int j, int k) {
-  const int o = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
-  const int PI = oct_len(dir_len(d, 0), i & 1);
-  const int PJ = PI * oct_len(dir_len(d, 1), j & 1);
-  return kOctBase[d * 8 + o] + (k >> 1) * PJ + (j >> 1) * PI + (i >> 1);
-}
-
-// patch-local edge l in [0,108) of the patch at brick-relative vertex (a,b,c):
-// the 4x4x4 box numbering of the library (x: 4 segments x 3 x 3 nodes, then
-// y, then z), as a staged-region index
-__device__ __forceinline__ int region_index(int l, int a, int b, int c) {
-  int d, i, j, k;
-  if (l < 36) {
-    d = 0; i = l % 4; j = (l / 4) % 3; k = l / 12;
-  } else if (l < 72) {
-    l -= 36; d = 1; i = l % 3; j = (l / 3) % 4; k = l / 12;
-  } else {
-    l -= 72; d = 2; i = l % 3; j = (l / 3) % 3; k = l / 9;
-  }
-  return region_at_c(d, i + 2 * a, j + 2 * b, k + 2 * c);
-}
-
-// patch-local edge -> owned-accumulator slot (or -1 if not owned by the brick)
-__device__ __forceinline__ int owned_index(int l, int a, int b, int c) {
-  int d, i, j, k;
-  if (l < 36) {
-    d = 0; i = l % 4; j = (l / 4) % 3 + 1; k = l / 12 + 1;
-  } else if (l < 72) {
-    l -= 36; d = 1; i = l % 3 + 1; j = (l / 3) % 4; k = l / 12 + 1;
-  } else {
-    l -= 72; d = 2; i = l % 3 + 1; j = (l / 3) % 3 + 1; k = l / 9;
-  }
-  // global coordinate minus brick origin 2*(I0,J0,K0): patch origin is 2(a,b,c) - 2
-  i += 2 * a - 2; j += 2 * b - 2; k += 2 * c - 2;
-  if ((unsigned)i >= (unsigned)kOwn || (unsigned)j >= (unsigned)kOwn || (unsigned)k >= (unsigned)kOwn) return -1;
-  return d * kOwn3 + (k * kOwn + j) * kOwn + i;
-}
-
-__device__ __forceinline__ int64_t gidx(int n, int d, int i, int j, int k) {
-  const int64_t N3 = (int64_t)n * (n - 1) * (n - 1);
-  if (d == 0) return ((int64_t)(k - 1) * (n - 1) + (j - 1)) * n + i;
-  if (d == 1) return N3 + ((int64_t)(k - 1) * n + j) * (n - 1) + (i - 1);
-  return 2 * N3 + ((int64_t)k * (n - 1) + (j - 1)) * (n - 1) + (i - 1);
-}
-
-// is (i,j,k) an interior edge of direction d on an n^3 mesh?
-__device__ __forceinline__ bool interior(int n, int d, int i, int j, int k) {
-  const int p[3] = {i, j, k};
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    if (a == d) {
-      if (p[a] < 0 || p[a] >= n) return false;
-    } else if (p[a] < 1 || p[a] > n - 1) {
-      return false;
-    }
-  }
-  return true;
-}
-
-// the 6 interior-space edges of brick-relative coarse element (a,b,c), in
-// the 2x2x2 box order (x segment 0/1, then y, then z), as offsets from the
-// brick origin 2*(I0,J0,K0)
-__device__ __forceinline__ void bubble_edge(int t, int a, int b, int c, int& d, int (&p)[3]) {
-  d = t >> 1;
-  const int s = t & 1;
-  p[0] = 2 * a + 1;
-  p[1] = 2 * b + 1;
-  p[2] = 2 * c + 1;
-  p[d] = 2 * (d == 0 ? a : d == 1 ? b : c) + s;
-}
-
-// region coordinates of patch-local edge l for the patch at brick-relative
-// vertex (0,0,0) (the 4x4x4 box numbering: x: 4 segments x 3 x 3 nodes, then
-// y, then z); constant-folds for a literal l
+// Patch-local edge l in [0,108): the canonical numbering of the 4x4x4 box
+// of cells around the vertex (x: 4 segments x 3 x 3 node lines, then y, then
+// z).  Its region coordinates for brick-relative vertex (a,b,c) are the box
+// coordinates + 2(a,b,c) - (0 along the edge, 1 across); everything below
+// constant-folds for a literal l.
 __host__ __device__ constexpr int local_dir(int l) { return l < 36 ? 0 : (l < 72 ? 1 : 2); }
 __host__ __device__ constexpr int local_ri(int l) { return l < 36 ? l % 4 : (l < 72 ? (l - 36) % 3 : (l - 72) % 3); }
 __host__ __device__ constexpr int local_rj(int l) {
@@ -307,62 +236,44 @@ __device__ __forceinline__ void gather_chunks(const float* R, uint8_t* A, int p,
   }
 }
 
-// box coordinates (direction, i, j, k) of patch-local edge l in the 4x4x4
-// numbering; constant-folds for a literal l
-__device__ __forceinline__ void local_box(int l, int& d, int& i, int& j, int& k) {
-  if (l < 36) {
-    d = 0; i = l % 4; j = (l / 4) % 3 + 1; k = l / 12 + 1;
-  } else if (l < 72) {
-    l -= 36; d = 1; i = l % 3 + 1; j = (l / 3) % 4; k = l / 12 + 1;
-  } else {
-    l -= 72; d = 2; i = l % 3 + 1; j = (l / 3) % 3 + 1; k = l / 9;
-  }
-}
-
-// add the 16 outputs l = CB..CB+15 of patch (a,b,c) that land on edges owned
-// by the brick into the accumulator; owned coordinates are box + 2(a,b,c) - 2
-template <int CB>
-__device__ __forceinline__ void scatter16(float* ACC, const float (&v)[16], int a, int b, int c) {
-  const int pbase = 2 * a + 2 * kOwn * b + 2 * kAccK * c - (2 + 2 * kOwn + 2 * kAccK);
+__device__ __forceinline__ bool interior(int n, int d, int i, int j, int k) {
+  const int p[3] = {i, j, k};
 #pragma unroll
-  for (int t = 0; t < 16; ++t) {
-    const int l = CB + t;
-    if (l < 108) {
-      int d, i, j, k;
-      local_box(l, d, i, j, k);
-      const int oi = i + 2 * a - 2, oj = j + 2 * b - 2, ok = k + 2 * c - 2;
-      if ((unsigned)oi < (unsigned)kOwn && (unsigned)oj < (unsigned)kOwn && (unsigned)ok < (unsigned)kOwn)
-        atomicAdd(ACC + d * kAccD + k * kAccK + j * kOwn + i + pbase, v[t]);
+  for (int a = 0; a < 3; ++a) {
+    if (a == d) {
+      if (p[a] < 0 || p[a] >= n) return false;
+    } else if (p[a] < 1 || p[a] > n - 1) {
+      return false;
     }
   }
+  return true;
 }
 
+// y[l * P + p] (per right-hand side) = (W W^t r_p)_l for every interior
+// vertex p = ((K-1) nv + (J-1)) nv + (I-1), nv = n/2 - 1
 template <bool FP16>
 __global__ void __launch_bounds__(kThreads, 3)
-    k_tc_smoother(int n, const uint8_t* __restrict__ img, const float* __restrict__ AinvT, float eta,
-                  const float* __restrict__ r, float* __restrict__ z, int* __restrict__ status) {
+    k_tc_patches(int n, const uint8_t* __restrict__ img, const float* __restrict__ r, float* __restrict__ y,
+                 int* __restrict__ status) {
   extern __shared__ __align__(128) uint8_t smem[];
   // a CTA of an earlier launch gave up on a wait: do nothing until the host
   // has read and cleared the status word
   if (*reinterpret_cast<volatile int*>(status) != 0) return;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nc = n / 2;
-  const int nbr = (nc + kB - 1) / kB;
-  // grid = bricks x right-hand sides (each a contiguous canonical vector)
-  const int rhs = blockIdx.x / (nbr * nbr * nbr);
-  const int brick = blockIdx.x - rhs * nbr * nbr * nbr;
-  const int bx = brick % nbr, by = (brick / nbr) % nbr, bz = brick / (nbr * nbr);
-  {
-    const int64_t off = (int64_t)rhs * 3 * (int64_t)n * (n - 1) * (n - 1);
-    r += off;
-    z += off;
-  }
-  const int I0 = bx * kB, J0 = by * kB, K0 = bz * kB;
+  const int nv = n / 2 - 1;
+  const int nbx = (nv + kBX - 1) / kBX, nby = (nv + kBY - 1) / kBY, nbz = (nv + kBZ - 1) / kBZ;
+  const int nbr = nbx * nby * nbz;
+  const int rhs = blockIdx.x / nbr;
+  const int brick = blockIdx.x - rhs * nbr;
+  const int bx = brick % nbx, by = (brick / nbx) % nby, bz = brick / (nbx * nby);
+  const int VX = 1 + bx * kBX, VY = 1 + by * kBY, VZ = 1 + bz * kBZ;  // first vertex of the brick
+  const uint32_t n1 = n - 1, N3 = (uint32_t)n * n1 * n1;            // < 2^31 (checked on the host)
+  const int64_t P = (int64_t)nv * nv * nv;
+  r += (int64_t)rhs * 3 * N3;
+  y += (int64_t)rhs * 108 * P;
 
   float* R = reinterpret_cast<float*>(smem + OFF_R);
-  float* ACC = reinterpret_cast<float*>(smem + OFF_ACC);
-  float* BUB = reinterpret_cast<float*>(smem + OFF_BUB);
   const uint32_t bar0 = smem_u32(smem + OFF_BAR), bar1 = bar0 + 8;
   uint32_t* tm_slot = reinterpret_cast<uint32_t*>(smem + OFF_TM);
   float* red = reinterpret_cast<float*>(smem + OFF_RED);
@@ -379,21 +290,18 @@ __global__ void __launch_bounds__(kThreads, 3)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar1), "r"(1) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // 1. r on the region: x-edges from (2I0-2, 2J0-1, 2K0-1), y-edges from
-  //    (2I0-1, 2J0-2, 2K0-1), z-edges from (2I0-1, 2J0-1, 2K0-2)
+  // 1. r on the region: edges of direction d start at global coordinates
+  //    2V0 - 2 along d and 2V0 - 1 across
   {
     const uint32_t rbase = smem_u32(R);
-    const int n1 = n - 1;
-    const uint32_t N3 = (uint32_t)n * n1 * n1;   // < 2^31 for the supported n (checked on the host)
-    for (int q = tid; q < 3 * kRegion; q += kThreads) {
-      const int d = q >= 2 * kRegion ? 2 : (q >= kRegion ? 1 : 0);
-      const int e = q - d * kRegion;
-      // region extents: along-axis 12 segments, 11 node lines across
-      const int Li = d == 0 ? kRE : kRN, Lj = d == 1 ? kRE : kRN;
+    for (int q = tid; q < kRegionAll; q += kThreads) {
+      const int d = q >= dir_size(0) + dir_size(1) ? 2 : (q >= dir_size(0) ? 1 : 0);
+      const int e = q - (d == 0 ? 0 : d == 1 ? dir_size(0) : dir_size(0) + dir_size(1));
+      const int Li = dir_len(d, 0), Lj = dir_len(d, 1);
       const int i = e % Li, jk = e / Li, j = jk % Lj, k = jk / Lj;
-      const int gi = 2 * I0 + i - (d == 0 ? 2 : 1);
-      const int gj = 2 * J0 + j - (d == 1 ? 2 : 1);
-      const int gk = 2 * K0 + k - (d == 2 ? 2 : 1);
+      const int gi = 2 * VX + i - (d == 0 ? 2 : 1);
+      const int gj = 2 * VY + j - (d == 1 ? 2 : 1);
+      const int gk = 2 * VZ + k - (d == 2 ? 2 : 1);
       const bool in = interior(n, d, gi, gj, gk);
       uint32_t off = 0;
       if (in) {
@@ -419,7 +327,7 @@ __global__ void __launch_bounds__(kThreads, 3)
   float rscale = 1.f;
   if constexpr (FP16) {
     float amax = 0.f;
-    for (int q = tid; q < 3 * kRegion; q += kThreads) amax = fmaxf(amax, fabsf(R[q]));
+    for (int q = tid; q < kRegionAll; q += kThreads) amax = fmaxf(amax, fabsf(R[q]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
     if (lane == 0) red[warp] = amax;
@@ -430,34 +338,11 @@ __global__ void __launch_bounds__(kThreads, 3)
     if (m > 0.f) rscale = exp2f(-ceilf(log2f(m)));
   }
 
-  // ---- 2. interior spaces of the brick's 64 coarse elements (FP32) ----------
-  if (tid < kB * kB * kB) {
-    const int a = tid % kB, b = (tid / kB) % kB, c = tid / (kB * kB);
-    float rv[6];
-#pragma unroll
-    for (int t = 0; t < 6; ++t) {
-      int d, p[3];
-      bubble_edge(t, a, b, c, d, p);
-      // brick-relative -> region coordinates: region origin sits 2 (along the
-      // edge) or 1 (across it) cells below the brick origin
-      rv[t] = R[region_at(d, p[0] + (d == 0 ? 2 : 1), p[1] + (d == 1 ? 2 : 1), p[2] + (d == 2 ? 2 : 1))];
-    }
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-      float acc = 0.f;
-#pragma unroll
-      for (int w = 0; w < 6; ++w) acc += __ldg(AinvT + q * 6 + w) * rv[w];
-      BUB[tid * 6 + q] = acc;
-    }
-  }
-
-  // ---- 3. gather the patch vectors into A (two threads per row; the loops
-  //         are unrolled so every patch-local offset is a compile-time constant)
+  // ---- 2. gather the patch vectors into A (two threads per row) --------------
   {
     const int p = tid & (kM - 1), half = tid >> 7;
-    const int a = p % 5, b = (p / 5) % 5, c = p / 25;
-    const bool live = p < 125 && (I0 + a) >= 1 && (I0 + a) <= nc - 1 && (J0 + b) >= 1 && (J0 + b) <= nc - 1 &&
-                      (K0 + c) >= 1 && (K0 + c) <= nc - 1;
+    const int a = p % kBX, b = (p / kBX) % kBY, c = p / (kBX * kBY);
+    const bool live = VX + a <= nv && VY + b <= nv && VZ + c <= nv;
     uint8_t* A = smem + OFF_A;
     if (half == 0)
       gather_chunks<0, FP16>(R, A, p, a, b, c, live, rscale);
@@ -467,9 +352,7 @@ __global__ void __launch_bounds__(kThreads, 3)
   fence_async_smem();
   __syncthreads();
 
-  // ---- 4. D = A W (one thread issues); meanwhile the others clear the
-  //         accumulator (the staged region is dead now) and seed it with the
-  //         interior-space results, pre-divided by the final output scale -----
+  // ---- 3. D = A W -------------------------------------------------------------
   if (tid == 0) {
     fence_after();
     const uint32_t a0 = smem_u32(smem + OFF_A), b0 = smem_u32(smem + OFF_B1);
@@ -480,22 +363,10 @@ __global__ void __launch_bounds__(kThreads, 3)
               idesc, kk > 0);
     mma_commit(bar0);
   }
-  for (int q = tid; q < kAccSize; q += kThreads) ACC[q] = 0.f;
-  __syncthreads();
-  if (tid < kB * kB * kB) {
-    const int a = tid % kB, b = (tid / kB) % kB, c = tid / (kB * kB);
-    const float pre = rscale / wscale;   // undone by eta * wscale / rscale at the end
-#pragma unroll
-    for (int t = 0; t < 6; ++t) {
-      int d, p[3];
-      bubble_edge(t, a, b, c, d, p);
-      ACC[d * kAccD + p[2] * kAccK + p[1] * kOwn + p[0]] += BUB[tid * 6 + t] * pre;
-    }
-  }
   bool ok = mbar_wait(bar0, 0);
   fence_after();
 
-  // ---- 5. A' = low-precision copy of D (8 warps: lane quadrant x column half)
+  // ---- 4. A' = low-precision copy of D (8 warps: lane quadrant x column half)
   if (ok) {
     const int p = (warp & 3) * 32 + lane;
     const int cb0 = (warp >> 2) * 32;
@@ -519,7 +390,7 @@ __global__ void __launch_bounds__(kThreads, 3)
   fence_before();
   __syncthreads();
 
-  // ---- 6. D' = A' W^t, written over D -----------------------------------------
+  // ---- 5. D' = A' W^t, written over D -----------------------------------------
   if (tid == 0 && ok) {
     fence_after();
     const uint32_t a0 = smem_u32(smem + OFF_A), b0 = smem_u32(smem + OFF_B2);
@@ -533,65 +404,126 @@ __global__ void __launch_bounds__(kThreads, 3)
   if (ok) ok = mbar_wait(bar1, 0);
   fence_after();
 
-  // ---- 7. accumulate owned outputs (columns split between warp w and w+4) -----
+  // ---- 6. y[l][p] = D' / (s_w^2 s_r): groups of 8 lanes are consecutive
+  //         vertices along x, so every store writes 32-byte runs ------------------
   if (ok) {
-    const int p = (warp & 3) * 32 + lane;
-    const int a = p % 5, b = (p / 5) % 5, c = p / 25;
-    const bool live = p < 125 && (I0 + a) >= 1 && (I0 + a) <= nc - 1 && (J0 + b) >= 1 && (J0 + b) <= nc - 1 &&
-                      (K0 + c) >= 1 && (K0 + c) <= nc - 1;
-    const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-    float v[16];
-    if ((warp >> 2) == 0) {
-      tmem_ld16(trow + 0, v);
-      if (live) scatter16<0>(ACC, v, a, b, c);
-      tmem_ld16(trow + 16, v);
-      if (live) scatter16<16>(ACC, v, a, b, c);
-      tmem_ld16(trow + 32, v);
-      if (live) scatter16<32>(ACC, v, a, b, c);
-      tmem_ld16(trow + 48, v);
-      if (live) scatter16<48>(ACC, v, a, b, c);
-    } else {
-      tmem_ld16(trow + 64, v);
-      if (live) scatter16<64>(ACC, v, a, b, c);
-      tmem_ld16(trow + 80, v);
-      if (live) scatter16<80>(ACC, v, a, b, c);
-      tmem_ld16(trow + 96, v);
-      if (live) scatter16<96>(ACC, v, a, b, c);
+    const int prow = (warp & 3) * 32 + lane;
+    const int a = prow % kBX, b = (prow / kBX) % kBY, c = prow / (kBX * kBY);
+    const bool live = VX + a <= nv && VY + b <= nv && VZ + c <= nv;
+    const int64_t pg = ((int64_t)(VZ + c - 1) * nv + (VY + b - 1)) * nv + (VX + a - 1);
+    const float sc = wscale / rscale;
+    const int cbeg = (warp >> 2) ? 64 : 0, cend = (warp >> 2) ? kN2 : 64;
+#pragma unroll 1
+    for (int cb = cbeg; cb < cend; cb += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + cb, v);
+      if (live) {
+#pragma unroll
+        for (int t = 0; t < 16; ++t)
+          if (cb + t < 108) y[(int64_t)(cb + t) * P + pg] = v[t] * sc;
+      }
     }
   } else if (tid == 0) {
     atomicExch(status, kTimeout);
   }
   fence_before();
   __syncthreads();
-
-  // ---- 8. z[owned] += eta * acc / (s_w^2 s_r) ---------------------------------
-  if (ok) {
-    // 1536 owned edges, 6 per thread: issue every load before the first add
-    constexpr int kPer = 3 * kOwn3 / kThreads;
-    static_assert(kPer * kThreads == 3 * kOwn3, "owned edges split evenly");
-    const float sc = eta * wscale / rscale;
-    int64_t gi[kPer];
-    float zv[kPer];
-#pragma unroll
-    for (int t = 0; t < kPer; ++t) {
-      const int q = tid + t * kThreads;
-      const int d = q / kOwn3, e = q - d * kOwn3;
-      const int i = 2 * I0 + e % kOwn, j = 2 * J0 + (e / kOwn) % kOwn, k = 2 * K0 + e / (kOwn * kOwn);
-      gi[t] = interior(n, d, i, j, k) ? gidx(n, d, i, j, k) : -1;
-      zv[t] = gi[t] >= 0 ? z[gi[t]] : 0.f;
-    }
-#pragma unroll
-    for (int t = 0; t < kPer; ++t) {
-      const int q = tid + t * kThreads;
-      const int d = q / kOwn3, e = q - d * kOwn3;
-      const int slot = d * kAccD + (e / (kOwn * kOwn)) * kAccK + e % (kOwn * kOwn);
-      if (gi[t] >= 0) z[gi[t]] = zv[t] + sc * ACC[slot];
-    }
-  }
   if (warp == 0) {
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
   }
+}
+
+// patch-local index of the edge whose box coordinates (in the 4x4x4 box of
+// its vertex) are (bi, bj, bk)
+__device__ __forceinline__ int box_local(int d, int bi, int bj, int bk) {
+  if (d == 0) return ((bk - 1) * 3 + (bj - 1)) * 4 + bi;
+  if (d == 1) return 36 + ((bk - 1) * 4 + bj) * 3 + (bi - 1);
+  return 72 + (bk * 3 + (bj - 1)) * 3 + (bi - 1);
+}
+
+// coarse vertices whose patch contains an edge: along the edge (segment s)
+// V with 2V - 2 <= s < 2V + 2; across (node t) V with |t - 2V| <= 1
+__device__ __forceinline__ int cand_along(int s, int (&V)[2]) {
+  V[0] = s >> 1;
+  V[1] = (s >> 1) + 1;
+  return 2;
+}
+__device__ __forceinline__ int cand_across(int t, int (&V)[2]) {
+  V[0] = t >> 1;
+  V[1] = (t + 1) >> 1;
+  return (t & 1) ? 2 : 1;
+}
+
+// z[e] += eta (row of the interior-space solve + sum of the patch outputs of e)
+// for the edge of direction d at lattice point (i, j, k)
+__device__ __forceinline__ void gather_edge(int n, int d, int i, int j, int k, const float* __restrict__ y, int64_t P,
+                                            const float* __restrict__ As, float eta, const float* __restrict__ r,
+                                            float* __restrict__ z) {
+  const int nv = n / 2 - 1;
+  const uint32_t n1 = n - 1, N3 = (uint32_t)n * n1 * n1;
+  const int c[3] = {i, j, k};
+  int VI[2], VJ[2], VK[2];
+  const int ni = d == 0 ? cand_along(i, VI) : cand_across(i, VI);
+  const int nj = d == 1 ? cand_along(j, VJ) : cand_across(j, VJ);
+  const int nk = d == 2 ? cand_along(k, VK) : cand_across(k, VK);
+  float s = 0.f;
+  for (int q = 0; q < nk; ++q) {
+    if (VK[q] < 1 || VK[q] > nv) continue;
+    for (int p = 0; p < nj; ++p) {
+      if (VJ[p] < 1 || VJ[p] > nv) continue;
+      for (int o = 0; o < ni; ++o) {
+        if (VI[o] < 1 || VI[o] > nv) continue;
+        const int l = box_local(d, i - 2 * VI[o] + 2, j - 2 * VJ[p] + 2, k - 2 * VK[q] + 2);
+        s += __ldg(y + (int64_t)l * P + ((int64_t)(VK[q] - 1) * nv + (VJ[p] - 1)) * nv + (VI[o] - 1));
+      }
+    }
+  }
+  // interior space of a coarse element: the edge is strictly inside it when
+  // both its node coordinates are odd; its row t = 2d + (segment parity)
+  const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+  if ((c[t1] & 1) && (c[t2] & 1)) {
+    const int E[3] = {c[0] >> 1, c[1] >> 1, c[2] >> 1};
+    const int row = 2 * d + (c[d] & 1);
+    float acc = 0.f;
+#pragma unroll
+    for (int w = 0; w < 6; ++w) {
+      const int dw = w >> 1;
+      int g[3] = {2 * E[0] + 1, 2 * E[1] + 1, 2 * E[2] + 1};
+      g[dw] = 2 * E[dw] + (w & 1);
+      uint32_t off;
+      if (dw == 0) off = ((uint32_t)(g[2] - 1) * n1 + (g[1] - 1)) * n + g[0];
+      else if (dw == 1) off = N3 + ((uint32_t)(g[2] - 1) * n + g[1]) * n1 + (g[0] - 1);
+      else off = 2 * N3 + ((uint32_t)g[2] * n1 + (g[1] - 1)) * n1 + (g[0] - 1);
+      acc += As[row * 6 + w] * __ldg(r + off);
+    }
+    s += acc;
+  }
+  uint32_t off;
+  if (d == 0) off = ((uint32_t)(k - 1) * n1 + (j - 1)) * n + i;
+  else if (d == 1) off = N3 + ((uint32_t)(k - 1) * n + j) * n1 + (i - 1);
+  else off = 2 * N3 + ((uint32_t)k * n1 + (j - 1)) * n1 + (i - 1);
+  z[off] += eta * s;
+}
+
+__global__ void __launch_bounds__(256) k_vertex_gather(int n, const float* __restrict__ y, const float* __restrict__ AinvT,
+                                                       float eta, const float* __restrict__ r, float* __restrict__ z) {
+  __shared__ float As[36];
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  if (tid < 36) As[tid] = AinvT[tid];
+  __syncthreads();
+  const int rhs = blockIdx.z / n;
+  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z - rhs * n;
+  if (i >= n || j >= n) return;
+  const int nv = n / 2 - 1;
+  const int64_t P = (int64_t)nv * nv * nv;
+  const int64_t N = 3LL * n * (n - 1) * (n - 1);
+  y += (int64_t)rhs * 108 * P;
+  r += (int64_t)rhs * N;
+  z += (int64_t)rhs * N;
+  if (interior(n, 0, i, j, k)) gather_edge(n, 0, i, j, k, y, P, As, eta, r, z);
+  if (interior(n, 1, i, j, k)) gather_edge(n, 1, i, j, k, y, P, As, eta, r, z);
+  if (interior(n, 2, i, j, k)) gather_edge(n, 2, i, j, k, y, P, As, eta, r, z);
 }
 
 }  // namespace
@@ -631,22 +563,31 @@ cudaError_t upload_tc_operand(void** dst, const std::vector<double>& W, bool fp1
 }
 
 cudaError_t prepare_tc_patch() {
-  cudaError_t e = cudaFuncSetAttribute(k_tc_smoother<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+  cudaError_t e = cudaFuncSetAttribute(k_tc_patches<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_tc_smoother<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    e = cudaFuncSetAttribute(k_tc_patches<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
   return e;
 }
 
-void launch_tc_smoother(cudaStream_t s, int n, const void* Wimg, const float* AinvT, bool fp16, double eta,
-                        const float* r, float* z, int* status, int R) {
-  const int nc = n / 2;
-  if (nc < 1) return;
-  const int nbr = (nc + kB - 1) / kB;
-  const int grid = nbr * nbr * nbr * R;
+int64_t tc_patch_buffer_floats(int n) {
+  const int64_t nv = n / 2 - 1;
+  return nv > 0 ? 108 * nv * nv * nv : 0;
+}
+
+void launch_tc_patches(cudaStream_t s, int n, const void* Wimg, bool fp16, const float* r, float* y, int* status,
+                       int R) {
+  const int nv = n / 2 - 1;
+  if (nv < 1) return;
+  const int grid = ((nv + kBX - 1) / kBX) * ((nv + kBY - 1) / kBY) * ((nv + kBZ - 1) / kBZ) * R;
   if (fp16)
-    k_tc_smoother<true><<<grid, kThreads, kSmem, s>>>(n, (const uint8_t*)Wimg, AinvT, (float)eta, r, z, status);
+    k_tc_patches<true><<<grid, kThreads, kSmem, s>>>(n, (const uint8_t*)Wimg, r, y, status);
   else
-    k_tc_smoother<false><<<grid, kThreads, kSmem, s>>>(n, (const uint8_t*)Wimg, AinvT, (float)eta, r, z, status);
+    k_tc_patches<false><<<grid, kThreads, kSmem, s>>>(n, (const uint8_t*)Wimg, r, y, status);
+}
+
+void launch_vertex_gather(cudaStream_t s, int n, const float* y, const float* AinvT, double eta, const float* r,
+                          float* z, int R) {
+  k_vertex_gather<<<dim3((n + 31) / 32, (n + 7) / 8, n * R), dim3(32, 8), 0, s>>>(n, y, AinvT, (float)eta, r, z);
 }
 
 }  // namespace ndmg

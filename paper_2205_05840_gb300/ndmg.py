@@ -51,6 +51,8 @@ _SIGS = {
     "ndmg_num_dofs": [_vp, _i32, _P(_i64)],
     "ndmg_apply": [_vp, _i32, _i32, _vp, _vp],
     "ndmg_residual": [_vp, _i32, _i32, _vp, _vp, _vp],
+    "ndmg_pencil": [_vp, _i32, _i32, _d, _d, _vp, _vp, _vp],
+    "ndmg_axpby": [_vp, _i32, _i32, _d, _vp, _d, _vp],
     "ndmg_smooth": [_vp, _i32, _i32, _vp, _vp, _i32],
     "ndmg_restrict": [_vp, _i32, _i32, _vp, _vp],
     "ndmg_prolong_add": [_vp, _i32, _i32, _vp, _vp],
@@ -162,6 +164,18 @@ class Solver:
         d = _dtype_code(g)
         self._check(_lib.ndmg_residual(self._h, level, d, self._vec(g, level), self._vec(z, level, g.dtype),
                                        self._vec(r, level, g.dtype)), "residual")
+
+    def pencil(self, a: float, b: float, x, y, g=None, level: int = -1):
+        """y = g + (a K + b M) x (ndmg_pencil); g=None gives y = (a K + b M) x."""
+        d = _dtype_code(x)
+        gp = None if g is None else self._vec(g, level, x.dtype)
+        self._check(_lib.ndmg_pencil(self._h, level, d, a, b, gp, self._vec(x, level), self._vec(y, level, x.dtype)),
+                    "pencil")
+
+    def axpby(self, a: float, x, b: float, y, level: int = -1):
+        """y = a x + b y (ndmg_axpby)."""
+        self._check(_lib.ndmg_axpby(self._h, level, _dtype_code(x), a, self._vec(x, level), b,
+                                    self._vec(y, level, x.dtype)), "axpby")
 
     def smooth(self, g, z, steps: int = 1, level: int = -1):
         self._check(_lib.ndmg_smooth(self._h, level, _dtype_code(g), self._vec(g, level), self._vec(z, level, g.dtype),

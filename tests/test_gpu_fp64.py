@@ -51,7 +51,8 @@ def patch_tol(n, alpha, base, L=1.0, beta=1.0):
 
 
 @pytest.mark.parametrize("n,n0,L,alpha,beta", [(2, 2, 1.0, 1.0, 1.0), (4, 2, 1.0, 0.3, 2.0), (6, 3, 2.0, 10.0, 1.0),
-                                              (8, 2, 1.0, 1.0, 1.0), (16, 4, 1.0, 0.01, 1.0), (12, 3, 1.0, 100.0, 0.5)])
+                                              (8, 2, 1.0, 1.0, 1.0), (16, 4, 1.0, 0.01, 1.0), (12, 3, 1.0, 100.0, 0.5),
+                                              (40, 5, 1.0, 2.0, 1.0), (72, 9, 1.0, 1.0, 1.0)])
 def test_apply_and_residual_parity(n, n0, L, alpha, beta):
     S = ndmg.Solver(n, n_coarsest=n0, L=L, alpha=alpha, beta=beta)
     A = hcurl.assemble(n, L, alpha, beta)

@@ -41,9 +41,11 @@ def test_gradient_matches_oracle_and_fd(prec):
     assert abs(g_alpha - dalpha_ref) < 1e-5 * abs(dalpha_ref)
     assert np.abs(g_f - lam_ref).max() < 1e-5 * np.abs(lam_ref).max()
 
+    # the finite-difference losses need solves well below the difference
+    # they resolve (the FP64 outer iteration reaches 1e-12 in either mode)
     def L(a):
         with torch.no_grad():
-            uu = autograd.solve(f.detach(), torch.tensor(a, dtype=torch.float64), S, tol=1e-10)
+            uu = autograd.solve(f.detach(), torch.tensor(a, dtype=torch.float64), S, tol=1e-12)
             return 0.5 * float(((uu - ut) ** 2).sum())
     eps = 1e-4 * alpha0
     fd = (L(alpha0 + eps) - L(alpha0 - eps)) / (2 * eps)
@@ -52,8 +54,8 @@ def test_gradient_matches_oracle_and_fd(prec):
     v = torch.tensor(np.random.default_rng(2).standard_normal(f_np.size), device="cuda")
     t = 1e-3
     with torch.no_grad():
-        Lp = 0.5 * float(((autograd.solve(f.detach() + t * v, torch.tensor(alpha0, dtype=torch.float64), S, 1e-10) - ut) ** 2).sum())
-        Lm = 0.5 * float(((autograd.solve(f.detach() - t * v, torch.tensor(alpha0, dtype=torch.float64), S, 1e-10) - ut) ** 2).sum())
+        Lp = 0.5 * float(((autograd.solve(f.detach() + t * v, torch.tensor(alpha0, dtype=torch.float64), S, 1e-12) - ut) ** 2).sum())
+        Lm = 0.5 * float(((autograd.solve(f.detach() - t * v, torch.tensor(alpha0, dtype=torch.float64), S, 1e-12) - ut) ** 2).sum())
     fdf = (Lp - Lm) / (2 * t)
     assert abs(float((f.grad * v).sum()) - fdf) < 1e-5 * abs(fdf)
 
@@ -73,7 +75,7 @@ def test_gradient_96_cubed_directional_fd():
 
     def L(al, ff):
         with torch.no_grad():
-            uu = autograd.solve(ff, torch.tensor(al, dtype=torch.float64), S, tol=1e-10)
+            uu = autograd.solve(ff, torch.tensor(al, dtype=torch.float64), S, tol=1e-12)
             return 0.5 * float(((uu - ut) ** 2).sum())
     eps = 1e-4 * alpha0
     fd = (L(alpha0 + eps, f.detach()) - L(alpha0 - eps, f.detach())) / (2 * eps)
