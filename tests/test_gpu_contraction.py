@@ -13,7 +13,7 @@ from oracle import hcurl, mg
 pytestmark = pytest.mark.gpu
 
 try:
-    from paper_2205_05840_gb300 import ndmg
+    from paper_2205_05840_gb300 import contraction, ndmg
 except ImportError:
     if torch.cuda.is_available():
         raise
@@ -70,3 +70,26 @@ def test_k2_contraction_matches_oracle(alpha, m):
     H = mg.Hierarchy(8, 2.0, alpha, 1.0, n0=2, kind="vertex", m=m)
     assert abs(rho - mg.contraction_dense(H)) < 1e-9
     assert abs(rho - _table2()[(alpha, 2)][m - 1]) < 0.03
+
+
+def test_lanczos_harness_k3_matches_oracle():
+    # the GPU Lanczos harness (library V-cycle and apply) against the oracle's
+    # Lanczos on the same start vector: level k = 3 (16^3), alpha = 1, m = 1
+    z0 = np.random.default_rng(3).standard_normal(hcurl.num_edges(16))
+    rho = contraction.contraction(16, 1.0, 1, steps=150, z0=z0)
+    H = mg.Hierarchy(16, 2.0, 1.0, 1.0, n0=2, kind="vertex", m=1)
+    assert abs(rho - mg.contraction_lanczos(H, steps=150, z0=z0)) < 1e-6
+    assert abs(rho - _table2()[(1.0, 3)][0]) < 0.03
+
+
+@pytest.mark.parametrize("alpha", [0.01, 100.0])
+def test_table2_k3_k4_rows(alpha):
+    # Table 2 at k = 3 (16^3) and k = 4 (32^3), m = 1..5: within 0.03 of the
+    # printed estimates, and h-independent (Theorem 10): k = 3 and k = 4 agree
+    ref3, ref4 = _table2()[(alpha, 3)], _table2()[(alpha, 4)]
+    for m in range(1, 6):
+        r3 = contraction.contraction(16, alpha, m, steps=150)
+        r4 = contraction.contraction(32, alpha, m, steps=150)
+        assert abs(r3 - ref3[m - 1]) < 0.03 and abs(r4 - ref4[m - 1]) < 0.03, (m, r3, r4)
+        assert abs(r3 - r4) < 0.01, (m, r3, r4)
+        assert (8 / 9) ** (2 * m) - 1e-9 <= r4 < 1.0
