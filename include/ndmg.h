@@ -76,7 +76,7 @@ typedef enum ndmg_precision {
 } ndmg_precision;
 
 typedef struct ndmg_opts {
-  int32_t n;          /* hexahedra per side on the finest level; even unless n == n_coarsest */
+  int32_t n;          /* hexahedra per side on the finest level, <= 1024; even unless n == n_coarsest */
   int32_t n_coarsest; /* hexahedra per side on the coarsest level (paper: 2); n = n_coarsest * 2^K */
   double L;           /* box side length, > 0 */
   double alpha;       /* curl-curl coefficient, > 0 (eq. 1) */
@@ -196,6 +196,15 @@ int ndmg_vcycle_iterate(ndmg_t* h, const double* f, double* u, double tol, int32
  * alpha-free curl-curl matrix (a(w,v) = alpha (curl w, curl v) + beta (w, v)).
  * lambda, u: double device vectors on the finest level; out: host, nrhs doubles. */
 int ndmg_grad_alpha(ndmg_t* h, const double* lambda, const double* u, double* out);
+
+/* Graph replay of the float V-cycle inside the mixed-precision solves (no
+ * counterpart in the paper; launch latency only): with on != 0 (the default)
+ * the V-cycle that preconditions each FP64 iteration is captured once as a
+ * CUDA graph on the handle's stream and replayed; on == 0 launches it kernel
+ * by kernel.  The graph is recaptured after ndmg_set_alpha or a change of
+ * ndmg_trace_enable.  Synchronises the handle's stream.  Errors: INVALID_ARG,
+ * CUDA_ERROR. */
+int ndmg_use_graphs(ndmg_t* h, int32_t on);
 
 /* Inner product in FP64: out[r] = x_r^T y_r for each of the nrhs right-hand
  * sides (out: host, nrhs doubles). */

@@ -93,28 +93,34 @@ def prolongation(nc: int, L: float = 1.0) -> sp.csr_matrix:
 # --------------------------------------------------------------------------
 
 
-def bubble_sets(n: int) -> np.ndarray:
-    """(nc^3, 6) fine edge indices of the interior space N_h^T of every coarse
-    element T (2x2x2 fine cells), coarse elements ordered x fastest."""
-    nc = n // 2
+def bubble_sets(n: int, s: int = 2) -> np.ndarray:
+    """(nc^3, 3 s (s-1)^2) fine edge indices of the interior space N_h^T of
+    every subdomain T (an s x s x s block of fine cells; s = 2: the coarse
+    elements of Sec. 3.2, 6 edges each), subdomains ordered x fastest, edges
+    of a block ordered (direction, k, j, i)."""
+    nc = n // s
     cz, cy, cx = np.meshgrid(np.arange(nc), np.arange(nc), np.arange(nc), indexing="ij")
-    cx, cy, cz = cx.ravel(), cy.ravel(), cz.ravel()
-    cols = []
-    for d in range(3):
-        for s in range(2):
-            o = [1, 1, 1]
-            o[d] = s              # segment index inside the block, nodes at the centre
-            cols.append(hcurl.edge_index(n, d, 2 * cx + o[0], 2 * cy + o[1], 2 * cz + o[2]))
-    out = np.stack(cols, axis=1)
+    lo = s * np.stack([cx.ravel(), cy.ravel(), cz.ravel()], axis=1)
+    if s == 2:
+        cols = []
+        for d in range(3):
+            for q in range(2):
+                o = [1, 1, 1]
+                o[d] = q          # segment index inside the block, nodes at the centre
+                cols.append(hcurl.edge_index(n, d, lo[:, 0] + o[0], lo[:, 1] + o[1], lo[:, 2] + o[2]))
+        out = np.stack(cols, axis=1)
+    else:
+        out, _, _ = _block_edges(n, lo, lo + s, s)
     assert (out >= 0).all()
     return out
 
 
-def _block_edges(n, lo, hi):
+def _block_edges(n, lo, hi, s=2):
     """Fine interior edges strictly inside the axis-aligned block of fine
     cells [lo, hi) (per-axis arrays of shape (P, 3)); returns (P, m) indices
     ordered (direction, k, j, i) and a boolean 'edge is a bubble edge' mask
-    w.r.t. the coarse grid (both transverse nodes odd)."""
+    w.r.t. the subdomain grid of spacing s (neither transverse node on a
+    subdomain face)."""
     P = lo.shape[0]
     idx, bub, kind = [], [], []
     ext = hi[0] - lo[0]
@@ -133,28 +139,32 @@ def _block_edges(n, lo, hi):
         idx.append(hcurl.edge_index(n, d, gi, gj, gk))
         tr = [gi, gj, gk]
         a, b = tr[(d + 1) % 3], tr[(d + 2) % 3]
-        bub.append((a % 2 == 1) & (b % 2 == 1))
-        kind.append(((a % 2 == 1).astype(int) + (b % 2 == 1).astype(int)))
+        bub.append((a % s != 0) & (b % s != 0))
+        kind.append(((a % s != 0).astype(int) + (b % s != 0).astype(int)))
     return np.concatenate(idx, axis=1), np.concatenate(bub, axis=1), np.concatenate(kind, axis=1)
 
 
-def vertex_patches(n: int):
-    """For every interior coarse vertex V (x fastest): the 108 fine edges of
-    the vertex patch, reordered as [48 bubble edges (I) ; 60 interface
-    edges (G)].  Returns (idx (P,108), nI=48)."""
-    nc = n // 2
+def vertex_patches(n: int, s: int = 2):
+    """For every interior vertex V of the subdomain grid (spacing s, x
+    fastest): the fine edges of the vertex patch (the 2s x 2s x 2s block
+    around V; 108 edges for s = 2, 1176 for s = 4), reordered as [bubble
+    edges (I) ; interface edges (G)].  Returns (idx (P, m), nI) with
+    nI = 8 * 3 s (s-1)^2."""
+    nc = n // s
+    m = 3 * 2 * s * (2 * s - 1) ** 2
+    nI = 8 * 3 * s * (s - 1) ** 2
     if nc < 2:
-        return np.zeros((0, 108), dtype=np.int64), 48
+        return np.zeros((0, m), dtype=np.int64), nI
     vz, vy, vx = np.meshgrid(np.arange(1, nc), np.arange(1, nc), np.arange(1, nc), indexing="ij")
     v = np.stack([vx.ravel(), vy.ravel(), vz.ravel()], axis=1)
-    lo = 2 * v - 2
-    hi = 2 * v + 2
-    idx, bub, _ = _block_edges(n, lo, hi)
-    assert idx.shape[1] == 108 and (idx >= 0).all()
+    lo = s * v - s
+    hi = s * v + s
+    idx, bub, _ = _block_edges(n, lo, hi, s)
+    assert idx.shape[1] == m and (idx >= 0).all()
     order = np.argsort(~bub[0], kind="stable")     # same pattern for every patch
-    assert bub[0].sum() == 48
+    assert bub[0].sum() == nI
     assert (bub == bub[0]).all()
-    return idx[:, order], 48
+    return idx[:, order], nI
 
 
 def edge_patches(n: int):
@@ -236,16 +246,20 @@ class Smoother:
     """M_{V,h}^{-1} (eq. Preconditioner P) or M_{E,h}^{-1} (eq.
     Preconditioner E) on one level."""
 
-    def __init__(self, A: sp.csr_matrix, n: int, kind: str = "vertex", eta: float | None = None):
+    def __init__(self, A: sp.csr_matrix, n: int, kind: str = "vertex", eta: float | None = None, s: int = 2):
         self.kind = kind
         self.eta = eta if eta is not None else (1.0 / 9.0 if kind == "vertex" else 1.0 / 13.0)
         self.N = A.shape[0]
-        self.bub = bubble_sets(n)
+        if n % s:
+            raise ValueError(f"level n={n} is not a multiple of the subdomain size s={s}")
+        if s != 2 and kind != "vertex":
+            raise ValueError("subdomain size s != 2 is built for the vertex-based smoother")
+        self.bub = bubble_sets(n, s)
         AT = _identical_blocks(A, self.bub)
         self.cT = sla.cho_factor(AT)
         self.patches = []
         if kind == "vertex":
-            idx, nI = vertex_patches(n)
+            idx, nI = vertex_patches(n, s)
             if idx.shape[0]:
                 Ap = _identical_blocks(A, idx)
                 self.patches.append((idx, SchurPatch(Ap, nI)))
@@ -262,7 +276,7 @@ class Smoother:
         """M^{-1} r: every local solve reads the same r; results are summed."""
         out = np.zeros_like(r)
         # sum_T J_T A_T^{-1} J_T^t r ; bubble sets are disjoint
-        yT = sla.cho_solve(self.cT, r[self.bub].T)          # (6, nT)
+        yT = sla.cho_solve(self.cT, r[self.bub].T)          # (edges per block, nT)
         out[self.bub.T.ravel()] += yT.ravel()
         # sum_V J_V A_V^{-1} J_V^t r (or the edge spaces)
         for idx, sp_ in self.patches:
@@ -280,7 +294,7 @@ class Hierarchy:
     """Levels n_0 < n_1 < ... < n_K = n with n_k = 2 n_{k-1}."""
 
     def __init__(self, n: int, L: float = 1.0, alpha: float = 1.0, beta: float = 1.0,
-                 n0: int = 2, kind: str = "vertex", eta: float | None = None, m: int = 2):
+                 n0: int = 2, kind: str = "vertex", eta: float | None = None, m: int = 2, s: int = 2):
         ns = [n]
         while ns[-1] > n0:
             if ns[-1] % 2:
@@ -292,7 +306,7 @@ class Hierarchy:
         self.L, self.alpha, self.beta, self.m = L, alpha, beta, m
         self.A = [assemble_cached(nk, L, alpha, beta) for nk in self.ns]
         self.P = [None] + [prolongation(self.ns[k - 1], L) for k in range(1, len(self.ns))]
-        self.S = [None] + [Smoother(self.A[k], self.ns[k], kind, eta) for k in range(1, len(self.ns))]
+        self.S = [None] + [Smoother(self.A[k], self.ns[k], kind, eta, s) for k in range(1, len(self.ns))]
         self.c0 = sla.cho_factor(self.A[0].toarray())
 
     @property

@@ -41,6 +41,18 @@ struct Span {
   Span(ndmg_t* h_, int cls, double units, int nlaunch = 1) : h(h_) {
     h->launch_total += nlaunch;
     if (!h->trace_on[cls]) return;
+    if (h->capturing) {  // event-record nodes of the graph being captured
+      ndmg_t::GraphSpan gs{cls, units, nlaunch, nullptr, nullptr};
+      if (cudaEventCreate(&gs.a) != cudaSuccess) return;
+      if (cudaEventCreate(&gs.b) != cudaSuccess) {
+        cudaEventDestroy(gs.a);
+        return;
+      }
+      cudaEventRecord(gs.a, h->stream);
+      h->vgraph_spans.push_back(gs);
+      end = gs.b;
+      return;
+    }
     std::pair<cudaEvent_t, cudaEvent_t> pr{nullptr, nullptr};
     if (!h->ev_free.empty()) {
       pr = h->ev_free.back();
@@ -58,6 +70,9 @@ struct Span {
     if (end) cudaEventRecord(end, h->stream);
   }
 };
+
+int collect_graph(ndmg_t* h);
+void drop_graph(ndmg_t* h);
 
 template <typename T>
 T* dev_alloc(int64_t count, cudaError_t* err) {
@@ -119,14 +134,14 @@ template <typename T>
 void op_residual(ndmg_t* h, int k, const T* g, const T* z, T* r) {
   DevLevel& L = h->lv[k];
   Span sp(h, NDMG_K_STENCIL, 3.0 * sizeof(T) * L.N * nrhs(h));  // read g, z; write r
-  launch_stencil<T>(h->stream, h->sm_count, L.n, L.cK, L.cM, z, g, r, nrhs(h));
+  launch_stencil<T>(h->stream, h->sm_count, L.n, L.cK, L.cM, z, g, r, nrhs(h), h->umax);
 }
 
 template <typename T>
 void op_apply(ndmg_t* h, int k, const T* x, T* y) {
   DevLevel& L = h->lv[k];
   Span sp(h, NDMG_K_STENCIL, 2.0 * sizeof(T) * L.N * nrhs(h));  // read x; write y
-  launch_stencil<T>(h->stream, h->sm_count, L.n, L.cK, L.cM, x, (const T*)nullptr, y, nrhs(h));
+  launch_stencil<T>(h->stream, h->sm_count, L.n, L.cK, L.cM, x, (const T*)nullptr, y, nrhs(h), h->umax);
 }
 
 // y = g + (a K + b M) x (or (a K + b M) x when g is null): the stencil in
@@ -136,8 +151,8 @@ void op_pencil(ndmg_t* h, int k, double a, double b, const T* g, const T* x, T* 
   DevLevel& L = h->lv[k];
   const double hk = L.h, h3 = hk * hk * hk;
   Span sp(h, NDMG_K_STENCIL, (g ? 3.0 : 2.0) * sizeof(T) * L.N * nrhs(h));
-  if (g) launch_stencil<T>(h->stream, h->sm_count, L.n, -a * hk, -b * h3, x, g, y, nrhs(h));
-  else launch_stencil<T>(h->stream, h->sm_count, L.n, a * hk, b * h3, x, (const T*)nullptr, y, nrhs(h));
+  if (g) launch_stencil<T>(h->stream, h->sm_count, L.n, -a * hk, -b * h3, x, g, y, nrhs(h), h->umax);
+  else launch_stencil<T>(h->stream, h->sm_count, L.n, a * hk, b * h3, x, (const T*)nullptr, y, nrhs(h), h->umax);
 }
 
 bool edge_smoother(const ndmg_t* h) { return h->o.smoother == NDMG_SMOOTHER_EDGE; }
@@ -186,13 +201,12 @@ void op_smoother<float>(ndmg_t* h, int k, const float* r, float* z) {
   }
   if (mixed(h) && L.Wtc) {
     // vertex patches on tensor cores (Gram form: two 108x60 products per
-    // patch), then one gather per edge that also adds the interior 6x6
-    // solves.  Algorithmic bytes of the pair: read r, read and write z
-    // (FP32); 25,920 flops per patch is ~86 flop/B, below the bf16 ridge of
-    // ~256 flop/B, so the work is memory-bound.
-    Span sp(h, NDMG_K_PATCH, 12.0 * L.N * R, 2);
-    launch_tc_patches(h->stream, L.n, L.Wtc, h->o.precision == NDMG_PREC_MIXED_FP16, r, L.ypatch, h->status, R);
-    launch_vertex_gather(h->stream, L.n, L.ypatch, L.AinvT32, h->o.eta, r, z, R);
+    // patch) and the interior 6x6 solves in one kernel.  Algorithmic bytes:
+    // read r, read and write z (FP32); 25,920 flops per patch is ~86 flop/B,
+    // below the bf16 ridge of ~256 flop/B, so the work is memory-bound.
+    Span sp(h, NDMG_K_PATCH, 12.0 * L.N * R);
+    launch_tc_smoother(h->stream, L.n, L.Wtc, h->o.precision == NDMG_PREC_MIXED_FP16, L.AinvT32, h->o.eta, r, z,
+                       h->status, R);
     return;
   }
   {
@@ -212,9 +226,10 @@ void op_smooth_steps(ndmg_t* h, int k, const T* g, T* z, int steps) {
   }
 }
 
-// MG(k, g, z, m) of Fig. 1 with z in/out
+// MG(k, g, z, m) of Fig. 1 with z in/out; z_zero: z is 0 on entry, so the
+// first pre-smoothing residual is g itself (no stencil pass)
 template <typename T>
-void op_vcycle(ndmg_t* h, int k, const T* g, T* z) {
+void op_vcycle(ndmg_t* h, int k, const T* g, T* z, bool z_zero = false) {
   const int R = nrhs(h);
   if (k == h->K) ++h->vcycle_total;
   if (k == 0) {
@@ -226,14 +241,19 @@ void op_vcycle(ndmg_t* h, int k, const T* g, T* z) {
   DevLevel& L = h->lv[k];
   DevLevel& C = h->lv[k - 1];
   T* r = lv_r<T>(L);
-  op_smooth_steps<T>(h, k, g, z, h->o.m);
+  if (z_zero) {
+    op_smoother<T>(h, k, g, z);
+    op_smooth_steps<T>(h, k, g, z, h->o.m - 1);
+  } else {
+    op_smooth_steps<T>(h, k, g, z, h->o.m);
+  }
   op_residual<T>(h, k, g, z, r);
   {
     Span sp(h, NDMG_K_RESTRICT, (double)sizeof(T) * (L.N + C.N) * R);
     launch_restrict<T>(h->stream, h->sm_count, L.n, r, lv_g<T>(C), R);
   }
   cudaMemsetAsync(lv_z<T>(C), 0, sizeof(T) * C.N * R, h->stream);
-  op_vcycle<T>(h, k - 1, lv_g<T>(C), lv_z<T>(C));
+  op_vcycle<T>(h, k - 1, lv_g<T>(C), lv_z<T>(C), true);
   {
     Span sp(h, NDMG_K_PROLONG, (double)sizeof(T) * (2 * L.N + C.N) * R);
     launch_prolong_add<T>(h->stream, h->sm_count, L.n, lv_z<T>(C), z, R);
@@ -255,6 +275,30 @@ int dot2(ndmg_t* h, int64_t N, const T* x, const T* y, const T* x2, const T* y2,
   NDMG_CK_LAUNCH();
   NDMG_CK(cudaMemcpyAsync(h->red_host, out, 2 * sizeof(double) * R, cudaMemcpyDeviceToHost, h->stream));
   NDMG_CK(cudaStreamSynchronize(h->stream));
+  if (int st = collect_graph(h)) return st;
+  a.resize(R);
+  if (b) b->resize(R);
+  for (int i = 0; i < R; ++i) {
+    a[i] = h->red_host[2 * i];
+    if (b) (*b)[i] = h->red_host[2 * i + 1];
+  }
+  return NDMG_OK;
+}
+
+// reads the per-right-hand-side sums a kernel pair left in out[2 r], [2 r + 1]
+// (and, with status, the device status word in the same synchronisation)
+int read_sums(ndmg_t* h, const double* out, std::vector<double>& a, std::vector<double>* b, bool status) {
+  const int R = nrhs(h);
+  NDMG_CK_LAUNCH();
+  NDMG_CK(cudaMemcpyAsync(h->red_host, out, 2 * sizeof(double) * R, cudaMemcpyDeviceToHost, h->stream));
+  if (status) NDMG_CK(cudaMemcpyAsync(h->status_host, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  NDMG_CK(cudaStreamSynchronize(h->stream));
+  if (int st = collect_graph(h)) return st;
+  if (status && *h->status_host != 0) {
+    const int code = *h->status_host;
+    cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
+    return fail(h, NDMG_DEVICE_TIMEOUT, "a device-side wait timed out (status " + std::to_string(code) + ")");
+  }
   a.resize(R);
   if (b) b->resize(R);
   for (int i = 0; i < R; ++i) {
@@ -379,7 +423,7 @@ int pcg64(ndmg_t* h, const double* f, double* u, double tol, int maxit, int* ite
   *relres = max_of(S.relres);
   if (all_done) return NDMG_OK;
   cudaMemsetAsync(z, 0, sizeof(double) * N * R, h->stream);
-  op_vcycle<double>(h, K, r, z);
+  op_vcycle<double>(h, K, r, z, true);
   if ((st = dot2<double>(h, N, r, z, (const double*)nullptr, (const double*)nullptr, S.rz, nullptr)) != NDMG_OK)
     return st;
   NDMG_CK(cudaMemcpyAsync(p, z, sizeof(double) * N * R, cudaMemcpyDeviceToDevice, h->stream));
@@ -400,7 +444,7 @@ int pcg64(ndmg_t* h, const double* f, double* u, double tol, int maxit, int* ite
     *relres = max_of(S.relres);
     if (all_done) return NDMG_OK;
     cudaMemsetAsync(z, 0, sizeof(double) * N * R, h->stream);
-    op_vcycle<double>(h, K, r, z);
+    op_vcycle<double>(h, K, r, z, true);
     if ((st = dot2<double>(h, N, r, z, (const double*)nullptr, (const double*)nullptr, rz_new, nullptr)) != NDMG_OK)
       return st;
     for (int i = 0; i < R; ++i) {
@@ -418,6 +462,75 @@ int pcg64(ndmg_t* h, const double* f, double* u, double tol, int maxit, int* ite
 }
 
 // the float V-cycle as preconditioner of FP64 vectors: z = ||r|| MG(r / ||r||)
+// CUDA graph of the float V-cycle on the finest level (r32 -> z32, z32 = 0
+// on entry): built on first use, dropped when the operators or the tracing
+// change
+void drop_graph(ndmg_t* h) {
+  if (h->vgraph) cudaGraphExecDestroy(h->vgraph);
+  h->vgraph = nullptr;
+  for (auto& gs : h->vgraph_spans) {
+    cudaEventDestroy(gs.a);
+    cudaEventDestroy(gs.b);
+  }
+  h->vgraph_spans.clear();
+  h->graph_pending = false;
+}
+
+// adds the traced times of the last replay (call after a synchronisation)
+int collect_graph(ndmg_t* h) {
+  if (!h->graph_pending) return NDMG_OK;
+  h->graph_pending = false;
+  for (auto& gs : h->vgraph_spans) {
+    float t = 0.f;
+    NDMG_CK(cudaEventElapsedTime(&t, gs.a, gs.b));
+    h->trace_ms_graph[gs.cls] += t;
+    h->trace_launches[gs.cls] += gs.nlaunch;
+    h->trace_units[gs.cls] += gs.units;
+  }
+  return NDMG_OK;
+}
+
+// z32 = MG(K, r32, 0, m) on the handle's float work vectors w32[4] -> w32[5]
+int vcycle_f32_graph(ndmg_t* h) {
+  const int K = h->K, R = nrhs(h);
+  const int64_t N = h->lv[K].N;
+  float *r32 = h->w32[4], *z32 = h->w32[5];
+  if (!h->use_graphs) {
+    cudaMemsetAsync(z32, 0, sizeof(float) * N * R, h->stream);
+    op_vcycle<float>(h, K, r32, z32, true);
+    return NDMG_OK;
+  }
+  if (h->graph_pending) {  // the previous replay's events are about to be reused
+    NDMG_CK(cudaStreamSynchronize(h->stream));
+    if (int st = collect_graph(h)) return st;
+  }
+  if (!h->vgraph) {
+    const int64_t l0 = h->launch_total, v0 = h->vcycle_total;
+    NDMG_CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeRelaxed));
+    h->capturing = true;
+    cudaMemsetAsync(z32, 0, sizeof(float) * N * R, h->stream);
+    op_vcycle<float>(h, K, r32, z32, true);
+    h->capturing = false;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->vgraph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    h->vgraph_launches = h->launch_total - l0;
+    h->vgraph_vcycles = h->vcycle_total - v0;
+    h->launch_total = l0;
+    h->vcycle_total = v0;
+    if (e != cudaSuccess) {
+      drop_graph(h);
+      return cuda_fail(h, e, "capturing the V-cycle graph");
+    }
+  }
+  NDMG_CK(cudaGraphLaunch(h->vgraph, h->stream));
+  h->launch_total += h->vgraph_launches;
+  h->vcycle_total += h->vgraph_vcycles;
+  h->graph_pending = !h->vgraph_spans.empty();
+  return NDMG_OK;
+}
+
 int precondition_mixed(ndmg_t* h, const double* r, double* z, const std::vector<double>& rnorm) {
   const int K = h->K, R = nrhs(h);
   const int64_t N = h->lv[K].N;
@@ -430,8 +543,7 @@ int precondition_mixed(ndmg_t* h, const double* r, double* z, const std::vector<
     Span sp(h, NDMG_K_BLAS, 12.0 * N * R);
     launch_to_f32(h->stream, sm, N, d, r, r32, R);
   }
-  cudaMemsetAsync(z32, 0, sizeof(float) * N * R, h->stream);
-  op_vcycle<float>(h, K, r32, z32);
+  if (int st = vcycle_f32_graph(h)) return st;
   {
     const double* d = push_coef(h, SLOT_FROM, rnorm);
     Span sp(h, NDMG_K_BLAS, 12.0 * N * R);
@@ -465,25 +577,41 @@ int pcg_mixed(ndmg_t* h, const double* f, double* u, double tol, int maxit, int*
   if ((st = dot2<double>(h, N, r, z, (const double*)nullptr, (const double*)nullptr, S.rz, nullptr)) != NDMG_OK)
     return st;
   NDMG_CK(cudaMemcpyAsync(p, z, sizeof(double) * N * R, cudaMemcpyDeviceToDevice, h->stream));
+  // per iteration: q = A p; (p.q); u, r update fused with (r.r) and the
+  // float right-hand side of the V-cycle (scaled by 1 / ||r|| of the previous
+  // iteration; the V-cycle is linear and the fp16 patch operands are rescaled
+  // per CTA, so any nearby scale serves); V-cycle; (r.z), (q.z) and
+  // p = z + beta p straight from the float V-cycle output
+  float *r32 = h->w32[4], *z32 = h->w32[5];
+  const int nb = reduction_blocks(sm);
+  double* out = h->red + 2 * (int64_t)nb * R;
+  std::vector<double> inv(R);
   for (int it = 1; it <= maxit; ++it) {
     op_apply<double>(h, K, p, q);
     if ((st = dot2<double>(h, N, p, q, (const double*)nullptr, (const double*)nullptr, pq, nullptr)) != NDMG_OK)
       return st;
     if ((st = cg_alpha(h, S, pq, a)) != NDMG_OK) return st;
+    for (int i = 0; i < R; ++i) inv[i] = rn[i] > 0 ? 1.0 / rn[i] : 0.0;
     {
       const double* da = push_coef(h, SLOT_ALPHA, a);
-      Span sp(h, NDMG_K_BLAS, 6.0 * 8 * N * R);
-      launch_cg_update<double>(h->stream, sm, N, da, p, q, u, r, R);
+      const double* dto = push_coef(h, SLOT_TO, inv);
+      Span sp(h, NDMG_K_BLAS, (6.0 * 8 + 4) * N * R, 2);
+      launch_cg_update_rr(h->stream, sm, N, da, p, q, u, r, dto, r32, h->red, out, R);
     }
-    if ((st = dot2<double>(h, N, r, r, (const double*)nullptr, (const double*)nullptr, rr, nullptr)) != NDMG_OK)
-      return st;
+    if ((st = read_sums(h, out, rr, nullptr, false)) != NDMG_OK) return st;
     *iters = it;
     if ((st = cg_check(h, S, rr, tol, &all_done)) != NDMG_OK) return st;
     *relres = max_of(S.relres);
     if (all_done) return NDMG_OK;
+    // z = rn_old * z32 with z32 = V-cycle(r / rn_old)
+    if ((st = vcycle_f32_graph(h)) != NDMG_OK) return st;
+    const double* dfrom = push_coef(h, SLOT_FROM, rn);
+    {
+      Span sp(h, NDMG_K_BLAS, (2.0 * 8 + 4) * N * R, 2);
+      launch_dot2_zf(h->stream, sm, N, r, q, dfrom, z32, h->red, out, R);
+    }
+    if ((st = read_sums(h, out, rz_new, &qz, true)) != NDMG_OK) return st;
     for (int i = 0; i < R; ++i) rn[i] = std::sqrt(rr[i]);
-    if ((st = precondition_mixed(h, r, z, rn)) != NDMG_OK) return st;
-    if ((st = dot2<double>(h, N, r, z, q, z, rz_new, &qz)) != NDMG_OK) return st;
     for (int i = 0; i < R; ++i) {
       ab[2 * i] = 1.0;
       ab[2 * i + 1] = (S.done[i] || S.rz[i] == 0.0) ? 0.0 : -a[i] * qz[i] / S.rz[i];
@@ -491,8 +619,8 @@ int pcg_mixed(ndmg_t* h, const double* f, double* u, double tol, int maxit, int*
     }
     {
       const double* dab = push_coef(h, SLOT_AB, ab);
-      Span sp(h, NDMG_K_BLAS, 3.0 * 8 * N * R);
-      launch_axpby<double>(h->stream, sm, N, dab, z, p, R);
+      Span sp(h, NDMG_K_BLAS, (2.0 * 8 + 4) * N * R);
+      launch_axpby_zf(h->stream, sm, N, dfrom, z32, dab, p, R);
     }
   }
   return fail(h, NDMG_NOT_CONVERGED, "PCG reached maxit");
@@ -514,7 +642,7 @@ int pcg32(ndmg_t* h, const float* b, float* d, double tol, int maxit, int* iters
   cudaMemsetAsync(d, 0, sizeof(float) * N * R, h->stream);
   NDMG_CK(cudaMemcpyAsync(r, b, sizeof(float) * N * R, cudaMemcpyDeviceToDevice, h->stream));
   cudaMemsetAsync(z, 0, sizeof(float) * N * R, h->stream);
-  op_vcycle<float>(h, K, r, z);
+  op_vcycle<float>(h, K, r, z, true);
   if (mixed(h) && (st = check_status(h)) != NDMG_OK) return st;
   if ((st = dot2<float>(h, N, b, b, r, z, bb, &S.rz)) != NDMG_OK) return st;
   std::vector<double> rz0 = S.rz;
@@ -538,7 +666,7 @@ int pcg32(ndmg_t* h, const float* b, float* d, double tol, int maxit, int* iters
     if ((st = cg_check(h, S, rr, tol, &all_done)) != NDMG_OK) return st;
     if (all_done) return NDMG_OK;
     cudaMemsetAsync(z, 0, sizeof(float) * N * R, h->stream);
-    op_vcycle<float>(h, K, r, z);
+    op_vcycle<float>(h, K, r, z, true);
     if (mixed(h) && (st = check_status(h)) != NDMG_OK) return st;
     if ((st = dot2<float>(h, N, r, z, q, z, rz_new, &qz)) != NDMG_OK) return st;
     for (int i = 0; i < R; ++i) {
@@ -608,17 +736,18 @@ int solve_ir(ndmg_t* h, const double* f, double* u, double tol, double inner_tol
 
 void free_handle(ndmg_t* h) {
   if (!h) return;
+  drop_graph(h);
   for (auto& L : h->lv) {
     cudaFree(L.g64); cudaFree(L.z64); cudaFree(L.r64);
     cudaFree(L.g32); cudaFree(L.z32); cudaFree(L.r32);
     cudaFree(L.AinvT64); cudaFree(L.AinvT32); cudaFree(L.Dv64); cudaFree(L.Dv32);
     cudaFree(L.De64); cudaFree(L.De32);
     cudaFree(L.Wtc);
-    cudaFree(L.ypatch);
   }
   cudaFree(h->Ainv0);
   for (int i = 0; i < 6; ++i) { cudaFree(h->w64[i]); cudaFree(h->w32[i]); }
   cudaFree(h->red);
+  cudaFree(h->umax);
   cudaFree(h->coef);
   cudaFree(h->status);
   if (h->red_host) cudaFreeHost(h->red_host);
@@ -651,11 +780,6 @@ int build_operators(ndmg_t* h) {
       if (mixed(h)) {
         cudaError_t e = upload_tc_operand(&L.Wtc, ops.Wv, o.precision == NDMG_PREC_MIXED_FP16);
         if (e != cudaSuccess) return cuda_fail(h, e, "upload_tc_operand");
-        if (!L.ypatch) {
-          const int64_t ny = tc_patch_buffer_floats(L.n) * o.nrhs;
-          e = cudaMalloc((void**)&L.ypatch, sizeof(float) * (ny > 0 ? ny : 1));
-          if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc(ypatch)");
-        }
       }
     }
     std::vector<double> inv = coarse_inverse(h->lv[0].n, o.L, o.alpha, o.beta);
@@ -704,9 +828,9 @@ int ndmg_create(const ndmg_opts* o, ndmg_t** out) {
   if (o->smoother != NDMG_SMOOTHER_VERTEX && o->smoother != NDMG_SMOOTHER_EDGE) return NDMG_INVALID_ARG;
   if (o->precision < NDMG_PREC_FP64 || o->precision > NDMG_PREC_FP32) return NDMG_INVALID_ARG;
   if (edges(o->n_coarsest) > 4096) return NDMG_INVALID_ARG;   // dense coarsest inverse
-  // 32-bit edge offsets inside the tensor-core smoother: 3 n (n-1)^2 < 2^32
-  if ((o->precision == NDMG_PREC_MIXED_BF16 || o->precision == NDMG_PREC_MIXED_FP16) && o->n > 1024)
-    return NDMG_INVALID_ARG;
+  // 32-bit edge offsets within one right-hand side (stencil, tensor-core
+  // smoother): 3 n (n-1)^2 < 2^32
+  if (o->n > 1024) return NDMG_INVALID_ARG;
   int K = 0;
   for (int n = o->n; n > o->n_coarsest; n /= 2, ++K)
     if (n % 2) return NDMG_INVALID_ARG;
@@ -757,6 +881,7 @@ int ndmg_create(const ndmg_opts* o, ndmg_t** out) {
     h->w32[i] = dev_alloc<float>(NF, &ae);
   }
   h->red = dev_alloc<double>(2 * (int64_t)reduction_blocks(h->sm_count) * R + 2 * R + 8, &ae);
+  h->umax = dev_alloc<unsigned long long>(R, &ae);
   h->coef = dev_alloc<double>(4 * 2 * R, &ae);
   h->status = dev_alloc<int>(4, &ae);
   if (ae == cudaSuccess) ae = cudaMallocHost((void**)&h->red_host, (2 * R + 8) * sizeof(double));
@@ -794,6 +919,7 @@ int ndmg_set_alpha(ndmg_t* h, double alpha) {
   if (!h) return NDMG_INVALID_ARG;
   if (!(alpha > 0)) return fail(h, NDMG_INVALID_ARG, "alpha must be > 0");
   NDMG_CK(cudaStreamSynchronize(h->stream));
+  drop_graph(h);  // the coefficients are captured in the graph's launches
   h->o.alpha = alpha;
   return build_operators(h);
 }
@@ -1009,7 +1135,7 @@ int ndmg_grad_alpha(ndmg_t* h, const double* lambda, const double* u, double* ou
   double* Ku = h->w64[3];
   {
     Span sp(h, NDMG_K_STENCIL, 16.0 * L.N * R);
-    launch_stencil<double>(h->stream, h->sm_count, L.n, L.h, 0.0, u, (const double*)nullptr, Ku, R);
+    launch_stencil<double>(h->stream, h->sm_count, L.n, L.h, 0.0, u, (const double*)nullptr, Ku, R, h->umax);
   }
   std::vector<double> v;
   if ((st = dot2<double>(h, L.N, lambda, Ku, (const double*)nullptr, (const double*)nullptr, v, nullptr)) != NDMG_OK)
@@ -1038,7 +1164,21 @@ int ndmg_dot(ndmg_t* h, int32_t level, int32_t dtype, const void* x, const void*
 int ndmg_trace_enable(ndmg_t* h, int32_t kernel_class, int32_t on) {
   if (!h) return NDMG_INVALID_ARG;
   if (kernel_class < 0 || kernel_class >= NDMG_K_COUNT) return fail(h, NDMG_INVALID_ARG, "bad kernel class");
+  if (h->trace_on[kernel_class] != (on != 0)) {
+    NDMG_CK(cudaStreamSynchronize(h->stream));
+    if (int st = collect_graph(h)) return st;
+    drop_graph(h);  // recaptured with (or without) this class's events
+  }
   h->trace_on[kernel_class] = on != 0;
+  return NDMG_OK;
+}
+
+int ndmg_use_graphs(ndmg_t* h, int32_t on) {
+  if (!h) return NDMG_INVALID_ARG;
+  NDMG_CK(cudaStreamSynchronize(h->stream));
+  if (int st = collect_graph(h)) return st;
+  drop_graph(h);
+  h->use_graphs = on != 0;
   return NDMG_OK;
 }
 
@@ -1046,7 +1186,9 @@ int ndmg_trace_read(ndmg_t* h, int32_t kernel_class, int64_t* launches, double* 
   if (!h) return NDMG_INVALID_ARG;
   if (kernel_class < 0 || kernel_class >= NDMG_K_COUNT) return fail(h, NDMG_INVALID_ARG, "bad kernel class");
   NDMG_CK(cudaStreamSynchronize(h->stream));
-  double total = 0.0;
+  if (int st = collect_graph(h)) return st;
+  double total = h->trace_ms_graph[kernel_class];
+  h->trace_ms_graph[kernel_class] = 0.0;
   for (auto& pr : h->ev_used[kernel_class]) {
     float t = 0.f;
     NDMG_CK(cudaEventElapsedTime(&t, pr.first, pr.second));

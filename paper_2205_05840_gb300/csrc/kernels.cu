@@ -2,6 +2,8 @@
 // grid transfers, interior-space and vertex-patch smoother pieces, coarsest
 // solve and FP64 reductions.  Templated on the vector element type
 // (double for the FP64 path, float for the mixed path's inner V-cycle).
+#include <type_traits>
+
 #include "kernels.cuh"
 
 namespace ndmg {
@@ -57,16 +59,101 @@ __device__ __forceinline__ void cp_async_elem(T* dst, const T* src, bool valid, 
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(sp), "r"(valid ? 4u : 0u) : "memory");
 }
 
-template <typename T>
+// In-plane part of one staged position (a, b) of the tile's plane: global
+// offsets (without the plane term) and whether the x-, y-, z-edge there is
+// interior as far as i and j decide; fixed for the whole column.
+struct PlanePos {
+  uint32_t ox, oy, oz;
+  bool vx, vy, vz;
+};
+
+__device__ __forceinline__ PlanePos plane_pos(int n, int i, int j) {
+  const uint32_t n1 = n - 1;
+  PlanePos p;
+  p.vx = in_seg(i, n) && in_node(j, n);
+  p.vy = in_node(i, n) && in_seg(j, n);
+  p.vz = in_node(i, n) && in_node(j, n);
+  p.ox = p.vx ? (uint32_t)(j - 1) * n + i : 0u;
+  p.oy = p.vy ? (uint32_t)j * n1 + (i - 1) : 0u;
+  p.oz = p.vz ? (uint32_t)(j - 1) * n1 + (i - 1) : 0u;
+  return p;
+}
+
+// FP64 operator on the integer pipe.  With the face and edge masses as the
+// integer three-point weights [1, 4, 1] (1/6 and 1/36 folded into the
+// coefficients), K u and M u have integer coefficients, so for u in fixed
+// point (u * 2^s truncated to int64, max |u| 2^s < 2^55) both are computed
+// exactly in int64: circulations stay below 2^57, face masses below 2^60, the
+// four-face sums and the 3x3 edge masses below 2^62.  Only the final
+// combination cK K u + cM M u and g - (...) run in FP64 (about 9 FP64
+// instructions per lattice point instead of about 60), which matters on a part
+// whose FP64 rate is 1/64 of its FP32 rate.  The scale comes from max |u| of
+// each right-hand side (k_absmax); the truncation error is below
+// 2^-54 max |u| per entry.
+__device__ __forceinline__ long long to_fixed(double v, int s) {
+  const long long b = __double_as_longlong(v);
+  const int e = (int)((b >> 52) & 0x7FF);
+  const long long m = (b & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
+  const int sh = e - 1075 + s;  // v 2^s = m 2^sh, sh <= 2 by the choice of s
+  long long r = sh >= 0 ? (m << sh) : (sh > -63 ? (m >> -sh) : 0LL);
+  r = e == 0 ? 0LL : r;         // zero and subnormals
+  return b < 0 ? -r : r;
+}
+
+// int64 -> double rounded to nearest (ties to even) on the integer pipe:
+// normalise |x| so that its leading one is bit 63, keep 53 bits, round on the
+// 11 bits below, assemble sign / exponent / fraction
+__device__ __forceinline__ double fixed_to_double(long long x) {
+  if (x == 0) return 0.0;
+  const unsigned long long sgn = (unsigned long long)x & 0x8000000000000000ull;
+  unsigned long long a = x < 0 ? 0ull - (unsigned long long)x : (unsigned long long)x;
+  const int lz = __clzll((long long)a);
+  a <<= lz;                                     // leading one at bit 63
+  unsigned long long m = a >> 11;               // 53 significant bits
+  const unsigned long long rest = a & 0x7FFull;  // the 11 bits rounded away
+  m += (rest > 0x400ull || (rest == 0x400ull && (m & 1ull))) ? 1ull : 0ull;
+  unsigned long long e = (unsigned long long)(1086 - lz);  // 1023 + 63 - lz
+  if (m >> 53) {                                // rounding carried into bit 53
+    m >>= 1;
+    ++e;
+  }
+  return __longlong_as_double((long long)(sgn | (e << 52) | (m & 0xFFFFFFFFFFFFFull)));
+}
+
+// max |x_r| of every right-hand side, as the bit pattern of |x| (monotonic as
+// an unsigned integer, with Inf and NaN above every finite value); out[r]
+// must be 0 on entry
+__global__ void __launch_bounds__(256) k_absmax(int64_t N, const double* __restrict__ x,
+                                                unsigned long long* __restrict__ out) {
+  const double* xr = x + (int64_t)blockIdx.y * N;
+  unsigned long long m = 0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(xr[e]) & 0x7FFFFFFFFFFFFFFFull;
+    m = b > m ? b : m;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
+    m = v > m ? v : m;
+  }
+  if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(out + blockIdx.y, m);
+}
+
+// T: vector type (float / double); S: arithmetic type of the stencil (T, or
+// long long for the fixed-point FP64 operator, which needs umax)
+template <typename T, typename S>
 __global__ void __launch_bounds__(kTX * kTY) k_stencil_stream(int n, int KZ, T cK, T cM, const T* __restrict__ u,
-                                                              const T* __restrict__ g, T* __restrict__ y) {
+                                                              const T* __restrict__ g, T* __restrict__ y,
+                                                              const unsigned long long* __restrict__ umax) {
+  static_assert(sizeof(S) == sizeof(T), "staged planes hold T and are read as S");
+  constexpr bool FX = !std::is_same<S, T>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* Ur = reinterpret_cast<T*>(smem_raw);  // [3 ring slots][x, y, z][kP]
-  T* Cx = Ur + 9 * kP;                     // circulations of the current step
-  T* Cy = Cx + kP;
-  T* Cz = Cy + kP;
-  T* Gr = Cz + kP;                         // [2 ring slots][x, y, z][kTP]
-  const int64_t N3 = (int64_t)n * (n - 1) * (n - 1);
+  S* Ur = reinterpret_cast<S*>(smem_raw);  // [3 ring slots][x, y, z][kP]
+  S* Cx = Ur + 9 * kP;                     // circulations of the current step
+  S* Cy = Cx + kP;
+  S* Cz = Cy + kP;
+  T* Gr = reinterpret_cast<T*>(Cz + kP);   // [2 ring slots][x, y, z][kTP]
+  const uint32_t n1 = n - 1, N3 = (uint32_t)n * n1 * n1;  // offsets within one right-hand side fit in 32 bits
   // grid z = (z chunks) x (right-hand sides); each right-hand side is a
   // contiguous canonical vector
   const int nzc = (n + KZ - 1) / KZ;
@@ -77,115 +164,141 @@ __global__ void __launch_bounds__(kTX * kTY) k_stencil_stream(int n, int KZ, T c
   const int i0 = blockIdx.x * kTX, j0 = blockIdx.y * kTY, k0 = (blockIdx.z - rhs * nzc) * KZ;
   const int T_out = min(KZ, n - k0);  // output planes k0 .. k0 + T_out - 1
   const int tid = threadIdx.y * kTX + threadIdx.x;
-  const int warp = tid >> 5, lane = tid & 31;
-  const int n1 = n - 1;
+  // fixed point: u 2^fs with max |u| 2^fs < 2^55; results carry 2^-fs
+  int fs = 0;
+  T cKo = cK * T(1.0 / 6.0), cMo = cM * T(1.0 / 36.0);  // three-point weights [1, 4, 1]
+  if constexpr (FX) {
+    const unsigned long long mb = umax[rhs];
+    const int E = (int)((mb >> 52) & 0x7FF);  // max |u| < 2^(E - 1022)
+    fs = mb == 0 ? 0 : 55 - (E - 1022);
+    cKo = ldexp(cKo, -fs);
+    cMo = ldexp(cMo, -fs);
+    if (mb >= 0x7FF0000000000000ull) {  // Inf or NaN in u: the product is not finite
+      fs = 0;
+      cKo = cMo = T(NAN);
+    }
+  }
+  // staged positions of this thread: q = tid and q = tid + kTP (when < kP)
+  const int qa = tid, qb = tid + kTP;
+  const bool has_b = qb < kP;
+  const PlanePos pa = plane_pos(n, i0 + qa % kPX - 1, j0 + qa / kPX - 1);
+  const PlanePos pb = plane_pos(n, i0 + qb % kPX - 1, j0 + qb / kPX - 1);
+  const PlanePos pg = plane_pos(n, i0 + threadIdx.x, j0 + threadIdx.y);  // this thread's output column
+  // plane terms of the global offsets of plane k (used only when valid)
+  auto px = [&](int k) { return (uint32_t)(k - 1) * n1 * n; };
+  auto py = [&](int k) { return N3 + (uint32_t)(k - 1) * n * n1; };
+  auto pz = [&](int k) { return 2u * N3 + (uint32_t)k * n1 * n1; };
+  auto stage_pos = [&](S* Sp, int q, const PlanePos& p, int k, bool kn, bool ks) {
+    const bool vx = p.vx && kn, vy = p.vy && kn, vz = p.vz && ks;
+    T* St = reinterpret_cast<T*>(Sp);
+    cp_async_elem(St + q, u + (vx ? px(k) + p.ox : 0u), vx, u);
+    cp_async_elem(St + kP + q, u + (vy ? py(k) + p.oy : 0u), vy, u);
+    cp_async_elem(St + 2 * kP + q, u + (vz ? pz(k) + p.oz : 0u), vz, u);
+  };
   // stage u on plane k, [i0-1, i0+TX] x [j0-1, j0+TY], into ring slot `slot`
-  // (one warp per row along i; offsets within one direction fit in 32 bits
-  // for n <= 1290)
   auto stage_u = [&](int k, int slot) {
-    T* Sx = Ur + slot * 3 * kP;
+    S* Sp = Ur + slot * 3 * kP;
     const bool kn = in_node(k, n), ks = in_seg(k, n);
-    for (int b = warp; b < kPY; b += kTY) {
-      const int j = j0 + b - 1;
-      const bool jn = in_node(j, n), js = in_seg(j, n);
-      const uint32_t rx = ((uint32_t)(k - 1) * n1 + (j - 1)) * n;  // + i
-      const uint32_t ry = ((uint32_t)(k - 1) * n + j) * n1 - 1;    // + i
-      const uint32_t rz = ((uint32_t)k * n1 + (j - 1)) * n1 - 1;   // + i
-      for (int a = lane; a < kPX; a += 32) {
-        const int i = i0 + a - 1;
-        const int q = b * kPX + a;
-        const bool vx = in_seg(i, n) && jn && kn;
-        const bool vy = in_node(i, n) && js && kn;
-        const bool vz = in_node(i, n) && jn && ks;
-        cp_async_elem(Sx + q, u + (vx ? rx + i : 0), vx, u);
-        cp_async_elem(Sx + kP + q, u + N3 + (vy ? ry + i : 0), vy, u);
-        cp_async_elem(Sx + 2 * kP + q, u + 2 * N3 + (vz ? rz + i : 0), vz, u);
+    stage_pos(Sp, qa, pa, k, kn, ks);
+    if (has_b) stage_pos(Sp, qb, pb, k, kn, ks);
+  };
+  // fixed point: this thread's own staged values of ring slot `slot`,
+  // converted in place once its copies have landed
+  auto convert_own = [&](int slot) {
+    if constexpr (FX) {
+      S* Sp = Ur + slot * 3 * kP;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        Sp[c * kP + qa] = to_fixed(reinterpret_cast<const double*>(Sp)[c * kP + qa], fs);
+        if (has_b) Sp[c * kP + qb] = to_fixed(reinterpret_cast<const double*>(Sp)[c * kP + qb], fs);
       }
     }
   };
-  // stage g on plane k of the tile into ring slot `slot` (row = warp)
+  // stage g on plane k of the tile into ring slot `slot`
   auto stage_g = [&](int k, int slot) {
     T* Sg = Gr + slot * 3 * kTP;
-    const int j = j0 + warp, i = i0 + lane;
-    const bool jn = in_node(j, n), js = in_seg(j, n), kn = in_node(k, n), ks = in_seg(k, n);
-    const bool vx = in_seg(i, n) && jn && kn;
-    const bool vy = in_node(i, n) && js && kn;
-    const bool vz = in_node(i, n) && jn && ks;
-    const uint32_t ox = vx ? ((uint32_t)(k - 1) * n1 + (j - 1)) * n + i : 0;
-    const uint32_t oy = vy ? ((uint32_t)(k - 1) * n + j) * n1 + i - 1 : 0;
-    const uint32_t oz = vz ? ((uint32_t)k * n1 + (j - 1)) * n1 + i - 1 : 0;
-    cp_async_elem(Sg + tid, g + ox, vx, g);
-    cp_async_elem(Sg + kTP + tid, g + N3 + oy, vy, g);
-    cp_async_elem(Sg + 2 * kTP + tid, g + 2 * N3 + oz, vz, g);
+    const bool kn = in_node(k, n), ks = in_seg(k, n);
+    const bool vx = pg.vx && kn, vy = pg.vy && kn, vz = pg.vz && ks;
+    cp_async_elem(Sg + tid, g + (vx ? px(k) + pg.ox : 0u), vx, g);
+    cp_async_elem(Sg + kTP + tid, g + (vy ? py(k) + pg.oy : 0u), vy, g);
+    cp_async_elem(Sg + 2 * kTP + tid, g + (vz ? pz(k) + pg.oz : 0u), vz, g);
   };
   // u plane p of the chunk is z = k0 - 1 + p, held in ring slot p % 3
   stage_u(k0 - 1, 0);
   asm volatile("cp.async.commit_group;" ::: "memory");
 
-  const T w6 = T(1.0 / 6.0), w23 = T(2.0 / 3.0);
   const int a = threadIdx.x + 1, b = threadIdx.y + 1;
-  const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
   const int q = b * kPX + a;
-  auto f3 = [&](T m, T c0, T p1) { return w6 * (m + p1) + w23 * c0; };
+  auto f3 = [&](S m, S c0, S p1) { return (m + p1) + S(4) * c0; };
   // face mass along x / y of the current plane at (a,b) and its neighbours
   auto Xf = [&](int r) { return f3(Cx[r - 1], Cx[r], Cx[r + 1]); };
   auto Yf = [&](int r) { return f3(Cy[r - kPX], Cy[r], Cy[r + kPX]); };
   // rolling state: Cz at (a,b), (a,b-1), (a-1,b) and the in-plane edge-mass
   // rows of x- and y-edges, for planes k-1 (0) and k (1); Xf, Yf of plane k-1
-  T cz0[3] = {T(0), T(0), T(0)}, cz1[3] = {T(0), T(0), T(0)};
-  T rx0 = T(0), rx1 = T(0), ry0 = T(0), ry1 = T(0), yf_prev = T(0), xf_prev = T(0);
+  S cz0[3] = {S(0), S(0), S(0)}, cz1[3] = {S(0), S(0), S(0)};
+  S rx0 = S(0), rx1 = S(0), ry0 = S(0), ry1 = S(0), yf_prev = S(0), xf_prev = S(0);
+  // the circulation positions of this thread (fixed): neighbours staged?
+  const bool ha_a = qa % kPX + 1 < kPX, hb_a = qa / kPX + 1 < kPY;
+  const bool ha_b = qb % kPX + 1 < kPX, hb_b = qb / kPX + 1 < kPY;
+  // y = g - (cK K u + cM M u) (or cK K u + cM M u) of one edge from its
+  // integer-weighted sums kv, mv
+  auto combine = [&](S kv, S mv, const T* Gp) -> T {
+    T kd, md;
+    if constexpr (FX) {
+      kd = fixed_to_double(kv);
+      md = fixed_to_double(mv);
+    } else {
+      kd = kv;
+      md = mv;
+    }
+    if (g) return fma(-cMo, md, fma(-cKo, kd, *Gp));
+    return fma(cMo, md, cKo * kd);
+  };
   // step t forms the circulations of the current plane k0 + t (x- and
   // y-normal faces, t >= -1), those of the z-normal faces on the next plane
   // k0 + t + 1 and the next plane's edge-mass rows; outputs for t >= 0
   for (int t = -2; t < T_out; ++t) {
     asm volatile("cp.async.wait_group 0;" ::: "memory");
+    convert_own((t + 2) % 3);
     __syncthreads();  // plane t+2 and g(t) landed; step t-1 is done with the ring
     if (t + 2 <= T_out) stage_u(k0 + t + 2, (t + 3) % 3);
     if (g && t + 1 >= 0 && t + 1 < T_out) stage_g(k0 + t + 1, (t + 1) & 1);
     asm volatile("cp.async.commit_group;" ::: "memory");
-    const T* Uc = Ur + ((t + 4) % 3) * 3 * kP;  // plane k0 + t
-    const T* Un = Ur + ((t + 2) % 3) * 3 * kP;  // plane k0 + t + 1
-    for (int r = tid; r < kP; r += kTP) {
-      const int ra = r % kPX, rb = r / kPX;
-      const bool ha = ra + 1 < kPX, hb = rb + 1 < kPY;
+    const S* Uc = Ur + ((t + 4) % 3) * 3 * kP;  // plane k0 + t
+    const S* Un = Ur + ((t + 2) % 3) * 3 * kP;  // plane k0 + t + 1
+    auto circ = [&](int r, bool ha, bool hb) {
       if (t >= -1) {
         // cx(i,j,k) = uz(i,j+1,k) - uz(i,j,k) - uy(i,j,k+1) + uy(i,j,k)
-        Cx[r] = hb ? Uc[2 * kP + r + kPX] - Uc[2 * kP + r] - Un[kP + r] + Uc[kP + r] : T(0);
+        Cx[r] = hb ? Uc[2 * kP + r + kPX] - Uc[2 * kP + r] - Un[kP + r] + Uc[kP + r] : S(0);
         // cy(i,j,k) = ux(i,j,k+1) - ux(i,j,k) - uz(i+1,j,k) + uz(i,j,k)
-        Cy[r] = ha ? Un[r] - Uc[r] - Uc[2 * kP + r + 1] + Uc[2 * kP + r] : T(0);
+        Cy[r] = ha ? Un[r] - Uc[r] - Uc[2 * kP + r + 1] + Uc[2 * kP + r] : S(0);
       }
       // cz(i,j,k+1) = uy(i+1,j,k+1) - uy(i,j,k+1) - ux(i,j+1,k+1) + ux(i,j,k+1)
-      Cz[r] = (ha && hb) ? Un[kP + r + 1] - Un[kP + r] - Un[r + kPX] + Un[r] : T(0);
-    }
+      Cz[r] = (ha && hb) ? Un[kP + r + 1] - Un[kP + r] - Un[r + kPX] + Un[r] : S(0);
+    };
+    circ(qa, ha_a, hb_a);
+    if (has_b) circ(qb, ha_b, hb_b);
     __syncthreads();
-    const T cz2[3] = {Cz[q], Cz[q - kPX], Cz[q - 1]};
-    const T rx2 = f3(Un[q - kPX], Un[q], Un[q + kPX]);               // x-edges vary in y
-    const T ry2 = f3(Un[kP + q - 1], Un[kP + q], Un[kP + q + 1]);    // y-edges vary in x
+    const S cz2[3] = {Cz[q], Cz[q - kPX], Cz[q - 1]};
+    const S rx2 = f3(Un[q - kPX], Un[q], Un[q + kPX]);               // x-edges vary in y
+    const S ry2 = f3(Un[kP + q - 1], Un[kP + q], Un[kP + q + 1]);    // y-edges vary in x
     if (t >= -1) {
-      const T yf = Yf(q), xf = Xf(q);
+      const S yf = Yf(q), xf = Xf(q);
       if (t >= 0) {
         const int k = k0 + t;
+        const bool kn = in_node(k, n), ks = in_seg(k, n);
         const T* G = Gr + (t & 1) * 3 * kTP;
-        const T zf = f3(cz0[0], cz1[0], cz2[0]);    // Zf(a, b, k)
-        const T zf_b = f3(cz0[1], cz1[1], cz2[1]);  // Zf(a, b-1, k)
-        const T zf_a = f3(cz0[2], cz1[2], cz2[2]);  // Zf(a-1, b, k)
-        if (in_seg(i, n) && in_node(j, n) && in_node(k, n)) {
-          const T kv = -yf + yf_prev + zf - zf_b;
-          const T v = cK * kv + cM * f3(rx0, rx1, rx2);
-          y[off_x(n, i, j, k)] = g ? G[tid] - v : v;
-        }
-        if (in_node(i, n) && in_seg(j, n) && in_node(k, n)) {
-          const T kv = -zf + zf_a + xf - xf_prev;
-          const T v = cK * kv + cM * f3(ry0, ry1, ry2);
-          y[N3 + off_y(n, i, j, k)] = g ? G[kTP + tid] - v : v;
-        }
-        if (in_node(i, n) && in_node(j, n) && in_seg(k, n)) {
-          const T* Uz = Uc + 2 * kP;
-          const T kv = -xf + Xf(q - kPX) + yf - Yf(q - 1);
-          const T mz = f3(f3(Uz[q - kPX - 1], Uz[q - 1], Uz[q + kPX - 1]), f3(Uz[q - kPX], Uz[q], Uz[q + kPX]),
+        const S zf = f3(cz0[0], cz1[0], cz2[0]);    // Zf(a, b, k)
+        const S zf_b = f3(cz0[1], cz1[1], cz2[1]);  // Zf(a, b-1, k)
+        const S zf_a = f3(cz0[2], cz1[2], cz2[2]);  // Zf(a-1, b, k)
+        if (pg.vx && kn) y[px(k) + pg.ox] = combine((yf_prev - yf) + (zf - zf_b), f3(rx0, rx1, rx2), G + tid);
+        if (pg.vy && kn) y[py(k) + pg.oy] = combine((zf_a - zf) + (xf - xf_prev), f3(ry0, ry1, ry2), G + kTP + tid);
+        if (pg.vz && ks) {
+          const S* Uz = Uc + 2 * kP;
+          const S kv = (Xf(q - kPX) - xf) + (yf - Yf(q - 1));
+          const S mz = f3(f3(Uz[q - kPX - 1], Uz[q - 1], Uz[q + kPX - 1]), f3(Uz[q - kPX], Uz[q], Uz[q + kPX]),
                           f3(Uz[q - kPX + 1], Uz[q + 1], Uz[q + kPX + 1]));
-          const T v = cK * kv + cM * mz;
-          y[2 * N3 + off_z(n, i, j, k)] = g ? G[2 * kTP + tid] - v : v;
+          y[pz(k) + pg.oz] = combine(kv, mz, G + 2 * kTP + tid);
         }
       }
       yf_prev = yf;
@@ -529,6 +642,52 @@ __global__ void __launch_bounds__(256) k_cg_update(int64_t N, const double* __re
   }
 }
 
+// Fused steps of the mixed flexible PCG (FP64 vectors, float preconditioner):
+// u += a p ; r -= a q ; g32 = sto * r (the float right-hand side of the next
+// V-cycle) and block sums of r.r (partials in the layout of k_dot2)
+__global__ void __launch_bounds__(256) k_cg_update_rr(int64_t N, const double* __restrict__ alpha,
+                                                      const double* __restrict__ p, const double* __restrict__ q,
+                                                      double* __restrict__ u, double* __restrict__ r,
+                                                      const double* __restrict__ sto, float* __restrict__ g32,
+                                                      double* __restrict__ partial) {
+  const int64_t off = (int64_t)blockIdx.y * N;
+  const double a = alpha[blockIdx.y], s = sto[blockIdx.y];
+  double v[2] = {0.0, 0.0};
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
+    u[off + e] += a * p[off + e];
+    const double rn = r[off + e] - a * q[off + e];
+    r[off + e] = rn;
+    g32[off + e] = (float)(s * rn);
+    v[0] += rn * rn;
+  }
+  block_sum_store<2>(v, partial + 2 * ((int64_t)blockIdx.y * gridDim.x + blockIdx.x));
+}
+
+// block sums of x.z and y.z with z = sc * z32 (the preconditioned residual,
+// never formed in double)
+__global__ void __launch_bounds__(256) k_dot2_zf(int64_t N, const double* __restrict__ x, const double* __restrict__ y,
+                                                 const double* __restrict__ sc, const float* __restrict__ z32,
+                                                 double* __restrict__ partial) {
+  const int64_t off = (int64_t)blockIdx.y * N;
+  const double s = sc[blockIdx.y];
+  double v[2] = {0.0, 0.0};
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
+    const double z = s * (double)z32[off + e];
+    v[0] += x[off + e] * z;
+    v[1] += y[off + e] * z;
+  }
+  block_sum_store<2>(v, partial + 2 * ((int64_t)blockIdx.y * gridDim.x + blockIdx.x));
+}
+
+// p = sc * z32 + b p with b = ab[2 rhs + 1]
+__global__ void __launch_bounds__(256) k_axpby_zf(int64_t N, const double* __restrict__ sc, const float* __restrict__ z32,
+                                                  const double* __restrict__ ab, double* __restrict__ p) {
+  const int64_t off = (int64_t)blockIdx.y * N;
+  const double s = sc[blockIdx.y], b = ab[2 * blockIdx.y + 1];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x)
+    p[off + e] = s * (double)z32[off + e] + b * p[off + e];
+}
+
 // dst (float) = s * src (double), s = sc[rhs]
 __global__ void __launch_bounds__(256) k_to_f32(int64_t N, const double* __restrict__ sc, const double* __restrict__ src,
                                                 float* __restrict__ dst) {
@@ -570,22 +729,33 @@ static inline int grid_for(int64_t work, int sm_count, int per_sm = 8) {
 template <typename T>
 size_t stencil_smem() { return sizeof(T) * (12 * kP + 6 * kTP); }
 
+// the FP64 operator runs in fixed point (k_stencil_stream<double, long long>)
+template <typename T>
+using StencilArith = typename std::conditional<std::is_same<T, double>::value, long long, T>::type;
+
 template <typename T>
 cudaError_t prepare_stencil() {
-  return cudaFuncSetAttribute(k_stencil_stream<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stencil_smem<T>());
+  return cudaFuncSetAttribute(k_stencil_stream<T, StencilArith<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)stencil_smem<T>());
 }
 
 template <typename T>
-void launch_stencil(cudaStream_t s, int sm, int n, double cK, double cM, const T* u, const T* g, T* y, int R) {
+void launch_stencil(cudaStream_t s, int sm, int n, double cK, double cM, const T* u, const T* g, T* y, int R,
+                    unsigned long long* umax) {
   const int64_t N = 3LL * n * (n - 1) * (n - 1);
   if (N == 0) return;
+  if constexpr (std::is_same<T, double>::value) {
+    cudaMemsetAsync(umax, 0, sizeof(unsigned long long) * R, s);
+    k_absmax<<<dim3(grid_for(N, sm, 4), R), 256, 0, s>>>(N, u, umax);
+  }
   // z chunk: the longest (fewest halo planes) that still gives about four
   // CTAs per SM
   const int64_t cols = (int64_t)((n + kTX - 1) / kTX) * ((n + kTY - 1) / kTY) * R;
   int KZ = n;
   while (KZ > 4 && cols * ((n + KZ - 1) / KZ) < 4LL * sm) KZ = (KZ + 1) / 2;
   dim3 grid((n + kTX - 1) / kTX, (n + kTY - 1) / kTY, ((n + KZ - 1) / KZ) * R);
-  k_stencil_stream<T><<<grid, dim3(kTX, kTY), stencil_smem<T>(), s>>>(n, KZ, (T)cK, (T)cM, u, g, y);
+  k_stencil_stream<T, StencilArith<T>>
+      <<<grid, dim3(kTX, kTY), stencil_smem<T>(), s>>>(n, KZ, (T)cK, (T)cM, u, g, y, umax);
 }
 
 template <typename T>
@@ -689,6 +859,23 @@ void launch_cg_update(cudaStream_t s, int sm, int64_t N, const double* alpha, co
   k_cg_update<T><<<blas_grid(N, sm, R), 256, 0, s>>>(N, alpha, p, q, u, r);
 }
 
+void launch_cg_update_rr(cudaStream_t s, int sm, int64_t N, const double* alpha, const double* p, const double* q,
+                         double* u, double* r, const double* sto, float* g32, double* partial, double* out, int R) {
+  const int nb = reduction_blocks(sm);
+  k_cg_update_rr<<<dim3(nb, R), 256, 0, s>>>(N, alpha, p, q, u, r, sto, g32, partial);
+  k_finish2<<<R, 256, 0, s>>>(nb, partial, out);
+}
+void launch_dot2_zf(cudaStream_t s, int sm, int64_t N, const double* x, const double* y, const double* sc,
+                    const float* z32, double* partial, double* out, int R) {
+  const int nb = reduction_blocks(sm);
+  k_dot2_zf<<<dim3(nb, R), 256, 0, s>>>(N, x, y, sc, z32, partial);
+  k_finish2<<<R, 256, 0, s>>>(nb, partial, out);
+}
+void launch_axpby_zf(cudaStream_t s, int sm, int64_t N, const double* sc, const float* z32, const double* ab, double* p,
+                     int R) {
+  k_axpby_zf<<<blas_grid(N, sm, R), 256, 0, s>>>(N, sc, z32, ab, p);
+}
+
 void launch_to_f32(cudaStream_t s, int sm, int64_t N, const double* sc, const double* src, float* dst, int R) {
   k_to_f32<<<blas_grid(N, sm, R), 256, 0, s>>>(N, sc, src, dst);
 }
@@ -700,7 +887,8 @@ void launch_add_f32(cudaStream_t s, int sm, int64_t N, const double* sc, const f
 }
 
 #define NDMG_INST(T)                                                                                   \
-  template void launch_stencil<T>(cudaStream_t, int, int, double, double, const T*, const T*, T*, int); \
+  template void launch_stencil<T>(cudaStream_t, int, int, double, double, const T*, const T*, T*, int,    \
+                                  unsigned long long*);                                               \
   template cudaError_t prepare_stencil<T>();                                                          \
   template void launch_restrict<T>(cudaStream_t, int, int, const T*, T*, int);                        \
   template void launch_prolong_add<T>(cudaStream_t, int, int, const T*, T*, int);                     \

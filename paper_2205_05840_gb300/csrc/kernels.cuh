@@ -5,8 +5,12 @@
 
 namespace ndmg {
 
+// y = g - (cK K + cM M) u, or (cK K + cM M) u when g is null (cK = alpha h,
+// cM = beta h^3 for A_k).  For double vectors the operator runs in exact
+// fixed point; umax is R words of device scratch for its scale.
 template <typename T>
-void launch_stencil(cudaStream_t s, int sm, int n, double cK, double cM, const T* u, const T* g, T* y, int R);
+void launch_stencil(cudaStream_t s, int sm, int n, double cK, double cM, const T* u, const T* g, T* y, int R,
+                    unsigned long long* umax);
 template <typename T>
 cudaError_t prepare_stencil();
 template <typename T>
@@ -45,6 +49,14 @@ void launch_axpby_scalar(cudaStream_t s, int sm, int64_t N, double a, const T* x
 template <typename T>
 void launch_cg_update(cudaStream_t s, int sm, int64_t N, const double* alpha, const T* p, const T* q, T* u, T* r,
                       int R);
+// fused steps of the mixed flexible PCG (reductions: partials + finisher into
+// out[2 rhs], like launch_dot2)
+void launch_cg_update_rr(cudaStream_t s, int sm, int64_t N, const double* alpha, const double* p, const double* q,
+                         double* u, double* r, const double* sto, float* g32, double* partial, double* out, int R);
+void launch_dot2_zf(cudaStream_t s, int sm, int64_t N, const double* x, const double* y, const double* sc,
+                    const float* z32, double* partial, double* out, int R);
+void launch_axpby_zf(cudaStream_t s, int sm, int64_t N, const double* sc, const float* z32, const double* ab, double* p,
+                     int R);
 void launch_to_f32(cudaStream_t s, int sm, int64_t N, const double* sc, const double* src, float* dst, int R);
 void launch_from_f32(cudaStream_t s, int sm, int64_t N, const double* sc, const float* src, double* dst, int R);
 void launch_add_f32(cudaStream_t s, int sm, int64_t N, const double* sc, const float* src, double* dst, int R);

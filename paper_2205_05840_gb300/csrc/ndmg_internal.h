@@ -65,7 +65,6 @@ struct DevLevel {
   double* De64 = nullptr;     // 3 * 42*42 (edge-based smoother)
   float* De32 = nullptr;
   void* Wtc = nullptr;        // tensor-core operand images (bf16/fp16), see tc kernel
-  float* ypatch = nullptr;    // per-patch outputs of the tensor-core smoother (108 x patches x R)
 };
 
 }  // namespace ndmg
@@ -85,6 +84,7 @@ struct ndmg_handle {
   double* coef = nullptr;                 // per-right-hand-side BLAS scalars (4 slots x 2R)
   double* coef_host = nullptr;            // pinned staging of those scalars
   int* status = nullptr;                  // device status word (timeouts)
+  unsigned long long* umax = nullptr;     // per right-hand side max |u| of the fixed-point FP64 stencil
   int* status_host = nullptr;             // pinned mirror of the status word
   std::string err;
   // tracing: per kernel class, event pairs recorded around launches
@@ -95,4 +95,20 @@ struct ndmg_handle {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_free;
   int64_t launch_total = 0;
   int64_t vcycle_total = 0;
+  double trace_ms_graph[NDMG_K_COUNT] = {};  // elapsed time collected from graph replays
+  // the float V-cycle of the mixed preconditioner (z32 = MG(K, r32, 0, m)),
+  // captured once as a CUDA graph and replayed; traced launches inside it are
+  // bracketed by event-record nodes whose times are collected after each replay
+  struct GraphSpan {
+    int cls;
+    double units;
+    int nlaunch;
+    cudaEvent_t a, b;
+  };
+  bool use_graphs = true;
+  bool capturing = false;
+  bool graph_pending = false;               // a replay whose spans are not collected yet
+  cudaGraphExec_t vgraph = nullptr;
+  std::vector<GraphSpan> vgraph_spans;
+  int64_t vgraph_launches = 0, vgraph_vcycles = 0;
 };

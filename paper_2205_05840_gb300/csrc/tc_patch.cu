@@ -5,24 +5,23 @@
 //
 // with J_V A_V^{-1} J_V^t = W W^t, W the 108x60 Gram factor of the vertex
 // space operator (identical for every patch: constant alpha, uniform grid).
-// Two kernels:
-//   k_tc_patches: every vertex patch exactly once.  One CTA takes a brick of
-//     8 x 4 x 4 interior coarse vertices (one 128-row MMA tile, neighbouring
-//     rows are neighbouring vertices along x; the brick shape keeps the staged
-//     region small enough for three CTAs per SM) and
-//       1. stages r on the cells the brick's patches cover (cp.async, zero
-//          fill outside the box = the boundary condition), split by the parity
-//          of the cell coordinates so that neighbouring patches read
-//          neighbouring words;
-//       2. gathers the 128 patch vectors into A (128 x 112, bf16/fp16, K-major);
-//       3. D = A W             (tcgen05.mma M=128 N=64  K=112, FP32 in TMEM);
-//       4. A' = lowp(D)        (tcgen05.ld -> registers -> smem, over A);
-//       5. D' = A' W^t         (tcgen05.mma M=128 N=112 K=64, FP32 in TMEM, over D);
-//       6. stores the 108 outputs of every patch to y[l][p] (coalesced along p).
-//   k_vertex_gather: one thread per lattice point and edge direction sums the
-//     (up to 8) patch outputs that belong to its edge, adds its row of the
-//     interior-space solve A_T^{-1} r_T (edges inside a coarse element) and
-//     updates z once.  No atomics, no recomputed patches.
+// One kernel, k_tc_smoother.  A CTA takes a brick of 8 x 4 x 4 interior coarse
+// vertices (one 128-row MMA tile; neighbouring rows are neighbouring vertices
+// along x) and
+//   1. stages r on the cells the brick's patches cover (row-wise cp.async,
+//      zero fill outside the box = the boundary condition), split by the
+//      parity of the cell coordinates so that neighbouring patches read
+//      neighbouring words;
+//   2. gathers the 128 patch vectors into A (128 x 112, bf16/fp16, K-major);
+//   3. D = A W             (tcgen05.mma M=128 N=64  K=112, FP32 in TMEM);
+//   4. A' = lowp(D)        (tcgen05.ld -> registers -> smem, over A);
+//   5. D' = A' W^t         (tcgen05.mma M=128 N=112 K=64, FP32 in TMEM, over D);
+//   6. adds the 108 outputs of every patch and the interior-space solves of
+//      the coarse elements the brick owns into a shared-memory copy of the
+//      region (over A'), and
+//   7. adds that copy, times eta, to z with coalesced global reductions.
+// Every patch is computed once; edges near a brick face receive the
+// contributions of both bricks through the global reductions.
 //
 // Operand layout (SWIZZLE_NONE, K-major canonical layout): 8-row x 16-byte
 // "core matrices" stored contiguously; core matrix (g, c) of an R x K
@@ -66,11 +65,6 @@ __host__ __device__ constexpr int oct_base(int d, int o) {
   for (int q = 0; q < o; ++q) base += oct_size(d, q);
   return base;
 }
-__constant__ int kOctBase[24] = {
-    oct_base(0, 0), oct_base(0, 1), oct_base(0, 2), oct_base(0, 3), oct_base(0, 4), oct_base(0, 5), oct_base(0, 6),
-    oct_base(0, 7), oct_base(1, 0), oct_base(1, 1), oct_base(1, 2), oct_base(1, 3), oct_base(1, 4), oct_base(1, 5),
-    oct_base(1, 6), oct_base(1, 7), oct_base(2, 0), oct_base(2, 1), oct_base(2, 2), oct_base(2, 3), oct_base(2, 4),
-    oct_base(2, 5), oct_base(2, 6), oct_base(2, 7)};
 static_assert(oct_base(2, 7) + oct_size(2, 7) == kRegionAll, "octants tile the region");
 
 __host__ __device__ constexpr int region_at_c(int d, int i, int j, int k) {
@@ -79,11 +73,64 @@ __host__ __device__ constexpr int region_at_c(int d, int i, int j, int k) {
   const int PJ = PI * oct_len(dir_len(d, 1), j & 1);
   return oct_base(d, o) + (k >> 1) * PJ + (j >> 1) * PI + (i >> 1);
 }
-__device__ __forceinline__ int region_at(int d, int i, int j, int k) {
-  const int o = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
-  const int PI = oct_len(dir_len(d, 0), i & 1);
-  const int PJ = PI * oct_len(dir_len(d, 1), j & 1);
-  return kOctBase[d * 8 + o] + (k >> 1) * PJ + (j >> 1) * PI + (i >> 1);
+
+// The staged region in canonical order, one direction after another (i
+// fastest): entry = octant-layout index | i << 13 | j << 18 | k << 22.  Both
+// the staging of r and the flush into z walk it with all lanes busy.
+struct RegionTable {
+  uint32_t v[kRegionAll];
+};
+constexpr RegionTable make_region_table() {
+  RegionTable t{};
+  int q = 0;
+  for (int d = 0; d < 3; ++d)
+    for (int k = 0; k < dir_len(d, 2); ++k)
+      for (int j = 0; j < dir_len(d, 1); ++j)
+        for (int i = 0; i < dir_len(d, 0); ++i)
+          t.v[q++] = (uint32_t)region_at_c(d, i, j, k) | ((uint32_t)i << 13) | ((uint32_t)j << 18) | ((uint32_t)k << 22);
+  return t;
+}
+static_assert(kRegionAll < (1 << 13) && kCX <= 32 && kCY <= 16 && kCZ <= 16, "region table fields");
+__device__ const RegionTable kRegionTab = make_region_table();
+
+// Calls f(octant index, global offset within one right-hand side, edge is
+// interior) for every element of the direction-D part of the region.  Region
+// element (i, j, k) of direction D is the edge at global coordinates
+// 2 V0 + (i, j, k) - (2 along D, 1 across).
+template <int D, typename F>
+__device__ __forceinline__ void walk_region(int n, int VX, int VY, int VZ, int tid, F&& f) {
+  constexpr int q0 = D == 0 ? 0 : (D == 1 ? dir_size(0) : dir_size(0) + dir_size(1));
+  const uint32_t n1 = n - 1, N3 = (uint32_t)n * n1 * n1;
+  const int gi0 = 2 * VX - (D == 0 ? 2 : 1), gj0 = 2 * VY - (D == 1 ? 2 : 1), gk0 = 2 * VZ - (D == 2 ? 2 : 1);
+  // all table entries of this thread first: the copies / reductions below are
+  // ordered memory operations, so a load inside the loop would wait a full
+  // round trip per element
+  constexpr int kIt = (dir_size(D) + kThreads - 1) / kThreads;
+  uint32_t ent[kIt];
+#pragma unroll
+  for (int it = 0; it < kIt; ++it) {
+    const int q = tid + it * kThreads;
+    ent[it] = q < dir_size(D) ? __ldg(&kRegionTab.v[q0 + q]) : 0u;
+  }
+#pragma unroll
+  for (int it = 0; it < kIt; ++it) {
+    if (tid + it * kThreads >= dir_size(D)) break;
+    const uint32_t e = ent[it];
+    const int gi = gi0 + (int)((e >> 13) & 31u), gj = gj0 + (int)((e >> 18) & 15u), gk = gk0 + (int)(e >> 22);
+    bool in;
+    uint32_t off;
+    if (D == 0) {
+      in = (unsigned)gi < (unsigned)n && (unsigned)(gj - 1) < n1 && (unsigned)(gk - 1) < n1;
+      off = ((uint32_t)(gk - 1) * n1 + (uint32_t)(gj - 1)) * n + (uint32_t)gi;
+    } else if (D == 1) {
+      in = (unsigned)(gi - 1) < n1 && (unsigned)gj < (unsigned)n && (unsigned)(gk - 1) < n1;
+      off = N3 + ((uint32_t)(gk - 1) * n + (uint32_t)gj) * n1 + (uint32_t)(gi - 1);
+    } else {
+      in = (unsigned)(gi - 1) < n1 && (unsigned)(gj - 1) < n1 && (unsigned)gk < (unsigned)n;
+      off = 2u * N3 + ((uint32_t)gk * n1 + (uint32_t)(gj - 1)) * n1 + (uint32_t)(gi - 1);
+    }
+    f((int)(e & 8191u), off, in);
+  }
 }
 
 // shared memory: A' aliases A (A is dead once the first MMA completed)
@@ -94,7 +141,10 @@ constexpr int OFF_R = OFF_B2 + kN2 * kK2 * 2;
 constexpr int OFF_BAR = OFF_R + ((kRegionAll * 4 + 15) / 16) * 16;
 constexpr int OFF_TM = OFF_BAR + 16;
 constexpr int OFF_RED = OFF_TM + 16;
-constexpr int kSmem = OFF_RED + 32;
+constexpr int OFF_AT = OFF_RED + 32;          // A_T^{-1} (6 x 6, FP32)
+constexpr int kSmem = OFF_AT + 36 * 4;
+constexpr int OFF_ACC = OFF_A;                // region accumulator, over A' once D' is complete
+static_assert(kRegionAll * 4 <= kM * kK1 * 2, "accumulator fits in the A operand");
 static_assert(OFF_BAR % 8 == 0, "mbarrier alignment");
 static_assert(3 * (kSmem + 1024) <= 228 * 1024, "three CTAs per SM (228 KB, 1 KB reserved per CTA)");
 
@@ -236,25 +286,35 @@ __device__ __forceinline__ void gather_chunks(const float* R, uint8_t* A, int p,
   }
 }
 
-__device__ __forceinline__ bool interior(int n, int d, int i, int j, int k) {
-  const int p[3] = {i, j, k};
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    if (a == d) {
-      if (p[a] < 0 || p[a] >= n) return false;
-    } else if (p[a] < 1 || p[a] > n - 1) {
-      return false;
-    }
-  }
-  return true;
+// Octant index of interior edge w of the coarse element E = V0 - 1 + (ei,
+// ej, ek): its edge of direction dw = w / 2 has segment 2 E_dw + (w & 1) and
+// nodes 2 E + 1 across, i.e. region coordinates 2 (ei, ej, ek) + (w & 1 along,
+// 0 across); the parities, hence the octant, are fixed by w
+__device__ __forceinline__ int bubble_elem(int w, int ei, int ej, int ek) {
+  const int dw = w >> 1, s = w & 1;
+  const int ri = 2 * ei + (dw == 0 ? s : 0), rj = 2 * ej + (dw == 1 ? s : 0), rk = 2 * ek + (dw == 2 ? s : 0);
+  const int o = (dw == 0 ? s : 0) | ((dw == 1 ? s : 0) << 1) | ((dw == 2 ? s : 0) << 2);
+  const int PI = oct_len(dir_len(dw, 0), ri & 1);
+  const int PJ = PI * oct_len(dir_len(dw, 1), rj & 1);
+  return oct_base(dw, o) + (rk >> 1) * PJ + (rj >> 1) * PI + (ri >> 1);
 }
 
-// y[l * P + p] (per right-hand side) = (W W^t r_p)_l for every interior
-// vertex p = ((K-1) nv + (J-1)) nv + (I-1), nv = n/2 - 1
+// 16 columns [C0, C0 + 16) of D' for this thread's patch row, added into the
+// accumulator at the patch's edges (compile-time patch-local indices)
+template <int C0>
+__device__ __forceinline__ void scatter16(uint32_t taddr, float* acc, int a, int b, int c, float sc) {
+  float v[16];
+  tmem_ld16(taddr + C0, v);
+#pragma unroll
+  for (int t = 0; t < 16; ++t) {
+    if (C0 + t < 108) atomicAdd(acc + patch_elem(C0 + t, a, b, c), v[t] * sc);
+  }
+}
+
 template <bool FP16>
 __global__ void __launch_bounds__(kThreads, 3)
-    k_tc_patches(int n, const uint8_t* __restrict__ img, const float* __restrict__ r, float* __restrict__ y,
-                 int* __restrict__ status) {
+    k_tc_smoother(int n, const uint8_t* __restrict__ img, const float* __restrict__ AinvT, float eta,
+                  const float* __restrict__ r, float* __restrict__ z, int* __restrict__ status) {
   extern __shared__ __align__(128) uint8_t smem[];
   // a CTA of an earlier launch gave up on a wait: do nothing until the host
   // has read and cleared the status word
@@ -269,11 +329,12 @@ __global__ void __launch_bounds__(kThreads, 3)
   const int bx = brick % nbx, by = (brick / nbx) % nby, bz = brick / (nbx * nby);
   const int VX = 1 + bx * kBX, VY = 1 + by * kBY, VZ = 1 + bz * kBZ;  // first vertex of the brick
   const uint32_t n1 = n - 1, N3 = (uint32_t)n * n1 * n1;            // < 2^31 (checked on the host)
-  const int64_t P = (int64_t)nv * nv * nv;
   r += (int64_t)rhs * 3 * N3;
-  y += (int64_t)rhs * 108 * P;
+  z += (int64_t)rhs * 3 * N3;
 
   float* R = reinterpret_cast<float*>(smem + OFF_R);
+  float* ACC = reinterpret_cast<float*>(smem + OFF_ACC);
+  float* At = reinterpret_cast<float*>(smem + OFF_AT);
   const uint32_t bar0 = smem_u32(smem + OFF_BAR), bar1 = bar0 + 8;
   uint32_t* tm_slot = reinterpret_cast<uint32_t*>(smem + OFF_TM);
   float* red = reinterpret_cast<float*>(smem + OFF_RED);
@@ -290,27 +351,13 @@ __global__ void __launch_bounds__(kThreads, 3)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar1), "r"(1) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // 1. r on the region: edges of direction d start at global coordinates
-  //    2V0 - 2 along d and 2V0 - 1 across
+  if (tid < 36) At[tid] = __ldg(AinvT + tid);
   {
     const uint32_t rbase = smem_u32(R);
-    for (int q = tid; q < kRegionAll; q += kThreads) {
-      const int d = q >= dir_size(0) + dir_size(1) ? 2 : (q >= dir_size(0) ? 1 : 0);
-      const int e = q - (d == 0 ? 0 : d == 1 ? dir_size(0) : dir_size(0) + dir_size(1));
-      const int Li = dir_len(d, 0), Lj = dir_len(d, 1);
-      const int i = e % Li, jk = e / Li, j = jk % Lj, k = jk / Lj;
-      const int gi = 2 * VX + i - (d == 0 ? 2 : 1);
-      const int gj = 2 * VY + j - (d == 1 ? 2 : 1);
-      const int gk = 2 * VZ + k - (d == 2 ? 2 : 1);
-      const bool in = interior(n, d, gi, gj, gk);
-      uint32_t off = 0;
-      if (in) {
-        if (d == 0) off = ((uint32_t)(gk - 1) * n1 + (gj - 1)) * n + gi;
-        else if (d == 1) off = N3 + ((uint32_t)(gk - 1) * n + gj) * n1 + (gi - 1);
-        else off = 2 * N3 + ((uint32_t)gk * n1 + (gj - 1)) * n1 + (gi - 1);
-      }
-      cp_async4(rbase + 4u * region_at(d, i, j, k), r + off, in ? 4u : 0u);
-    }
+    auto stage = [&](int q, uint32_t off, bool in) { cp_async4(rbase + 4u * q, r + (in ? off : 0u), in ? 4u : 0u); };
+    walk_region<0>(n, VX, VY, VZ, tid, stage);
+    walk_region<1>(n, VX, VY, VZ, tid, stage);
+    walk_region<2>(n, VX, VY, VZ, tid, stage);
     const uint4* src = reinterpret_cast<const uint4*>(img);
     const uint32_t wbase = smem_u32(smem + OFF_B1);
     for (int q = tid; q < kImgBytes / 16; q += kThreads)
@@ -403,127 +450,73 @@ __global__ void __launch_bounds__(kThreads, 3)
   }
   if (ok) ok = mbar_wait(bar1, 0);
   fence_after();
+  // A' has been read by the tensor cores: its space becomes the accumulator;
+  // the CTA goes on only if every thread saw both products complete
+  for (int q = tid; q < kRegionAll; q += kThreads) ACC[q] = 0.f;
+  ok = __syncthreads_and(ok) != 0;
 
-  // ---- 6. y[l][p] = D' / (s_w^2 s_r): groups of 8 lanes are consecutive
-  //         vertices along x, so every store writes 32-byte runs ------------------
+  // ---- 6. accumulate: patch outputs (rows of D') and interior-space solves ----
   if (ok) {
     const int prow = (warp & 3) * 32 + lane;
     const int a = prow % kBX, b = (prow / kBX) % kBY, c = prow / (kBX * kBY);
     const bool live = VX + a <= nv && VY + b <= nv && VZ + c <= nv;
-    const int64_t pg = ((int64_t)(VZ + c - 1) * nv + (VY + b - 1)) * nv + (VX + a - 1);
     const float sc = wscale / rscale;
-    const int cbeg = (warp >> 2) ? 64 : 0, cend = (warp >> 2) ? kN2 : 64;
-#pragma unroll 1
-    for (int cb = cbeg; cb < cend; cb += 16) {
-      float v[16];
-      tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + cb, v);
-      if (live) {
-#pragma unroll
-        for (int t = 0; t < 16; ++t)
-          if (cb + t < 108) y[(int64_t)(cb + t) * P + pg] = v[t] * sc;
-      }
+    const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    // tcgen05.ld is warp-collective: every lane loads, live rows add
+    const float scl = live ? sc : 0.f;
+    if (warp < 4) {
+      scatter16<0>(taddr, ACC, a, b, c, scl);
+      scatter16<16>(taddr, ACC, a, b, c, scl);
+      scatter16<32>(taddr, ACC, a, b, c, scl);
+      scatter16<48>(taddr, ACC, a, b, c, scl);
+    } else {
+      scatter16<64>(taddr, ACC, a, b, c, scl);
+      scatter16<80>(taddr, ACC, a, b, c, scl);
+      scatter16<96>(taddr, ACC, a, b, c, scl);
     }
   } else if (tid == 0) {
     atomicExch(status, kTimeout);
   }
+  // interior spaces of the coarse elements the brick owns: E in [V0-1, V1-1]
+  // per axis, plus element nv on the last brick of an axis (its last vertex
+  // is nv); the 6 interior edges of E are row t = 2d + (segment parity)
+  if (ok) {
+    const int ex1 = VX + kBX - 1 >= nv ? nv : VX + kBX - 2;
+    const int ey1 = VY + kBY - 1 >= nv ? nv : VY + kBY - 2;
+    const int ez1 = VZ + kBZ - 1 >= nv ? nv : VZ + kBZ - 2;
+    const int mx = ex1 - VX + 2, my = ey1 - VY + 2, mz = ez1 - VZ + 2;
+    for (int q = tid; q < mx * my * mz * 6; q += kThreads) {
+      const int t = q % 6, e = q / 6;
+      const int ei = e % mx, ej = (e / mx) % my, ek = e / (mx * my);  // E - (V0 - 1)
+      int idx[6];
+#pragma unroll
+      for (int w = 0; w < 6; ++w) idx[w] = bubble_elem(w, ei, ej, ek);
+      float s = 0.f;
+      int it = idx[0];
+#pragma unroll
+      for (int w = 0; w < 6; ++w) {
+        s += At[t * 6 + w] * R[idx[w]];
+        if (w == t) it = idx[w];
+      }
+      atomicAdd(ACC + it, s);
+    }
+  }
   fence_before();
   __syncthreads();
+
+  // ---- 7. z += eta * accumulator ---------------------------------------------
+  if (ok) {
+    auto flush = [&](int q, uint32_t off, bool in) {
+      if (in) atomicAdd(z + off, eta * ACC[q]);
+    };
+    walk_region<0>(n, VX, VY, VZ, tid, flush);
+    walk_region<1>(n, VX, VY, VZ, tid, flush);
+    walk_region<2>(n, VX, VY, VZ, tid, flush);
+  }
   if (warp == 0) {
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
   }
-}
-
-// patch-local index of the edge whose box coordinates (in the 4x4x4 box of
-// its vertex) are (bi, bj, bk)
-__device__ __forceinline__ int box_local(int d, int bi, int bj, int bk) {
-  if (d == 0) return ((bk - 1) * 3 + (bj - 1)) * 4 + bi;
-  if (d == 1) return 36 + ((bk - 1) * 4 + bj) * 3 + (bi - 1);
-  return 72 + (bk * 3 + (bj - 1)) * 3 + (bi - 1);
-}
-
-// coarse vertices whose patch contains an edge: along the edge (segment s)
-// V with 2V - 2 <= s < 2V + 2; across (node t) V with |t - 2V| <= 1
-__device__ __forceinline__ int cand_along(int s, int (&V)[2]) {
-  V[0] = s >> 1;
-  V[1] = (s >> 1) + 1;
-  return 2;
-}
-__device__ __forceinline__ int cand_across(int t, int (&V)[2]) {
-  V[0] = t >> 1;
-  V[1] = (t + 1) >> 1;
-  return (t & 1) ? 2 : 1;
-}
-
-// z[e] += eta (row of the interior-space solve + sum of the patch outputs of e)
-// for the edge of direction d at lattice point (i, j, k)
-__device__ __forceinline__ void gather_edge(int n, int d, int i, int j, int k, const float* __restrict__ y, int64_t P,
-                                            const float* __restrict__ As, float eta, const float* __restrict__ r,
-                                            float* __restrict__ z) {
-  const int nv = n / 2 - 1;
-  const uint32_t n1 = n - 1, N3 = (uint32_t)n * n1 * n1;
-  const int c[3] = {i, j, k};
-  int VI[2], VJ[2], VK[2];
-  const int ni = d == 0 ? cand_along(i, VI) : cand_across(i, VI);
-  const int nj = d == 1 ? cand_along(j, VJ) : cand_across(j, VJ);
-  const int nk = d == 2 ? cand_along(k, VK) : cand_across(k, VK);
-  float s = 0.f;
-  for (int q = 0; q < nk; ++q) {
-    if (VK[q] < 1 || VK[q] > nv) continue;
-    for (int p = 0; p < nj; ++p) {
-      if (VJ[p] < 1 || VJ[p] > nv) continue;
-      for (int o = 0; o < ni; ++o) {
-        if (VI[o] < 1 || VI[o] > nv) continue;
-        const int l = box_local(d, i - 2 * VI[o] + 2, j - 2 * VJ[p] + 2, k - 2 * VK[q] + 2);
-        s += __ldg(y + (int64_t)l * P + ((int64_t)(VK[q] - 1) * nv + (VJ[p] - 1)) * nv + (VI[o] - 1));
-      }
-    }
-  }
-  // interior space of a coarse element: the edge is strictly inside it when
-  // both its node coordinates are odd; its row t = 2d + (segment parity)
-  const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
-  if ((c[t1] & 1) && (c[t2] & 1)) {
-    const int E[3] = {c[0] >> 1, c[1] >> 1, c[2] >> 1};
-    const int row = 2 * d + (c[d] & 1);
-    float acc = 0.f;
-#pragma unroll
-    for (int w = 0; w < 6; ++w) {
-      const int dw = w >> 1;
-      int g[3] = {2 * E[0] + 1, 2 * E[1] + 1, 2 * E[2] + 1};
-      g[dw] = 2 * E[dw] + (w & 1);
-      uint32_t off;
-      if (dw == 0) off = ((uint32_t)(g[2] - 1) * n1 + (g[1] - 1)) * n + g[0];
-      else if (dw == 1) off = N3 + ((uint32_t)(g[2] - 1) * n + g[1]) * n1 + (g[0] - 1);
-      else off = 2 * N3 + ((uint32_t)g[2] * n1 + (g[1] - 1)) * n1 + (g[0] - 1);
-      acc += As[row * 6 + w] * __ldg(r + off);
-    }
-    s += acc;
-  }
-  uint32_t off;
-  if (d == 0) off = ((uint32_t)(k - 1) * n1 + (j - 1)) * n + i;
-  else if (d == 1) off = N3 + ((uint32_t)(k - 1) * n + j) * n1 + (i - 1);
-  else off = 2 * N3 + ((uint32_t)k * n1 + (j - 1)) * n1 + (i - 1);
-  z[off] += eta * s;
-}
-
-__global__ void __launch_bounds__(256) k_vertex_gather(int n, const float* __restrict__ y, const float* __restrict__ AinvT,
-                                                       float eta, const float* __restrict__ r, float* __restrict__ z) {
-  __shared__ float As[36];
-  const int tid = threadIdx.y * 32 + threadIdx.x;
-  if (tid < 36) As[tid] = AinvT[tid];
-  __syncthreads();
-  const int rhs = blockIdx.z / n;
-  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z - rhs * n;
-  if (i >= n || j >= n) return;
-  const int nv = n / 2 - 1;
-  const int64_t P = (int64_t)nv * nv * nv;
-  const int64_t N = 3LL * n * (n - 1) * (n - 1);
-  y += (int64_t)rhs * 108 * P;
-  r += (int64_t)rhs * N;
-  z += (int64_t)rhs * N;
-  if (interior(n, 0, i, j, k)) gather_edge(n, 0, i, j, k, y, P, As, eta, r, z);
-  if (interior(n, 1, i, j, k)) gather_edge(n, 1, i, j, k, y, P, As, eta, r, z);
-  if (interior(n, 2, i, j, k)) gather_edge(n, 2, i, j, k, y, P, As, eta, r, z);
 }
 
 }  // namespace
@@ -563,31 +556,21 @@ cudaError_t upload_tc_operand(void** dst, const std::vector<double>& W, bool fp1
 }
 
 cudaError_t prepare_tc_patch() {
-  cudaError_t e = cudaFuncSetAttribute(k_tc_patches<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+  cudaError_t e = cudaFuncSetAttribute(k_tc_smoother<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_tc_patches<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    e = cudaFuncSetAttribute(k_tc_smoother<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
   return e;
 }
 
-int64_t tc_patch_buffer_floats(int n) {
-  const int64_t nv = n / 2 - 1;
-  return nv > 0 ? 108 * nv * nv * nv : 0;
-}
-
-void launch_tc_patches(cudaStream_t s, int n, const void* Wimg, bool fp16, const float* r, float* y, int* status,
-                       int R) {
+void launch_tc_smoother(cudaStream_t s, int n, const void* Wimg, bool fp16, const float* AinvT, double eta,
+                        const float* r, float* z, int* status, int R) {
   const int nv = n / 2 - 1;
   if (nv < 1) return;
   const int grid = ((nv + kBX - 1) / kBX) * ((nv + kBY - 1) / kBY) * ((nv + kBZ - 1) / kBZ) * R;
   if (fp16)
-    k_tc_patches<true><<<grid, kThreads, kSmem, s>>>(n, (const uint8_t*)Wimg, r, y, status);
+    k_tc_smoother<true><<<grid, kThreads, kSmem, s>>>(n, (const uint8_t*)Wimg, AinvT, (float)eta, r, z, status);
   else
-    k_tc_patches<false><<<grid, kThreads, kSmem, s>>>(n, (const uint8_t*)Wimg, r, y, status);
-}
-
-void launch_vertex_gather(cudaStream_t s, int n, const float* y, const float* AinvT, double eta, const float* r,
-                          float* z, int R) {
-  k_vertex_gather<<<dim3((n + 31) / 32, (n + 7) / 8, n * R), dim3(32, 8), 0, s>>>(n, y, AinvT, (float)eta, r, z);
+    k_tc_smoother<false><<<grid, kThreads, kSmem, s>>>(n, (const uint8_t*)Wimg, AinvT, (float)eta, r, z, status);
 }
 
 }  // namespace ndmg

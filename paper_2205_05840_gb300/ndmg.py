@@ -67,6 +67,7 @@ _SIGS = {
     "ndmg_trace_enable": [_vp, _i32, _i32],
     "ndmg_trace_read": [_vp, _i32, _P(_i64), _P(_d), _P(_d)],
     "ndmg_counters": [_vp, _P(_i64), _P(_i64)],
+    "ndmg_use_graphs": [_vp, _i32],
     "ndmg_dot_noalloc": [_i32, _vp, _vp, _i64, _P(_d), _vp],
 }
 for _name, _args in _SIGS.items():
@@ -260,6 +261,10 @@ class Solver:
         self._check(_lib.ndmg_trace_read(self._h, kernel_class, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(u)),
                     "trace_read")
         return n.value, ms.value, u.value
+
+    def use_graphs(self, on: bool = True):
+        """Replay the mixed-precision V-cycle as a CUDA graph (ndmg_use_graphs)."""
+        self._check(_lib.ndmg_use_graphs(self._h, 1 if on else 0), "use_graphs")
 
     def counters(self):
         """(kernels launched, finest-level V-cycles) since creation."""

@@ -79,6 +79,31 @@ def test_apply_and_residual_parity(n, n0, L, alpha, beta):
         assert rel(N(yl), Al @ xl) < 1e-13
 
 
+def test_apply_fixed_point_scales_and_nonfinite():
+    # the FP64 operator runs in exact fixed point scaled by max |u|: tiny,
+    # huge and widely spread inputs keep FP64 accuracy; Inf / NaN propagate
+    n = 12
+    S = ndmg.Solver(n, n_coarsest=3, alpha=2.0, beta=0.7)
+    A = hcurl.assemble(n, 1.0, 2.0, 0.7)
+    rng = np.random.default_rng(9)
+    x0 = rng.standard_normal(A.shape[0])
+    spread = x0 * 10.0 ** rng.uniform(-12, 0, x0.size)
+    for x in (1e-200 * x0, 1e200 * x0, spread, np.zeros_like(x0)):
+        y = torch.empty(A.shape[0], dtype=torch.float64, device=DEV)
+        S.apply(T(x), y)
+        ref = A @ x
+        if not ref.any():
+            assert not N(y).any()
+        else:
+            assert rel(N(y), ref) < 1e-13
+    for bad in (np.inf, np.nan):
+        x = x0.copy()
+        x[17] = bad
+        y = torch.empty(A.shape[0], dtype=torch.float64, device=DEV)
+        S.apply(T(x), y)
+        assert not np.isfinite(N(y)).all()
+
+
 @pytest.mark.parametrize("nc", [2, 3, 4, 8])
 def test_transfer_parity(nc):
     S = ndmg.Solver(2 * nc, n_coarsest=nc)
@@ -234,3 +259,5 @@ def test_error_paths():
     assert st == ndmg.INVALID_ARG
     with pytest.raises(ndmg.NdmgError):
         ndmg.Solver(8, n_coarsest=2, alpha=-1.0)
+    with pytest.raises(ndmg.NdmgError):      # 32-bit offsets within a right-hand side
+        ndmg.Solver(2048, n_coarsest=4)

@@ -162,3 +162,31 @@ def test_mixed_manufactured_64():
     sig = (np.sin(np.pi * h / 2) / (np.pi * h / 2)) ** 2
     c = (2 * np.pi ** 2 * alpha + 1) * sig ** 2 / (8 * alpha * np.sin(np.pi * h / 2) ** 2 * mu / h ** 2 + mu ** 2)
     assert rr <= 1e-8 and rel(N(u), c * inputs.sine_interpolant(n)) < 1e-6
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_graph_replay_matches_direct_launches(prec):
+    # the mixed solve replays its float V-cycle as a CUDA graph; direct
+    # launches give the same iteration count and launch / V-cycle counters,
+    # solutions agree to the solve tolerance (FP32 atomics make the last bits
+    # run-dependent), and traced kernel times are collected from the replays
+    n = 32
+    f = torch.tensor(inputs.random_load(n, 3), dtype=torch.float64, device=DEV)
+    out = {}
+    for graphs in (False, True):
+        S = ndmg.Solver(n, n_coarsest=4, precision=prec_code(prec))
+        S.use_graphs(graphs)
+        S.trace(ndmg.K_PATCH, True)
+        S.trace_read(ndmg.K_PATCH)
+        u = torch.zeros_like(f)
+        l0, v0 = S.counters()
+        st, it, rr = S.solve(f, u, tol=1e-10)
+        l1, v1 = S.counters()
+        n_l, ms, units = S.trace_read(ndmg.K_PATCH)
+        assert rr <= 1e-10 and n_l > 0 and ms > 0 and units > 0
+        out[graphs] = (it, l1 - l0, v1 - v0, n_l, units, u.cpu().numpy())
+    a, b = out[False], out[True]
+    assert abs(a[0] - b[0]) <= 1                      # iterations (last-bit effects only)
+    assert a[1] * b[2] == b[1] * a[2]                  # launches per V-cycle
+    assert a[3] * b[2] == b[3] * a[2] and abs(a[4] / a[3] - b[4] / b[3]) < 1e-9 * a[4] / a[3]
+    assert np.linalg.norm(a[5] - b[5]) <= 1e-8 * np.linalg.norm(a[5])
