@@ -87,6 +87,9 @@ typedef struct ndmg_opts {
   int32_t precision;  /* ndmg_precision */
   int32_t nrhs;       /* right-hand sides per call, >= 1 */
   void* stream;       /* cudaStream_t, NULL = legacy default stream */
+  int32_t subdomain;  /* cells per side of a smoother subdomain: 2 (Sec. 3.2: the coarse elements) or 4
+                         (4x4x4 blocks, 1176-edge vertex patches; vertex smoother only; every smoothed
+                         level a multiple of 4, i.e. n_coarsest even); 0 selects 2 */
 } ndmg_opts;
 
 typedef struct ndmg_handle ndmg_t;

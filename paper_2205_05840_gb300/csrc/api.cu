@@ -38,6 +38,7 @@ int cuda_fail(ndmg_t* h, cudaError_t e, const char* what) {
 struct Span {
   ndmg_t* h;
   cudaEvent_t end = nullptr;
+  bool external = false;  // recorded into a graph being captured
   Span(ndmg_t* h_, int cls, double units, int nlaunch = 1) : h(h_) {
     h->launch_total += nlaunch;
     if (!h->trace_on[cls]) return;
@@ -48,9 +49,10 @@ struct Span {
         cudaEventDestroy(gs.a);
         return;
       }
-      cudaEventRecord(gs.a, h->stream);
+      cudaEventRecordWithFlags(gs.a, h->stream, cudaEventRecordExternal);
       h->vgraph_spans.push_back(gs);
       end = gs.b;
+      external = true;
       return;
     }
     std::pair<cudaEvent_t, cudaEvent_t> pr{nullptr, nullptr};
@@ -67,7 +69,8 @@ struct Span {
     end = pr.second;
   }
   ~Span() {
-    if (end) cudaEventRecord(end, h->stream);
+    if (end && external) cudaEventRecordWithFlags(end, h->stream, cudaEventRecordExternal);
+    else if (end) cudaEventRecord(end, h->stream);
   }
 };
 
@@ -171,10 +174,37 @@ void op_edge_terms(ndmg_t* h, int k, const T* De, const T* r, T* z) {
 }
 
 // z += M_k^{-1} r (eta included), eq. (Preconditioner P) or (Preconditioner E)
+// subdomain size 4 (CUDA cores in every precision mode): interior spaces of
+// the 4x4x4 subdomains (108x108 dense) and the 1176-edge vertex patches in
+// Gram form
+const double* lv_Wg(DevLevel& L, double*) { return L.Wg64; }
+const float* lv_Wg(DevLevel& L, float*) { return L.Wg32; }
+const double* lv_WgT(DevLevel& L, double*) { return L.WgT64; }
+const float* lv_WgT(DevLevel& L, float*) { return L.WgT32; }
+
+template <typename T>
+void op_smoother_s4(ndmg_t* h, int k, const T* r, T* z) {
+  DevLevel& L = h->lv[k];
+  const int R = nrhs(h);
+  {
+    const PatchFamily fam = subdomain4_family(L.n);
+    Span sp(h, NDMG_K_BUBBLE, (double)fam.np[0] * fam.np[1] * fam.np[2] * 2.0 * 108 * 108 * R);
+    launch_patch_dense<T>(h->stream, h->sm_count, L.n, fam, lv_Ainv(L, (T*)nullptr), h->o.eta, r, z, R);
+  }
+  const PatchFamily fam = vertex4_family(L.n);
+  Span sp(h, NDMG_K_PATCH, (double)fam.np[0] * fam.np[1] * fam.np[2] * 4.0 * 1176 * 312 * R);
+  launch_patch_gram<T>(h->stream, h->sm_count, L.n, fam, 312, lv_Wg(L, (T*)nullptr), lv_WgT(L, (T*)nullptr),
+                       h->o.eta, r, z, R);
+}
+
 template <typename T>
 void op_smoother(ndmg_t* h, int k, const T* r, T* z) {
   DevLevel& L = h->lv[k];
   const int R = nrhs(h);
+  if (h->o.subdomain == 4) {
+    op_smoother_s4<T>(h, k, r, z);
+    return;
+  }
   {
     Span sp(h, NDMG_K_BUBBLE, bubble_bytes(L.n, sizeof(T)) * R);
     launch_bubble<T>(h->stream, h->sm_count, L.n, lv_Ainv(L, (T*)nullptr), h->o.eta, r, z, R);
@@ -191,6 +221,10 @@ template <>
 void op_smoother<float>(ndmg_t* h, int k, const float* r, float* z) {
   DevLevel& L = h->lv[k];
   const int R = nrhs(h);
+  if (h->o.subdomain == 4) {
+    op_smoother_s4<float>(h, k, r, z);
+    return;
+  }
   if (edge_smoother(h)) {  // the edge-based smoother runs on CUDA cores in every precision mode
     {
       Span sp(h, NDMG_K_BUBBLE, bubble_bytes(L.n, sizeof(float)) * R);
@@ -505,14 +539,20 @@ int vcycle_f32_graph(ndmg_t* h) {
     if (int st = collect_graph(h)) return st;
   }
   if (!h->vgraph) {
+    // captured on a private stream (the caller's may be the legacy default
+    // stream, which cannot be captured), replayed on the caller's
+    if (!h->cap_stream) NDMG_CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
     const int64_t l0 = h->launch_total, v0 = h->vcycle_total;
-    NDMG_CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeRelaxed));
+    cudaStream_t user = h->stream;
+    NDMG_CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed));
+    h->stream = h->cap_stream;
     h->capturing = true;
     cudaMemsetAsync(z32, 0, sizeof(float) * N * R, h->stream);
     op_vcycle<float>(h, K, r32, z32, true);
     h->capturing = false;
+    h->stream = user;
     cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
     if (e == cudaSuccess) e = cudaGraphInstantiate(&h->vgraph, g, 0);
     if (g) cudaGraphDestroy(g);
     h->vgraph_launches = h->launch_total - l0;
@@ -737,12 +777,14 @@ int solve_ir(ndmg_t* h, const double* f, double* u, double tol, double inner_tol
 void free_handle(ndmg_t* h) {
   if (!h) return;
   drop_graph(h);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (auto& L : h->lv) {
     cudaFree(L.g64); cudaFree(L.z64); cudaFree(L.r64);
     cudaFree(L.g32); cudaFree(L.z32); cudaFree(L.r32);
     cudaFree(L.AinvT64); cudaFree(L.AinvT32); cudaFree(L.Dv64); cudaFree(L.Dv32);
     cudaFree(L.De64); cudaFree(L.De32);
     cudaFree(L.Wtc);
+    cudaFree(L.Wg64); cudaFree(L.WgT64); cudaFree(L.Wg32); cudaFree(L.WgT32);
   }
   cudaFree(h->Ainv0);
   for (int i = 0; i < 6; ++i) { cudaFree(h->w64[i]); cudaFree(h->w32[i]); }
@@ -768,9 +810,20 @@ int build_operators(ndmg_t* h) {
     for (int k = 1; k <= h->K; ++k) {
       DevLevel& L = h->lv[k];
       LocalOps ops;
-      build_local_ops(L.n, o.L, o.alpha, o.beta, &ops);
+      build_local_ops(L.n, o.L, o.alpha, o.beta, &ops, o.subdomain);
       NDMG_CK(upload(&L.AinvT64, ops.AinvT));
       NDMG_CK(upload(&L.AinvT32, ops.AinvT));
+      if (o.subdomain == 4) {
+        // Gram factor (1176 x 312) and its transpose for k_patch_gram
+        std::vector<double> WT(ops.Wv.size());
+        for (int e = 0; e < ops.mV; ++e)
+          for (int c = 0; c < ops.nG; ++c) WT[(size_t)c * ops.mV + e] = ops.Wv[(size_t)e * ops.nG + c];
+        NDMG_CK(upload(&L.Wg64, ops.Wv));
+        NDMG_CK(upload(&L.WgT64, WT));
+        NDMG_CK(upload(&L.Wg32, ops.Wv));
+        NDMG_CK(upload(&L.WgT32, WT));
+        continue;
+      }
       NDMG_CK(upload(&L.Dv64, ops.Dv));
       NDMG_CK(upload(&L.Dv32, ops.Dv));
       std::vector<double> de;
@@ -815,6 +868,7 @@ int ndmg_opts_default(ndmg_opts* o) {
   o->precision = NDMG_PREC_FP64;
   o->nrhs = 1;
   o->stream = nullptr;
+  o->subdomain = 2;
   return NDMG_OK;
 }
 
@@ -826,6 +880,9 @@ int ndmg_create(const ndmg_opts* o, ndmg_t** out) {
   if (!(o->L > 0) || !(o->alpha > 0) || !(o->beta > 0) || o->m < 1 || o->nrhs < 1) return NDMG_INVALID_ARG;
   if (o->nrhs > 4096) return NDMG_INVALID_ARG;
   if (o->smoother != NDMG_SMOOTHER_VERTEX && o->smoother != NDMG_SMOOTHER_EDGE) return NDMG_INVALID_ARG;
+  const int sub = o->subdomain == 0 ? 2 : o->subdomain;
+  if (sub != 2 && sub != 4) return NDMG_INVALID_ARG;
+  if (sub == 4 && (o->smoother != NDMG_SMOOTHER_VERTEX || o->n_coarsest % 2 != 0)) return NDMG_INVALID_ARG;
   if (o->precision < NDMG_PREC_FP64 || o->precision > NDMG_PREC_FP32) return NDMG_INVALID_ARG;
   if (edges(o->n_coarsest) > 4096) return NDMG_INVALID_ARG;   // dense coarsest inverse
   // 32-bit edge offsets within one right-hand side (stencil, tensor-core
@@ -840,6 +897,7 @@ int ndmg_create(const ndmg_opts* o, ndmg_t** out) {
   if (!h) return NDMG_OUT_OF_MEMORY;
   h->o = *o;
   if (!(h->o.eta > 0)) h->o.eta = h->o.smoother == NDMG_SMOOTHER_EDGE ? 1.0 / 13.0 : 1.0 / 9.0;
+  if (h->o.subdomain == 0) h->o.subdomain = 2;
   h->stream = (cudaStream_t)o->stream;
   h->K = K;
   int dev = 0;
@@ -892,6 +950,8 @@ int ndmg_create(const ndmg_opts* o, ndmg_t** out) {
   if (ae == cudaSuccess) ae = prepare_stencil<float>();
   if (ae == cudaSuccess) ae = prepare_vertex_dense<double>();
   if (ae == cudaSuccess) ae = prepare_vertex_dense<float>();
+  if (ae == cudaSuccess && h->o.subdomain == 4) ae = prepare_patch_gram<double>();
+  if (ae == cudaSuccess && h->o.subdomain == 4) ae = prepare_patch_gram<float>();
   if (ae == cudaSuccess && mixed(h)) ae = prepare_tc_patch();
   if (ae != cudaSuccess) {
     free_handle(h);

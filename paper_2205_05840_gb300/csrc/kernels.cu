@@ -509,7 +509,8 @@ __global__ void __launch_bounds__(128) k_patch_dense(int n, PatchFamily fam, con
     const int pc = (int)(P / ((int64_t)fam.np[0] * fam.np[1])) + fam.p0[2];
     const int c = loc[l];
     const int d = c >> 12, i = (c >> 8) & 15, j = (c >> 4) & 15, k = c & 15;
-    return edge_gidx(n, d, 2 * pa - fam.shift[0] + i, 2 * pb - fam.shift[1] + j, 2 * pc - fam.shift[2] + k);
+    return edge_gidx(n, d, fam.stride * pa - fam.shift[0] + i, fam.stride * pb - fam.shift[1] + j,
+                     fam.stride * pc - fam.shift[2] + k);
   };
   for (int64_t base = (int64_t)blockIdx.x * PB; base < NP; base += (int64_t)gridDim.x * PB) {
     __syncthreads();
@@ -531,6 +532,84 @@ __global__ void __launch_bounds__(128) k_patch_dense(int n, PatchFamily fam, con
 #pragma unroll
       for (int p = 0; p < PB; ++p)
         if (base + p < NP) atomicAdd(z + gidx_of(base + p, row), eta * acc[p]);
+    }
+  }
+}
+
+// Vertex-space solves of large patches in Gram form (subdomain size 4: 1176
+// edges, 312 on the interface): a CTA takes PB patches at a time, gathers
+// their residuals, forms t = W^t r_p (nG values per patch; threads along the
+// columns of W, so W is read coalesced from L2) and y = W t (threads along
+// the rows, reading W^t coalesced), and adds eta * y to z.
+template <typename T, int PB>
+__global__ void __launch_bounds__(256) k_patch_gram(int n, PatchFamily fam, int nG, const T* __restrict__ W,
+                                                    const T* __restrict__ WT, T eta, const T* __restrict__ r,
+                                                    T* __restrict__ z) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nl = fam.nloc;
+  T* Rs = reinterpret_cast<T*>(smem_raw);           // nl * PB
+  T* Ts = Rs + (size_t)nl * PB;                      // nG * PB
+  int* loc = reinterpret_cast<int*>(Ts + (size_t)nG * PB);
+  const int64_t NP = (int64_t)fam.np[0] * fam.np[1] * fam.np[2];
+  const int64_t N3 = (int64_t)n * (n - 1) * (n - 1);
+  r += (int64_t)blockIdx.y * 3 * N3;
+  z += (int64_t)blockIdx.y * 3 * N3;
+  const int bx = fam.b[0], by = fam.b[1], bz = fam.b[2];
+  const int cx = bx * (by - 1) * (bz - 1), cy = (bx - 1) * by * (bz - 1);
+  for (int l = threadIdx.x; l < nl; l += blockDim.x) {
+    int d, i, j, k, e = l;
+    if (e < cx) {
+      d = 0; i = e % bx; j = (e / bx) % (by - 1) + 1; k = e / (bx * (by - 1)) + 1;
+    } else if ((e -= cx) < cy) {
+      d = 1; i = e % (bx - 1) + 1; j = (e / (bx - 1)) % by; k = e / ((bx - 1) * by) + 1;
+    } else {
+      e -= cy;
+      d = 2; i = e % (bx - 1) + 1; j = (e / (bx - 1)) % (by - 1) + 1; k = e / ((bx - 1) * (by - 1));
+    }
+    loc[l] = (((d * 16 + i) * 16 + j) * 16) + k;
+  }
+  auto gidx_of = [&](int64_t P, int l) {
+    const int pa = (int)(P % fam.np[0]) + fam.p0[0];
+    const int pb = (int)((P / fam.np[0]) % fam.np[1]) + fam.p0[1];
+    const int pc = (int)(P / ((int64_t)fam.np[0] * fam.np[1])) + fam.p0[2];
+    const int c = loc[l];
+    const int d = c >> 12, i = (c >> 8) & 15, j = (c >> 4) & 15, k = c & 15;
+    return edge_gidx(n, d, fam.stride * pa - fam.shift[0] + i, fam.stride * pb - fam.shift[1] + j,
+                     fam.stride * pc - fam.shift[2] + k);
+  };
+  for (int64_t base = (int64_t)blockIdx.x * PB; base < NP; base += (int64_t)gridDim.x * PB) {
+    __syncthreads();
+    for (int q = threadIdx.x; q < nl * PB; q += blockDim.x) {
+      const int p = q / nl, l = q % nl;
+      const int64_t P = base + p;
+      Rs[l * PB + p] = P < NP ? __ldg(r + gidx_of(P, l)) : T(0);
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < nG; c += blockDim.x) {
+      T acc[PB];
+#pragma unroll
+      for (int p = 0; p < PB; ++p) acc[p] = T(0);
+      for (int l = 0; l < nl; ++l) {
+        const T w = __ldg(W + (size_t)l * nG + c);
+#pragma unroll
+        for (int p = 0; p < PB; ++p) acc[p] += w * Rs[l * PB + p];
+      }
+#pragma unroll
+      for (int p = 0; p < PB; ++p) Ts[c * PB + p] = acc[p];
+    }
+    __syncthreads();
+    for (int l = threadIdx.x; l < nl; l += blockDim.x) {
+      T acc[PB];
+#pragma unroll
+      for (int p = 0; p < PB; ++p) acc[p] = T(0);
+      for (int c = 0; c < nG; ++c) {
+        const T w = __ldg(WT + (size_t)c * nl + l);
+#pragma unroll
+        for (int p = 0; p < PB; ++p) acc[p] += w * Ts[c * PB + p];
+      }
+#pragma unroll
+      for (int p = 0; p < PB; ++p)
+        if (base + p < NP) atomicAdd(z + gidx_of(base + p, l), eta * acc[p]);
     }
   }
 }
@@ -808,6 +887,47 @@ PatchFamily vertex_family(int n) {
   return PatchFamily{108, {4, 4, 4}, {nv, nv, nv}, {1, 1, 1}, {2, 2, 2}};
 }
 
+PatchFamily subdomain4_family(int n) {
+  const int nc = n / 4;
+  PatchFamily f{108, {4, 4, 4}, {nc, nc, nc}, {0, 0, 0}, {0, 0, 0}};
+  f.stride = 4;
+  return f;
+}
+
+PatchFamily vertex4_family(int n) {
+  const int nv = n / 4 - 1;
+  PatchFamily f{1176, {8, 8, 8}, {nv, nv, nv}, {1, 1, 1}, {4, 4, 4}};
+  f.stride = 4;
+  return f;
+}
+
+constexpr int kGramPB64 = 8, kGramPB32 = 16;
+template <typename T>
+static constexpr int gram_pb() { return sizeof(T) == 8 ? kGramPB64 : kGramPB32; }
+template <typename T>
+size_t patch_gram_smem(int nloc, int nG) {
+  return sizeof(T) * (size_t)(nloc + nG) * gram_pb<T>() + sizeof(int) * nloc;
+}
+
+template <typename T>
+cudaError_t prepare_patch_gram() {
+  return cudaFuncSetAttribute(k_patch_gram<T, gram_pb<T>()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)patch_gram_smem<T>(1176, 312));
+}
+
+template <typename T>
+void launch_patch_gram(cudaStream_t s, int sm, int n, const PatchFamily& fam, int nG, const T* W, const T* WT,
+                       double eta, const T* r, T* z, int R) {
+  const int64_t NP = (int64_t)fam.np[0] * fam.np[1] * fam.np[2];
+  if (NP <= 0) return;
+  constexpr int PB = gram_pb<T>();
+  int64_t blocks = (NP + PB - 1) / PB;
+  const int64_t cap = (int64_t)sm * 2;
+  if (blocks > cap) blocks = cap;
+  k_patch_gram<T, PB><<<dim3((int)blocks, R), 256, patch_gram_smem<T>(fam.nloc, nG), s>>>(n, fam, nG, W, WT,
+                                                                                           (T)eta, r, z);
+}
+
 PatchFamily edge_family(int n, int d) {
   const int nc = n / 2;
   PatchFamily f{42, {4, 4, 4}, {nc - 1, nc - 1, nc - 1}, {1, 1, 1}, {2, 2, 2}};
@@ -900,6 +1020,9 @@ void launch_add_f32(cudaStream_t s, int sm, int64_t N, const double* sc, const f
   template void launch_dot2<T>(cudaStream_t, int, int64_t, const T*, const T*, const T*, const T*,    \
                                double*, double*, int);                                                \
   template void launch_axpby<T>(cudaStream_t, int, int64_t, const double*, const T*, T*, int);         \
+  template void launch_patch_gram<T>(cudaStream_t, int, int, const PatchFamily&, int, const T*, const T*, \
+                                     double, const T*, T*, int);                                       \
+  template cudaError_t prepare_patch_gram<T>();                                                       \
   template void launch_axpby_scalar<T>(cudaStream_t, int, int64_t, double, const T*, double, T*);      \
   template void launch_cg_update<T>(cudaStream_t, int, int64_t, const double*, const T*, const T*, T*, T*, int);
 NDMG_INST(double)

@@ -25,14 +25,26 @@ template <typename T>
 void launch_vertex_dense(cudaStream_t s, int sm, int n, const T* D, double eta, const T* r, T* z, int R);
 // A lattice of box-shaped patches (see k_patch_dense in kernels.cu).
 struct PatchFamily {
-  int nloc;      // interior edges of one box
-  int b[3];      // box extents in cells
-  int np[3];     // patches per axis
-  int p0[3];     // first patch index per axis
-  int shift[3];  // box origin = 2 * patch index - shift
+  int nloc;        // interior edges of one box
+  int b[3];        // box extents in cells
+  int np[3];       // patches per axis
+  int p0[3];       // first patch index per axis
+  int shift[3];    // box origin = stride * patch index - shift
+  int stride = 2;  // cells between neighbouring patches
 };
 PatchFamily vertex_family(int n);
 PatchFamily edge_family(int n, int d);
+// subdomain size 4: the 4x4x4-cell subdomains (interior spaces, 108 edges)
+// and the 8x8x8-cell vertex patches around their interior vertices (1176)
+PatchFamily subdomain4_family(int n);
+PatchFamily vertex4_family(int n);
+// z += eta * W (W^t r_p) for every patch p of the family (W: nloc x nG
+// row-major, WT: its transpose), batches of patches per CTA
+template <typename T>
+void launch_patch_gram(cudaStream_t s, int sm, int n, const PatchFamily& fam, int nG, const T* W, const T* WT,
+                       double eta, const T* r, T* z, int R);
+template <typename T>
+cudaError_t prepare_patch_gram();
 template <typename T>
 void launch_patch_dense(cudaStream_t s, int sm, int n, const PatchFamily& fam, const T* D, double eta, const T* r,
                         T* z, int R);

@@ -32,17 +32,22 @@ struct Box {
 struct LocalOps {
   int n;                      // cells per side on this level
   double h;
-  std::vector<double> AinvT;  // 6x6 inverse of the interior-space matrix A_T
-  std::vector<double> Dv;     // 108x108 J_V A_V^{-1} J_V^t (patch-local order)
-  std::vector<double> Wv;     // 108x60 Gram factor, Dv = Wv Wv^t
-  std::vector<double> De[3];  // 42x42 J_E A_E^{-1} J_E^t for coarse edges along x, y, z
+  int s = 2;                  // subdomain size (cells per side of a subdomain)
+  int mT = 6;                 // interior edges of one subdomain: 3 s (s-1)^2
+  int mV = 108;               // edges of one vertex patch: 3 (2s) (2s-1)^2
+  int nG = 60;                // interface edges of one vertex patch
+  std::vector<double> AinvT;  // mT x mT inverse of the interior-space matrix A_T
+  std::vector<double> Dv;     // mV x mV J_V A_V^{-1} J_V^t (patch-local order; s = 2 only)
+  std::vector<double> Wv;     // mV x nG Gram factor, J_V A_V^{-1} J_V^t = Wv Wv^t
+  std::vector<double> De[3];  // 42x42 J_E A_E^{-1} J_E^t for coarse edges along x, y, z (s = 2)
 };
 
 // Dense assembled matrix of a box with Dirichlet (interior-edge) DOFs for
 // a(w,v) = alpha (curl w, curl v) + beta (w, v) on cubes of side h.
 std::vector<double> box_matrix(const Box& box, double h, double alpha, double beta);
-// Vertex-patch operator and Gram factor, interior-space inverse for level n.
-void build_local_ops(int n, double L, double alpha, double beta, LocalOps* out);
+// Vertex-patch operator and Gram factor, interior-space inverse for level n
+// with subdomains of s x s x s cells (s = 2: the coarse elements).
+void build_local_ops(int n, double L, double alpha, double beta, LocalOps* out, int s = 2);
 // Inverse of the coarsest operator (n0^3 box).
 std::vector<double> coarse_inverse(int n0, double L, double alpha, double beta);
 // In-place Cholesky of an SPD matrix (lower), returns false if not SPD.
@@ -65,6 +70,10 @@ struct DevLevel {
   double* De64 = nullptr;     // 3 * 42*42 (edge-based smoother)
   float* De32 = nullptr;
   void* Wtc = nullptr;        // tensor-core operand images (bf16/fp16), see tc kernel
+  // subdomain size 4: Gram factor of the 1176-edge vertex patches (1176 x 312)
+  // and its transpose, for k_patch_gram
+  double *Wg64 = nullptr, *WgT64 = nullptr;
+  float *Wg32 = nullptr, *WgT32 = nullptr;
 };
 
 }  // namespace ndmg
@@ -109,6 +118,7 @@ struct ndmg_handle {
   bool capturing = false;
   bool graph_pending = false;               // a replay whose spans are not collected yet
   cudaGraphExec_t vgraph = nullptr;
+  cudaStream_t cap_stream = nullptr;        // private stream the graph is captured on
   std::vector<GraphSpan> vgraph_spans;
   int64_t vgraph_launches = 0, vgraph_vcycles = 0;
 };

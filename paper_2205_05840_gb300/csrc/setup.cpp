@@ -152,33 +152,37 @@ std::vector<double> spd_inverse(const std::vector<double>& a, int n, bool* ok) {
 
 // J_D A_D^{-1} J_D^t for the discrete-harmonic patch space of a box of
 // cells (Sec. 3.2, eq. vertex space / edge space): the box's edges split into
-// the interiors of its 2x2x2 coarse elements (I) and the rest (G); with
+// the interiors of its s x s x s subdomains (I) and the rest (G); with
 // S = A_GG - A_GI A_II^{-1} A_IG = R R^t and H = [-A_II^{-1} A_IG ; I],
 // W = H R^{-t} and D = W W^t (= A_p^{-1} - sum_T J_T A_T^{-1} J_T^t).
-// AinvT: the 6x6 interior-space inverse (for the self-check).
-static void patch_operator(const Box& pb, double h, double alpha, double beta, const std::vector<double>& AinvT,
-                           std::vector<double>* D, std::vector<double>* W, int* n_interface) {
+// AinvT: the interior-space inverse of one subdomain in the canonical order
+// of its s-box (for the self-check).  D may be null (large patches: only W).
+static void patch_operator(const Box& pb, int s, double h, double alpha, double beta,
+                           const std::vector<double>& AinvT, std::vector<double>* D, std::vector<double>* W,
+                           int* n_interface) {
   const int np = (int)pb.size();
   std::vector<double> Ap = box_matrix(pb, h, alpha, beta);
-  // the interior spaces of the coarse elements inside the box, each in the
-  // 2x2x2 box order; Bblk = sum_T J_T A_T^{-1} J_T^t restricted to the box
+  // the interior spaces of the subdomains inside the box, each in its s-box
+  // order; Bblk = sum_T J_T A_T^{-1} J_T^t restricted to the box
+  const Box sb{{s, s, s}};
+  const int mT = (int)sb.size();
   std::vector<int> isB(np, 0);
   std::vector<double> Bblk((size_t)np * np, 0.0);
-  for (int sr = 0; sr < pb.b[2] / 2; ++sr)
-    for (int sq = 0; sq < pb.b[1] / 2; ++sq)
-      for (int sp = 0; sp < pb.b[0] / 2; ++sp) {
-        const int o[3] = {2 * sp, 2 * sq, 2 * sr};
-        int ids[6];
-        int t = 0;
+  std::vector<int> ids(mT);
+  for (int sr = 0; sr < pb.b[2] / s; ++sr)
+    for (int sq = 0; sq < pb.b[1] / s; ++sq)
+      for (int sp = 0; sp < pb.b[0] / s; ++sp) {
+        const int o[3] = {s * sp, s * sq, s * sr};
         for (int d = 0; d < 3; ++d)
-          for (int s = 0; s < 2; ++s) {
-            int p[3] = {o[0] + 1, o[1] + 1, o[2] + 1};
-            p[d] = o[d] + s;
-            ids[t++] = (int)pb.index(d, p[0], p[1], p[2]);
-          }
-        for (int a = 0; a < 6; ++a) {
+          for (int k = 0; k < s; ++k)
+            for (int j = 0; j < s; ++j)
+              for (int i = 0; i < s; ++i) {
+                const int64_t l = sb.index(d, i, j, k);
+                if (l >= 0) ids[l] = (int)pb.index(d, o[0] + i, o[1] + j, o[2] + k);
+              }
+        for (int a = 0; a < mT; ++a) {
           isB[ids[a]] = 1;
-          for (int b = 0; b < 6; ++b) Bblk[(size_t)ids[a] * np + ids[b]] = AinvT[a * 6 + b];
+          for (int b = 0; b < mT; ++b) Bblk[(size_t)ids[a] * np + ids[b]] = AinvT[(size_t)a * mT + b];
         }
       }
 
@@ -222,15 +226,18 @@ static void patch_operator(const Box& pb, double h, double alpha, double beta, c
   std::vector<double> R = S;
   if (!cholesky(R, nG)) throw std::runtime_error("Schur complement is not SPD");
   // W^t = R^{-1} H^t with H = [-X ; I] (patch order): forward substitution on
-  // each of the 108 columns of H^t
+  // each of the np columns of H^t
   (*W).assign((size_t)np * nG, 0.0);
+  std::vector<int> pos(np);
+  for (int a = 0; a < nI; ++a) pos[I[a]] = a;
+  for (int g = 0; g < nG; ++g) pos[G[g]] = g;
   std::vector<double> ht(nG);
   for (int e = 0; e < np; ++e) {
     if (isB[e]) {
-      const int a = (int)(std::find(I.begin(), I.end(), e) - I.begin());
+      const int a = pos[e];
       for (int c = 0; c < nG; ++c) ht[c] = -X[(size_t)a * nG + c];
     } else {
-      const int g = (int)(std::find(G.begin(), G.end(), e) - G.begin());
+      const int g = pos[e];
       for (int c = 0; c < nG; ++c) ht[c] = (c == g) ? 1.0 : 0.0;
     }
     forward_solve(R, nG, ht.data());
@@ -239,51 +246,71 @@ static void patch_operator(const Box& pb, double h, double alpha, double beta, c
   // The dense operator used by the CUDA-core kernels is D = W W^t as well:
   // forming A_p^{-1} - Bblk instead would cancel the large bubble entries and
   // lose ~cond(A_p) digits.  Self-check with a residual that stays well
-  // scaled: A_p (D + Bblk) = I (Sec. 3.2: the patch space is the direct sum of
-  // the 8 interior spaces and the a-orthogonal vertex space).
-  (*D).assign((size_t)np * np, 0.0);
-  for (int a = 0; a < np; ++a)
-    for (int b = 0; b < np; ++b) {
-      double sdot = 0.0;
-      for (int c = 0; c < nG; ++c) sdot += (*W)[(size_t)a * nG + c] * (*W)[(size_t)b * nG + c];
-      (*D)[(size_t)a * np + b] = sdot;
-    }
+  // scaled: A_p (W W^t + Bblk) = I (Sec. 3.2: the patch space is the direct
+  // sum of the subdomain interior spaces and the a-orthogonal vertex space),
+  // on every column for small patches and on a spread of columns for large ones.
+  if (D) {
+    (*D).assign((size_t)np * np, 0.0);
+    for (int a = 0; a < np; ++a)
+      for (int b = 0; b < np; ++b) {
+        double sdot = 0.0;
+        for (int c = 0; c < nG; ++c) sdot += (*W)[(size_t)a * nG + c] * (*W)[(size_t)b * nG + c];
+        (*D)[(size_t)a * np + b] = sdot;
+      }
+  }
+  const int step = np <= 200 ? 1 : 37;
+  std::vector<double> pcol(np), tmp(nG);
   double err = 0.0;
-  for (int a = 0; a < np; ++a)
-    for (int b = 0; b < np; ++b) {
+  for (int b = 0; b < np; b += step) {
+    // pcol = (W W^t + Bblk) e_b
+    for (int c = 0; c < nG; ++c) tmp[c] = (*W)[(size_t)b * nG + c];
+    for (int a = 0; a < np; ++a) {
+      double sdot = Bblk[(size_t)a * np + b];
+      for (int c = 0; c < nG; ++c) sdot += (*W)[(size_t)a * nG + c] * tmp[c];
+      pcol[a] = sdot;
+    }
+    for (int a = 0; a < np; ++a) {
       double sdot = 0.0;
-      for (int c = 0; c < np; ++c)
-        sdot += Ap[(size_t)a * np + c] * ((*D)[(size_t)c * np + b] + Bblk[(size_t)c * np + b]);
+      for (int c = 0; c < np; ++c) sdot += Ap[(size_t)a * np + c] * pcol[c];
       err = std::fmax(err, std::fabs(sdot - (a == b ? 1.0 : 0.0)));
     }
+  }
   // rounding grows like cond(A_p)^2 eps here (cond ~ alpha / (beta h^2));
   // an indexing mistake gives O(1), so 1e-3 separates the two up to n ~ 1000
   if (!(err <= 1e-3)) throw std::runtime_error("Gram factor does not reproduce the patch operator");
 }
 
 
-void build_local_ops(int n, double L, double alpha, double beta, LocalOps* out) {
+void build_local_ops(int n, double L, double alpha, double beta, LocalOps* out, int s) {
   const double h = L / n;
   out->n = n;
   out->h = h;
+  out->s = s;
   bool ok = false;
-  // interior space N_h^T of one coarse element (2x2x2 cells, 6 edges)
-  const Box bub{{2, 2, 2}};
+  // interior space N_h^T of one subdomain (s x s x s cells; s = 2: a coarse
+  // element with 6 interior edges)
+  const Box bub{{s, s, s}};
+  out->mT = (int)bub.size();
   std::vector<double> AT = box_matrix(bub, h, alpha, beta);
-  out->AinvT = spd_inverse(AT, 6, &ok);
+  out->AinvT = spd_inverse(AT, out->mT, &ok);
   if (!ok) throw std::runtime_error("interior-space matrix is not SPD");
-  // vertex patch: 4x4x4 cells around a coarse vertex, 108 interior edges,
-  // 60 of them on the interface (eq. vertex space)
+  // vertex patch: the 2s x 2s x 2s cells around a subdomain vertex; 108
+  // interior edges and 60 on the interface for s = 2 (eq. vertex space),
+  // 1176 and 312 for s = 4
+  const Box vb{{2 * s, 2 * s, 2 * s}};
+  out->mV = (int)vb.size();
   int nG = 0;
-  patch_operator(Box{{4, 4, 4}}, h, alpha, beta, out->AinvT, &out->Dv, &out->Wv, &nG);
-  if (nG != 60) throw std::runtime_error("unexpected vertex-patch split");
+  patch_operator(vb, s, h, alpha, beta, out->AinvT, s == 2 ? &out->Dv : nullptr, &out->Wv, &nG);
+  out->nG = nG;
+  if (nG != out->mV - 8 * out->mT) throw std::runtime_error("unexpected vertex-patch split");
+  if (s != 2) return;
   // edge patches: 2 cells along the coarse edge, 4 x 4 across, 42 interior
   // edges, 18 on the interface (eq. edge space); one operator per direction
   for (int d = 0; d < 3; ++d) {
     Box eb{{4, 4, 4}};
     eb.b[d] = 2;
     std::vector<double> We;
-    patch_operator(eb, h, alpha, beta, out->AinvT, &out->De[d], &We, &nG);
+    patch_operator(eb, 2, h, alpha, beta, out->AinvT, &out->De[d], &We, &nG);
     if (nG != 18) throw std::runtime_error("unexpected edge-patch split");
   }
 }

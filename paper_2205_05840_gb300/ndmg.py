@@ -37,7 +37,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("n_coarsest", ctypes.c_int32), ("L", ctypes.c_double),
                 ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("smoother", ctypes.c_int32),
                 ("eta", ctypes.c_double), ("m", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("nrhs", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("nrhs", ctypes.c_int32), ("stream", ctypes.c_void_p), ("subdomain", ctypes.c_int32)]
 
 
 _vp, _i32, _i64, _d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
@@ -104,11 +104,12 @@ class Solver:
 
     def __init__(self, n: int, n_coarsest: int = 2, L: float = 1.0, alpha: float = 1.0, beta: float = 1.0,
                  smoother: int = SMOOTHER_VERTEX, eta: float = 0.0, m: int = 2, precision: int = PREC_FP64,
-                 nrhs: int = 1, stream: torch.cuda.Stream | None = None):
+                 nrhs: int = 1, stream: torch.cuda.Stream | None = None, subdomain: int = 2):
         o = Opts()
         _lib.ndmg_opts_default(ctypes.byref(o))
         o.n, o.n_coarsest, o.L, o.alpha, o.beta = n, n_coarsest, L, alpha, beta
         o.smoother, o.eta, o.m, o.precision, o.nrhs = smoother, eta, m, precision, nrhs
+        o.subdomain = subdomain
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         o.stream = self.stream.cuda_stream
         self._h = _vp()
