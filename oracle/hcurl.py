@@ -210,6 +210,27 @@ def assemble_parts(n: int, L: float = 1.0):
     return K, M
 
 
+def assemble_field(n: int, L: float, alpha_cells: np.ndarray, beta: float = 1.0):
+    """A_h for a curl-curl coefficient that is constant on every hexahedron
+    (eq. 1 with alpha piecewise constant; the concluding remarks' jumping
+    coefficients): sum_T (alpha_T K_T + beta M_T).  alpha_cells: n^3 values,
+    hexahedra ordered x fastest (as the elements of _element_dofs)."""
+    h = L / n
+    a = np.asarray(alpha_cells, dtype=float).ravel()
+    if a.size != n ** 3:
+        raise ValueError("alpha_cells needs n^3 values")
+    KT, MT = element_matrices(h)
+    dofs = _element_dofs(n)
+    N = num_edges(n)
+    r = np.repeat(dofs, 12, axis=1).ravel()
+    c = np.tile(dofs, (1, 12)).ravel()
+    keep = (r >= 0) & (c >= 0)
+    vals = (a[:, None] * KT.ravel()[None, :] + beta * MT.ravel()[None, :]).ravel()
+    A = sp.csr_matrix((vals[keep], (r[keep], c[keep])), shape=(N, N))
+    A.sum_duplicates()
+    return A
+
+
 def apply_rows(n: int, L: float, alpha: float, beta: float, u: np.ndarray, rows) -> np.ndarray:
     """(A_h u)[rows] by summing the element contributions of the (up to 4)
     hexahedra around each requested edge; usable at any n because it never

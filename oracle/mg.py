@@ -200,6 +200,28 @@ def edge_patches(n: int):
 # --------------------------------------------------------------------------
 
 
+def coarsen_field(alpha_cells: np.ndarray, n: int) -> np.ndarray:
+    """Curl-curl coefficient of the (n/2)^3 coarse hexahedra: the mean of the
+    8 fine ones each contains (reading for coefficients that vary per
+    hexahedron; the paper's analysis assumes a constant one)."""
+    a = np.asarray(alpha_cells, dtype=float).reshape(n, n, n)      # [k, j, i]
+    return a.reshape(n // 2, 2, n // 2, 2, n // 2, 2).mean(axis=(1, 3, 5)).ravel()
+
+
+def _block_groups(A, idx):
+    """Group the subdomains / patches of idx by their local matrix (equal up
+    to rounding): returns a list of (patch numbers, local matrix)."""
+    groups = {}
+    for p in range(idx.shape[0]):
+        Ap = A[idx[p]][:, idx[p]].toarray()
+        key = np.round(Ap / abs(Ap).max(), 11).tobytes() + np.float64(abs(Ap).max()).round(11).tobytes()
+        if key in groups:
+            groups[key][0].append(p)
+        else:
+            groups[key] = ([p], Ap)
+    return [(np.array(ps), Ap) for ps, Ap in groups.values()]
+
+
 def _identical_blocks(A, idx, sample=64, seed=0):
     """Extract A[idx_p, idx_p] for a sample of patches, check they are all
     equal (constant alpha on a uniform grid), return the first one."""
@@ -246,7 +268,11 @@ class Smoother:
     """M_{V,h}^{-1} (eq. Preconditioner P) or M_{E,h}^{-1} (eq.
     Preconditioner E) on one level."""
 
-    def __init__(self, A: sp.csr_matrix, n: int, kind: str = "vertex", eta: float | None = None, s: int = 2):
+    def __init__(self, A: sp.csr_matrix, n: int, kind: str = "vertex", eta: float | None = None, s: int = 2,
+                 varying: bool = False):
+        """varying: the local matrices differ between subdomains (a
+        coefficient that varies per hexahedron); they are then grouped by
+        equality and factored once per group."""
         self.kind = kind
         self.eta = eta if eta is not None else (1.0 / 9.0 if kind == "vertex" else 1.0 / 13.0)
         self.N = A.shape[0]
@@ -255,18 +281,28 @@ class Smoother:
         if s != 2 and kind != "vertex":
             raise ValueError("subdomain size s != 2 is built for the vertex-based smoother")
         self.bub = bubble_sets(n, s)
-        AT = _identical_blocks(A, self.bub)
-        self.cT = sla.cho_factor(AT)
+        self.varying = varying
+        if varying:
+            self.bub_groups = [(ps, sla.cho_factor(AT)) for ps, AT in _block_groups(A, self.bub)]
+        else:
+            AT = _identical_blocks(A, self.bub)
+            self.cT = sla.cho_factor(AT)
         self.patches = []
         if kind == "vertex":
             idx, nI = vertex_patches(n, s)
-            if idx.shape[0]:
+            if idx.shape[0] and varying:
+                for ps, Ap in _block_groups(A, idx):
+                    self.patches.append((idx[ps], SchurPatch(Ap, nI)))
+            elif idx.shape[0]:
                 Ap = _identical_blocks(A, idx)
                 self.patches.append((idx, SchurPatch(Ap, nI)))
         elif kind == "edge":
             lists, nI = edge_patches(n)
             for idx in lists:
-                if idx.shape[0]:
+                if idx.shape[0] and varying:
+                    for ps, Ap in _block_groups(A, idx):
+                        self.patches.append((idx[ps], SchurPatch(Ap, nI)))
+                elif idx.shape[0]:
                     Ap = _identical_blocks(A, idx)
                     self.patches.append((idx, SchurPatch(Ap, nI)))
         else:
@@ -276,8 +312,13 @@ class Smoother:
         """M^{-1} r: every local solve reads the same r; results are summed."""
         out = np.zeros_like(r)
         # sum_T J_T A_T^{-1} J_T^t r ; bubble sets are disjoint
-        yT = sla.cho_solve(self.cT, r[self.bub].T)          # (edges per block, nT)
-        out[self.bub.T.ravel()] += yT.ravel()
+        if self.varying:
+            for ps, cT in self.bub_groups:
+                b = self.bub[ps]
+                out[b.T.ravel()] += sla.cho_solve(cT, r[b].T).ravel()
+        else:
+            yT = sla.cho_solve(self.cT, r[self.bub].T)      # (edges per block, nT)
+            out[self.bub.T.ravel()] += yT.ravel()
         # sum_V J_V A_V^{-1} J_V^t r (or the edge spaces)
         for idx, sp_ in self.patches:
             y = sp_.apply(r[idx].T)                          # (m, P)
@@ -304,9 +345,19 @@ class Hierarchy:
             raise ValueError(f"n={n} does not coarsen to n0={n0}")
         self.ns = ns[::-1]
         self.L, self.alpha, self.beta, self.m = L, alpha, beta, m
-        self.A = [assemble_cached(nk, L, alpha, beta) for nk in self.ns]
+        field = np.ndim(alpha) > 0
+        if field:
+            # a coefficient per finest hexahedron, averaged onto coarser grids
+            fields = [np.asarray(alpha, dtype=float).ravel()]
+            for nk in ns[:-1]:
+                fields.append(coarsen_field(fields[-1], nk))
+            self.fields = fields[::-1]
+            self.A = [hcurl.assemble_field(nk, L, a, beta) for nk, a in zip(self.ns, self.fields)]
+        else:
+            self.A = [assemble_cached(nk, L, alpha, beta) for nk in self.ns]
         self.P = [None] + [prolongation(self.ns[k - 1], L) for k in range(1, len(self.ns))]
-        self.S = [None] + [Smoother(self.A[k], self.ns[k], kind, eta, s) for k in range(1, len(self.ns))]
+        self.S = [None] + [Smoother(self.A[k], self.ns[k], kind, eta, s, varying=field)
+                           for k in range(1, len(self.ns))]
         self.c0 = sla.cho_factor(self.A[0].toarray())
 
     @property

@@ -1,0 +1,92 @@
+"""Pins of the oracle for a curl-curl coefficient that is constant per
+hexahedron (jumping coefficients, concluding remarks): facts that hold
+whatever the field and do not restate the assembly."""
+import numpy as np
+import pytest
+
+from oracle import hcurl, mg
+
+
+def checker(n, block, lo=1.0, hi=100.0):
+    k, j, i = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    return np.where(((i // block) + (j // block) + (k // block)) % 2 == 0, lo, hi).ravel()
+
+
+def test_constant_field_is_the_scalar_operator():
+    n = 6
+    A = hcurl.assemble_field(n, 1.0, np.full(n ** 3, 2.5), 0.7)
+    assert abs(A - hcurl.assemble(n, 1.0, 2.5, 0.7)).max() < 1e-14 * abs(A).max()
+    H1 = mg.Hierarchy(8, 1.0, 0.7, 1.0, n0=2, m=1)
+    H2 = mg.Hierarchy(8, 1.0, np.full(8 ** 3, 0.7), 1.0, n0=2, m=1)
+    f = np.random.default_rng(0).standard_normal(H1.A[-1].shape[0])
+    z1, z2 = H1.vcycle(f, np.zeros_like(f)), H2.vcycle(f, np.zeros_like(f))
+    assert np.abs(z1 - z2).max() < 1e-12 * np.abs(z1).max()
+
+
+def test_field_operator_de_rham_and_spd():
+    # curl grad = 0 cell by cell, so K_alpha G = 0 for any field; A is SPD
+    n = 6
+    a = np.random.default_rng(1).uniform(0.01, 100.0, n ** 3)
+    A = hcurl.assemble_field(n, 1.0, a, 1.0)
+    K = hcurl.assemble_field(n, 1.0, a, 0.0)
+    G = hcurl.nodal_gradient(n, 1.0)
+    assert abs(K @ G).max() < 1e-12 * abs(K).max()
+    Ad = A.toarray()
+    assert np.allclose(Ad, Ad.T) and np.linalg.eigvalsh(Ad).min() > 0
+
+
+def test_field_is_local():
+    # changing alpha on one hexahedron changes only the rows / columns of its
+    # 12 edges (interior ones), by (delta alpha) K_T
+    n = 5
+    a = np.random.default_rng(2).uniform(0.5, 2.0, n ** 3)
+    A0 = hcurl.assemble_field(n, 1.0, a, 1.0)
+    b = a.copy()
+    cell = (2 * n + 3) * n + 1                 # (i, j, k) = (1, 3, 2)
+    b[cell] += 7.0
+    D = (hcurl.assemble_field(n, 1.0, b, 1.0) - A0).toarray()
+    KT, _ = hcurl.element_matrices(1.0 / n)
+    dofs = hcurl._element_dofs(n)[cell]
+    ref = np.zeros_like(D)
+    for x in range(12):
+        for y in range(12):
+            if dofs[x] >= 0 and dofs[y] >= 0:
+                ref[dofs[x], dofs[y]] += 7.0 * KT[x, y]
+    assert np.abs(D - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_coarsened_field_is_the_cell_mean():
+    a = np.arange(4 ** 3, dtype=float)
+    c = mg.coarsen_field(a, 4)
+    assert c.shape == (8,) and c[0] == np.mean([0, 1, 4, 5, 16, 17, 20, 21])
+
+
+@pytest.mark.parametrize("m", [1, 2])
+def test_interior_gradient_eigenmode_with_jumps(m):
+    # curl grad psi = 0, so a(grad psi, v) = beta (grad psi, v) whatever alpha:
+    # the interior-gradient mode keeps its exact factor (1 - eta)^(2m)
+    n, eta = 8, 1 / 9
+    H = mg.Hierarchy(n, 1.0, checker(n, 2), 1.0, n0=2, m=m)
+    z0 = np.zeros(hcurl.num_edges(n))
+    c = (3, 1, 5)
+    for d in range(3):
+        lo = list(c)
+        lo[d] -= 1
+        z0[hcurl.edge_index(n, d, *lo)] = 1.0
+        z0[hcurl.edge_index(n, d, *c)] = -1.0
+    z1 = H.vcycle(np.zeros_like(z0), z0)
+    # exact up to rounding, which the local solves amplify by their condition
+    # number (~ alpha / h^2 = 6400 here)
+    assert np.allclose(z1, (1 - eta) ** (2 * m) * z0, rtol=0, atol=1e-10)
+
+
+def test_jumping_field_error_operator_spsd_and_contractive():
+    # the V-cycle error operator stays a-self-adjoint PSD with norm < 1 for a
+    # coefficient jumping by 10^4 between 2x2x2 blocks
+    H = mg.Hierarchy(8, 1.0, checker(8, 2, 0.01, 100.0), 1.0, n0=2, m=1)
+    A = H.A[-1].toarray()
+    E = mg.error_operator(H)
+    AE = A @ E
+    assert np.allclose(AE, AE.T, atol=1e-9 * abs(AE).max())
+    rho = mg.contraction_dense(H)
+    assert (8 / 9) ** 2 - 1e-9 <= rho < 0.95
