@@ -118,6 +118,38 @@ const char* ndmg_last_error(const ndmg_t* h);
 /* Rebuild the local operators for a new alpha (eq. 1), keeping all buffers. */
 int ndmg_set_alpha(ndmg_t* h, double alpha);
 
+/* Curl-curl coefficient constant on every hexahedron (eq. 1 with a
+ * piecewise-constant alpha; the jumping coefficients named in the concluding
+ * remarks).  alpha_cells: HOST pointer to n^3 doubles for the finest level,
+ * cell (i, j, k) (the hexahedron [i,i+1]x[j,j+1]x[k,k+1] h) at (k n + j) n + i,
+ * each finite and > 0; copied, not kept.  Coarser levels take the mean of the 8
+ * fine coefficients in each coarse hexahedron (rediscretisation).  The
+ * smoother keeps the paper's spaces (Sec. 3.2) with the local matrices of the
+ * actual coefficients: subdomains and patches whose cells carry bitwise equal
+ * coefficients share one factorisation, so the number of distinct local
+ * problems per family and level is limited to 8192 (piecewise-constant
+ * materials stay far below; a field that differs in every cell does not).
+ * With a field set, K in ndmg_pencil and ndmg_grad_alpha is the
+ * coefficient-weighted curl-curl matrix sum_T alpha_T K_T (so A = K + beta M,
+ * and ndmg_grad_alpha gives the derivative for alpha scaled by a common
+ * factor, at factor 1); ndmg_set_alpha returns to a constant coefficient.
+ * Subdomain size 2 only.  Synchronises the handle's stream; host set-up time
+ * grows with the number of distinct local problems (one 108-edge Schur
+ * complement each).  Errors: INVALID_ARG (NULL, non-positive or non-finite
+ * values, subdomain size 4, too many distinct local problems; the handle keeps
+ * its previous coefficients), OUT_OF_MEMORY, CUDA_ERROR. */
+int ndmg_set_alpha_field(ndmg_t* h, const double* alpha_cells);
+
+/* Per-hexahedron derivative of a loss L(u(f, alpha)) with respect to the
+ * coefficient of each finest-level cell, given the adjoint lambda (A lambda =
+ * dL/du): out[r n^3 + cell] = -lambda_r^T K_T u_r, with K_T the alpha-free
+ * curl-curl element matrix of that cell (its derivative of a(., .) = sum_T
+ * alpha_T (curl ., curl .)_T + beta (., .)).  Valid with or without a field.
+ * lambda, u: double device vectors of the finest level [x nrhs]; out: double
+ * device array of n^3 x nrhs, caller-owned; all 16-byte aligned.
+ * Asynchronous on the handle's stream.  Errors: INVALID_ARG, CUDA_ERROR. */
+int ndmg_grad_alpha_field(ndmg_t* h, const double* lambda, const double* u, double* out);
+
 /* Number of levels K+1. */
 int ndmg_num_levels(const ndmg_t* h, int32_t* out);
 

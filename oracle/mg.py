@@ -36,6 +36,7 @@ from __future__ import annotations
 import numpy as np
 import scipy.linalg as sla
 import scipy.sparse as sp
+import scipy.sparse.linalg as spla
 
 from . import hcurl
 
@@ -542,3 +543,27 @@ def loss_and_grad(H: Hierarchy, f, u_t, tol=1e-12):
     lam, *_ = pcg(H, res, tol=tol, maxit=500)
     K, _ = _ASM_CACHE[(H.ns[-1], H.L)]
     return 0.5 * float(res @ res), lam, -float(lam @ (K @ u)), u
+
+
+def grad_cells(n: int, L: float, lam, u):
+    """-lambda_T^t K_T u_T for every hexahedron T (x fastest): the derivative
+    of a(u, lambda) = sum_T alpha_T (curl u, curl lambda)_T + beta (u, lambda)
+    in the coefficient of T, from the element matrix of T and the element's
+    edge values (zero on boundary edges)."""
+    KT, _ = hcurl.element_matrices(L / n)
+    dofs = hcurl._element_dofs(n)
+    ln = np.where(dofs >= 0, np.asarray(lam)[np.maximum(dofs, 0)], 0.0)
+    un = np.where(dofs >= 0, np.asarray(u)[np.maximum(dofs, 0)], 0.0)
+    return -np.einsum("ca,ab,cb->c", ln, KT, un)
+
+
+def loss_and_grad_field(n: int, L: float, alpha_cells, beta, f, u_t):
+    """L = 0.5 ||u - u_t||^2 with A(alpha) u = f for a coefficient per
+    hexahedron, by sparse direct solves: returns (L, dL/dalpha per cell, u);
+    dL/dalpha_T = -lambda^T K_T u with A lambda = u - u_t (A symmetric)."""
+    A = hcurl.assemble_field(n, L, alpha_cells, beta).tocsc()
+    lu = spla.splu(A)
+    u = lu.solve(np.asarray(f, dtype=float))
+    res = u - u_t
+    lam = lu.solve(res)
+    return 0.5 * float(res @ res), grad_cells(n, L, lam, u), u

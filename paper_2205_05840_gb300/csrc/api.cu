@@ -6,6 +6,7 @@
 #include <cstring>
 #include <exception>
 #include <new>
+#include <type_traits>
 
 #include "kernels.cuh"
 #include "tc_patch.cuh"
@@ -97,6 +98,18 @@ cudaError_t upload(T** dst, const std::vector<double>& src) {
   return cudaMemcpy(*dst, tmp.data(), sizeof(T) * tmp.size(), cudaMemcpyHostToDevice);
 }
 
+// fresh device copy of a host array (any previous buffer freed first)
+template <typename D, typename S>
+cudaError_t upload_fresh(D** dst, const std::vector<S>& src) {
+  cudaFree(*dst);
+  *dst = nullptr;
+  std::vector<D> tmp(src.begin(), src.end());
+  if (tmp.empty()) tmp.resize(1);
+  cudaError_t e = cudaMalloc((void**)dst, sizeof(D) * tmp.size());
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, tmp.data(), sizeof(D) * tmp.size(), cudaMemcpyHostToDevice);
+}
+
 int64_t edges(int n) { return 3LL * n * (n - 1) * (n - 1); }
 double bubble_bytes(int n, size_t w) {
   const double c = n / 2;
@@ -133,18 +146,33 @@ bool mixed(const ndmg_t* h) {
 // ---------------------------------------------------------------------------
 int nrhs(const ndmg_t* h) { return h->o.nrhs; }
 
+const double* lv_a(DevLevel& L, double*) { return L.a64; }
+const float* lv_a(DevLevel& L, float*) { return L.a32; }
+
+// y = g - (cK K + cM M) u (or (cK K + cM M) u when g is null) on level k: the
+// constant-coefficient stencil, or with a coefficient per hexahedron the
+// field stencil (cK = h times the factor; the coefficients are in K)
+template <typename T>
+void stencil(ndmg_t* h, int k, double cK, double cM, const T* u, const T* g, T* y) {
+  DevLevel& L = h->lv[k];
+  if (h->field)
+    launch_stencil_field<T>(h->stream, h->sm_count, L.n, cK, cM, u, g, y, nrhs(h), lv_a(L, (T*)nullptr));
+  else
+    launch_stencil<T>(h->stream, h->sm_count, L.n, cK, cM, u, g, y, nrhs(h), h->umax);
+}
+
 template <typename T>
 void op_residual(ndmg_t* h, int k, const T* g, const T* z, T* r) {
   DevLevel& L = h->lv[k];
   Span sp(h, NDMG_K_STENCIL, 3.0 * sizeof(T) * L.N * nrhs(h));  // read g, z; write r
-  launch_stencil<T>(h->stream, h->sm_count, L.n, L.cK, L.cM, z, g, r, nrhs(h), h->umax);
+  stencil<T>(h, k, L.cK, L.cM, z, g, r);
 }
 
 template <typename T>
 void op_apply(ndmg_t* h, int k, const T* x, T* y) {
   DevLevel& L = h->lv[k];
   Span sp(h, NDMG_K_STENCIL, 2.0 * sizeof(T) * L.N * nrhs(h));  // read x; write y
-  launch_stencil<T>(h->stream, h->sm_count, L.n, L.cK, L.cM, x, (const T*)nullptr, y, nrhs(h), h->umax);
+  stencil<T>(h, k, L.cK, L.cM, x, (const T*)nullptr, y);
 }
 
 // y = g + (a K + b M) x (or (a K + b M) x when g is null): the stencil in
@@ -154,8 +182,8 @@ void op_pencil(ndmg_t* h, int k, double a, double b, const T* g, const T* x, T* 
   DevLevel& L = h->lv[k];
   const double hk = L.h, h3 = hk * hk * hk;
   Span sp(h, NDMG_K_STENCIL, (g ? 3.0 : 2.0) * sizeof(T) * L.N * nrhs(h));
-  if (g) launch_stencil<T>(h->stream, h->sm_count, L.n, -a * hk, -b * h3, x, g, y, nrhs(h), h->umax);
-  else launch_stencil<T>(h->stream, h->sm_count, L.n, a * hk, b * h3, x, (const T*)nullptr, y, nrhs(h), h->umax);
+  if (g) stencil<T>(h, k, -a * hk, -b * h3, x, g, y);
+  else stencil<T>(h, k, a * hk, b * h3, x, (const T*)nullptr, y);
 }
 
 bool edge_smoother(const ndmg_t* h) { return h->o.smoother == NDMG_SMOOTHER_EDGE; }
@@ -197,10 +225,53 @@ void op_smoother_s4(ndmg_t* h, int k, const T* r, T* z) {
                        h->o.eta, r, z, R);
 }
 
+// coefficient per hexahedron: interior solves and patch solves with one
+// operator per group of subdomains / patches (tensor cores for the vertex
+// patches in the MIXED modes)
+const double* lv_bubA(DevLevel& L, double*) { return L.bubA64; }
+const float* lv_bubA(DevLevel& L, float*) { return L.bubA32; }
+const double* grp_op(DevGrouped& G, double*) { return G.op64; }
+const float* grp_op(DevGrouped& G, float*) { return G.op32; }
+
+template <typename T>
+void op_smoother_field(ndmg_t* h, int k, const T* r, T* z) {
+  DevLevel& L = h->lv[k];
+  const int R = nrhs(h);
+  if constexpr (std::is_same<T, float>::value) {
+    if (mixed(h) && !edge_smoother(h) && L.Wtc_tab) {
+      Span sp(h, NDMG_K_PATCH, 12.0 * L.N * R);
+      launch_tc_smoother_field(h->stream, L.n, L.Wtc_tab, h->o.precision == NDMG_PREC_MIXED_FP16, L.bubA32,
+                               L.bub_gid, L.tc_off, L.tc_grp, L.tc_mask, h->o.eta, r, z, h->status, R);
+      return;
+    }
+  }
+  {
+    Span sp(h, NDMG_K_BUBBLE, bubble_bytes(L.n, sizeof(T)) * R);
+    launch_bubble_grouped<T>(h->stream, h->sm_count, L.n, lv_bubA(L, (T*)nullptr), L.bub_gid, h->o.eta, r, z, R);
+  }
+  if (edge_smoother(h)) {
+    for (int d = 0; d < 3; ++d) {
+      const PatchFamily fam = edge_family(L.n, d);
+      Span sp(h, NDMG_K_PATCH, (double)fam.np[0] * fam.np[1] * fam.np[2] * 2.0 * 42 * 42 * R);
+      launch_patch_grouped<T>(h->stream, h->sm_count, L.n, fam, grp_op(L.edg[d], (T*)nullptr), L.edg[d].chunks,
+                              L.edg[d].nchunks, L.edg[d].plist, h->o.eta, r, z, R);
+    }
+    return;
+  }
+  const PatchFamily fam = vertex_family(L.n);
+  Span sp(h, NDMG_K_PATCH, num_patches(L.n) * 2.0 * 108 * 108 * R);
+  launch_patch_grouped<T>(h->stream, h->sm_count, L.n, fam, grp_op(L.vtx, (T*)nullptr), L.vtx.chunks, L.vtx.nchunks,
+                          L.vtx.plist, h->o.eta, r, z, R);
+}
+
 template <typename T>
 void op_smoother(ndmg_t* h, int k, const T* r, T* z) {
   DevLevel& L = h->lv[k];
   const int R = nrhs(h);
+  if (h->field) {
+    op_smoother_field<T>(h, k, r, z);
+    return;
+  }
   if (h->o.subdomain == 4) {
     op_smoother_s4<T>(h, k, r, z);
     return;
@@ -221,6 +292,10 @@ template <>
 void op_smoother<float>(ndmg_t* h, int k, const float* r, float* z) {
   DevLevel& L = h->lv[k];
   const int R = nrhs(h);
+  if (h->field) {
+    op_smoother_field<float>(h, k, r, z);
+    return;
+  }
   if (h->o.subdomain == 4) {
     op_smoother_s4<float>(h, k, r, z);
     return;
@@ -774,8 +849,24 @@ int solve_ir(ndmg_t* h, const double* f, double* u, double tol, double inner_tol
   return fail(h, NDMG_NOT_CONVERGED, "refinement stalled");
 }
 
+void free_field(ndmg_t* h) {
+  for (auto& L : h->lv) {
+    cudaFree(L.a64); cudaFree(L.a32); cudaFree(L.bub_gid); cudaFree(L.bubA64); cudaFree(L.bubA32);
+    L.a64 = nullptr; L.a32 = nullptr; L.bub_gid = nullptr; L.bubA64 = nullptr; L.bubA32 = nullptr;
+    DevGrouped* gs[4] = {&L.vtx, &L.edg[0], &L.edg[1], &L.edg[2]};
+    for (DevGrouped* G : gs) {
+      cudaFree(G->chunks); cudaFree(G->plist); cudaFree(G->op64); cudaFree(G->op32);
+      *G = DevGrouped();
+    }
+    cudaFree(L.Wtc_tab); cudaFree(L.tc_off); cudaFree(L.tc_grp); cudaFree(L.tc_mask);
+    L.Wtc_tab = nullptr; L.tc_off = nullptr; L.tc_grp = nullptr; L.tc_mask = nullptr;
+  }
+  h->field = false;
+}
+
 void free_handle(ndmg_t* h) {
   if (!h) return;
+  free_field(h);
   drop_graph(h);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (auto& L : h->lv) {
@@ -804,44 +895,155 @@ void free_handle(ndmg_t* h) {
   delete h;
 }
 
+// why a mixed handle refuses a level: the rounded Gram factor no longer
+// represents the vertex-patch operator (the smoother would diverge)
+std::string lowp_message(int n, double lam, bool fp16) {
+  char buf[320];
+  std::snprintf(buf, sizeof(buf),
+                "%s tensor-core operands cannot represent the vertex-patch operator of the %d^3 level "
+                "(largest eigenvalue of A_p W~W~^t = %.3g > %.0g; the patch matrix is too ill-conditioned, "
+                "alpha / (beta h^2) too large)%s",
+                fp16 ? "fp16" : "bf16", n, lam, kTcSpectralMax,
+                fp16 ? "; use NDMG_PREC_FP32" : "; use NDMG_PREC_MIXED_FP16 or NDMG_PREC_FP32");
+  return buf;
+}
+
 int build_operators(ndmg_t* h) {
   const ndmg_opts& o = h->o;
+  const bool fp16 = o.precision == NDMG_PREC_MIXED_FP16;
+  // host work for every level first: a rejected coefficient leaves the
+  // device operators untouched
+  std::vector<LocalOps> all(h->K + 1);
+  std::vector<double> inv;
   try {
-    for (int k = 1; k <= h->K; ++k) {
+    for (int k = h->K; k >= 1; --k) {
       DevLevel& L = h->lv[k];
-      LocalOps ops;
-      build_local_ops(L.n, o.L, o.alpha, o.beta, &ops, o.subdomain);
-      NDMG_CK(upload(&L.AinvT64, ops.AinvT));
-      NDMG_CK(upload(&L.AinvT32, ops.AinvT));
-      if (o.subdomain == 4) {
-        // Gram factor (1176 x 312) and its transpose for k_patch_gram
-        std::vector<double> WT(ops.Wv.size());
-        for (int e = 0; e < ops.mV; ++e)
-          for (int c = 0; c < ops.nG; ++c) WT[(size_t)c * ops.mV + e] = ops.Wv[(size_t)e * ops.nG + c];
-        NDMG_CK(upload(&L.Wg64, ops.Wv));
-        NDMG_CK(upload(&L.WgT64, WT));
-        NDMG_CK(upload(&L.Wg32, ops.Wv));
-        NDMG_CK(upload(&L.WgT32, WT));
-        continue;
-      }
-      NDMG_CK(upload(&L.Dv64, ops.Dv));
-      NDMG_CK(upload(&L.Dv32, ops.Dv));
-      std::vector<double> de;
-      for (int d = 0; d < 3; ++d) de.insert(de.end(), ops.De[d].begin(), ops.De[d].end());
-      NDMG_CK(upload(&L.De64, de));
-      NDMG_CK(upload(&L.De32, de));
-      if (mixed(h)) {
-        cudaError_t e = upload_tc_operand(&L.Wtc, ops.Wv, o.precision == NDMG_PREC_MIXED_FP16);
-        if (e != cudaSuccess) return cuda_fail(h, e, "upload_tc_operand");
+      build_local_ops(L.n, o.L, o.alpha, o.beta, &all[k], o.subdomain);
+      if (mixed(h) && o.subdomain == 2) {
+        const double lam =
+            tc_operand_spectral_max(all[k].Wv.data(), box_matrix(Box{{4, 4, 4}}, L.h, o.alpha, o.beta), fp16);
+        if (!(lam <= kTcSpectralMax)) return fail(h, NDMG_INVALID_ARG, lowp_message(L.n, lam, fp16));
       }
     }
-    std::vector<double> inv = coarse_inverse(h->lv[0].n, o.L, o.alpha, o.beta);
-    NDMG_CK(upload(&h->Ainv0, inv));
+    inv = coarse_inverse(h->lv[0].n, o.L, o.alpha, o.beta);
   } catch (const std::exception& ex) {
     return fail(h, NDMG_INVALID_ARG, ex.what());
   }
+  for (int k = 1; k <= h->K; ++k) {
+    DevLevel& L = h->lv[k];
+    const LocalOps& ops = all[k];
+    NDMG_CK(upload(&L.AinvT64, ops.AinvT));
+    NDMG_CK(upload(&L.AinvT32, ops.AinvT));
+    if (o.subdomain == 4) {
+      // Gram factor (1176 x 312) and its transpose for k_patch_gram
+      std::vector<double> WT(ops.Wv.size());
+      for (int e = 0; e < ops.mV; ++e)
+        for (int c = 0; c < ops.nG; ++c) WT[(size_t)c * ops.mV + e] = ops.Wv[(size_t)e * ops.nG + c];
+      NDMG_CK(upload(&L.Wg64, ops.Wv));
+      NDMG_CK(upload(&L.WgT64, WT));
+      NDMG_CK(upload(&L.Wg32, ops.Wv));
+      NDMG_CK(upload(&L.WgT32, WT));
+      continue;
+    }
+    NDMG_CK(upload(&L.Dv64, ops.Dv));
+    NDMG_CK(upload(&L.Dv32, ops.Dv));
+    std::vector<double> de;
+    for (int d = 0; d < 3; ++d) de.insert(de.end(), ops.De[d].begin(), ops.De[d].end());
+    NDMG_CK(upload(&L.De64, de));
+    NDMG_CK(upload(&L.De32, de));
+    if (mixed(h)) {
+      cudaError_t e = upload_tc_operand(&L.Wtc, ops.Wv, fp16);
+      if (e != cudaSuccess) return cuda_fail(h, e, "upload_tc_operand");
+    }
+  }
+  NDMG_CK(upload(&h->Ainv0, inv));
   for (auto& L : h->lv) {
     L.cK = o.alpha * L.h;
+    L.cM = o.beta * L.h * L.h * L.h;
+  }
+  return NDMG_OK;
+}
+
+// Most distinct local problems one family may have on one level (each one
+// is factored on the host).
+constexpr int kMaxFieldGroups = 8192;
+
+cudaError_t upload_grouped(DevGrouped* G, const GroupedFamily& g) {
+  std::vector<int> plist, chunks;
+  group_chunks(g, patch_group_size(), &plist, &chunks);
+  G->nchunks = (int)(chunks.size() / 4);
+  cudaError_t e = upload_fresh(&G->plist, plist);
+  if (e == cudaSuccess) e = upload_fresh((int**)&G->chunks, chunks);
+  if (e == cudaSuccess) e = upload_fresh(&G->op64, g.op);
+  if (e == cudaSuccess) e = upload_fresh(&G->op32, g.op);
+  return e;
+}
+
+// Coefficient per hexahedron (cells: n^3 finest-level values): the fields of
+// every level (mean coarsening), grouped local operators, tensor-core images
+// and brick lists, the coarsest inverse.  Host work first (it may reject the
+// field), device uploads after.
+int build_field_operators(ndmg_t* h, const double* cells) {
+  const ndmg_opts& o = h->o;
+  const int K = h->K;
+  const bool edge = edge_smoother(h);
+  std::vector<std::vector<double>> fld(K + 1);
+  const size_t nf = (size_t)o.n * o.n * o.n;
+  fld[K].assign(cells, cells + nf);
+  for (int k = K; k >= 1; --k) fld[k - 1] = coarsen_cells(fld[k], h->lv[k].n);
+  std::vector<FieldOps> ops(K + 1);
+  std::vector<double> inv0;
+  try {
+    // finest first: the level with the most distinct local problems rejects a field soonest
+    const int lowp = mixed(h) && !edge ? (o.precision == NDMG_PREC_MIXED_FP16 ? 2 : 1) : 0;
+    for (int k = K; k >= 1; --k) {
+      build_field_ops(h->lv[k].n, o.L, fld[k], o.beta, edge, kMaxFieldGroups, &ops[k], lowp);
+      if (lowp && !(ops[k].vtx.tc_spectral <= kTcSpectralMax))
+        return fail(h, NDMG_INVALID_ARG, lowp_message(h->lv[k].n, ops[k].vtx.tc_spectral, lowp == 2));
+    }
+    inv0 = coarse_inverse_cells(h->lv[0].n, o.L, fld[0], o.beta);
+  } catch (const std::exception& ex) {
+    return fail(h, NDMG_INVALID_ARG, ex.what());
+  }
+  free_field(h);
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k <= K && e == cudaSuccess; ++k) {
+    DevLevel& L = h->lv[k];
+    e = upload_fresh(&L.a64, fld[k]);
+    if (e == cudaSuccess) e = upload_fresh(&L.a32, fld[k]);
+    if (k == 0 || e != cudaSuccess) continue;
+    const FieldOps& F = ops[k];
+    e = upload_fresh(&L.bub_gid, F.bub.gid);
+    if (e == cudaSuccess) e = upload_fresh(&L.bubA64, F.bub.op);
+    if (e == cudaSuccess) e = upload_fresh(&L.bubA32, F.bub.op);
+    if (edge) {
+      for (int d = 0; d < 3 && e == cudaSuccess; ++d) e = upload_grouped(&L.edg[d], F.edge[d]);
+      continue;
+    }
+    if (e == cudaSuccess) e = upload_grouped(&L.vtx, F.vtx);
+    if (e == cudaSuccess && mixed(h)) {
+      std::vector<int> off, grp;
+      std::vector<uint32_t> mask;
+      tc_brick_groups(L.n, F.vtx.gid, &off, &grp, &mask);
+      e = upload_fresh((uint8_t**)&L.Wtc_tab,
+                       tc_images(F.vtx.W, F.vtx.ngroups, o.precision == NDMG_PREC_MIXED_FP16));
+      if (e == cudaSuccess) e = upload_fresh(&L.tc_off, off);
+      if (e == cudaSuccess) e = upload_fresh(&L.tc_grp, grp);
+      if (e == cudaSuccess) e = upload_fresh((uint32_t**)&L.tc_mask, mask);
+    }
+  }
+  if (e == cudaSuccess) {
+    cudaFree(h->Ainv0);
+    h->Ainv0 = nullptr;
+    e = upload(&h->Ainv0, inv0);
+  }
+  if (e != cudaSuccess) {
+    free_field(h);
+    return cuda_fail(h, e, "coefficient field upload");
+  }
+  h->field = true;
+  for (auto& L : h->lv) {
+    L.cK = L.h;  // the coefficients live in the field stencil
     L.cM = o.beta * L.h * L.h * L.h;
   }
   return NDMG_OK;
@@ -953,6 +1155,10 @@ int ndmg_create(const ndmg_opts* o, ndmg_t** out) {
   if (ae == cudaSuccess && h->o.subdomain == 4) ae = prepare_patch_gram<double>();
   if (ae == cudaSuccess && h->o.subdomain == 4) ae = prepare_patch_gram<float>();
   if (ae == cudaSuccess && mixed(h)) ae = prepare_tc_patch();
+  if (ae == cudaSuccess) ae = prepare_stencil_field<double>();
+  if (ae == cudaSuccess) ae = prepare_stencil_field<float>();
+  if (ae == cudaSuccess) ae = prepare_patch_grouped<double>();
+  if (ae == cudaSuccess) ae = prepare_patch_grouped<float>();
   if (ae != cudaSuccess) {
     free_handle(h);
     return ae == cudaErrorMemoryAllocation ? NDMG_OUT_OF_MEMORY : NDMG_CUDA_ERROR;
@@ -980,8 +1186,53 @@ int ndmg_set_alpha(ndmg_t* h, double alpha) {
   if (!(alpha > 0)) return fail(h, NDMG_INVALID_ARG, "alpha must be > 0");
   NDMG_CK(cudaStreamSynchronize(h->stream));
   drop_graph(h);  // the coefficients are captured in the graph's launches
+  const double old = h->o.alpha;
+  const bool had_field = h->field;
   h->o.alpha = alpha;
-  return build_operators(h);
+  h->field = false;             // build_operators rebuilds the constant-coefficient operators
+  const int st = build_operators(h);
+  if (st != NDMG_OK) {          // rejected on the host: the previous operators stay
+    h->o.alpha = old;
+    h->field = had_field;
+    return st;
+  }
+  free_field(h);
+  return NDMG_OK;
+}
+
+int ndmg_set_alpha_field(ndmg_t* h, const double* alpha_cells) {
+  if (!h) return NDMG_INVALID_ARG;
+  if (!alpha_cells) return fail(h, NDMG_INVALID_ARG, "null coefficient field");
+  if (h->o.subdomain != 2) return fail(h, NDMG_INVALID_ARG, "a coefficient field needs subdomain size 2");
+  const size_t nf = (size_t)h->o.n * h->o.n * h->o.n;
+  for (size_t c = 0; c < nf; ++c)
+    if (!(alpha_cells[c] > 0) || !std::isfinite(alpha_cells[c]))
+      return fail(h, NDMG_INVALID_ARG, "coefficients must be finite and > 0");
+  NDMG_CK(cudaStreamSynchronize(h->stream));
+  drop_graph(h);
+  const int st = build_field_operators(h, alpha_cells);
+  if (st != NDMG_OK && !h->field) {
+    // the handle keeps working with its constant coefficient
+    const std::string msg = h->err;
+    free_field(h);
+    build_operators(h);
+    h->err = msg;
+  }
+  return st;
+}
+
+int ndmg_grad_alpha_field(ndmg_t* h, const double* lambda, const double* u, double* out) {
+  if (!h) return NDMG_INVALID_ARG;
+  int st;
+  if ((st = check_ptrs(h, {lambda, u, out}))) return st;
+  const int K = h->K, R = nrhs(h);
+  DevLevel& L = h->lv[K];
+  {
+    Span sp(h, NDMG_K_STENCIL, (16.0 * L.N + 8.0 * L.n * L.n * L.n) * R);
+    launch_grad_cells(h->stream, h->sm_count, L.n, L.h, lambda, u, out, R);
+  }
+  NDMG_CK_LAUNCH();
+  return NDMG_OK;
 }
 
 int ndmg_num_levels(const ndmg_t* h, int32_t* out) {
@@ -1195,7 +1446,7 @@ int ndmg_grad_alpha(ndmg_t* h, const double* lambda, const double* u, double* ou
   double* Ku = h->w64[3];
   {
     Span sp(h, NDMG_K_STENCIL, 16.0 * L.N * R);
-    launch_stencil<double>(h->stream, h->sm_count, L.n, L.h, 0.0, u, (const double*)nullptr, Ku, R, h->umax);
+    stencil<double>(h, K, L.h, 0.0, u, (const double*)nullptr, Ku);
   }
   std::vector<double> v;
   if ((st = dot2<double>(h, L.N, lambda, Ku, (const double*)nullptr, (const double*)nullptr, v, nullptr)) != NDMG_OK)

@@ -140,19 +140,27 @@ __global__ void __launch_bounds__(256) k_absmax(int64_t N, const double* __restr
 }
 
 // T: vector type (float / double); S: arithmetic type of the stencil (T, or
-// long long for the fixed-point FP64 operator, which needs umax)
-template <typename T, typename S>
+// long long for the fixed-point FP64 operator, which needs umax).  FLD: the
+// curl-curl coefficient is constant per hexahedron (acell, n^3 values, cell
+// (i, j, k) at (k n + j) n + i; cK = h times the pencil's factor): the face
+// mass along the normal then weighs each of the two cells beside a face by its
+// own coefficient, alpha_lo (c_lo + 2 c) + alpha_hi (2 c + c_hi) over 6, which
+// is alpha (c_lo + 4 c + c_hi) / 6 for a constant one.
+template <typename T, typename S, bool FLD = false>
 __global__ void __launch_bounds__(kTX * kTY) k_stencil_stream(int n, int KZ, T cK, T cM, const T* __restrict__ u,
                                                               const T* __restrict__ g, T* __restrict__ y,
-                                                              const unsigned long long* __restrict__ umax) {
+                                                              const unsigned long long* __restrict__ umax,
+                                                              const T* __restrict__ acell = nullptr) {
   static_assert(sizeof(S) == sizeof(T), "staged planes hold T and are read as S");
   constexpr bool FX = !std::is_same<S, T>::value;
+  static_assert(!(FX && FLD), "the coefficient field runs in the vector type's own arithmetic");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   S* Ur = reinterpret_cast<S*>(smem_raw);  // [3 ring slots][x, y, z][kP]
   S* Cx = Ur + 9 * kP;                     // circulations of the current step
   S* Cy = Cx + kP;
   S* Cz = Cy + kP;
   T* Gr = reinterpret_cast<T*>(Cz + kP);   // [2 ring slots][x, y, z][kTP]
+  T* Ar = Gr + 6 * kTP;                    // FLD: [3 ring slots][kP] cell coefficients
   const uint32_t n1 = n - 1, N3 = (uint32_t)n * n1 * n1;  // offsets within one right-hand side fit in 32 bits
   // grid z = (z chunks) x (right-hand sides); each right-hand side is a
   // contiguous canonical vector
@@ -223,6 +231,23 @@ __global__ void __launch_bounds__(kTX * kTY) k_stencil_stream(int n, int KZ, T c
     cp_async_elem(Sg + kTP + tid, g + (vy ? py(k) + pg.oy : 0u), vy, g);
     cp_async_elem(Sg + 2 * kTP + tid, g + (vz ? pz(k) + pg.oz : 0u), vz, g);
   };
+  // FLD: the coefficients of the cells of plane c (the hexahedra between
+  // node planes c and c + 1) at the staged positions, cell plane p of the
+  // chunk (c = k0 - 1 + p) in ring slot p % 3; zero outside the box (those
+  // cells only meet faces whose circulation is zero)
+  auto stage_a = [&](int c, int slot) {
+    if constexpr (FLD) {
+      T* Sa = Ar + slot * kP;
+      const bool kc = (unsigned)c < (unsigned)n;
+      auto one = [&](int qq) {
+        const int ci = i0 + qq % kPX - 1, cj = j0 + qq / kPX - 1;
+        const bool v = kc && (unsigned)ci < (unsigned)n && (unsigned)cj < (unsigned)n;
+        cp_async_elem(Sa + qq, acell + (v ? ((uint32_t)c * n + (uint32_t)cj) * n + (uint32_t)ci : 0u), v, acell);
+      };
+      one(qa);
+      if (has_b) one(qb);
+    }
+  };
   // u plane p of the chunk is z = k0 - 1 + p, held in ring slot p % 3
   stage_u(k0 - 1, 0);
   asm volatile("cp.async.commit_group;" ::: "memory");
@@ -230,9 +255,24 @@ __global__ void __launch_bounds__(kTX * kTY) k_stencil_stream(int n, int KZ, T c
   const int a = threadIdx.x + 1, b = threadIdx.y + 1;
   const int q = b * kPX + a;
   auto f3 = [&](S m, S c0, S p1) { return (m + p1) + S(4) * c0; };
+  // coefficient planes of the current step (FLD): cells of planes k - 1, k
+  const T* Aprev = Ar;
+  const T* Acur = Ar;
   // face mass along x / y of the current plane at (a,b) and its neighbours
-  auto Xf = [&](int r) { return f3(Cx[r - 1], Cx[r], Cx[r + 1]); };
-  auto Yf = [&](int r) { return f3(Cy[r - kPX], Cy[r], Cy[r + kPX]); };
+  auto Xf = [&](int r) -> S {
+    if constexpr (FLD) return Acur[r - 1] * (Cx[r - 1] + S(2) * Cx[r]) + Acur[r] * (S(2) * Cx[r] + Cx[r + 1]);
+    else return f3(Cx[r - 1], Cx[r], Cx[r + 1]);
+  };
+  auto Yf = [&](int r) -> S {
+    if constexpr (FLD)
+      return Acur[r - kPX] * (Cy[r - kPX] + S(2) * Cy[r]) + Acur[r] * (S(2) * Cy[r] + Cy[r + kPX]);
+    else return f3(Cy[r - kPX], Cy[r], Cy[r + kPX]);
+  };
+  // face mass along z at the face plane k between the cells (r, k-1) and (r, k)
+  auto Zf = [&](int r, S m, S c0, S p1) -> S {
+    if constexpr (FLD) return Aprev[r] * (m + S(2) * c0) + Acur[r] * (S(2) * c0 + p1);
+    else return f3(m, c0, p1);
+  };
   // rolling state: Cz at (a,b), (a,b-1), (a-1,b) and the in-plane edge-mass
   // rows of x- and y-edges, for planes k-1 (0) and k (1); Xf, Yf of plane k-1
   S cz0[3] = {S(0), S(0), S(0)}, cz1[3] = {S(0), S(0), S(0)};
@@ -263,9 +303,14 @@ __global__ void __launch_bounds__(kTX * kTY) k_stencil_stream(int n, int KZ, T c
     __syncthreads();  // plane t+2 and g(t) landed; step t-1 is done with the ring
     if (t + 2 <= T_out) stage_u(k0 + t + 2, (t + 3) % 3);
     if (g && t + 1 >= 0 && t + 1 < T_out) stage_g(k0 + t + 1, (t + 1) & 1);
+    if (FLD && t + 2 <= T_out) stage_a(k0 + t + 1, (t + 2) % 3);  // cell plane p = t + 2
     asm volatile("cp.async.commit_group;" ::: "memory");
     const S* Uc = Ur + ((t + 4) % 3) * 3 * kP;  // plane k0 + t
     const S* Un = Ur + ((t + 2) % 3) * 3 * kP;  // plane k0 + t + 1
+    if constexpr (FLD) {
+      Aprev = Ar + ((t + 3) % 3) * kP;  // cell plane k0 + t - 1 (p = t)
+      Acur = Ar + ((t + 4) % 3) * kP;   // cell plane k0 + t (p = t + 1)
+    }
     auto circ = [&](int r, bool ha, bool hb) {
       if (t >= -1) {
         // cx(i,j,k) = uz(i,j+1,k) - uz(i,j,k) - uy(i,j,k+1) + uy(i,j,k)
@@ -288,9 +333,9 @@ __global__ void __launch_bounds__(kTX * kTY) k_stencil_stream(int n, int KZ, T c
         const int k = k0 + t;
         const bool kn = in_node(k, n), ks = in_seg(k, n);
         const T* G = Gr + (t & 1) * 3 * kTP;
-        const S zf = f3(cz0[0], cz1[0], cz2[0]);    // Zf(a, b, k)
-        const S zf_b = f3(cz0[1], cz1[1], cz2[1]);  // Zf(a, b-1, k)
-        const S zf_a = f3(cz0[2], cz1[2], cz2[2]);  // Zf(a-1, b, k)
+        const S zf = Zf(q, cz0[0], cz1[0], cz2[0]);          // Zf(a, b, k)
+        const S zf_b = Zf(q - kPX, cz0[1], cz1[1], cz2[1]);  // Zf(a, b-1, k)
+        const S zf_a = Zf(q - 1, cz0[2], cz1[2], cz2[2]);    // Zf(a-1, b, k)
         if (pg.vx && kn) y[px(k) + pg.ox] = combine((yf_prev - yf) + (zf - zf_b), f3(rx0, rx1, rx2), G + tid);
         if (pg.vy && kn) y[py(k) + pg.oy] = combine((zf_a - zf) + (xf - xf_prev), f3(ry0, ry1, ry2), G + kTP + tid);
         if (pg.vz && ks) {
@@ -371,17 +416,25 @@ __global__ void __launch_bounds__(256) k_restrict(int nf, const T* __restrict__ 
 }
 
 // weights of the coarse hat across an edge: fine node p -> coarse nodes
-// p/2 (weight 1) if p is even, (p-1)/2 and (p+1)/2 (weight 1/2) if odd
+// p/2 (weight 1) if p is even, (p-1)/2 and (p+1)/2 (weight 1/2) if odd,
+// written as two fixed terms (second weight 0 on even p) with coarse nodes
+// outside the interior given weight 0 and a valid index, so that all loads
+// of a fine edge are independent and issued together
 template <typename T>
-__device__ __forceinline__ int hat(int p, int (&C)[2], T (&w)[2]) {
-  C[0] = p >> 1;
-  C[1] = (p >> 1) + 1;
-  if (p & 1) {
-    w[0] = w[1] = T(0.5);
-    return 2;
+__device__ __forceinline__ void hat2(int p, int nc, int& p0, int& p1, T& w0, T& w1) {
+  const bool odd = p & 1;
+  p0 = p >> 1;
+  p1 = (p + 1) >> 1;
+  w0 = odd ? T(0.5) : T(1);
+  w1 = odd ? T(0.5) : T(0);
+  if (!in_node(p0, nc)) {
+    w0 = T(0);
+    p0 = 1;
   }
-  w[0] = T(1);
-  return 1;
+  if (!in_node(p1, nc)) {
+    w1 = T(0);
+    p1 = 1;
+  }
 }
 
 template <typename T>
@@ -394,33 +447,40 @@ __global__ void __launch_bounds__(256) k_prolong_add(int nf, const T* __restrict
   const int64_t N3f = (int64_t)nf * (nf - 1) * (nf - 1);
   zc += (int64_t)rhs * 3 * N3c;
   zf += (int64_t)rhs * 3 * N3f;
-  int A[2], B[2];
-  T wa[2], wb[2];
-  if (in_node(j, nf) && in_node(k, nf)) {  // x-edge: injection along x, hats in y and z
-    const int na = hat(j, A, wa), nb = hat(k, B, wb);
-    T s = T(0);
-    for (int a = 0; a < na; ++a)
-      for (int b = 0; b < nb; ++b)
-        if (in_node(A[a], nc) && in_node(B[b], nc)) s += wa[a] * wb[b] * __ldg(zc + off_x(nc, i >> 1, A[a], B[b]));
-    zf[off_x(nf, i, j, k)] += s;
+  int I0, I1, J0, J1, K0, K1;
+  T wi0, wi1, wj0, wj1, wk0, wk1;
+  hat2(i, nc, I0, I1, wi0, wi1);
+  hat2(j, nc, J0, J1, wj0, wj1);
+  hat2(k, nc, K0, K1, wk0, wk1);
+  const bool nj = in_node(j, nf), nk = in_node(k, nf), ni = in_node(i, nf);
+  // x-edge: injection along x (segment i / 2), hats in y and z
+  T vx[4] = {T(0), T(0), T(0), T(0)}, vy[4] = {T(0), T(0), T(0), T(0)}, vz[4] = {T(0), T(0), T(0), T(0)};
+  if (nj && nk) {
+    const int c = i >> 1;
+    vx[0] = __ldg(zc + off_x(nc, c, J0, K0));
+    vx[1] = __ldg(zc + off_x(nc, c, J1, K0));
+    vx[2] = __ldg(zc + off_x(nc, c, J0, K1));
+    vx[3] = __ldg(zc + off_x(nc, c, J1, K1));
   }
-  if (in_node(i, nf) && in_node(k, nf)) {
-    const int na = hat(i, A, wa), nb = hat(k, B, wb);
-    T s = T(0);
-    for (int a = 0; a < na; ++a)
-      for (int b = 0; b < nb; ++b)
-        if (in_node(A[a], nc) && in_node(B[b], nc)) s += wa[a] * wb[b] * __ldg(zc + N3c + off_y(nc, A[a], j >> 1, B[b]));
-    zf[N3f + off_y(nf, i, j, k)] += s;
+  if (ni && nk) {
+    const int c = j >> 1;
+    vy[0] = __ldg(zc + N3c + off_y(nc, I0, c, K0));
+    vy[1] = __ldg(zc + N3c + off_y(nc, I1, c, K0));
+    vy[2] = __ldg(zc + N3c + off_y(nc, I0, c, K1));
+    vy[3] = __ldg(zc + N3c + off_y(nc, I1, c, K1));
   }
-  if (in_node(i, nf) && in_node(j, nf)) {
-    const int na = hat(i, A, wa), nb = hat(j, B, wb);
-    T s = T(0);
-    for (int a = 0; a < na; ++a)
-      for (int b = 0; b < nb; ++b)
-        if (in_node(A[a], nc) && in_node(B[b], nc))
-          s += wa[a] * wb[b] * __ldg(zc + 2 * N3c + off_z(nc, A[a], B[b], k >> 1));
-    zf[2 * N3f + off_z(nf, i, j, k)] += s;
+  if (ni && nj) {
+    const int c = k >> 1;
+    vz[0] = __ldg(zc + 2 * N3c + off_z(nc, I0, J0, c));
+    vz[1] = __ldg(zc + 2 * N3c + off_z(nc, I1, J0, c));
+    vz[2] = __ldg(zc + 2 * N3c + off_z(nc, I0, J1, c));
+    vz[3] = __ldg(zc + 2 * N3c + off_z(nc, I1, J1, c));
   }
+  if (nj && nk) zf[off_x(nf, i, j, k)] += wk0 * (wj0 * vx[0] + wj1 * vx[1]) + wk1 * (wj0 * vx[2] + wj1 * vx[3]);
+  if (ni && nk)
+    zf[N3f + off_y(nf, i, j, k)] += wk0 * (wi0 * vy[0] + wi1 * vy[1]) + wk1 * (wi0 * vy[2] + wi1 * vy[3]);
+  if (ni && nj)
+    zf[2 * N3f + off_z(nf, i, j, k)] += wj0 * (wi0 * vz[0] + wi1 * vz[1]) + wj1 * (wi0 * vz[2] + wi1 * vz[3]);
 }
 
 // ---------------------------------------------------------------------------
@@ -615,33 +675,205 @@ __global__ void __launch_bounds__(256) k_patch_gram(int n, PatchFamily fam, int 
 }
 
 // ---------------------------------------------------------------------------
-// Coarsest solve (Fig. 1, k = 0): z = A_0^{-1} g with the precomputed dense
-// inverse, one CTA.
+// Local solves for a curl-curl coefficient that is constant per hexahedron.
+// The local matrices of the subdomains (eq. ATDef) and patches (eq. AVDef,
+// eq. AEDef) then depend on the coefficients of their cells; the host groups
+// them by those values and builds one operator per group.
 // ---------------------------------------------------------------------------
+// Interior spaces: as k_bubble, with the 6x6 inverse of coarse element t at
+// Atab + 36 gid[t] (coarse elements in x-fastest order).
 template <typename T>
-__global__ void __launch_bounds__(256) k_coarse(int N0, const double* __restrict__ Ainv, const T* __restrict__ g,
-                                                T* __restrict__ z) {
-  extern __shared__ double gs[];
-  g += (int64_t)blockIdx.x * N0;
-  z += (int64_t)blockIdx.x * N0;
-  for (int i = threadIdx.x; i < N0; i += blockDim.x) gs[i] = (double)g[i];
-  __syncthreads();
-  for (int i = threadIdx.x; i < N0; i += blockDim.x) {
+__global__ void __launch_bounds__(256) k_bubble_grouped(int n, const T* __restrict__ Atab, const int* __restrict__ gid,
+                                                        T eta, const T* __restrict__ r, T* __restrict__ z) {
+  const int nc = n / 2;
+  const int64_t NT = (int64_t)nc * nc * nc;
+  const int64_t N3 = (int64_t)n * (n - 1) * (n - 1);
+  r += (int64_t)blockIdx.y * 3 * N3;
+  z += (int64_t)blockIdx.y * 3 * N3;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < NT; t += (int64_t)gridDim.x * blockDim.x) {
+    const int I = (int)(t % nc), J = (int)((t / nc) % nc), K = (int)(t / ((int64_t)nc * nc));
+    const T* As = Atab + 36 * (int64_t)__ldg(gid + t);
+    int64_t gi[6];
+    int q = 0;
+    for (int d = 0; d < 3; ++d)
+      for (int s = 0; s < 2; ++s) {
+        int p[3] = {2 * I + 1, 2 * J + 1, 2 * K + 1};
+        p[d] = (d == 0 ? 2 * I : d == 1 ? 2 * J : 2 * K) + s;
+        gi[q++] = edge_gidx(n, d, p[0], p[1], p[2]);
+      }
+    T rv[6];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) rv[a] = __ldg(r + gi[a]);
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+      T s = T(0);
+#pragma unroll
+      for (int b = 0; b < 6; ++b) s += __ldg(As + a * 6 + b) * rv[b];
+      z[gi[a]] += eta * s;
+    }
+  }
+}
+
+// Patch solves with one dense operator per group: the patches of a family
+// are listed group by group (plist), cut into chunks of at most PB patches of
+// one group (chunk = {group, first list entry, count}); a CTA walks a
+// contiguous range of chunks and stages a group's operator in shared memory
+// only when the group changes.  z += eta * D_group r_p, atomics for overlaps.
+template <typename T, int PB>
+__global__ void __launch_bounds__(128) k_patch_grouped(int n, PatchFamily fam, const T* __restrict__ Dtab,
+                                                       const int4* __restrict__ chunks, int nchunks,
+                                                       const int* __restrict__ plist, T eta,
+                                                       const T* __restrict__ r, T* __restrict__ z) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nl = fam.nloc;
+  T* Ds = reinterpret_cast<T*>(smem_raw);          // nl * nl
+  T* Rs = Ds + nl * nl;                            // nl * PB
+  int* loc = reinterpret_cast<int*>(Rs + nl * PB); // packed (d, i, j, k) of each local edge
+  int* pidx = loc + nl;                            // PB patch numbers of the current chunk
+  const int64_t N3 = (int64_t)n * (n - 1) * (n - 1);
+  r += (int64_t)blockIdx.y * 3 * N3;
+  z += (int64_t)blockIdx.y * 3 * N3;
+  const int bx = fam.b[0], by = fam.b[1], bz = fam.b[2];
+  const int cx = bx * (by - 1) * (bz - 1), cy = (bx - 1) * by * (bz - 1);
+  for (int l = threadIdx.x; l < nl; l += blockDim.x) {
+    int d, i, j, k, e = l;
+    if (e < cx) {
+      d = 0; i = e % bx; j = (e / bx) % (by - 1) + 1; k = e / (bx * (by - 1)) + 1;
+    } else if ((e -= cx) < cy) {
+      d = 1; i = e % (bx - 1) + 1; j = (e / (bx - 1)) % by; k = e / ((bx - 1) * by) + 1;
+    } else {
+      e -= cy;
+      d = 2; i = e % (bx - 1) + 1; j = (e / (bx - 1)) % (by - 1) + 1; k = e / ((bx - 1) * (by - 1));
+    }
+    loc[l] = (((d * 16 + i) * 16 + j) * 16) + k;
+  }
+  auto gidx_of = [&](int64_t P, int l) {
+    const int pa = (int)(P % fam.np[0]) + fam.p0[0];
+    const int pb = (int)((P / fam.np[0]) % fam.np[1]) + fam.p0[1];
+    const int pc = (int)(P / ((int64_t)fam.np[0] * fam.np[1])) + fam.p0[2];
+    const int c = loc[l];
+    const int d = c >> 12, i = (c >> 8) & 15, j = (c >> 4) & 15, k = c & 15;
+    return edge_gidx(n, d, fam.stride * pa - fam.shift[0] + i, fam.stride * pb - fam.shift[1] + j,
+                     fam.stride * pc - fam.shift[2] + k);
+  };
+  const int c0 = (int)((int64_t)blockIdx.x * nchunks / gridDim.x);
+  const int c1 = (int)((int64_t)(blockIdx.x + 1) * nchunks / gridDim.x);
+  int staged = -1;
+  for (int ch = c0; ch < c1; ++ch) {
+    const int4 cd = __ldg(chunks + ch);  // group, first entry, count
+    __syncthreads();                     // the previous chunk is done with Ds, Rs, pidx
+    if (cd.x != staged) {
+      const T* D = Dtab + (int64_t)cd.x * nl * nl;
+      for (int q = threadIdx.x; q < nl * nl; q += blockDim.x) Ds[q] = __ldg(D + q);
+      staged = cd.x;
+    }
+    if (threadIdx.x < PB) pidx[threadIdx.x] = threadIdx.x < cd.z ? __ldg(plist + cd.y + threadIdx.x) : -1;
+    __syncthreads();
+    for (int q = threadIdx.x; q < nl * PB; q += blockDim.x) {
+      const int p = q / nl, l = q % nl;
+      const int P = pidx[p];
+      Rs[l * PB + p] = P >= 0 ? __ldg(r + gidx_of(P, l)) : T(0);
+    }
+    __syncthreads();
+    for (int row = threadIdx.x; row < nl; row += blockDim.x) {
+      T acc[PB];
+#pragma unroll
+      for (int p = 0; p < PB; ++p) acc[p] = T(0);
+      for (int c = 0; c < nl; ++c) {
+        const T dv = Ds[c * nl + row];
+#pragma unroll
+        for (int p = 0; p < PB; ++p) acc[p] += dv * Rs[c * PB + p];
+      }
+#pragma unroll
+      for (int p = 0; p < PB; ++p)
+        if (pidx[p] >= 0) atomicAdd(z + gidx_of(pidx[p], row), eta * acc[p]);
+    }
+  }
+}
+
+// Per-hexahedron derivative of a(., .) in its coefficient: out_T = -lambda^T
+// K_T u, K_T = h sum_d C_{T,d}^t m C_{T,d} (the curl of a lowest-order edge
+// field on a cube has, per axis d, a component that varies linearly between
+// the circulations of the two faces normal to d; m = [[1/3,1/6],[1/6,1/3]]).
+// One thread per cell; out[rhs n^3 + (k n + j) n + i].
+__device__ __forceinline__ double edge_val(const double* __restrict__ x, int n, int64_t N3, int d, int i, int j,
+                                           int k) {
+  if (d == 0) return in_seg(i, n) && in_node(j, n) && in_node(k, n) ? __ldg(x + off_x(n, i, j, k)) : 0.0;
+  if (d == 1) return in_node(i, n) && in_seg(j, n) && in_node(k, n) ? __ldg(x + N3 + off_y(n, i, j, k)) : 0.0;
+  return in_node(i, n) && in_node(j, n) && in_seg(k, n) ? __ldg(x + 2 * N3 + off_z(n, i, j, k)) : 0.0;
+}
+
+__device__ __forceinline__ void cell_circulations(const double* __restrict__ x, int n, int64_t N3, int i, int j,
+                                                  int k, double c[3][2]) {
+  double ex[2][2], ey[2][2], ez[2][2];  // x-edges [dj][dk], y-edges [di][dk], z-edges [di][dj]
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      ex[a][b] = edge_val(x, n, N3, 0, i, j + a, k + b);
+      ey[a][b] = edge_val(x, n, N3, 1, i + a, j, k + b);
+      ez[a][b] = edge_val(x, n, N3, 2, i + a, j + b, k);
+    }
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    c[0][s] = ez[s][1] - ez[s][0] - ey[s][1] + ey[s][0];  // x-normal face at x = i + s
+    c[1][s] = ex[s][1] - ex[s][0] - ez[1][s] + ez[0][s];  // y-normal face at y = j + s
+    c[2][s] = ey[1][s] - ey[0][s] - ex[1][s] + ex[0][s];  // z-normal face at z = k + s
+  }
+}
+
+__global__ void __launch_bounds__(256) k_grad_cells(int n, double h, const double* __restrict__ lam,
+                                                    const double* __restrict__ u, double* __restrict__ out) {
+  const int64_t N3 = (int64_t)n * (n - 1) * (n - 1);
+  const int64_t NC = (int64_t)n * n * n;
+  lam += (int64_t)blockIdx.y * 3 * N3;
+  u += (int64_t)blockIdx.y * 3 * N3;
+  out += (int64_t)blockIdx.y * NC;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < NC; t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % n), j = (int)((t / n) % n), k = (int)(t / ((int64_t)n * n));
+    double a[3][2], b[3][2];
+    cell_circulations(lam, n, N3, i, j, k, a);
+    cell_circulations(u, n, N3, i, j, k, b);
     double s = 0.0;
-    for (int j = 0; j < N0; ++j) s += Ainv[(int64_t)j * N0 + i] * gs[j];
-    z[i] = (T)s;
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      s += 2.0 * (a[d][0] * b[d][0] + a[d][1] * b[d][1]) + a[d][0] * b[d][1] + a[d][1] * b[d][0];
+    out[t] = -h * s / 6.0;
   }
 }
 
 // ---------------------------------------------------------------------------
-// BLAS-1 with FP64 accumulation.  Reductions are two-stage and deterministic:
-// a fixed number of blocks writes partial sums, one block adds them.
+// Coarsest solve (Fig. 1, k = 0): z = A_0^{-1} g with the precomputed dense
+// inverse (symmetric, so row i is column i): one warp per row, lanes along
+// the row (coalesced), g staged in shared memory; 8 rows per CTA.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_coarse(int N0, const double* __restrict__ Ainv, const T* __restrict__ g,
+                                                T* __restrict__ z) {
+  extern __shared__ double gs[];
+  g += (int64_t)blockIdx.y * N0;
+  z += (int64_t)blockIdx.y * N0;
+  for (int i = threadIdx.x; i < N0; i += blockDim.x) gs[i] = (double)g[i];
+  __syncthreads();
+  const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (row >= N0) return;
+  const double* a = Ainv + (int64_t)row * N0;
+  double s = 0.0;
+  for (int j = lane; j < N0; j += 32) s += __ldg(a + j) * gs[j];
+  s = warp_sum(s);
+  if (lane == 0) z[row] = (T)s;
+}
+
+// ---------------------------------------------------------------------------
+// BLAS-1 with FP64 accumulation.  Reductions are two-stage and deterministic:
+// a fixed number of blocks writes partial sums, one block adds them.
+// ---------------------------------------------------------------------------
 
 template <int NV>
 __device__ __forceinline__ void block_sum_store(double (&v)[NV], double* out) {
@@ -666,7 +898,10 @@ __device__ __forceinline__ void block_sum_store(double (&v)[NV], double* out) {
 
 // Batched BLAS-1: grid y (or x for the finishing kernel) is the right-hand
 // side; every right-hand side is a contiguous vector of N entries; scalars
-// come from per-right-hand-side device arrays.
+// come from per-right-hand-side device arrays.  The FP64 vector kernels move
+// two entries per access (16-byte loads; every right-hand side starts on a
+// 16-byte boundary when N is even, else the scalar path runs) so that enough
+// bytes are in flight to keep HBM busy.
 // partial[(rhs * gridDim.x + b) * 2 + {0,1}] = block sums of x.y and x2.y2
 template <typename T>
 __global__ void __launch_bounds__(256) k_dot2(int64_t N, const T* __restrict__ x, const T* __restrict__ y,
@@ -674,7 +909,25 @@ __global__ void __launch_bounds__(256) k_dot2(int64_t N, const T* __restrict__ x
                                               double* __restrict__ partial) {
   const int64_t off = (int64_t)blockIdx.y * N;
   double v[2] = {0.0, 0.0};
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
+  int64_t e0 = 0;
+  if constexpr (std::is_same<T, double>::value) if ((N & 1) == 0) {
+    const int64_t N2 = N / 2;
+    const double2* x_ = reinterpret_cast<const double2*>(x + off);
+    const double2* y_ = reinterpret_cast<const double2*>(y + off);
+    const double2* x2_ = reinterpret_cast<const double2*>(x2 ? x2 + off : x + off);
+    const double2* y2_ = reinterpret_cast<const double2*>(y2 ? y2 + off : y + off);
+    for (int64_t e = t0; e < N2; e += st) {
+      const double2 a = __ldg(x_ + e), b = __ldg(y_ + e);
+      v[0] += a.x * b.x + a.y * b.y;
+      if (x2) {
+        const double2 c = __ldg(x2_ + e), d = __ldg(y2_ + e);
+        v[1] += c.x * d.x + c.y * d.y;
+      }
+    }
+    e0 = N;
+  }
+  for (int64_t e = e0 + t0; e < N; e += st) {
     v[0] += (double)x[off + e] * (double)y[off + e];
     if (x2) v[1] += (double)x2[off + e] * (double)y2[off + e];
   }
@@ -732,7 +985,29 @@ __global__ void __launch_bounds__(256) k_cg_update_rr(int64_t N, const double* _
   const int64_t off = (int64_t)blockIdx.y * N;
   const double a = alpha[blockIdx.y], s = sto[blockIdx.y];
   double v[2] = {0.0, 0.0};
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
+  int64_t e0 = 0;
+  if ((N & 1) == 0) {
+    const double2* p_ = reinterpret_cast<const double2*>(p + off);
+    const double2* q_ = reinterpret_cast<const double2*>(q + off);
+    double2* u_ = reinterpret_cast<double2*>(u + off);
+    double2* r_ = reinterpret_cast<double2*>(r + off);
+    float2* g_ = reinterpret_cast<float2*>(g32 + off);
+    for (int64_t e = t0; e < N / 2; e += st) {
+      const double2 pv = __ldg(p_ + e), qv = __ldg(q_ + e);
+      double2 uv = u_[e], rv = r_[e];
+      uv.x += a * pv.x;
+      uv.y += a * pv.y;
+      rv.x -= a * qv.x;
+      rv.y -= a * qv.y;
+      u_[e] = uv;
+      r_[e] = rv;
+      g_[e] = make_float2((float)(s * rv.x), (float)(s * rv.y));
+      v[0] += rv.x * rv.x + rv.y * rv.y;
+    }
+    e0 = N;
+  }
+  for (int64_t e = e0 + t0; e < N; e += st) {
     u[off + e] += a * p[off + e];
     const double rn = r[off + e] - a * q[off + e];
     r[off + e] = rn;
@@ -750,7 +1025,22 @@ __global__ void __launch_bounds__(256) k_dot2_zf(int64_t N, const double* __rest
   const int64_t off = (int64_t)blockIdx.y * N;
   const double s = sc[blockIdx.y];
   double v[2] = {0.0, 0.0};
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
+  int64_t e0 = 0;
+  if ((N & 1) == 0) {
+    const double2* x_ = reinterpret_cast<const double2*>(x + off);
+    const double2* y_ = reinterpret_cast<const double2*>(y + off);
+    const float2* z_ = reinterpret_cast<const float2*>(z32 + off);
+    for (int64_t e = t0; e < N / 2; e += st) {
+      const double2 a = __ldg(x_ + e), b = __ldg(y_ + e);
+      const float2 zf = __ldg(z_ + e);
+      const double z0 = s * (double)zf.x, z1 = s * (double)zf.y;
+      v[0] += a.x * z0 + a.y * z1;
+      v[1] += b.x * z0 + b.y * z1;
+    }
+    e0 = N;
+  }
+  for (int64_t e = e0 + t0; e < N; e += st) {
     const double z = s * (double)z32[off + e];
     v[0] += x[off + e] * z;
     v[1] += y[off + e] * z;
@@ -763,8 +1053,21 @@ __global__ void __launch_bounds__(256) k_axpby_zf(int64_t N, const double* __res
                                                   const double* __restrict__ ab, double* __restrict__ p) {
   const int64_t off = (int64_t)blockIdx.y * N;
   const double s = sc[blockIdx.y], b = ab[2 * blockIdx.y + 1];
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x)
-    p[off + e] = s * (double)z32[off + e] + b * p[off + e];
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
+  int64_t e0 = 0;
+  if ((N & 1) == 0) {
+    const float2* z_ = reinterpret_cast<const float2*>(z32 + off);
+    double2* p_ = reinterpret_cast<double2*>(p + off);
+    for (int64_t e = t0; e < N / 2; e += st) {
+      const float2 zf = __ldg(z_ + e);
+      double2 pv = p_[e];
+      pv.x = s * (double)zf.x + b * pv.x;
+      pv.y = s * (double)zf.y + b * pv.y;
+      p_[e] = pv;
+    }
+    e0 = N;
+  }
+  for (int64_t e = e0 + t0; e < N; e += st) p[off + e] = s * (double)z32[off + e] + b * p[off + e];
 }
 
 // dst (float) = s * src (double), s = sc[rhs]
@@ -818,6 +1121,16 @@ cudaError_t prepare_stencil() {
                               (int)stencil_smem<T>());
 }
 
+// z chunk: the longest (fewest halo planes) that still gives about four
+// CTAs per SM
+static inline dim3 stencil_grid(int n, int sm, int R, int* KZ) {
+  const int64_t cols = (int64_t)((n + kTX - 1) / kTX) * ((n + kTY - 1) / kTY) * R;
+  int kz = n;
+  while (kz > 2 && cols * ((n + kz - 1) / kz) < 4LL * sm) kz = (kz + 1) / 2;
+  *KZ = kz;
+  return dim3((n + kTX - 1) / kTX, (n + kTY - 1) / kTY, ((n + kz - 1) / kz) * R);
+}
+
 template <typename T>
 void launch_stencil(cudaStream_t s, int sm, int n, double cK, double cM, const T* u, const T* g, T* y, int R,
                     unsigned long long* umax) {
@@ -827,14 +1140,30 @@ void launch_stencil(cudaStream_t s, int sm, int n, double cK, double cM, const T
     cudaMemsetAsync(umax, 0, sizeof(unsigned long long) * R, s);
     k_absmax<<<dim3(grid_for(N, sm, 4), R), 256, 0, s>>>(N, u, umax);
   }
-  // z chunk: the longest (fewest halo planes) that still gives about four
-  // CTAs per SM
-  const int64_t cols = (int64_t)((n + kTX - 1) / kTX) * ((n + kTY - 1) / kTY) * R;
-  int KZ = n;
-  while (KZ > 4 && cols * ((n + KZ - 1) / KZ) < 4LL * sm) KZ = (KZ + 1) / 2;
-  dim3 grid((n + kTX - 1) / kTX, (n + kTY - 1) / kTY, ((n + KZ - 1) / KZ) * R);
+  int KZ = 0;
+  const dim3 grid = stencil_grid(n, sm, R, &KZ);
   k_stencil_stream<T, StencilArith<T>>
       <<<grid, dim3(kTX, kTY), stencil_smem<T>(), s>>>(n, KZ, (T)cK, (T)cM, u, g, y, umax);
+}
+
+// coefficient field: three more staged planes (the cell coefficients)
+template <typename T>
+size_t stencil_field_smem() { return stencil_smem<T>() + sizeof(T) * 3 * kP; }
+
+template <typename T>
+cudaError_t prepare_stencil_field() {
+  return cudaFuncSetAttribute(k_stencil_stream<T, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)stencil_field_smem<T>());
+}
+
+template <typename T>
+void launch_stencil_field(cudaStream_t s, int sm, int n, double cK, double cM, const T* u, const T* g, T* y, int R,
+                          const T* acell) {
+  if (n < 2) return;
+  int KZ = 0;
+  const dim3 grid = stencil_grid(n, sm, R, &KZ);
+  k_stencil_stream<T, T, true>
+      <<<grid, dim3(kTX, kTY), stencil_field_smem<T>(), s>>>(n, KZ, (T)cK, (T)cM, u, g, y, nullptr, acell);
 }
 
 template <typename T>
@@ -945,10 +1274,10 @@ void launch_vertex_dense(cudaStream_t s, int sm, int n, const T* D, double eta, 
 
 template <typename T>
 void launch_coarse(cudaStream_t s, int N0, const double* Ainv, const T* g, T* z, int R) {
-  k_coarse<T><<<R, 256, sizeof(double) * N0, s>>>(N0, Ainv, g, z);
+  k_coarse<T><<<dim3((N0 + 7) / 8, R), 256, sizeof(double) * N0, s>>>(N0, Ainv, g, z);
 }
 
-int reduction_blocks(int sm) { return sm * 4; }
+int reduction_blocks(int sm) { return sm * 8; }
 
 template <typename T>
 void launch_dot2(cudaStream_t s, int sm, int64_t N, const T* x, const T* y, const T* x2, const T* y2, double* partial,
@@ -1006,10 +1335,56 @@ void launch_add_f32(cudaStream_t s, int sm, int64_t N, const double* sc, const f
   k_add_f32<<<blas_grid(N, sm, R), 256, 0, s>>>(N, sc, src, dst);
 }
 
+// ---- coefficient field ------------------------------------------------------
+template <typename T>
+void launch_bubble_grouped(cudaStream_t s, int sm, int n, const T* Atab, const int* gid, double eta, const T* r, T* z,
+                           int R) {
+  const int64_t nc = n / 2;
+  k_bubble_grouped<T><<<dim3(grid_for(nc * nc * nc, sm, 16), R), 256, 0, s>>>(n, Atab, gid, (T)eta, r, z);
+}
+
+constexpr int kGroupPB = 8;
+
+template <typename T>
+size_t patch_grouped_smem(int nloc) {
+  return sizeof(T) * (size_t)(nloc * nloc + nloc * kGroupPB) + sizeof(int) * (size_t)(nloc + kGroupPB);
+}
+
+template <typename T>
+cudaError_t prepare_patch_grouped() {
+  return cudaFuncSetAttribute(k_patch_grouped<T, kGroupPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)patch_grouped_smem<T>(108));
+}
+
+int patch_group_size() { return kGroupPB; }
+
+template <typename T>
+void launch_patch_grouped(cudaStream_t s, int sm, int n, const PatchFamily& fam, const T* Dtab, const int4* chunks,
+                          int nchunks, const int* plist, double eta, const T* r, T* z, int R) {
+  if (nchunks <= 0) return;
+  int blocks = sm * 2;
+  if (blocks > nchunks) blocks = nchunks;
+  k_patch_grouped<T, kGroupPB><<<dim3(blocks, R), 128, patch_grouped_smem<T>(fam.nloc), s>>>(
+      n, fam, Dtab, chunks, nchunks, plist, (T)eta, r, z);
+}
+
+void launch_grad_cells(cudaStream_t s, int sm, int n, double h, const double* lam, const double* u, double* out,
+                       int R) {
+  const int64_t nc = (int64_t)n * n * n;
+  k_grad_cells<<<dim3(grid_for(nc, sm, 8), R), 256, 0, s>>>(n, h, lam, u, out);
+}
+
 #define NDMG_INST(T)                                                                                   \
   template void launch_stencil<T>(cudaStream_t, int, int, double, double, const T*, const T*, T*, int,    \
                                   unsigned long long*);                                               \
   template cudaError_t prepare_stencil<T>();                                                          \
+  template cudaError_t prepare_stencil_field<T>();                                                    \
+  template void launch_stencil_field<T>(cudaStream_t, int, int, double, double, const T*, const T*, T*, int, \
+                                        const T*);                                                    \
+  template void launch_bubble_grouped<T>(cudaStream_t, int, int, const T*, const int*, double, const T*, T*, int); \
+  template cudaError_t prepare_patch_grouped<T>();                                                    \
+  template void launch_patch_grouped<T>(cudaStream_t, int, int, const PatchFamily&, const T*, const int4*, int, \
+                                        const int*, double, const T*, T*, int);                       \
   template void launch_restrict<T>(cudaStream_t, int, int, const T*, T*, int);                        \
   template void launch_prolong_add<T>(cudaStream_t, int, int, const T*, T*, int);                     \
   template void launch_bubble<T>(cudaStream_t, int, int, const T*, double, const T*, T*, int);        \

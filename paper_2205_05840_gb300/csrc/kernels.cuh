@@ -50,6 +50,25 @@ void launch_patch_dense(cudaStream_t s, int sm, int n, const PatchFamily& fam, c
                         T* z, int R);
 template <typename T>
 void launch_coarse(cudaStream_t s, int N0, const double* Ainv, const T* g, T* z, int R);
+// coefficient field: the operator with a coefficient per cell (acell, n^3;
+// cK = h times the pencil factor), interior solves and patch solves with one
+// operator per group, and the per-cell derivative -lambda^T K_T u
+template <typename T>
+cudaError_t prepare_stencil_field();
+template <typename T>
+void launch_stencil_field(cudaStream_t s, int sm, int n, double cK, double cM, const T* u, const T* g, T* y, int R,
+                          const T* acell);
+template <typename T>
+void launch_bubble_grouped(cudaStream_t s, int sm, int n, const T* Atab, const int* gid, double eta, const T* r, T* z,
+                           int R);
+int patch_group_size();
+template <typename T>
+cudaError_t prepare_patch_grouped();
+template <typename T>
+void launch_patch_grouped(cudaStream_t s, int sm, int n, const PatchFamily& fam, const T* Dtab, const int4* chunks,
+                          int nchunks, const int* plist, double eta, const T* r, T* z, int R);
+void launch_grad_cells(cudaStream_t s, int sm, int n, double h, const double* lam, const double* u, double* out,
+                       int R);
 int reduction_blocks(int sm);
 template <typename T>
 void launch_dot2(cudaStream_t s, int sm, int64_t N, const T* x, const T* y, const T* x2, const T* y2,

@@ -45,6 +45,14 @@ struct LocalOps {
 // Dense assembled matrix of a box with Dirichlet (interior-edge) DOFs for
 // a(w,v) = alpha (curl w, curl v) + beta (w, v) on cubes of side h.
 std::vector<double> box_matrix(const Box& box, double h, double alpha, double beta);
+// The same with a curl-curl coefficient per cell of the box (acell: one value
+// per cell, x fastest).
+std::vector<double> box_matrix_cells(const Box& box, double h, const double* acell, double beta);
+// J_D A_D^{-1} J_D^t of the discrete-harmonic space of a box of cells split
+// into s x s x s subdomains, from the box's assembled matrix Ap: dense D
+// (optional) and Gram factor W (np x n_interface).
+void patch_operator(const Box& pb, int s, const std::vector<double>& Ap, std::vector<double>* D,
+                    std::vector<double>* W, int* n_interface);
 // Vertex-patch operator and Gram factor, interior-space inverse for level n
 // with subdomains of s x s x s cells (s = 2: the coarse elements).
 void build_local_ops(int n, double L, double alpha, double beta, LocalOps* out, int s = 2);
@@ -54,7 +62,46 @@ std::vector<double> coarse_inverse(int n0, double L, double alpha, double beta);
 bool cholesky(std::vector<double>& a, int n);
 std::vector<double> spd_inverse(const std::vector<double>& a, int n, bool* ok);
 
+// ---- curl-curl coefficient constant per hexahedron (field.cpp) ---------------
+// One family of local problems on one level (interior spaces, vertex or edge
+// patches), grouped by the coefficients of the cells each one covers.
+struct GroupedFamily {
+  int nloc = 0;             // edges of one local problem
+  int nG = 0;               // interface edges (vertex patches)
+  int ngroups = 0;
+  std::vector<int> gid;     // group of every member, in family order
+  std::vector<double> op;   // ngroups x nloc x nloc: A_T^{-1} (interior) or J A^{-1} J^t (patches)
+  std::vector<double> W;    // ngroups x nloc x nG Gram factors (vertex patches)
+  double tc_spectral = 0.0; // largest eigenvalue of A_p W~ W~^t over the groups (rounded operands; 0 unchecked)
+};
+struct FieldOps {
+  GroupedFamily bub;        // interior spaces of the coarse elements
+  GroupedFamily vtx;        // vertex patches (vertex-based smoother)
+  GroupedFamily edge[3];    // edge patches along x, y, z (edge-based smoother)
+};
+// mean of the 8 fine coefficients of every coarse hexahedron (n -> n/2)
+std::vector<double> coarsen_cells(const std::vector<double>& a, int n);
+// local operators of level n for cell coefficients acell (n^3, x fastest);
+// throws if a family has more than max_groups distinct local problems
+// lowp: 0, or the tensor-core operand type to check the vertex groups for
+// (1 = bf16, 2 = fp16; sets vtx.tc_spectral)
+void build_field_ops(int n, double L, const std::vector<double>& acell, double beta, bool edge, int max_groups,
+                     FieldOps* out, int lowp = 0);
+std::vector<double> coarse_inverse_cells(int n0, double L, const std::vector<double>& acell, double beta);
+// members listed group by group (plist) and chunks {group, first, count, 0}
+// of at most pb members of one group
+void group_chunks(const GroupedFamily& g, int pb, std::vector<int>* plist, std::vector<int>* chunks);
+
 // ---- device side -----------------------------------------------------------
+// a grouped family on the device (coefficient field)
+struct DevGrouped {
+  int nchunks = 0;
+  int4* chunks = nullptr;   // {group, first plist entry, count, 0}
+  int* plist = nullptr;     // members, group by group
+  double* op64 = nullptr;   // ngroups x nloc x nloc
+  float* op32 = nullptr;
+};
+
 struct DevLevel {
   int n;
   int64_t N;                  // edges on this level
@@ -74,6 +121,17 @@ struct DevLevel {
   // and its transpose, for k_patch_gram
   double *Wg64 = nullptr, *WgT64 = nullptr;
   float *Wg32 = nullptr, *WgT32 = nullptr;
+  // curl-curl coefficient per hexahedron (ndmg_set_alpha_field); cK is then h
+  double* a64 = nullptr;      // n^3 cell coefficients
+  float* a32 = nullptr;
+  int* bub_gid = nullptr;     // group of every coarse element's interior space
+  double* bubA64 = nullptr;   // 36 per group
+  float* bubA32 = nullptr;
+  DevGrouped vtx, edg[3];     // vertex patches; edge patches along x, y, z
+  void* Wtc_tab = nullptr;    // tensor-core operand image per vertex group
+  int* tc_off = nullptr;      // per brick: first entry of its group list (nbricks + 1)
+  int* tc_grp = nullptr;      // per entry: group
+  uint4* tc_mask = nullptr;   // per entry: the brick's rows (patches) in that group
 };
 
 }  // namespace ndmg
@@ -96,6 +154,7 @@ struct ndmg_handle {
   unsigned long long* umax = nullptr;     // per right-hand side max |u| of the fixed-point FP64 stencil
   int* status_host = nullptr;             // pinned mirror of the status word
   std::string err;
+  bool field = false;                     // curl-curl coefficient per hexahedron (ndmg_set_alpha_field)
   // tracing: per kernel class, event pairs recorded around launches
   bool trace_on[NDMG_K_COUNT] = {};
   int64_t trace_launches[NDMG_K_COUNT] = {};

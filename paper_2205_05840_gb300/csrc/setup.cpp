@@ -68,16 +68,18 @@ void element_matrix(double h, double alpha, double beta, double out[12][12]) {
 
 }  // namespace
 
-std::vector<double> box_matrix(const Box& box, double h, double alpha, double beta) {
+// Sum of the element matrices of the box's cells over its interior edges;
+// elem(cell) gives the 12x12 matrix of cell (ci, cj, ck), cell = (ck by + cj) bx + ci.
+template <typename Elem>
+static std::vector<double> assemble_box(const Box& box, Elem&& elem) {
   const int64_t N = box.size();
   std::vector<double> A((size_t)(N * N), 0.0);
-  double E[12][12];
-  element_matrix(h, alpha, beta, E);
   int64_t gid[12];
   for (int ck = 0; ck < box.b[2]; ++ck)
     for (int cj = 0; cj < box.b[1]; ++cj)
       for (int ci = 0; ci < box.b[0]; ++ci) {
         const int c[3] = {ci, cj, ck};
+        const double(&E)[12][12] = elem((ck * box.b[1] + cj) * box.b[0] + ci);
         for (int e = 0; e < 12; ++e) {
           LocalEdge le = local_edge(e);
           int p[3] = {c[0], c[1], c[2]};
@@ -94,6 +96,23 @@ std::vector<double> box_matrix(const Box& box, double h, double alpha, double be
         }
       }
   return A;
+}
+
+std::vector<double> box_matrix(const Box& box, double h, double alpha, double beta) {
+  double E[12][12];
+  element_matrix(h, alpha, beta, E);
+  return assemble_box(box, [&](int) -> const double(&)[12][12] { return E; });
+}
+
+std::vector<double> box_matrix_cells(const Box& box, double h, const double* acell, double beta) {
+  double Kh[12][12], Mh[12][12], E[12][12];
+  element_matrix(h, 1.0, 0.0, Kh);
+  element_matrix(h, 0.0, 1.0, Mh);
+  return assemble_box(box, [&](int c) -> const double(&)[12][12] {
+    for (int p = 0; p < 12; ++p)
+      for (int q = 0; q < 12; ++q) E[p][q] = acell[c] * Kh[p][q] + beta * Mh[p][q];
+    return E;
+  });
 }
 
 bool cholesky(std::vector<double>& a, int n) {
@@ -155,13 +174,12 @@ std::vector<double> spd_inverse(const std::vector<double>& a, int n, bool* ok) {
 // the interiors of its s x s x s subdomains (I) and the rest (G); with
 // S = A_GG - A_GI A_II^{-1} A_IG = R R^t and H = [-A_II^{-1} A_IG ; I],
 // W = H R^{-t} and D = W W^t (= A_p^{-1} - sum_T J_T A_T^{-1} J_T^t).
-// AinvT: the interior-space inverse of one subdomain in the canonical order
-// of its s-box (for the self-check).  D may be null (large patches: only W).
-static void patch_operator(const Box& pb, int s, double h, double alpha, double beta,
-                           const std::vector<double>& AinvT, std::vector<double>* D, std::vector<double>* W,
-                           int* n_interface) {
+// Ap: the assembled matrix of the box (its own canonical order); the
+// subdomains' interior-space inverses (its diagonal blocks on I) serve the
+// self-check.  D may be null (large patches: only W).
+void patch_operator(const Box& pb, int s, const std::vector<double>& Ap, std::vector<double>* D,
+                    std::vector<double>* W, int* n_interface) {
   const int np = (int)pb.size();
-  std::vector<double> Ap = box_matrix(pb, h, alpha, beta);
   // the interior spaces of the subdomains inside the box, each in its s-box
   // order; Bblk = sum_T J_T A_T^{-1} J_T^t restricted to the box
   const Box sb{{s, s, s}};
@@ -180,6 +198,13 @@ static void patch_operator(const Box& pb, int s, double h, double alpha, double 
                 const int64_t l = sb.index(d, i, j, k);
                 if (l >= 0) ids[l] = (int)pb.index(d, o[0] + i, o[1] + j, o[2] + k);
               }
+        // this subdomain's interior-space inverse (its block of A_p)
+        std::vector<double> AT((size_t)mT * mT);
+        for (int a = 0; a < mT; ++a)
+          for (int b = 0; b < mT; ++b) AT[(size_t)a * mT + b] = Ap[(size_t)ids[a] * np + ids[b]];
+        bool ok = false;
+        const std::vector<double> AinvT = spd_inverse(AT, mT, &ok);
+        if (!ok) throw std::runtime_error("interior-space block is not SPD");
         for (int a = 0; a < mT; ++a) {
           isB[ids[a]] = 1;
           for (int b = 0; b < mT; ++b) Bblk[(size_t)ids[a] * np + ids[b]] = AinvT[(size_t)a * mT + b];
@@ -300,7 +325,7 @@ void build_local_ops(int n, double L, double alpha, double beta, LocalOps* out, 
   const Box vb{{2 * s, 2 * s, 2 * s}};
   out->mV = (int)vb.size();
   int nG = 0;
-  patch_operator(vb, s, h, alpha, beta, out->AinvT, s == 2 ? &out->Dv : nullptr, &out->Wv, &nG);
+  patch_operator(vb, s, box_matrix(vb, h, alpha, beta), s == 2 ? &out->Dv : nullptr, &out->Wv, &nG);
   out->nG = nG;
   if (nG != out->mV - 8 * out->mT) throw std::runtime_error("unexpected vertex-patch split");
   if (s != 2) return;
@@ -310,7 +335,7 @@ void build_local_ops(int n, double L, double alpha, double beta, LocalOps* out, 
     Box eb{{4, 4, 4}};
     eb.b[d] = 2;
     std::vector<double> We;
-    patch_operator(eb, 2, h, alpha, beta, out->AinvT, &out->De[d], &We, &nG);
+    patch_operator(eb, 2, box_matrix(eb, h, alpha, beta), &out->De[d], &We, &nG);
     if (nG != 18) throw std::runtime_error("unexpected edge-patch split");
   }
 }

@@ -30,6 +30,7 @@
 // byte offset (next 8-row group) = K/8 * 128.
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "tc_patch.cuh"
 
@@ -93,8 +94,10 @@ constexpr RegionTable make_region_table() {
 static_assert(kRegionAll < (1 << 13) && kCX <= 32 && kCY <= 16 && kCZ <= 16, "region table fields");
 __device__ const RegionTable kRegionTab = make_region_table();
 
-// Calls f(octant index, global offset within one right-hand side, edge is
-// interior) for every element of the direction-D part of the region.  Region
+// Calls f(table entry, global offset within one right-hand side, edge is
+// interior) for every element of the direction-D part of the region (the
+// entry holds the octant-layout index in bits 0-12 and the region
+// coordinates i, j, k in bits 13-17, 18-21, 22-25).  Region
 // element (i, j, k) of direction D is the edge at global coordinates
 // 2 V0 + (i, j, k) - (2 along D, 1 across).
 template <int D, typename F>
@@ -129,7 +132,7 @@ __device__ __forceinline__ void walk_region(int n, int VX, int VY, int VZ, int t
       in = (unsigned)(gi - 1) < n1 && (unsigned)(gj - 1) < n1 && (unsigned)gk < (unsigned)n;
       off = 2u * N3 + ((uint32_t)gk * n1 + (uint32_t)(gj - 1)) * n1 + (uint32_t)(gi - 1);
     }
-    f((int)(e & 8191u), off, in);
+    f(e, off, in);
   }
 }
 
@@ -143,12 +146,18 @@ constexpr int OFF_TM = OFF_BAR + 16;
 constexpr int OFF_RED = OFF_TM + 16;
 constexpr int OFF_AT = OFF_RED + 32;          // A_T^{-1} (6 x 6, FP32)
 constexpr int kSmem = OFF_AT + 36 * 4;
-constexpr int OFF_ACC = OFF_A;                // region accumulator, over A' once D' is complete
-static_assert(kRegionAll * 4 <= kM * kK1 * 2, "accumulator fits in the A operand");
 static_assert(OFF_BAR % 8 == 0, "mbarrier alignment");
 static_assert(3 * (kSmem + 1024) <= 228 * 1024, "three CTAs per SM (228 KB, 1 KB reserved per CTA)");
 
+// coefficient field (one W per group of patches): A is kept for every group
+// of the brick, so A' and the accumulator get their own space
+constexpr int OFF_A2F = (kSmem + 127) / 128 * 128;
+constexpr int OFF_ACCF = OFF_A2F + kM * kK2 * 2;
+constexpr int kSmemF = OFF_ACCF + ((kRegionAll * 4 + 15) / 16) * 16;
+static_assert(2 * (kSmemF + 1024) <= 228 * 1024, "two CTAs per SM (228 KB, 1 KB reserved per CTA)");
+
 constexpr int kImgBytes = (kN1 * kK1 + kN2 * kK2) * 2;  // both W images
+constexpr int kImgStride = kImgBytes + 16;               // one image and its scale
 static_assert(OFF_B2 - OFF_B1 == kN1 * kK1 * 2 && OFF_R - OFF_B1 == kImgBytes, "W images are one block");
 constexpr int kTimeout = 1;                              // status code
 
@@ -311,6 +320,142 @@ __device__ __forceinline__ void scatter16(uint32_t taddr, float* acc, int a, int
   }
 }
 
+// D = A W: M = 128, N = 64, K = 112 (one elected thread)
+template <bool FP16>
+__device__ __forceinline__ void issue_mma1(uint32_t tmem, uint32_t a0, uint32_t b0, uint32_t bar) {
+  const uint32_t idesc = instr_desc(kM, kN1, FP16);
+#pragma unroll
+  for (int kk = 0; kk < kK1 / 16; ++kk)
+    mma_f16(tmem, smem_desc(a0 + kk * 256, 128, (kK1 / 8) * 128), smem_desc(b0 + kk * 256, 128, (kK1 / 8) * 128),
+            idesc, kk > 0);
+  mma_commit(bar);
+}
+
+// D' = A' W^t: M = 128, N = 112, K = 64 (one elected thread)
+template <bool FP16>
+__device__ __forceinline__ void issue_mma2(uint32_t tmem, uint32_t a0, uint32_t b0, uint32_t bar) {
+  const uint32_t idesc = instr_desc(kM, kN2, FP16);
+#pragma unroll
+  for (int kk = 0; kk < kK2 / 16; ++kk)
+    mma_f16(tmem, smem_desc(a0 + kk * 256, 128, (kK2 / 8) * 128), smem_desc(b0 + kk * 256, 128, (kK2 / 8) * 128),
+            idesc, kk > 0);
+  mma_commit(bar);
+}
+
+// A' = low-precision copy of D (8 warps: lane quadrant x column half)
+template <bool FP16>
+__device__ __forceinline__ void convert_d(uint32_t tmem, uint8_t* A2, int warp, int lane) {
+  const int p = (warp & 3) * 32 + lane;
+  const int cb0 = (warp >> 2) * 32;
+#pragma unroll 1
+  for (int cb = cb0; cb < cb0 + 32; cb += 16) {
+    float v[16];
+    tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + cb, v);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      uint4 w;
+      w.x = pack2<FP16>(v[8 * h + 0], v[8 * h + 1]);
+      w.y = pack2<FP16>(v[8 * h + 2], v[8 * h + 3]);
+      w.z = pack2<FP16>(v[8 * h + 4], v[8 * h + 5]);
+      w.w = pack2<FP16>(v[8 * h + 6], v[8 * h + 7]);
+      *reinterpret_cast<uint4*>(A2 + core_off(p, cb + 8 * h, kK2)) = w;
+    }
+  }
+}
+
+// rows of D' (this warp's lane quadrant, its column half) added into the
+// region accumulator, scaled by scl (0 for rows that add nothing)
+__device__ __forceinline__ void scatter_rows(uint32_t tmem, float* acc, int warp, int lane, float scl) {
+  const int prow = (warp & 3) * 32 + lane;
+  const int a = prow % kBX, b = (prow / kBX) % kBY, c = prow / (kBX * kBY);
+  const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+  // tcgen05.ld is warp-collective: every lane loads
+  if (warp < 4) {
+    scatter16<0>(taddr, acc, a, b, c, scl);
+    scatter16<16>(taddr, acc, a, b, c, scl);
+    scatter16<32>(taddr, acc, a, b, c, scl);
+    scatter16<48>(taddr, acc, a, b, c, scl);
+  } else {
+    scatter16<64>(taddr, acc, a, b, c, scl);
+    scatter16<80>(taddr, acc, a, b, c, scl);
+    scatter16<96>(taddr, acc, a, b, c, scl);
+  }
+}
+
+// D' in shared memory for the gather below: row p (patch) at p * kDS, its 108
+// outputs contiguous (a row stride of 108 floats keeps the 16-byte stores of a
+// warp's 32 rows spread over all banks)
+constexpr int kDS = 108;
+static_assert(kM * kDS * 4 <= OFF_R - OFF_A, "D' fits over A and the W images");
+
+// this warp's rows (lane quadrant) and column half of D' from TMEM to ds
+__device__ __forceinline__ void stage_rows(uint32_t tmem, float* ds, int warp, int lane) {
+  const int prow = (warp & 3) * 32 + lane;
+  const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+  float* dst = ds + prow * kDS;
+  const int c0 = (warp >> 2) * 64;  // warp-uniform: columns [0, 64) or [64, 108)
+#pragma unroll
+  for (int cb = 0; cb < 64; cb += 16) {
+    if (c0 + cb >= 108) break;
+    float v[16];
+    tmem_ld16(taddr + c0 + cb, v);
+#pragma unroll
+    for (int t = 0; t < 16; t += 4)
+      if (c0 + cb + t < 108)
+        *reinterpret_cast<float4*>(dst + c0 + cb + t) = make_float4(v[t], v[t + 1], v[t + 2], v[t + 3]);
+  }
+}
+
+// Sum of the outputs of every patch of the brick that holds region edge
+// (ri, rj, rk) of direction D (2, 4 or 8 patches: two along the edge, one or
+// two across per axis), read from ds.  Patch a covers region segments
+// [2a, 2a + 4) along its edges and nodes [2a, 2a + 2] across them; the local
+// index is the canonical numbering of the patch box (x: 4 x 3 x 3, y: 3 x 4 x
+// 3, z: 3 x 3 x 4).  *covered: some patch holds the edge.
+template <int D>
+__device__ __forceinline__ float gather_patches(const float* ds, int ri, int rj, int rk, bool* covered) {
+  const int r3[3] = {ri, rj, rk};
+  int P[3][2], np[3];
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    const int x = r3[ax];
+    if (ax == D) {                 // along the edge: segment x in [2a, 2a + 4)
+      P[ax][0] = (x >> 1) - 1;
+      P[ax][1] = x >> 1;
+      np[ax] = 2;
+    } else if (x & 1) {            // across, odd node: one patch
+      P[ax][0] = x >> 1;
+      P[ax][1] = -1;
+      np[ax] = 1;
+    } else {                       // across, even node: two patches
+      P[ax][0] = (x >> 1) - 1;
+      P[ax][1] = x >> 1;
+      np[ax] = 2;
+    }
+  }
+  constexpr int kDim[3] = {kBX, kBY, kBZ};
+  float s = 0.f;
+  bool any = false;
+#pragma unroll
+  for (int ic = 0; ic < 2; ++ic)
+#pragma unroll
+    for (int ib = 0; ib < 2; ++ib)
+#pragma unroll
+      for (int ia = 0; ia < 2; ++ia) {
+        const int a = P[0][ia], b = P[1][ib], c = P[2][ic];
+        const bool ok = ia < np[0] && ib < np[1] && ic < np[2] && (unsigned)a < (unsigned)kDim[0] &&
+                        (unsigned)b < (unsigned)kDim[1] && (unsigned)c < (unsigned)kDim[2];
+        const int li = ri - 2 * a, lj = rj - 2 * b, lk = rk - 2 * c;
+        const int l = D == 0 ? (lk * 3 + lj) * 4 + li : D == 1 ? 36 + (lk * 4 + lj) * 3 + li : 72 + (lk * 3 + lj) * 3 + li;
+        if (ok) {
+          s += ds[(a + kBX * (b + kBY * c)) * kDS + l];
+          any = true;
+        }
+      }
+  *covered = any;
+  return s;
+}
+
 template <bool FP16>
 __global__ void __launch_bounds__(kThreads, 3)
     k_tc_smoother(int n, const uint8_t* __restrict__ img, const float* __restrict__ AinvT, float eta,
@@ -333,7 +478,7 @@ __global__ void __launch_bounds__(kThreads, 3)
   z += (int64_t)rhs * 3 * N3;
 
   float* R = reinterpret_cast<float*>(smem + OFF_R);
-  float* ACC = reinterpret_cast<float*>(smem + OFF_ACC);
+  float* DS = reinterpret_cast<float*>(smem + OFF_A);  // D' once both products are done
   float* At = reinterpret_cast<float*>(smem + OFF_AT);
   const uint32_t bar0 = smem_u32(smem + OFF_BAR), bar1 = bar0 + 8;
   uint32_t* tm_slot = reinterpret_cast<uint32_t*>(smem + OFF_TM);
@@ -354,7 +499,9 @@ __global__ void __launch_bounds__(kThreads, 3)
   if (tid < 36) At[tid] = __ldg(AinvT + tid);
   {
     const uint32_t rbase = smem_u32(R);
-    auto stage = [&](int q, uint32_t off, bool in) { cp_async4(rbase + 4u * q, r + (in ? off : 0u), in ? 4u : 0u); };
+    auto stage = [&](uint32_t e, uint32_t off, bool in) {
+      cp_async4(rbase + 4u * (e & 8191u), r + (in ? off : 0u), in ? 4u : 0u);
+    };
     walk_region<0>(n, VX, VY, VZ, tid, stage);
     walk_region<1>(n, VX, VY, VZ, tid, stage);
     walk_region<2>(n, VX, VY, VZ, tid, stage);
@@ -402,37 +549,13 @@ __global__ void __launch_bounds__(kThreads, 3)
   // ---- 3. D = A W -------------------------------------------------------------
   if (tid == 0) {
     fence_after();
-    const uint32_t a0 = smem_u32(smem + OFF_A), b0 = smem_u32(smem + OFF_B1);
-    const uint32_t idesc = instr_desc(kM, kN1, FP16);
-#pragma unroll
-    for (int kk = 0; kk < kK1 / 16; ++kk)
-      mma_f16(tmem, smem_desc(a0 + kk * 256, 128, (kK1 / 8) * 128), smem_desc(b0 + kk * 256, 128, (kK1 / 8) * 128),
-              idesc, kk > 0);
-    mma_commit(bar0);
+    issue_mma1<FP16>(tmem, smem_u32(smem + OFF_A), smem_u32(smem + OFF_B1), bar0);
   }
   bool ok = mbar_wait(bar0, 0);
   fence_after();
 
   // ---- 4. A' = low-precision copy of D (8 warps: lane quadrant x column half)
-  if (ok) {
-    const int p = (warp & 3) * 32 + lane;
-    const int cb0 = (warp >> 2) * 32;
-    uint8_t* A2 = smem + OFF_A;
-#pragma unroll 1
-    for (int cb = cb0; cb < cb0 + 32; cb += 16) {
-      float v[16];
-      tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + cb, v);
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        uint4 w;
-        w.x = pack2<FP16>(v[8 * h + 0], v[8 * h + 1]);
-        w.y = pack2<FP16>(v[8 * h + 2], v[8 * h + 3]);
-        w.z = pack2<FP16>(v[8 * h + 4], v[8 * h + 5]);
-        w.w = pack2<FP16>(v[8 * h + 6], v[8 * h + 7]);
-        *reinterpret_cast<uint4*>(A2 + core_off(p, cb + 8 * h, kK2)) = w;
-      }
-    }
-  }
+  if (ok) convert_d<FP16>(tmem, smem + OFF_A, warp, lane);
   fence_async_smem();
   fence_before();
   __syncthreads();
@@ -440,54 +563,212 @@ __global__ void __launch_bounds__(kThreads, 3)
   // ---- 5. D' = A' W^t, written over D -----------------------------------------
   if (tid == 0 && ok) {
     fence_after();
-    const uint32_t a0 = smem_u32(smem + OFF_A), b0 = smem_u32(smem + OFF_B2);
-    const uint32_t idesc = instr_desc(kM, kN2, FP16);
-#pragma unroll
-    for (int kk = 0; kk < kK2 / 16; ++kk)
-      mma_f16(tmem, smem_desc(a0 + kk * 256, 128, (kK2 / 8) * 128), smem_desc(b0 + kk * 256, 128, (kK2 / 8) * 128),
-              idesc, kk > 0);
-    mma_commit(bar1);
+    issue_mma2<FP16>(tmem, smem_u32(smem + OFF_A), smem_u32(smem + OFF_B2), bar1);
   }
   if (ok) ok = mbar_wait(bar1, 0);
   fence_after();
-  // A' has been read by the tensor cores: its space becomes the accumulator;
-  // the CTA goes on only if every thread saw both products complete
-  for (int q = tid; q < kRegionAll; q += kThreads) ACC[q] = 0.f;
+  // the CTA goes on only if every thread saw both products complete; then A,
+  // A' and the W images are dead and D' takes their place
   ok = __syncthreads_and(ok) != 0;
 
-  // ---- 6. accumulate: patch outputs (rows of D') and interior-space solves ----
+  // ---- 6. D' to shared memory --------------------------------------------------
+  if (ok) stage_rows(tmem, DS, warp, lane);
+  else if (tid == 0) atomicExch(status, kTimeout);
+  fence_before();
+  __syncthreads();
+
+  // ---- 7. z += eta * (patch outputs + interior-space solves), per region edge --
+  // Each region edge gathers the outputs of the patches that hold it; an edge
+  // inside a coarse element the brick owns (E in [V0-1, V1-1] per axis, plus
+  // element nv on the last brick of an axis) also gets row t = 2d + (segment
+  // parity) of that element's interior solve.
   if (ok) {
-    const int prow = (warp & 3) * 32 + lane;
-    const int a = prow % kBX, b = (prow / kBX) % kBY, c = prow / (kBX * kBY);
-    const bool live = VX + a <= nv && VY + b <= nv && VZ + c <= nv;
     const float sc = wscale / rscale;
-    const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-    // tcgen05.ld is warp-collective: every lane loads, live rows add
-    const float scl = live ? sc : 0.f;
-    if (warp < 4) {
-      scatter16<0>(taddr, ACC, a, b, c, scl);
-      scatter16<16>(taddr, ACC, a, b, c, scl);
-      scatter16<32>(taddr, ACC, a, b, c, scl);
-      scatter16<48>(taddr, ACC, a, b, c, scl);
-    } else {
-      scatter16<64>(taddr, ACC, a, b, c, scl);
-      scatter16<80>(taddr, ACC, a, b, c, scl);
-      scatter16<96>(taddr, ACC, a, b, c, scl);
-    }
-  } else if (tid == 0) {
-    atomicExch(status, kTimeout);
+    const int ex1 = VX + kBX - 1 >= nv ? nv : VX + kBX - 2;
+    const int ey1 = VY + kBY - 1 >= nv ? nv : VY + kBY - 2;
+    const int ez1 = VZ + kBZ - 1 >= nv ? nv : VZ + kBZ - 2;
+    const int mx = ex1 - VX + 2, my = ey1 - VY + 2, mz = ez1 - VZ + 2;
+    auto bubble = [&](int d, int ri, int rj, int rk, float* v) {
+      const int al = d == 0 ? ri : d == 1 ? rj : rk;
+      const int x1 = d == 0 ? rj : ri, x2 = d == 2 ? rj : rk;  // the two across coordinates
+      if ((x1 | x2) & 1) return false;                        // not inside a coarse element
+      const int ei = ri >> 1, ej = rj >> 1, ek = rk >> 1;
+      if (ei >= mx || ej >= my || ek >= mz) return false;     // not owned
+      const int t = 2 * d + (al & 1);
+      float s = 0.f;
+#pragma unroll
+      for (int w = 0; w < 6; ++w) s += At[t * 6 + w] * R[bubble_elem(w, ei, ej, ek)];
+      *v = s;
+      return true;
+    };
+    auto visit = [&](auto dtag, uint32_t e, uint32_t off, bool in) {
+      constexpr int d = decltype(dtag)::value;
+      const int ri = (int)((e >> 13) & 31u), rj = (int)((e >> 18) & 15u), rk = (int)(e >> 22);
+      bool cov;
+      float v = gather_patches<d>(DS, ri, rj, rk, &cov) * sc;
+      float b;
+      const bool hb = bubble(d, ri, rj, rk, &b);
+      if (hb) v += b;
+      if (in && (cov || hb)) atomicAdd(z + off, eta * v);
+    };
+    walk_region<0>(n, VX, VY, VZ, tid, [&](uint32_t e, uint32_t off, bool in) {
+      visit(std::integral_constant<int, 0>(), e, off, in);
+    });
+    walk_region<1>(n, VX, VY, VZ, tid, [&](uint32_t e, uint32_t off, bool in) {
+      visit(std::integral_constant<int, 1>(), e, off, in);
+    });
+    walk_region<2>(n, VX, VY, VZ, tid, [&](uint32_t e, uint32_t off, bool in) {
+      visit(std::integral_constant<int, 2>(), e, off, in);
+    });
   }
-  // interior spaces of the coarse elements the brick owns: E in [V0-1, V1-1]
-  // per axis, plus element nv on the last brick of an axis (its last vertex
-  // is nv); the 6 interior edges of E are row t = 2d + (segment parity)
+  if (warp == 0) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+// The same smoother for a curl-curl coefficient constant per hexahedron:
+// the brick's patches fall into groups with their own Gram factors W_g
+// (host lists per brick: groups[off[b] .. off[b+1]) with 128-bit row masks).
+// A is gathered once; for each group the kernel loads W_g, forms D = A W_g
+// and D' = lowp(D) W_g^t, and adds only the rows of that group.  The interior
+// solves use the 6x6 inverse of each coarse element's group (Atab, 36 floats
+// per group, bub_gid per coarse element).
+template <bool FP16>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_tc_smoother_field(int n, const uint8_t* __restrict__ imgs, const float* __restrict__ Atab,
+                        const int* __restrict__ bub_gid, const int* __restrict__ goff, const int* __restrict__ ggrp,
+                        const uint4* __restrict__ gmask, float eta, const float* __restrict__ r,
+                        float* __restrict__ z, int* __restrict__ status) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  if (*reinterpret_cast<volatile int*>(status) != 0) return;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nv = n / 2 - 1, nc = n / 2;
+  const int nbx = (nv + kBX - 1) / kBX, nby = (nv + kBY - 1) / kBY, nbz = (nv + kBZ - 1) / kBZ;
+  const int nbr = nbx * nby * nbz;
+  const int rhs = blockIdx.x / nbr;
+  const int brick = blockIdx.x - rhs * nbr;
+  const int bx = brick % nbx, by = (brick / nbx) % nby, bz = brick / (nbx * nby);
+  const int VX = 1 + bx * kBX, VY = 1 + by * kBY, VZ = 1 + bz * kBZ;
+  const uint32_t n1 = n - 1, N3 = (uint32_t)n * n1 * n1;
+  r += (int64_t)rhs * 3 * N3;
+  z += (int64_t)rhs * 3 * N3;
+
+  float* R = reinterpret_cast<float*>(smem + OFF_R);
+  float* ACC = reinterpret_cast<float*>(smem + OFF_ACCF);
+  uint8_t* A2 = smem + OFF_A2F;
+  const uint32_t bar0 = smem_u32(smem + OFF_BAR), bar1 = bar0 + 8;
+  uint32_t* tm_slot = reinterpret_cast<uint32_t*>(smem + OFF_TM);
+  float* red = reinterpret_cast<float*>(smem + OFF_RED);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tm_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar0), "r"(1) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar1), "r"(1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  {
+    const uint32_t rbase = smem_u32(R);
+    auto stage = [&](uint32_t e, uint32_t off, bool in) {
+      cp_async4(rbase + 4u * (e & 8191u), r + (in ? off : 0u), in ? 4u : 0u);
+    };
+    walk_region<0>(n, VX, VY, VZ, tid, stage);
+    walk_region<1>(n, VX, VY, VZ, tid, stage);
+    walk_region<2>(n, VX, VY, VZ, tid, stage);
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+  }
+  for (int q = tid; q < kRegionAll; q += kThreads) ACC[q] = 0.f;
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tm_slot;
+
+  float rscale = 1.f;
+  if constexpr (FP16) {
+    float amax = 0.f;
+    for (int q = tid; q < kRegionAll; q += kThreads) amax = fmaxf(amax, fabsf(R[q]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if (lane == 0) red[warp] = amax;
+    __syncthreads();
+    float m = 0.f;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) m = fmaxf(m, red[w]);
+    if (m > 0.f) rscale = exp2f(-ceilf(log2f(m)));
+  }
+
+  {
+    const int p = tid & (kM - 1), half = tid >> 7;
+    const int a = p % kBX, b = (p / kBX) % kBY, c = p / (kBX * kBY);
+    const bool live = VX + a <= nv && VY + b <= nv && VZ + c <= nv;
+    uint8_t* A = smem + OFF_A;
+    if (half == 0)
+      gather_chunks<0, FP16>(R, A, p, a, b, c, live, rscale);
+    else
+      gather_chunks<7, FP16>(R, A, p, a, b, c, live, rscale);
+  }
+
+  // ---- one pass per group of patches in the brick ---------------------------
+  const int e0 = __ldg(goff + brick), e1 = __ldg(goff + brick + 1);
+  const int prow = (warp & 3) * 32 + lane;
+  const int pa = prow % kBX, pb = (prow / kBX) % kBY, pc = prow / (kBX * kBY);
+  const bool live = VX + pa <= nv && VY + pb <= nv && VZ + pc <= nv;
+  bool ok = true;
+  const uint32_t wbase = smem_u32(smem + OFF_B1);
+  for (int e = e0; e < e1 && ok; ++e) {
+    const uint32_t parity = (uint32_t)(e - e0) & 1u;
+    const uint8_t* img = imgs + (size_t)__ldg(ggrp + e) * kImgStride;
+    const uint4 mk = __ldg(gmask + e);
+    const uint32_t word = prow < 32 ? mk.x : prow < 64 ? mk.y : prow < 96 ? mk.z : mk.w;
+    const bool mine = live && ((word >> (prow & 31)) & 1u);
+    // W_g into B1 / B2 (the previous group's products have completed)
+    const uint4* src = reinterpret_cast<const uint4*>(img);
+    for (int q = tid; q < kImgBytes / 16; q += kThreads)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(wbase + 16u * q), "l"(src + q) : "memory");
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+    const float wscale = __ldg(reinterpret_cast<const float*>(img + kImgBytes));
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      fence_after();
+      issue_mma1<FP16>(tmem, smem_u32(smem + OFF_A), wbase, bar0);
+    }
+    bool okg = mbar_wait(bar0, parity);
+    fence_after();
+    if (okg) convert_d<FP16>(tmem, A2, warp, lane);
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    if (tid == 0 && okg) {
+      fence_after();
+      issue_mma2<FP16>(tmem, smem_u32(A2), smem_u32(smem + OFF_B2), bar1);
+    }
+    if (okg) okg = mbar_wait(bar1, parity);
+    fence_after();
+    ok = __syncthreads_and(okg) != 0;
+    if (ok) scatter_rows(tmem, ACC, warp, lane, mine ? wscale / rscale : 0.f);
+    fence_before();
+    __syncthreads();  // TMEM, A' and B are free for the next group
+    fence_after();
+  }
+  if (!ok && tid == 0) atomicExch(status, kTimeout);
+
+  // interior spaces of the coarse elements the brick owns (see k_tc_smoother)
   if (ok) {
     const int ex1 = VX + kBX - 1 >= nv ? nv : VX + kBX - 2;
     const int ey1 = VY + kBY - 1 >= nv ? nv : VY + kBY - 2;
     const int ez1 = VZ + kBZ - 1 >= nv ? nv : VZ + kBZ - 2;
     const int mx = ex1 - VX + 2, my = ey1 - VY + 2, mz = ez1 - VZ + 2;
-    for (int q = tid; q < mx * my * mz * 6; q += kThreads) {
-      const int t = q % 6, e = q / 6;
-      const int ei = e % mx, ej = (e / mx) % my, ek = e / (mx * my);  // E - (V0 - 1)
+    auto item = [&](int t, int ei, int ej, int ek) {
+      const int EI = VX - 1 + ei, EJ = VY - 1 + ej, EK = VZ - 1 + ek;  // coarse element
+      const float* At = Atab + 36 * (size_t)__ldg(bub_gid + ((size_t)EK * nc + EJ) * nc + EI);
       int idx[6];
 #pragma unroll
       for (int w = 0; w < 6; ++w) idx[w] = bubble_elem(w, ei, ej, ek);
@@ -495,19 +776,22 @@ __global__ void __launch_bounds__(kThreads, 3)
       int it = idx[0];
 #pragma unroll
       for (int w = 0; w < 6; ++w) {
-        s += At[t * 6 + w] * R[idx[w]];
+        s += __ldg(At + t * 6 + w) * R[idx[w]];
         if (w == t) it = idx[w];
       }
       atomicAdd(ACC + it, s);
+    };
+    for (int q = tid; q < mx * my * mz * 6; q += kThreads) {
+      const int e = q / 6;
+      item(q % 6, e % mx, (e / mx) % my, e / (mx * my));
     }
   }
   fence_before();
   __syncthreads();
 
-  // ---- 7. z += eta * accumulator ---------------------------------------------
   if (ok) {
-    auto flush = [&](int q, uint32_t off, bool in) {
-      if (in) atomicAdd(z + off, eta * ACC[q]);
+    auto flush = [&](uint32_t e, uint32_t off, bool in) {
+      if (in) atomicAdd(z + off, eta * ACC[e & 8191u]);
     };
     walk_region<0>(n, VX, VY, VZ, tid, flush);
     walk_region<1>(n, VX, VY, VZ, tid, flush);
@@ -521,12 +805,14 @@ __global__ void __launch_bounds__(kThreads, 3)
 
 }  // namespace
 
-cudaError_t upload_tc_operand(void** dst, const std::vector<double>& W, bool fp16) {
-  // W: 108 x 60 row-major.  Scale by a power of two so that max |W| <= 1.
+// image of one Gram factor W (108 x 60 row-major) at img (kImgStride bytes):
+// both operand layouts, scaled by a power of two so that max |W| <= 1, then
+// the float 1 / scale^2
+static void tc_image(const double* Wp, bool fp16, uint8_t* img) {
+  const std::vector<double> W(Wp, Wp + 108 * 60);
   double mx = 0.0;
   for (double v : W) mx = std::fmax(mx, std::fabs(v));
   const double sw = mx > 0 ? std::exp2(-std::ceil(std::log2(mx))) : 1.0;
-  std::vector<uint8_t> img(kImgBytes + 16, 0);
   auto put = [&](uint8_t* base, int row, int k, int K, double v) {
     uint16_t bits;
     if (fp16) {
@@ -538,8 +824,9 @@ cudaError_t upload_tc_operand(void** dst, const std::vector<double>& W, bool fp1
     }
     std::memcpy(base + core_off(row, k, K), &bits, 2);
   };
-  uint8_t* b1 = img.data();                    // B1[n][k] = W[k][n]: N = 64, K = 112
-  uint8_t* b2 = img.data() + kN1 * kK1 * 2;    // B2[n][k] = W[n][k]: N = 112, K = 64
+  std::memset(img, 0, kImgStride);
+  uint8_t* b1 = img;                           // B1[n][k] = W[k][n]: N = 64, K = 112
+  uint8_t* b2 = img + kN1 * kK1 * 2;           // B2[n][k] = W[n][k]: N = 112, K = 64
   for (int l = 0; l < 108; ++l)
     for (int c = 0; c < 60; ++c) {
       const double v = W[(size_t)l * 60 + c] * sw;
@@ -547,7 +834,71 @@ cudaError_t upload_tc_operand(void** dst, const std::vector<double>& W, bool fp1
       put(b2, l, c, kK2, v);
     }
   const float inv = (float)(1.0 / (sw * sw));
-  std::memcpy(img.data() + kImgBytes, &inv, sizeof(float));
+  std::memcpy(img + kImgBytes, &inv, sizeof(float));
+}
+
+// Largest eigenvalue of A_p W~ W~^t with W~ the operand image's rounded W
+// (scale included): 1 for the exact Gram factor (A_p W W^t is a projection),
+// larger as the rounding meets ill-conditioned patches.  Power iteration on
+// A_p^{1/2} W~ W~^t A_p^{1/2} (symmetric PSD) through y = W~ W~^t A_p x.
+double tc_operand_spectral_max(const double* Wp, const std::vector<double>& Ap, bool fp16) {
+  std::vector<uint8_t> img(kImgStride, 0);
+  tc_image(Wp, fp16, img.data());
+  float inv = 0.f;
+  std::memcpy(&inv, img.data() + kImgBytes, sizeof(float));
+  std::vector<double> Wr((size_t)108 * 60);
+  const uint8_t* b2 = img.data() + kN1 * kK1 * 2;  // B2[l][c] = W[l][c] (scaled)
+  for (int l = 0; l < 108; ++l)
+    for (int c = 0; c < 60; ++c) {
+      uint16_t bits;
+      std::memcpy(&bits, b2 + core_off(l, c, kK2), 2);
+      double v;
+      if (fp16) {
+        __half hv;
+        std::memcpy(&hv, &bits, 2);
+        v = (double)__half2float(hv);
+      } else {
+        __nv_bfloat16 bv;
+        std::memcpy(&bv, &bits, 2);
+        v = (double)__bfloat162float(bv);
+      }
+      Wr[(size_t)l * 60 + c] = v * std::sqrt((double)inv);
+    }
+  std::vector<double> x(108, 1.0), ax(108), t(60), y(108);
+  for (int l = 0; l < 108; ++l) x[l] = 1.0 + 0.01 * l;  // not orthogonal to the top eigenvector
+  double lam = 0.0;
+  for (int it = 0; it < 60; ++it) {
+    for (int a = 0; a < 108; ++a) {
+      double s = 0.0;
+      for (int b = 0; b < 108; ++b) s += Ap[(size_t)a * 108 + b] * x[b];
+      ax[a] = s;
+    }
+    for (int c = 0; c < 60; ++c) {
+      double s = 0.0;
+      for (int l = 0; l < 108; ++l) s += Wr[(size_t)l * 60 + c] * ax[l];
+      t[c] = s;
+    }
+    double num = 0.0, den = 0.0;
+    for (int l = 0; l < 108; ++l) {
+      double s = 0.0;
+      for (int c = 0; c < 60; ++c) s += Wr[(size_t)l * 60 + c] * t[c];
+      y[l] = s;
+      den += x[l] * ax[l];
+    }
+    for (int c = 0; c < 60; ++c) num += t[c] * t[c];  // x^t A W~ W~^t A x
+    lam = den > 0 ? num / den : 0.0;                   // Rayleigh quotient in the A_p inner product
+    double nrm = 0.0;
+    for (int l = 0; l < 108; ++l) nrm += y[l] * y[l];
+    nrm = std::sqrt(nrm);
+    if (!(nrm > 0)) break;
+    for (int l = 0; l < 108; ++l) x[l] = y[l] / nrm;
+  }
+  return lam;
+}
+
+cudaError_t upload_tc_operand(void** dst, const std::vector<double>& W, bool fp16) {
+  std::vector<uint8_t> img(kImgStride, 0);
+  tc_image(W.data(), fp16, img.data());
   if (!*dst) {
     cudaError_t e = cudaMalloc(dst, img.size());
     if (e != cudaSuccess) return e;
@@ -559,7 +910,58 @@ cudaError_t prepare_tc_patch() {
   cudaError_t e = cudaFuncSetAttribute(k_tc_smoother<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_tc_smoother<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tc_smoother_field<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemF);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tc_smoother_field<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemF);
   return e;
+}
+
+std::vector<uint8_t> tc_images(const std::vector<double>& W, int ngroups, bool fp16) {
+  std::vector<uint8_t> out((size_t)ngroups * kImgStride);
+  for (int q = 0; q < ngroups; ++q) tc_image(W.data() + (size_t)q * 108 * 60, fp16, out.data() + (size_t)q * kImgStride);
+  return out;
+}
+
+void tc_brick_groups(int n, const std::vector<int>& vgid, std::vector<int>* off, std::vector<int>* grp,
+                     std::vector<uint32_t>* mask) {
+  const int nv = n / 2 - 1;
+  const int nbx = (nv + kBX - 1) / kBX, nby = (nv + kBY - 1) / kBY, nbz = (nv + kBZ - 1) / kBZ;
+  off->assign(1, 0);
+  grp->clear();
+  mask->clear();
+  for (int bz = 0; bz < nbz; ++bz)
+    for (int by = 0; by < nby; ++by)
+      for (int bx = 0; bx < nbx; ++bx) {
+        const size_t first = grp->size();
+        for (int p = 0; p < kM; ++p) {
+          const int vx = 1 + bx * kBX + p % kBX, vy = 1 + by * kBY + (p / kBX) % kBY, vz = 1 + bz * kBZ + p / (kBX * kBY);
+          if (vx > nv || vy > nv || vz > nv) continue;
+          const int g = vgid[((size_t)(vz - 1) * nv + (vy - 1)) * nv + (vx - 1)];
+          size_t e = first;
+          while (e < grp->size() && (*grp)[e] != g) ++e;
+          if (e == grp->size()) {
+            grp->push_back(g);
+            mask->insert(mask->end(), 4, 0u);
+          }
+          (*mask)[4 * e + p / 32] |= 1u << (p % 32);
+        }
+        off->push_back((int)grp->size());
+      }
+}
+
+void launch_tc_smoother_field(cudaStream_t s, int n, const void* imgs, bool fp16, const float* Atab,
+                              const int* bub_gid, const int* goff, const int* ggrp, const uint4* gmask, double eta,
+                              const float* r, float* z, int* status, int R) {
+  const int nv = n / 2 - 1;
+  if (nv < 1) return;
+  const int grid = ((nv + kBX - 1) / kBX) * ((nv + kBY - 1) / kBY) * ((nv + kBZ - 1) / kBZ) * R;
+  if (fp16)
+    k_tc_smoother_field<true><<<grid, kThreads, kSmemF, s>>>(n, (const uint8_t*)imgs, Atab, bub_gid, goff, ggrp,
+                                                               gmask, (float)eta, r, z, status);
+  else
+    k_tc_smoother_field<false><<<grid, kThreads, kSmemF, s>>>(n, (const uint8_t*)imgs, Atab, bub_gid, goff, ggrp,
+                                                                gmask, (float)eta, r, z, status);
 }
 
 void launch_tc_smoother(cudaStream_t s, int n, const void* Wimg, bool fp16, const float* AinvT, double eta,
@@ -572,5 +974,6 @@ void launch_tc_smoother(cudaStream_t s, int n, const void* Wimg, bool fp16, cons
   else
     k_tc_smoother<false><<<grid, kThreads, kSmem, s>>>(n, (const uint8_t*)Wimg, AinvT, (float)eta, r, z, status);
 }
+
 
 }  // namespace ndmg

@@ -29,6 +29,27 @@ def random_target(n: int, seed: int = 1) -> np.ndarray:
     return np.random.default_rng(seed).uniform(-1.0, 1.0, num_edges(n))
 
 
+def checker_field(n: int, block: int, lo: float = 1.0, hi: float = 100.0) -> np.ndarray:
+    """Curl-curl coefficient per hexahedron: two materials in a checkerboard of
+    block^3-cell cubes (cell (i, j, k) at (k n + j) n + i)."""
+    k, j, i = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    return np.where(((i // block) + (j // block) + (k // block)) % 2 == 0, lo, hi).ravel().astype(float)
+
+
+def inclusion_field(n: int, lo: float = 1.0, hi: float = 100.0) -> np.ndarray:
+    """A cube of material hi (cells [n/4, 3n/4)^3) inside material lo."""
+    k, j, i = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    a, b = n // 4, 3 * n // 4
+    inside = (i >= a) & (i < b) & (j >= a) & (j < b) & (k >= a) & (k < b)
+    return np.where(inside, hi, lo).ravel().astype(float)
+
+
+def random_field(n: int, seed: int = 0, lo: float = 0.1, hi: float = 10.0) -> np.ndarray:
+    """Log-uniform coefficient in [lo, hi] drawn independently for every hexahedron."""
+    rng = np.random.default_rng(seed)
+    return np.exp(rng.uniform(np.log(lo), np.log(hi), n ** 3))
+
+
 def _edge_nodes(n: int):
     """Lattice coordinates (d, i, j, k) of every interior edge, canonical order."""
     parts = []

@@ -69,6 +69,8 @@ _SIGS = {
     "ndmg_counters": [_vp, _P(_i64), _P(_i64)],
     "ndmg_use_graphs": [_vp, _i32],
     "ndmg_dot_noalloc": [_i32, _vp, _vp, _i64, _P(_d), _vp],
+    "ndmg_set_alpha_field": [_vp, _vp],
+    "ndmg_grad_alpha_field": [_vp, _vp, _vp, _vp],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -117,6 +119,7 @@ class Solver:
         if st != OK:
             raise NdmgError(st, "ndmg_create failed")
         self.n, self.precision, self.nrhs, self.alpha = n, precision, nrhs, alpha
+        self.field = None                   # coefficient per hexahedron last set (CPU float64), if any
         lv = _i32()
         _lib.ndmg_num_levels(self._h, ctypes.byref(lv))
         self.num_levels = lv.value
@@ -156,6 +159,31 @@ class Solver:
     def set_alpha(self, alpha: float):
         self._check(_lib.ndmg_set_alpha(self._h, alpha), "set_alpha")
         self.alpha = alpha
+        self.field = None
+
+    def set_alpha_field(self, alpha_cells):
+        """Curl-curl coefficient per finest-level hexahedron (ndmg_set_alpha_field):
+        n^3 values, cell (i, j, k) at (k n + j) n + i (numpy array or CPU tensor)."""
+        a = torch.as_tensor(alpha_cells, dtype=torch.float64).detach().cpu().contiguous().reshape(-1)
+        if a.numel() != self.n ** 3:
+            raise ValueError(f"expected {self.n ** 3} cell coefficients, got {a.numel()}")
+        if self.field is not None and torch.equal(self.field, a):
+            return                          # the handle holds this field already
+        self._check(_lib.ndmg_set_alpha_field(self._h, a.data_ptr()), "set_alpha_field")
+        self.alpha = None
+        self.field = a.clone()
+
+    def grad_alpha_field(self, lam, u, out=None):
+        """-lambda_r^T K_T u_r for every finest-level cell T (ndmg_grad_alpha_field):
+        a float64 CUDA tensor of n^3 x nrhs values, queued on the handle's stream."""
+        if out is None:
+            out = torch.empty(self.n ** 3 * self.nrhs, dtype=torch.float64, device=lam.device)
+        if not out.is_cuda or out.dtype != torch.float64 or not out.is_contiguous() or \
+                out.numel() != self.n ** 3 * self.nrhs:
+            raise TypeError("expected a contiguous float64 CUDA tensor of n^3 x nrhs entries")
+        self._check(_lib.ndmg_grad_alpha_field(self._h, self._vec(lam, -1, torch.float64),
+                                               self._vec(u, -1, torch.float64), out.data_ptr()), "grad_alpha_field")
+        return out
 
     # -- level operations ---------------------------------------------------
     def apply(self, x, y, level: int = -1):

@@ -190,3 +190,23 @@ def test_graph_replay_matches_direct_launches(prec):
     assert a[1] * b[2] == b[1] * a[2]                  # launches per V-cycle
     assert a[3] * b[2] == b[3] * a[2] and abs(a[4] / a[3] - b[4] / b[3]) < 1e-9 * a[4] / a[3]
     assert np.linalg.norm(a[5] - b[5]) <= 1e-8 * np.linalg.norm(a[5])
+
+
+def test_bf16_rejects_operator_it_cannot_represent():
+    # alpha / (beta h^2) = 4.1e5 (alpha = 100 at 64^3): the bf16-rounded Gram
+    # factor gives A_p W~W~^t an eigenvalue of 22 instead of 1 and the solve
+    # diverged; the library refuses it at set-up and fp16 handles the case
+    with pytest.raises(ndmg.NdmgError) as e:
+        ndmg.Solver(64, n_coarsest=4, alpha=100.0, precision=ndmg.PREC_MIXED_BF16)
+    assert e.value.status == ndmg.INVALID_ARG
+    f = T(inputs.random_load(64, 0), torch.float64)
+    S = ndmg.Solver(64, n_coarsest=4, alpha=1.0, precision=ndmg.PREC_MIXED_BF16)
+    with pytest.raises(ndmg.NdmgError):
+        S.set_alpha(100.0)
+    u = torch.zeros_like(f)
+    st, it, rr = S.solve(f, u, tol=1e-8)          # still the alpha = 1 operators
+    assert rr <= 1e-8
+    S16 = ndmg.Solver(64, n_coarsest=4, alpha=100.0, precision=ndmg.PREC_MIXED_FP16)
+    u = torch.zeros_like(f)
+    st, it, rr = S16.solve(f, u, tol=1e-8)
+    assert rr <= 1e-8

@@ -90,3 +90,25 @@ def test_jumping_field_error_operator_spsd_and_contractive():
     assert np.allclose(AE, AE.T, atol=1e-9 * abs(AE).max())
     rho = mg.contraction_dense(H)
     assert (8 / 9) ** 2 - 1e-9 <= rho < 0.95
+
+
+def test_cell_gradient_finite_differences():
+    # dL/dalpha_T = -lambda^T K_T u against central differences of the loss
+    # (direct solves), and the weighted sum identity sum_T alpha_T g_T = -lambda^T K_alpha u
+    n = 4
+    rng = np.random.default_rng(3)
+    a = np.exp(rng.uniform(np.log(0.1), np.log(10.0), n ** 3))
+    N = hcurl.num_edges(n)
+    f, ut = rng.uniform(-1, 1, N), 0.1 * rng.uniform(-1, 1, N)
+    L0, g, u = mg.loss_and_grad_field(n, 1.0, a, 0.8, f, ut)
+    for cell in (0, 21, 42, 63):
+        eps = 1e-3 * a[cell]                   # O(eps^2) truncation ~1e-7 relative
+        ap, am = a.copy(), a.copy()
+        ap[cell] += eps
+        am[cell] -= eps
+        fd = (mg.loss_and_grad_field(n, 1.0, ap, 0.8, f, ut)[0] - mg.loss_and_grad_field(n, 1.0, am, 0.8, f, ut)[0]) / (2 * eps)
+        assert abs(fd - g[cell]) <= 1e-6 * max(abs(fd), 1e-3 * np.abs(g).max()), cell
+    lam = rng.standard_normal(N)
+    K = hcurl.assemble_field(n, 1.0, a, 0.0)
+    gc = mg.grad_cells(n, 1.0, lam, u)
+    assert abs(a @ gc + lam @ (K @ u)) < 1e-12 * (np.abs(lam) @ np.abs(K @ u))
