@@ -264,10 +264,10 @@ def whole_job_value(world: int, dofs: int, vcycles_per_step: float, steps: int, 
 # dram__bytes_write.sum, one ncu capture at 128^3, profiles/), valid only for
 # the kernel source it was measured on (sha256 prefix of the file)
 PROFILED_TRAFFIC = {
-    "patch": {"bytes": 49.649408e6 + 0.004608e6, "algorithmic": 12.0 * 6193536,
-              "source": "paper_2205_05840_gb300/csrc/tc_patch.cu", "sha256": "0e98633ca11c9211"},
-    "stencil": {"bytes": 49.562624e6 + 1.336064e6, "algorithmic": 12.0 * 6193536,
-                "source": "paper_2205_05840_gb300/csrc/kernels.cu", "sha256": "e934fffa53a0fa72"},
+    "patch": {"bytes": 49.649664e6 + 0.001024e6, "algorithmic": 12.0 * 6193536,
+              "source": "paper_2205_05840_gb300/csrc/tc_patch.cu", "sha256": "340110f913048f4f"},
+    "stencil": {"bytes": 49.5616e6 + 1.219072e6, "algorithmic": 12.0 * 6193536,
+                "source": "paper_2205_05840_gb300/csrc/kernels.cu", "sha256": "0c98e39698808b31"},
 }
 
 
@@ -297,6 +297,7 @@ def time_solves(ndmg, inputs, torch, dev, prec, alpha, nrhs, rank, reps=2):
     stream = torch.cuda.Stream(device=dev)
     S = ndmg.Solver(N_GRID, n_coarsest=N_COARSEST, alpha=alpha, m=M_SMOOTH, precision=prec, nrhs=nrhs,
                     stream=stream)
+    S.autotune()
     Nd = S.num_dofs()
     if nrhs == 1:
         f = torch.tensor(inputs.random_load(N_GRID, seed=rank), dtype=torch.float64, device=dev)
@@ -355,6 +356,7 @@ def run_ours(args):
                   ndmg.PREC_MIXED_FP16: "fp16-tc/f32+f64-refinement"}[prec]
     stream = torch.cuda.Stream(device=dev)
     S = ndmg.Solver(N_GRID, n_coarsest=N_COARSEST, alpha=ALPHA, m=M_SMOOTH, precision=prec, stream=stream)
+    tuned = S.autotune()                 # stencil z-planes per CTA, per level (untimed set-up)
     Nd = S.num_dofs()
     f = torch.tensor(inputs.random_load(N_GRID, seed=rank), dtype=torch.float64, device=dev)
     u = torch.zeros_like(f)
@@ -396,6 +398,7 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed")  # lets a profiler select the timed solves (ncu --nvtx-include timed/)
     with ClockSampler(local) as clk:
         for s in range(args.steps):
             with torch.cuda.stream(stream):
@@ -407,6 +410,7 @@ def run_ours(args):
                 ev[s][1].record(stream)
             iters.append((it, rr))
         torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     l1, v1 = S.counters()
     ms = [a.elapsed_time(b) for a, b in ev]
     ms_total = max_over_ranks(sum(ms), world, dev)
@@ -484,7 +488,11 @@ def run_ours(args):
                                       f"uniform load (seed=rank), PCG + V-cycle (vertex DD smoother, eta=1/9, "
                                       f"m={M_SMOOTH}, coarsest {N_COARSEST}^3) to {TOL:g}",
                           "n": N_GRID, "dofs": Nd, "tol": TOL, "l2": "flushed (256 MB write) between timed steps",
-                          "parallelism": f"replicas{world}"},
+                          "parallelism": f"replicas{world}",
+                          "autotuned": {str(N_COARSEST << k): {"stencil_planes_per_cta_f32": v[0],
+                                                               "stencil_planes_per_cta_f64": v[1],
+                                                               "tensor_core_smoother": bool(v[2])}
+                                        for k, v in tuned.items()}},
                "time_to_tol_ms": ms_total / args.steps, "vcycles_per_solve": vcyc_per_step,
                "pcg_iterations": iters[-1][0], "final_relres": iters[-1][1],
                "gpu_launches": launches, "roofline": roof, "kernels_one_solve": breakdown,

@@ -150,6 +150,21 @@ int ndmg_set_alpha_field(ndmg_t* h, const double* alpha_cells);
  * Asynchronous on the handle's stream.  Errors: INVALID_ARG, CUDA_ERROR. */
 int ndmg_grad_alpha_field(ndmg_t* h, const double* lambda, const double* u, double* out);
 
+/* Autotuner for the kernels' launch shapes (no counterpart in the paper):
+ * for every level and both vector types (float, double) it times the
+ * streaming stencil for each power-of-two number of z-planes per CTA (1 ..
+ * n_k; twenty launches each, CUDA events on the handle's stream, with the
+ * handle's nrhs) and keeps the fastest; every choice computes bitwise the same
+ * result.  On MIXED handles with the vertex smoother it also times, per level,
+ * the tensor-core smoother against the FP32 CUDA-core one (small levels have
+ * too few bricks of patches to fill the GPU) and keeps the faster; the FP32
+ * kernels are at least as accurate.  Synchronises the stream, overwrites the
+ * handle's solver workspaces and drops a captured V-cycle graph.  choices:
+ * NULL or a host array of 3 (K+1) ints, level-major: [3k] planes per CTA for
+ * float, [3k+1] for double, [3k+2] 1 if level k smooths on tensor cores.
+ * Errors: INVALID_ARG, CUDA_ERROR, DEVICE_TIMEOUT. */
+int ndmg_autotune(ndmg_t* h, int32_t* choices);
+
 /* Number of levels K+1. */
 int ndmg_num_levels(const ndmg_t* h, int32_t* out);
 
@@ -265,7 +280,9 @@ int ndmg_trace_enable(ndmg_t* h, int32_t kernel_class, int32_t on);
 /* Synchronise, then report and reset the class's totals since the last read:
  * launches, summed device time in ms, and summed algorithmic work: bytes a
  * launch must move to or from memory (every vector read or written once) for
- * the memory-bound classes, arithmetic operations (flops) for NDMG_K_PATCH. */
+ * the memory-bound classes; for NDMG_K_PATCH arithmetic operations (flops) on
+ * FP64 / FP32 handles and, on MIXED handles (memory-bound there), the
+ * smoother's 12 bytes per edge of float vectors (read r, read and write z). */
 int ndmg_trace_read(ndmg_t* h, int32_t kernel_class, int64_t* launches, double* ms, double* units);
 
 /* Running totals since ndmg_create: kernels launched by this handle (all

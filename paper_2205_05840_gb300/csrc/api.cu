@@ -155,10 +155,11 @@ const float* lv_a(DevLevel& L, float*) { return L.a32; }
 template <typename T>
 void stencil(ndmg_t* h, int k, double cK, double cM, const T* u, const T* g, T* y) {
   DevLevel& L = h->lv[k];
+  const int kz = L.kz[sizeof(T) == 8 ? 1 : 0];
   if (h->field)
-    launch_stencil_field<T>(h->stream, h->sm_count, L.n, cK, cM, u, g, y, nrhs(h), lv_a(L, (T*)nullptr));
+    launch_stencil_field<T>(h->stream, h->sm_count, L.n, cK, cM, u, g, y, nrhs(h), lv_a(L, (T*)nullptr), kz);
   else
-    launch_stencil<T>(h->stream, h->sm_count, L.n, cK, cM, u, g, y, nrhs(h), h->umax);
+    launch_stencil<T>(h->stream, h->sm_count, L.n, cK, cM, u, g, y, nrhs(h), h->umax, kz);
 }
 
 template <typename T>
@@ -238,7 +239,7 @@ void op_smoother_field(ndmg_t* h, int k, const T* r, T* z) {
   DevLevel& L = h->lv[k];
   const int R = nrhs(h);
   if constexpr (std::is_same<T, float>::value) {
-    if (mixed(h) && !edge_smoother(h) && L.Wtc_tab) {
+    if (mixed(h) && !edge_smoother(h) && L.Wtc_tab && L.tc) {
       Span sp(h, NDMG_K_PATCH, 12.0 * L.N * R);
       launch_tc_smoother_field(h->stream, L.n, L.Wtc_tab, h->o.precision == NDMG_PREC_MIXED_FP16, L.bubA32,
                                L.bub_gid, L.tc_off, L.tc_grp, L.tc_mask, h->o.eta, r, z, h->status, R);
@@ -259,7 +260,7 @@ void op_smoother_field(ndmg_t* h, int k, const T* r, T* z) {
     return;
   }
   const PatchFamily fam = vertex_family(L.n);
-  Span sp(h, NDMG_K_PATCH, num_patches(L.n) * 2.0 * 108 * 108 * R);
+  Span sp(h, NDMG_K_PATCH, mixed(h) && sizeof(T) == 4 ? 12.0 * L.N * R : num_patches(L.n) * 2.0 * 108 * 108 * R);
   launch_patch_grouped<T>(h->stream, h->sm_count, L.n, fam, grp_op(L.vtx, (T*)nullptr), L.vtx.chunks, L.vtx.nchunks,
                           L.vtx.plist, h->o.eta, r, z, R);
 }
@@ -308,7 +309,7 @@ void op_smoother<float>(ndmg_t* h, int k, const float* r, float* z) {
     op_edge_terms<float>(h, k, L.De32, r, z);
     return;
   }
-  if (mixed(h) && L.Wtc) {
+  if (mixed(h) && L.Wtc && L.tc) {
     // vertex patches on tensor cores (Gram form: two 108x60 products per
     // patch) and the interior 6x6 solves in one kernel.  Algorithmic bytes:
     // read r, read and write z (FP32); 25,920 flops per patch is ~86 flop/B,
@@ -322,7 +323,10 @@ void op_smoother<float>(ndmg_t* h, int k, const float* r, float* z) {
     Span sp(h, NDMG_K_BUBBLE, bubble_bytes(L.n, sizeof(float)) * R);
     launch_bubble<float>(h->stream, h->sm_count, L.n, L.AinvT32, h->o.eta, r, z, R);
   }
-  Span sp(h, NDMG_K_PATCH, num_patches(L.n) * 2.0 * 108 * 108 * R);
+  // MIXED handles (a level where the autotuner preferred these kernels) count
+  // the smoother's algorithmic bytes here, as for the tensor-core kernel;
+  // FP32 handles count flops
+  Span sp(h, NDMG_K_PATCH, mixed(h) ? 12.0 * L.N * R : num_patches(L.n) * 2.0 * 108 * 108 * R);
   launch_vertex_dense<float>(h->stream, h->sm_count, L.n, L.Dv32, h->o.eta, r, z, R);
 }
 
@@ -1233,6 +1237,86 @@ int ndmg_grad_alpha_field(ndmg_t* h, const double* lambda, const double* u, doub
   }
   NDMG_CK_LAUNCH();
   return NDMG_OK;
+}
+
+// launches timed per candidate (small levels run near the launch rate, where
+// a handful of launches is noise)
+constexpr int kTuneReps = 20;
+
+int ndmg_autotune(ndmg_t* h, int32_t* choices) {
+  if (!h) return NDMG_INVALID_ARG;
+  NDMG_CK(cudaStreamSynchronize(h->stream));
+  drop_graph(h);  // the graph holds the launch shapes
+  const int R = nrhs(h);
+  const int64_t NF = h->lv[h->K].N * R;
+  NDMG_CK(cudaMemsetAsync(h->w32[0], 0, sizeof(float) * NF, h->stream));
+  NDMG_CK(cudaMemsetAsync(h->w32[1], 0, sizeof(float) * NF, h->stream));
+  NDMG_CK(cudaMemsetAsync(h->w64[0], 0, sizeof(double) * NF, h->stream));
+  NDMG_CK(cudaMemsetAsync(h->w64[1], 0, sizeof(double) * NF, h->stream));
+  cudaEvent_t e0, e1;
+  NDMG_CK(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(h, NDMG_CUDA_ERROR, "cudaEventCreate");
+  }
+  int st = NDMG_OK;
+  for (int k = 0; k <= h->K && st == NDMG_OK; ++k) {
+    DevLevel& L = h->lv[k];
+    for (int t = 0; t < 2 && st == NDMG_OK; ++t) {
+      float best = 0.f;
+      int best_kz = 0;
+      for (int kz = 1; kz <= L.n && st == NDMG_OK; kz *= 2) {
+        L.kz[t] = kz;
+        auto run = [&] {
+          if (t == 0) stencil<float>(h, k, L.cK, L.cM, h->w32[0], h->w32[1], h->w32[2]);
+          else stencil<double>(h, k, L.cK, L.cM, h->w64[0], h->w64[1], h->w64[2]);
+        };
+        run();  // warm-up
+        run();
+        cudaEventRecord(e0, h->stream);
+        for (int rep = 0; rep < kTuneReps; ++rep) run();
+        cudaEventRecord(e1, h->stream);
+        float ms = 0.f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+          st = fail(h, NDMG_CUDA_ERROR, "autotune timing");
+          break;
+        }
+        if (best_kz == 0 || ms < best) {
+          best = ms;
+          best_kz = kz;
+        }
+      }
+      L.kz[t] = best_kz;
+      if (choices) choices[3 * k + t] = best_kz;
+    }
+  }
+  // MIXED modes, vertex smoother: tensor-core kernel or FP32 CUDA-core kernels
+  // per level (small levels have too few bricks to fill the GPU)
+  const bool tc_choice = mixed(h) && !edge_smoother(h) && h->o.subdomain == 2;
+  for (int k = 1; k <= h->K && st == NDMG_OK && tc_choice; ++k) {
+    DevLevel& L = h->lv[k];
+    float t_tc = 0.f, t_cc = 0.f;
+    for (int v = 0; v < 2 && st == NDMG_OK; ++v) {
+      L.tc = v == 0;
+      op_smoother<float>(h, k, h->w32[0], h->w32[1]);  // warm-up
+      cudaEventRecord(e0, h->stream);
+      for (int rep = 0; rep < kTuneReps; ++rep) op_smoother<float>(h, k, h->w32[0], h->w32[1]);
+      cudaEventRecord(e1, h->stream);
+      float ms = 0.f;
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        st = fail(h, NDMG_CUDA_ERROR, "autotune timing");
+        break;
+      }
+      (v == 0 ? t_tc : t_cc) = ms;
+    }
+    L.tc = !(t_cc < t_tc);
+  }
+  for (int k = 0; k <= h->K && choices; ++k) choices[3 * k + 2] = mixed(h) && k >= 1 && h->lv[k].tc ? 1 : 0;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st == NDMG_OK && cudaGetLastError() != cudaSuccess) st = fail(h, NDMG_CUDA_ERROR, "autotune launch");
+  if (st == NDMG_OK && mixed(h)) st = check_status(h);
+  return st;
 }
 
 int ndmg_num_levels(const ndmg_t* h, int32_t* out) {

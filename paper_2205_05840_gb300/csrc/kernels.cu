@@ -898,10 +898,7 @@ __device__ __forceinline__ void block_sum_store(double (&v)[NV], double* out) {
 
 // Batched BLAS-1: grid y (or x for the finishing kernel) is the right-hand
 // side; every right-hand side is a contiguous vector of N entries; scalars
-// come from per-right-hand-side device arrays.  The FP64 vector kernels move
-// two entries per access (16-byte loads; every right-hand side starts on a
-// 16-byte boundary when N is even, else the scalar path runs) so that enough
-// bytes are in flight to keep HBM busy.
+// come from per-right-hand-side device arrays.
 // partial[(rhs * gridDim.x + b) * 2 + {0,1}] = block sums of x.y and x2.y2
 template <typename T>
 __global__ void __launch_bounds__(256) k_dot2(int64_t N, const T* __restrict__ x, const T* __restrict__ y,
@@ -909,25 +906,7 @@ __global__ void __launch_bounds__(256) k_dot2(int64_t N, const T* __restrict__ x
                                               double* __restrict__ partial) {
   const int64_t off = (int64_t)blockIdx.y * N;
   double v[2] = {0.0, 0.0};
-  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
-  int64_t e0 = 0;
-  if constexpr (std::is_same<T, double>::value) if ((N & 1) == 0) {
-    const int64_t N2 = N / 2;
-    const double2* x_ = reinterpret_cast<const double2*>(x + off);
-    const double2* y_ = reinterpret_cast<const double2*>(y + off);
-    const double2* x2_ = reinterpret_cast<const double2*>(x2 ? x2 + off : x + off);
-    const double2* y2_ = reinterpret_cast<const double2*>(y2 ? y2 + off : y + off);
-    for (int64_t e = t0; e < N2; e += st) {
-      const double2 a = __ldg(x_ + e), b = __ldg(y_ + e);
-      v[0] += a.x * b.x + a.y * b.y;
-      if (x2) {
-        const double2 c = __ldg(x2_ + e), d = __ldg(y2_ + e);
-        v[1] += c.x * d.x + c.y * d.y;
-      }
-    }
-    e0 = N;
-  }
-  for (int64_t e = e0 + t0; e < N; e += st) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
     v[0] += (double)x[off + e] * (double)y[off + e];
     if (x2) v[1] += (double)x2[off + e] * (double)y2[off + e];
   }
@@ -985,29 +964,7 @@ __global__ void __launch_bounds__(256) k_cg_update_rr(int64_t N, const double* _
   const int64_t off = (int64_t)blockIdx.y * N;
   const double a = alpha[blockIdx.y], s = sto[blockIdx.y];
   double v[2] = {0.0, 0.0};
-  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
-  int64_t e0 = 0;
-  if ((N & 1) == 0) {
-    const double2* p_ = reinterpret_cast<const double2*>(p + off);
-    const double2* q_ = reinterpret_cast<const double2*>(q + off);
-    double2* u_ = reinterpret_cast<double2*>(u + off);
-    double2* r_ = reinterpret_cast<double2*>(r + off);
-    float2* g_ = reinterpret_cast<float2*>(g32 + off);
-    for (int64_t e = t0; e < N / 2; e += st) {
-      const double2 pv = __ldg(p_ + e), qv = __ldg(q_ + e);
-      double2 uv = u_[e], rv = r_[e];
-      uv.x += a * pv.x;
-      uv.y += a * pv.y;
-      rv.x -= a * qv.x;
-      rv.y -= a * qv.y;
-      u_[e] = uv;
-      r_[e] = rv;
-      g_[e] = make_float2((float)(s * rv.x), (float)(s * rv.y));
-      v[0] += rv.x * rv.x + rv.y * rv.y;
-    }
-    e0 = N;
-  }
-  for (int64_t e = e0 + t0; e < N; e += st) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
     u[off + e] += a * p[off + e];
     const double rn = r[off + e] - a * q[off + e];
     r[off + e] = rn;
@@ -1025,22 +982,7 @@ __global__ void __launch_bounds__(256) k_dot2_zf(int64_t N, const double* __rest
   const int64_t off = (int64_t)blockIdx.y * N;
   const double s = sc[blockIdx.y];
   double v[2] = {0.0, 0.0};
-  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
-  int64_t e0 = 0;
-  if ((N & 1) == 0) {
-    const double2* x_ = reinterpret_cast<const double2*>(x + off);
-    const double2* y_ = reinterpret_cast<const double2*>(y + off);
-    const float2* z_ = reinterpret_cast<const float2*>(z32 + off);
-    for (int64_t e = t0; e < N / 2; e += st) {
-      const double2 a = __ldg(x_ + e), b = __ldg(y_ + e);
-      const float2 zf = __ldg(z_ + e);
-      const double z0 = s * (double)zf.x, z1 = s * (double)zf.y;
-      v[0] += a.x * z0 + a.y * z1;
-      v[1] += b.x * z0 + b.y * z1;
-    }
-    e0 = N;
-  }
-  for (int64_t e = e0 + t0; e < N; e += st) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
     const double z = s * (double)z32[off + e];
     v[0] += x[off + e] * z;
     v[1] += y[off + e] * z;
@@ -1053,21 +995,8 @@ __global__ void __launch_bounds__(256) k_axpby_zf(int64_t N, const double* __res
                                                   const double* __restrict__ ab, double* __restrict__ p) {
   const int64_t off = (int64_t)blockIdx.y * N;
   const double s = sc[blockIdx.y], b = ab[2 * blockIdx.y + 1];
-  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
-  int64_t e0 = 0;
-  if ((N & 1) == 0) {
-    const float2* z_ = reinterpret_cast<const float2*>(z32 + off);
-    double2* p_ = reinterpret_cast<double2*>(p + off);
-    for (int64_t e = t0; e < N / 2; e += st) {
-      const float2 zf = __ldg(z_ + e);
-      double2 pv = p_[e];
-      pv.x = s * (double)zf.x + b * pv.x;
-      pv.y = s * (double)zf.y + b * pv.y;
-      p_[e] = pv;
-    }
-    e0 = N;
-  }
-  for (int64_t e = e0 + t0; e < N; e += st) p[off + e] = s * (double)z32[off + e] + b * p[off + e];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x)
+    p[off + e] = s * (double)z32[off + e] + b * p[off + e];
 }
 
 // dst (float) = s * src (double), s = sc[rhs]
@@ -1123,17 +1052,19 @@ cudaError_t prepare_stencil() {
 
 // z chunk: the longest (fewest halo planes) that still gives about four
 // CTAs per SM
-static inline dim3 stencil_grid(int n, int sm, int R, int* KZ) {
+// (kz > 0: the chunk length chosen by ndmg_autotune)
+static inline dim3 stencil_grid(int n, int sm, int R, int* KZ, int kz_choice) {
   const int64_t cols = (int64_t)((n + kTX - 1) / kTX) * ((n + kTY - 1) / kTY) * R;
   int kz = n;
   while (kz > 2 && cols * ((n + kz - 1) / kz) < 4LL * sm) kz = (kz + 1) / 2;
+  if (kz_choice > 0) kz = kz_choice < n ? kz_choice : n;
   *KZ = kz;
   return dim3((n + kTX - 1) / kTX, (n + kTY - 1) / kTY, ((n + kz - 1) / kz) * R);
 }
 
 template <typename T>
 void launch_stencil(cudaStream_t s, int sm, int n, double cK, double cM, const T* u, const T* g, T* y, int R,
-                    unsigned long long* umax) {
+                    unsigned long long* umax, int kz) {
   const int64_t N = 3LL * n * (n - 1) * (n - 1);
   if (N == 0) return;
   if constexpr (std::is_same<T, double>::value) {
@@ -1141,7 +1072,7 @@ void launch_stencil(cudaStream_t s, int sm, int n, double cK, double cM, const T
     k_absmax<<<dim3(grid_for(N, sm, 4), R), 256, 0, s>>>(N, u, umax);
   }
   int KZ = 0;
-  const dim3 grid = stencil_grid(n, sm, R, &KZ);
+  const dim3 grid = stencil_grid(n, sm, R, &KZ, kz);
   k_stencil_stream<T, StencilArith<T>>
       <<<grid, dim3(kTX, kTY), stencil_smem<T>(), s>>>(n, KZ, (T)cK, (T)cM, u, g, y, umax);
 }
@@ -1158,10 +1089,10 @@ cudaError_t prepare_stencil_field() {
 
 template <typename T>
 void launch_stencil_field(cudaStream_t s, int sm, int n, double cK, double cM, const T* u, const T* g, T* y, int R,
-                          const T* acell) {
+                          const T* acell, int kz) {
   if (n < 2) return;
   int KZ = 0;
-  const dim3 grid = stencil_grid(n, sm, R, &KZ);
+  const dim3 grid = stencil_grid(n, sm, R, &KZ, kz);
   k_stencil_stream<T, T, true>
       <<<grid, dim3(kTX, kTY), stencil_field_smem<T>(), s>>>(n, KZ, (T)cK, (T)cM, u, g, y, nullptr, acell);
 }
@@ -1277,7 +1208,7 @@ void launch_coarse(cudaStream_t s, int N0, const double* Ainv, const T* g, T* z,
   k_coarse<T><<<dim3((N0 + 7) / 8, R), 256, sizeof(double) * N0, s>>>(N0, Ainv, g, z);
 }
 
-int reduction_blocks(int sm) { return sm * 8; }
+int reduction_blocks(int sm) { return sm * 4; }
 
 template <typename T>
 void launch_dot2(cudaStream_t s, int sm, int64_t N, const T* x, const T* y, const T* x2, const T* y2, double* partial,
@@ -1376,11 +1307,11 @@ void launch_grad_cells(cudaStream_t s, int sm, int n, double h, const double* la
 
 #define NDMG_INST(T)                                                                                   \
   template void launch_stencil<T>(cudaStream_t, int, int, double, double, const T*, const T*, T*, int,    \
-                                  unsigned long long*);                                               \
+                                  unsigned long long*, int);                                          \
   template cudaError_t prepare_stencil<T>();                                                          \
   template cudaError_t prepare_stencil_field<T>();                                                    \
   template void launch_stencil_field<T>(cudaStream_t, int, int, double, double, const T*, const T*, T*, int, \
-                                        const T*);                                                    \
+                                        const T*, int);                                               \
   template void launch_bubble_grouped<T>(cudaStream_t, int, int, const T*, const int*, double, const T*, T*, int); \
   template cudaError_t prepare_patch_grouped<T>();                                                    \
   template void launch_patch_grouped<T>(cudaStream_t, int, int, const PatchFamily&, const T*, const int4*, int, \

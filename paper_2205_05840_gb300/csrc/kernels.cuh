@@ -7,10 +7,11 @@ namespace ndmg {
 
 // y = g - (cK K + cM M) u, or (cK K + cM M) u when g is null (cK = alpha h,
 // cM = beta h^3 for A_k).  For double vectors the operator runs in exact
-// fixed point; umax is R words of device scratch for its scale.
+// fixed point; umax is R words of device scratch for its scale.  kz: planes
+// per CTA along z (0 = the built-in choice; any value gives the same result).
 template <typename T>
 void launch_stencil(cudaStream_t s, int sm, int n, double cK, double cM, const T* u, const T* g, T* y, int R,
-                    unsigned long long* umax);
+                    unsigned long long* umax, int kz = 0);
 template <typename T>
 cudaError_t prepare_stencil();
 template <typename T>
@@ -57,7 +58,7 @@ template <typename T>
 cudaError_t prepare_stencil_field();
 template <typename T>
 void launch_stencil_field(cudaStream_t s, int sm, int n, double cK, double cM, const T* u, const T* g, T* y, int R,
-                          const T* acell);
+                          const T* acell, int kz = 0);
 template <typename T>
 void launch_bubble_grouped(cudaStream_t s, int sm, int n, const T* Atab, const int* gid, double eta, const T* r, T* z,
                            int R);

@@ -106,6 +106,9 @@ struct DevLevel {
   int n;
   int64_t N;                  // edges on this level
   double h, cK, cM;           // alpha*h, beta*h^3
+  int kz[2] = {0, 0};         // stencil planes per CTA for float / double vectors (ndmg_autotune; 0 = built-in)
+  bool tc = true;             // MIXED modes: vertex patches on tensor cores on this level (ndmg_autotune may
+                              // pick the FP32 CUDA-core kernels where they finish sooner)
   // FP64 workspaces (coarse levels) and FP32 workspaces
   double *g64 = nullptr, *z64 = nullptr, *r64 = nullptr;
   float *g32 = nullptr, *z32 = nullptr, *r32 = nullptr;

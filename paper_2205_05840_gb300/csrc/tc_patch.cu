@@ -136,7 +136,8 @@ __device__ __forceinline__ void walk_region(int n, int VX, int VY, int VZ, int t
   }
 }
 
-// shared memory: A' aliases A (A is dead once the first MMA completed)
+// shared memory: A' aliases A (A is dead once the first MMA completed), and
+// the region accumulator aliases A' once both products are complete
 constexpr int OFF_A = 0;
 constexpr int OFF_B1 = OFF_A + kM * kK1 * 2;  // W images, contiguous
 constexpr int OFF_B2 = OFF_B1 + kN1 * kK1 * 2;
@@ -146,6 +147,7 @@ constexpr int OFF_TM = OFF_BAR + 16;
 constexpr int OFF_RED = OFF_TM + 16;
 constexpr int OFF_AT = OFF_RED + 32;          // A_T^{-1} (6 x 6, FP32)
 constexpr int kSmem = OFF_AT + 36 * 4;
+static_assert(kRegionAll * 4 <= kM * kK1 * 2, "accumulator fits in the A operand");
 static_assert(OFF_BAR % 8 == 0, "mbarrier alignment");
 static_assert(3 * (kSmem + 1024) <= 228 * 1024, "three CTAs per SM (228 KB, 1 KB reserved per CTA)");
 
@@ -382,80 +384,6 @@ __device__ __forceinline__ void scatter_rows(uint32_t tmem, float* acc, int warp
   }
 }
 
-// D' in shared memory for the gather below: row p (patch) at p * kDS, its 108
-// outputs contiguous (a row stride of 108 floats keeps the 16-byte stores of a
-// warp's 32 rows spread over all banks)
-constexpr int kDS = 108;
-static_assert(kM * kDS * 4 <= OFF_R - OFF_A, "D' fits over A and the W images");
-
-// this warp's rows (lane quadrant) and column half of D' from TMEM to ds
-__device__ __forceinline__ void stage_rows(uint32_t tmem, float* ds, int warp, int lane) {
-  const int prow = (warp & 3) * 32 + lane;
-  const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-  float* dst = ds + prow * kDS;
-  const int c0 = (warp >> 2) * 64;  // warp-uniform: columns [0, 64) or [64, 108)
-#pragma unroll
-  for (int cb = 0; cb < 64; cb += 16) {
-    if (c0 + cb >= 108) break;
-    float v[16];
-    tmem_ld16(taddr + c0 + cb, v);
-#pragma unroll
-    for (int t = 0; t < 16; t += 4)
-      if (c0 + cb + t < 108)
-        *reinterpret_cast<float4*>(dst + c0 + cb + t) = make_float4(v[t], v[t + 1], v[t + 2], v[t + 3]);
-  }
-}
-
-// Sum of the outputs of every patch of the brick that holds region edge
-// (ri, rj, rk) of direction D (2, 4 or 8 patches: two along the edge, one or
-// two across per axis), read from ds.  Patch a covers region segments
-// [2a, 2a + 4) along its edges and nodes [2a, 2a + 2] across them; the local
-// index is the canonical numbering of the patch box (x: 4 x 3 x 3, y: 3 x 4 x
-// 3, z: 3 x 3 x 4).  *covered: some patch holds the edge.
-template <int D>
-__device__ __forceinline__ float gather_patches(const float* ds, int ri, int rj, int rk, bool* covered) {
-  const int r3[3] = {ri, rj, rk};
-  int P[3][2], np[3];
-#pragma unroll
-  for (int ax = 0; ax < 3; ++ax) {
-    const int x = r3[ax];
-    if (ax == D) {                 // along the edge: segment x in [2a, 2a + 4)
-      P[ax][0] = (x >> 1) - 1;
-      P[ax][1] = x >> 1;
-      np[ax] = 2;
-    } else if (x & 1) {            // across, odd node: one patch
-      P[ax][0] = x >> 1;
-      P[ax][1] = -1;
-      np[ax] = 1;
-    } else {                       // across, even node: two patches
-      P[ax][0] = (x >> 1) - 1;
-      P[ax][1] = x >> 1;
-      np[ax] = 2;
-    }
-  }
-  constexpr int kDim[3] = {kBX, kBY, kBZ};
-  float s = 0.f;
-  bool any = false;
-#pragma unroll
-  for (int ic = 0; ic < 2; ++ic)
-#pragma unroll
-    for (int ib = 0; ib < 2; ++ib)
-#pragma unroll
-      for (int ia = 0; ia < 2; ++ia) {
-        const int a = P[0][ia], b = P[1][ib], c = P[2][ic];
-        const bool ok = ia < np[0] && ib < np[1] && ic < np[2] && (unsigned)a < (unsigned)kDim[0] &&
-                        (unsigned)b < (unsigned)kDim[1] && (unsigned)c < (unsigned)kDim[2];
-        const int li = ri - 2 * a, lj = rj - 2 * b, lk = rk - 2 * c;
-        const int l = D == 0 ? (lk * 3 + lj) * 4 + li : D == 1 ? 36 + (lk * 4 + lj) * 3 + li : 72 + (lk * 3 + lj) * 3 + li;
-        if (ok) {
-          s += ds[(a + kBX * (b + kBY * c)) * kDS + l];
-          any = true;
-        }
-      }
-  *covered = any;
-  return s;
-}
-
 template <bool FP16>
 __global__ void __launch_bounds__(kThreads, 3)
     k_tc_smoother(int n, const uint8_t* __restrict__ img, const float* __restrict__ AinvT, float eta,
@@ -478,7 +406,7 @@ __global__ void __launch_bounds__(kThreads, 3)
   z += (int64_t)rhs * 3 * N3;
 
   float* R = reinterpret_cast<float*>(smem + OFF_R);
-  float* DS = reinterpret_cast<float*>(smem + OFF_A);  // D' once both products are done
+  float* ACC = reinterpret_cast<float*>(smem + OFF_A);  // region accumulator, over A' once D' is complete
   float* At = reinterpret_cast<float*>(smem + OFF_AT);
   const uint32_t bar0 = smem_u32(smem + OFF_BAR), bar1 = bar0 + 8;
   uint32_t* tm_slot = reinterpret_cast<uint32_t*>(smem + OFF_TM);
@@ -567,59 +495,55 @@ __global__ void __launch_bounds__(kThreads, 3)
   }
   if (ok) ok = mbar_wait(bar1, 0);
   fence_after();
-  // the CTA goes on only if every thread saw both products complete; then A,
-  // A' and the W images are dead and D' takes their place
+  // A' has been read by the tensor cores: its space becomes the accumulator;
+  // the CTA goes on only if every thread saw both products complete
+  for (int q = tid; q < kRegionAll; q += kThreads) ACC[q] = 0.f;
   ok = __syncthreads_and(ok) != 0;
 
-  // ---- 6. D' to shared memory --------------------------------------------------
-  if (ok) stage_rows(tmem, DS, warp, lane);
-  else if (tid == 0) atomicExch(status, kTimeout);
-  fence_before();
-  __syncthreads();
-
-  // ---- 7. z += eta * (patch outputs + interior-space solves), per region edge --
-  // Each region edge gathers the outputs of the patches that hold it; an edge
-  // inside a coarse element the brick owns (E in [V0-1, V1-1] per axis, plus
-  // element nv on the last brick of an axis) also gets row t = 2d + (segment
-  // parity) of that element's interior solve.
+  // ---- 6. accumulate: patch outputs (rows of D') and interior-space solves ----
   if (ok) {
-    const float sc = wscale / rscale;
+    const int prow = (warp & 3) * 32 + lane;
+    const int a = prow % kBX, b = (prow / kBX) % kBY, c = prow / (kBX * kBY);
+    const bool live = VX + a <= nv && VY + b <= nv && VZ + c <= nv;
+    scatter_rows(tmem, ACC, warp, lane, live ? wscale / rscale : 0.f);  // live rows add
+  } else if (tid == 0) {
+    atomicExch(status, kTimeout);
+  }
+  // interior spaces of the coarse elements the brick owns: E in [V0-1, V1-1]
+  // per axis, plus element nv on the last brick of an axis (its last vertex
+  // is nv); the 6 interior edges of E are row t = 2d + (segment parity)
+  if (ok) {
     const int ex1 = VX + kBX - 1 >= nv ? nv : VX + kBX - 2;
     const int ey1 = VY + kBY - 1 >= nv ? nv : VY + kBY - 2;
     const int ez1 = VZ + kBZ - 1 >= nv ? nv : VZ + kBZ - 2;
     const int mx = ex1 - VX + 2, my = ey1 - VY + 2, mz = ez1 - VZ + 2;
-    auto bubble = [&](int d, int ri, int rj, int rk, float* v) {
-      const int al = d == 0 ? ri : d == 1 ? rj : rk;
-      const int x1 = d == 0 ? rj : ri, x2 = d == 2 ? rj : rk;  // the two across coordinates
-      if ((x1 | x2) & 1) return false;                        // not inside a coarse element
-      const int ei = ri >> 1, ej = rj >> 1, ek = rk >> 1;
-      if (ei >= mx || ej >= my || ek >= mz) return false;     // not owned
-      const int t = 2 * d + (al & 1);
-      float s = 0.f;
+    for (int q = tid; q < mx * my * mz * 6; q += kThreads) {
+      const int t = q % 6, e = q / 6;
+      const int ei = e % mx, ej = (e / mx) % my, ek = e / (mx * my);  // E - (V0 - 1)
+      int idx[6];
 #pragma unroll
-      for (int w = 0; w < 6; ++w) s += At[t * 6 + w] * R[bubble_elem(w, ei, ej, ek)];
-      *v = s;
-      return true;
+      for (int w = 0; w < 6; ++w) idx[w] = bubble_elem(w, ei, ej, ek);
+      float s = 0.f;
+      int it = idx[0];
+#pragma unroll
+      for (int w = 0; w < 6; ++w) {
+        s += At[t * 6 + w] * R[idx[w]];
+        if (w == t) it = idx[w];
+      }
+      atomicAdd(ACC + it, s);
+    }
+  }
+  fence_before();
+  __syncthreads();
+
+  // ---- 7. z += eta * accumulator ---------------------------------------------
+  if (ok) {
+    auto flush = [&](uint32_t e, uint32_t off, bool in) {
+      if (in) atomicAdd(z + off, eta * ACC[e & 8191u]);
     };
-    auto visit = [&](auto dtag, uint32_t e, uint32_t off, bool in) {
-      constexpr int d = decltype(dtag)::value;
-      const int ri = (int)((e >> 13) & 31u), rj = (int)((e >> 18) & 15u), rk = (int)(e >> 22);
-      bool cov;
-      float v = gather_patches<d>(DS, ri, rj, rk, &cov) * sc;
-      float b;
-      const bool hb = bubble(d, ri, rj, rk, &b);
-      if (hb) v += b;
-      if (in && (cov || hb)) atomicAdd(z + off, eta * v);
-    };
-    walk_region<0>(n, VX, VY, VZ, tid, [&](uint32_t e, uint32_t off, bool in) {
-      visit(std::integral_constant<int, 0>(), e, off, in);
-    });
-    walk_region<1>(n, VX, VY, VZ, tid, [&](uint32_t e, uint32_t off, bool in) {
-      visit(std::integral_constant<int, 1>(), e, off, in);
-    });
-    walk_region<2>(n, VX, VY, VZ, tid, [&](uint32_t e, uint32_t off, bool in) {
-      visit(std::integral_constant<int, 2>(), e, off, in);
-    });
+    walk_region<0>(n, VX, VY, VZ, tid, flush);
+    walk_region<1>(n, VX, VY, VZ, tid, flush);
+    walk_region<2>(n, VX, VY, VZ, tid, flush);
   }
   if (warp == 0) {
     fence_after();

@@ -70,6 +70,7 @@ _SIGS = {
     "ndmg_use_graphs": [_vp, _i32],
     "ndmg_dot_noalloc": [_i32, _vp, _vp, _i64, _P(_d), _vp],
     "ndmg_set_alpha_field": [_vp, _vp],
+    "ndmg_autotune": [_vp, _P(_i32)],
     "ndmg_grad_alpha_field": [_vp, _vp, _vp, _vp],
 }
 for _name, _args in _SIGS.items():
@@ -290,6 +291,13 @@ class Solver:
         self._check(_lib.ndmg_trace_read(self._h, kernel_class, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(u)),
                     "trace_read")
         return n.value, ms.value, u.value
+
+    def autotune(self):
+        """Pick launch shapes by timing (ndmg_autotune); returns {level:
+        (stencil planes per CTA for float, for double, tensor-core smoother 0/1)}."""
+        out = (_i32 * (3 * self.num_levels))()
+        self._check(_lib.ndmg_autotune(self._h, out), "autotune")
+        return {k: (out[3 * k], out[3 * k + 1], out[3 * k + 2]) for k in range(self.num_levels)}
 
     def use_graphs(self, on: bool = True):
         """Replay the mixed-precision V-cycle as a CUDA graph (ndmg_use_graphs)."""

@@ -210,3 +210,43 @@ def test_bf16_rejects_operator_it_cannot_represent():
     u = torch.zeros_like(f)
     st, it, rr = S16.solve(f, u, tol=1e-8)
     assert rr <= 1e-8
+
+
+def test_autotune_changes_launch_shapes_not_results():
+    # ndmg_autotune picks the stencil's z-planes per CTA per level by timing;
+    # every choice computes the same values, bit for bit
+    n = 64
+    S = ndmg.Solver(n, n_coarsest=4, precision=ndmg.PREC_MIXED_FP16)
+    rng = np.random.default_rng(5)
+    res = {}
+    for dt in (torch.float32, torch.float64):
+        for lv in range(S.num_levels):
+            Nl = S.num_dofs(lv)
+            x, g = T(rng.standard_normal(Nl), dt), T(rng.standard_normal(Nl), dt)
+            r = torch.empty_like(x)
+            S.residual(g, x, r, level=lv)
+            res[(dt, lv)] = (x, g, N(r))
+    f = T(inputs.random_load(n, 0), torch.float64)
+    u = torch.zeros_like(f)
+    _, it0, _ = S.solve(f, u, tol=1e-8)
+    choices = S.autotune()
+    assert set(choices) == set(range(S.num_levels))
+    for lv, (cf, cd, tc) in choices.items():
+        nl = 4 << lv
+        for c in (cf, cd):
+            assert c >= 1 and c <= nl and (c & (c - 1)) == 0
+        assert tc in (0, 1) and (lv > 0 or tc == 0)
+    for (dt, lv), (x, g, r0) in res.items():
+        r = torch.empty_like(x)
+        S.residual(g, x, r, level=lv)
+        assert np.array_equal(N(r), r0), (dt, lv)
+    u = torch.zeros_like(f)
+    _, it1, rr = S.solve(f, u, tol=1e-8)
+    assert rr <= 1e-8 and abs(it1 - it0) <= 2
+    # whatever smoother each level got, one smoothing step still matches the oracle
+    A = hcurl.assemble(n, 1.0, 1.0, 1.0)
+    Sm = mg.Smoother(A, n, "vertex")
+    g = rng.standard_normal(A.shape[0]).astype(np.float32).astype(np.float64)
+    zt = torch.zeros(A.shape[0], dtype=torch.float32, device=DEV)
+    S.smooth(T(g), zt, steps=1)
+    assert rel(N(zt), Sm.apply(g)) < 16 * U["fp16"]
