@@ -104,8 +104,11 @@ int ndmg_opts_default(ndmg_opts* o);
  * dense 108x108 matrix and as a Gram factor W (108x60, W W^t = the same
  * operator), and the coarsest inverse A_0^{-1} (Fig. 1, k = 0).  Allocates all
  * device workspaces.  *out receives the handle (NULL on failure).  Errors:
- * INVALID_ARG (bad sizes, alpha/beta/L <= 0, nrhs < 1, unsupported smoother),
- * OUT_OF_MEMORY, CUDA_ERROR. */
+ * INVALID_ARG (bad sizes, alpha/beta/L <= 0, nrhs < 1, unsupported smoother;
+ * MIXED precision whose rounded Gram factor W~ cannot carry the vertex-patch
+ * operator: largest eigenvalue of A_p W~W~^t above 16, which bf16 operands reach
+ * near alpha / (beta h^2) = 2.8e5 and fp16 ones near 2.5e7 -- the smoother would
+ * diverge; the message names the level), OUT_OF_MEMORY, CUDA_ERROR. */
 int ndmg_create(const ndmg_opts* o, ndmg_t** out);
 
 /* Free every resource of the handle (NULL is accepted). */
@@ -115,7 +118,10 @@ int ndmg_destroy(ndmg_t* h);
  * handle, valid until the next call on it. */
 const char* ndmg_last_error(const ndmg_t* h);
 
-/* Rebuild the local operators for a new alpha (eq. 1), keeping all buffers. */
+/* Rebuild the local operators for a new alpha (eq. 1), keeping all buffers
+ * (a coefficient field, if one was set, is dropped).  Errors: INVALID_ARG
+ * (alpha <= 0, or a MIXED handle whose operands cannot carry the new operator,
+ * as for ndmg_create; the handle keeps its previous coefficient), CUDA_ERROR. */
 int ndmg_set_alpha(ndmg_t* h, double alpha);
 
 /* Curl-curl coefficient constant on every hexahedron (eq. 1 with a
@@ -136,8 +142,10 @@ int ndmg_set_alpha(ndmg_t* h, double alpha);
  * Subdomain size 2 only.  Synchronises the handle's stream; host set-up time
  * grows with the number of distinct local problems (one 108-edge Schur
  * complement each).  Errors: INVALID_ARG (NULL, non-positive or non-finite
- * values, subdomain size 4, too many distinct local problems; the handle keeps
- * its previous coefficients), OUT_OF_MEMORY, CUDA_ERROR. */
+ * values, subdomain size 4, too many distinct local problems, a MIXED handle
+ * whose operands cannot carry some vertex-patch operator of the field (as for
+ * ndmg_create); the handle keeps its previous coefficients), OUT_OF_MEMORY,
+ * CUDA_ERROR. */
 int ndmg_set_alpha_field(ndmg_t* h, const double* alpha_cells);
 
 /* Per-hexahedron derivative of a loss L(u(f, alpha)) with respect to the
