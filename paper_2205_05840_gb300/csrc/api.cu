@@ -133,9 +133,7 @@ template <> float* lv_r<float>(DevLevel& L) { return L.r32; }
 const double* lv_Ainv(DevLevel& L, double*) { return L.AinvT64; }
 const float* lv_Ainv(DevLevel& L, float*) { return L.AinvT32; }
 const double* lv_D(DevLevel& L, double*) { return L.Dv64; }
-const float* lv_D(DevLevel& L, float*) { return L.Dv32; }
 const double* lv_De(DevLevel& L, double*) { return L.De64; }
-const float* lv_De(DevLevel& L, float*) { return L.De32; }
 
 bool mixed(const ndmg_t* h) {
   return h->o.precision == NDMG_PREC_MIXED_BF16 || h->o.precision == NDMG_PREC_MIXED_FP16;
