@@ -291,12 +291,15 @@ BATCH_RHS = 32
 BATCH_ALPHA = 1e-2 ** 2 / 4.0
 
 
-def time_solves(ndmg, inputs, torch, dev, prec, alpha, nrhs, rank, reps=2):
+def time_solves(ndmg, inputs, torch, dev, prec, alpha, nrhs, rank, reps=2, field=None):
     """Time-to-1e-8 of `reps` solves of nrhs right-hand sides at N_GRID^3
-    (one warm-up solve first); CUDA events on the handle's stream."""
+    (one warm-up solve first); CUDA events on the handle's stream.  field: a
+    curl-curl coefficient per hexahedron instead of alpha."""
     stream = torch.cuda.Stream(device=dev)
     S = ndmg.Solver(N_GRID, n_coarsest=N_COARSEST, alpha=alpha, m=M_SMOOTH, precision=prec, nrhs=nrhs,
                     stream=stream)
+    if field is not None:
+        S.set_alpha_field(field)
     S.autotune()
     Nd = S.num_dofs()
     if nrhs == 1:
@@ -323,7 +326,8 @@ def time_solves(ndmg, inputs, torch, dev, prec, alpha, nrhs, rank, reps=2):
         b.synchronize()
         ms += a.elapsed_time(b)
     vc = (S.counters()[1] - v0) / reps
-    out = {"time_to_tol_ms": ms / reps, "vcycles": vc, "nrhs": nrhs, "alpha": alpha, "relres": rr,
+    out = {"time_to_tol_ms": ms / reps, "vcycles": vc, "nrhs": nrhs,
+           "alpha": alpha if field is None else "field", "relres": rr,
            "value": nrhs * Nd * vc / (ms / reps / 1e3), "unit": "DoF*cycles/s",
            "precision": {ndmg.PREC_FP64: "fp64", ndmg.PREC_FP32: "fp32", ndmg.PREC_MIXED_BF16: "bf16",
                          ndmg.PREC_MIXED_FP16: "fp16"}[prec]}
@@ -488,6 +492,10 @@ def run_ours(args):
     if not args.no_extra:
         extra["fp64"] = time_solves(ndmg, inputs, torch, dev, ndmg.PREC_FP64, ALPHA, 1, rank, reps=2)
         extra["batched"] = time_solves(ndmg, inputs, torch, dev, prec, BATCH_ALPHA, BATCH_RHS, rank, reps=2)
+        # jumping coefficient: a cube of alpha = 10 (cells [32, 96)^3) in alpha = 1
+        extra["field"] = time_solves(ndmg, inputs, torch, dev, prec, 1.0, 1, rank, reps=2,
+                                     field=inputs.inclusion_field(N_GRID, 1.0, 10.0))
+        extra["field"]["field"] = "inclusion: alpha = 10 on cells [n/4, 3n/4)^3, 1 elsewhere"
     del S
     torch.cuda.empty_cache()
 
