@@ -60,14 +60,17 @@ def parse():
 def run_grad_sweep(args):
     """Differentiable solve: u = A(alpha)^{-1} f forward, lambda = A^{-1}(u - u_t)
     and dL/dalpha = -lambda^T K u backward, for n in 32, 64, 96, 128, 192, 256
-    (coarsest 4^3, or 3^3 when n is a multiple of 3); bf16 tensor-core
+    (coarsest 4^3, or 3^3 when n is a multiple of 3); --precision (default fp16) tensor-core
     V-cycle inside FP64 PCG, tolerance 1e-8; times of --steps fwd+bwd passes."""
     import torch
 
     from paper_2205_05840_gb300 import autograd, inputs, ndmg
     for n in (32, 64, 96, 128, 192, 256):
         n0 = 3 if n % 3 == 0 else 4
-        S = ndmg.Solver(n, n_coarsest=n0, alpha=1.0, precision=ndmg.PREC_MIXED_BF16)
+        prec = {"auto": ndmg.PREC_MIXED_FP16, "fp64": ndmg.PREC_FP64, "fp32": ndmg.PREC_FP32,
+                "bf16": ndmg.PREC_MIXED_BF16, "fp16": ndmg.PREC_MIXED_FP16}[args.precision]
+        S = ndmg.Solver(n, n_coarsest=n0, alpha=1.0, precision=prec)
+        S.autotune()
         f = torch.tensor(inputs.random_load(n, 0), device="cuda", requires_grad=True)
         ut = torch.tensor(1e-3 * inputs.random_target(n, 1), device="cuda")
         a = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
@@ -88,7 +91,8 @@ def run_grad_sweep(args):
                 times.append((e0.elapsed_time(e1), S.counters()[1] - v0))
         ms = sum(t for t, _ in times) / len(times)
         vc = sum(c for _, c in times) / len(times)
-        print(json.dumps({"case": "fwd+bwd", "n": n, "dofs": S.num_dofs(), "ms": ms, "vcycles": vc,
+        print(json.dumps({"case": "fwd+bwd", "n": n, "precision": args.precision, "dofs": S.num_dofs(), "ms": ms,
+                          "vcycles": vc,
                           "dof_cycles_per_s": S.num_dofs() * vc / (ms / 1e3), "dL_dalpha": float(a.grad)}),
               flush=True)
         del S, f, ut, u
