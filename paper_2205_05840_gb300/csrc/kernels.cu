@@ -415,72 +415,73 @@ __global__ void __launch_bounds__(256) k_restrict(int nf, const T* __restrict__ 
   }
 }
 
-// weights of the coarse hat across an edge: fine node p -> coarse nodes
-// p/2 (weight 1) if p is even, (p-1)/2 and (p+1)/2 (weight 1/2) if odd,
-// written as two fixed terms (second weight 0 on even p) with coarse nodes
-// outside the interior given weight 0 and a valid index, so that all loads
-// of a fine edge are independent and issued together
+// One thread per coarse cell (I, J, K) updates the 24 fine edges of its
+// 2 x 2 x 2 block of fine lattice points, (2I + di, 2J + dj, 2K + dk): along
+// a coarse edge both fine halves take its value; across it the coarse hat is
+// linear (fine node 2P: weight 1 at coarse node P; fine node 2P + 1: weight
+// 1/2 at P and P + 1).  The 12 coarse values it needs (4 per direction, 0 on
+// coarse boundary nodes) are loaded once; the fine x-edge pair (2I, 2I+1) is
+// one 2-element access.
 template <typename T>
-__device__ __forceinline__ void hat2(int p, int nc, int& p0, int& p1, T& w0, T& w1) {
-  const bool odd = p & 1;
-  p0 = p >> 1;
-  p1 = (p + 1) >> 1;
-  w0 = odd ? T(0.5) : T(1);
-  w1 = odd ? T(0.5) : T(0);
-  if (!in_node(p0, nc)) {
-    w0 = T(0);
-    p0 = 1;
-  }
-  if (!in_node(p1, nc)) {
-    w1 = T(0);
-    p1 = 1;
-  }
-}
+struct Vec2;
+template <>
+struct Vec2<float> { using type = float2; };
+template <>
+struct Vec2<double> { using type = double2; };
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_prolong_add(int nf, const T* __restrict__ zc, T* __restrict__ zf) {
   const int nc = nf / 2;
-  const int rhs = blockIdx.z / nf;
-  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z - rhs * nf;
-  if (i >= nf || j >= nf) return;
+  const int rhs = blockIdx.z / nc;
+  const int I = blockIdx.x * 32 + threadIdx.x, J = blockIdx.y * 8 + threadIdx.y, K = blockIdx.z - rhs * nc;
+  if (I >= nc || J >= nc) return;
   const int64_t N3c = (int64_t)nc * (nc - 1) * (nc - 1);
   const int64_t N3f = (int64_t)nf * (nf - 1) * (nf - 1);
   zc += (int64_t)rhs * 3 * N3c;
   zf += (int64_t)rhs * 3 * N3f;
-  int I0, I1, J0, J1, K0, K1;
-  T wi0, wi1, wj0, wj1, wk0, wk1;
-  hat2(i, nc, I0, I1, wi0, wi1);
-  hat2(j, nc, J0, J1, wj0, wj1);
-  hat2(k, nc, K0, K1, wk0, wk1);
-  const bool nj = in_node(j, nf), nk = in_node(k, nf), ni = in_node(i, nf);
-  // x-edge: injection along x (segment i / 2), hats in y and z
-  T vx[4] = {T(0), T(0), T(0), T(0)}, vy[4] = {T(0), T(0), T(0), T(0)}, vz[4] = {T(0), T(0), T(0), T(0)};
-  if (nj && nk) {
-    const int c = i >> 1;
-    vx[0] = __ldg(zc + off_x(nc, c, J0, K0));
-    vx[1] = __ldg(zc + off_x(nc, c, J1, K0));
-    vx[2] = __ldg(zc + off_x(nc, c, J0, K1));
-    vx[3] = __ldg(zc + off_x(nc, c, J1, K1));
-  }
-  if (ni && nk) {
-    const int c = j >> 1;
-    vy[0] = __ldg(zc + N3c + off_y(nc, I0, c, K0));
-    vy[1] = __ldg(zc + N3c + off_y(nc, I1, c, K0));
-    vy[2] = __ldg(zc + N3c + off_y(nc, I0, c, K1));
-    vy[3] = __ldg(zc + N3c + off_y(nc, I1, c, K1));
-  }
-  if (ni && nj) {
-    const int c = k >> 1;
-    vz[0] = __ldg(zc + 2 * N3c + off_z(nc, I0, J0, c));
-    vz[1] = __ldg(zc + 2 * N3c + off_z(nc, I1, J0, c));
-    vz[2] = __ldg(zc + 2 * N3c + off_z(nc, I0, J1, c));
-    vz[3] = __ldg(zc + 2 * N3c + off_z(nc, I1, J1, c));
-  }
-  if (nj && nk) zf[off_x(nf, i, j, k)] += wk0 * (wj0 * vx[0] + wj1 * vx[1]) + wk1 * (wj0 * vx[2] + wj1 * vx[3]);
-  if (ni && nk)
-    zf[N3f + off_y(nf, i, j, k)] += wk0 * (wi0 * vy[0] + wi1 * vy[1]) + wk1 * (wi0 * vy[2] + wi1 * vy[3]);
-  if (ni && nj)
-    zf[2 * N3f + off_z(nf, i, j, k)] += wj0 * (wi0 * vz[0] + wi1 * vz[1]) + wj1 * (wi0 * vz[2] + wi1 * vz[3]);
+  auto cin = [&](int p) { return in_node(p, nc); };  // interior coarse node
+  T X[2][2], Y[2][2], Z[2][2];  // [first across node offset][second across node offset]
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      X[a][b] = cin(J + a) && cin(K + b) ? __ldg(zc + off_x(nc, I, J + a, K + b)) : T(0);
+      Y[a][b] = cin(I + a) && cin(K + b) ? __ldg(zc + N3c + off_y(nc, I + a, J, K + b)) : T(0);
+      Z[a][b] = cin(I + a) && cin(J + b) ? __ldg(zc + 2 * N3c + off_z(nc, I + a, J + b, K)) : T(0);
+    }
+  // value at fine across-offsets (d1, d2) from the 2 x 2 coarse values V
+  auto lerp = [](const T (&V)[2][2], int d1, int d2) -> T {
+    const T v0 = d1 ? T(0.5) * (V[0][0] + V[1][0]) : V[0][0];
+    const T v1 = d1 ? T(0.5) * (V[0][1] + V[1][1]) : V[0][1];
+    return d2 ? T(0.5) * (v0 + v1) : v0;
+  };
+  using T2 = typename Vec2<T>::type;
+#pragma unroll
+  for (int d2 = 0; d2 < 2; ++d2)
+#pragma unroll
+    for (int d1 = 0; d1 < 2; ++d1) {
+      // x-edges (2I, 2I+1) at nodes (2J + d1, 2K + d2): fine node 0 is on the boundary
+      if ((d1 || J >= 1) && (d2 || K >= 1)) {
+        const T v = lerp(X, d1, d2);
+        T2* p = reinterpret_cast<T2*>(zf + off_x(nf, 2 * I, 2 * J + d1, 2 * K + d2));
+        T2 w = *p;
+        w.x += v;
+        w.y += v;
+        *p = w;
+      }
+      // y-edges (segments 2J, 2J+1) at nodes (2I + d1, 2K + d2)
+      if ((d1 || I >= 1) && (d2 || K >= 1)) {
+        const T v = lerp(Y, d1, d2);
+        zf[N3f + off_y(nf, 2 * I + d1, 2 * J, 2 * K + d2)] += v;
+        zf[N3f + off_y(nf, 2 * I + d1, 2 * J + 1, 2 * K + d2)] += v;
+      }
+      // z-edges (segments 2K, 2K+1) at nodes (2I + d1, 2J + d2)
+      if ((d1 || I >= 1) && (d2 || J >= 1)) {
+        const T v = lerp(Z, d1, d2);
+        zf[2 * N3f + off_z(nf, 2 * I + d1, 2 * J + d2, 2 * K)] += v;
+        zf[2 * N3f + off_z(nf, 2 * I + d1, 2 * J + d2, 2 * K + 1)] += v;
+      }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1106,7 +1107,9 @@ void launch_restrict(cudaStream_t s, int, int nf, const T* rf, T* gc, int R) {
 
 template <typename T>
 void launch_prolong_add(cudaStream_t s, int, int nf, const T* zc, T* zf, int R) {
-  k_prolong_add<T><<<dim3((nf + 31) / 32, (nf + 7) / 8, nf * R), dim3(32, 8), 0, s>>>(nf, zc, zf);
+  const int nc = nf / 2;
+  if (nc < 1) return;
+  k_prolong_add<T><<<dim3((nc + 31) / 32, (nc + 7) / 8, nc * R), dim3(32, 8), 0, s>>>(nf, zc, zf);
 }
 
 template <typename T>
