@@ -1264,6 +1264,7 @@ int ndmg_autotune(ndmg_t* h, int32_t* choices) {
       float best = 0.f;
       int best_kz = 0;
       for (int kz = 1; kz <= L.n && st == NDMG_OK; kz *= 2) {
+        if ((int64_t)((L.n + kz - 1) / kz) * R > 65535) continue;  // grid z: chunks x right-hand sides
         L.kz[t] = kz;
         auto run = [&] {
           if (t == 0) stencil<float>(h, k, L.cK, L.cM, h->w32[0], h->w32[1], h->w32[2]);
