@@ -725,9 +725,13 @@ int pcg_mixed(ndmg_t* h, const double* f, double* u, double tol, int maxit, int*
     const double* dfrom = push_coef(h, SLOT_FROM, rn);
     {
       Span sp(h, NDMG_K_BLAS, (2.0 * 8 + 4) * N * R, 2);
-      launch_dot2_zf(h->stream, sm, N, r, q, dfrom, z32, h->red, out, R);
+      launch_dot2_zf(h->stream, sm, N, r, q, z32, h->red, out, R);
     }
     if ((st = read_sums(h, out, rz_new, &qz, true)) != NDMG_OK) return st;
+    for (int i = 0; i < R; ++i) {  // z = rn_old * z32
+      rz_new[i] *= rn[i];
+      qz[i] *= rn[i];
+    }
     for (int i = 0; i < R; ++i) rn[i] = std::sqrt(rr[i]);
     for (int i = 0; i < R; ++i) {
       ab[2 * i] = 1.0;

@@ -954,6 +954,20 @@ __global__ void __launch_bounds__(256) k_cg_update(int64_t N, const double* __re
   }
 }
 
+// float -> double on the integer pipe: exact for normal floats, subnormals
+// flush to signed zero.  The FP64 vector kernels of the mixed PCG are bound
+// by the FP64 pipe (about 2 FMA per clock per SM on this part), which
+// conversions share.
+__device__ __forceinline__ double f2d_bits(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t e = (b >> 23) & 0xFFu;
+  const unsigned long long sgn = (unsigned long long)(b >> 31) << 63;
+  const unsigned long long ed = e == 0xFFu ? 0x7FFull : (unsigned long long)(e + 896u);  // 1023 - 127
+  const unsigned long long bits =
+      e == 0u ? sgn : (sgn | (ed << 52) | ((unsigned long long)(b & 0x7FFFFFu) << 29));
+  return __longlong_as_double((long long)bits);
+}
+
 // Fused steps of the mixed flexible PCG (FP64 vectors, float preconditioner):
 // u += a p ; r -= a q ; g32 = sto * r (the float right-hand side of the next
 // V-cycle) and block sums of r.r (partials in the layout of k_dot2)
@@ -975,16 +989,15 @@ __global__ void __launch_bounds__(256) k_cg_update_rr(int64_t N, const double* _
   block_sum_store<2>(v, partial + 2 * ((int64_t)blockIdx.y * gridDim.x + blockIdx.x));
 }
 
-// block sums of x.z and y.z with z = sc * z32 (the preconditioned residual,
-// never formed in double)
+// block sums of x.z32 and y.z32 (the preconditioned residual is sc * z32;
+// the caller applies sc to the two sums, one FP64 product per sum instead of
+// one per entry)
 __global__ void __launch_bounds__(256) k_dot2_zf(int64_t N, const double* __restrict__ x, const double* __restrict__ y,
-                                                 const double* __restrict__ sc, const float* __restrict__ z32,
-                                                 double* __restrict__ partial) {
+                                                 const float* __restrict__ z32, double* __restrict__ partial) {
   const int64_t off = (int64_t)blockIdx.y * N;
-  const double s = sc[blockIdx.y];
   double v[2] = {0.0, 0.0};
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
-    const double z = s * (double)z32[off + e];
+    const double z = f2d_bits(z32[off + e]);
     v[0] += x[off + e] * z;
     v[1] += y[off + e] * z;
   }
@@ -997,7 +1010,7 @@ __global__ void __launch_bounds__(256) k_axpby_zf(int64_t N, const double* __res
   const int64_t off = (int64_t)blockIdx.y * N;
   const double s = sc[blockIdx.y], b = ab[2 * blockIdx.y + 1];
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x)
-    p[off + e] = s * (double)z32[off + e] + b * p[off + e];
+    p[off + e] = s * f2d_bits(z32[off + e]) + b * p[off + e];
 }
 
 // dst (float) = s * src (double), s = sc[rhs]
@@ -1248,10 +1261,10 @@ void launch_cg_update_rr(cudaStream_t s, int sm, int64_t N, const double* alpha,
   k_cg_update_rr<<<dim3(nb, R), 256, 0, s>>>(N, alpha, p, q, u, r, sto, g32, partial);
   k_finish2<<<R, 256, 0, s>>>(nb, partial, out);
 }
-void launch_dot2_zf(cudaStream_t s, int sm, int64_t N, const double* x, const double* y, const double* sc,
-                    const float* z32, double* partial, double* out, int R) {
+void launch_dot2_zf(cudaStream_t s, int sm, int64_t N, const double* x, const double* y, const float* z32,
+                    double* partial, double* out, int R) {
   const int nb = reduction_blocks(sm);
-  k_dot2_zf<<<dim3(nb, R), 256, 0, s>>>(N, x, y, sc, z32, partial);
+  k_dot2_zf<<<dim3(nb, R), 256, 0, s>>>(N, x, y, z32, partial);
   k_finish2<<<R, 256, 0, s>>>(nb, partial, out);
 }
 void launch_axpby_zf(cudaStream_t s, int sm, int64_t N, const double* sc, const float* z32, const double* ab, double* p,

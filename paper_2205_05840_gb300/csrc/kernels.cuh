@@ -85,8 +85,10 @@ void launch_cg_update(cudaStream_t s, int sm, int64_t N, const double* alpha, co
 // out[2 rhs], like launch_dot2)
 void launch_cg_update_rr(cudaStream_t s, int sm, int64_t N, const double* alpha, const double* p, const double* q,
                          double* u, double* r, const double* sto, float* g32, double* partial, double* out, int R);
-void launch_dot2_zf(cudaStream_t s, int sm, int64_t N, const double* x, const double* y, const double* sc,
-                    const float* z32, double* partial, double* out, int R);
+// out[2 rhs + {0,1}] = x.z32, y.z32 (unscaled: the caller multiplies by the
+// scale of z32)
+void launch_dot2_zf(cudaStream_t s, int sm, int64_t N, const double* x, const double* y, const float* z32,
+                    double* partial, double* out, int R);
 void launch_axpby_zf(cudaStream_t s, int sm, int64_t N, const double* sc, const float* z32, const double* ab, double* p,
                      int R);
 void launch_to_f32(cudaStream_t s, int sm, int64_t N, const double* sc, const double* src, float* dst, int R);
