@@ -112,3 +112,32 @@ def test_cell_gradient_finite_differences():
     K = hcurl.assemble_field(n, 1.0, a, 0.0)
     gc = mg.grad_cells(n, 1.0, lam, u)
     assert abs(a @ gc + lam @ (K @ u)) < 1e-12 * (np.abs(lam) @ np.abs(K @ u))
+
+
+@pytest.mark.parametrize("kind", ["vertex", "edge"])
+def test_grouped_smoother_equals_patchwise_solves(kind):
+    # the smoother groups equal local matrices; the same sum of local solves
+    # done patch by patch straight from the assembled matrix (the vertex or
+    # edge term as A_p^{-1} minus the interior solves of the subdomains inside)
+    n = 8
+    a = checker(n, 2, 0.5, 20.0)
+    A = hcurl.assemble_field(n, 1.0, a, 1.0).tocsr()
+    Sm = mg.Smoother(A, n, kind, varying=True)
+    r = np.random.default_rng(4).standard_normal(A.shape[0])
+    ref = np.zeros_like(r)
+    bub = mg.bubble_sets(n)
+    for b in bub:
+        ref[b] += np.linalg.solve(A[b][:, b].toarray(), r[b])
+    lists = [mg.vertex_patches(n)[0]] if kind == "vertex" else list(mg.edge_patches(n)[0])
+    for idx in lists:
+        for p in idx:
+            Ap = A[p][:, p].toarray()
+            y = np.linalg.solve(Ap, r[p])
+            # remove the interior-space part: subdomains wholly inside the patch
+            inside = [b for b in bub if set(b) <= set(p)]
+            for b in inside:
+                pos = [list(p).index(e) for e in b]
+                y[pos] -= np.linalg.solve(A[b][:, b].toarray(), r[b])
+            ref[p] += y
+    eta = 1.0 / 9.0 if kind == "vertex" else 1.0 / 13.0
+    assert np.abs(Sm.apply(r) - eta * ref).max() < 1e-10 * np.abs(eta * ref).max()
