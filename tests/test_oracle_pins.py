@@ -363,3 +363,66 @@ def test_adjoint_gradient_matches_finite_differences():
     t = 1e-3
     fdf = (loss(alpha, f + t * v) - loss(alpha, f - t * v)) / (2 * t)
     assert abs(lam @ v - fdf) < 1e-5 * abs(fdf)
+
+
+# ------------------------------------------------- Sec. 2, element by element --
+
+def _boundary_adjacent_rows(n):
+    """Every edge with a node or segment on the first or last interior plane
+    of some axis (those are the rows whose element sums meet the boundary)."""
+    d, i, j, k = hcurl.edge_coords(n)
+    near = np.zeros(d.shape, dtype=bool)
+    for c in (i, j, k):
+        near |= (c <= 1) | (c >= n - 2)
+    return np.nonzero(near)[0]
+
+
+@pytest.mark.parametrize("n", [4, 7, 16])
+def test_apply_rows_equals_assembled_rows(n):
+    # (A_h u)[rows] summed element by element (used for the expected values of
+    # sampled rows on grids too large to assemble) against the sparse assembly
+    # of Sec. 2, with alpha, beta != 1 so that a dropped or swapped term shows
+    alpha, beta, L = 0.37, 2.9, 1.3
+    A = hcurl.assemble(n, L, alpha, beta)
+    u = np.random.default_rng(n).standard_normal(hcurl.num_edges(n))
+    rng = np.random.default_rng(100 + n)
+    rows = np.unique(np.concatenate([_boundary_adjacent_rows(n),
+                                     rng.choice(hcurl.num_edges(n), size=min(200, hcurl.num_edges(n)),
+                                                replace=False)]))
+    got = hcurl.apply_rows(n, L, alpha, beta, u, rows)
+    ref = (A @ u)[rows]
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(A).max() * np.abs(u).max() * 33
+
+
+@pytest.mark.parametrize("n", [32, 64])
+def test_apply_rows_sine_eigenpair(n):
+    # the closed-form eigenpair of Sec. 2 at sizes the assembly is not used at:
+    # A Pi u = (alpha 8 h sin^2(pi h / 2) mu + beta h^3 mu^2) Pi u on the unit cube
+    alpha, beta = 3.0, 0.5
+    h = 1.0 / n
+    mu = (2.0 + np.cos(np.pi * h)) / 3.0
+    lam = alpha * 8 * h * np.sin(np.pi * h / 2) ** 2 * mu + beta * h ** 3 * mu ** 2
+    Pu = inputs.sine_interpolant(n)
+    rows = np.unique(np.concatenate([_boundary_adjacent_rows(n)[::7],
+                                     np.random.default_rng(n).choice(Pu.size, 3000, replace=False)]))
+    got = hcurl.apply_rows(n, 1.0, alpha, beta, Pu, rows)
+    assert np.abs(got - lam * Pu[rows]).max() <= 1e-12 * lam
+
+
+@pytest.mark.parametrize("n,alpha", [(8, 1.0), (16, 0.05), (16, 50.0)])
+def test_pcg_solution_equals_direct_solve(n, alpha):
+    # PCG with the V-cycle preconditioner (textbook Hestenes-Stiefel with
+    # B = MG(K, ., 0, m)) returns the solution of A u = f: compared with a
+    # sparse direct solve and with the true (not recursively updated) residual
+    H = mg.Hierarchy(n, 1.0, alpha, 1.0, n0=2, kind="vertex", m=2)
+    f = inputs.random_load(n, 3)
+    u, it, rr, hist = mg.pcg(H, f, tol=1e-10)
+    A = H.A[-1]
+    ud = spla.spsolve(A.tocsc(), f)
+    true_rel = np.linalg.norm(f - A @ u) / np.linalg.norm(f)
+    assert rr <= 1e-10 and true_rel <= 2e-10, (rr, true_rel)
+    # the error is bounded by cond(A) times the residual; the sizes here keep
+    # cond(A) below 1e3
+    assert np.linalg.norm(u - ud) <= 1e-7 * np.linalg.norm(ud)
+    # and PCG needs fewer iterations than the standalone V-cycle contraction allows
+    assert it < 40
