@@ -54,6 +54,12 @@ def parse():
     p.add_argument("--n", type=int, default=N_GRID)
     p.add_argument("--grad-sweep", action="store_true",
                    help="forward + adjoint solve throughput for 32^3 .. 256^3 (one JSON line per size)")
+    p.add_argument("--oracle-job", choices=["none", "solve", "vcycles"], default="none",
+                   help="(internal) run the FP64 CPU oracle in this process: 'solve' = one PCG solve at --n "
+                        "(solution written to --out), 'vcycles' = V-cycles at --n; prints one JSON line")
+    p.add_argument("--out", default="")
+    p.add_argument("--oracle-tol", type=float, default=1e-10)
+    p.add_argument("--cycles", type=int, default=2)
     return p.parse_args()
 
 
@@ -211,10 +217,94 @@ def oracle_rate(n: int, cycles: int):
 
 
 def cores_used():
+    """Threads the oracle's BLAS may use in this process: the value the
+    thread-count variables set, else every core the process may run on."""
     for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS"):
         if os.environ.get(var):
             return int(os.environ[var])
-    return os.cpu_count() or 1
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu), its logical CPU count and the
+    machine type."""
+    name = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() == "Model name":
+                name = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return {"model": name, "logical_cpus": os.cpu_count(), "machine": platform.machine()}
+
+
+def oracle_job(args):
+    """The oracle in a process of its own (thread count fixed by the
+    environment the parent set): 'solve' = FP64 PCG with the oracle's V-cycle
+    at --n to --oracle-tol from u = 0 (seed-0 load), solution saved to --out;
+    'vcycles' = --cycles V-cycles at --n.  One JSON line with the timings."""
+    import numpy as np
+    from oracle import mg
+    from paper_2205_05840_gb300 import inputs
+    t0 = time.perf_counter()
+    H = mg.Hierarchy(args.n, 1.0, ALPHA, 1.0, n0=N_COARSEST, kind="vertex", m=M_SMOOTH)
+    f = inputs.random_load(args.n, 0)
+    t1 = time.perf_counter()
+    out = {"n": args.n, "threads": cores_used(), "setup_s": t1 - t0}
+    if args.oracle_job == "solve":
+        u, it, rr, hist = mg.pcg(H, f, tol=args.oracle_tol)
+        t2 = time.perf_counter()
+        # time to 1e-8: the iteration at which the relative residual first met it
+        it8 = next((i for i, v in enumerate(hist) if v <= TOL), it)
+        np.save(args.out, u)
+        out.update({"solve_s": t2 - t1, "iters": it, "relres": rr, "tol": args.oracle_tol, "iters_to_1e-8": it8,
+                    "time_to_1e-8_s": (t2 - t1) * it8 / max(it, 1)})
+    else:
+        z = np.zeros_like(f)
+        t2 = time.perf_counter()
+        for _ in range(args.cycles):
+            z = H.vcycle(f, z)
+        dt = time.perf_counter() - t2
+        out.update({"cycles": args.cycles, "s": dt, "value": num_edges(args.n) * args.cycles / dt})
+    print(json.dumps(out), flush=True)
+
+
+def spawn_oracle(job: str, n: int, threads: int, extra=(), nice: int = 0):
+    """Starts the oracle as a separate Python process (fork + exec: no CUDA
+    state is inherited) with BLAS / OpenMP limited to `threads`."""
+    env = dict(os.environ)
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[var] = str(threads)
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--oracle-job", job, "--n", str(n), *extra]
+    pre = (lambda: os.nice(nice)) if nice else None
+    return subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env, cwd=ROOT,
+                            preexec_fn=pre)
+
+
+def oracle_result(proc, timeout=None):
+    try:
+        out, err = proc.communicate(timeout=timeout)
+    except subprocess.TimeoutExpired:
+        proc.kill()
+        proc.communicate()
+        return None
+    lines = [ln for ln in out.splitlines() if ln.strip().startswith("{")]
+    return json.loads(lines[-1]) if proc.returncode == 0 and lines else None
+
+
+def cpu_baseline_runs(n: int, cycles: int):
+    """The oracle's V-cycle rate at n^3 with one thread and with every core,
+    each in its own process (run one after the other)."""
+    allc = cores_used()
+    one = oracle_result(spawn_oracle("vcycles", n, 1, ["--cycles", str(cycles)]), timeout=900)
+    full = oracle_result(spawn_oracle("vcycles", n, allc, ["--cycles", str(cycles)]), timeout=900)
+    return one, full, allc
 
 
 def run_reference(args):
@@ -291,6 +381,43 @@ def profiled_traffic(kernel: str):
     return t["bytes"], t["algorithmic"]
 
 
+def grad_legs(torch, ndmg, inputs, dev, sizes, prec, steps=2, warmup=1):
+    """Forward solve + adjoint solve + dL/dalpha (autograd.solve, loss
+    0.5 ||u - u_t||^2, tolerance 1e-8) at each n in sizes: mean ms and
+    DoF*cycles/s over `steps` passes after `warmup`."""
+    from paper_2205_05840_gb300 import autograd
+    out = {}
+    for n in sizes:
+        n0 = 3 if n % 3 == 0 else 4
+        S = ndmg.Solver(n, n_coarsest=n0, alpha=1.0, precision=prec)
+        S.autotune()
+        f = torch.tensor(inputs.random_load(n, 0), device=dev, requires_grad=True)
+        ut = torch.tensor(1e-3 * inputs.random_target(n, 1), device=dev)
+        a = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+        ms, vc = 0.0, 0
+        for s in range(warmup + steps):
+            f.grad = None
+            a.grad = None
+            v0 = S.counters()[1]
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            u = autograd.solve(f, a, S, tol=TOL)
+            loss = 0.5 * ((u - ut) ** 2).sum()
+            loss.backward()
+            e1.record()
+            torch.cuda.synchronize()
+            if s >= warmup:
+                ms += e0.elapsed_time(e1)
+                vc += S.counters()[1] - v0
+        out[str(n)] = {"dofs": S.num_dofs(), "fwd_bwd_ms": ms / steps, "vcycles": vc / steps,
+                       "dof_cycles_per_s": S.num_dofs() * (vc / steps) / (ms / steps / 1e3),
+                       "dL_dalpha": float(a.grad)}
+        del S, f, ut, u
+        torch.cuda.empty_cache()
+    return out
+
+
 BATCH_RHS = 32
 BATCH_ALPHA = 1e-2 ** 2 / 4.0
 
@@ -350,6 +477,17 @@ def run_ours(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    # config 3's reference solution: the FP64 oracle's PCG solve of the same
+    # 128^3 problem (seed-0 load), in a process of its own started before any
+    # CUDA work, on half the host cores at lower priority; it runs while the
+    # GPU legs run and is compared with the mixed solution at the end
+    c3 = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import tempfile
+        c3_dir = tempfile.mkdtemp(prefix="ndmg_c3_")
+        c3_path = os.path.join(c3_dir, "u_oracle.npy")
+        c3_threads = max(1, cores_used() // 2)
+        c3 = spawn_oracle("solve", N_GRID, c3_threads, ["--out", c3_path, "--oracle-tol", "1e-10"], nice=10)
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl")
@@ -378,6 +516,7 @@ def run_ours(args):
     for _ in range(args.warmup):
         one_solve()
     torch.cuda.synchronize()
+    u_seed0 = u.detach().cpu().numpy() if rank == 0 else None   # the mixed solution of the seed-0 load
 
     # one untimed solve with every kernel class traced: the per-class
     # breakdown, and which class dominates; inside the timed region only that
@@ -500,14 +639,39 @@ def run_ours(args):
         extra["field"] = time_solves(ndmg, inputs, torch, dev, prec, 1.0, 1, rank, reps=2,
                                      field=inputs.inclusion_field(N_GRID, 1.0, 10.0))
         extra["field"]["field"] = "inclusion: alpha = 10 on cells [n/4, 3n/4)^3, 1 elsewhere"
+        extra["grad"] = grad_legs(torch, ndmg, inputs, dev, (96, 256), prec)
     del S
     torch.cuda.empty_cache()
 
     cpu = None
+    err = None
+    if c3 is not None:
+        import numpy as np
+        res = oracle_result(c3, timeout=1800)
+        if res is not None and os.path.exists(c3_path):
+            uo = np.load(c3_path)
+            d = u_seed0 - uo
+            err = {"max_rel": float(np.abs(d).max() / np.abs(uo).max()),
+                   "l2_rel": float(np.linalg.norm(d) / np.linalg.norm(uo)),
+                   "compared": f"{dtype_name} solve to {TOL:g} (seed-0 load) vs the FP64 oracle's PCG solve to "
+                               f"{res['tol']:g} ({res['iters']} iterations)"}
+            os.remove(c3_path)
+        os.rmdir(c3_dir)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, dt = oracle_rate(ORACLE_SAMPLE_N, 2)
-        cpu = {"value": rate, "unit": "DoF*cycles/s", "cores": cores_used(), "kind": "oracle",
-               "sample": f"2 FP64 oracle V-cycles on the {ORACLE_SAMPLE_N}^3 grid ({dt:.1f} s)"}
+        one, full, allc = cpu_baseline_runs(ORACLE_SAMPLE_N, 2)
+        if one and full:
+            cpu = {"value": full["value"], "unit": "DoF*cycles/s", "cores": allc, "kind": "oracle",
+                   "sample": f"2 FP64 oracle V-cycles on the {ORACLE_SAMPLE_N}^3 grid (a bounded sample of the "
+                             f"128^3 workload) in a process of its own",
+                   "single_thread": {"value": one["value"], "cores": 1, "s": one["s"]},
+                   "all_cores": {"value": full["value"], "cores": allc, "s": full["s"]},
+                   "cpu": cpu_model()}
+        if c3 is not None and res is not None:
+            if cpu is None:
+                cpu = {"kind": "oracle", "cpu": cpu_model()}
+            cpu["solve_128"] = {"time_to_1e-8_s": res["time_to_1e-8_s"], "iters_to_1e-8": res["iters_to_1e-8"],
+                                "setup_s": res["setup_s"], "threads": res["threads"],
+                                "note": "one oracle PCG solve of the 128^3 problem, run beside the GPU legs"}
 
     if rank == 0:
         out = {"metric": "V-cycle DoF*cycles/s (solve to 1e-8 at 128^3)", "value": value, "unit": "DoF*cycles/s",
@@ -528,7 +692,7 @@ def run_ours(args):
                "gpu_launches": launches, "roofline": roof, "kernels_one_solve": breakdown,
                "e2e": {"value": e2e_value, "unit": "DoF*cycles/s", "h2d_bytes_per_step": 2 * 8 * Nd,
                        "d2h_bytes_per_step": 8 * Nd},
-               "clocks": clk.summary(), "cpu_baseline": cpu, **extra}
+               "clocks": clk.summary(), "cpu_baseline": cpu, "error_vs_oracle": err, **extra}
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -542,7 +706,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.oracle_job != "none":
+        oracle_job(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.profile_case != "none":
         run_profile_case(args)

@@ -251,8 +251,12 @@ int ndmg_vcycle_iterate(ndmg_t* h, const double* f, double* u, double tol, int32
 
 /* dL/dalpha of a loss L(u(f, alpha)) given the adjoint lambda (A lambda =
  * dL/du; A is symmetric, Remark 6): out[r] = -lambda_r^T K u_r with K the
- * alpha-free curl-curl matrix (a(w,v) = alpha (curl w, curl v) + beta (w, v)).
- * lambda, u: double device vectors on the finest level; out: host, nrhs doubles. */
+ * alpha-free curl-curl matrix (a(w,v) = alpha (curl w, curl v) + beta (w, v));
+ * with a coefficient per hexahedron K = sum_T alpha_T K_T.  One fused kernel
+ * forms the face circulations of lambda and u cell by cell, pairs them through
+ * the face mass and reduces in FP64 (then a finishing kernel per right-hand
+ * side).  lambda, u: double device vectors on the finest level; out: host,
+ * nrhs doubles (synchronises the handle's stream). */
 int ndmg_grad_alpha(ndmg_t* h, const double* lambda, const double* u, double* out);
 
 /* Graph replay of the float V-cycle inside the mixed-precision solves (no
@@ -293,6 +297,16 @@ int ndmg_trace_enable(ndmg_t* h, int32_t kernel_class, int32_t on);
  * smoother's 12 bytes per edge of float vectors (read r, read and write z). */
 int ndmg_trace_read(ndmg_t* h, int32_t kernel_class, int64_t* launches, double* ms, double* units);
 
+/* Host-side fault injection for tests (no counterpart in the paper): writes
+ * code (>= 0) into the handle's device status word, exactly as a tensor-core
+ * kernel does when one of its bounded waits gives up.  While the word is
+ * nonzero the kernels that check it (the tensor-core smoothers of MIXED
+ * handles) return without doing anything; the next entry point that reads it
+ * (ndmg_solve, ndmg_vcycle, ndmg_smooth on float vectors of a MIXED handle)
+ * returns NDMG_DEVICE_TIMEOUT and clears it, after which the handle works as
+ * before.  Synchronises the handle's stream.  Errors: INVALID_ARG, CUDA_ERROR. */
+int ndmg_inject_status(ndmg_t* h, int32_t code);
+
 /* Running totals since ndmg_create: kernels launched by this handle (all
  * classes) and V-cycles MG(K, ., ., m) performed on the finest level.  Either
  * pointer may be NULL. */
@@ -307,14 +321,19 @@ int ndmg_counters(const ndmg_t* h, int64_t* launches, int64_t* vcycles);
  * No handle is needed and nothing is allocated: the partial sums live in a
  * fixed 32 KB device array inside the library, which every GPU that loads the
  * library holds until the process exits.
- *   x, y   device pointers, 16-byte aligned, n elements each (caller-owned)
+ *   x, y   device pointers, n elements each (caller-owned), 16-byte aligned
+ *          like every vector of this library (the kernels themselves read
+ *          single elements, so element alignment would be enough for them)
  *   n      0 <= n <= 67,108,864; larger n returns NDMG_INVALID_ARG (and a
  *          message on stderr) before anything is launched
  *   out    host pointer, written before return
  *   stream cudaStream_t (NULL = legacy default stream); the call queues two
  *          kernels and a copy on it and synchronises it.
  * The first call on a device looks up the device address of the array (with
- * that device current); make that first call before any stream capture.  All
+ * that device current) and keeps it for the device's current CUDA context; a
+ * call in another context of the device (after cudaDeviceReset, or under a
+ * non-primary context) looks it up again.  Make that first call before any
+ * stream capture.  All
  * calls share the one array, so calls that overlap on the GPU (other host
  * threads, other streams) race and give wrong results; serialise them.  The
  * array keeps the last call's contents; each call overwrites every slot it

@@ -38,6 +38,10 @@ class _Solve(torch.autograd.Function):
         lam = torch.zeros_like(u)
         S.solve(gu.detach().contiguous().to(u.dtype), lam, tol=ctx.tol, maxit=ctx.maxit)
         dalpha = S.grad_alpha(lam, u)
+        if isinstance(dalpha, list):
+            # a batch of right-hand sides shares the one alpha: its gradient is
+            # the sum of the per-right-hand-side -lambda_r^T K u_r
+            dalpha = sum(dalpha)
         return lam, torch.tensor(dalpha, dtype=torch.float64), None, None, None
 
 

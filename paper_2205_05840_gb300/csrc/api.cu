@@ -1530,15 +1530,17 @@ int ndmg_grad_alpha(ndmg_t* h, const double* lambda, const double* u, double* ou
   if (!out) return fail(h, NDMG_INVALID_ARG, "null output");
   const int K = h->K, R = nrhs(h);
   DevLevel& L = h->lv[K];
-  double* Ku = h->w64[3];
+  // one fused pass: circulations of lambda and u per cell, face-mass pairs,
+  // FP64 block sums (reads lambda and u; each edge from its 4 cells via L1)
+  const int nb = reduction_blocks(h->sm_count);
+  double* sums = h->red + 2 * (int64_t)nb * R;
   {
-    Span sp(h, NDMG_K_STENCIL, 16.0 * L.N * R);
-    stencil<double>(h, K, L.h, 0.0, u, (const double*)nullptr, Ku);
+    Span sp(h, NDMG_K_BLAS, 16.0 * L.N * R, 2);
+    launch_grad_alpha_sum(h->stream, h->sm_count, L.n, L.h, lambda, u, h->field ? L.a64 : nullptr, h->red, sums, R);
   }
   std::vector<double> v;
-  if ((st = dot2<double>(h, L.N, lambda, Ku, (const double*)nullptr, (const double*)nullptr, v, nullptr)) != NDMG_OK)
-    return st;
-  for (int i = 0; i < R; ++i) out[i] = -v[i];
+  if ((st = read_sums(h, sums, v, nullptr, false)) != NDMG_OK) return st;
+  for (int i = 0; i < R; ++i) out[i] = v[i];
   return NDMG_OK;
 }
 
@@ -1599,6 +1601,16 @@ int ndmg_trace_read(ndmg_t* h, int32_t kernel_class, int64_t* launches, double* 
   if (units) *units = h->trace_units[kernel_class];
   h->trace_launches[kernel_class] = 0;
   h->trace_units[kernel_class] = 0.0;
+  return NDMG_OK;
+}
+
+int ndmg_inject_status(ndmg_t* h, int32_t code) {
+  if (!h) return NDMG_INVALID_ARG;
+  if (code < 0) return fail(h, NDMG_INVALID_ARG, "status code must be >= 0");
+  NDMG_CK(cudaStreamSynchronize(h->stream));
+  *h->status_host = code;
+  NDMG_CK(cudaMemcpyAsync(h->status, h->status_host, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  NDMG_CK(cudaStreamSynchronize(h->stream));
   return NDMG_OK;
 }
 

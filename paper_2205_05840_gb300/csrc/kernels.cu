@@ -924,6 +924,35 @@ __global__ void k_finish2(int nb, const double* __restrict__ partial, double* __
   block_sum_store<2>(v, out + 2 * blockIdx.x);
 }
 
+// dL/dalpha = -lambda^T K u in one pass: per cell the face pairs of the
+// circulations of lambda and u (as k_grad_cells, times the cell's
+// coefficient when acell is given, i.e. K = sum_T alpha_T K_T), accumulated
+// in FP64 per thread and reduced per block into partial (layout of k_dot2,
+// second slot 0); k_finish2 adds the blocks of every right-hand side
+__global__ void __launch_bounds__(256) k_grad_alpha_sum(int n, double h, const double* __restrict__ lam,
+                                                        const double* __restrict__ u,
+                                                        const double* __restrict__ acell,
+                                                        double* __restrict__ partial) {
+  const int64_t N3 = (int64_t)n * (n - 1) * (n - 1);
+  const int64_t NC = (int64_t)n * n * n;
+  lam += (int64_t)blockIdx.y * 3 * N3;
+  u += (int64_t)blockIdx.y * 3 * N3;
+  double v[2] = {0.0, 0.0};
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < NC; t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % n), j = (int)((t / n) % n), k = (int)(t / ((int64_t)n * n));
+    double a[3][2], b[3][2];
+    cell_circulations(lam, n, N3, i, j, k, a);
+    cell_circulations(u, n, N3, i, j, k, b);
+    double s = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      s += 2.0 * (a[d][0] * b[d][0] + a[d][1] * b[d][1]) + a[d][0] * b[d][1] + a[d][1] * b[d][0];
+    v[0] += acell ? acell[t] * s : s;
+  }
+  v[0] *= -h / 6.0;
+  block_sum_store<2>(v, partial + 2 * ((int64_t)blockIdx.y * gridDim.x + blockIdx.x));
+}
+
 // y = a x + b y with (a, b) = ab[2 rhs], ab[2 rhs + 1]
 template <typename T>
 __global__ void __launch_bounds__(256) k_axpby(int64_t N, const double* __restrict__ ab, const T* __restrict__ x,
@@ -1111,18 +1140,34 @@ void launch_stencil_field(cudaStream_t s, int sm, int n, double cK, double cM, c
       <<<grid, dim3(kTX, kTY), stencil_field_smem<T>(), s>>>(n, KZ, (T)cK, (T)cM, u, g, y, nullptr, acell);
 }
 
+// grid z of the transfers = coarse planes x right-hand sides; batches whose
+// product would pass the 65,535 limit of grid z go in groups of right-hand
+// sides (contiguous vectors, so a group is a pointer offset)
+constexpr int kMaxGridZ = 65535;
+
 template <typename T>
 void launch_restrict(cudaStream_t s, int, int nf, const T* rf, T* gc, int R) {
   const int nc = nf / 2;
   if (nc < 2) return;
-  k_restrict<T><<<dim3((nc + 31) / 32, (nc + 7) / 8, nc * R), dim3(32, 8), 0, s>>>(nf, rf, gc);
+  const int64_t Nf = 3LL * nf * (nf - 1) * (nf - 1), Nc = 3LL * nc * (nc - 1) * (nc - 1);
+  const int group = kMaxGridZ / nc;
+  for (int r0 = 0; r0 < R; r0 += group) {
+    const int rg = R - r0 < group ? R - r0 : group;
+    k_restrict<T><<<dim3((nc + 31) / 32, (nc + 7) / 8, nc * rg), dim3(32, 8), 0, s>>>(nf, rf + r0 * Nf, gc + r0 * Nc);
+  }
 }
 
 template <typename T>
 void launch_prolong_add(cudaStream_t s, int, int nf, const T* zc, T* zf, int R) {
   const int nc = nf / 2;
   if (nc < 1) return;
-  k_prolong_add<T><<<dim3((nc + 31) / 32, (nc + 7) / 8, nc * R), dim3(32, 8), 0, s>>>(nf, zc, zf);
+  const int64_t Nf = 3LL * nf * (nf - 1) * (nf - 1), Nc = 3LL * nc * (nc - 1) * (nc - 1);
+  const int group = kMaxGridZ / nc;
+  for (int r0 = 0; r0 < R; r0 += group) {
+    const int rg = R - r0 < group ? R - r0 : group;
+    k_prolong_add<T><<<dim3((nc + 31) / 32, (nc + 7) / 8, nc * rg), dim3(32, 8), 0, s>>>(nf, zc + r0 * Nc,
+                                                                                          zf + r0 * Nf);
+  }
 }
 
 template <typename T>
@@ -1313,6 +1358,13 @@ void launch_patch_grouped(cudaStream_t s, int sm, int n, const PatchFamily& fam,
   if (blocks > nchunks) blocks = nchunks;
   k_patch_grouped<T, kGroupPB><<<dim3(blocks, R), 128, patch_grouped_smem<T>(fam.nloc), s>>>(
       n, fam, Dtab, chunks, nchunks, plist, (T)eta, r, z);
+}
+
+void launch_grad_alpha_sum(cudaStream_t s, int sm, int n, double h, const double* lam, const double* u,
+                           const double* acell, double* partial, double* out, int R) {
+  const int nb = reduction_blocks(sm);
+  k_grad_alpha_sum<<<dim3(nb, R), 256, 0, s>>>(n, h, lam, u, acell, partial);
+  k_finish2<<<R, 256, 0, s>>>(nb, partial, out);
 }
 
 void launch_grad_cells(cudaStream_t s, int sm, int n, double h, const double* lam, const double* u, double* out,

@@ -70,6 +70,10 @@ void launch_patch_grouped(cudaStream_t s, int sm, int n, const PatchFamily& fam,
                           int nchunks, const int* plist, double eta, const T* r, T* z, int R);
 void launch_grad_cells(cudaStream_t s, int sm, int n, double h, const double* lam, const double* u, double* out,
                        int R);
+// -lambda_r^T K u_r per right-hand side into out[2 r] in one fused pass (K
+// the alpha-free curl-curl matrix, or sum_T acell_T K_T when acell is given)
+void launch_grad_alpha_sum(cudaStream_t s, int sm, int n, double h, const double* lam, const double* u,
+                           const double* acell, double* partial, double* out, int R);
 int reduction_blocks(int sm);
 template <typename T>
 void launch_dot2(cudaStream_t s, int sm, int64_t N, const T* x, const T* y, const T* x2, const T* y2,

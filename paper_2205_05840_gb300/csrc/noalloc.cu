@@ -10,6 +10,8 @@
 #include <cstdio>
 #include <mutex>
 
+#include <cuda.h>
+
 #include "ndmg_internal.h"
 
 namespace ndmg {
@@ -63,10 +65,41 @@ __global__ void __launch_bounds__(kThreads) k_dot_finish(const double* __restric
   if (threadIdx.x == 0) *result = v;
 }
 
-// device address of g_dot_scratch, looked up once per device
+// device address of g_dot_scratch, looked up once per device and CUDA
+// context: a cudaDeviceReset (or a non-primary context on the same device)
+// loads the module again, possibly at another address, so the cache is keyed
+// by the id of the context current at the call (driver entry points fetched
+// through the runtime, so the library needs no link against libcuda)
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-double* g_addr[kMaxDevices] = {};
+struct Cached {
+  unsigned long long ctx_id = 0;  // 0: not looked up yet (driver context ids start at 1)
+  double* addr = nullptr;
+};
+Cached g_addr[kMaxDevices];
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+
+// id of the context current on this thread (after the runtime made one current)
+cudaError_t current_context_id(unsigned long long* id) {
+  if (!g_ctx_current || !g_ctx_id) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = cudaDriverEntryPointSymbolNotFound;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+    if (e == cudaSuccess) e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+    if (e != cudaSuccess) return e;
+    if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess) return cudaErrorNotSupported;
+    g_ctx_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+    g_ctx_id = reinterpret_cast<CtxGetIdFn>(f2);
+  }
+  CUcontext ctx = nullptr;
+  if (g_ctx_current(&ctx) != CUDA_SUCCESS || !ctx) return cudaErrorDeviceUninitialized;
+  return g_ctx_id(ctx, id) == CUDA_SUCCESS ? cudaSuccess : cudaErrorDeviceUninitialized;
+}
 
 cudaError_t scratch_for_current_device(double** out) {
   int dev = 0;
@@ -74,13 +107,19 @@ cudaError_t scratch_for_current_device(double** out) {
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
+  unsigned long long id = 0;
+  // no context current yet on this thread, a new context, or a first call:
+  // look the address up (the lookup makes the device's primary context
+  // current), then record which context it belongs to
+  if (current_context_id(&id) != cudaSuccess || g_addr[dev].ctx_id != id || !g_addr[dev].addr) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_dot_scratch);
+    if (e == cudaSuccess) e = current_context_id(&id);
     if (e != cudaSuccess) return e;
-    g_addr[dev] = static_cast<double*>(p);
+    g_addr[dev].addr = static_cast<double*>(p);
+    g_addr[dev].ctx_id = id;
   }
-  *out = g_addr[dev];
+  *out = g_addr[dev].addr;
   return cudaSuccess;
 }
 

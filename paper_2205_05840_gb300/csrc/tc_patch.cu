@@ -145,7 +145,7 @@ constexpr int OFF_R = OFF_B2 + kN2 * kK2 * 2;
 constexpr int OFF_BAR = OFF_R + ((kRegionAll * 4 + 15) / 16) * 16;
 constexpr int OFF_TM = OFF_BAR + 16;
 constexpr int OFF_RED = OFF_TM + 16;
-constexpr int OFF_AT = OFF_RED + 32;          // A_T^{-1} (6 x 6, FP32)
+constexpr int OFF_AT = OFF_RED + 48;          // A_T^{-1} (6 x 6, FP32); red: 8 warp maxima + 1 flag
 constexpr int kSmem = OFF_AT + 36 * 4;
 static_assert(kRegionAll * 4 <= kM * kK1 * 2, "accumulator fits in the A operand");
 static_assert(OFF_BAR % 8 == 0, "mbarrier alignment");
@@ -489,16 +489,37 @@ __global__ void __launch_bounds__(kThreads, 3)
   __syncthreads();
 
   // ---- 5. D' = A' W^t, written over D -----------------------------------------
-  if (tid == 0 && ok) {
-    fence_after();
-    issue_mma2<FP16>(tmem, smem_u32(smem + OFF_A), smem_u32(smem + OFF_B2), bar1);
+  // (issued only when thread 0 saw the first product complete; red[8] tells
+  // every thread whether it was)
+  if (tid == 0) {
+    red[8] = ok ? 1.f : 0.f;
+    if (ok) {
+      fence_after();
+      issue_mma2<FP16>(tmem, smem_u32(smem + OFF_A), smem_u32(smem + OFF_B2), bar1);
+    }
   }
   if (ok) ok = mbar_wait(bar1, 0);
   fence_after();
-  // A' has been read by the tensor cores: its space becomes the accumulator;
   // the CTA goes on only if every thread saw both products complete
-  for (int q = tid; q < kRegionAll; q += kThreads) ACC[q] = 0.f;
   ok = __syncthreads_and(ok) != 0;
+  if (!ok) {
+    // a wait gave up: the products issued so far may still be reading A', W
+    // and writing TMEM.  Record the timeout, touch no shared memory, wait
+    // (again bounded) for those products, free TMEM and return.
+    if (tid == 0) atomicExch(status, kTimeout);
+    mbar_wait(bar0, 0);
+    if (red[8] != 0.f) mbar_wait(bar1, 0);
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+      fence_after();
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+    return;
+  }
+  // A' has been read by the tensor cores: its space becomes the accumulator
+  for (int q = tid; q < kRegionAll; q += kThreads) ACC[q] = 0.f;
+  __syncthreads();
 
   // ---- 6. accumulate: patch outputs (rows of D') and interior-space solves ----
   if (ok) {
@@ -506,8 +527,6 @@ __global__ void __launch_bounds__(kThreads, 3)
     const int a = prow % kBX, b = (prow / kBX) % kBY, c = prow / (kBX * kBY);
     const bool live = VX + a <= nv && VY + b <= nv && VZ + c <= nv;
     scatter_rows(tmem, ACC, warp, lane, live ? wscale / rscale : 0.f);  // live rows add
-  } else if (tid == 0) {
-    atomicExch(status, kTimeout);
   }
   // interior spaces of the coarse elements the brick owns: E in [V0-1, V1-1]
   // per axis, plus element nv on the last brick of an axis (its last vertex
@@ -645,8 +664,10 @@ __global__ void __launch_bounds__(kThreads, 2)
   const bool live = VX + pa <= nv && VY + pb <= nv && VZ + pc <= nv;
   bool ok = true;
   const uint32_t wbase = smem_u32(smem + OFF_B1);
+  uint32_t last_parity = 0;
   for (int e = e0; e < e1 && ok; ++e) {
     const uint32_t parity = (uint32_t)(e - e0) & 1u;
+    last_parity = parity;
     const uint8_t* img = imgs + (size_t)__ldg(ggrp + e) * kImgStride;
     const uint4 mk = __ldg(gmask + e);
     const uint32_t word = prow < 32 ? mk.x : prow < 64 ? mk.y : prow < 96 ? mk.z : mk.w;
@@ -670,9 +691,12 @@ __global__ void __launch_bounds__(kThreads, 2)
     fence_async_smem();
     fence_before();
     __syncthreads();
-    if (tid == 0 && okg) {
-      fence_after();
-      issue_mma2<FP16>(tmem, smem_u32(A2), smem_u32(smem + OFF_B2), bar1);
+    if (tid == 0) {
+      red[8] = okg ? 1.f : 0.f;  // whether the second product of this group was issued
+      if (okg) {
+        fence_after();
+        issue_mma2<FP16>(tmem, smem_u32(A2), smem_u32(smem + OFF_B2), bar1);
+      }
     }
     if (okg) okg = mbar_wait(bar1, parity);
     fence_after();
@@ -682,7 +706,20 @@ __global__ void __launch_bounds__(kThreads, 2)
     __syncthreads();  // TMEM, A' and B are free for the next group
     fence_after();
   }
-  if (!ok && tid == 0) atomicExch(status, kTimeout);
+  if (!ok) {
+    // a wait gave up: record it, wait (bounded) for the products of the last
+    // group, which may still read A, A', W and write TMEM, free TMEM, return
+    if (tid == 0) atomicExch(status, kTimeout);
+    mbar_wait(bar0, last_parity);
+    if (red[8] != 0.f) mbar_wait(bar1, last_parity);
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+      fence_after();
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+    return;
+  }
 
   // interior spaces of the coarse elements the brick owns (see k_tc_smoother)
   if (ok) {

@@ -72,6 +72,7 @@ _SIGS = {
     "ndmg_set_alpha_field": [_vp, _vp],
     "ndmg_autotune": [_vp, _P(_i32)],
     "ndmg_grad_alpha_field": [_vp, _vp, _vp, _vp],
+    "ndmg_inject_status": [_vp, _i32],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -308,3 +309,8 @@ class Solver:
         a, b = _i64(), _i64()
         self._check(_lib.ndmg_counters(self._h, ctypes.byref(a), ctypes.byref(b)), "counters")
         return a.value, b.value
+
+    def inject_status(self, code: int):
+        """Test hook: set the handle's device status word (ndmg_inject_status),
+        as a tensor-core kernel whose bounded wait gave up would."""
+        self._check(_lib.ndmg_inject_status(self._h, int(code)), "inject_status")

@@ -1,5 +1,6 @@
-"""The allocation-free inner product (ndmg_dot_noalloc) against the handle's
-inner product (ndmg_dot), through the C ABI.
+"""The allocation-free inner product (ndmg_dot_noalloc) through the C ABI,
+against an FP64 NumPy dot of the host copies and against the handle's inner
+product (ndmg_dot).
 
 Some callers cannot allocate device memory (an allocator that owns every
 device byte, or a place where cudaMalloc's possible device synchronisation is
@@ -28,21 +29,31 @@ def _noalloc(dtype_code, x, y, n, stream):
     return st, out.value
 
 
-def test_noalloc_dot_matches_handle_dot_two_calls():
+def test_noalloc_dot_matches_numpy_and_handle_dot_two_calls():
     S = ndmg.Solver(32, n_coarsest=4)
     N = S.num_dofs()
     stream = S.stream.cuda_stream
-    for call, (dtype, code, tol) in enumerate(((torch.float64, ndmg.F64, 1e-13), (torch.float64, ndmg.F64, 1e-13),
-                                               (torch.float32, ndmg.F32, 1e-12))):
+    # two FP64 calls in a row (the second reuses the array the first left
+    # behind), then an FP32 call
+    for call, (dtype, code) in enumerate(((torch.float64, ndmg.F64), (torch.float64, ndmg.F64),
+                                          (torch.float32, ndmg.F32))):
         g = np.random.default_rng(10 + call)
-        x = torch.tensor(g.standard_normal(N), dtype=dtype, device="cuda")
-        y = torch.tensor(g.standard_normal(N), dtype=dtype, device="cuda")
+        xh = g.standard_normal(N)
+        yh = g.standard_normal(N)
+        x = torch.tensor(xh, dtype=dtype, device="cuda")
+        y = torch.tensor(yh, dtype=dtype, device="cuda")
         torch.cuda.synchronize()
-        ref = S.dot(x, y)
         st, got = _noalloc(code, x, y, N, stream)
         assert st == ndmg.OK
-        scale = float(torch.linalg.vector_norm(x.double()) * torch.linalg.vector_norm(y.double()))
-        assert abs(got - ref) <= tol * scale, (call, got, ref)
+        # FP64 dot of exactly the values on the device (FP32 entries are exact in FP64)
+        ref_np = float(np.dot(x.cpu().double().numpy(), y.cpu().double().numpy()))
+        ref_h = S.dot(x, y)
+        scale = float(np.linalg.norm(x.cpu().double().numpy()) * np.linalg.norm(y.cpu().double().numpy()))
+        # both sides accumulate N products in FP64 in different orders: random
+        # data keeps the difference near sqrt(N) eps |x||y| ~ 7e-14 |x||y|
+        tol = 1e-12 * scale
+        assert abs(got - ref_np) <= tol, (call, got, ref_np)
+        assert abs(got - ref_h) <= tol, (call, got, ref_h)
 
 
 def test_noalloc_dot_limits():
