@@ -685,7 +685,8 @@ def run_ours(args):
                           "parallelism": f"replicas{world}",
                           "autotuned": {str(N_COARSEST << k): {"stencil_planes_per_cta_f32": v[0],
                                                                "stencil_planes_per_cta_f64": v[1],
-                                                               "tensor_core_smoother": bool(v[2])}
+                                                               "tensor_core_smoother": bool(v[2]),
+                                                               "smoother_cell_layers_per_item": v[2]}
                                         for k, v in tuned.items()}},
                "time_to_tol_ms": ms_total / args.steps, "vcycles_per_solve": vcyc_per_step,
                "pcg_iterations": iters[-1][0], "final_relres": iters[-1][1],

@@ -164,12 +164,16 @@ int ndmg_grad_alpha_field(ndmg_t* h, const double* lambda, const double* u, doub
  * n_k; twenty launches each, CUDA events on the handle's stream, with the
  * handle's nrhs) and keeps the fastest; every choice computes bitwise the same
  * result.  On MIXED handles with the vertex smoother it also times, per level,
- * the tensor-core smoother against the FP32 CUDA-core one (small levels have
- * too few bricks of patches to fill the GPU) and keeps the faster; the FP32
+ * the tensor-core smoother for every number of cell layers per work item
+ * (its own balance model, then 1, 2, 4, ... n_k / 2) and against the FP32
+ * CUDA-core smoother (small levels have too little work to fill the GPU), and
+ * keeps the fastest; the layer count does not change the result, the FP32
  * kernels are at least as accurate.  Synchronises the stream, overwrites the
  * handle's solver workspaces and drops a captured V-cycle graph.  choices:
  * NULL or a host array of 3 (K+1) ints, level-major: [3k] planes per CTA for
- * float, [3k+1] for double, [3k+2] 1 if level k smooths on tensor cores.
+ * float, [3k+1] for double, [3k+2] 0 if level k smooths on CUDA cores, else
+ * the cell layers per work item of the tensor-core smoother (n_k / 2 + 1:
+ * its balance model's choice).
  * Errors: INVALID_ARG, CUDA_ERROR, DEVICE_TIMEOUT. */
 int ndmg_autotune(ndmg_t* h, int32_t* choices);
 

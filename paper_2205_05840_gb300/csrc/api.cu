@@ -8,7 +8,9 @@
 #include <new>
 #include <type_traits>
 
+#include "coarse_cycle.cuh"
 #include "kernels.cuh"
+#include "tc_cell.cuh"
 #include "tc_patch.cuh"
 
 using namespace ndmg;
@@ -138,6 +140,11 @@ const double* lv_De(DevLevel& L, double*) { return L.De64; }
 bool mixed(const ndmg_t* h) {
   return h->o.precision == NDMG_PREC_MIXED_BF16 || h->o.precision == NDMG_PREC_MIXED_FP16;
 }
+
+// kernels with bounded device-side waits may have written the status word:
+// the tensor-core smoothers (MIXED handles) and the persistent small-level
+// kernel (float V-cycles)
+bool waits_on_device(const ndmg_t* h) { return mixed(h) || h->Kc > 0; }
 
 // ---------------------------------------------------------------------------
 // Level operations (every launch covers the R = nrhs right-hand sides)
@@ -307,14 +314,15 @@ void op_smoother<float>(ndmg_t* h, int k, const float* r, float* z) {
     op_edge_terms<float>(h, k, L.De32, r, z);
     return;
   }
-  if (mixed(h) && L.Wtc && L.tc) {
-    // vertex patches on tensor cores (Gram form: two 108x60 products per
-    // patch) and the interior 6x6 solves in one kernel.  Algorithmic bytes:
-    // read r, read and write z (FP32); 25,920 flops per patch is ~86 flop/B,
-    // below the bf16 ridge of ~256 flop/B, so the work is memory-bound.
+  if (mixed(h) && L.Wcell && L.tc) {
+    // vertex patches on tensor cores (Gram form W W^t, cell-owned rows:
+    // shifted-row GEMMs, one writer per edge) and the interior 6x6 solves in
+    // one persistent kernel.  Algorithmic bytes: read r, read and write z
+    // (FP32); 25,920 flops per patch is ~86 flop/B, below the bf16 ridge of
+    // ~256 flop/B, so the work is memory-bound.
     Span sp(h, NDMG_K_PATCH, 12.0 * L.N * R);
-    launch_tc_smoother(h->stream, L.n, L.Wtc, h->o.precision == NDMG_PREC_MIXED_FP16, L.AinvT32, h->o.eta, r, z,
-                       h->status, R);
+    launch_tc_cell_smoother(h->stream, h->sm_count, L.n, L.Wcell, h->o.precision == NDMG_PREC_MIXED_FP16, L.AinvT32,
+                            h->o.eta, r, z, h->status, R, L.zlen);
     return;
   }
   {
@@ -337,12 +345,45 @@ void op_smooth_steps(ndmg_t* h, int k, const T* g, T* z, int steps) {
   }
 }
 
+// the persistent small-level kernel serves float V-cycles on levels 1 .. Kc
+// that start from z = 0 (constant coefficient, vertex smoother, subdomain 2)
+bool coarse_cycle_on(const ndmg_t* h, int k) {
+  return h->coarse_on && h->Kc > 0 && k >= 1 && k <= h->Kc && h->coarse_grid > 0 && !h->field;
+}
+
+// z = MG(k, g, 0, m) for k <= Kc in one cooperative launch
+void op_coarse_cycle(ndmg_t* h, int k, const float* g, float* z) {
+  CoarseLevel cl[kCoarseMaxLevels + 1];
+  double units = 0.0;
+  for (int j = 0; j <= k; ++j) {
+    DevLevel& L = h->lv[j];
+    cl[j].n = L.n;
+    cl[j].cK = L.cK;
+    cl[j].cM = L.cM;
+    cl[j].g = j == k ? const_cast<float*>(g) : L.g32;
+    cl[j].z = j == k ? z : L.z32;
+    cl[j].r = L.r32;
+    cl[j].W = L.Wv32;
+    cl[j].AinvT = L.AinvT32;
+    units += 74.0 * L.N * nrhs(h);   // FP32 bytes of one V-cycle level (read / write of g, z, r)
+  }
+  Span sp(h, NDMG_K_COARSE, units);
+  launch_coarse_cycle(h->stream, h->coarse_grid, cl, k, (int)h->lv[0].N, h->Ainv0, h->lv[0].g32, h->lv[0].z32,
+                      h->o.eta, h->o.m, nrhs(h), h->coarse_count, h->status);
+}
+
 // MG(k, g, z, m) of Fig. 1 with z in/out; z_zero: z is 0 on entry, so the
 // first pre-smoothing residual is g itself (no stencil pass)
 template <typename T>
 void op_vcycle(ndmg_t* h, int k, const T* g, T* z, bool z_zero = false) {
   const int R = nrhs(h);
   if (k == h->K) ++h->vcycle_total;
+  if constexpr (std::is_same<T, float>::value) {
+    if (z_zero && coarse_cycle_on(h, k)) {
+      op_coarse_cycle(h, k, g, z);
+      return;
+    }
+  }
   if (k == 0) {
     const double N0 = (double)h->lv[0].N;
     Span sp(h, NDMG_K_COARSE, (2.0 * sizeof(T) * N0 + 8.0 * N0 * N0) * R);
@@ -433,6 +474,60 @@ const double* push_coef(ndmg_t* h, int slot, const std::vector<double>& v) {
   return dp;
 }
 
+// device PCG scalars of the handle
+CgScalars cg_scalars(ndmg_t* h) {
+  const int R = nrhs(h);
+  double* b = h->cg;
+  return CgScalars{b, b + R, b + 3 * R, b + 4 * R, b + 5 * R, b + 6 * R, b + 7 * R};
+}
+
+// writes rr, rz and the done flags of every right-hand side to the device
+int cg_push_state(ndmg_t* h, const std::vector<double>& rr, const std::vector<double>& rz,
+                  const std::vector<char>& done) {
+  const int R = nrhs(h);
+  const CgScalars S = cg_scalars(h);
+  double* hp = h->cg_host;
+  for (int i = 0; i < R; ++i) {
+    hp[i] = rr[i];
+    hp[R + i] = rz[i];
+    hp[2 * R + i] = done[i] ? 1.0 : 0.0;
+  }
+  NDMG_CK(cudaMemcpyAsync(S.rr, hp, sizeof(double) * R, cudaMemcpyHostToDevice, h->stream));
+  NDMG_CK(cudaMemcpyAsync(S.rz, hp + R, sizeof(double) * R, cudaMemcpyHostToDevice, h->stream));
+  NDMG_CK(cudaMemcpyAsync(S.done, hp + 2 * R, sizeof(double) * R, cudaMemcpyHostToDevice, h->stream));
+  NDMG_CK(cudaStreamSynchronize(h->stream));   // the pinned buffer is reused right away
+  return NDMG_OK;
+}
+
+// the one synchronisation of a PCG iteration: rr of every right-hand side and
+// the status word (a breakdown the device detected, a device-side timeout)
+int cg_read_rr(ndmg_t* h, std::vector<double>& rr) {
+  const int R = nrhs(h);
+  const CgScalars S = cg_scalars(h);
+  NDMG_CK_LAUNCH();
+  NDMG_CK(cudaMemcpyAsync(h->cg_host, S.rr, sizeof(double) * R, cudaMemcpyDeviceToHost, h->stream));
+  NDMG_CK(cudaMemcpyAsync(h->status_host, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  NDMG_CK(cudaStreamSynchronize(h->stream));
+  if (int st = collect_graph(h)) return st;
+  if (const int code = *h->status_host) {
+    cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
+    if (code & kStatusBreakdown) return fail(h, NDMG_BREAKDOWN, "non-positive curvature p^T A p");
+    return fail(h, NDMG_DEVICE_TIMEOUT, "a device-side wait timed out (status " + std::to_string(code) + ")");
+  }
+  rr.assign(h->cg_host, h->cg_host + R);
+  return NDMG_OK;
+}
+
+// done flags to the device after a convergence check (pinned staging slot
+// 2R.., rewritten only after the next synchronisation)
+int cg_push_done(ndmg_t* h, const std::vector<char>& done) {
+  const int R = nrhs(h);
+  double* hp = h->cg_host + 2 * R;
+  for (int i = 0; i < R; ++i) hp[i] = done[i] ? 1.0 : 0.0;
+  NDMG_CK(cudaMemcpyAsync(cg_scalars(h).done, hp, sizeof(double) * R, cudaMemcpyHostToDevice, h->stream));
+  return NDMG_OK;
+}
+
 int check_level(ndmg_t* h, int32_t& level, bool need_fine_transfer) {
   if (level == -1) level = h->K;
   if (level < 0 || level > h->K) return fail(h, NDMG_INVALID_ARG, "level out of range");
@@ -517,13 +612,15 @@ int cg_init(ndmg_t* h, CGState& S, const std::vector<double>& ff, const std::vec
   return cg_check(h, S, rr, tol, all_done);
 }
 
-// FP64 PCG preconditioned by one FP64 V-cycle
+// FP64 PCG preconditioned by one FP64 V-cycle.  The scalars alpha, beta
+// and rz live on the device (k_cg_scalars); each iteration reads back only
+// ||r||^2 (and the status word) for the convergence test.
 int pcg64(ndmg_t* h, const double* f, double* u, double tol, int maxit, int* iters, double* relres) {
   const int K = h->K, R = nrhs(h);
   const int64_t N = h->lv[K].N;
-  const int sm = h->sm_count;
+  const int sm = h->sm_count, nb = reduction_blocks(sm);
   double *r = h->w64[0], *z = h->w64[1], *p = h->w64[2], *q = h->w64[3];
-  std::vector<double> ff, rr, pq, rz_new, a, ab(2 * R);
+  std::vector<double> ff, rr, rz0;
   CGState S;
   bool all_done = false;
   int st;
@@ -535,38 +632,43 @@ int pcg64(ndmg_t* h, const double* f, double* u, double tol, int maxit, int* ite
   if (all_done) return NDMG_OK;
   cudaMemsetAsync(z, 0, sizeof(double) * N * R, h->stream);
   op_vcycle<double>(h, K, r, z, true);
-  if ((st = dot2<double>(h, N, r, z, (const double*)nullptr, (const double*)nullptr, S.rz, nullptr)) != NDMG_OK)
+  if ((st = dot2<double>(h, N, r, z, (const double*)nullptr, (const double*)nullptr, rz0, nullptr)) != NDMG_OK)
     return st;
+  if ((st = cg_push_state(h, rr, rz0, S.done)) != NDMG_OK) return st;
   NDMG_CK(cudaMemcpyAsync(p, z, sizeof(double) * N * R, cudaMemcpyDeviceToDevice, h->stream));
+  const CgScalars C = cg_scalars(h);
   for (int it = 1; it <= maxit; ++it) {
     op_apply<double>(h, K, p, q);
-    if ((st = dot2<double>(h, N, p, q, (const double*)nullptr, (const double*)nullptr, pq, nullptr)) != NDMG_OK)
-      return st;
-    if ((st = cg_alpha(h, S, pq, a)) != NDMG_OK) return st;
     {
-      const double* da = push_coef(h, SLOT_ALPHA, a);
-      Span sp(h, NDMG_K_BLAS, 6.0 * 8 * N * R);
-      launch_cg_update<double>(h->stream, sm, N, da, p, q, u, r, R);
+      Span sp(h, NDMG_K_BLAS, 2.0 * 8 * N * R, 2);
+      launch_dot2_partial<double>(h->stream, sm, N, p, q, nullptr, nullptr, h->red, R);
+      launch_cg_scalars(h->stream, CG_ALPHA, nb, h->red, C, false, h->status, R);
     }
-    if ((st = dot2<double>(h, N, r, r, (const double*)nullptr, (const double*)nullptr, rr, nullptr)) != NDMG_OK)
-      return st;
+    {
+      Span sp(h, NDMG_K_BLAS, 6.0 * 8 * N * R);
+      launch_cg_update<double>(h->stream, sm, N, C.alpha, p, q, u, r, R);
+    }
+    {
+      Span sp(h, NDMG_K_BLAS, 1.0 * 8 * N * R, 2);
+      launch_dot2_partial<double>(h->stream, sm, N, r, r, nullptr, nullptr, h->red, R);
+      launch_cg_scalars(h->stream, CG_RR, nb, h->red, C, false, h->status, R);
+    }
+    if ((st = cg_read_rr(h, rr)) != NDMG_OK) return st;
     *iters = it;
     if ((st = cg_check(h, S, rr, tol, &all_done)) != NDMG_OK) return st;
     *relres = max_of(S.relres);
     if (all_done) return NDMG_OK;
+    if ((st = cg_push_done(h, S.done)) != NDMG_OK) return st;
     cudaMemsetAsync(z, 0, sizeof(double) * N * R, h->stream);
     op_vcycle<double>(h, K, r, z, true);
-    if ((st = dot2<double>(h, N, r, z, (const double*)nullptr, (const double*)nullptr, rz_new, nullptr)) != NDMG_OK)
-      return st;
-    for (int i = 0; i < R; ++i) {
-      ab[2 * i] = 1.0;
-      ab[2 * i + 1] = (S.done[i] || S.rz[i] == 0.0) ? 0.0 : rz_new[i] / S.rz[i];
-      S.rz[i] = rz_new[i];
+    {
+      Span sp(h, NDMG_K_BLAS, 2.0 * 8 * N * R, 2);
+      launch_dot2_partial<double>(h->stream, sm, N, r, z, nullptr, nullptr, h->red, R);
+      launch_cg_scalars(h->stream, CG_BETA, nb, h->red, C, false, h->status, R);
     }
     {
-      const double* dab = push_coef(h, SLOT_AB, ab);
       Span sp(h, NDMG_K_BLAS, 3.0 * 8 * N * R);
-      launch_axpby<double>(h->stream, sm, N, dab, z, p, R);
+      launch_axpby<double>(h->stream, sm, N, C.ab, z, p, R);
     }
   }
   return fail(h, NDMG_NOT_CONVERGED, "PCG reached maxit");
@@ -637,8 +739,14 @@ int vcycle_f32_graph(ndmg_t* h) {
     h->launch_total = l0;
     h->vcycle_total = v0;
     if (e != cudaSuccess) {
+      // this stream cannot capture the V-cycle's launches: replay them
+      // directly from now on
       drop_graph(h);
-      return cuda_fail(h, e, "capturing the V-cycle graph");
+      cudaGetLastError();
+      h->use_graphs = false;
+      cudaMemsetAsync(z32, 0, sizeof(float) * N * R, h->stream);
+      op_vcycle<float>(h, K, r32, z32, true);
+      return NDMG_OK;
     }
   }
   NDMG_CK(cudaGraphLaunch(h->vgraph, h->stream));
@@ -666,20 +774,21 @@ int precondition_mixed(ndmg_t* h, const double* r, double* z, const std::vector<
     Span sp(h, NDMG_K_BLAS, 12.0 * N * R);
     launch_from_f32(h->stream, sm, N, d, z32, z, R);
   }
-  return mixed(h) ? check_status(h) : NDMG_OK;
+  return waits_on_device(h) ? check_status(h) : NDMG_OK;
 }
 
 // FP64 flexible PCG preconditioned by the float V-cycle (mixed handles):
 // r, p, q, u and every inner product stay in double; the preconditioner sees
 // r / ||r|| in float (keeps fp16 operands in range) and returns z in double.
 // beta = -a (q . z_new) / (r . z)_old (flexible form: the low-precision
-// V-cycle is symmetric only up to rounding).
+// V-cycle is symmetric only up to rounding).  The scalars live on the device
+// (k_cg_scalars); each iteration reads back only ||r||^2 and the status word.
 int pcg_mixed(ndmg_t* h, const double* f, double* u, double tol, int maxit, int* iters, double* relres) {
   const int K = h->K, R = nrhs(h);
   const int64_t N = h->lv[K].N;
-  const int sm = h->sm_count;
+  const int sm = h->sm_count, nb = reduction_blocks(sm);
   double *r = h->w64[0], *z = h->w64[1], *p = h->w64[2], *q = h->w64[3];
-  std::vector<double> ff, rr, pq, rz_new, qz, a, ab(2 * R), rn(R);
+  std::vector<double> ff, rr, rz0, rn(R);
   CGState S;
   bool all_done = false;
   int st;
@@ -691,57 +800,45 @@ int pcg_mixed(ndmg_t* h, const double* f, double* u, double tol, int maxit, int*
   if (all_done) return NDMG_OK;
   for (int i = 0; i < R; ++i) rn[i] = std::sqrt(rr[i]);
   if ((st = precondition_mixed(h, r, z, rn)) != NDMG_OK) return st;
-  if ((st = dot2<double>(h, N, r, z, (const double*)nullptr, (const double*)nullptr, S.rz, nullptr)) != NDMG_OK)
+  if ((st = dot2<double>(h, N, r, z, (const double*)nullptr, (const double*)nullptr, rz0, nullptr)) != NDMG_OK)
     return st;
+  if ((st = cg_push_state(h, rr, rz0, S.done)) != NDMG_OK) return st;
   NDMG_CK(cudaMemcpyAsync(p, z, sizeof(double) * N * R, cudaMemcpyDeviceToDevice, h->stream));
-  // per iteration: q = A p; (p.q); u, r update fused with (r.r) and the
-  // float right-hand side of the V-cycle (scaled by 1 / ||r|| of the previous
-  // iteration; the V-cycle is linear and the fp16 patch operands are rescaled
-  // per CTA, so any nearby scale serves); V-cycle; (r.z), (q.z) and
-  // p = z + beta p straight from the float V-cycle output
-  float *r32 = h->w32[4], *z32 = h->w32[5];
-  const int nb = reduction_blocks(sm);
-  double* out = h->red + 2 * (int64_t)nb * R;
-  std::vector<double> inv(R);
+  // per iteration: q = A p; alpha = rz / (p.q) and the scales 1 / ||r||,
+  // ||r|| of the current residual (device); u, r update fused with (r.r) and
+  // the float right-hand side of the V-cycle; the one read-back; V-cycle;
+  // (r.z), (q.z) and beta (device); p = z + beta p straight from the float
+  // V-cycle output
+  float* z32 = h->w32[5];
+  const CgScalars C = cg_scalars(h);
   for (int it = 1; it <= maxit; ++it) {
     op_apply<double>(h, K, p, q);
-    if ((st = dot2<double>(h, N, p, q, (const double*)nullptr, (const double*)nullptr, pq, nullptr)) != NDMG_OK)
-      return st;
-    if ((st = cg_alpha(h, S, pq, a)) != NDMG_OK) return st;
-    for (int i = 0; i < R; ++i) inv[i] = rn[i] > 0 ? 1.0 / rn[i] : 0.0;
     {
-      const double* da = push_coef(h, SLOT_ALPHA, a);
-      const double* dto = push_coef(h, SLOT_TO, inv);
-      Span sp(h, NDMG_K_BLAS, (6.0 * 8 + 4) * N * R, 2);
-      launch_cg_update_rr(h->stream, sm, N, da, p, q, u, r, dto, r32, h->red, out, R);
+      Span sp(h, NDMG_K_BLAS, 2.0 * 8 * N * R, 2);
+      launch_dot2_partial<double>(h->stream, sm, N, p, q, nullptr, nullptr, h->red, R);
+      launch_cg_scalars(h->stream, CG_ALPHA, nb, h->red, C, true, h->status, R);
     }
-    if ((st = read_sums(h, out, rr, nullptr, false)) != NDMG_OK) return st;
+    {
+      Span sp(h, NDMG_K_BLAS, (6.0 * 8 + 4) * N * R, 2);
+      launch_cg_update_rr_partial(h->stream, sm, N, C.alpha, p, q, u, r, C.sto, h->w32[4], h->red, R);
+      launch_cg_scalars(h->stream, CG_RR, nb, h->red, C, true, h->status, R);
+    }
+    if ((st = cg_read_rr(h, rr)) != NDMG_OK) return st;
     *iters = it;
     if ((st = cg_check(h, S, rr, tol, &all_done)) != NDMG_OK) return st;
     *relres = max_of(S.relres);
     if (all_done) return NDMG_OK;
-    // z = rn_old * z32 with z32 = V-cycle(r / rn_old)
+    if ((st = cg_push_done(h, S.done)) != NDMG_OK) return st;
+    // z = ||r_old|| z32 with z32 = V-cycle(r / ||r_old||)
     if ((st = vcycle_f32_graph(h)) != NDMG_OK) return st;
-    const double* dfrom = push_coef(h, SLOT_FROM, rn);
     {
       Span sp(h, NDMG_K_BLAS, (2.0 * 8 + 4) * N * R, 2);
-      launch_dot2_zf(h->stream, sm, N, r, q, z32, h->red, out, R);
-    }
-    if ((st = read_sums(h, out, rz_new, &qz, true)) != NDMG_OK) return st;
-    for (int i = 0; i < R; ++i) {  // z = rn_old * z32
-      rz_new[i] *= rn[i];
-      qz[i] *= rn[i];
-    }
-    for (int i = 0; i < R; ++i) rn[i] = std::sqrt(rr[i]);
-    for (int i = 0; i < R; ++i) {
-      ab[2 * i] = 1.0;
-      ab[2 * i + 1] = (S.done[i] || S.rz[i] == 0.0) ? 0.0 : -a[i] * qz[i] / S.rz[i];
-      S.rz[i] = rz_new[i];
+      launch_dot2_zf_partial(h->stream, sm, N, r, q, z32, h->red, R);
+      launch_cg_scalars(h->stream, CG_BETA_FLEX, nb, h->red, C, true, h->status, R);
     }
     {
-      const double* dab = push_coef(h, SLOT_AB, ab);
       Span sp(h, NDMG_K_BLAS, (2.0 * 8 + 4) * N * R);
-      launch_axpby_zf(h->stream, sm, N, dfrom, z32, dab, p, R);
+      launch_axpby_zf(h->stream, sm, N, C.sfrom, z32, C.ab, p, R);
     }
   }
   return fail(h, NDMG_NOT_CONVERGED, "PCG reached maxit");
@@ -764,7 +861,7 @@ int pcg32(ndmg_t* h, const float* b, float* d, double tol, int maxit, int* iters
   NDMG_CK(cudaMemcpyAsync(r, b, sizeof(float) * N * R, cudaMemcpyDeviceToDevice, h->stream));
   cudaMemsetAsync(z, 0, sizeof(float) * N * R, h->stream);
   op_vcycle<float>(h, K, r, z, true);
-  if (mixed(h) && (st = check_status(h)) != NDMG_OK) return st;
+  if (waits_on_device(h) && (st = check_status(h)) != NDMG_OK) return st;
   if ((st = dot2<float>(h, N, b, b, r, z, bb, &S.rz)) != NDMG_OK) return st;
   std::vector<double> rz0 = S.rz;
   if ((st = cg_init(h, S, bb, bb, 2.0, &all_done)) != NDMG_OK) return st;   // relres = 1 < 2: none done
@@ -788,7 +885,7 @@ int pcg32(ndmg_t* h, const float* b, float* d, double tol, int maxit, int* iters
     if (all_done) return NDMG_OK;
     cudaMemsetAsync(z, 0, sizeof(float) * N * R, h->stream);
     op_vcycle<float>(h, K, r, z, true);
-    if (mixed(h) && (st = check_status(h)) != NDMG_OK) return st;
+    if (waits_on_device(h) && (st = check_status(h)) != NDMG_OK) return st;
     if ((st = dot2<float>(h, N, r, z, q, z, rz_new, &qz)) != NDMG_OK) return st;
     for (int i = 0; i < R; ++i) {
       ab[2 * i] = 1.0;
@@ -881,6 +978,8 @@ void free_handle(ndmg_t* h) {
     cudaFree(L.AinvT64); cudaFree(L.AinvT32); cudaFree(L.Dv64); cudaFree(L.Dv32);
     cudaFree(L.De64); cudaFree(L.De32);
     cudaFree(L.Wtc);
+    cudaFree(L.Wcell);
+    cudaFree(L.Wv32);
     cudaFree(L.Wg64); cudaFree(L.WgT64); cudaFree(L.Wg32); cudaFree(L.WgT32);
   }
   cudaFree(h->Ainv0);
@@ -888,9 +987,12 @@ void free_handle(ndmg_t* h) {
   cudaFree(h->red);
   cudaFree(h->umax);
   cudaFree(h->coef);
+  cudaFree(h->cg);
   cudaFree(h->status);
+  cudaFree(h->coarse_count);
   if (h->red_host) cudaFreeHost(h->red_host);
   if (h->coef_host) cudaFreeHost(h->coef_host);
+  if (h->cg_host) cudaFreeHost(h->cg_host);
   if (h->status_host) cudaFreeHost(h->status_host);
   for (int c = 0; c < NDMG_K_COUNT; ++c)
     for (auto& pr : h->ev_used[c]) h->ev_free.push_back(pr);
@@ -953,6 +1055,7 @@ int build_operators(ndmg_t* h) {
     }
     NDMG_CK(upload(&L.Dv64, ops.Dv));
     NDMG_CK(upload(&L.Dv32, ops.Dv));
+    NDMG_CK(upload(&L.Wv32, ops.Wv));
     std::vector<double> de;
     for (int d = 0; d < 3; ++d) de.insert(de.end(), ops.De[d].begin(), ops.De[d].end());
     NDMG_CK(upload(&L.De64, de));
@@ -960,6 +1063,9 @@ int build_operators(ndmg_t* h) {
     if (mixed(h)) {
       cudaError_t e = upload_tc_operand(&L.Wtc, ops.Wv, fp16);
       if (e != cudaSuccess) return cuda_fail(h, e, "upload_tc_operand");
+      const std::vector<uint8_t> img = tc_cell_image(ops.Wv, fp16);
+      if (!L.Wcell) NDMG_CK(cudaMalloc(&L.Wcell, img.size()));
+      NDMG_CK(cudaMemcpy(L.Wcell, img.data(), img.size(), cudaMemcpyHostToDevice));
     }
   }
   NDMG_CK(upload(&h->Ainv0, inv));
@@ -1149,9 +1255,11 @@ int ndmg_create(const ndmg_opts* o, ndmg_t** out) {
   h->red = dev_alloc<double>(2 * (int64_t)reduction_blocks(h->sm_count) * R + 2 * R + 8, &ae);
   h->umax = dev_alloc<unsigned long long>(R, &ae);
   h->coef = dev_alloc<double>(4 * 2 * R, &ae);
+  h->cg = dev_alloc<double>(8 * R, &ae);
   h->status = dev_alloc<int>(4, &ae);
   if (ae == cudaSuccess) ae = cudaMallocHost((void**)&h->red_host, (2 * R + 8) * sizeof(double));
   if (ae == cudaSuccess) ae = cudaMallocHost((void**)&h->coef_host, 4 * 2 * R * sizeof(double));
+  if (ae == cudaSuccess) ae = cudaMallocHost((void**)&h->cg_host, 3 * R * sizeof(double));
   if (ae == cudaSuccess) ae = cudaMallocHost((void**)&h->status_host, 4 * sizeof(int));
   if (ae == cudaSuccess) ae = cudaMemset(h->status, 0, 4 * sizeof(int));
   if (ae == cudaSuccess) ae = prepare_stencil<double>();
@@ -1161,6 +1269,21 @@ int ndmg_create(const ndmg_opts* o, ndmg_t** out) {
   if (ae == cudaSuccess && h->o.subdomain == 4) ae = prepare_patch_gram<double>();
   if (ae == cudaSuccess && h->o.subdomain == 4) ae = prepare_patch_gram<float>();
   if (ae == cudaSuccess && mixed(h)) ae = prepare_tc_patch();
+  if (ae == cudaSuccess && mixed(h)) ae = prepare_tc_cell();
+  // small levels in one persistent kernel: levels 1 .. Kc with n <= 32
+  // (constant coefficient, vertex smoother, subdomain 2, coarsest <= 4^3)
+  if (ae == cudaSuccess && h->o.smoother == NDMG_SMOOTHER_VERTEX && h->o.subdomain == 2 && h->lv[0].N <= 108) {
+    int Kc = 0;
+    while (Kc + 1 <= K && Kc + 1 <= kCoarseMaxLevels && h->lv[Kc + 1].n <= kCoarseMaxN) ++Kc;
+    if (Kc > 0) {
+      ae = prepare_coarse_cycle();
+      if (ae == cudaSuccess) h->coarse_count = dev_alloc<unsigned>(1, &ae);
+      if (ae == cudaSuccess) {
+        h->coarse_grid = coarse_cycle_grid(h->sm_count, Kc);
+        h->Kc = h->coarse_grid > 0 ? Kc : 0;
+      }
+    }
+  }
   if (ae == cudaSuccess) ae = prepare_stencil_field<double>();
   if (ae == cudaSuccess) ae = prepare_stencil_field<float>();
   if (ae == cudaSuccess) ae = prepare_patch_grouped<double>();
@@ -1296,29 +1419,65 @@ int ndmg_autotune(ndmg_t* h, int32_t* choices) {
   // MIXED modes, vertex smoother: tensor-core kernel or FP32 CUDA-core kernels
   // per level (small levels have too few bricks to fill the GPU)
   const bool tc_choice = mixed(h) && !edge_smoother(h) && h->o.subdomain == 2;
+  // (the tensor-core kernel also for each number of cell layers per work
+  // item: 0 = its own balance model, then powers of two up to n_k / 2)
+  auto time_smoother = [&](int k, float* ms) -> int {
+    op_smoother<float>(h, k, h->w32[0], h->w32[1]);  // warm-up
+    cudaEventRecord(e0, h->stream);
+    for (int rep = 0; rep < kTuneReps; ++rep) op_smoother<float>(h, k, h->w32[0], h->w32[1]);
+    cudaEventRecord(e1, h->stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(ms, e0, e1) != cudaSuccess)
+      return fail(h, NDMG_CUDA_ERROR, "autotune timing");
+    return NDMG_OK;
+  };
   for (int k = 1; k <= h->K && st == NDMG_OK && tc_choice; ++k) {
     DevLevel& L = h->lv[k];
     float t_tc = 0.f, t_cc = 0.f;
-    for (int v = 0; v < 2 && st == NDMG_OK; ++v) {
-      L.tc = v == 0;
-      op_smoother<float>(h, k, h->w32[0], h->w32[1]);  // warm-up
-      cudaEventRecord(e0, h->stream);
-      for (int rep = 0; rep < kTuneReps; ++rep) op_smoother<float>(h, k, h->w32[0], h->w32[1]);
-      cudaEventRecord(e1, h->stream);
+    int best_z = 0;
+    L.tc = true;
+    for (int zl = 0; zl <= L.n / 2 && st == NDMG_OK; zl = zl == 0 ? 1 : 2 * zl) {
+      L.zlen = zl;
       float ms = 0.f;
-      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-        st = fail(h, NDMG_CUDA_ERROR, "autotune timing");
-        break;
+      st = time_smoother(k, &ms);
+      if (st == NDMG_OK && (zl == 0 || ms < t_tc)) {
+        t_tc = ms;
+        best_z = zl;
       }
-      (v == 0 ? t_tc : t_cc) = ms;
     }
+    L.zlen = best_z;
+    L.tc = false;
+    if (st == NDMG_OK) st = time_smoother(k, &t_cc);
     L.tc = !(t_cc < t_tc);
   }
-  for (int k = 0; k <= h->K && choices; ++k) choices[3 * k + 2] = mixed(h) && k >= 1 && h->lv[k].tc ? 1 : 0;
+  for (int k = 0; k <= h->K && choices; ++k) {
+    const DevLevel& L = h->lv[k];
+    choices[3 * k + 2] = mixed(h) && k >= 1 && L.tc ? (L.zlen > 0 ? L.zlen : L.n / 2 + 1) : 0;
+  }
+  // the small levels: one persistent launch or the separate launches
+  if (st == NDMG_OK && h->Kc > 0 && !h->field) {
+    const int kc = h->Kc;
+    float t_on = 0.f, t_off = 0.f;
+    for (int v = 0; v < 2 && st == NDMG_OK; ++v) {
+      h->coarse_on = v == 0;
+      auto cycle = [&] {
+        cudaMemsetAsync(h->lv[kc].z32, 0, sizeof(float) * h->lv[kc].N * R, h->stream);
+        op_vcycle<float>(h, kc, h->lv[kc].r32, h->lv[kc].z32, true);
+      };
+      cycle();
+      cudaEventRecord(e0, h->stream);
+      for (int rep = 0; rep < kTuneReps; ++rep) cycle();
+      cudaEventRecord(e1, h->stream);
+      float ms = 0.f;
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+        st = fail(h, NDMG_CUDA_ERROR, "autotune timing");
+      (v == 0 ? t_on : t_off) = ms;
+    }
+    h->coarse_on = !(t_off < t_on);
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st == NDMG_OK && cudaGetLastError() != cudaSuccess) st = fail(h, NDMG_CUDA_ERROR, "autotune launch");
-  if (st == NDMG_OK && mixed(h)) st = check_status(h);
+  if (st == NDMG_OK && waits_on_device(h)) st = check_status(h);
   return st;
 }
 
@@ -1392,7 +1551,7 @@ int ndmg_smooth(ndmg_t* h, int32_t level, int32_t dtype, const void* g, void* z,
   if (dtype == NDMG_F64) op_smooth_steps<double>(h, level, (const double*)g, (double*)z, steps);
   else op_smooth_steps<float>(h, level, (const float*)g, (float*)z, steps);
   NDMG_CK_LAUNCH();
-  return dtype == NDMG_F32 && mixed(h) ? check_status(h) : NDMG_OK;
+  return dtype == NDMG_F32 && waits_on_device(h) ? check_status(h) : NDMG_OK;
 }
 
 int ndmg_restrict(ndmg_t* h, int32_t level, int32_t dtype, const void* r_fine, void* g_coarse) {
@@ -1445,7 +1604,7 @@ int ndmg_vcycle(ndmg_t* h, int32_t dtype, const void* g, void* z) {
   if (dtype == NDMG_F64) op_vcycle<double>(h, h->K, (const double*)g, (double*)z);
   else op_vcycle<float>(h, h->K, (const float*)g, (float*)z);
   NDMG_CK_LAUNCH();
-  return dtype == NDMG_F32 && mixed(h) ? check_status(h) : NDMG_OK;
+  return dtype == NDMG_F32 && waits_on_device(h) ? check_status(h) : NDMG_OK;
 }
 
 int ndmg_solve(ndmg_t* h, const double* f, double* u, double tol, int32_t maxit, int32_t* iters, double* relres) {

@@ -953,6 +953,58 @@ __global__ void __launch_bounds__(256) k_grad_alpha_sum(int n, double h, const d
   block_sum_store<2>(v, partial + 2 * ((int64_t)blockIdx.y * gridDim.x + blockIdx.x));
 }
 
+// PCG scalars kept on the device (one block per right-hand side, which
+// first adds the block partial sums of one reduction in the layout of
+// k_dot2): the host then reads one residual norm per iteration instead of
+// three inner products.
+//   CG_ALPHA: p.q -> alpha = rz / p.q (0 for a converged right-hand side;
+//             a non-positive or non-finite curvature sets kStatusBreakdown);
+//             also sto = 1 / ||r||, sfrom = ||r|| from the last rr
+//   CG_RR:    rr = r.r
+//   CG_BETA:  r.z -> beta = rz_new / rz (textbook CG), rz = rz_new
+//   CG_BETA_FLEX: r.z32, q.z32 with z = sfrom z32 -> beta = -alpha q.z / rz
+//             (flexible form), rz = r.z
+//   CG_RZ:    rz = scale r.z (scale = sfrom for a float preconditioner, else 1)
+__global__ void k_cg_scalars(int mode, int nb, const double* __restrict__ partial, CgScalars S, int flex,
+                             int* __restrict__ status) {
+  partial += 2 * (int64_t)blockIdx.x * nb;
+  double v[2] = {0.0, 0.0};
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    v[0] += partial[2 * b];
+    v[1] += partial[2 * b + 1];
+  }
+  __shared__ double tot[2];
+  block_sum_store<2>(v, tot);
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const int i = blockIdx.x;
+  const double s0 = tot[0], s1 = tot[1];
+  const bool done = S.done[i] != 0.0;
+  if (mode == CG_ALPHA) {
+    double a = 0.0;
+    if (!done) {
+      if (s0 > 0.0 && isfinite(s0)) a = S.rz[i] / s0;
+      else atomicOr(status, kStatusBreakdown);
+    }
+    S.alpha[i] = a;
+    const double rn = sqrt(S.rr[i]);
+    S.sto[i] = rn > 0.0 ? 1.0 / rn : 0.0;
+    S.sfrom[i] = rn;
+  } else if (mode == CG_RR) {
+    S.rr[i] = s0;
+  } else if (mode == CG_BETA || mode == CG_BETA_FLEX) {
+    const double rz_new = mode == CG_BETA ? s0 : S.sfrom[i] * s0;
+    double b = 0.0;
+    if (!done && S.rz[i] != 0.0)
+      b = mode == CG_BETA ? rz_new / S.rz[i] : -S.alpha[i] * (S.sfrom[i] * s1) / S.rz[i];
+    S.rz[i] = rz_new;
+    S.ab[2 * i] = 1.0;
+    S.ab[2 * i + 1] = b;
+  } else {  // CG_RZ
+    S.rz[i] = (flex ? S.sfrom[i] : 1.0) * s0;
+  }
+}
+
 // y = a x + b y with (a, b) = ab[2 rhs], ab[2 rhs + 1]
 template <typename T>
 __global__ void __launch_bounds__(256) k_axpby(int64_t N, const double* __restrict__ ab, const T* __restrict__ x,
@@ -1279,6 +1331,24 @@ void launch_dot2(cudaStream_t s, int sm, int64_t N, const T* x, const T* y, cons
   k_finish2<<<R, 256, 0, s>>>(nb, partial, out);
 }
 
+template <typename T>
+void launch_dot2_partial(cudaStream_t s, int sm, int64_t N, const T* x, const T* y, const T* x2, const T* y2,
+                         double* partial, int R) {
+  k_dot2<T><<<dim3(reduction_blocks(sm), R), 256, 0, s>>>(N, x, y, x2, y2, partial);
+}
+template void launch_dot2_partial<double>(cudaStream_t, int, int64_t, const double*, const double*, const double*,
+                                          const double*, double*, int);
+
+void launch_cg_update_rr_partial(cudaStream_t s, int sm, int64_t N, const double* alpha, const double* p,
+                                 const double* q, double* u, double* r, const double* sto, float* g32,
+                                 double* partial, int R) {
+  k_cg_update_rr<<<dim3(reduction_blocks(sm), R), 256, 0, s>>>(N, alpha, p, q, u, r, sto, g32, partial);
+}
+void launch_dot2_zf_partial(cudaStream_t s, int sm, int64_t N, const double* x, const double* y, const float* z32,
+                            double* partial, int R) {
+  k_dot2_zf<<<dim3(reduction_blocks(sm), R), 256, 0, s>>>(N, x, y, z32, partial);
+}
+
 static inline dim3 blas_grid(int64_t N, int sm, int R) {
   const int per = R > 1 ? 2 : 8;
   return dim3(grid_for(N, sm, per), R);
@@ -1358,6 +1428,11 @@ void launch_patch_grouped(cudaStream_t s, int sm, int n, const PatchFamily& fam,
   if (blocks > nchunks) blocks = nchunks;
   k_patch_grouped<T, kGroupPB><<<dim3(blocks, R), 128, patch_grouped_smem<T>(fam.nloc), s>>>(
       n, fam, Dtab, chunks, nchunks, plist, (T)eta, r, z);
+}
+
+void launch_cg_scalars(cudaStream_t s, int mode, int nb, const double* partial, const CgScalars& S, bool flex,
+                       int* status, int R) {
+  k_cg_scalars<<<R, 256, 0, s>>>(mode, nb, partial, S, flex ? 1 : 0, status);
 }
 
 void launch_grad_alpha_sum(cudaStream_t s, int sm, int n, double h, const double* lam, const double* u,

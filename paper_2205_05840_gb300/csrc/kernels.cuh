@@ -75,6 +75,19 @@ void launch_grad_cells(cudaStream_t s, int sm, int n, double h, const double* la
 void launch_grad_alpha_sum(cudaStream_t s, int sm, int n, double h, const double* lam, const double* u,
                            const double* acell, double* partial, double* out, int R);
 int reduction_blocks(int sm);
+// PCG scalars on the device from the block partial sums of one reduction
+// (modes CgMode; flex: the preconditioned residual is sfrom * z32)
+void launch_cg_scalars(cudaStream_t s, int mode, int nb, const double* partial, const CgScalars& S, bool flex,
+                       int* status, int R);
+// reductions that leave their block partial sums for launch_cg_scalars
+template <typename T>
+void launch_dot2_partial(cudaStream_t s, int sm, int64_t N, const T* x, const T* y, const T* x2, const T* y2,
+                         double* partial, int R);
+void launch_cg_update_rr_partial(cudaStream_t s, int sm, int64_t N, const double* alpha, const double* p,
+                                 const double* q, double* u, double* r, const double* sto, float* g32,
+                                 double* partial, int R);
+void launch_dot2_zf_partial(cudaStream_t s, int sm, int64_t N, const double* x, const double* y, const float* z32,
+                            double* partial, int R);
 template <typename T>
 void launch_dot2(cudaStream_t s, int sm, int64_t N, const T* x, const T* y, const T* x2, const T* y2,
                  double* partial, double* out, int R);

@@ -93,6 +93,15 @@ std::vector<double> coarse_inverse_cells(int n0, double L, const std::vector<dou
 void group_chunks(const GroupedFamily& g, int pb, std::vector<int>* plist, std::vector<int>* chunks);
 
 // ---- device side -----------------------------------------------------------
+// bits of the handle's device status word
+constexpr int kStatusBreakdown = 64;     // PCG met a non-positive or non-finite curvature p^T A p
+
+// PCG scalars on the device, R entries each (ab: 2 per right-hand side)
+struct CgScalars {
+  double *alpha, *ab, *sto, *sfrom, *rz, *rr, *done;
+};
+enum CgMode { CG_ALPHA = 0, CG_RR = 1, CG_BETA = 2, CG_BETA_FLEX = 3, CG_RZ = 4 };
+
 // a grouped family on the device (coefficient field)
 struct DevGrouped {
   int nchunks = 0;
@@ -120,6 +129,9 @@ struct DevLevel {
   double* De64 = nullptr;     // 3 * 42*42 (edge-based smoother)
   float* De32 = nullptr;
   void* Wtc = nullptr;        // tensor-core operand images (bf16/fp16), see tc kernel
+  void* Wcell = nullptr;      // the same factor in the per-neighbour blocks of the cell-owned kernel (tc_cell.cu)
+  float* Wv32 = nullptr;      // the Gram factor W (108 x 60, FP32) for the persistent small-level kernel
+  int zlen = 0;               // cell-owned smoother: cell layers per work item (ndmg_autotune; 0 = built-in)
   // subdomain size 4: Gram factor of the 1176-edge vertex patches (1176 x 312)
   // and its transpose, for k_patch_gram
   double *Wg64 = nullptr, *WgT64 = nullptr;
@@ -153,7 +165,15 @@ struct ndmg_handle {
   double* red_host = nullptr;             // pinned mirror of the results (2 per right-hand side)
   double* coef = nullptr;                 // per-right-hand-side BLAS scalars (4 slots x 2R)
   double* coef_host = nullptr;            // pinned staging of those scalars
+  double* cg = nullptr;                   // device PCG scalars (CgScalars, 8 R doubles)
+  double* cg_host = nullptr;              // pinned: rr read back, done flags pushed (2 R doubles)
   int* status = nullptr;                  // device status word (timeouts)
+  // persistent kernel for the small levels of the float V-cycle (coarse_cycle.cu):
+  // levels 1 .. Kc (n <= 32) and the coarsest in one cooperative launch
+  int Kc = 0;                             // 0: not available for this handle
+  int coarse_grid = 0;                    // CTAs of its cooperative grid
+  bool coarse_on = true;                  // ndmg_autotune may prefer the separate launches
+  unsigned* coarse_count = nullptr;       // its grid-barrier counter
   unsigned long long* umax = nullptr;     // per right-hand side max |u| of the fixed-point FP64 stencil
   int* status_host = nullptr;             // pinned mirror of the status word
   std::string err;

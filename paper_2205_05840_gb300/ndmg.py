@@ -295,7 +295,8 @@ class Solver:
 
     def autotune(self):
         """Pick launch shapes by timing (ndmg_autotune); returns {level:
-        (stencil planes per CTA for float, for double, tensor-core smoother 0/1)}."""
+        (stencil planes per CTA for float, for double, tensor-core smoother:
+        0 = CUDA cores, else its cell layers per work item)}."""
         out = (_i32 * (3 * self.num_levels))()
         self._check(_lib.ndmg_autotune(self._h, out), "autotune")
         return {k: (out[3 * k], out[3 * k + 1], out[3 * k + 2]) for k in range(self.num_levels)}

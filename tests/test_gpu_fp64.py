@@ -163,6 +163,28 @@ def test_vcycle_iterates_parity(n, n0, alpha, m):
         assert rel(N(zt), z) < tol, it
 
 
+@pytest.mark.parametrize("alpha", [0.01, 1.0, 100.0])
+def test_vcycle_iterates_parity_64(alpha):
+    # config 2's grid: 64^3 coarsening to 4^3, subdomain size 2, seeded load;
+    # three standalone V-cycle iterates against the oracle's.  The measured
+    # deviation is printed (run with -s) beside the bound it is held to
+    n, n0 = 64, 4
+    S = ndmg.Solver(n, n_coarsest=n0, alpha=alpha, m=2)
+    H = mg.Hierarchy(n, 1.0, alpha, 1.0, n0=n0, m=2)
+    f = inputs.random_load(n, 0)
+    z = np.zeros_like(f)
+    zt = T(z)
+    ft = T(f)
+    tol = patch_tol(n, alpha, 1e-10)
+    errs = []
+    for it in range(3):
+        z = H.vcycle(f, z)
+        S.vcycle(ft, zt)
+        errs.append(rel(N(zt), z))
+    print(f"\n64^3 alpha={alpha}: per-iterate relative deviation {['%.2e' % e for e in errs]} (bound {tol:.2e})")
+    assert max(errs) < tol, errs
+
+
 def test_config1_standalone_vcycle_iteration():
     # unit cube 8^3, alpha = 1, seed-0 load, 8->4->2, m = 2: cycles to 1e-8 equal the oracle's
     H = mg.Hierarchy(8, 1.0, 1.0, 1.0, n0=2, m=2)

@@ -12,6 +12,7 @@ conditioned patches and grows with the patch condition (cond ~ alpha/h^2):
 the FP64 path does.
 """
 import numpy as np
+import scipy.linalg as sla
 import pytest
 import torch
 
@@ -66,6 +67,71 @@ def test_tc_smoothing_step(prec, n, n0, alpha):
     S.smooth(T(g), zt, steps=1, level=-1)
     got = N(zt) - z
     assert rel(got, corr) < 16 * U[prec]
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+@pytest.mark.parametrize("n", [64, 128])
+def test_tc_smoothing_step_sampled_cells(prec, n):
+    # one tensor-core smoothing step at 64^3 and 128^3 against the oracle on
+    # every edge of sampled coarse cells: the domain faces, the borders of the
+    # kernel's 14-cell column tiles (13|14, 27|28, ...) and random cells.  The
+    # oracle's patch and interior operators come from an 8^3 grid with the same
+    # h (every interior patch matrix is the same), the residual from its
+    # element-by-element rows
+    nc = n // 2
+    h = 1.0 / n
+    S = ndmg.Solver(n, n_coarsest=4, precision=prec_code(prec))
+    rng = np.random.default_rng(n + 1)
+    Nn = hcurl.num_edges(n)
+    g = rng.standard_normal(Nn).astype(np.float32).astype(np.float64)
+    z = rng.standard_normal(Nn).astype(np.float32).astype(np.float64)
+    zt = T(z)
+    S.smooth(T(g), zt, steps=1, level=-1)
+    got = N(zt) - z
+    small = mg.Smoother(hcurl.assemble(8, 8 * h, 1.0, 1.0), 8, "vertex")
+    (pidx8, patch), = small.patches
+    cT = small.cT
+    # local numbering of a patch / interior space: the small grid's first
+    # patch and block, shifted to the vertex / cell of interest
+    d8, i8, j8, k8 = hcurl.edge_coords_of(8, pidx8[0])
+    bub8 = mg.bubble_sets(8)[0]
+    db, ib, jb, kb = hcurl.edge_coords_of(8, bub8)
+    edges_of = lambda d, i, j, k: hcurl.edge_index(n, d, i, j, k)
+    border = sorted({0, 1, nc - 2, nc - 1} | {c for q in range(1, nc // 14 + 1) for c in (14 * q - 1, 14 * q)
+                                              if c < nc})
+    cells = [(cx, cy, cz) for cx in border[::2] for cy in border[1::2] for cz in (0, nc // 2, nc - 1)]
+    cells += [tuple(rng.integers(0, nc, 3)) for _ in range(12)]
+    want, have = [], []
+    for (cx, cy, cz) in cells:
+        own = {}
+        for d in range(3):
+            for c in range(2):
+                for b in range(2):
+                    for a in range(2):
+                        e = edges_of(d, 2 * cx + a, 2 * cy + b, 2 * cz + c)
+                        if e >= 0:
+                            own[int(e)] = 0.0
+        keys = np.array(list(own))
+        # vertex patches containing the cell's edges: V in C + {0, 1}^3, interior
+        for V in [(cx + a, cy + b, cz + c) for c in range(2) for b in range(2) for a in range(2)]:
+            if min(V) < 1 or max(V) > nc - 1:
+                continue
+            sh = 2 * (np.array(V) - 1)   # the small grid's first patch sits at vertex (1, 1, 1)
+            rows = edges_of(d8, i8 + sh[0], j8 + sh[1], k8 + sh[2])
+            rv = g[rows] - hcurl.apply_rows(n, 1.0, 1.0, 1.0, z, rows)
+            y = patch.apply(rv[:, None])[:, 0]
+            for e, val in zip(rows, y):
+                if int(e) in own:
+                    own[int(e)] += val
+        # interior space of the cell itself
+        rows = edges_of(db, ib + 2 * cx, jb + 2 * cy, kb + 2 * cz)
+        rv = g[rows] - hcurl.apply_rows(n, 1.0, 1.0, 1.0, z, rows)
+        for e, val in zip(rows, sla.cho_solve(cT, rv)):
+            own[int(e)] += val
+        want.extend(small.eta * own[int(e)] for e in keys)
+        have.extend(got[keys])
+    want, have = np.array(want), np.array(have)
+    assert rel(have, want) < 16 * U[prec]
 
 
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
@@ -169,21 +235,27 @@ def test_graph_replay_matches_direct_launches(prec):
     # the mixed solve replays its float V-cycle as a CUDA graph; direct
     # launches give the same iteration count and launch / V-cycle counters,
     # solutions agree to the solve tolerance (FP32 atomics make the last bits
-    # run-dependent), and traced kernel times are collected from the replays
-    n = 32
+    # run-dependent), and traced kernel times are collected from the replays.
+    # 64^3: the finest level smooths on tensor cores, the levels <= 32^3 run in
+    # the persistent small-level kernel (one launch per V-cycle, traced too)
+    n = 64
     f = torch.tensor(inputs.random_load(n, 3), dtype=torch.float64, device=DEV)
     out = {}
     for graphs in (False, True):
         S = ndmg.Solver(n, n_coarsest=4, precision=prec_code(prec))
         S.use_graphs(graphs)
         S.trace(ndmg.K_PATCH, True)
+        S.trace(ndmg.K_COARSE, True)
         S.trace_read(ndmg.K_PATCH)
+        S.trace_read(ndmg.K_COARSE)
         u = torch.zeros_like(f)
         l0, v0 = S.counters()
         st, it, rr = S.solve(f, u, tol=1e-10)
         l1, v1 = S.counters()
         n_l, ms, units = S.trace_read(ndmg.K_PATCH)
+        n_c, ms_c, _ = S.trace_read(ndmg.K_COARSE)
         assert rr <= 1e-10 and n_l > 0 and ms > 0 and units > 0
+        assert n_c == v1 - v0 and ms_c > 0            # one small-level launch per V-cycle
         out[graphs] = (it, l1 - l0, v1 - v0, n_l, units, u.cpu().numpy())
     a, b = out[False], out[True]
     assert abs(a[0] - b[0]) <= 1                      # iterations (last-bit effects only)
@@ -235,7 +307,10 @@ def test_autotune_changes_launch_shapes_not_results():
         nl = 4 << lv
         for c in (cf, cd):
             assert c >= 1 and c <= nl and (c & (c - 1)) == 0
-        assert tc in (0, 1) and (lv > 0 or tc == 0)
+        # 0: CUDA-core smoother; else the tensor-core kernel's cell layers per
+        # work item (a power of two up to n / 2, or n / 2 + 1 for its own model)
+        assert (lv > 0 or tc == 0) and 0 <= tc <= nl // 2 + 1
+        assert tc in (0, nl // 2 + 1) or (tc & (tc - 1)) == 0
     for (dt, lv), (x, g, r0) in res.items():
         r = torch.empty_like(x)
         S.residual(g, x, r, level=lv)
