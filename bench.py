@@ -422,10 +422,12 @@ BATCH_RHS = 32
 BATCH_ALPHA = 1e-2 ** 2 / 4.0
 
 
-def time_solves(ndmg, inputs, torch, dev, prec, alpha, nrhs, rank, reps=2, field=None):
+def time_solves(ndmg, inputs, torch, dev, prec, alpha, nrhs, rank, reps=2, field=None, patch_roof=False):
     """Time-to-1e-8 of `reps` solves of nrhs right-hand sides at N_GRID^3
     (one warm-up solve first); CUDA events on the handle's stream.  field: a
-    curl-curl coefficient per hexahedron instead of alpha."""
+    curl-curl coefficient per hexahedron instead of alpha.  patch_roof: also
+    trace the smoother's patch solves over one more solve (their flops
+    against the measured CUDA-core FMA rate of the precision)."""
     stream = torch.cuda.Stream(device=dev)
     S = ndmg.Solver(N_GRID, n_coarsest=N_COARSEST, alpha=alpha, m=M_SMOOTH, precision=prec, nrhs=nrhs,
                     stream=stream)
@@ -457,11 +459,27 @@ def time_solves(ndmg, inputs, torch, dev, prec, alpha, nrhs, rank, reps=2, field
         b.synchronize()
         ms += a.elapsed_time(b)
     vc = (S.counters()[1] - v0) / reps
+    roof = None
+    if patch_roof:
+        S.trace_read(ndmg.K_PATCH)
+        S.trace(ndmg.K_PATCH, True)
+        with torch.cuda.stream(stream):
+            u.zero_()
+        S.solve(f, u, tol=TOL, maxit=500)
+        n_l, k_ms, flops = S.trace_read(ndmg.K_PATCH)
+        S.trace(ndmg.K_PATCH, False)
+        peak = ndmg.fma_rate_tflops(ndmg.F64 if prec == ndmg.PREC_FP64 else ndmg.F32)
+        ach = flops / (k_ms / 1e3) / 1e12
+        roof = {"kernel": "patch (dense 108 x 108 vertex operator per patch, CUDA cores)", "bound": "alu",
+                "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "peak_source": "measured (ndmg_probe_fma_rate)", "launches": n_l, "ms": k_ms}
     out = {"time_to_tol_ms": ms / reps, "vcycles": vc, "nrhs": nrhs,
            "alpha": alpha if field is None else "field", "relres": rr,
            "value": nrhs * Nd * vc / (ms / reps / 1e3), "unit": "DoF*cycles/s",
            "precision": {ndmg.PREC_FP64: "fp64", ndmg.PREC_FP32: "fp32", ndmg.PREC_MIXED_BF16: "bf16",
                          ndmg.PREC_MIXED_FP16: "fp16"}[prec]}
+    if roof:
+        out["roofline_patch"] = roof
     del S, f, u
     torch.cuda.empty_cache()
     return out
@@ -589,12 +607,15 @@ def run_ours(args):
     except OSError:
         pass
     hbm = peaks.get("hbm_gbs", 6800.0)
-    bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
-    if dom == "patch" and prec not in (ndmg.PREC_MIXED_BF16, ndmg.PREC_MIXED_FP16):
+    bf16 = peaks.get("bf16_tflops", 1900.0)            # burst: the kernels are timed launch by launch
+    fp64_peak = ndmg.fma_rate_tflops(ndmg.F64)         # measured CUDA-core FMA rates (ndmg_probe_fma_rate)
+    fp32_peak = ndmg.fma_rate_tflops(ndmg.F32)
+    mixed_prec = prec in (ndmg.PREC_MIXED_BF16, ndmg.PREC_MIXED_FP16)
+    if dom == "patch" and not mixed_prec:
         if prec == ndmg.PREC_FP64:
-            bound, peak, unit, scale = "alu", FP64_PEAK_TFLOPS, "TFLOP/s", 1e12
+            bound, peak, unit, scale = "alu", fp64_peak, "TFLOP/s", 1e12
         else:
-            bound, peak, unit, scale = "alu", FP32_PEAK_TFLOPS, "TFLOP/s", 1e12
+            bound, peak, unit, scale = "alu", fp32_peak, "TFLOP/s", 1e12
     else:
         bound, peak, unit, scale = "hbm", hbm, "GB/s", 1e9
     achieved = kd["units"] / (kd["ms"] / 1e3) / scale if kd["ms"] > 0 else 0.0
@@ -603,11 +624,37 @@ def run_ours(args):
             "frac": achieved / peak if peak else None, "traffic": traffic,
             "traffic_note": "DRAM bytes of one finest-level (128^3) launch from ncu; algorithmic bytes of that "
                             f"launch: {traffic_alg}" if traffic else "no capture of the current kernel source",
-            "peak_source": "MEASURED_PEAKS.json" if bound in ("hbm", "tensor") else "nominal (CUDA-core rate of the part)",
+            "peak_source": "MEASURED_PEAKS.json" if bound in ("hbm", "tensor") else "measured (ndmg_probe_fma_rate)",
             "launches": kd["launches"], "ms": kd["ms"],
             "timing": f"CUDA events around every launch of the class over {args.steps} further timed steps "
                       f"(same workload; {ms_traced / args.steps:.2f} ms per step with those events, "
-                      f"{ms_total / args.steps:.2f} ms without)"}
+                      f"{ms_total / args.steps:.2f} ms without)",
+            "cuda_core_peaks_tflops": {"fp64": fp64_peak, "fp32": fp32_peak}}
+    if dom == "patch" and mixed_prec:
+        # the same launches against the tensor pipe: 25,920 flops per vertex
+        # patch (Gram form W (W^t r_p)), 4 smoothing steps per level and V-cycle
+        patches = sum(max(0, (N_GRID >> k) // 2 - 1) ** 3 for k in range(0, 10) if (N_GRID >> k) >= 2 * N_COARSEST)
+        flops = 4 * patches * 25920.0 * vcyc_per_step * args.steps
+        tens = flops / (kd["ms"] / 1e3) / 1e12 if kd["ms"] > 0 else 0.0
+        roof["tensor"] = {"achieved": tens, "peak": bf16, "unit": "TFLOP/s", "frac": tens / bf16,
+                          "peak_source": "MEASURED_PEAKS.json bf16 burst (fp16 dense rate equal)",
+                          "flops": "25,920 per vertex patch"}
+        # the finest level alone: one smoothing step at 128^3, 20 launches
+        g32 = torch.tensor(inputs.random_load(N_GRID, seed=rank), dtype=torch.float32, device=dev)
+        z32 = torch.zeros_like(g32)
+        S.smooth(g32, z32, steps=1)
+        S.trace_read(dom_c)
+        S.trace(dom_c, True)
+        for _ in range(20):
+            S.smooth(g32, z32, steps=1)
+        n_l, k_ms, units = S.trace_read(dom_c)
+        S.trace(dom_c, False)
+        us = 1e3 * k_ms / n_l
+        pf = (N_GRID // 2 - 1) ** 3 * 25920.0
+        roof["finest_level"] = {"n": N_GRID, "us_per_launch": us, "GB_per_s": units / n_l / (us * 1e-6) / 1e9,
+                                "hbm_frac": units / n_l / (us * 1e-6) / 1e9 / hbm,
+                                "TFLOP_per_s": pf / (us * 1e-6) / 1e12, "tensor_frac": pf / (us * 1e-6) / 1e12 / bf16}
+        del g32, z32
 
     # end to end through the host-buffer entry point
     e2e_value = None
@@ -633,7 +680,8 @@ def run_ours(args):
     # (alpha = dt^2 / (4 mu), dt = 1e-2, mu = 1, mass coefficient 1)
     extra = {}
     if not args.no_extra:
-        extra["fp64"] = time_solves(ndmg, inputs, torch, dev, ndmg.PREC_FP64, ALPHA, 1, rank, reps=2)
+        extra["fp64"] = time_solves(ndmg, inputs, torch, dev, ndmg.PREC_FP64, ALPHA, 1, rank, reps=2,
+                                    patch_roof=True)
         extra["batched"] = time_solves(ndmg, inputs, torch, dev, prec, BATCH_ALPHA, BATCH_RHS, rank, reps=2)
         # jumping coefficient: a cube of alpha = 10 (cells [32, 96)^3) in alpha = 1
         extra["field"] = time_solves(ndmg, inputs, torch, dev, prec, 1.0, 1, rank, reps=2,
@@ -685,8 +733,8 @@ def run_ours(args):
                           "parallelism": f"replicas{world}",
                           "autotuned": {str(N_COARSEST << k): {"stencil_planes_per_cta_f32": v[0],
                                                                "stencil_planes_per_cta_f64": v[1],
-                                                               "tensor_core_smoother": bool(v[2]),
-                                                               "smoother_cell_layers_per_item": v[2]}
+                                                               "smoother": ["cuda-core", "tensor-core brick",
+                                                                            "tensor-core cell rows"][v[2]]}
                                         for k, v in tuned.items()}},
                "time_to_tol_ms": ms_total / args.steps, "vcycles_per_solve": vcyc_per_step,
                "pcg_iterations": iters[-1][0], "final_relres": iters[-1][1],
@@ -698,11 +746,6 @@ def run_ours(args):
     if world > 1:
         dist.destroy_process_group()
 
-
-# nominal CUDA-core peaks for ALU-bound kernels (GB300: FP64 1.25 TFLOP/s as
-# stated for this part; FP32 from 152 SMs x 128 FMA/clk x 2 x 2.07 GHz)
-FP64_PEAK_TFLOPS = 1.25
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 def main():

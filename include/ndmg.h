@@ -164,18 +164,31 @@ int ndmg_grad_alpha_field(ndmg_t* h, const double* lambda, const double* u, doub
  * n_k; twenty launches each, CUDA events on the handle's stream, with the
  * handle's nrhs) and keeps the fastest; every choice computes bitwise the same
  * result.  On MIXED handles with the vertex smoother it also times, per level,
- * the tensor-core smoother for every number of cell layers per work item
- * (its own balance model, then 1, 2, 4, ... n_k / 2) and against the FP32
- * CUDA-core smoother (small levels have too little work to fill the GPU), and
- * keeps the fastest; the layer count does not change the result, the FP32
- * kernels are at least as accurate.  Synchronises the stream, overwrites the
- * handle's solver workspaces and drops a captured V-cycle graph.  choices:
- * NULL or a host array of 3 (K+1) ints, level-major: [3k] planes per CTA for
- * float, [3k+1] for double, [3k+2] 0 if level k smooths on CUDA cores, else
- * the cell layers per work item of the tensor-core smoother (n_k / 2 + 1:
- * its balance model's choice).
+ * the two tensor-core smoothers (per brick of 128 vertex patches; cell-owned
+ * rows, for every number of cell layers per work item: its own balance model,
+ * then 1, 2, 4, ... n_k / 2) and the FP32 CUDA-core smoother (small levels
+ * have too little work to fill the GPU), and keeps the fastest; the FP32
+ * kernels are at least as accurate.  It then times the levels n <= 32 in one
+ * persistent launch against separate launches and keeps the faster.
+ * Synchronises the stream, overwrites the handle's solver workspaces and
+ * drops a captured V-cycle graph.  choices: NULL or a host array of 3 (K+1)
+ * ints, level-major: [3k] planes per CTA for float, [3k+1] for double, [3k+2]
+ * the smoother of level k: 0 CUDA cores, 1 tensor cores per brick, 2 tensor
+ * cores on cell-owned rows.
  * Errors: INVALID_ARG, CUDA_ERROR, DEVICE_TIMEOUT. */
 int ndmg_autotune(ndmg_t* h, int32_t* choices);
+
+/* Chooses the smoother kernel of a level by hand (what ndmg_autotune decides
+ * by timing): kind 0 FP32 CUDA cores, 1 tensor cores per brick of 128 vertex
+ * patches, 2 tensor cores on cell-owned rows (both tensor-core kernels compute
+ * eq. (Preconditioner P) with the same operand precision; they differ in how
+ * the overlapping patch outputs are summed).  level: 1 .. K, or -1 for every
+ * level.  Kinds 1 and 2 need a MIXED handle with the vertex smoother and
+ * subdomain size 2.  level 0 instead selects how float V-cycles run the
+ * levels n <= 32 (when the handle has them): kind 1 in one persistent launch,
+ * 0 in separate launches per step.  Synchronises the stream and drops a captured V-cycle
+ * graph.  Errors: INVALID_ARG, CUDA_ERROR. */
+int ndmg_select_smoother(ndmg_t* h, int32_t level, int32_t kind);
 
 /* Number of levels K+1. */
 int ndmg_num_levels(const ndmg_t* h, int32_t* out);
@@ -315,6 +328,15 @@ int ndmg_inject_status(ndmg_t* h, int32_t code);
  * classes) and V-cycles MG(K, ., ., m) performed on the finest level.  Either
  * pointer may be NULL. */
 int ndmg_counters(const ndmg_t* h, int64_t* launches, int64_t* vcycles);
+
+/* Measured FMA rate of the CUDA cores of the current device (no counterpart
+ * in the paper; the roofline denominator of kernels bound by the FP64 or FP32
+ * pipe): *tflops = 2 x fused multiply-adds per second of many independent
+ * FMA chains (dtype NDMG_F64 or NDMG_F32), timed with CUDA events over five
+ * launches of ~50 ms total at the clocks the GPU runs (nothing is locked).
+ * Allocates and frees one element; synchronises the device's legacy stream.
+ * Errors: INVALID_ARG, CUDA_ERROR. */
+int ndmg_probe_fma_rate(int32_t dtype, double* tflops);
 
 /* ---- allocation-free inner product (no counterpart in the paper) ---------
  * out = x^T y in FP64 for n elements of type dtype (NDMG_F64 or NDMG_F32),

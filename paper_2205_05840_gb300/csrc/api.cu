@@ -314,7 +314,7 @@ void op_smoother<float>(ndmg_t* h, int k, const float* r, float* z) {
     op_edge_terms<float>(h, k, L.De32, r, z);
     return;
   }
-  if (mixed(h) && L.Wcell && L.tc) {
+  if (mixed(h) && L.tc && L.tc_kind == 2 && L.Wcell) {
     // vertex patches on tensor cores (Gram form W W^t, cell-owned rows:
     // shifted-row GEMMs, one writer per edge) and the interior 6x6 solves in
     // one persistent kernel.  Algorithmic bytes: read r, read and write z
@@ -323,6 +323,14 @@ void op_smoother<float>(ndmg_t* h, int k, const float* r, float* z) {
     Span sp(h, NDMG_K_PATCH, 12.0 * L.N * R);
     launch_tc_cell_smoother(h->stream, h->sm_count, L.n, L.Wcell, h->o.precision == NDMG_PREC_MIXED_FP16, L.AinvT32,
                             h->o.eta, r, z, h->status, R, L.zlen);
+    return;
+  }
+  if (mixed(h) && L.tc && L.Wtc) {
+    // the same on tensor cores per brick of 128 vertex patches (gathered
+    // operand, shared-memory accumulation, global reductions)
+    Span sp(h, NDMG_K_PATCH, 12.0 * L.N * R);
+    launch_tc_smoother(h->stream, L.n, L.Wtc, h->o.precision == NDMG_PREC_MIXED_FP16, L.AinvT32, h->o.eta, r, z,
+                       h->status, R);
     return;
   }
   {
@@ -401,10 +409,11 @@ void op_vcycle(ndmg_t* h, int k, const T* g, T* z, bool z_zero = false) {
   }
   op_residual<T>(h, k, g, z, r);
   {
-    Span sp(h, NDMG_K_RESTRICT, (double)sizeof(T) * (L.N + C.N) * R);
-    launch_restrict<T>(h->stream, h->sm_count, L.n, r, lv_g<T>(C), R);
+    // the restriction also zeroes the coarse solution (no memset between
+    // dependent launches)
+    Span sp(h, NDMG_K_RESTRICT, (double)sizeof(T) * (L.N + 2 * C.N) * R);
+    launch_restrict<T>(h->stream, h->sm_count, L.n, r, lv_g<T>(C), R, lv_z<T>(C));
   }
-  cudaMemsetAsync(lv_z<T>(C), 0, sizeof(T) * C.N * R, h->stream);
   op_vcycle<T>(h, k - 1, lv_g<T>(C), lv_z<T>(C), true);
   {
     Span sp(h, NDMG_K_PROLONG, (double)sizeof(T) * (2 * L.N + C.N) * R);
@@ -1277,7 +1286,7 @@ int ndmg_create(const ndmg_opts* o, ndmg_t** out) {
     while (Kc + 1 <= K && Kc + 1 <= kCoarseMaxLevels && h->lv[Kc + 1].n <= kCoarseMaxN) ++Kc;
     if (Kc > 0) {
       ae = prepare_coarse_cycle();
-      if (ae == cudaSuccess) h->coarse_count = dev_alloc<unsigned>(1, &ae);
+      if (ae == cudaSuccess) h->coarse_count = dev_alloc<unsigned>(64, &ae);   // counter, flag 128 B apart
       if (ae == cudaSuccess) {
         h->coarse_grid = coarse_cycle_grid(h->sm_count, Kc);
         h->Kc = h->coarse_grid > 0 ? Kc : 0;
@@ -1432,26 +1441,30 @@ int ndmg_autotune(ndmg_t* h, int32_t* choices) {
   };
   for (int k = 1; k <= h->K && st == NDMG_OK && tc_choice; ++k) {
     DevLevel& L = h->lv[k];
-    float t_tc = 0.f, t_cc = 0.f;
+    float t_cell = 0.f, t_brick = 0.f, t_cc = 0.f;
     int best_z = 0;
     L.tc = true;
+    L.tc_kind = 2;
     for (int zl = 0; zl <= L.n / 2 && st == NDMG_OK; zl = zl == 0 ? 1 : 2 * zl) {
       L.zlen = zl;
       float ms = 0.f;
       st = time_smoother(k, &ms);
-      if (st == NDMG_OK && (zl == 0 || ms < t_tc)) {
-        t_tc = ms;
+      if (st == NDMG_OK && (zl == 0 || ms < t_cell)) {
+        t_cell = ms;
         best_z = zl;
       }
     }
     L.zlen = best_z;
+    L.tc_kind = 1;
+    if (st == NDMG_OK) st = time_smoother(k, &t_brick);
     L.tc = false;
     if (st == NDMG_OK) st = time_smoother(k, &t_cc);
-    L.tc = !(t_cc < t_tc);
+    L.tc = !(t_cc < t_cell && t_cc < t_brick);
+    L.tc_kind = t_cell < t_brick ? 2 : 1;
   }
   for (int k = 0; k <= h->K && choices; ++k) {
     const DevLevel& L = h->lv[k];
-    choices[3 * k + 2] = mixed(h) && k >= 1 && L.tc ? (L.zlen > 0 ? L.zlen : L.n / 2 + 1) : 0;
+    choices[3 * k + 2] = mixed(h) && k >= 1 && L.tc ? L.tc_kind : 0;
   }
   // the small levels: one persistent launch or the separate launches
   if (st == NDMG_OK && h->Kc > 0 && !h->field) {
@@ -1479,6 +1492,31 @@ int ndmg_autotune(ndmg_t* h, int32_t* choices) {
   if (st == NDMG_OK && cudaGetLastError() != cudaSuccess) st = fail(h, NDMG_CUDA_ERROR, "autotune launch");
   if (st == NDMG_OK && waits_on_device(h)) st = check_status(h);
   return st;
+}
+
+int ndmg_select_smoother(ndmg_t* h, int32_t level, int32_t kind) {
+  if (!h) return NDMG_INVALID_ARG;
+  if (kind < 0 || kind > 2) return fail(h, NDMG_INVALID_ARG, "kind must be 0, 1 or 2");
+  if (level < -1 || level > h->K) return fail(h, NDMG_INVALID_ARG, "level out of range");
+  if (level == 0) {   // the small levels: one persistent launch (1) or separate launches (0)
+    if (kind == 2) return fail(h, NDMG_INVALID_ARG, "level 0 takes kind 0 or 1");
+    NDMG_CK(cudaStreamSynchronize(h->stream));
+    if (int st = collect_graph(h)) return st;
+    drop_graph(h);
+    h->coarse_on = kind == 1;
+    return NDMG_OK;
+  }
+  if (kind > 0 && (!mixed(h) || edge_smoother(h) || h->o.subdomain != 2))
+    return fail(h, NDMG_INVALID_ARG, "tensor-core smoothers need a MIXED handle with the vertex smoother, subdomain 2");
+  NDMG_CK(cudaStreamSynchronize(h->stream));
+  if (int st = collect_graph(h)) return st;
+  drop_graph(h);   // the graph holds the launches
+  for (int k = 1; k <= h->K; ++k) {
+    if (level != -1 && k != level) continue;
+    h->lv[k].tc = kind > 0;
+    if (kind > 0) h->lv[k].tc_kind = kind;
+  }
+  return NDMG_OK;
 }
 
 int ndmg_num_levels(const ndmg_t* h, int32_t* out) {

@@ -26,7 +26,7 @@
 namespace ndmg {
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
 constexpr int kWStride = 61;                 // W rows padded to an odd stride (conflict-free both ways)
 constexpr int kMaxN0 = 108;                  // coarsest level 4^3 at most
@@ -47,6 +47,7 @@ struct Args {
   Lv lv[kCoarseMaxLevels + 1];   // [0] coarsest (g, z only), [1 .. Kc]
   const double* Ainv0;           // N0 x N0 (symmetric)
   unsigned* count;               // barrier arrivals (0 at launch)
+  unsigned* flag;                // last barrier opened (0 at launch), another cache line
   int* status;
 };
 
@@ -55,10 +56,15 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 
-// Grid barrier number `*epoch` (0-based): the arrival counter only grows;
-// the barrier is complete when it reaches (epoch + 1) * gridDim.x.  Bounded:
-// returns false (status written) when the wait gives up.
+// Grid barrier number *epoch (1-based after the increment): every CTA adds
+// one to the arrival counter; the CTA that completes the count writes the
+// epoch to a release flag on another cache line, which the others poll (so
+// the polls never contend with the arrivals).  Bounded: returns false
+// (status written) when the wait gives up or another CTA already gave up.
 __device__ bool grid_barrier(const Args& A, unsigned* epoch) {
   __shared__ int ok_s;
   __syncthreads();
@@ -66,16 +72,20 @@ __device__ bool grid_barrier(const Args& A, unsigned* epoch) {
   if (threadIdx.x == 0) {
     const unsigned target = *epoch * gridDim.x;
     __threadfence();
-    atomicAdd(A.count, 1u);
+    const unsigned prev = atomicAdd(A.count, 1u);
     int ok = 1;
-    const long long t0 = clock64();
-    while (ld_acquire(A.count) < target) {
-      if (clock64() - t0 > kBarrierLimit || *reinterpret_cast<volatile int*>(A.status) != 0) {
-        ok = 0;
-        atomicCAS(A.status, 0, kTimeout);
-        break;
+    if (prev + 1 == target) {
+      st_release(A.flag, *epoch);
+    } else {
+      const long long t0 = clock64();
+      while (ld_acquire(A.flag) < *epoch) {
+        if (clock64() - t0 > kBarrierLimit || *reinterpret_cast<volatile int*>(A.status) != 0) {
+          ok = 0;
+          atomicCAS(A.status, 0, kTimeout);
+          break;
+        }
+        __nanosleep(32);
       }
-      __nanosleep(64);
     }
     __threadfence();
     ok_s = ok;
@@ -401,7 +411,7 @@ int coarse_cycle_grid(int sm_count, int Kc) {
           cudaSuccess ||
       per_sm < 1)
     return 0;
-  return sm_count * (per_sm < 2 ? per_sm : 2);
+  return sm_count;   // one CTA per SM: fewer arrivals per barrier
 }
 
 cudaError_t launch_coarse_cycle(cudaStream_t s, int grid, const CoarseLevel* lv, int Kc, int N0, const double* Ainv0,
@@ -430,8 +440,9 @@ cudaError_t launch_coarse_cycle(cudaStream_t s, int grid, const CoarseLevel* lv,
   a.lv[0].n = lv[0].n;
   a.Ainv0 = Ainv0;
   a.count = count;
+  a.flag = count + 32;
   a.status = status;
-  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned), s);
+  cudaError_t e = cudaMemsetAsync(count, 0, 64 * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);

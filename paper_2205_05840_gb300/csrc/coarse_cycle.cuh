@@ -21,7 +21,8 @@ cudaError_t prepare_coarse_cycle();
 int coarse_cycle_grid(int sm_count, int Kc);
 // z_Kc = MG(Kc, g_Kc, 0, m) of Fig. 1 over levels lv[Kc] .. lv[1] and the
 // coarsest level (g0, z0: N0 values per right-hand side, Ainv0 its inverse);
-// z_Kc must be zero on entry.  count: one device word (reset here), status:
+// z_Kc must be zero on entry.  count: 64 device words (barrier counter and
+// flag, reset here), status:
 // the handle's status word (a barrier that gives up writes 2 there).
 cudaError_t launch_coarse_cycle(cudaStream_t s, int grid, const CoarseLevel* lv, int Kc, int N0, const double* Ainv0,
                                 float* g0, float* z0, double eta, int m, int R, unsigned* count, int* status);

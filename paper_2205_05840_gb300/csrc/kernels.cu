@@ -5,6 +5,7 @@
 #include <type_traits>
 
 #include "kernels.cuh"
+#include "pdl.cuh"
 
 namespace ndmg {
 
@@ -125,6 +126,7 @@ __device__ __forceinline__ double fixed_to_double(long long x) {
 // must be 0 on entry
 __global__ void __launch_bounds__(256) k_absmax(int64_t N, const double* __restrict__ x,
                                                 unsigned long long* __restrict__ out) {
+  pdl_start();
   const double* xr = x + (int64_t)blockIdx.y * N;
   unsigned long long m = 0;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
@@ -151,6 +153,7 @@ __global__ void __launch_bounds__(kTX * kTY) k_stencil_stream(int n, int KZ, T c
                                                               const T* __restrict__ g, T* __restrict__ y,
                                                               const unsigned long long* __restrict__ umax,
                                                               const T* __restrict__ acell = nullptr) {
+  pdl_start();
   static_assert(sizeof(S) == sizeof(T), "staged planes hold T and are read as S");
   constexpr bool FX = !std::is_same<S, T>::value;
   static_assert(!(FX && FLD), "the coefficient field runs in the vector type's own arithmetic");
@@ -369,8 +372,12 @@ __global__ void __launch_bounds__(kTX * kTY) k_stencil_stream(int n, int KZ, T c
 // One thread per lattice point (i, j, k) of the output mesh handles the x-,
 // y- and z-edge that start there (when they are interior); blocks of 32 x 8
 // threads run along i, the grid's z index is k.
+// zc (optional): the coarse solution, set to 0 at the same entries (the
+// V-cycle recursion starts the coarse level from z = 0)
 template <typename T>
-__global__ void __launch_bounds__(256) k_restrict(int nf, const T* __restrict__ rf, T* __restrict__ gc) {
+__global__ void __launch_bounds__(256) k_restrict(int nf, const T* __restrict__ rf, T* __restrict__ gc,
+                                                  T* __restrict__ zc) {
+  pdl_start();
   const int nc = nf / 2;
   const int rhs = blockIdx.z / nc;
   const int I = blockIdx.x * 32 + threadIdx.x, J = blockIdx.y * 8 + threadIdx.y, K = blockIdx.z - rhs * nc;
@@ -379,6 +386,12 @@ __global__ void __launch_bounds__(256) k_restrict(int nf, const T* __restrict__ 
   const int64_t N3f = (int64_t)nf * (nf - 1) * (nf - 1);
   rf += (int64_t)rhs * 3 * N3f;
   gc += (int64_t)rhs * 3 * N3c;
+  if (zc) {
+    zc += (int64_t)rhs * 3 * N3c;
+    if (in_node(J, nc) && in_node(K, nc)) zc[off_x(nc, I, J, K)] = T(0);
+    if (in_node(I, nc) && in_node(K, nc)) zc[N3c + off_y(nc, I, J, K)] = T(0);
+    if (in_node(I, nc) && in_node(J, nc)) zc[2 * N3c + off_z(nc, I, J, K)] = T(0);
+  }
   const T w[3] = {T(0.5), T(1), T(0.5)};
   // coarse x-edge (I, J, K): fine x-edges 2I+a, 2J+b, 2K+c with weight w_b w_c
   if (in_node(J, nc) && in_node(K, nc)) {
@@ -431,6 +444,7 @@ struct Vec2<double> { using type = double2; };
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_prolong_add(int nf, const T* __restrict__ zc, T* __restrict__ zf) {
+  pdl_start();
   const int nc = nf / 2;
   const int rhs = blockIdx.z / nc;
   const int I = blockIdx.x * 32 + threadIdx.x, J = blockIdx.y * 8 + threadIdx.y, K = blockIdx.z - rhs * nc;
@@ -499,6 +513,7 @@ __device__ __forceinline__ int64_t edge_gidx(int n, int d, int i, int j, int k) 
 template <typename T>
 __global__ void __launch_bounds__(256) k_bubble(int n, const T* __restrict__ Ainv, T eta, const T* __restrict__ r,
                                                 T* __restrict__ z) {
+  pdl_start();
   const int nc = n / 2;
   const int64_t NT = (int64_t)nc * nc * nc;
   const int64_t N3 = (int64_t)n * (n - 1) * (n - 1);
@@ -540,6 +555,7 @@ __global__ void __launch_bounds__(256) k_bubble(int n, const T* __restrict__ Ain
 template <typename T, int PB>
 __global__ void __launch_bounds__(128) k_patch_dense(int n, PatchFamily fam, const T* __restrict__ D, T eta,
                                                      const T* __restrict__ r, T* __restrict__ z) {
+  pdl_start();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nl = fam.nloc;
   T* Ds = reinterpret_cast<T*>(smem_raw);          // nl * nl
@@ -606,6 +622,7 @@ template <typename T, int PB>
 __global__ void __launch_bounds__(256) k_patch_gram(int n, PatchFamily fam, int nG, const T* __restrict__ W,
                                                     const T* __restrict__ WT, T eta, const T* __restrict__ r,
                                                     T* __restrict__ z) {
+  pdl_start();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nl = fam.nloc;
   T* Rs = reinterpret_cast<T*>(smem_raw);           // nl * PB
@@ -686,6 +703,7 @@ __global__ void __launch_bounds__(256) k_patch_gram(int n, PatchFamily fam, int 
 template <typename T>
 __global__ void __launch_bounds__(256) k_bubble_grouped(int n, const T* __restrict__ Atab, const int* __restrict__ gid,
                                                         T eta, const T* __restrict__ r, T* __restrict__ z) {
+  pdl_start();
   const int nc = n / 2;
   const int64_t NT = (int64_t)nc * nc * nc;
   const int64_t N3 = (int64_t)n * (n - 1) * (n - 1);
@@ -725,6 +743,7 @@ __global__ void __launch_bounds__(128) k_patch_grouped(int n, PatchFamily fam, c
                                                        const int4* __restrict__ chunks, int nchunks,
                                                        const int* __restrict__ plist, T eta,
                                                        const T* __restrict__ r, T* __restrict__ z) {
+  pdl_start();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nl = fam.nloc;
   T* Ds = reinterpret_cast<T*>(smem_raw);          // nl * nl
@@ -825,6 +844,7 @@ __device__ __forceinline__ void cell_circulations(const double* __restrict__ x, 
 
 __global__ void __launch_bounds__(256) k_grad_cells(int n, double h, const double* __restrict__ lam,
                                                     const double* __restrict__ u, double* __restrict__ out) {
+  pdl_start();
   const int64_t N3 = (int64_t)n * (n - 1) * (n - 1);
   const int64_t NC = (int64_t)n * n * n;
   lam += (int64_t)blockIdx.y * 3 * N3;
@@ -857,6 +877,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 template <typename T>
 __global__ void __launch_bounds__(256) k_coarse(int N0, const double* __restrict__ Ainv, const T* __restrict__ g,
                                                 T* __restrict__ z) {
+  pdl_start();
   extern __shared__ double gs[];
   g += (int64_t)blockIdx.y * N0;
   z += (int64_t)blockIdx.y * N0;
@@ -905,6 +926,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_dot2(int64_t N, const T* __restrict__ x, const T* __restrict__ y,
                                               const T* __restrict__ x2, const T* __restrict__ y2,
                                               double* __restrict__ partial) {
+  pdl_start();
   const int64_t off = (int64_t)blockIdx.y * N;
   double v[2] = {0.0, 0.0};
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
@@ -915,6 +937,7 @@ __global__ void __launch_bounds__(256) k_dot2(int64_t N, const T* __restrict__ x
 }
 
 __global__ void k_finish2(int nb, const double* __restrict__ partial, double* __restrict__ out) {
+  pdl_start();
   partial += 2 * (int64_t)blockIdx.x * nb;
   double v[2] = {0.0, 0.0};
   for (int b = threadIdx.x; b < nb; b += blockDim.x) {
@@ -933,6 +956,7 @@ __global__ void __launch_bounds__(256) k_grad_alpha_sum(int n, double h, const d
                                                         const double* __restrict__ u,
                                                         const double* __restrict__ acell,
                                                         double* __restrict__ partial) {
+  pdl_start();
   const int64_t N3 = (int64_t)n * (n - 1) * (n - 1);
   const int64_t NC = (int64_t)n * n * n;
   lam += (int64_t)blockIdx.y * 3 * N3;
@@ -967,6 +991,7 @@ __global__ void __launch_bounds__(256) k_grad_alpha_sum(int n, double h, const d
 //   CG_RZ:    rz = scale r.z (scale = sfrom for a float preconditioner, else 1)
 __global__ void k_cg_scalars(int mode, int nb, const double* __restrict__ partial, CgScalars S, int flex,
                              int* __restrict__ status) {
+  pdl_start();
   partial += 2 * (int64_t)blockIdx.x * nb;
   double v[2] = {0.0, 0.0};
   for (int b = threadIdx.x; b < nb; b += blockDim.x) {
@@ -1009,6 +1034,7 @@ __global__ void k_cg_scalars(int mode, int nb, const double* __restrict__ partia
 template <typename T>
 __global__ void __launch_bounds__(256) k_axpby(int64_t N, const double* __restrict__ ab, const T* __restrict__ x,
                                                T* __restrict__ y) {
+  pdl_start();
   const int64_t off = (int64_t)blockIdx.y * N;
   const double a = ab[2 * blockIdx.y], b = ab[2 * blockIdx.y + 1];
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x)
@@ -1019,6 +1045,7 @@ __global__ void __launch_bounds__(256) k_axpby(int64_t N, const double* __restri
 template <typename T>
 __global__ void __launch_bounds__(256) k_axpby_scalar(int64_t N, double a, const T* __restrict__ x, double b,
                                                       T* __restrict__ y) {
+  pdl_start();
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x)
     y[e] = b == 0.0 ? (T)(a * (double)x[e]) : (T)(a * (double)x[e] + b * (double)y[e]);
 }
@@ -1027,6 +1054,7 @@ __global__ void __launch_bounds__(256) k_axpby_scalar(int64_t N, double a, const
 template <typename T>
 __global__ void __launch_bounds__(256) k_cg_update(int64_t N, const double* __restrict__ alpha, const T* __restrict__ p,
                                                    const T* __restrict__ q, T* __restrict__ u, T* __restrict__ r) {
+  pdl_start();
   const int64_t off = (int64_t)blockIdx.y * N;
   const double a = alpha[blockIdx.y];
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
@@ -1057,6 +1085,7 @@ __global__ void __launch_bounds__(256) k_cg_update_rr(int64_t N, const double* _
                                                       double* __restrict__ u, double* __restrict__ r,
                                                       const double* __restrict__ sto, float* __restrict__ g32,
                                                       double* __restrict__ partial) {
+  pdl_start();
   const int64_t off = (int64_t)blockIdx.y * N;
   const double a = alpha[blockIdx.y], s = sto[blockIdx.y];
   double v[2] = {0.0, 0.0};
@@ -1075,6 +1104,7 @@ __global__ void __launch_bounds__(256) k_cg_update_rr(int64_t N, const double* _
 // one per entry)
 __global__ void __launch_bounds__(256) k_dot2_zf(int64_t N, const double* __restrict__ x, const double* __restrict__ y,
                                                  const float* __restrict__ z32, double* __restrict__ partial) {
+  pdl_start();
   const int64_t off = (int64_t)blockIdx.y * N;
   double v[2] = {0.0, 0.0};
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
@@ -1088,6 +1118,7 @@ __global__ void __launch_bounds__(256) k_dot2_zf(int64_t N, const double* __rest
 // p = sc * z32 + b p with b = ab[2 rhs + 1]
 __global__ void __launch_bounds__(256) k_axpby_zf(int64_t N, const double* __restrict__ sc, const float* __restrict__ z32,
                                                   const double* __restrict__ ab, double* __restrict__ p) {
+  pdl_start();
   const int64_t off = (int64_t)blockIdx.y * N;
   const double s = sc[blockIdx.y], b = ab[2 * blockIdx.y + 1];
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x)
@@ -1097,6 +1128,7 @@ __global__ void __launch_bounds__(256) k_axpby_zf(int64_t N, const double* __res
 // dst (float) = s * src (double), s = sc[rhs]
 __global__ void __launch_bounds__(256) k_to_f32(int64_t N, const double* __restrict__ sc, const double* __restrict__ src,
                                                 float* __restrict__ dst) {
+  pdl_start();
   const int64_t off = (int64_t)blockIdx.y * N;
   const double s = sc[blockIdx.y];
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x)
@@ -1106,6 +1138,7 @@ __global__ void __launch_bounds__(256) k_to_f32(int64_t N, const double* __restr
 // dst (double) = s * src (float)
 __global__ void __launch_bounds__(256) k_from_f32(int64_t N, const double* __restrict__ sc, const float* __restrict__ src,
                                                   double* __restrict__ dst) {
+  pdl_start();
   const int64_t off = (int64_t)blockIdx.y * N;
   const double s = sc[blockIdx.y];
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x)
@@ -1115,6 +1148,7 @@ __global__ void __launch_bounds__(256) k_from_f32(int64_t N, const double* __res
 // dst (double) += s * src (float)
 __global__ void __launch_bounds__(256) k_add_f32(int64_t N, const double* __restrict__ sc, const float* __restrict__ src,
                                                  double* __restrict__ dst) {
+  pdl_start();
   const int64_t off = (int64_t)blockIdx.y * N;
   const double s = sc[blockIdx.y];
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x)
@@ -1164,12 +1198,12 @@ void launch_stencil(cudaStream_t s, int sm, int n, double cK, double cM, const T
   if (N == 0) return;
   if constexpr (std::is_same<T, double>::value) {
     cudaMemsetAsync(umax, 0, sizeof(unsigned long long) * R, s);
-    k_absmax<<<dim3(grid_for(N, sm, 4), R), 256, 0, s>>>(N, u, umax);
+    launch_pdl(k_absmax, dim3(grid_for(N, sm, 4), R), 256, 0, s, N, u, umax);
   }
   int KZ = 0;
   const dim3 grid = stencil_grid(n, sm, R, &KZ, kz);
-  k_stencil_stream<T, StencilArith<T>>
-      <<<grid, dim3(kTX, kTY), stencil_smem<T>(), s>>>(n, KZ, (T)cK, (T)cM, u, g, y, umax);
+  launch_pdl(k_stencil_stream<T, StencilArith<T>>, grid, dim3(kTX, kTY), stencil_smem<T>(), s, n, KZ, (T)cK, (T)cM, u, g,
+             y, (const unsigned long long*)umax, (const T*)nullptr);
 }
 
 // coefficient field: three more staged planes (the cell coefficients)
@@ -1188,8 +1222,7 @@ void launch_stencil_field(cudaStream_t s, int sm, int n, double cK, double cM, c
   if (n < 2) return;
   int KZ = 0;
   const dim3 grid = stencil_grid(n, sm, R, &KZ, kz);
-  k_stencil_stream<T, T, true>
-      <<<grid, dim3(kTX, kTY), stencil_field_smem<T>(), s>>>(n, KZ, (T)cK, (T)cM, u, g, y, nullptr, acell);
+  launch_pdl(k_stencil_stream<T, T, true>, grid, dim3(kTX, kTY), stencil_field_smem<T>(), s, n, KZ, (T)cK, (T)cM, u, g, y, nullptr, acell);
 }
 
 // grid z of the transfers = coarse planes x right-hand sides; batches whose
@@ -1198,14 +1231,15 @@ void launch_stencil_field(cudaStream_t s, int sm, int n, double cK, double cM, c
 constexpr int kMaxGridZ = 65535;
 
 template <typename T>
-void launch_restrict(cudaStream_t s, int, int nf, const T* rf, T* gc, int R) {
+void launch_restrict(cudaStream_t s, int, int nf, const T* rf, T* gc, int R, T* zc) {
   const int nc = nf / 2;
   if (nc < 2) return;
   const int64_t Nf = 3LL * nf * (nf - 1) * (nf - 1), Nc = 3LL * nc * (nc - 1) * (nc - 1);
   const int group = kMaxGridZ / nc;
   for (int r0 = 0; r0 < R; r0 += group) {
     const int rg = R - r0 < group ? R - r0 : group;
-    k_restrict<T><<<dim3((nc + 31) / 32, (nc + 7) / 8, nc * rg), dim3(32, 8), 0, s>>>(nf, rf + r0 * Nf, gc + r0 * Nc);
+    launch_pdl(k_restrict<T>, dim3((nc + 31) / 32, (nc + 7) / 8, nc * rg), dim3(32, 8), 0, s, nf, rf + r0 * Nf, gc + r0 * Nc,
+               zc ? zc + r0 * Nc : zc);
   }
 }
 
@@ -1217,7 +1251,7 @@ void launch_prolong_add(cudaStream_t s, int, int nf, const T* zc, T* zf, int R) 
   const int group = kMaxGridZ / nc;
   for (int r0 = 0; r0 < R; r0 += group) {
     const int rg = R - r0 < group ? R - r0 : group;
-    k_prolong_add<T><<<dim3((nc + 31) / 32, (nc + 7) / 8, nc * rg), dim3(32, 8), 0, s>>>(nf, zc + r0 * Nc,
+    launch_pdl(k_prolong_add<T>, dim3((nc + 31) / 32, (nc + 7) / 8, nc * rg), dim3(32, 8), 0, s, nf, zc + r0 * Nc,
                                                                                           zf + r0 * Nf);
   }
 }
@@ -1225,7 +1259,7 @@ void launch_prolong_add(cudaStream_t s, int, int nf, const T* zc, T* zf, int R) 
 template <typename T>
 void launch_bubble(cudaStream_t s, int sm, int n, const T* Ainv, double eta, const T* r, T* z, int R) {
   const int64_t nc = n / 2;
-  k_bubble<T><<<dim3(grid_for(nc * nc * nc, sm, 16), R), 256, 0, s>>>(n, Ainv, (T)eta, r, z);
+  launch_pdl(k_bubble<T>, dim3(grid_for(nc * nc * nc, sm, 16), R), 256, 0, s, n, Ainv, (T)eta, r, z);
 }
 
 constexpr int kPB64 = 8;
@@ -1252,7 +1286,7 @@ void launch_patch_dense(cudaStream_t s, int sm, int n, const PatchFamily& fam, c
   int64_t blocks = (NP + PB - 1) / PB;
   const int64_t cap = (int64_t)sm * 2;
   if (blocks > cap) blocks = cap;
-  k_patch_dense<T, PB><<<dim3((int)blocks, R), 128, patch_dense_smem<T>(fam.nloc), s>>>(n, fam, D, (T)eta, r, z);
+  launch_pdl(k_patch_dense<T, PB>, dim3((int)blocks, R), 128, patch_dense_smem<T>(fam.nloc), s, n, fam, D, (T)eta, r, z);
 }
 
 PatchFamily vertex_family(int n) {
@@ -1297,7 +1331,7 @@ void launch_patch_gram(cudaStream_t s, int sm, int n, const PatchFamily& fam, in
   int64_t blocks = (NP + PB - 1) / PB;
   const int64_t cap = (int64_t)sm * 2;
   if (blocks > cap) blocks = cap;
-  k_patch_gram<T, PB><<<dim3((int)blocks, R), 256, patch_gram_smem<T>(fam.nloc, nG), s>>>(n, fam, nG, W, WT,
+  launch_pdl(k_patch_gram<T, PB>, dim3((int)blocks, R), 256, patch_gram_smem<T>(fam.nloc, nG), s, n, fam, nG, W, WT,
                                                                                            (T)eta, r, z);
 }
 
@@ -1318,7 +1352,7 @@ void launch_vertex_dense(cudaStream_t s, int sm, int n, const T* D, double eta, 
 
 template <typename T>
 void launch_coarse(cudaStream_t s, int N0, const double* Ainv, const T* g, T* z, int R) {
-  k_coarse<T><<<dim3((N0 + 7) / 8, R), 256, sizeof(double) * N0, s>>>(N0, Ainv, g, z);
+  launch_pdl(k_coarse<T>, dim3((N0 + 7) / 8, R), 256, sizeof(double) * N0, s, N0, Ainv, g, z);
 }
 
 int reduction_blocks(int sm) { return sm * 4; }
@@ -1327,14 +1361,14 @@ template <typename T>
 void launch_dot2(cudaStream_t s, int sm, int64_t N, const T* x, const T* y, const T* x2, const T* y2, double* partial,
                  double* out, int R) {
   const int nb = reduction_blocks(sm);
-  k_dot2<T><<<dim3(nb, R), 256, 0, s>>>(N, x, y, x2, y2, partial);
-  k_finish2<<<R, 256, 0, s>>>(nb, partial, out);
+  launch_pdl(k_dot2<T>, dim3(nb, R), 256, 0, s, N, x, y, x2, y2, partial);
+  launch_pdl(k_finish2, R, 256, 0, s, nb, partial, out);
 }
 
 template <typename T>
 void launch_dot2_partial(cudaStream_t s, int sm, int64_t N, const T* x, const T* y, const T* x2, const T* y2,
                          double* partial, int R) {
-  k_dot2<T><<<dim3(reduction_blocks(sm), R), 256, 0, s>>>(N, x, y, x2, y2, partial);
+  launch_pdl(k_dot2<T>, dim3(reduction_blocks(sm), R), 256, 0, s, N, x, y, x2, y2, partial);
 }
 template void launch_dot2_partial<double>(cudaStream_t, int, int64_t, const double*, const double*, const double*,
                                           const double*, double*, int);
@@ -1342,11 +1376,11 @@ template void launch_dot2_partial<double>(cudaStream_t, int, int64_t, const doub
 void launch_cg_update_rr_partial(cudaStream_t s, int sm, int64_t N, const double* alpha, const double* p,
                                  const double* q, double* u, double* r, const double* sto, float* g32,
                                  double* partial, int R) {
-  k_cg_update_rr<<<dim3(reduction_blocks(sm), R), 256, 0, s>>>(N, alpha, p, q, u, r, sto, g32, partial);
+  launch_pdl(k_cg_update_rr, dim3(reduction_blocks(sm), R), 256, 0, s, N, alpha, p, q, u, r, sto, g32, partial);
 }
 void launch_dot2_zf_partial(cudaStream_t s, int sm, int64_t N, const double* x, const double* y, const float* z32,
                             double* partial, int R) {
-  k_dot2_zf<<<dim3(reduction_blocks(sm), R), 256, 0, s>>>(N, x, y, z32, partial);
+  launch_pdl(k_dot2_zf, dim3(reduction_blocks(sm), R), 256, 0, s, N, x, y, z32, partial);
 }
 
 static inline dim3 blas_grid(int64_t N, int sm, int R) {
@@ -1356,45 +1390,45 @@ static inline dim3 blas_grid(int64_t N, int sm, int R) {
 
 template <typename T>
 void launch_axpby(cudaStream_t s, int sm, int64_t N, const double* ab, const T* x, T* y, int R) {
-  k_axpby<T><<<blas_grid(N, sm, R), 256, 0, s>>>(N, ab, x, y);
+  launch_pdl(k_axpby<T>, blas_grid(N, sm, R), 256, 0, s, N, ab, x, y);
 }
 
 template <typename T>
 void launch_axpby_scalar(cudaStream_t s, int sm, int64_t N, double a, const T* x, double b, T* y) {
   if (N <= 0) return;
-  k_axpby_scalar<T><<<grid_for(N, sm, 8), 256, 0, s>>>(N, a, x, b, y);
+  launch_pdl(k_axpby_scalar<T>, grid_for(N, sm, 8), 256, 0, s, N, a, x, b, y);
 }
 
 template <typename T>
 void launch_cg_update(cudaStream_t s, int sm, int64_t N, const double* alpha, const T* p, const T* q, T* u, T* r, int R) {
-  k_cg_update<T><<<blas_grid(N, sm, R), 256, 0, s>>>(N, alpha, p, q, u, r);
+  launch_pdl(k_cg_update<T>, blas_grid(N, sm, R), 256, 0, s, N, alpha, p, q, u, r);
 }
 
 void launch_cg_update_rr(cudaStream_t s, int sm, int64_t N, const double* alpha, const double* p, const double* q,
                          double* u, double* r, const double* sto, float* g32, double* partial, double* out, int R) {
   const int nb = reduction_blocks(sm);
-  k_cg_update_rr<<<dim3(nb, R), 256, 0, s>>>(N, alpha, p, q, u, r, sto, g32, partial);
-  k_finish2<<<R, 256, 0, s>>>(nb, partial, out);
+  launch_pdl(k_cg_update_rr, dim3(nb, R), 256, 0, s, N, alpha, p, q, u, r, sto, g32, partial);
+  launch_pdl(k_finish2, R, 256, 0, s, nb, partial, out);
 }
 void launch_dot2_zf(cudaStream_t s, int sm, int64_t N, const double* x, const double* y, const float* z32,
                     double* partial, double* out, int R) {
   const int nb = reduction_blocks(sm);
-  k_dot2_zf<<<dim3(nb, R), 256, 0, s>>>(N, x, y, z32, partial);
-  k_finish2<<<R, 256, 0, s>>>(nb, partial, out);
+  launch_pdl(k_dot2_zf, dim3(nb, R), 256, 0, s, N, x, y, z32, partial);
+  launch_pdl(k_finish2, R, 256, 0, s, nb, partial, out);
 }
 void launch_axpby_zf(cudaStream_t s, int sm, int64_t N, const double* sc, const float* z32, const double* ab, double* p,
                      int R) {
-  k_axpby_zf<<<blas_grid(N, sm, R), 256, 0, s>>>(N, sc, z32, ab, p);
+  launch_pdl(k_axpby_zf, blas_grid(N, sm, R), 256, 0, s, N, sc, z32, ab, p);
 }
 
 void launch_to_f32(cudaStream_t s, int sm, int64_t N, const double* sc, const double* src, float* dst, int R) {
-  k_to_f32<<<blas_grid(N, sm, R), 256, 0, s>>>(N, sc, src, dst);
+  launch_pdl(k_to_f32, blas_grid(N, sm, R), 256, 0, s, N, sc, src, dst);
 }
 void launch_from_f32(cudaStream_t s, int sm, int64_t N, const double* sc, const float* src, double* dst, int R) {
-  k_from_f32<<<blas_grid(N, sm, R), 256, 0, s>>>(N, sc, src, dst);
+  launch_pdl(k_from_f32, blas_grid(N, sm, R), 256, 0, s, N, sc, src, dst);
 }
 void launch_add_f32(cudaStream_t s, int sm, int64_t N, const double* sc, const float* src, double* dst, int R) {
-  k_add_f32<<<blas_grid(N, sm, R), 256, 0, s>>>(N, sc, src, dst);
+  launch_pdl(k_add_f32, blas_grid(N, sm, R), 256, 0, s, N, sc, src, dst);
 }
 
 // ---- coefficient field ------------------------------------------------------
@@ -1402,7 +1436,7 @@ template <typename T>
 void launch_bubble_grouped(cudaStream_t s, int sm, int n, const T* Atab, const int* gid, double eta, const T* r, T* z,
                            int R) {
   const int64_t nc = n / 2;
-  k_bubble_grouped<T><<<dim3(grid_for(nc * nc * nc, sm, 16), R), 256, 0, s>>>(n, Atab, gid, (T)eta, r, z);
+  launch_pdl(k_bubble_grouped<T>, dim3(grid_for(nc * nc * nc, sm, 16), R), 256, 0, s, n, Atab, gid, (T)eta, r, z);
 }
 
 constexpr int kGroupPB = 8;
@@ -1426,26 +1460,26 @@ void launch_patch_grouped(cudaStream_t s, int sm, int n, const PatchFamily& fam,
   if (nchunks <= 0) return;
   int blocks = sm * 2;
   if (blocks > nchunks) blocks = nchunks;
-  k_patch_grouped<T, kGroupPB><<<dim3(blocks, R), 128, patch_grouped_smem<T>(fam.nloc), s>>>(
+  launch_pdl(k_patch_grouped<T, kGroupPB>, dim3(blocks, R), 128, patch_grouped_smem<T>(fam.nloc), s, 
       n, fam, Dtab, chunks, nchunks, plist, (T)eta, r, z);
 }
 
 void launch_cg_scalars(cudaStream_t s, int mode, int nb, const double* partial, const CgScalars& S, bool flex,
                        int* status, int R) {
-  k_cg_scalars<<<R, 256, 0, s>>>(mode, nb, partial, S, flex ? 1 : 0, status);
+  launch_pdl(k_cg_scalars, R, 256, 0, s, mode, nb, partial, S, flex ? 1 : 0, status);
 }
 
 void launch_grad_alpha_sum(cudaStream_t s, int sm, int n, double h, const double* lam, const double* u,
                            const double* acell, double* partial, double* out, int R) {
   const int nb = reduction_blocks(sm);
-  k_grad_alpha_sum<<<dim3(nb, R), 256, 0, s>>>(n, h, lam, u, acell, partial);
-  k_finish2<<<R, 256, 0, s>>>(nb, partial, out);
+  launch_pdl(k_grad_alpha_sum, dim3(nb, R), 256, 0, s, n, h, lam, u, acell, partial);
+  launch_pdl(k_finish2, R, 256, 0, s, nb, partial, out);
 }
 
 void launch_grad_cells(cudaStream_t s, int sm, int n, double h, const double* lam, const double* u, double* out,
                        int R) {
   const int64_t nc = (int64_t)n * n * n;
-  k_grad_cells<<<dim3(grid_for(nc, sm, 8), R), 256, 0, s>>>(n, h, lam, u, out);
+  launch_pdl(k_grad_cells, dim3(grid_for(nc, sm, 8), R), 256, 0, s, n, h, lam, u, out);
 }
 
 #define NDMG_INST(T)                                                                                   \
@@ -1459,7 +1493,7 @@ void launch_grad_cells(cudaStream_t s, int sm, int n, double h, const double* la
   template cudaError_t prepare_patch_grouped<T>();                                                    \
   template void launch_patch_grouped<T>(cudaStream_t, int, int, const PatchFamily&, const T*, const int4*, int, \
                                         const int*, double, const T*, T*, int);                       \
-  template void launch_restrict<T>(cudaStream_t, int, int, const T*, T*, int);                        \
+  template void launch_restrict<T>(cudaStream_t, int, int, const T*, T*, int, T*);                    \
   template void launch_prolong_add<T>(cudaStream_t, int, int, const T*, T*, int);                     \
   template void launch_bubble<T>(cudaStream_t, int, int, const T*, double, const T*, T*, int);        \
   template cudaError_t prepare_vertex_dense<T>();                                                     \

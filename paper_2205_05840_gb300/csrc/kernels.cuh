@@ -14,8 +14,9 @@ void launch_stencil(cudaStream_t s, int sm, int n, double cK, double cM, const T
                     unsigned long long* umax, int kz = 0);
 template <typename T>
 cudaError_t prepare_stencil();
+// g_c = P^t r_f; with zc, also z_c = 0
 template <typename T>
-void launch_restrict(cudaStream_t s, int sm, int nf, const T* rf, T* gc, int R);
+void launch_restrict(cudaStream_t s, int sm, int nf, const T* rf, T* gc, int R, T* zc = nullptr);
 template <typename T>
 void launch_prolong_add(cudaStream_t s, int sm, int nf, const T* zc, T* zf, int R);
 template <typename T>

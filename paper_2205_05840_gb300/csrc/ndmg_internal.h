@@ -132,6 +132,7 @@ struct DevLevel {
   void* Wcell = nullptr;      // the same factor in the per-neighbour blocks of the cell-owned kernel (tc_cell.cu)
   float* Wv32 = nullptr;      // the Gram factor W (108 x 60, FP32) for the persistent small-level kernel
   int zlen = 0;               // cell-owned smoother: cell layers per work item (ndmg_autotune; 0 = built-in)
+  int tc_kind = 1;            // tensor-core smoother: 1 brick kernel (tc_patch.cu), 2 cell-owned kernel (tc_cell.cu)
   // subdomain size 4: Gram factor of the 1176-edge vertex patches (1176 x 312)
   // and its transpose, for k_patch_gram
   double *Wg64 = nullptr, *WgT64 = nullptr;
@@ -172,7 +173,8 @@ struct ndmg_handle {
   // levels 1 .. Kc (n <= 32) and the coarsest in one cooperative launch
   int Kc = 0;                             // 0: not available for this handle
   int coarse_grid = 0;                    // CTAs of its cooperative grid
-  bool coarse_on = true;                  // ndmg_autotune may prefer the separate launches
+  bool coarse_on = false;                 // off by default (the separate launches measured faster);
+                                          // ndmg_autotune / ndmg_select_smoother may switch it on
   unsigned* coarse_count = nullptr;       // its grid-barrier counter
   unsigned long long* umax = nullptr;     // per right-hand side max |u| of the fixed-point FP64 stencil
   int* status_host = nullptr;             // pinned mirror of the status word

@@ -51,6 +51,7 @@
 
 #include "tc_cell.cuh"
 #include "tc_common.cuh"
+#include "pdl.cuh"
 
 namespace ndmg {
 namespace {
@@ -294,19 +295,22 @@ __device__ __forceinline__ void cell_smoother_body(const CellArgs& A) {
     float* bub = reinterpret_cast<float*>(smem + OFF_BUB) + m * 6;
     auto bub_slot = [&](int layer) { return bub + (((layer % 3) + 3) % 3) * (kRows * 6); };
 
-    // out of cell layer c (its GEMM2 complete) added into z; rb: the FP32
-    // interior-space values of that layer
-    auto epilogue = [&](int c) {
+    // out of cell layer c added into z, in two steps: epi_load issues the
+    // loads of this cell's z (before the wait for GEMM2, so that their
+    // latency overlaps it), epi_finish reads out from TMEM once GEMM2 is
+    // complete and stores z + eta out
+    float zv[16];
+    auto epi_load = [&](int c) {
+      const uint32_t lm = (own_xy && c >= k0 && c < k1) ? layer_mask(c) : 0u;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) zv[i] = ((lm >> i) & 1u) ? z[addr(i, c)] : 0.f;
+    };
+    auto epi_finish = [&](int c) {
       const float inv0 = wscale / sc[4 + (c & 3)], inv1 = wscale / sc[4 + ((c + 1) & 3)];
       const uint32_t lm = (own_xy && c >= k0 && c < k1) ? layer_mask(c) : 0u;
-      // groups of 8 positions: this cell's z first (every load in flight at
-      // once), then out from TMEM, then the stores
 #pragma unroll
       for (int grp = 0; grp < 2; ++grp) {
         if (h == 1 && grp == 1) break;
-        float zv[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) zv[i] = ((lm >> (8 * grp + i)) & 1u) ? z[addr(8 * grp + i, c)] : 0.f;
         float o0[8], o1[8];
         const uint32_t col = (uint32_t)(16 * h + 8 * grp);
         tmem_ld8x2(tq + 128 + col, tq + 160 + col, o0, o1);
@@ -328,7 +332,7 @@ __device__ __forceinline__ void cell_smoother_body(const CellArgs& A) {
         }
 #pragma unroll
         for (int i = 0; i < 8; ++i)
-          if ((lm >> (8 * grp + i)) & 1u) z[addr(8 * grp + i, c)] = zv[i] + A.eta * o0[i];
+          if ((lm >> (8 * grp + i)) & 1u) z[addr(8 * grp + i, c)] = zv[8 * grp + i] + A.eta * o0[i];
       }
     };
 
@@ -373,7 +377,7 @@ __device__ __forceinline__ void cell_smoother_body(const CellArgs& A) {
       fence_after();
       // descriptors = a base descriptor plus the operand's byte offset / 16
       // in the address field (every address stays below 256 KB)
-      const uint32_t slo = sR + (uint32_t)((((kv + 2) % 3) % 3) * R_LAYER);   // (kv - 1) mod 3, kv >= -1
+      const uint32_t slo = sR + (uint32_t)(((kv + 2) % 3) * R_LAYER);   // (kv - 1) mod 3, kv >= 0
       const uint32_t shi = sR + (uint32_t)((((kv % 3) + 3) % 3) * R_LAYER);
       const uint64_t alo = smem_desc(slo, LBO_R, 128), ahi = smem_desc(shi, LBO_R, 128);
       const uint64_t alo2 = smem_desc(slo, 2 * LBO_R, 128), ahi2 = smem_desc(shi, 2 * LBO_R, 128);
@@ -439,10 +443,11 @@ __device__ __forceinline__ void cell_smoother_body(const CellArgs& A) {
     // GEMM2 of cell layer kv - 1 and GEMM1 of vertex layer kv + 1 back to back
     for (int kv = k0; kv <= k1; ++kv) {
       if (kv >= k0 + 2) {
+        epi_load(kv - 2);
         if (mbar_wait(bar_g2, n2done & 1u)) ++n2done;
         else bad = true;
         fence_after();
-        if (!__any_sync(0xffffffffu, bad)) epilogue(kv - 2);
+        if (!__any_sync(0xffffffffu, bad)) epi_finish(kv - 2);
       }
       if (kv + 1 <= k1) {
         stage(kv + 1);
@@ -487,11 +492,12 @@ __device__ __forceinline__ void cell_smoother_body(const CellArgs& A) {
     }
     if (bad) break;
     // out of the last cell layer of the chunk
+    epi_load(k1 - 1);
     if (mbar_wait(bar_g2, n2done & 1u)) ++n2done;
     else bad = true;
     fence_after();
     if (agree()) break;
-    epilogue(k1 - 1);
+    epi_finish(k1 - 1);
     fence_before();
     __syncthreads();   // TMEM and the rings are free for the next item
   }
@@ -511,8 +517,14 @@ __device__ __forceinline__ void cell_smoother_body(const CellArgs& A) {
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 1) k_tc_cell_smoother_f16(CellArgs A) { cell_smoother_body<true>(A); }
-__global__ void __launch_bounds__(kThreads, 1) k_tc_cell_smoother_bf16(CellArgs A) { cell_smoother_body<false>(A); }
+__global__ void __launch_bounds__(kThreads, 1) k_tc_cell_smoother_f16(CellArgs A) {
+  pdl_start();
+  cell_smoother_body<true>(A);
+}
+__global__ void __launch_bounds__(kThreads, 1) k_tc_cell_smoother_bf16(CellArgs A) {
+  pdl_start();
+  cell_smoother_body<false>(A);
+}
 
 }  // namespace
 
@@ -626,8 +638,8 @@ void launch_tc_cell_smoother(cudaStream_t s, int sm, int n, const void* img, boo
   a.z = z;
   a.status = status;
   const int grid = a.items < sm ? a.items : sm;
-  if (fp16) k_tc_cell_smoother_f16<<<grid, kThreads, kSmem, s>>>(a);
-  else k_tc_cell_smoother_bf16<<<grid, kThreads, kSmem, s>>>(a);
+  if (fp16) launch_pdl(k_tc_cell_smoother_f16, grid, kThreads, kSmem, s, a);
+  else launch_pdl(k_tc_cell_smoother_bf16, grid, kThreads, kSmem, s, a);
 }
 
 int tc_cell_image_bytes() { return kImgTotal; }

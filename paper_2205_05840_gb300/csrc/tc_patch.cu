@@ -33,6 +33,7 @@
 #include <type_traits>
 
 #include "tc_patch.cuh"
+#include "pdl.cuh"
 
 namespace ndmg {
 namespace {
@@ -388,6 +389,7 @@ template <bool FP16>
 __global__ void __launch_bounds__(kThreads, 3)
     k_tc_smoother(int n, const uint8_t* __restrict__ img, const float* __restrict__ AinvT, float eta,
                   const float* __restrict__ r, float* __restrict__ z, int* __restrict__ status) {
+  pdl_start();
   extern __shared__ __align__(128) uint8_t smem[];
   // a CTA of an earlier launch gave up on a wait: do nothing until the host
   // has read and cleared the status word
@@ -583,6 +585,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                         const int* __restrict__ bub_gid, const int* __restrict__ goff, const int* __restrict__ ggrp,
                         const uint4* __restrict__ gmask, float eta, const float* __restrict__ r,
                         float* __restrict__ z, int* __restrict__ status) {
+  pdl_start();
   extern __shared__ __align__(128) uint8_t smem[];
   if (*reinterpret_cast<volatile int*>(status) != 0) return;
 
@@ -918,10 +921,10 @@ void launch_tc_smoother_field(cudaStream_t s, int n, const void* imgs, bool fp16
   if (nv < 1) return;
   const int grid = ((nv + kBX - 1) / kBX) * ((nv + kBY - 1) / kBY) * ((nv + kBZ - 1) / kBZ) * R;
   if (fp16)
-    k_tc_smoother_field<true><<<grid, kThreads, kSmemF, s>>>(n, (const uint8_t*)imgs, Atab, bub_gid, goff, ggrp,
+    launch_pdl(k_tc_smoother_field<true>, grid, kThreads, kSmemF, s, n, (const uint8_t*)imgs, Atab, bub_gid, goff, ggrp,
                                                                gmask, (float)eta, r, z, status);
   else
-    k_tc_smoother_field<false><<<grid, kThreads, kSmemF, s>>>(n, (const uint8_t*)imgs, Atab, bub_gid, goff, ggrp,
+    launch_pdl(k_tc_smoother_field<false>, grid, kThreads, kSmemF, s, n, (const uint8_t*)imgs, Atab, bub_gid, goff, ggrp,
                                                                 gmask, (float)eta, r, z, status);
 }
 
@@ -931,9 +934,9 @@ void launch_tc_smoother(cudaStream_t s, int n, const void* Wimg, bool fp16, cons
   if (nv < 1) return;
   const int grid = ((nv + kBX - 1) / kBX) * ((nv + kBY - 1) / kBY) * ((nv + kBZ - 1) / kBZ) * R;
   if (fp16)
-    k_tc_smoother<true><<<grid, kThreads, kSmem, s>>>(n, (const uint8_t*)Wimg, AinvT, (float)eta, r, z, status);
+    launch_pdl(k_tc_smoother<true>, grid, kThreads, kSmem, s, n, (const uint8_t*)Wimg, AinvT, (float)eta, r, z, status);
   else
-    k_tc_smoother<false><<<grid, kThreads, kSmem, s>>>(n, (const uint8_t*)Wimg, AinvT, (float)eta, r, z, status);
+    launch_pdl(k_tc_smoother<false>, grid, kThreads, kSmem, s, n, (const uint8_t*)Wimg, AinvT, (float)eta, r, z, status);
 }
 
 

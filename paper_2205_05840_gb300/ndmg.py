@@ -73,6 +73,8 @@ _SIGS = {
     "ndmg_autotune": [_vp, _P(_i32)],
     "ndmg_grad_alpha_field": [_vp, _vp, _vp, _vp],
     "ndmg_inject_status": [_vp, _i32],
+    "ndmg_select_smoother": [_vp, _i32, _i32],
+    "ndmg_probe_fma_rate": [_i32, _P(_d)],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -80,6 +82,16 @@ for _name, _args in _SIGS.items():
     _f.restype = ctypes.c_int
 _lib.ndmg_last_error.argtypes = [_vp]
 _lib.ndmg_last_error.restype = ctypes.c_char_p
+
+
+def fma_rate_tflops(dtype: int) -> float:
+    """Measured CUDA-core FMA rate of the current device in TFLOP/s
+    (ndmg_probe_fma_rate; dtype F64 or F32)."""
+    out = _d()
+    st = _lib.ndmg_probe_fma_rate(int(dtype), ctypes.byref(out))
+    if st != OK:
+        raise NdmgError(st, "ndmg_probe_fma_rate failed")
+    return out.value
 
 
 def header_functions(path: str = HEADER) -> list[str]:
@@ -295,8 +307,8 @@ class Solver:
 
     def autotune(self):
         """Pick launch shapes by timing (ndmg_autotune); returns {level:
-        (stencil planes per CTA for float, for double, tensor-core smoother:
-        0 = CUDA cores, else its cell layers per work item)}."""
+        (stencil planes per CTA for float, for double, smoother: 0 CUDA cores,
+        1 tensor cores per brick, 2 tensor cores on cell-owned rows)}."""
         out = (_i32 * (3 * self.num_levels))()
         self._check(_lib.ndmg_autotune(self._h, out), "autotune")
         return {k: (out[3 * k], out[3 * k + 1], out[3 * k + 2]) for k in range(self.num_levels)}
@@ -315,3 +327,9 @@ class Solver:
         """Test hook: set the handle's device status word (ndmg_inject_status),
         as a tensor-core kernel whose bounded wait gave up would."""
         self._check(_lib.ndmg_inject_status(self._h, int(code)), "inject_status")
+
+    def select_smoother(self, kind: int, level: int = -1):
+        """Smoother kernel of a level (ndmg_select_smoother): 0 CUDA cores,
+        1 tensor cores per brick, 2 tensor cores on cell-owned rows; level 0:
+        the levels n <= 32 in one persistent launch (1) or separate ones (0)."""
+        self._check(_lib.ndmg_select_smoother(self._h, int(level), int(kind)), "select_smoother")

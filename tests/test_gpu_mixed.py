@@ -49,14 +49,19 @@ def rel(a, b):
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
 
 
+KERNELS = {"brick": 1, "cell": 2}
+
+
+@pytest.mark.parametrize("kernel", ["brick", "cell"])
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
 @pytest.mark.parametrize("n,n0,alpha", [(4, 2, 1.0), (8, 4, 1.0), (12, 6, 0.01), (20, 10, 100.0), (32, 4, 1.0),
                                         (40, 5, 1.0)])
-def test_tc_smoothing_step(prec, n, n0, alpha):
+def test_tc_smoothing_step(kernel, prec, n, n0, alpha):
     # one smoothing step z <- z + M_V^{-1}(g - A z) on float vectors, patch
-    # solves on tensor cores, against the FP64 oracle (sizes: one brick,
-    # several bricks, partial bricks)
+    # solves on tensor cores (both kernels), against the FP64 oracle (sizes:
+    # one brick / column tile, several, partial ones)
     S = ndmg.Solver(n, n_coarsest=n0, alpha=alpha, precision=prec_code(prec))
+    S.select_smoother(KERNELS[kernel])
     A = hcurl.assemble(n, 1.0, alpha, 1.0)
     Sm = mg.Smoother(A, n, "vertex")
     rng = np.random.default_rng(n)
@@ -69,9 +74,10 @@ def test_tc_smoothing_step(prec, n, n0, alpha):
     assert rel(got, corr) < 16 * U[prec]
 
 
+@pytest.mark.parametrize("kernel", ["brick", "cell"])
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
 @pytest.mark.parametrize("n", [64, 128])
-def test_tc_smoothing_step_sampled_cells(prec, n):
+def test_tc_smoothing_step_sampled_cells(kernel, prec, n):
     # one tensor-core smoothing step at 64^3 and 128^3 against the oracle on
     # every edge of sampled coarse cells: the domain faces, the borders of the
     # kernel's 14-cell column tiles (13|14, 27|28, ...) and random cells.  The
@@ -81,6 +87,7 @@ def test_tc_smoothing_step_sampled_cells(prec, n):
     nc = n // 2
     h = 1.0 / n
     S = ndmg.Solver(n, n_coarsest=4, precision=prec_code(prec))
+    S.select_smoother(KERNELS[kernel])
     rng = np.random.default_rng(n + 1)
     Nn = hcurl.num_edges(n)
     g = rng.standard_normal(Nn).astype(np.float32).astype(np.float64)
@@ -134,12 +141,14 @@ def test_tc_smoothing_step_sampled_cells(prec, n):
     assert rel(have, want) < 16 * U[prec]
 
 
+@pytest.mark.parametrize("kernel", ["brick", "cell"])
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
-def test_tc_patch_columns(prec):
+def test_tc_patch_columns(kernel, prec):
     # a unit residual on single edges: the correction is one column of the
     # smoother (every patch index must land on the right edge)
     n = 12
     S = ndmg.Solver(n, n_coarsest=6, precision=prec_code(prec))
+    S.select_smoother(KERNELS[kernel])
     A = hcurl.assemble(n, 1.0, 1.0, 1.0)
     Sm = mg.Smoother(A, n, "vertex")
     Nn = A.shape[0]
@@ -155,10 +164,16 @@ def test_tc_patch_columns(prec):
         assert set(np.nonzero(np.abs(got) > 1e-3 * np.abs(col).max())[0]) <= set(np.nonzero(col)[0])
 
 
+@pytest.mark.parametrize("small", ["persistent", "separate"])
+@pytest.mark.parametrize("kernel", ["brick", "cell"])
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
-@pytest.mark.parametrize("n,n0", [(16, 2), (32, 4), (24, 3)])
-def test_mixed_vcycle_close_to_oracle(prec, n, n0):
+@pytest.mark.parametrize("n,n0", [(16, 2), (32, 4), (24, 3), (64, 4)])
+def test_mixed_vcycle_close_to_oracle(small, kernel, prec, n, n0):
+    # the levels <= 32^3 below the finest in one persistent launch (FP32 CUDA
+    # cores) or in separate launches (tensor-core smoother)
     S = ndmg.Solver(n, n_coarsest=n0, precision=prec_code(prec))
+    S.select_smoother(KERNELS[kernel])
+    S.select_smoother(1 if small == "persistent" else 0, level=0)
     H = mg.Hierarchy(n, 1.0, 1.0, 1.0, n0=n0, m=2)
     f = inputs.random_load(n, 0)
     ref = H.vcycle(f, np.zeros_like(f))
@@ -243,6 +258,7 @@ def test_graph_replay_matches_direct_launches(prec):
     out = {}
     for graphs in (False, True):
         S = ndmg.Solver(n, n_coarsest=4, precision=prec_code(prec))
+        S.select_smoother(1, level=0)          # the levels <= 32^3 in one persistent launch
         S.use_graphs(graphs)
         S.trace(ndmg.K_PATCH, True)
         S.trace(ndmg.K_COARSE, True)
@@ -307,10 +323,8 @@ def test_autotune_changes_launch_shapes_not_results():
         nl = 4 << lv
         for c in (cf, cd):
             assert c >= 1 and c <= nl and (c & (c - 1)) == 0
-        # 0: CUDA-core smoother; else the tensor-core kernel's cell layers per
-        # work item (a power of two up to n / 2, or n / 2 + 1 for its own model)
-        assert (lv > 0 or tc == 0) and 0 <= tc <= nl // 2 + 1
-        assert tc in (0, nl // 2 + 1) or (tc & (tc - 1)) == 0
+        # 0: CUDA-core smoother, 1: tensor cores per brick, 2: cell-owned rows
+        assert tc in (0, 1, 2) and (lv > 0 or tc == 0)
     for (dt, lv), (x, g, r0) in res.items():
         r = torch.empty_like(x)
         S.residual(g, x, r, level=lv)
