@@ -52,6 +52,10 @@ def parse():
     p.add_argument("--profile-case", choices=["none", "smooth", "residual", "vcycle"], default="none",
                    help="run only a few launches of one kernel class on an --n grid (for ncu captures)")
     p.add_argument("--n", type=int, default=N_GRID)
+    p.add_argument("--tune-out", default="", help="write the autotuned launch shapes (JSON) to this file")
+    p.add_argument("--tune-in", default="",
+                   help="apply launch shapes from this file instead of autotuning (e.g. for a profiler run, "
+                        "whose slowed launches would distort the timings)")
     p.add_argument("--grad-sweep", action="store_true",
                    help="forward + adjoint solve throughput for 32^3 .. 256^3 (one JSON line per size)")
     p.add_argument("--oracle-job", choices=["none", "solve", "vcycles"], default="none",
@@ -214,6 +218,21 @@ class OracleSample:
 def oracle_rate(n: int, cycles: int):
     """DoF*cycles/s of the FP64 CPU oracle's V-cycle on an n^3 problem."""
     return OracleSample(n).cycles(cycles)
+
+
+def launch_shapes(S, args):
+    """ndmg_autotune, or the shapes a previous run saved (--tune-in); --tune-out
+    saves them."""
+    if args.tune_in:
+        with open(args.tune_in) as fh:
+            tuned = {int(k): tuple(v) for k, v in json.load(fh).items()}
+        S.set_launch_shapes(tuned)
+    else:
+        tuned = S.autotune()
+    if args.tune_out:
+        with open(args.tune_out, "w") as fh:
+            json.dump({str(k): list(v) for k, v in tuned.items()}, fh)
+    return tuned
 
 
 def cores_used():
@@ -520,7 +539,7 @@ def run_ours(args):
                   ndmg.PREC_MIXED_FP16: "fp16-tc/f32+f64-refinement"}[prec]
     stream = torch.cuda.Stream(device=dev)
     S = ndmg.Solver(N_GRID, n_coarsest=N_COARSEST, alpha=ALPHA, m=M_SMOOTH, precision=prec, stream=stream)
-    tuned = S.autotune()                 # stencil z-planes per CTA, per level (untimed set-up)
+    tuned = launch_shapes(S, args)       # stencil z-planes per CTA and smoother, per level (untimed set-up)
     Nd = S.num_dofs()
     f = torch.tensor(inputs.random_load(N_GRID, seed=rank), dtype=torch.float64, device=dev)
     u = torch.zeros_like(f)
@@ -733,9 +752,11 @@ def run_ours(args):
                           "parallelism": f"replicas{world}",
                           "autotuned": {str(N_COARSEST << k): {"stencil_planes_per_cta_f32": v[0],
                                                                "stencil_planes_per_cta_f64": v[1],
-                                                               "smoother": ["cuda-core", "tensor-core brick",
-                                                                            "tensor-core cell rows"][v[2]]}
-                                        for k, v in tuned.items()}},
+                                                               "smoother": ("coarsest solve" if k == 0 else
+                                                                            ["cuda-core", "tensor-core brick",
+                                                                             "tensor-core cell rows"][v[2]])}
+                                        for k, v in tuned.items()},
+                          "levels_le_16_in_one_cluster_launch": bool(tuned[0][2])},
                "time_to_tol_ms": ms_total / args.steps, "vcycles_per_solve": vcyc_per_step,
                "pcg_iterations": iters[-1][0], "final_relres": iters[-1][1],
                "gpu_launches": launches, "roofline": roof, "kernels_one_solve": breakdown,

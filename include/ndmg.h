@@ -168,15 +168,28 @@ int ndmg_grad_alpha_field(ndmg_t* h, const double* lambda, const double* u, doub
  * rows, for every number of cell layers per work item: its own balance model,
  * then 1, 2, 4, ... n_k / 2) and the FP32 CUDA-core smoother (small levels
  * have too little work to fill the GPU), and keeps the fastest; the FP32
- * kernels are at least as accurate.  It then times the levels n <= 32 in one
- * persistent launch against separate launches and keeps the faster.
+ * kernels are at least as accurate.  It then times the levels n <= 16 in one
+ * launch of a thread-block cluster against separate launches per step and
+ * keeps the faster.
  * Synchronises the stream, overwrites the handle's solver workspaces and
  * drops a captured V-cycle graph.  choices: NULL or a host array of 3 (K+1)
  * ints, level-major: [3k] planes per CTA for float, [3k+1] for double, [3k+2]
- * the smoother of level k: 0 CUDA cores, 1 tensor cores per brick, 2 tensor
- * cores on cell-owned rows.
+ * (k >= 1) the smoother of level k: 0 CUDA cores, 1 tensor cores per brick,
+ * 2 tensor cores on cell-owned rows; [2] (the coarsest level has no smoother)
+ * 1 when the levels n <= 16 run in one cluster launch, else 0.
  * Errors: INVALID_ARG, CUDA_ERROR, DEVICE_TIMEOUT. */
 int ndmg_autotune(ndmg_t* h, int32_t* choices);
+
+/* Applies launch shapes chosen earlier (by ndmg_autotune on a handle of the
+ * same size, levels, precision and nrhs, on the same kind of GPU) without
+ * timing anything: choices is a host array of 3 (K+1) ints in ndmg_autotune's
+ * format (planes per CTA 0 = the built-in choice; the cell-owned smoother, if
+ * chosen, takes its built-in number of cell layers per work item).  The
+ * planes per CTA leave results bitwise unchanged; the smoother kinds differ
+ * in summation order only.  Synchronises the stream and drops
+ * a captured V-cycle graph.  Errors: INVALID_ARG (an entry out of range for
+ * the handle; nothing is changed), CUDA_ERROR. */
+int ndmg_set_launch_shapes(ndmg_t* h, const int32_t* choices);
 
 /* Chooses the smoother kernel of a level by hand (what ndmg_autotune decides
  * by timing): kind 0 FP32 CUDA cores, 1 tensor cores per brick of 128 vertex
@@ -185,9 +198,10 @@ int ndmg_autotune(ndmg_t* h, int32_t* choices);
  * the overlapping patch outputs are summed).  level: 1 .. K, or -1 for every
  * level.  Kinds 1 and 2 need a MIXED handle with the vertex smoother and
  * subdomain size 2.  level 0 instead selects how float V-cycles run the
- * levels n <= 32 (when the handle has them): kind 1 in one persistent launch,
- * 0 in separate launches per step.  Synchronises the stream and drops a captured V-cycle
- * graph.  Errors: INVALID_ARG, CUDA_ERROR. */
+ * levels n <= 16 (when the handle has them): kind 1 in one launch of a
+ * thread-block cluster, 0 (the default) in separate launches per step.
+ * Synchronises the stream and drops a captured V-cycle graph.
+ * Errors: INVALID_ARG, CUDA_ERROR. */
 int ndmg_select_smoother(ndmg_t* h, int32_t level, int32_t kind);
 
 /* Number of levels K+1. */

@@ -142,9 +142,8 @@ bool mixed(const ndmg_t* h) {
 }
 
 // kernels with bounded device-side waits may have written the status word:
-// the tensor-core smoothers (MIXED handles) and the persistent small-level
-// kernel (float V-cycles)
-bool waits_on_device(const ndmg_t* h) { return mixed(h) || h->Kc > 0; }
+// the tensor-core smoothers (MIXED handles)
+bool waits_on_device(const ndmg_t* h) { return mixed(h); }
 
 // ---------------------------------------------------------------------------
 // Level operations (every launch covers the R = nrhs right-hand sides)
@@ -353,13 +352,13 @@ void op_smooth_steps(ndmg_t* h, int k, const T* g, T* z, int steps) {
   }
 }
 
-// the persistent small-level kernel serves float V-cycles on levels 1 .. Kc
+// the small-level cluster kernel serves float V-cycles on levels 1 .. Kc
 // that start from z = 0 (constant coefficient, vertex smoother, subdomain 2)
 bool coarse_cycle_on(const ndmg_t* h, int k) {
   return h->coarse_on && h->Kc > 0 && k >= 1 && k <= h->Kc && h->coarse_grid > 0 && !h->field;
 }
 
-// z = MG(k, g, 0, m) for k <= Kc in one cooperative launch
+// z = MG(k, g, 0, m) for k <= Kc in one cluster launch
 void op_coarse_cycle(ndmg_t* h, int k, const float* g, float* z) {
   CoarseLevel cl[kCoarseMaxLevels + 1];
   double units = 0.0;
@@ -377,7 +376,7 @@ void op_coarse_cycle(ndmg_t* h, int k, const float* g, float* z) {
   }
   Span sp(h, NDMG_K_COARSE, units);
   launch_coarse_cycle(h->stream, h->coarse_grid, cl, k, (int)h->lv[0].N, h->Ainv0, h->lv[0].g32, h->lv[0].z32,
-                      h->o.eta, h->o.m, nrhs(h), h->coarse_count, h->status);
+                      h->o.eta, h->o.m, nrhs(h), h->status);
 }
 
 // MG(k, g, z, m) of Fig. 1 with z in/out; z_zero: z is 0 on entry, so the
@@ -998,7 +997,6 @@ void free_handle(ndmg_t* h) {
   cudaFree(h->coef);
   cudaFree(h->cg);
   cudaFree(h->status);
-  cudaFree(h->coarse_count);
   if (h->red_host) cudaFreeHost(h->red_host);
   if (h->coef_host) cudaFreeHost(h->coef_host);
   if (h->cg_host) cudaFreeHost(h->cg_host);
@@ -1279,14 +1277,13 @@ int ndmg_create(const ndmg_opts* o, ndmg_t** out) {
   if (ae == cudaSuccess && h->o.subdomain == 4) ae = prepare_patch_gram<float>();
   if (ae == cudaSuccess && mixed(h)) ae = prepare_tc_patch();
   if (ae == cudaSuccess && mixed(h)) ae = prepare_tc_cell();
-  // small levels in one persistent kernel: levels 1 .. Kc with n <= 32
+  // the smallest levels in one cluster launch: levels 1 .. Kc with n <= 16
   // (constant coefficient, vertex smoother, subdomain 2, coarsest <= 4^3)
   if (ae == cudaSuccess && h->o.smoother == NDMG_SMOOTHER_VERTEX && h->o.subdomain == 2 && h->lv[0].N <= 108) {
     int Kc = 0;
     while (Kc + 1 <= K && Kc + 1 <= kCoarseMaxLevels && h->lv[Kc + 1].n <= kCoarseMaxN) ++Kc;
     if (Kc > 0) {
       ae = prepare_coarse_cycle();
-      if (ae == cudaSuccess) h->coarse_count = dev_alloc<unsigned>(64, &ae);   // counter, flag 128 B apart
       if (ae == cudaSuccess) {
         h->coarse_grid = coarse_cycle_grid(h->sm_count, Kc);
         h->Kc = h->coarse_grid > 0 ? Kc : 0;
@@ -1462,11 +1459,11 @@ int ndmg_autotune(ndmg_t* h, int32_t* choices) {
     L.tc = !(t_cc < t_cell && t_cc < t_brick);
     L.tc_kind = t_cell < t_brick ? 2 : 1;
   }
-  for (int k = 0; k <= h->K && choices; ++k) {
+  for (int k = 1; k <= h->K && choices; ++k) {
     const DevLevel& L = h->lv[k];
-    choices[3 * k + 2] = mixed(h) && k >= 1 && L.tc ? L.tc_kind : 0;
+    choices[3 * k + 2] = mixed(h) && L.tc ? L.tc_kind : 0;
   }
-  // the small levels: one persistent launch or the separate launches
+  // the small levels: one cluster launch or the separate launches
   if (st == NDMG_OK && h->Kc > 0 && !h->field) {
     const int kc = h->Kc;
     float t_on = 0.f, t_off = 0.f;
@@ -1487,6 +1484,7 @@ int ndmg_autotune(ndmg_t* h, int32_t* choices) {
     }
     h->coarse_on = !(t_off < t_on);
   }
+  if (choices) choices[2] = coarse_cycle_on(h, h->Kc) ? 1 : 0;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st == NDMG_OK && cudaGetLastError() != cudaSuccess) st = fail(h, NDMG_CUDA_ERROR, "autotune launch");
@@ -1498,7 +1496,7 @@ int ndmg_select_smoother(ndmg_t* h, int32_t level, int32_t kind) {
   if (!h) return NDMG_INVALID_ARG;
   if (kind < 0 || kind > 2) return fail(h, NDMG_INVALID_ARG, "kind must be 0, 1 or 2");
   if (level < -1 || level > h->K) return fail(h, NDMG_INVALID_ARG, "level out of range");
-  if (level == 0) {   // the small levels: one persistent launch (1) or separate launches (0)
+  if (level == 0) {   // the small levels: one cluster launch (1) or separate launches (0)
     if (kind == 2) return fail(h, NDMG_INVALID_ARG, "level 0 takes kind 0 or 1");
     NDMG_CK(cudaStreamSynchronize(h->stream));
     if (int st = collect_graph(h)) return st;
@@ -1516,6 +1514,40 @@ int ndmg_select_smoother(ndmg_t* h, int32_t level, int32_t kind) {
     h->lv[k].tc = kind > 0;
     if (kind > 0) h->lv[k].tc_kind = kind;
   }
+  return NDMG_OK;
+}
+
+int ndmg_set_launch_shapes(ndmg_t* h, const int32_t* choices) {
+  if (!h || !choices) return NDMG_INVALID_ARG;
+  const int R = nrhs(h);
+  const bool tc_ok = mixed(h) && !edge_smoother(h) && h->o.subdomain == 2;
+  for (int k = 0; k <= h->K; ++k) {
+    const int n = h->lv[k].n;
+    for (int t = 0; t < 2; ++t) {
+      const int kz = choices[3 * k + t];
+      if (kz < 0 || kz > n || (kz > 0 && (int64_t)((n + kz - 1) / kz) * R > 65535))
+        return fail(h, NDMG_INVALID_ARG, "planes per CTA out of range for a level");
+    }
+    const int kind = choices[3 * k + 2];
+    if (k == 0 && (kind < 0 || kind > 1 || (kind == 1 && !(h->Kc > 0 && h->coarse_grid > 0 && !h->field))))
+      return fail(h, NDMG_INVALID_ARG, "entry 2 must be 0, or 1 where the handle has levels n <= 16 for one launch");
+    if (k > 0 && (kind < 0 || kind > 2 || (kind > 0 && !tc_ok)))
+      return fail(h, NDMG_INVALID_ARG, "smoother kind out of range for the handle");
+  }
+  NDMG_CK(cudaStreamSynchronize(h->stream));
+  if (int st = collect_graph(h)) return st;
+  drop_graph(h);  // the graph holds the launch shapes
+  for (int k = 0; k <= h->K; ++k) {
+    DevLevel& L = h->lv[k];
+    L.kz[0] = choices[3 * k];
+    L.kz[1] = choices[3 * k + 1];
+    if (k > 0 && tc_ok) {
+      L.tc = choices[3 * k + 2] > 0;
+      if (L.tc) L.tc_kind = choices[3 * k + 2];
+      L.zlen = 0;
+    }
+  }
+  h->coarse_on = choices[2] == 1;
   return NDMG_OK;
 }
 

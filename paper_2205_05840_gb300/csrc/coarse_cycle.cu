@@ -1,10 +1,13 @@
-// The small levels of the float V-cycle (Fig. 1) in one persistent kernel.
+// The smallest levels of the float V-cycle (Fig. 1) in one thread-block
+// cluster.
 //
-// Below a few hundred thousand edges a level's launches cost more than
-// their work: every kernel of the multi-launch V-cycle pays its ramp-up and
-// tail, about 5-15 us, for a few microseconds of arithmetic.  This kernel
-// runs MG(Kc, g, 0, m) for the levels n_Kc <= 32 .. n_0 as a sequence of
-// grid-wide phases of one cooperative launch (every CTA co-resident):
+// On the levels n <= 16 a V-cycle step (a residual, a smoothing sweep, a
+// transfer) is a few microseconds of arithmetic, while a separate launch per
+// step costs about 8-13 us of launch and ramp-up, and a grid-wide barrier
+// through global atomics about 5-7 us.  This kernel runs MG(Kc, g, 0, m) for
+// the levels n_Kc <= 16 .. n_0 in one launch of one cluster of CTAs, whose
+// steps are separated by the hardware cluster barrier (release / acquire at
+// cluster scope, which also orders the CTAs' global-memory writes):
 //
 //   pre-smoothing  z = S g ; m - 1 times { r = g - A z ; z += S r }
 //   r = g - A z ; g_{k-1} = P^t r ; z_{k-1} = 0        (down to level 1)
@@ -15,10 +18,7 @@
 // (Preconditioner P) on CUDA cores in FP32 (one warp per vertex patch, W of
 // every level in shared memory, overlapping patch outputs added with
 // atomics), the operator as a direct 33-point stencil per edge in the
-// factored form K = C^t M_F C, and the transfers of Sec. 3.1.  Phases are
-// separated by a grid barrier whose waits are bounded: a CTA that gives up
-// writes the status word and returns (the others give up at their next
-// barrier), so a lost CTA cannot hang the GPU.
+// factored form K = C^t M_F C, and the transfers of Sec. 3.1.
 #include <cstring>
 
 #include "coarse_cycle.cuh"
@@ -29,9 +29,9 @@ namespace {
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
 constexpr int kWStride = 61;                 // W rows padded to an odd stride (conflict-free both ways)
+constexpr int kWarpScratch = 176;            // floats of per-warp scratch (gathered r_p, then W^t r_p)
 constexpr int kMaxN0 = 108;                  // coarsest level 4^3 at most
-constexpr int kTimeout = 2;                  // status code of a barrier that gave up
-constexpr long long kBarrierLimit = 400000000LL;   // ~0.2 s at 2 GHz
+constexpr int kCluster = 16;                 // CTAs of the cluster (one per SM)
 
 struct Lv {
   int n;
@@ -46,52 +46,13 @@ struct Args {
   float eta;
   Lv lv[kCoarseMaxLevels + 1];   // [0] coarsest (g, z only), [1 .. Kc]
   const double* Ainv0;           // N0 x N0 (symmetric)
-  unsigned* count;               // barrier arrivals (0 at launch)
-  unsigned* flag;                // last barrier opened (0 at launch), another cache line
   int* status;
 };
 
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Grid barrier number *epoch (1-based after the increment): every CTA adds
-// one to the arrival counter; the CTA that completes the count writes the
-// epoch to a release flag on another cache line, which the others poll (so
-// the polls never contend with the arrivals).  Bounded: returns false
-// (status written) when the wait gives up or another CTA already gave up.
-__device__ bool grid_barrier(const Args& A, unsigned* epoch) {
-  __shared__ int ok_s;
-  __syncthreads();
-  ++*epoch;
-  if (threadIdx.x == 0) {
-    const unsigned target = *epoch * gridDim.x;
-    __threadfence();
-    const unsigned prev = atomicAdd(A.count, 1u);
-    int ok = 1;
-    if (prev + 1 == target) {
-      st_release(A.flag, *epoch);
-    } else {
-      const long long t0 = clock64();
-      while (ld_acquire(A.flag) < *epoch) {
-        if (clock64() - t0 > kBarrierLimit || *reinterpret_cast<volatile int*>(A.status) != 0) {
-          ok = 0;
-          atomicCAS(A.status, 0, kTimeout);
-          break;
-        }
-        __nanosleep(32);
-      }
-    }
-    __threadfence();
-    ok_s = ok;
-  }
-  __syncthreads();
-  return ok_s != 0;
+// every thread of every CTA of the cluster: the step before is complete and
+// its global-memory writes are visible to the whole cluster
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 // ---- edges of level n (canonical layout of ndmg.h) ---------------------------
@@ -169,6 +130,21 @@ __host__ __device__ __forceinline__ void edge_coords(int n, int e, int* d, int* 
   } else {
     *i = l % n1 + 1; l /= n1; *j = l % n1 + 1; *k = l / n1;
   }
+}
+
+// edge of local index l (canonical numbering of the 4 x 4 x 4 box of cells)
+// of vertex patch p (interior vertices, x fastest, nv per axis) on level n
+__device__ __forceinline__ int patch_edge(int n, int nv, int p, int l) {
+  const int vx = 1 + p % nv, vy = 1 + (p / nv) % nv, vz = 1 + p / (nv * nv);
+  int d, bi, bj, bk;
+  if (l < 36) {
+    d = 0; bi = l % 4; bj = (l / 4) % 3 + 1; bk = l / 12 + 1;
+  } else if (l < 72) {
+    d = 1; bi = (l - 36) % 3 + 1; bj = ((l - 36) / 3) % 4; bk = (l - 36) / 12 + 1;
+  } else {
+    d = 2; bi = (l - 72) % 3 + 1; bj = ((l - 72) / 3) % 3 + 1; bk = (l - 72) / 9;
+  }
+  return idx_d(n, d, 2 * vx - 2 + bi, 2 * vy - 2 + bj, 2 * vz - 2 + bk);
 }
 
 // ---- phases ------------------------------------------------------------------
@@ -351,7 +327,7 @@ __global__ void __launch_bounds__(kThreads) k_coarse_vcycle(Args A) {
   extern __shared__ __align__(16) float sm[];
   if (*reinterpret_cast<volatile int*>(A.status) != 0) return;
   float* Wall = sm;                                     // Kc levels x 108 x kWStride
-  float* wscr = sm + A.Kc * 108 * kWStride + (threadIdx.x >> 5) * 176;
+  float* wscr = sm + A.Kc * 108 * kWStride + (threadIdx.x >> 5) * kWarpScratch;
   for (int k = 1; k <= A.Kc; ++k)
     for (int q = threadIdx.x; q < 108 * 60; q += kThreads)
       Wall[(k - 1) * 108 * kWStride + (q / 60) * kWStride + q % 60] = A.lv[k].W[q];
@@ -359,10 +335,8 @@ __global__ void __launch_bounds__(kThreads) k_coarse_vcycle(Args A) {
   const int lane = threadIdx.x & 31;
   const int gtid = blockIdx.x * kThreads + threadIdx.x, gsize = gridDim.x * kThreads;
   const int gwarp = blockIdx.x * kWarps + (threadIdx.x >> 5), nwarps = gridDim.x * kWarps;
-  unsigned epoch = 0;
   auto Wof = [&](int k) { return Wall + (k - 1) * 108 * kWStride; };
-#define NDMG_BARRIER() \
-  if (!grid_barrier(A, &epoch)) return;
+#define NDMG_BARRIER() cluster_sync()
   // down: level Kc .. 1 (z_Kc = 0 on entry, coarser z zeroed by the restriction)
   for (int k = A.Kc; k >= 1; --k) {
     const Lv& L = A.lv[k];
@@ -396,27 +370,49 @@ __global__ void __launch_bounds__(kThreads) k_coarse_vcycle(Args A) {
 #undef NDMG_BARRIER
 }
 
-size_t coarse_smem(int Kc) { return sizeof(float) * ((size_t)Kc * 108 * kWStride + kWarps * 176); }
+size_t coarse_smem(int Kc) {
+  // W of every level, then the per-warp scratch (16-byte aligned: 108 * 61 * 4 * Kc is a multiple of 16)
+  return sizeof(float) * ((size_t)Kc * 108 * kWStride + (size_t)kWarps * kWarpScratch);
+}
 
 }  // namespace
 
 cudaError_t prepare_coarse_cycle() {
-  return cudaFuncSetAttribute(k_coarse_vcycle, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)coarse_smem(kCoarseMaxLevels));
+  cudaError_t e = cudaFuncSetAttribute(k_coarse_vcycle, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)coarse_smem(kCoarseMaxLevels));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_coarse_vcycle, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  return e;
 }
 
-int coarse_cycle_grid(int sm_count, int Kc) {
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_vcycle, kThreads, coarse_smem(Kc)) !=
-          cudaSuccess ||
-      per_sm < 1)
+static cudaLaunchConfig_t cluster_config(int Kc, cudaStream_t s, cudaLaunchAttribute* attr) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kCluster);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = coarse_smem(Kc);
+  cfg.stream = s;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kCluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+int coarse_cycle_grid(int, int Kc) {
+  cudaLaunchAttribute attr[1];
+  const cudaLaunchConfig_t cfg = cluster_config(Kc, nullptr, attr);
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, k_coarse_vcycle, &cfg) != cudaSuccess || clusters < 1) {
+    cudaGetLastError();
     return 0;
-  return sm_count;   // one CTA per SM: fewer arrivals per barrier
+  }
+  return kCluster;
 }
 
 cudaError_t launch_coarse_cycle(cudaStream_t s, int grid, const CoarseLevel* lv, int Kc, int N0, const double* Ainv0,
-                                float* g0, float* z0, double eta, int m, int R, unsigned* count, int* status) {
-  if (Kc < 1 || Kc > kCoarseMaxLevels || N0 > kMaxN0 || grid < 1) return cudaErrorInvalidValue;
+                                float* g0, float* z0, double eta, int m, int R, int* status) {
+  if (Kc < 1 || Kc > kCoarseMaxLevels || N0 > kMaxN0 || grid != kCluster) return cudaErrorInvalidValue;
   Args a;
   std::memset(&a, 0, sizeof(a));
   a.Kc = Kc;
@@ -439,21 +435,9 @@ cudaError_t launch_coarse_cycle(cudaStream_t s, int grid, const CoarseLevel* lv,
   }
   a.lv[0].n = lv[0].n;
   a.Ainv0 = Ainv0;
-  a.count = count;
-  a.flag = count + 32;
   a.status = status;
-  cudaError_t e = cudaMemsetAsync(count, 0, 64 * sizeof(unsigned), s);
-  if (e != cudaSuccess) return e;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = coarse_smem(Kc);
-  cfg.stream = s;
   cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cudaLaunchConfig_t cfg = cluster_config(Kc, s, attr);
   return cudaLaunchKernelEx(&cfg, k_coarse_vcycle, a);
 }
 

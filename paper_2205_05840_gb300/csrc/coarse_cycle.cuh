@@ -1,4 +1,4 @@
-// The small levels of the float V-cycle in one persistent cooperative kernel
+// The smallest levels of the float V-cycle in one thread-block cluster
 // (coarse_cycle.cu).
 #pragma once
 #include "ndmg_internal.h"
@@ -6,7 +6,7 @@
 namespace ndmg {
 
 constexpr int kCoarseMaxLevels = 3;   // levels above the coarsest handled by one launch
-constexpr int kCoarseMaxN = 32;       // largest level size n handled
+constexpr int kCoarseMaxN = 16;       // largest level size n handled
 
 struct CoarseLevel {
   int n;
@@ -17,14 +17,13 @@ struct CoarseLevel {
 };
 
 cudaError_t prepare_coarse_cycle();
-// CTAs of the cooperative grid (every CTA co-resident), 0 if it cannot run
+// CTAs of the cluster, 0 if such a cluster cannot be resident on this device
 int coarse_cycle_grid(int sm_count, int Kc);
 // z_Kc = MG(Kc, g_Kc, 0, m) of Fig. 1 over levels lv[Kc] .. lv[1] and the
 // coarsest level (g0, z0: N0 values per right-hand side, Ainv0 its inverse);
-// z_Kc must be zero on entry.  count: 64 device words (barrier counter and
-// flag, reset here), status:
-// the handle's status word (a barrier that gives up writes 2 there).
+// z_Kc must be zero on entry.  status: the handle's status word (the kernel
+// does nothing while it is nonzero).  grid: coarse_cycle_grid's value.
 cudaError_t launch_coarse_cycle(cudaStream_t s, int grid, const CoarseLevel* lv, int Kc, int N0, const double* Ainv0,
-                                float* g0, float* z0, double eta, int m, int R, unsigned* count, int* status);
+                                float* g0, float* z0, double eta, int m, int R, int* status);
 
 }  // namespace ndmg

@@ -158,12 +158,12 @@ __global__ void __launch_bounds__(kTX * kTY) k_stencil_stream(int n, int KZ, T c
   constexpr bool FX = !std::is_same<S, T>::value;
   static_assert(!(FX && FLD), "the coefficient field runs in the vector type's own arithmetic");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  S* Ur = reinterpret_cast<S*>(smem_raw);  // [3 ring slots][x, y, z][kP]
-  S* Cx = Ur + 9 * kP;                     // circulations of the current step
+  S* Ur = reinterpret_cast<S*>(smem_raw);  // [4 ring slots][x, y, z][kP]
+  S* Cx = Ur + 12 * kP;                    // circulations of the current step
   S* Cy = Cx + kP;
   S* Cz = Cy + kP;
-  T* Gr = reinterpret_cast<T*>(Cz + kP);   // [2 ring slots][x, y, z][kTP]
-  T* Ar = Gr + 6 * kTP;                    // FLD: [3 ring slots][kP] cell coefficients
+  T* Gr = reinterpret_cast<T*>(Cz + kP);   // [3 ring slots][x, y, z][kTP]
+  T* Ar = Gr + 9 * kTP;                    // FLD: [4 ring slots][kP] cell coefficients
   const uint32_t n1 = n - 1, N3 = (uint32_t)n * n1 * n1;  // offsets within one right-hand side fit in 32 bits
   // grid z = (z chunks) x (right-hand sides); each right-hand side is a
   // contiguous canonical vector
@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(kTX * kTY) k_stencil_stream(int n, int KZ, T c
   };
   // FLD: the coefficients of the cells of plane c (the hexahedra between
   // node planes c and c + 1) at the staged positions, cell plane p of the
-  // chunk (c = k0 - 1 + p) in ring slot p % 3; zero outside the box (those
+  // chunk (c = k0 - 1 + p) in ring slot p % 4; zero outside the box (those
   // cells only meet faces whose circulation is zero)
   auto stage_a = [&](int c, int slot) {
     if constexpr (FLD) {
@@ -251,8 +251,13 @@ __global__ void __launch_bounds__(kTX * kTY) k_stencil_stream(int n, int KZ, T c
       if (has_b) one(qb);
     }
   };
-  // u plane p of the chunk is z = k0 - 1 + p, held in ring slot p % 3
+  // u plane p of the chunk is z = k0 - 1 + p, held in ring slot p % 4; the
+  // copies run two planes ahead of use (planes 0 and 1, and cell plane 0,
+  // before the first step; one commit group per step)
   stage_u(k0 - 1, 0);
+  stage_a(k0 - 1, 0);
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  stage_u(k0, 1);
   asm volatile("cp.async.commit_group;" ::: "memory");
 
   const int a = threadIdx.x + 1, b = threadIdx.y + 1;
@@ -301,18 +306,18 @@ __global__ void __launch_bounds__(kTX * kTY) k_stencil_stream(int n, int KZ, T c
   // y-normal faces, t >= -1), those of the z-normal faces on the next plane
   // k0 + t + 1 and the next plane's edge-mass rows; outputs for t >= 0
   for (int t = -2; t < T_out; ++t) {
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    convert_own((t + 2) % 3);
-    __syncthreads();  // plane t+2 and g(t) landed; step t-1 is done with the ring
-    if (t + 2 <= T_out) stage_u(k0 + t + 2, (t + 3) % 3);
-    if (g && t + 1 >= 0 && t + 1 < T_out) stage_g(k0 + t + 1, (t + 1) & 1);
-    if (FLD && t + 2 <= T_out) stage_a(k0 + t + 1, (t + 2) % 3);  // cell plane p = t + 2
+    asm volatile("cp.async.wait_group 1;" ::: "memory");  // all but the newest group
+    convert_own((t + 2) % 4);
+    __syncthreads();  // u plane t+2, g(t) and cell plane t+1 landed; step t-1 is done with the rings
+    if (t + 3 <= T_out) stage_u(k0 + t + 3, (t + 4) % 4);                 // u plane p = t + 4
+    if (g && t + 2 < T_out) stage_g(k0 + t + 2, (t + 2) % 3);
+    if (FLD && t + 3 <= T_out) stage_a(k0 + t + 2, (t + 3) % 4);         // cell plane p = t + 3
     asm volatile("cp.async.commit_group;" ::: "memory");
-    const S* Uc = Ur + ((t + 4) % 3) * 3 * kP;  // plane k0 + t
-    const S* Un = Ur + ((t + 2) % 3) * 3 * kP;  // plane k0 + t + 1
+    const S* Uc = Ur + ((t + 5) % 4) * 3 * kP;  // plane k0 + t
+    const S* Un = Ur + ((t + 2) % 4) * 3 * kP;  // plane k0 + t + 1
     if constexpr (FLD) {
-      Aprev = Ar + ((t + 3) % 3) * kP;  // cell plane k0 + t - 1 (p = t)
-      Acur = Ar + ((t + 4) % 3) * kP;   // cell plane k0 + t (p = t + 1)
+      Aprev = Ar + ((t + 4) % 4) * kP;  // cell plane k0 + t - 1 (p = t)
+      Acur = Ar + ((t + 5) % 4) * kP;   // cell plane k0 + t (p = t + 1)
     }
     auto circ = [&](int r, bool ha, bool hb) {
       if (t >= -1) {
@@ -335,7 +340,7 @@ __global__ void __launch_bounds__(kTX * kTY) k_stencil_stream(int n, int KZ, T c
       if (t >= 0) {
         const int k = k0 + t;
         const bool kn = in_node(k, n), ks = in_seg(k, n);
-        const T* G = Gr + (t & 1) * 3 * kTP;
+        const T* G = Gr + (t % 3) * 3 * kTP;
         const S zf = Zf(q, cz0[0], cz1[0], cz2[0]);          // Zf(a, b, k)
         const S zf_b = Zf(q - kPX, cz0[1], cz1[1], cz2[1]);  // Zf(a, b-1, k)
         const S zf_a = Zf(q - 1, cz0[2], cz1[2], cz2[2]);    // Zf(a-1, b, k)
@@ -610,6 +615,162 @@ __global__ void __launch_bounds__(128) k_patch_dense(int n, PatchFamily fam, con
       for (int p = 0; p < PB; ++p)
         if (base + p < NP) atomicAdd(z + gidx_of(base + p, row), eta * acc[p]);
     }
+  }
+}
+
+// The FP64 dense patch solves in double-float arithmetic on the FP32 pipe.
+// This part's FP64 rate is about 1/64 of its FP32 rate, and the dense
+// 108 x 108 patch products bound the FP64 V-cycle.  Every value is split
+// into a pair of floats (hi = fl(v), lo = fl(v - hi), about 48 significant
+// bits together); a product term d r is formed as hi*hi (rounded) plus its
+// exact rounding error (fma) plus the two cross terms, and added to a
+// running float sum with an error-free two-sum whose error joins a float
+// compensation; every kFold terms the pair is folded into an FP64
+// accumulator.  The residual block of a pass is scaled by a power of two so
+// that its largest entry is near 1 (the float exponent range then holds
+// every useful entry), and the result is scaled back.  The sums stay within
+// about 1e-14 of the FP64 ones relative to the largest term.
+constexpr int kFold = 16;
+constexpr int kDfThreads = 256;             // two thread halves, one row each
+constexpr int kPBdf = 16;                   // patches per pass: 8 per half
+
+// lin_d(i, j, k): the affine part of edge_gidx for direction d, so that
+// edge_gidx(n, d, o + (i, j, k)) = edge_gidx(n, d, o) + lin_d(i, j, k)
+__device__ __forceinline__ int edge_lin(int n, int d, int i, int j, int k) {
+  return d == 0 ? i + n * j + n * (n - 1) * k : d == 1 ? i + (n - 1) * j + n * (n - 1) * k
+                                                     : i + (n - 1) * j + (n - 1) * (n - 1) * k;
+}
+
+__global__ void __launch_bounds__(kDfThreads) k_patch_dense_df(int n, PatchFamily fam, const double* __restrict__ D,
+                                                               double eta, const double* __restrict__ r,
+                                                               double* __restrict__ z) {
+  pdl_start();
+  constexpr int H = kPBdf / 2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nl = fam.nloc;
+  const int nl2 = (nl * nl + 3) & ~3;               // keeps Rh, Rl 16-byte aligned
+  float* Dh = reinterpret_cast<float*>(smem_raw);   // nl * nl
+  float* Dl = Dh + nl2;
+  float* Rh = Dl + nl2;                             // nl * kPBdf
+  float* Rl = Rh + nl * kPBdf;
+  unsigned* loff = reinterpret_cast<unsigned*>(Rl + nl * kPBdf);  // lin_d of each local edge, d in the top 2 bits
+  long long* pbase = reinterpret_cast<long long*>(loff + ((nl + 1) & ~1));  // [kPBdf][3] edge_gidx of the origins
+  unsigned* amax = reinterpret_cast<unsigned*>(pbase + 3 * kPBdf);
+  const int64_t NP = (int64_t)fam.np[0] * fam.np[1] * fam.np[2];
+  const int64_t N3 = (int64_t)n * (n - 1) * (n - 1);
+  r += (int64_t)blockIdx.y * 3 * N3;
+  z += (int64_t)blockIdx.y * 3 * N3;
+  for (int q = threadIdx.x; q < nl * nl; q += blockDim.x) {
+    const double d = D[q];
+    const float h = (float)d;
+    Dh[q] = h;
+    Dl[q] = (float)(d - (double)h);
+  }
+  const int bx = fam.b[0], by = fam.b[1], bz = fam.b[2];
+  const int cx = bx * (by - 1) * (bz - 1), cy = (bx - 1) * by * (bz - 1);
+  for (int l = threadIdx.x; l < nl; l += blockDim.x) {
+    int d, i, j, k, e = l;
+    if (e < cx) {
+      d = 0; i = e % bx; j = (e / bx) % (by - 1) + 1; k = e / (bx * (by - 1)) + 1;
+    } else if ((e -= cx) < cy) {
+      d = 1; i = e % (bx - 1) + 1; j = (e / (bx - 1)) % by; k = e / ((bx - 1) * by) + 1;
+    } else {
+      e -= cy;
+      d = 2; i = e % (bx - 1) + 1; j = (e / (bx - 1)) % (by - 1) + 1; k = e / ((bx - 1) * (by - 1));
+    }
+    loff[l] = (unsigned)edge_lin(n, d, i, j, k) | ((unsigned)d << 30);
+  }
+  __syncthreads();
+  const int half = threadIdx.x / 128, row = threadIdx.x % 128;
+  const bool active = row < nl;
+  const int my_off = active ? (int)(loff[row] & 0x3FFFFFFFu) : 0, my_d = active ? (int)(loff[row] >> 30) : 0;
+  for (int64_t base = (int64_t)blockIdx.x * kPBdf; base < NP; base += (int64_t)gridDim.x * kPBdf) {
+    // the origins of this pass's patches (one 64-bit division per patch)
+    if (threadIdx.x < kPBdf * 3) {
+      const int pp = threadIdx.x / 3, d = threadIdx.x % 3;
+      const int64_t P = base + pp < NP ? base + pp : NP - 1;
+      const int pa = (int)(P % fam.np[0]) + fam.p0[0];
+      const int pb = (int)((P / fam.np[0]) % fam.np[1]) + fam.p0[1];
+      const int pc = (int)(P / ((int64_t)fam.np[0] * fam.np[1])) + fam.p0[2];
+      pbase[threadIdx.x] = edge_gidx(n, d, fam.stride * pa - fam.shift[0], fam.stride * pb - fam.shift[1],
+                                     fam.stride * pc - fam.shift[2]);
+    }
+    if (threadIdx.x == 0) *amax = 0u;
+    __syncthreads();
+    // gather: thread (half, row) loads local edge `row` of the half's 8 patches;
+    // m: the largest upper word of |r| (ordered like |r|, Inf and NaN on top)
+    double rv[H];
+    unsigned m = 0;
+#pragma unroll
+    for (int p = 0; p < H; ++p) {
+      const int pp = half * H + p;
+      rv[p] = active && base + pp < NP ? __ldg(r + pbase[3 * pp + my_d] + my_off) : 0.0;
+      m = max(m, (unsigned)((unsigned long long)__double_as_longlong(rv[p]) >> 32) & 0x7FFFFFFFu);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(amax, m);
+    __syncthreads();
+    // a power of two that brings the largest entry of the pass into [1, 2)
+    // (a pass of zeros keeps 1; Inf or NaN propagate)
+    const unsigned mw = *amax;
+    const int ex = mw == 0 ? 0 : (int)(mw >> 20) - 1023;
+    const double sc = ldexp(1.0, -ex);
+    if (active) {
+#pragma unroll
+      for (int p = 0; p < H; ++p) {
+        const double v = rv[p] * sc;
+        const float h = (float)v;
+        Rh[row * kPBdf + half * H + p] = h;
+        Rl[row * kPBdf + half * H + p] = (float)(v - (double)h);
+      }
+    }
+    __syncthreads();
+    if (active) {
+      double acc[H];
+      float sh[H], sl[H];
+#pragma unroll
+      for (int p = 0; p < H; ++p) {
+        acc[p] = 0.0;
+        sh[p] = 0.f;
+        sl[p] = 0.f;
+      }
+      for (int c0 = 0; c0 < nl; c0 += kFold) {
+        const int c1 = c0 + kFold < nl ? c0 + kFold : nl;
+        for (int c = c0; c < c1; ++c) {
+          const float dh = Dh[c * nl + row], dl = Dl[c * nl + row];
+          const float4* rh4 = reinterpret_cast<const float4*>(Rh + c * kPBdf + half * H);
+          const float4* rl4 = reinterpret_cast<const float4*>(Rl + c * kPBdf + half * H);
+          const float4 h0 = rh4[0], h1 = rh4[1], l0 = rl4[0], l1 = rl4[1];
+          const float rh[H] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+          const float rl[H] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
+#pragma unroll
+          for (int p = 0; p < H; ++p) {
+            const float prod = __fmul_rn(dh, rh[p]);
+            const float err = fmaf(dh, rh[p], -prod);               // exact: dh rh = prod + err
+            const float low = fmaf(dh, rl[p], fmaf(dl, rh[p], err));
+            const float t = __fadd_rn(sh[p], prod);                 // two-sum: sh + prod = t + e2 exactly
+            const float bb = __fsub_rn(t, sh[p]);
+            const float e2 = __fadd_rn(__fsub_rn(sh[p], __fsub_rn(t, bb)), __fsub_rn(prod, bb));
+            sh[p] = t;
+            sl[p] = __fadd_rn(sl[p], __fadd_rn(e2, low));
+          }
+        }
+#pragma unroll
+        for (int p = 0; p < H; ++p) {
+          acc[p] += (double)sh[p] + (double)sl[p];
+          sh[p] = 0.f;
+          sl[p] = 0.f;
+        }
+      }
+      const double back = eta / sc;
+#pragma unroll
+      for (int p = 0; p < H; ++p) {
+        const int pp = half * H + p;
+        if (base + pp < NP) atomicAdd(z + pbase[3 * pp + my_d] + my_off, back * acc[p]);
+      }
+    }
+    __syncthreads();  // pbase, Rh, Rl are rewritten by the next pass
   }
 }
 
@@ -1167,7 +1328,7 @@ static inline int grid_for(int64_t work, int sm_count, int per_sm = 8) {
 }
 
 template <typename T>
-size_t stencil_smem() { return sizeof(T) * (12 * kP + 6 * kTP); }
+size_t stencil_smem() { return sizeof(T) * (15 * kP + 9 * kTP); }
 
 // the FP64 operator runs in fixed point (k_stencil_stream<double, long long>)
 template <typename T>
@@ -1208,7 +1369,7 @@ void launch_stencil(cudaStream_t s, int sm, int n, double cK, double cM, const T
 
 // coefficient field: three more staged planes (the cell coefficients)
 template <typename T>
-size_t stencil_field_smem() { return stencil_smem<T>() + sizeof(T) * 3 * kP; }
+size_t stencil_field_smem() { return stencil_smem<T>() + sizeof(T) * 4 * kP; }
 
 template <typename T>
 cudaError_t prepare_stencil_field() {
@@ -1271,8 +1432,18 @@ static constexpr int pb_for() { return sizeof(T) == 8 ? kPB64 : kPB32; }
 template <typename T>
 size_t patch_dense_smem(int nloc) { return sizeof(T) * (nloc * nloc + nloc * pb_for<T>()) + sizeof(int) * nloc; }
 
+// double-float kernel for FP64 vectors: hi / lo floats of D and of the
+// pass's residuals, local offsets, patch origins, the pass maximum
+size_t patch_dense_df_smem(int nloc) {
+  return sizeof(float) * 2 * ((size_t)((nloc * nloc + 3) & ~3) + (size_t)nloc * kPBdf) +
+         sizeof(int) * ((nloc + 1) & ~1) + sizeof(long long) * 3 * kPBdf + 16;
+}
+
 template <typename T>
 cudaError_t prepare_vertex_dense() {
+  if constexpr (std::is_same<T, double>::value)
+    return cudaFuncSetAttribute(k_patch_dense_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)patch_dense_df_smem(108));
   return cudaFuncSetAttribute(k_patch_dense<T, pb_for<T>()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)patch_dense_smem<T>(108));
 }
@@ -1286,6 +1457,13 @@ void launch_patch_dense(cudaStream_t s, int sm, int n, const PatchFamily& fam, c
   int64_t blocks = (NP + PB - 1) / PB;
   const int64_t cap = (int64_t)sm * 2;
   if (blocks > cap) blocks = cap;
+  if constexpr (std::is_same<T, double>::value) {
+    int64_t bdf = (NP + kPBdf - 1) / kPBdf;
+    if (bdf > cap) bdf = cap;
+    launch_pdl(k_patch_dense_df, dim3((int)bdf, R), kDfThreads, patch_dense_df_smem(fam.nloc), s, n, fam, D, eta, r,
+               z);
+    return;
+  }
   launch_pdl(k_patch_dense<T, PB>, dim3((int)blocks, R), 128, patch_dense_smem<T>(fam.nloc), s, n, fam, D, (T)eta, r, z);
 }
 

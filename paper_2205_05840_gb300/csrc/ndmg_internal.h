@@ -169,13 +169,11 @@ struct ndmg_handle {
   double* cg = nullptr;                   // device PCG scalars (CgScalars, 8 R doubles)
   double* cg_host = nullptr;              // pinned: rr read back, done flags pushed (2 R doubles)
   int* status = nullptr;                  // device status word (timeouts)
-  // persistent kernel for the small levels of the float V-cycle (coarse_cycle.cu):
-  // levels 1 .. Kc (n <= 32) and the coarsest in one cooperative launch
+  // the smallest levels of the float V-cycle in one cluster launch
+  // (coarse_cycle.cu): levels 1 .. Kc (n <= 16) and the coarsest
   int Kc = 0;                             // 0: not available for this handle
-  int coarse_grid = 0;                    // CTAs of its cooperative grid
-  bool coarse_on = false;                 // off by default (the separate launches measured faster);
-                                          // ndmg_autotune / ndmg_select_smoother may switch it on
-  unsigned* coarse_count = nullptr;       // its grid-barrier counter
+  int coarse_grid = 0;                    // CTAs of its cluster
+  bool coarse_on = false;                 // ndmg_autotune / ndmg_select_smoother may switch it on
   unsigned long long* umax = nullptr;     // per right-hand side max |u| of the fixed-point FP64 stencil
   int* status_host = nullptr;             // pinned mirror of the status word
   std::string err;

@@ -71,6 +71,7 @@ _SIGS = {
     "ndmg_dot_noalloc": [_i32, _vp, _vp, _i64, _P(_d), _vp],
     "ndmg_set_alpha_field": [_vp, _vp],
     "ndmg_autotune": [_vp, _P(_i32)],
+    "ndmg_set_launch_shapes": [_vp, _P(_i32)],
     "ndmg_grad_alpha_field": [_vp, _vp, _vp, _vp],
     "ndmg_inject_status": [_vp, _i32],
     "ndmg_select_smoother": [_vp, _i32, _i32],
@@ -308,10 +309,22 @@ class Solver:
     def autotune(self):
         """Pick launch shapes by timing (ndmg_autotune); returns {level:
         (stencil planes per CTA for float, for double, smoother: 0 CUDA cores,
-        1 tensor cores per brick, 2 tensor cores on cell-owned rows)}."""
+        1 tensor cores per brick, 2 tensor cores on cell-owned rows)}; level
+        0's smoother entry is 1 when the levels n <= 16 run in one cluster
+        launch."""
         out = (_i32 * (3 * self.num_levels))()
         self._check(_lib.ndmg_autotune(self._h, out), "autotune")
         return {k: (out[3 * k], out[3 * k + 1], out[3 * k + 2]) for k in range(self.num_levels)}
+
+    def set_launch_shapes(self, tuned):
+        """Apply launch shapes in autotune()'s format without timing
+        (ndmg_set_launch_shapes); tuned: {level: (planes f32, planes f64,
+        smoother)}; level 0's smoother entry is the small-level cluster switch."""
+        arr = (_i32 * (3 * self.num_levels))()
+        for k in range(self.num_levels):
+            a, b, c = tuned[k]
+            arr[3 * k], arr[3 * k + 1], arr[3 * k + 2] = int(a), int(b), int(c)
+        self._check(_lib.ndmg_set_launch_shapes(self._h, arr), "set_launch_shapes")
 
     def use_graphs(self, on: bool = True):
         """Replay the mixed-precision V-cycle as a CUDA graph (ndmg_use_graphs)."""
@@ -331,5 +344,5 @@ class Solver:
     def select_smoother(self, kind: int, level: int = -1):
         """Smoother kernel of a level (ndmg_select_smoother): 0 CUDA cores,
         1 tensor cores per brick, 2 tensor cores on cell-owned rows; level 0:
-        the levels n <= 32 in one persistent launch (1) or separate ones (0)."""
+        the levels n <= 16 in one cluster launch (1) or separate ones (0)."""
         self._check(_lib.ndmg_select_smoother(self._h, int(level), int(kind)), "select_smoother")

@@ -169,7 +169,7 @@ def test_tc_patch_columns(kernel, prec):
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
 @pytest.mark.parametrize("n,n0", [(16, 2), (32, 4), (24, 3), (64, 4)])
 def test_mixed_vcycle_close_to_oracle(small, kernel, prec, n, n0):
-    # the levels <= 32^3 below the finest in one persistent launch (FP32 CUDA
+    # the levels <= 16^3 below the finest in one cluster launch (FP32 CUDA
     # cores) or in separate launches (tensor-core smoother)
     S = ndmg.Solver(n, n_coarsest=n0, precision=prec_code(prec))
     S.select_smoother(KERNELS[kernel])
@@ -251,14 +251,14 @@ def test_graph_replay_matches_direct_launches(prec):
     # launches give the same iteration count and launch / V-cycle counters,
     # solutions agree to the solve tolerance (FP32 atomics make the last bits
     # run-dependent), and traced kernel times are collected from the replays.
-    # 64^3: the finest level smooths on tensor cores, the levels <= 32^3 run in
-    # the persistent small-level kernel (one launch per V-cycle, traced too)
+    # 64^3: the finest levels smooth on tensor cores, the levels <= 16^3 run in
+    # the small-level cluster kernel (one launch per V-cycle, traced too)
     n = 64
     f = torch.tensor(inputs.random_load(n, 3), dtype=torch.float64, device=DEV)
     out = {}
     for graphs in (False, True):
         S = ndmg.Solver(n, n_coarsest=4, precision=prec_code(prec))
-        S.select_smoother(1, level=0)          # the levels <= 32^3 in one persistent launch
+        S.select_smoother(1, level=0)          # the levels <= 16^3 in one cluster launch
         S.use_graphs(graphs)
         S.trace(ndmg.K_PATCH, True)
         S.trace(ndmg.K_COARSE, True)
@@ -323,8 +323,9 @@ def test_autotune_changes_launch_shapes_not_results():
         nl = 4 << lv
         for c in (cf, cd):
             assert c >= 1 and c <= nl and (c & (c - 1)) == 0
-        # 0: CUDA-core smoother, 1: tensor cores per brick, 2: cell-owned rows
-        assert tc in (0, 1, 2) and (lv > 0 or tc == 0)
+        # 0: CUDA-core smoother, 1: tensor cores per brick, 2: cell-owned rows;
+        # level 0 (no smoother): 1 when the levels <= 16^3 run in one launch
+        assert tc in (0, 1, 2) and (lv > 0 or tc in (0, 1))
     for (dt, lv), (x, g, r0) in res.items():
         r = torch.empty_like(x)
         S.residual(g, x, r, level=lv)
@@ -339,3 +340,39 @@ def test_autotune_changes_launch_shapes_not_results():
     zt = torch.zeros(A.shape[0], dtype=torch.float32, device=DEV)
     S.smooth(T(g), zt, steps=1)
     assert rel(N(zt), Sm.apply(g)) < 16 * U["fp16"]
+
+
+@pytest.mark.gpu
+def test_set_launch_shapes_reproduces_autotuned_handle():
+    # ndmg_set_launch_shapes applies ndmg_autotune's choices to another handle
+    # without timing: the same V-cycle count, solutions within the float
+    # V-cycle's summation-order noise, and every entry checked before use
+    n = 64
+    f = T(inputs.random_load(n, 0), torch.float64)
+    S1 = ndmg.Solver(n, n_coarsest=4, precision=ndmg.PREC_MIXED_FP16)
+    tuned = S1.autotune()
+    u1 = torch.zeros_like(f)
+    _, it1, rr1 = S1.solve(f, u1, tol=1e-8)
+    S2 = ndmg.Solver(n, n_coarsest=4, precision=ndmg.PREC_MIXED_FP16)
+    S2.set_launch_shapes(tuned)
+    u2 = torch.zeros_like(f)
+    _, it2, rr2 = S2.solve(f, u2, tol=1e-8)
+    assert rr1 <= 1e-8 and rr2 <= 1e-8 and it1 == it2
+    assert rel(N(u2), N(u1)) < 1e-7
+    # the other way round: every smoother forced, then applied by hand
+    forced = {k: (1, 1, 0 if k == 0 else 2) for k in tuned}
+    S2.set_launch_shapes(forced)
+    u2.zero_()
+    _, it3, rr3 = S2.solve(f, u2, tol=1e-8)
+    assert rr3 <= 1e-8 and abs(it3 - it1) <= 2
+    bad = dict(tuned)
+    bad[S2.num_levels - 1] = (n + 1, 1, 1)      # more planes per CTA than the level has
+    with pytest.raises(ndmg.NdmgError):
+        S2.set_launch_shapes(bad)
+    bad = dict(tuned)
+    bad[1] = (1, 1, 3)                          # no smoother kind 3
+    with pytest.raises(ndmg.NdmgError):
+        S2.set_launch_shapes(bad)
+    S64 = ndmg.Solver(16, n_coarsest=4)
+    with pytest.raises(ndmg.NdmgError):          # tensor-core smoothers need a MIXED handle
+        S64.set_launch_shapes({0: (1, 1, 0), 1: (1, 1, 1), 2: (1, 1, 0)})
