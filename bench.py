@@ -727,9 +727,13 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         one, full, allc = cpu_baseline_runs(ORACLE_SAMPLE_N, 2)
         if one and full:
-            cpu = {"value": full["value"], "unit": "DoF*cycles/s", "cores": allc, "kind": "oracle",
+            # the faster of the two runs is the baseline (the oracle's sparse
+            # and small dense work gains nothing from more BLAS threads)
+            best, bcores = (one, 1) if one["value"] >= full["value"] else (full, allc)
+            cpu = {"value": best["value"], "unit": "DoF*cycles/s", "cores": bcores, "kind": "oracle",
                    "sample": f"2 FP64 oracle V-cycles on the {ORACLE_SAMPLE_N}^3 grid (a bounded sample of the "
-                             f"128^3 workload) in a process of its own",
+                             f"128^3 workload) in a process of its own; the faster of a 1-thread and an "
+                             f"all-core run",
                    "single_thread": {"value": one["value"], "cores": 1, "s": one["s"]},
                    "all_cores": {"value": full["value"], "cores": allc, "s": full["s"]},
                    "cpu": cpu_model()}

@@ -108,7 +108,11 @@ int ndmg_opts_default(ndmg_opts* o);
  * MIXED precision whose rounded Gram factor W~ cannot carry the vertex-patch
  * operator: largest eigenvalue of A_p W~W~^t above 16, which bf16 operands reach
  * near alpha / (beta h^2) = 2.8e5 and fp16 ones near 2.5e7 -- the smoother would
- * diverge; the message names the level), OUT_OF_MEMORY, CUDA_ERROR. */
+ * diverge; the message names the level), OUT_OF_MEMORY, CUDA_ERROR.
+ * Debugging aid: with the environment variable NDMG_POISON_WORKSPACES=1 set
+ * when the handle is created, every device workspace starts as all-one bytes
+ * (NaN in float and double), so a read of an entry nothing has written shows
+ * up as NaN results. */
 int ndmg_create(const ndmg_opts* o, ndmg_t** out);
 
 /* Free every resource of the handle (NULL is accepted). */

@@ -1,6 +1,7 @@
 // C ABI of libndmg (include/ndmg.h): handle, level hierarchy, V-cycle driver
 // (Fig. 1), PCG and the FP64 iterative-refinement loop.  All vector work runs
 // in the kernels of kernels.cu / tc_patch.cu on the handle's stream.
+#include <cstdlib>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -80,11 +81,18 @@ struct Span {
 int collect_graph(ndmg_t* h);
 void drop_graph(ndmg_t* h);
 
+// NDMG_POISON_WORKSPACES=1 at ndmg_create: workspaces start as all-one bytes
+bool poison_workspaces() {
+  const char* v = std::getenv("NDMG_POISON_WORKSPACES");
+  return v && v[0] == '1';
+}
+
 template <typename T>
-T* dev_alloc(int64_t count, cudaError_t* err) {
+T* dev_alloc(int64_t count, cudaError_t* err, bool poison = false) {
   void* p = nullptr;
   if (count <= 0) count = 1;
   cudaError_t e = cudaMalloc(&p, sizeof(T) * count);
+  if (e == cudaSuccess && poison) e = cudaMemset(p, 0xFF, sizeof(T) * count);
   if (e != cudaSuccess && *err == cudaSuccess) *err = e;
   return (T*)p;
 }
@@ -98,6 +106,31 @@ cudaError_t upload(T** dst, const std::vector<double>& src) {
     if (e != cudaSuccess) return e;
   }
   return cudaMemcpy(*dst, tmp.data(), sizeof(T) * tmp.size(), cudaMemcpyHostToDevice);
+}
+
+// FP64 dense local operators (nl x nl each, `count` of them back to back in
+// src) in the layout k_patch_dense_df reads: per operator the FP64 entries,
+// then the float parts hi = fl(d) and lo = fl(d - hi) of every entry, i.e.
+// dense_stride<double>(nl) doubles per operator
+cudaError_t upload_dense64(double** dst, const std::vector<double>& src, int nl) {
+  const size_t m = (size_t)nl * nl, count = src.size() / m;
+  std::vector<double> tmp(count * dense_stride<double>(nl));
+  for (size_t o = 0; o < count; ++o) {
+    double* blk = tmp.data() + o * dense_stride<double>(nl);
+    float* hl = reinterpret_cast<float*>(blk + m);
+    for (size_t q = 0; q < m; ++q) {
+      const double d = src[o * m + q];
+      const float hi = (float)d;
+      blk[q] = d;
+      hl[q] = hi;
+      hl[m + q] = (float)(d - (double)hi);
+    }
+  }
+  if (!*dst) {
+    cudaError_t e = cudaMalloc((void**)dst, sizeof(double) * tmp.size());
+    if (e != cudaSuccess) return e;
+  }
+  return cudaMemcpy(*dst, tmp.data(), sizeof(double) * tmp.size(), cudaMemcpyHostToDevice);
 }
 
 // fresh device copy of a host array (any previous buffer freed first)
@@ -202,7 +235,7 @@ void op_edge_terms(ndmg_t* h, int k, const T* De, const T* r, T* z) {
   for (int d = 0; d < 3; ++d) {
     const PatchFamily fam = edge_family(L.n, d);
     Span sp(h, NDMG_K_PATCH, (double)fam.np[0] * fam.np[1] * fam.np[2] * 2.0 * 42 * 42 * R);
-    launch_patch_dense<T>(h->stream, h->sm_count, L.n, fam, De + d * 42 * 42, h->o.eta, r, z, R);
+    launch_patch_dense<T>(h->stream, h->sm_count, L.n, fam, De + d * dense_stride<T>(42), h->o.eta, r, z, R);
   }
 }
 
@@ -328,8 +361,8 @@ void op_smoother<float>(ndmg_t* h, int k, const float* r, float* z) {
     // the same on tensor cores per brick of 128 vertex patches (gathered
     // operand, shared-memory accumulation, global reductions)
     Span sp(h, NDMG_K_PATCH, 12.0 * L.N * R);
-    launch_tc_smoother(h->stream, L.n, L.Wtc, h->o.precision == NDMG_PREC_MIXED_FP16, L.AinvT32, h->o.eta, r, z,
-                       h->status, R);
+    launch_tc_smoother(h->stream, h->sm_count, L.n, L.Wtc, h->o.precision == NDMG_PREC_MIXED_FP16, L.AinvT32,
+                       h->o.eta, r, z, h->status, R);
     return;
   }
   {
@@ -1047,7 +1080,8 @@ int build_operators(ndmg_t* h) {
   for (int k = 1; k <= h->K; ++k) {
     DevLevel& L = h->lv[k];
     const LocalOps& ops = all[k];
-    NDMG_CK(upload(&L.AinvT64, ops.AinvT));
+    if (o.subdomain == 4) NDMG_CK(upload_dense64(&L.AinvT64, ops.AinvT, 108));  // 108 x 108 interior solves
+    else NDMG_CK(upload(&L.AinvT64, ops.AinvT));
     NDMG_CK(upload(&L.AinvT32, ops.AinvT));
     if (o.subdomain == 4) {
       // Gram factor (1176 x 312) and its transpose for k_patch_gram
@@ -1060,12 +1094,12 @@ int build_operators(ndmg_t* h) {
       NDMG_CK(upload(&L.WgT32, WT));
       continue;
     }
-    NDMG_CK(upload(&L.Dv64, ops.Dv));
+    NDMG_CK(upload_dense64(&L.Dv64, ops.Dv, 108));
     NDMG_CK(upload(&L.Dv32, ops.Dv));
     NDMG_CK(upload(&L.Wv32, ops.Wv));
     std::vector<double> de;
     for (int d = 0; d < 3; ++d) de.insert(de.end(), ops.De[d].begin(), ops.De[d].end());
-    NDMG_CK(upload(&L.De64, de));
+    NDMG_CK(upload_dense64(&L.De64, de, 42));
     NDMG_CK(upload(&L.De32, de));
     if (mixed(h)) {
       cudaError_t e = upload_tc_operand(&L.Wtc, ops.Wv, fp16);
@@ -1240,29 +1274,30 @@ int ndmg_create(const ndmg_opts* o, ndmg_t** out) {
   h->lv.resize(K + 1);
   cudaError_t ae = cudaSuccess;
   const int64_t R = o->nrhs;
+  const bool pz = poison_workspaces();
   for (int k = 0; k <= K; ++k) {
     DevLevel& L = h->lv[k];
     L.n = o->n_coarsest << k;
     L.N = edges(L.n);
     L.h = o->L / L.n;
-    L.r64 = dev_alloc<double>(L.N * R, &ae);
-    L.r32 = dev_alloc<float>(L.N * R, &ae);
+    L.r64 = dev_alloc<double>(L.N * R, &ae, pz);
+    L.r32 = dev_alloc<float>(L.N * R, &ae, pz);
     if (k < K) {
-      L.g64 = dev_alloc<double>(L.N * R, &ae);
-      L.z64 = dev_alloc<double>(L.N * R, &ae);
-      L.g32 = dev_alloc<float>(L.N * R, &ae);
-      L.z32 = dev_alloc<float>(L.N * R, &ae);
+      L.g64 = dev_alloc<double>(L.N * R, &ae, pz);
+      L.z64 = dev_alloc<double>(L.N * R, &ae, pz);
+      L.g32 = dev_alloc<float>(L.N * R, &ae, pz);
+      L.z32 = dev_alloc<float>(L.N * R, &ae, pz);
     }
   }
   const int64_t NF = h->lv[K].N * R;
   for (int i = 0; i < 6; ++i) {
-    h->w64[i] = dev_alloc<double>(NF, &ae);
-    h->w32[i] = dev_alloc<float>(NF, &ae);
+    h->w64[i] = dev_alloc<double>(NF, &ae, pz);
+    h->w32[i] = dev_alloc<float>(NF, &ae, pz);
   }
-  h->red = dev_alloc<double>(2 * (int64_t)reduction_blocks(h->sm_count) * R + 2 * R + 8, &ae);
-  h->umax = dev_alloc<unsigned long long>(R, &ae);
-  h->coef = dev_alloc<double>(4 * 2 * R, &ae);
-  h->cg = dev_alloc<double>(8 * R, &ae);
+  h->red = dev_alloc<double>(2 * (int64_t)reduction_blocks(h->sm_count) * R + 2 * R + 8, &ae, pz);
+  h->umax = dev_alloc<unsigned long long>(R, &ae, pz);
+  h->coef = dev_alloc<double>(4 * 2 * R, &ae, pz);
+  h->cg = dev_alloc<double>(8 * R, &ae, pz);
   h->status = dev_alloc<int>(4, &ae);
   if (ae == cudaSuccess) ae = cudaMallocHost((void**)&h->red_host, (2 * R + 8) * sizeof(double));
   if (ae == cudaSuccess) ae = cudaMallocHost((void**)&h->coef_host, 4 * 2 * R * sizeof(double));

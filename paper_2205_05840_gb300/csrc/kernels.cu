@@ -625,8 +625,9 @@ __global__ void __launch_bounds__(128) k_patch_dense(int n, PatchFamily fam, con
 // bits together); a product term d r is formed as hi*hi (rounded) plus its
 // exact rounding error (fma) plus the two cross terms, and added to a
 // running float sum with an error-free two-sum whose error joins a float
-// compensation; every kFold terms the pair is folded into an FP64
-// accumulator.  The residual block of a pass is scaled by a power of two so
+// compensation; every kFold terms that pair is folded the same way into a
+// running pair, converted to FP64 once at the end (FP64 instructions run at
+// 1/64 of the FP32 rate here, so none sits in the inner loops).  The residual block of a pass is scaled by a power of two so
 // that its largest entry is near 1 (the float exponent range then holds
 // every useful entry), and the result is scaled back.  The sums stay within
 // about 1e-14 of the FP64 ones relative to the largest term.
@@ -641,7 +642,41 @@ __device__ __forceinline__ int edge_lin(int n, int d, int i, int j, int k) {
                                                      : i + (n - 1) * j + (n - 1) * (n - 1) * k;
 }
 
-__global__ void __launch_bounds__(kDfThreads) k_patch_dense_df(int n, PatchFamily fam, const double* __restrict__ D,
+// v 2^-ex as a pair of floats hi + lo on the integer pipe (no FP64
+// instruction): hi takes the top 24 bits of the significand, lo the next 24
+// (the last 5 of 53 are dropped: relative error below 2^-47 of |v|); v whose
+// scaled magnitude is below 2^-100 (the pass maximum is scaled into [1, 2))
+// gives 0; Inf and NaN give NaN
+__device__ __forceinline__ void split_scaled(double v, int ex, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7FF);
+  const int eu = e - 1023 - ex;
+  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const unsigned r29 = (unsigned)(m & 0x1FFFFFFFull);
+  const int top = 31 - __clz(r29 | 1u);  // leading one of the low 29 bits
+  const int el = eu - 52 + top;
+  const unsigned ml = top >= 23 ? r29 >> (top - 23) : r29 << (23 - top);
+  const bool tiny = e == 0 || eu < -100;
+  hi = tiny ? 0.f : __uint_as_float(sign | ((unsigned)(eu + 127) << 23) | ((unsigned)(m >> 29) & 0x7FFFFFu));
+  lo = (tiny || r29 == 0u || el < -126) ? 0.f : __uint_as_float(sign | ((unsigned)(el + 127) << 23) | (ml & 0x7FFFFFu));
+  if (e == 0x7FF) hi = lo = __uint_as_float(0x7FC00000u);
+}
+
+// a float as a double on the integer pipe: normal floats and zeros exactly,
+// subnormals as zero, Inf and NaN as NaN
+__device__ __forceinline__ double float_bits_to_double(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned long long s = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned ef = (u >> 23) & 0xFFu;
+  const unsigned long long bits =
+      ef == 0u ? s
+               : (ef == 0xFFu ? 0x7FF8000000000000ull
+                              : s | ((unsigned long long)(ef + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29));
+  return __longlong_as_double((long long)bits);
+}
+
+__global__ void __launch_bounds__(kDfThreads, 2) k_patch_dense_df(int n, PatchFamily fam, const double* __restrict__ D,
                                                                double eta, const double* __restrict__ r,
                                                                double* __restrict__ z) {
   pdl_start();
@@ -660,11 +695,13 @@ __global__ void __launch_bounds__(kDfThreads) k_patch_dense_df(int n, PatchFamil
   const int64_t N3 = (int64_t)n * (n - 1) * (n - 1);
   r += (int64_t)blockIdx.y * 3 * N3;
   z += (int64_t)blockIdx.y * 3 * N3;
-  for (int q = threadIdx.x; q < nl * nl; q += blockDim.x) {
-    const double d = D[q];
-    const float h = (float)d;
-    Dh[q] = h;
-    Dl[q] = (float)(d - (double)h);
+  {
+    // the operator's float parts follow its FP64 entries (dense_stride)
+    const float* hl = reinterpret_cast<const float*>(D + nl * nl);
+    for (int q = threadIdx.x; q < nl * nl; q += blockDim.x) {
+      Dh[q] = __ldg(hl + q);
+      Dl[q] = __ldg(hl + nl * nl + q);
+    }
   }
   const int bx = fam.b[0], by = fam.b[1], bz = fam.b[2];
   const int cx = bx * (by - 1) * (bz - 1), cy = (bx - 1) * by * (bz - 1);
@@ -711,32 +748,30 @@ __global__ void __launch_bounds__(kDfThreads) k_patch_dense_df(int n, PatchFamil
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) atomicMax(amax, m);
     __syncthreads();
-    // a power of two that brings the largest entry of the pass into [1, 2)
-    // (a pass of zeros keeps 1; Inf or NaN propagate)
+    // 2^-ex brings the largest entry of the pass into [1, 2) (a pass of zeros
+    // keeps ex = 0; Inf or NaN propagate as NaN)
     const unsigned mw = *amax;
     const int ex = mw == 0 ? 0 : (int)(mw >> 20) - 1023;
-    const double sc = ldexp(1.0, -ex);
     if (active) {
 #pragma unroll
       for (int p = 0; p < H; ++p) {
-        const double v = rv[p] * sc;
-        const float h = (float)v;
-        Rh[row * kPBdf + half * H + p] = h;
-        Rl[row * kPBdf + half * H + p] = (float)(v - (double)h);
+        float hi, lo;
+        split_scaled(rv[p], ex, hi, lo);
+        Rh[row * kPBdf + half * H + p] = hi;
+        Rl[row * kPBdf + half * H + p] = lo;
       }
     }
     __syncthreads();
     if (active) {
-      double acc[H];
-      float sh[H], sl[H];
+      float ah[H], al[H], sh[H], sl[H];
 #pragma unroll
       for (int p = 0; p < H; ++p) {
-        acc[p] = 0.0;
-        sh[p] = 0.f;
-        sl[p] = 0.f;
+        ah[p] = al[p] = 0.f;
+        sh[p] = sl[p] = 0.f;
       }
       for (int c0 = 0; c0 < nl; c0 += kFold) {
         const int c1 = c0 + kFold < nl ? c0 + kFold : nl;
+        #pragma unroll 2
         for (int c = c0; c < c1; ++c) {
           const float dh = Dh[c * nl + row], dl = Dl[c * nl + row];
           const float4* rh4 = reinterpret_cast<const float4*>(Rh + c * kPBdf + half * H);
@@ -756,18 +791,24 @@ __global__ void __launch_bounds__(kDfThreads) k_patch_dense_df(int n, PatchFamil
             sl[p] = __fadd_rn(sl[p], __fadd_rn(e2, low));
           }
         }
+        // fold the chunk's pair into the running pair (ah, al) the same way
 #pragma unroll
         for (int p = 0; p < H; ++p) {
-          acc[p] += (double)sh[p] + (double)sl[p];
-          sh[p] = 0.f;
-          sl[p] = 0.f;
+          const float t = __fadd_rn(ah[p], sh[p]);
+          const float bb = __fsub_rn(t, ah[p]);
+          const float e2 = __fadd_rn(__fsub_rn(ah[p], __fsub_rn(t, bb)), __fsub_rn(sh[p], bb));
+          ah[p] = t;
+          al[p] = __fadd_rn(al[p], __fadd_rn(e2, sl[p]));
+          sh[p] = sl[p] = 0.f;
         }
       }
-      const double back = eta / sc;
+      const double back = ldexp(eta, ex);
 #pragma unroll
       for (int p = 0; p < H; ++p) {
         const int pp = half * H + p;
-        if (base + pp < NP) atomicAdd(z + pbase[3 * pp + my_d] + my_off, back * acc[p]);
+        if (base + pp < NP)
+          atomicAdd(z + pbase[3 * pp + my_d] + my_off,
+                    back * (float_bits_to_double(ah[p]) + float_bits_to_double(al[p])));
       }
     }
     __syncthreads();  // pbase, Rh, Rl are rewritten by the next pass
@@ -1444,8 +1485,9 @@ cudaError_t prepare_vertex_dense() {
   if constexpr (std::is_same<T, double>::value)
     return cudaFuncSetAttribute(k_patch_dense_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)patch_dense_df_smem(108));
-  return cudaFuncSetAttribute(k_patch_dense<T, pb_for<T>()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)patch_dense_smem<T>(108));
+  else
+    return cudaFuncSetAttribute(k_patch_dense<T, pb_for<T>()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)patch_dense_smem<T>(108));
 }
 
 template <typename T>
@@ -1462,9 +1504,10 @@ void launch_patch_dense(cudaStream_t s, int sm, int n, const PatchFamily& fam, c
     if (bdf > cap) bdf = cap;
     launch_pdl(k_patch_dense_df, dim3((int)bdf, R), kDfThreads, patch_dense_df_smem(fam.nloc), s, n, fam, D, eta, r,
                z);
-    return;
+  } else {
+    launch_pdl(k_patch_dense<T, PB>, dim3((int)blocks, R), 128, patch_dense_smem<T>(fam.nloc), s, n, fam, D, (T)eta,
+               r, z);
   }
-  launch_pdl(k_patch_dense<T, PB>, dim3((int)blocks, R), 128, patch_dense_smem<T>(fam.nloc), s, n, fam, D, (T)eta, r, z);
 }
 
 PatchFamily vertex_family(int n) {

@@ -47,6 +47,15 @@ void launch_patch_gram(cudaStream_t s, int sm, int n, const PatchFamily& fam, in
                        double eta, const T* r, T* z, int R);
 template <typename T>
 cudaError_t prepare_patch_gram();
+// entries of one dense nl x nl operator in device memory: FP32 operators
+// plain; FP64 ones followed by their hi / lo float parts (the double-float
+// kernel's operands)
+template <typename T>
+constexpr size_t dense_stride(int nl) {
+  return sizeof(T) == 8 ? 2 * (size_t)nl * nl : (size_t)nl * nl;
+}
+// z += eta * D r_p for every patch p of the family; D: one operator in the
+// dense_stride<T> layout (FP64: the double-float kernel)
 template <typename T>
 void launch_patch_dense(cudaStream_t s, int sm, int n, const PatchFamily& fam, const T* D, double eta, const T* r,
                         T* z, int R);

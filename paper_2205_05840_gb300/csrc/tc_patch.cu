@@ -388,33 +388,26 @@ __device__ __forceinline__ void scatter_rows(uint32_t tmem, float* acc, int warp
 template <bool FP16>
 __global__ void __launch_bounds__(kThreads, 3)
     k_tc_smoother(int n, const uint8_t* __restrict__ img, const float* __restrict__ AinvT, float eta,
-                  const float* __restrict__ r, float* __restrict__ z, int* __restrict__ status) {
-  pdl_start();
+                  const float* __restrict__ r, float* __restrict__ z, int* __restrict__ status, int R) {
+  // the next kernel may start its own set-up now; this kernel's set-up
+  // (TMEM, barriers, the W images and A_T^{-1}) reads nothing the previous
+  // kernel writes, so it runs before the wait for that kernel
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   extern __shared__ __align__(128) uint8_t smem[];
-  // a CTA of an earlier launch gave up on a wait: do nothing until the host
-  // has read and cleared the status word
-  if (*reinterpret_cast<volatile int*>(status) != 0) return;
-
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nv = n / 2 - 1;
   const int nbx = (nv + kBX - 1) / kBX, nby = (nv + kBY - 1) / kBY, nbz = (nv + kBZ - 1) / kBZ;
   const int nbr = nbx * nby * nbz;
-  const int rhs = blockIdx.x / nbr;
-  const int brick = blockIdx.x - rhs * nbr;
-  const int bx = brick % nbx, by = (brick / nbx) % nby, bz = brick / (nbx * nby);
-  const int VX = 1 + bx * kBX, VY = 1 + by * kBY, VZ = 1 + bz * kBZ;  // first vertex of the brick
-  const uint32_t n1 = n - 1, N3 = (uint32_t)n * n1 * n1;            // < 2^31 (checked on the host)
-  r += (int64_t)rhs * 3 * N3;
-  z += (int64_t)rhs * 3 * N3;
+  const uint32_t n1 = n - 1, N3 = (uint32_t)n * n1 * n1;  // < 2^31 (checked on the host)
 
-  float* R = reinterpret_cast<float*>(smem + OFF_R);
+  float* R_ = reinterpret_cast<float*>(smem + OFF_R);
   float* ACC = reinterpret_cast<float*>(smem + OFF_A);  // region accumulator, over A' once D' is complete
   float* At = reinterpret_cast<float*>(smem + OFF_AT);
   const uint32_t bar0 = smem_u32(smem + OFF_BAR), bar1 = bar0 + 8;
   uint32_t* tm_slot = reinterpret_cast<uint32_t*>(smem + OFF_TM);
   float* red = reinterpret_cast<float*>(smem + OFF_RED);
 
-  // ---- set-up: TMEM, barriers; copies of r and of both W images --------------
+  // ---- set-up, once per CTA: TMEM, barriers, both W images, A_T^{-1} ---------
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tm_slot)),
                  "r"(kTmemCols)
@@ -428,144 +421,171 @@ __global__ void __launch_bounds__(kThreads, 3)
   }
   if (tid < 36) At[tid] = __ldg(AinvT + tid);
   {
-    const uint32_t rbase = smem_u32(R);
-    auto stage = [&](uint32_t e, uint32_t off, bool in) {
-      cp_async4(rbase + 4u * (e & 8191u), r + (in ? off : 0u), in ? 4u : 0u);
-    };
-    walk_region<0>(n, VX, VY, VZ, tid, stage);
-    walk_region<1>(n, VX, VY, VZ, tid, stage);
-    walk_region<2>(n, VX, VY, VZ, tid, stage);
     const uint4* src = reinterpret_cast<const uint4*>(img);
     const uint32_t wbase = smem_u32(smem + OFF_B1);
     for (int q = tid; q < kImgBytes / 16; q += kThreads)
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(wbase + 16u * q), "l"(src + q) : "memory");
-    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+    asm volatile("cp.async.commit_group;" ::: "memory");
   }
   const float wscale = __ldg(reinterpret_cast<const float*>(img + kImgBytes));  // 1 / s_w^2
+  asm volatile("griddepcontrol.wait;" ::: "memory");  // r, z and the status word of the previous kernels
+  // a CTA of an earlier launch gave up on a wait: do nothing until the host
+  // has read and cleared the status word
+  const bool quiet = *reinterpret_cast<volatile int*>(status) != 0;
   fence_before();
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tm_slot;
 
-  // fp16 operands: scale r by a power of two so that max |r| <= 1 on the region
-  float rscale = 1.f;
-  if constexpr (FP16) {
-    float amax = 0.f;
-    for (int q = tid; q < kRegionAll; q += kThreads) amax = fmaxf(amax, fabsf(R[q]));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-    if (lane == 0) red[warp] = amax;
-    __syncthreads();
-    float m = 0.f;
-#pragma unroll
-    for (int w = 0; w < kThreads / 32; ++w) m = fmaxf(m, red[w]);
-    if (m > 0.f) rscale = exp2f(-ceilf(log2f(m)));
-  }
+  // ---- one brick of one right-hand side per pass -----------------------------
+  uint32_t parity = 0;
+  for (int w = quiet ? R * nbr : blockIdx.x; w < R * nbr; w += gridDim.x, parity ^= 1u) {
+    const int rhs = w / nbr, brick = w - rhs * nbr;
+    const int bx = brick % nbx, by = (brick / nbx) % nby, bz = brick / (nbx * nby);
+    const int VX = 1 + bx * kBX, VY = 1 + by * kBY, VZ = 1 + bz * kBZ;  // first vertex of the brick
+    const float* rr = r + (int64_t)rhs * 3 * N3;
+    float* zr = z + (int64_t)rhs * 3 * N3;
 
-  // ---- 2. gather the patch vectors into A (two threads per row) --------------
-  {
-    const int p = tid & (kM - 1), half = tid >> 7;
-    const int a = p % kBX, b = (p / kBX) % kBY, c = p / (kBX * kBY);
-    const bool live = VX + a <= nv && VY + b <= nv && VZ + c <= nv;
-    uint8_t* A = smem + OFF_A;
-    if (half == 0)
-      gather_chunks<0, FP16>(R, A, p, a, b, c, live, rscale);
-    else
-      gather_chunks<7, FP16>(R, A, p, a, b, c, live, rscale);
-  }
-  fence_async_smem();
-  __syncthreads();
-
-  // ---- 3. D = A W -------------------------------------------------------------
-  if (tid == 0) {
-    fence_after();
-    issue_mma1<FP16>(tmem, smem_u32(smem + OFF_A), smem_u32(smem + OFF_B1), bar0);
-  }
-  bool ok = mbar_wait(bar0, 0);
-  fence_after();
-
-  // ---- 4. A' = low-precision copy of D (8 warps: lane quadrant x column half)
-  if (ok) convert_d<FP16>(tmem, smem + OFF_A, warp, lane);
-  fence_async_smem();
-  fence_before();
-  __syncthreads();
-
-  // ---- 5. D' = A' W^t, written over D -----------------------------------------
-  // (issued only when thread 0 saw the first product complete; red[8] tells
-  // every thread whether it was)
-  if (tid == 0) {
-    red[8] = ok ? 1.f : 0.f;
-    if (ok) {
-      fence_after();
-      issue_mma2<FP16>(tmem, smem_u32(smem + OFF_A), smem_u32(smem + OFF_B2), bar1);
+    // ---- 1. stage r on the region ---------------------------------------------
+    {
+      const uint32_t rbase = smem_u32(R_);
+      auto stage = [&](uint32_t e, uint32_t off, bool in) {
+        cp_async4(rbase + 4u * (e & 8191u), rr + (in ? off : 0u), in ? 4u : 0u);
+      };
+      walk_region<0>(n, VX, VY, VZ, tid, stage);
+      walk_region<1>(n, VX, VY, VZ, tid, stage);
+      walk_region<2>(n, VX, VY, VZ, tid, stage);
+      asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
     }
-  }
-  if (ok) ok = mbar_wait(bar1, 0);
-  fence_after();
-  // the CTA goes on only if every thread saw both products complete
-  ok = __syncthreads_and(ok) != 0;
-  if (!ok) {
-    // a wait gave up: the products issued so far may still be reading A', W
-    // and writing TMEM.  Record the timeout, touch no shared memory, wait
-    // (again bounded) for those products, free TMEM and return.
-    if (tid == 0) atomicExch(status, kTimeout);
-    mbar_wait(bar0, 0);
-    if (red[8] != 0.f) mbar_wait(bar1, 0);
     fence_before();
     __syncthreads();
-    if (warp == 0) {
+    fence_after();
+
+    // fp16 operands: scale r by a power of two so that max |r| <= 1 on the region
+    float rscale = 1.f;
+    if constexpr (FP16) {
+      float amax = 0.f;
+      for (int q = tid; q < kRegionAll; q += kThreads) amax = fmaxf(amax, fabsf(R_[q]));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+      if (lane == 0) red[warp] = amax;
+      __syncthreads();
+      float m = 0.f;
+#pragma unroll
+      for (int q = 0; q < kThreads / 32; ++q) m = fmaxf(m, red[q]);
+      if (m > 0.f) rscale = exp2f(-ceilf(log2f(m)));
+    }
+
+    // ---- 2. gather the patch vectors into A (two threads per row) --------------
+    {
+      const int p = tid & (kM - 1), half = tid >> 7;
+      const int a = p % kBX, b = (p / kBX) % kBY, c = p / (kBX * kBY);
+      const bool live = VX + a <= nv && VY + b <= nv && VZ + c <= nv;
+      uint8_t* A = smem + OFF_A;
+      if (half == 0)
+        gather_chunks<0, FP16>(R_, A, p, a, b, c, live, rscale);
+      else
+        gather_chunks<7, FP16>(R_, A, p, a, b, c, live, rscale);
+    }
+    fence_async_smem();
+    __syncthreads();
+
+    // ---- 3. D = A W -------------------------------------------------------------
+    if (tid == 0) {
       fence_after();
-      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+      issue_mma1<FP16>(tmem, smem_u32(smem + OFF_A), smem_u32(smem + OFF_B1), bar0);
     }
-    return;
-  }
-  // A' has been read by the tensor cores: its space becomes the accumulator
-  for (int q = tid; q < kRegionAll; q += kThreads) ACC[q] = 0.f;
-  __syncthreads();
+    bool ok = mbar_wait(bar0, parity);
+    fence_after();
 
-  // ---- 6. accumulate: patch outputs (rows of D') and interior-space solves ----
-  if (ok) {
-    const int prow = (warp & 3) * 32 + lane;
-    const int a = prow % kBX, b = (prow / kBX) % kBY, c = prow / (kBX * kBY);
-    const bool live = VX + a <= nv && VY + b <= nv && VZ + c <= nv;
-    scatter_rows(tmem, ACC, warp, lane, live ? wscale / rscale : 0.f);  // live rows add
-  }
-  // interior spaces of the coarse elements the brick owns: E in [V0-1, V1-1]
-  // per axis, plus element nv on the last brick of an axis (its last vertex
-  // is nv); the 6 interior edges of E are row t = 2d + (segment parity)
-  if (ok) {
-    const int ex1 = VX + kBX - 1 >= nv ? nv : VX + kBX - 2;
-    const int ey1 = VY + kBY - 1 >= nv ? nv : VY + kBY - 2;
-    const int ez1 = VZ + kBZ - 1 >= nv ? nv : VZ + kBZ - 2;
-    const int mx = ex1 - VX + 2, my = ey1 - VY + 2, mz = ez1 - VZ + 2;
-    for (int q = tid; q < mx * my * mz * 6; q += kThreads) {
-      const int t = q % 6, e = q / 6;
-      const int ei = e % mx, ej = (e / mx) % my, ek = e / (mx * my);  // E - (V0 - 1)
-      int idx[6];
-#pragma unroll
-      for (int w = 0; w < 6; ++w) idx[w] = bubble_elem(w, ei, ej, ek);
-      float s = 0.f;
-      int it = idx[0];
-#pragma unroll
-      for (int w = 0; w < 6; ++w) {
-        s += At[t * 6 + w] * R[idx[w]];
-        if (w == t) it = idx[w];
+    // ---- 4. A' = low-precision copy of D (8 warps: lane quadrant x column half)
+    if (ok) convert_d<FP16>(tmem, smem + OFF_A, warp, lane);
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+
+    // ---- 5. D' = A' W^t, written over D -----------------------------------------
+    // (issued only when thread 0 saw the first product complete; red[8] tells
+    // every thread whether it was)
+    if (tid == 0) {
+      red[8] = ok ? 1.f : 0.f;
+      if (ok) {
+        fence_after();
+        issue_mma2<FP16>(tmem, smem_u32(smem + OFF_A), smem_u32(smem + OFF_B2), bar1);
       }
-      atomicAdd(ACC + it, s);
     }
-  }
-  fence_before();
-  __syncthreads();
+    if (ok) ok = mbar_wait(bar1, parity);
+    fence_after();
+    // the CTA goes on only if every thread saw both products complete
+    ok = __syncthreads_and(ok) != 0;
+    if (!ok) {
+      // a wait gave up: the products issued so far may still be reading A', W
+      // and writing TMEM.  Record the timeout, touch no shared memory, wait
+      // (again bounded) for those products, free TMEM and return.
+      if (tid == 0) atomicExch(status, kTimeout);
+      mbar_wait(bar0, parity);
+      if (red[8] != 0.f) mbar_wait(bar1, parity);
+      fence_before();
+      __syncthreads();
+      if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+      }
+      return;
+    }
+    // A' has been read by the tensor cores: its space becomes the accumulator
+    for (int q = tid; q < kRegionAll; q += kThreads) ACC[q] = 0.f;
+    __syncthreads();
 
-  // ---- 7. z += eta * accumulator ---------------------------------------------
-  if (ok) {
-    auto flush = [&](uint32_t e, uint32_t off, bool in) {
-      if (in) atomicAdd(z + off, eta * ACC[e & 8191u]);
-    };
-    walk_region<0>(n, VX, VY, VZ, tid, flush);
-    walk_region<1>(n, VX, VY, VZ, tid, flush);
-    walk_region<2>(n, VX, VY, VZ, tid, flush);
+    // ---- 6. accumulate: patch outputs (rows of D') and interior-space solves ----
+    {
+      const int prow = (warp & 3) * 32 + lane;
+      const int a = prow % kBX, b = (prow / kBX) % kBY, c = prow / (kBX * kBY);
+      const bool live = VX + a <= nv && VY + b <= nv && VZ + c <= nv;
+      scatter_rows(tmem, ACC, warp, lane, live ? wscale / rscale : 0.f);  // live rows add
+    }
+    // interior spaces of the coarse elements the brick owns: E in [V0-1, V1-1]
+    // per axis, plus element nv on the last brick of an axis (its last vertex
+    // is nv); the 6 interior edges of E are row t = 2d + (segment parity)
+    {
+      const int ex1 = VX + kBX - 1 >= nv ? nv : VX + kBX - 2;
+      const int ey1 = VY + kBY - 1 >= nv ? nv : VY + kBY - 2;
+      const int ez1 = VZ + kBZ - 1 >= nv ? nv : VZ + kBZ - 2;
+      const int mx = ex1 - VX + 2, my = ey1 - VY + 2, mz = ez1 - VZ + 2;
+      for (int q = tid; q < mx * my * mz * 6; q += kThreads) {
+        const int t = q % 6, e = q / 6;
+        const int ei = e % mx, ej = (e / mx) % my, ek = e / (mx * my);  // E - (V0 - 1)
+        int idx[6];
+#pragma unroll
+        for (int u = 0; u < 6; ++u) idx[u] = bubble_elem(u, ei, ej, ek);
+        float sum = 0.f;
+        int it = idx[0];
+#pragma unroll
+        for (int u = 0; u < 6; ++u) {
+          sum += At[t * 6 + u] * R_[idx[u]];
+          if (u == t) it = idx[u];
+        }
+        atomicAdd(ACC + it, sum);
+      }
+    }
+    fence_before();
+    __syncthreads();
+
+    // ---- 7. z += eta * accumulator ---------------------------------------------
+    {
+      auto flush = [&](uint32_t e, uint32_t off, bool in) {
+        if (in) atomicAdd(zr + off, eta * ACC[e & 8191u]);
+      };
+      walk_region<0>(n, VX, VY, VZ, tid, flush);
+      walk_region<1>(n, VX, VY, VZ, tid, flush);
+      walk_region<2>(n, VX, VY, VZ, tid, flush);
+    }
+    // the next pass rewrites R, A (= the accumulator) and TMEM
+    fence_before();
+    __syncthreads();
+    fence_after();
   }
+  if (quiet) asm volatile("cp.async.wait_group 0;" ::: "memory");  // the W images copied for nothing
   if (warp == 0) {
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
@@ -928,15 +948,20 @@ void launch_tc_smoother_field(cudaStream_t s, int n, const void* imgs, bool fp16
                                                                 gmask, (float)eta, r, z, status);
 }
 
-void launch_tc_smoother(cudaStream_t s, int n, const void* Wimg, bool fp16, const float* AinvT, double eta,
+void launch_tc_smoother(cudaStream_t s, int sm, int n, const void* Wimg, bool fp16, const float* AinvT, double eta,
                         const float* r, float* z, int* status, int R) {
   const int nv = n / 2 - 1;
   if (nv < 1) return;
-  const int grid = ((nv + kBX - 1) / kBX) * ((nv + kBY - 1) / kBY) * ((nv + kBZ - 1) / kBZ) * R;
+  // persistent: at most three CTAs per SM (the shared-memory limit), each
+  // taking every grid-th brick of every right-hand side
+  const int64_t work = (int64_t)((nv + kBX - 1) / kBX) * ((nv + kBY - 1) / kBY) * ((nv + kBZ - 1) / kBZ) * R;
+  const int grid = (int)(work < 3LL * sm ? work : 3LL * sm);
   if (fp16)
-    launch_pdl(k_tc_smoother<true>, grid, kThreads, kSmem, s, n, (const uint8_t*)Wimg, AinvT, (float)eta, r, z, status);
+    launch_pdl(k_tc_smoother<true>, grid, kThreads, kSmem, s, n, (const uint8_t*)Wimg, AinvT, (float)eta, r, z, status,
+               R);
   else
-    launch_pdl(k_tc_smoother<false>, grid, kThreads, kSmem, s, n, (const uint8_t*)Wimg, AinvT, (float)eta, r, z, status);
+    launch_pdl(k_tc_smoother<false>, grid, kThreads, kSmem, s, n, (const uint8_t*)Wimg, AinvT, (float)eta, r, z,
+               status, R);
 }
 
 

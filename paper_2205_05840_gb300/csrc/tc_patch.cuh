@@ -19,8 +19,9 @@ cudaError_t prepare_tc_patch();
 // z += eta * (sum_T J_T A_T^{-1} J_T^t r + sum_V J_V A_V^{-1} J_V^t r) on
 // level n (eq. (Preconditioner P); float r, z; R right-hand sides; AinvT the
 // 6x6 interior-space inverse, row-major); on a device-side timeout the
-// kernel writes a nonzero code to *status and adds nothing.
-void launch_tc_smoother(cudaStream_t s, int n, const void* Wimg, bool fp16, const float* AinvT, double eta,
+// kernel writes a nonzero code to *status and adds nothing.  Persistent grid
+// of at most 3 CTAs per SM (sm: the device's SM count).
+void launch_tc_smoother(cudaStream_t s, int sm, int n, const void* Wimg, bool fp16, const float* AinvT, double eta,
                         const float* r, float* z, int* status, int R);
 // Coefficient per hexahedron: device images of the Gram factors of ngroups
 // vertex-patch groups (W: ngroups x 108 x 60), the per-brick group lists
