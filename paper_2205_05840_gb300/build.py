@@ -15,7 +15,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libndmg.so")
-SOURCES = ["setup.cpp", "field.cpp", "kernels.cu", "tc_patch.cu", "tc_cell.cu", "coarse_cycle.cu", "api.cu", "noalloc.cu", "probe.cu"]
+SOURCES = ["setup.cpp", "field.cpp", "kernels.cu", "tc_patch.cu", "tc_cell.cu", "coarse_cycle.cu", "api.cu", "noalloc.cu", "probe.cu", "patch_sym.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr", "-I" + os.path.join(PKG, "..", "include")]

@@ -133,6 +133,29 @@ cudaError_t upload_dense64(double** dst, const std::vector<double>& src, int nl)
   return cudaMemcpy(*dst, tmp.data(), sizeof(double) * tmp.size(), cudaMemcpyHostToDevice);
 }
 
+// an FP64 dense patch operator in the mirror-symmetry basis of its box
+// (words = 0: the dense double-float kernel is used instead)
+cudaError_t upload_sym(uint32_t** dst, int* words, const PatchFamily& fam, const std::vector<double>& D) {
+  std::vector<uint32_t> blob;
+  double dropped = 0.0;
+  // the off-block part of D is its set-up rounding (it is zero for the exact
+  // operator); more than that means the box lacks the symmetry
+  if (!build_patch_sym(fam, D.data(), &blob, &dropped) || !(dropped < 1e-6)) {
+    *words = 0;
+    return cudaSuccess;
+  }
+  if (*dst && *words != (int)blob.size()) {
+    cudaFree(*dst);
+    *dst = nullptr;
+  }
+  if (!*dst) {
+    cudaError_t e = cudaMalloc((void**)dst, sizeof(uint32_t) * blob.size());
+    if (e != cudaSuccess) return e;
+  }
+  *words = (int)blob.size();
+  return cudaMemcpy(*dst, blob.data(), sizeof(uint32_t) * blob.size(), cudaMemcpyHostToDevice);
+}
+
 // fresh device copy of a host array (any previous buffer freed first)
 template <typename D, typename S>
 cudaError_t upload_fresh(D** dst, const std::vector<S>& src) {
@@ -189,14 +212,15 @@ const float* lv_a(DevLevel& L, float*) { return L.a32; }
 // y = g - (cK K + cM M) u (or (cK K + cM M) u when g is null) on level k: the
 // constant-coefficient stencil, or with a coefficient per hexahedron the
 // field stencil (cK = h times the factor; the coefficients are in K)
+// (umax_ready: h->umax already holds max |u| per right-hand side)
 template <typename T>
-void stencil(ndmg_t* h, int k, double cK, double cM, const T* u, const T* g, T* y) {
+void stencil(ndmg_t* h, int k, double cK, double cM, const T* u, const T* g, T* y, bool umax_ready = false) {
   DevLevel& L = h->lv[k];
   const int kz = L.kz[sizeof(T) == 8 ? 1 : 0];
   if (h->field)
     launch_stencil_field<T>(h->stream, h->sm_count, L.n, cK, cM, u, g, y, nrhs(h), lv_a(L, (T*)nullptr), kz);
   else
-    launch_stencil<T>(h->stream, h->sm_count, L.n, cK, cM, u, g, y, nrhs(h), h->umax, kz);
+    launch_stencil<T>(h->stream, h->sm_count, L.n, cK, cM, u, g, y, nrhs(h), h->umax, kz, umax_ready);
 }
 
 template <typename T>
@@ -207,10 +231,10 @@ void op_residual(ndmg_t* h, int k, const T* g, const T* z, T* r) {
 }
 
 template <typename T>
-void op_apply(ndmg_t* h, int k, const T* x, T* y) {
+void op_apply(ndmg_t* h, int k, const T* x, T* y, bool umax_ready = false) {
   DevLevel& L = h->lv[k];
   Span sp(h, NDMG_K_STENCIL, 2.0 * sizeof(T) * L.N * nrhs(h));  // read x; write y
-  stencil<T>(h, k, L.cK, L.cM, x, (const T*)nullptr, y);
+  stencil<T>(h, k, L.cK, L.cM, x, (const T*)nullptr, y, umax_ready);
 }
 
 // y = g + (a K + b M) x (or (a K + b M) x when g is null): the stencil in
@@ -235,6 +259,11 @@ void op_edge_terms(ndmg_t* h, int k, const T* De, const T* r, T* z) {
   for (int d = 0; d < 3; ++d) {
     const PatchFamily fam = edge_family(L.n, d);
     Span sp(h, NDMG_K_PATCH, (double)fam.np[0] * fam.np[1] * fam.np[2] * 2.0 * 42 * 42 * R);
+    if constexpr (std::is_same<T, double>::value)
+      if (L.sym_e_words[d] > 0) {
+        launch_patch_sym(h->stream, h->sm_count, L.n, fam, L.sym_e[d], L.sym_e_words[d], h->o.eta, r, z, R);
+        continue;
+      }
     launch_patch_dense<T>(h->stream, h->sm_count, L.n, fam, De + d * dense_stride<T>(42), h->o.eta, r, z, R);
   }
 }
@@ -255,7 +284,13 @@ void op_smoother_s4(ndmg_t* h, int k, const T* r, T* z) {
   {
     const PatchFamily fam = subdomain4_family(L.n);
     Span sp(h, NDMG_K_BUBBLE, (double)fam.np[0] * fam.np[1] * fam.np[2] * 2.0 * 108 * 108 * R);
-    launch_patch_dense<T>(h->stream, h->sm_count, L.n, fam, lv_Ainv(L, (T*)nullptr), h->o.eta, r, z, R);
+    bool done = false;
+    if constexpr (std::is_same<T, double>::value)
+      if (L.sym_s4_words > 0) {
+        launch_patch_sym(h->stream, h->sm_count, L.n, fam, L.sym_s4, L.sym_s4_words, h->o.eta, r, z, R);
+        done = true;
+      }
+    if (!done) launch_patch_dense<T>(h->stream, h->sm_count, L.n, fam, lv_Ainv(L, (T*)nullptr), h->o.eta, r, z, R);
   }
   const PatchFamily fam = vertex4_family(L.n);
   Span sp(h, NDMG_K_PATCH, (double)fam.np[0] * fam.np[1] * fam.np[2] * 4.0 * 1176 * 312 * R);
@@ -323,6 +358,11 @@ void op_smoother(ndmg_t* h, int k, const T* r, T* z) {
     return;
   }
   Span sp(h, NDMG_K_PATCH, num_patches(L.n) * 2.0 * 108 * 108 * R);  // dense 108x108 per patch
+  if constexpr (std::is_same<T, double>::value)
+    if (L.sym_v_words > 0) {
+      launch_patch_sym(h->stream, h->sm_count, L.n, vertex_family(L.n), L.sym_v, L.sym_v_words, h->o.eta, r, z, R);
+      return;
+    }
   launch_vertex_dense<T>(h->stream, h->sm_count, L.n, lv_D(L, (T*)nullptr), h->o.eta, r, z, R);
 }
 
@@ -363,6 +403,13 @@ void op_smoother<float>(ndmg_t* h, int k, const float* r, float* z) {
     Span sp(h, NDMG_K_PATCH, 12.0 * L.N * R);
     launch_tc_smoother(h->stream, h->sm_count, L.n, L.Wtc, h->o.precision == NDMG_PREC_MIXED_FP16, L.AinvT32,
                        h->o.eta, r, z, h->status, R);
+    return;
+  }
+  if (smooth_direct_fits(L.n)) {
+    // a small level: interior and patch solves in one launch, the operator
+    // read from L2
+    Span sp(h, NDMG_K_PATCH, mixed(h) ? 12.0 * L.N * R : num_patches(L.n) * 2.0 * 108 * 108 * R);
+    launch_smooth_direct(h->stream, L.n, L.Dv32, L.AinvT32, h->o.eta, r, z, R);
     return;
   }
   {
@@ -678,8 +725,12 @@ int pcg64(ndmg_t* h, const double* f, double* u, double tol, int maxit, int* ite
   if ((st = cg_push_state(h, rr, rz0, S.done)) != NDMG_OK) return st;
   NDMG_CK(cudaMemcpyAsync(p, z, sizeof(double) * N * R, cudaMemcpyDeviceToDevice, h->stream));
   const CgScalars C = cg_scalars(h);
+  // from the second iteration on, the update that forms p also forms the
+  // fixed-point stencil's max |p| (no separate pass over p); the coefficient
+  // field's FP64 stencil runs in plain FP64 and needs none
+  const bool fuse_max = !h->field;
   for (int it = 1; it <= maxit; ++it) {
-    op_apply<double>(h, K, p, q);
+    op_apply<double>(h, K, p, q, fuse_max && it > 1);
     {
       Span sp(h, NDMG_K_BLAS, 2.0 * 8 * N * R, 2);
       launch_dot2_partial<double>(h->stream, sm, N, p, q, nullptr, nullptr, h->red, R);
@@ -852,8 +903,12 @@ int pcg_mixed(ndmg_t* h, const double* f, double* u, double tol, int maxit, int*
   // V-cycle output
   float* z32 = h->w32[5];
   const CgScalars C = cg_scalars(h);
+  // from the second iteration on, the update that forms p also forms the
+  // fixed-point stencil's max |p| (no separate pass over p); the coefficient
+  // field's FP64 stencil runs in plain FP64 and needs none
+  const bool fuse_max = !h->field;
   for (int it = 1; it <= maxit; ++it) {
-    op_apply<double>(h, K, p, q);
+    op_apply<double>(h, K, p, q, fuse_max && it > 1);
     {
       Span sp(h, NDMG_K_BLAS, 2.0 * 8 * N * R, 2);
       launch_dot2_partial<double>(h->stream, sm, N, p, q, nullptr, nullptr, h->red, R);
@@ -874,12 +929,12 @@ int pcg_mixed(ndmg_t* h, const double* f, double* u, double tol, int maxit, int*
     if ((st = vcycle_f32_graph(h)) != NDMG_OK) return st;
     {
       Span sp(h, NDMG_K_BLAS, (2.0 * 8 + 4) * N * R, 2);
-      launch_dot2_zf_partial(h->stream, sm, N, r, q, z32, h->red, R);
+      launch_dot2_zf_partial(h->stream, sm, N, r, q, z32, h->red, R, fuse_max ? h->umax : nullptr);
       launch_cg_scalars(h->stream, CG_BETA_FLEX, nb, h->red, C, true, h->status, R);
     }
     {
       Span sp(h, NDMG_K_BLAS, (2.0 * 8 + 4) * N * R);
-      launch_axpby_zf(h->stream, sm, N, C.sfrom, z32, C.ab, p, R);
+      launch_axpby_zf(h->stream, sm, N, C.sfrom, z32, C.ab, p, R, fuse_max ? h->umax : nullptr);
     }
   }
   return fail(h, NDMG_NOT_CONVERGED, "PCG reached maxit");
@@ -1018,6 +1073,7 @@ void free_handle(ndmg_t* h) {
     cudaFree(L.g32); cudaFree(L.z32); cudaFree(L.r32);
     cudaFree(L.AinvT64); cudaFree(L.AinvT32); cudaFree(L.Dv64); cudaFree(L.Dv32);
     cudaFree(L.De64); cudaFree(L.De32);
+    cudaFree(L.sym_v); cudaFree(L.sym_e[0]); cudaFree(L.sym_e[1]); cudaFree(L.sym_e[2]); cudaFree(L.sym_s4);
     cudaFree(L.Wtc);
     cudaFree(L.Wcell);
     cudaFree(L.Wv32);
@@ -1080,7 +1136,10 @@ int build_operators(ndmg_t* h) {
   for (int k = 1; k <= h->K; ++k) {
     DevLevel& L = h->lv[k];
     const LocalOps& ops = all[k];
-    if (o.subdomain == 4) NDMG_CK(upload_dense64(&L.AinvT64, ops.AinvT, 108));  // 108 x 108 interior solves
+    if (o.subdomain == 4) {  // 108 x 108 interior solves
+      NDMG_CK(upload_dense64(&L.AinvT64, ops.AinvT, 108));
+      NDMG_CK(upload_sym(&L.sym_s4, &L.sym_s4_words, subdomain4_family(L.n), ops.AinvT));
+    }
     else NDMG_CK(upload(&L.AinvT64, ops.AinvT));
     NDMG_CK(upload(&L.AinvT32, ops.AinvT));
     if (o.subdomain == 4) {
@@ -1095,6 +1154,8 @@ int build_operators(ndmg_t* h) {
       continue;
     }
     NDMG_CK(upload_dense64(&L.Dv64, ops.Dv, 108));
+    NDMG_CK(upload_sym(&L.sym_v, &L.sym_v_words, vertex_family(L.n), ops.Dv));
+    for (int d = 0; d < 3; ++d) NDMG_CK(upload_sym(&L.sym_e[d], &L.sym_e_words[d], edge_family(L.n, d), ops.De[d]));
     NDMG_CK(upload(&L.Dv32, ops.Dv));
     NDMG_CK(upload(&L.Wv32, ops.Wv));
     std::vector<double> de;
@@ -1307,6 +1368,8 @@ int ndmg_create(const ndmg_opts* o, ndmg_t** out) {
   if (ae == cudaSuccess) ae = prepare_stencil<double>();
   if (ae == cudaSuccess) ae = prepare_stencil<float>();
   if (ae == cudaSuccess) ae = prepare_vertex_dense<double>();
+  if (ae == cudaSuccess) ae = prepare_patch_sym();
+  if (ae == cudaSuccess) ae = prepare_smooth_direct();
   if (ae == cudaSuccess) ae = prepare_vertex_dense<float>();
   if (ae == cudaSuccess && h->o.subdomain == 4) ae = prepare_patch_gram<double>();
   if (ae == cudaSuccess && h->o.subdomain == 4) ae = prepare_patch_gram<float>();

@@ -815,6 +815,124 @@ __global__ void __launch_bounds__(kDfThreads, 2) k_patch_dense_df(int n, PatchFa
   }
 }
 
+// The whole smoother correction of eq. (Preconditioner P) for a small level
+// in one launch on CUDA cores: CTAs [0, npb) take PB vertex patches each
+// (every element of the dense 108 x 108 operator feeds PB patches from a
+// register), the other CTAs take the 6 x 6 interior solves of 128 coarse
+// elements each; both add into z with atomics (vertex patches contain
+// element-interior edges).  The operator is
+// copied into shared memory before the kernel waits for its predecessor (it
+// is constant), so on levels with a few hundred patches a CTA's critical path
+// is one gather, the product and the atomics.
+template <int PB>
+__global__ void __launch_bounds__(128) k_smooth_direct(int n, PatchFamily fam, const float* __restrict__ D,
+                                                       const float* __restrict__ Ainv, float eta, int npb,
+                                                       const float* __restrict__ r, float* __restrict__ z) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  constexpr int NL = 108;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* Ds = reinterpret_cast<float*>(smem_raw);  // NL x NL
+  __shared__ float Rs[NL * PB];
+  __shared__ unsigned loff[NL];
+  __shared__ long long pbase[3 * PB];
+  __shared__ float As[36];
+  const int tid = threadIdx.x;
+  const int64_t N3 = (int64_t)n * (n - 1) * (n - 1);
+  if ((int)blockIdx.x < npb) {
+    // the operator (constant: copied before the wait for the previous kernel)
+    {
+      const uint32_t dst = static_cast<uint32_t>(__cvta_generic_to_shared(Ds));
+      const float4* src = reinterpret_cast<const float4*>(D);
+      for (int q = tid; q < NL * NL / 4; q += blockDim.x)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + 16u * q), "l"(src + q) : "memory");
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    // local offsets of the 108 patch edges (independent of the previous kernel)
+    if (tid < NL) {
+      const int bx = fam.b[0], by = fam.b[1], bz = fam.b[2];
+      const int cx = bx * (by - 1) * (bz - 1), cy = (bx - 1) * by * (bz - 1);
+      int d, i, j, k, e = tid;
+      if (e < cx) {
+        d = 0; i = e % bx; j = (e / bx) % (by - 1) + 1; k = e / (bx * (by - 1)) + 1;
+      } else if ((e -= cx) < cy) {
+        d = 1; i = e % (bx - 1) + 1; j = (e / (bx - 1)) % by; k = e / ((bx - 1) * by) + 1;
+      } else {
+        e -= cy;
+        d = 2; i = e % (bx - 1) + 1; j = (e / (bx - 1)) % (by - 1) + 1; k = e / ((bx - 1) * (by - 1));
+      }
+      loff[tid] = (unsigned)edge_lin(n, d, i, j, k) | ((unsigned)d << 30);
+    }
+    const int64_t NP = (int64_t)fam.np[0] * fam.np[1] * fam.np[2];
+    const int64_t base = (int64_t)blockIdx.x * PB;
+    if (tid < 3 * PB) {
+      const int pp = tid / 3, d = tid % 3;
+      const int64_t P = base + pp < NP ? base + pp : NP - 1;
+      const int pa = (int)(P % fam.np[0]) + fam.p0[0];
+      const int pb = (int)((P / fam.np[0]) % fam.np[1]) + fam.p0[1];
+      const int pc = (int)(P / ((int64_t)fam.np[0] * fam.np[1])) + fam.p0[2];
+      pbase[tid] = edge_gidx(n, d, fam.stride * pa - fam.shift[0], fam.stride * pb - fam.shift[1],
+                             fam.stride * pc - fam.shift[2]);
+    }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    r += (int64_t)blockIdx.y * 3 * N3;
+    z += (int64_t)blockIdx.y * 3 * N3;
+    __syncthreads();
+    for (int q = tid; q < NL * PB; q += blockDim.x) {
+      const int pp = q / NL, l = q - pp * NL;
+      const unsigned c = loff[l];
+      Rs[l * PB + pp] = base + pp < NP ? __ldg(r + pbase[3 * pp + (int)(c >> 30)] + (int)(c & 0x3FFFFFFFu)) : 0.f;
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    if (tid < NL) {
+      float acc[PB];
+#pragma unroll
+      for (int p = 0; p < PB; ++p) acc[p] = 0.f;
+#pragma unroll 4
+      for (int c = 0; c < NL; ++c) {
+        const float dv = Ds[c * NL + tid];
+#pragma unroll
+        for (int p = 0; p < PB; ++p) acc[p] = fmaf(dv, Rs[c * PB + p], acc[p]);
+      }
+      const unsigned c = loff[tid];
+      const int d = (int)(c >> 30), off = (int)(c & 0x3FFFFFFFu);
+#pragma unroll
+      for (int p = 0; p < PB; ++p)
+        if (base + p < NP) atomicAdd(z + pbase[3 * p + d] + off, eta * acc[p]);
+    }
+    return;
+  }
+  // interior spaces: one coarse element per thread
+  if (tid < 36) As[tid] = __ldg(Ainv + tid);
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  r += (int64_t)blockIdx.y * 3 * N3;
+  z += (int64_t)blockIdx.y * 3 * N3;
+  __syncthreads();
+  const int nc = n / 2;
+  const int64_t NT = (int64_t)nc * nc * nc;
+  const int64_t t = (int64_t)(blockIdx.x - npb) * blockDim.x + tid;
+  if (t >= NT) return;
+  const int I = (int)(t % nc), J = (int)((t / nc) % nc), K = (int)(t / ((int64_t)nc * nc));
+  int64_t g[6];
+  int q = 0;
+  for (int d = 0; d < 3; ++d)
+    for (int s2 = 0; s2 < 2; ++s2) {
+      int p[3] = {2 * I + 1, 2 * J + 1, 2 * K + 1};
+      p[d] = (d == 0 ? 2 * I : d == 1 ? 2 * J : 2 * K) + s2;
+      g[q++] = edge_gidx(n, d, p[0], p[1], p[2]);
+    }
+  float rv[6];
+#pragma unroll
+  for (int a = 0; a < 6; ++a) rv[a] = __ldg(r + g[a]);
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    float sum = 0.f;
+#pragma unroll
+    for (int b = 0; b < 6; ++b) sum = fmaf(As[a * 6 + b], rv[b], sum);
+    atomicAdd(z + g[a], eta * sum);
+  }
+}
+
 // Vertex-space solves of large patches in Gram form (subdomain size 4: 1176
 // edges, 312 on the interface): a CTA takes PB patches at a time, gathers
 // their residuals, forms t = W^t r_p (nG values per patch; threads along the
@@ -1304,9 +1422,13 @@ __global__ void __launch_bounds__(256) k_cg_update_rr(int64_t N, const double* _
 // block sums of x.z32 and y.z32 (the preconditioned residual is sc * z32;
 // the caller applies sc to the two sums, one FP64 product per sum instead of
 // one per entry)
+// umax0 (optional): the next stencil's max |p| words, set to 0 here for
+// k_axpby_zf to fill
 __global__ void __launch_bounds__(256) k_dot2_zf(int64_t N, const double* __restrict__ x, const double* __restrict__ y,
-                                                 const float* __restrict__ z32, double* __restrict__ partial) {
+                                                 const float* __restrict__ z32, double* __restrict__ partial,
+                                                 unsigned long long* __restrict__ umax0) {
   pdl_start();
+  if (umax0 && blockIdx.x == 0 && threadIdx.x == 0) umax0[blockIdx.y] = 0ull;
   const int64_t off = (int64_t)blockIdx.y * N;
   double v[2] = {0.0, 0.0};
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
@@ -1317,14 +1439,36 @@ __global__ void __launch_bounds__(256) k_dot2_zf(int64_t N, const double* __rest
   block_sum_store<2>(v, partial + 2 * ((int64_t)blockIdx.y * gridDim.x + blockIdx.x));
 }
 
-// p = sc * z32 + b p with b = ab[2 rhs + 1]
+// p = sc * z32 + b p with b = ab[2 rhs + 1]; umax (optional, 0 on entry):
+// max |p| of each right-hand side as k_absmax forms it, for the fixed-point
+// stencil that applies A to p next
 __global__ void __launch_bounds__(256) k_axpby_zf(int64_t N, const double* __restrict__ sc, const float* __restrict__ z32,
-                                                  const double* __restrict__ ab, double* __restrict__ p) {
+                                                  const double* __restrict__ ab, double* __restrict__ p,
+                                                  unsigned long long* __restrict__ umax) {
   pdl_start();
   const int64_t off = (int64_t)blockIdx.y * N;
   const double s = sc[blockIdx.y], b = ab[2 * blockIdx.y + 1];
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x)
-    p[off + e] = s * f2d_bits(z32[off + e]) + b * p[off + e];
+  unsigned long long m = 0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
+    const double v = s * f2d_bits(z32[off + e]) + b * p[off + e];
+    p[off + e] = v;
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+    m = bits > m ? bits : m;
+  }
+  if (umax) {  // one atomic per block (all blocks meet on one word per right-hand side)
+    __shared__ unsigned long long wm[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
+      m = v > m ? v : m;
+    }
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = wm[w] > m ? wm[w] : m;
+      if (m > 0) atomicMax(umax + blockIdx.y, m);
+    }
+  }
 }
 
 // dst (float) = s * src (double), s = sc[rhs]
@@ -1395,10 +1539,10 @@ static inline dim3 stencil_grid(int n, int sm, int R, int* KZ, int kz_choice) {
 
 template <typename T>
 void launch_stencil(cudaStream_t s, int sm, int n, double cK, double cM, const T* u, const T* g, T* y, int R,
-                    unsigned long long* umax, int kz) {
+                    unsigned long long* umax, int kz, bool umax_ready) {
   const int64_t N = 3LL * n * (n - 1) * (n - 1);
   if (N == 0) return;
-  if constexpr (std::is_same<T, double>::value) {
+  if constexpr (std::is_same<T, double>::value) if (!umax_ready) {
     cudaMemsetAsync(umax, 0, sizeof(unsigned long long) * R, s);
     launch_pdl(k_absmax, dim3(grid_for(N, sm, 4), R), 256, 0, s, N, u, umax);
   }
@@ -1510,6 +1654,31 @@ void launch_patch_dense(cudaStream_t s, int sm, int n, const PatchFamily& fam, c
   }
 }
 
+// levels with at most this many vertex patches take k_smooth_direct
+constexpr int64_t kDirectMaxPatches = 4096;
+constexpr int kPBdirect = 4;
+
+bool smooth_direct_fits(int n) {
+  const int64_t nv = n / 2 - 1;
+  return nv >= 1 && nv * nv * nv <= kDirectMaxPatches;
+}
+
+void launch_smooth_direct(cudaStream_t s, int n, const float* D, const float* Ainv, double eta, const float* r,
+                          float* z, int R) {
+  const PatchFamily fam = vertex_family(n);
+  const int64_t NP = (int64_t)fam.np[0] * fam.np[1] * fam.np[2];
+  const int64_t nc = n / 2;
+  const int npb = (int)((NP + kPBdirect - 1) / kPBdirect);
+  const int nbb = (int)((nc * nc * nc + 127) / 128);
+  launch_pdl(k_smooth_direct<kPBdirect>, dim3(npb + nbb, R), 128, sizeof(float) * 108 * 108, s, n, fam, D, Ainv,
+             (float)eta, npb, r, z);
+}
+
+cudaError_t prepare_smooth_direct() {
+  return cudaFuncSetAttribute(k_smooth_direct<kPBdirect>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(sizeof(float) * 108 * 108));
+}
+
 PatchFamily vertex_family(int n) {
   const int nv = n / 2 - 1;
   return PatchFamily{108, {4, 4, 4}, {nv, nv, nv}, {1, 1, 1}, {2, 2, 2}};
@@ -1600,8 +1769,8 @@ void launch_cg_update_rr_partial(cudaStream_t s, int sm, int64_t N, const double
   launch_pdl(k_cg_update_rr, dim3(reduction_blocks(sm), R), 256, 0, s, N, alpha, p, q, u, r, sto, g32, partial);
 }
 void launch_dot2_zf_partial(cudaStream_t s, int sm, int64_t N, const double* x, const double* y, const float* z32,
-                            double* partial, int R) {
-  launch_pdl(k_dot2_zf, dim3(reduction_blocks(sm), R), 256, 0, s, N, x, y, z32, partial);
+                            double* partial, int R, unsigned long long* umax0) {
+  launch_pdl(k_dot2_zf, dim3(reduction_blocks(sm), R), 256, 0, s, N, x, y, z32, partial, umax0);
 }
 
 static inline dim3 blas_grid(int64_t N, int sm, int R) {
@@ -1634,12 +1803,12 @@ void launch_cg_update_rr(cudaStream_t s, int sm, int64_t N, const double* alpha,
 void launch_dot2_zf(cudaStream_t s, int sm, int64_t N, const double* x, const double* y, const float* z32,
                     double* partial, double* out, int R) {
   const int nb = reduction_blocks(sm);
-  launch_pdl(k_dot2_zf, dim3(nb, R), 256, 0, s, N, x, y, z32, partial);
+  launch_pdl(k_dot2_zf, dim3(nb, R), 256, 0, s, N, x, y, z32, partial, (unsigned long long*)nullptr);
   launch_pdl(k_finish2, R, 256, 0, s, nb, partial, out);
 }
 void launch_axpby_zf(cudaStream_t s, int sm, int64_t N, const double* sc, const float* z32, const double* ab, double* p,
-                     int R) {
-  launch_pdl(k_axpby_zf, blas_grid(N, sm, R), 256, 0, s, N, sc, z32, ab, p);
+                     int R, unsigned long long* umax) {
+  launch_pdl(k_axpby_zf, blas_grid(N, sm, R), 256, 0, s, N, sc, z32, ab, p, umax);
 }
 
 void launch_to_f32(cudaStream_t s, int sm, int64_t N, const double* sc, const double* src, float* dst, int R) {
@@ -1705,7 +1874,7 @@ void launch_grad_cells(cudaStream_t s, int sm, int n, double h, const double* la
 
 #define NDMG_INST(T)                                                                                   \
   template void launch_stencil<T>(cudaStream_t, int, int, double, double, const T*, const T*, T*, int,    \
-                                  unsigned long long*, int);                                          \
+                                  unsigned long long*, int, bool);                                    \
   template cudaError_t prepare_stencil<T>();                                                          \
   template cudaError_t prepare_stencil_field<T>();                                                    \
   template void launch_stencil_field<T>(cudaStream_t, int, int, double, double, const T*, const T*, T*, int, \

@@ -7,11 +7,13 @@ namespace ndmg {
 
 // y = g - (cK K + cM M) u, or (cK K + cM M) u when g is null (cK = alpha h,
 // cM = beta h^3 for A_k).  For double vectors the operator runs in exact
-// fixed point; umax is R words of device scratch for its scale.  kz: planes
-// per CTA along z (0 = the built-in choice; any value gives the same result).
+// fixed point; umax is R words of device scratch for its scale, which the
+// launch forms from u first unless umax_ready (then they hold max |u| bits
+// already).  kz: planes per CTA along z (0 = the built-in choice; any value
+// gives the same result).
 template <typename T>
 void launch_stencil(cudaStream_t s, int sm, int n, double cK, double cM, const T* u, const T* g, T* y, int R,
-                    unsigned long long* umax, int kz = 0);
+                    unsigned long long* umax, int kz = 0, bool umax_ready = false);
 template <typename T>
 cudaError_t prepare_stencil();
 // g_c = P^t r_f; with zc, also z_c = 0
@@ -23,6 +25,13 @@ template <typename T>
 void launch_bubble(cudaStream_t s, int sm, int n, const T* Ainv, double eta, const T* r, T* z, int R);
 template <typename T>
 cudaError_t prepare_vertex_dense();
+// small levels (at most 4096 vertex patches): interior and vertex-patch
+// solves of eq. (Preconditioner P) in one launch, FP32 (D: the 108 x 108
+// operator, Ainv: the 6 x 6 interior inverse), z += eta * M^{-1} r
+bool smooth_direct_fits(int n);
+cudaError_t prepare_smooth_direct();
+void launch_smooth_direct(cudaStream_t s, int n, const float* D, const float* Ainv, double eta, const float* r,
+                          float* z, int R);
 template <typename T>
 void launch_vertex_dense(cudaStream_t s, int sm, int n, const T* D, double eta, const T* r, T* z, int R);
 // A lattice of box-shaped patches (see k_patch_dense in kernels.cu).
@@ -54,6 +63,16 @@ template <typename T>
 constexpr size_t dense_stride(int nl) {
   return sizeof(T) == 8 ? 2 * (size_t)nl * nl : (size_t)nl * nl;
 }
+// FP64 patch solves in the basis of the patch box's mirror symmetries
+// (patch_sym.cu): build_patch_sym turns a dense nloc x nloc operator D of the
+// family's box into the kernel's tables and block-diagonal factor (false:
+// the box has no such structure; dropped: the largest off-block entry, which
+// is rounding noise, relative to the largest entry); launch_patch_sym adds
+// eta * D r_p into z for every patch p
+bool build_patch_sym(const PatchFamily& fam, const double* D, std::vector<uint32_t>* blob, double* dropped);
+cudaError_t prepare_patch_sym();
+void launch_patch_sym(cudaStream_t s, int sm, int n, const PatchFamily& fam, const uint32_t* blob, int blob_words,
+                      double eta, const double* r, double* z, int R);
 // z += eta * D r_p for every patch p of the family; D: one operator in the
 // dense_stride<T> layout (FP64: the double-float kernel)
 template <typename T>
@@ -96,8 +115,9 @@ void launch_dot2_partial(cudaStream_t s, int sm, int64_t N, const T* x, const T*
 void launch_cg_update_rr_partial(cudaStream_t s, int sm, int64_t N, const double* alpha, const double* p,
                                  const double* q, double* u, double* r, const double* sto, float* g32,
                                  double* partial, int R);
+// (umax0: optional words set to 0 for launch_axpby_zf)
 void launch_dot2_zf_partial(cudaStream_t s, int sm, int64_t N, const double* x, const double* y, const float* z32,
-                            double* partial, int R);
+                            double* partial, int R, unsigned long long* umax0 = nullptr);
 template <typename T>
 void launch_dot2(cudaStream_t s, int sm, int64_t N, const T* x, const T* y, const T* x2, const T* y2,
                  double* partial, double* out, int R);
@@ -116,8 +136,10 @@ void launch_cg_update_rr(cudaStream_t s, int sm, int64_t N, const double* alpha,
 // scale of z32)
 void launch_dot2_zf(cudaStream_t s, int sm, int64_t N, const double* x, const double* y, const float* z32,
                     double* partial, double* out, int R);
+// p = sc z32 + b p; umax (optional, zeroed by launch_dot2_zf_partial): max |p|
+// per right-hand side for the next fixed-point stencil on p
 void launch_axpby_zf(cudaStream_t s, int sm, int64_t N, const double* sc, const float* z32, const double* ab, double* p,
-                     int R);
+                     int R, unsigned long long* umax = nullptr);
 void launch_to_f32(cudaStream_t s, int sm, int64_t N, const double* sc, const double* src, float* dst, int R);
 void launch_from_f32(cudaStream_t s, int sm, int64_t N, const double* sc, const float* src, double* dst, int R);
 void launch_add_f32(cudaStream_t s, int sm, int64_t N, const double* sc, const float* src, double* dst, int R);

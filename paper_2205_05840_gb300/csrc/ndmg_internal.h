@@ -127,6 +127,12 @@ struct DevLevel {
   double* Dv64 = nullptr;     // 108*108
   float* Dv32 = nullptr;
   double* De64 = nullptr;     // 3 * 42*42 (edge-based smoother)
+  // the FP64 dense operators in the mirror-symmetry basis (patch_sym.cu):
+  // vertex patches, edge patches per direction, subdomain-4 interiors
+  uint32_t* sym_v = nullptr;
+  uint32_t* sym_e[3] = {nullptr, nullptr, nullptr};
+  uint32_t* sym_s4 = nullptr;
+  int sym_v_words = 0, sym_e_words[3] = {0, 0, 0}, sym_s4_words = 0;
   float* De32 = nullptr;
   void* Wtc = nullptr;        // tensor-core operand images (bf16/fp16), see tc kernel
   void* Wcell = nullptr;      // the same factor in the per-neighbour blocks of the cell-owned kernel (tc_cell.cu)

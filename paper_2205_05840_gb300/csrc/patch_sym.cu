@@ -1,0 +1,486 @@
+// FP64 dense patch solves z += eta * D r_p (eq. (Preconditioner P): the
+// vertex-space operator J_V A_V^{-1} J_V^t; eq. (Preconditioner E): the
+// edge-space ones) in a basis adapted to the patch's mirror symmetries.
+//
+// With a constant coefficient on a uniform grid a patch box is mapped onto
+// itself by the three reflections through its centre, x -> b_x - x and so on
+// (an edge along the reflected axis reverses its orientation, so its degree
+// of freedom changes sign), and its matrix commutes with all three.  So does
+// D.  The reflections generate the group Z2^3; its eight characters chi split
+// the patch space into eigenspaces that D maps into themselves.  Each row of
+// the transform T is the signed sum of the degrees of freedom of one edge
+// orbit under the group for one character compatible with the orbit (entries
+// +-1, rows orthogonal, T T^t = Lambda = the orbit sizes).  Then
+//     D = T^t M T,   M = Lambda^{-1} (T D T^t) Lambda^{-1},
+// and M is block diagonal, one block per character: for the 108-edge vertex
+// patch the blocks have 24, 16, 16, 16, 10, 10, 10 and 6 rows, 1,680 entries
+// against 11,664 for D, so the product costs a seventh of the dense one.
+//
+// The kernel keeps FP64 accuracy on the FP32 pipe: the residuals of a pass of
+// patches are scaled by a power of two and taken to int64 fixed point, T is
+// applied exactly in integers, each transformed entry becomes a pair of
+// floats (48 significant bits), the block products run in double-float
+// arithmetic (an exact product error by fma, error-free two-sums), T^t sums
+// the block outputs the same way, and only the final value and its atomic
+// addition into z are FP64.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <stdexcept>
+#include <vector>
+
+#include "kernels.cuh"
+#include "pdl.cuh"
+
+namespace ndmg {
+
+namespace {
+
+// blob layout (32-bit words): [0] nloc, [1] blocks, [2] M entries;
+// [3 + 3q ..] per block: first row, rows, offset of its entries in M;
+// rows: 3 words each (members 0-3 and 4-7 as bytes, then count | signs << 8 |
+// block << 16); edges: 3 words each (rows 0-3, 4-7, count | signs << 8);
+// then M hi, M lo (floats, column-major per block)
+constexpr int kHdr = 3 + 3 * 8;
+__host__ __device__ constexpr int rows_at() { return kHdr; }
+__host__ __device__ constexpr int edges_at(int nl) { return kHdr + 3 * nl; }
+__host__ __device__ constexpr int m_at(int nl) { return kHdr + 6 * nl; }
+
+struct Edge {
+  int d, i, j, k;
+};
+
+// patch-local edge l of a box of b[0] x b[1] x b[2] cells (interior edges,
+// the order every dense patch kernel uses)
+Edge local_edge(const int b[3], int l) {
+  const int bx = b[0], by = b[1], bz = b[2];
+  const int cx = bx * (by - 1) * (bz - 1), cy = (bx - 1) * by * (bz - 1);
+  Edge e;
+  int q = l;
+  if (q < cx) {
+    e = {0, q % bx, (q / bx) % (by - 1) + 1, q / (bx * (by - 1)) + 1};
+  } else if ((q -= cx) < cy) {
+    e = {1, q % (bx - 1) + 1, (q / (bx - 1)) % by, q / ((bx - 1) * by) + 1};
+  } else {
+    q -= cy;
+    e = {2, q % (bx - 1) + 1, (q / (bx - 1)) % (by - 1) + 1, q / ((bx - 1) * (by - 1))};
+  }
+  return e;
+}
+
+int local_index(const int b[3], const Edge& e) {
+  const int bx = b[0], by = b[1], bz = b[2];
+  const int cx = bx * (by - 1) * (bz - 1), cy = (bx - 1) * by * (bz - 1);
+  if (e.d == 0) return e.i + bx * ((e.j - 1) + (by - 1) * (e.k - 1));
+  if (e.d == 1) return cx + (e.i - 1) + (bx - 1) * (e.j + by * (e.k - 1));
+  return cx + cy + (e.i - 1) + (bx - 1) * ((e.j - 1) + (by - 1) * e.k);
+}
+
+}  // namespace
+
+bool build_patch_sym(const PatchFamily& fam, const double* D, std::vector<uint32_t>* blob, double* dropped) {
+  const int nl = fam.nloc;
+  if (nl > 128) return false;
+  const int* b = fam.b;
+  for (int l = 0; l < nl; ++l)
+    if (local_index(b, local_edge(b, l)) != l) throw std::logic_error("patch-local edge numbering");
+  // the image and sign of edge l under the group element g (bit a: reflect axis a)
+  auto act = [&](int l, int g, int* sign) {
+    Edge e = local_edge(b, l);
+    int s = 1;
+    int c[3] = {e.i, e.j, e.k};
+    for (int a = 0; a < 3; ++a)
+      if ((g >> a) & 1) {
+        if (e.d == a) {
+          c[a] = b[a] - 1 - c[a];
+          s = -s;
+        } else {
+          c[a] = b[a] - c[a];
+        }
+      }
+    *sign = s;
+    return local_index(b, Edge{e.d, c[0], c[1], c[2]});
+  };
+  // rows: (character, orbit) pairs compatible with the orbit's stabiliser
+  struct Row {
+    int chi;
+    std::vector<int> mem, sgn;
+  };
+  std::vector<Row> rows;
+  for (int chi = 0; chi < 8; ++chi) {
+    std::vector<bool> seen(nl, false);
+    for (int l = 0; l < nl; ++l) {
+      if (seen[l]) continue;
+      // coefficient of each orbit member: chi(g) sign(g); compatible iff consistent
+      std::vector<int> coef(nl, 0);
+      bool ok = true;
+      for (int g = 0; g < 8; ++g) {
+        int s;
+        const int m = act(l, g, &s);
+        seen[m] = true;
+        const int c = s * ((__builtin_popcount(g & chi) & 1) ? -1 : 1);
+        if (coef[m] == 0) coef[m] = c;
+        else if (coef[m] != c) ok = false;
+      }
+      if (!ok) continue;
+      Row r{chi, {}, {}};
+      for (int m = 0; m < nl; ++m)
+        if (coef[m] != 0) {
+          r.mem.push_back(m);
+          r.sgn.push_back(coef[m]);
+        }
+      rows.push_back(r);
+    }
+  }
+  if ((int)rows.size() != nl) return false;
+  // block structure (rows are grouped by character by construction)
+  std::vector<int> first, size;
+  for (int r = 0; r < nl; ++r) {
+    if (r == 0 || rows[r].chi != rows[r - 1].chi) {
+      first.push_back(r);
+      size.push_back(0);
+    }
+    ++size.back();
+  }
+  const int nb = (int)first.size();
+  // Bt = T D T^t, M = Lambda^{-1} Bt Lambda^{-1} on the diagonal blocks
+  std::vector<double> TD((size_t)nl * nl, 0.0);
+  for (int r = 0; r < nl; ++r)
+    for (size_t q = 0; q < rows[r].mem.size(); ++q) {
+      const int m = rows[r].mem[q];
+      for (int c = 0; c < nl; ++c) TD[(size_t)r * nl + c] += rows[r].sgn[q] * D[(size_t)m * nl + c];
+    }
+  std::vector<double> Bt((size_t)nl * nl, 0.0);
+  for (int r = 0; r < nl; ++r)
+    for (int s = 0; s < nl; ++s) {
+      double v = 0.0;
+      for (size_t q = 0; q < rows[s].mem.size(); ++q) v += TD[(size_t)r * nl + rows[s].mem[q]] * rows[s].sgn[q];
+      Bt[(size_t)r * nl + s] = v;
+    }
+  double off = 0.0, all = 0.0;
+  std::vector<int> blk(nl);
+  for (int q = 0; q < nb; ++q)
+    for (int r = first[q]; r < first[q] + size[q]; ++r) blk[r] = q;
+  for (int r = 0; r < nl; ++r)
+    for (int s = 0; s < nl; ++s) {
+      const double v = Bt[(size_t)r * nl + s] / ((double)rows[r].mem.size() * rows[s].mem.size());
+      all = std::max(all, std::fabs(v));
+      if (blk[r] != blk[s]) off = std::max(off, std::fabs(v));
+    }
+  *dropped = all > 0 ? off / all : 0.0;
+  int mtot = 0;
+  for (int q = 0; q < nb; ++q) mtot += size[q] * size[q];
+  blob->assign(m_at(nl) + 2 * mtot, 0u);
+  uint32_t* w = blob->data();
+  w[0] = nl;
+  w[1] = nb;
+  w[2] = mtot;
+  int moff = 0;
+  for (int q = 0; q < nb; ++q) {
+    w[3 + 3 * q] = first[q];
+    w[4 + 3 * q] = size[q];
+    w[5 + 3 * q] = moff;
+    moff += size[q] * size[q];
+  }
+  for (int r = 0; r < nl; ++r) {
+    uint8_t mem[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    uint32_t signs = 0;
+    for (size_t q = 0; q < rows[r].mem.size(); ++q) {
+      mem[q] = (uint8_t)rows[r].mem[q];
+      if (rows[r].sgn[q] < 0) signs |= 1u << q;
+    }
+    std::memcpy(&w[rows_at() + 3 * r], mem, 8);
+    w[rows_at() + 3 * r + 2] = (uint32_t)rows[r].mem.size() | signs << 8 | (uint32_t)blk[r] << 16;
+  }
+  for (int e = 0; e < nl; ++e) {
+    uint8_t rr[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    uint32_t signs = 0, cnt = 0;
+    for (int r = 0; r < nl; ++r)
+      for (size_t q = 0; q < rows[r].mem.size(); ++q)
+        if (rows[r].mem[q] == e) {
+          rr[cnt] = (uint8_t)r;
+          if (rows[r].sgn[q] < 0) signs |= 1u << cnt;
+          ++cnt;
+        }
+    if (cnt == 0 || cnt > 8) return false;
+    std::memcpy(&w[edges_at(nl) + 3 * e], rr, 8);
+    w[edges_at(nl) + 3 * e + 2] = cnt | signs << 8;
+  }
+  float* mh = reinterpret_cast<float*>(w + m_at(nl));
+  float* ml = mh + mtot;
+  for (int q = 0; q < nb; ++q)
+    for (int r = 0; r < size[q]; ++r)
+      for (int s = 0; s < size[q]; ++s) {
+        const int R = first[q] + r, S = first[q] + s;
+        const double v = Bt[(size_t)R * nl + S] / ((double)rows[R].mem.size() * rows[S].mem.size());
+        const float hi = (float)v;
+        const int o = (int)w[5 + 3 * q] + s * size[q] + r;  // column-major: a warp reads consecutive rows
+        mh[o] = hi;
+        ml[o] = (float)(v - (double)hi);
+      }
+  return true;
+}
+
+namespace {
+
+// global index of edge (d, i, j, k) (layout of ndmg.h) and its affine part
+__device__ __forceinline__ int64_t sym_edge_gidx(int n, int d, int i, int j, int k) {
+  const int64_t N3 = (int64_t)n * (n - 1) * (n - 1);
+  if (d == 0) return ((int64_t)(k - 1) * (n - 1) + (j - 1)) * n + i;
+  if (d == 1) return N3 + ((int64_t)(k - 1) * n + j) * (n - 1) + (i - 1);
+  return 2 * N3 + ((int64_t)k * (n - 1) + (j - 1)) * (n - 1) + (i - 1);
+}
+__device__ __forceinline__ int sym_edge_lin(int n, int d, int i, int j, int k) {
+  return d == 0 ? i + n * j + n * (n - 1) * k : d == 1 ? i + (n - 1) * j + n * (n - 1) * k
+                                                     : i + (n - 1) * j + (n - 1) * (n - 1) * k;
+}
+
+constexpr int kSymThreads = 256;
+constexpr int kSymPB = 16;  // patches per pass, 8 per thread half
+
+// v 2^s truncated to int64 on the integer pipe (|v| 2^s < 2^62)
+__device__ __forceinline__ long long scaled_fixed(double v, int s) {
+  const long long bits = __double_as_longlong(v);
+  const int e = (int)((bits >> 52) & 0x7FF);
+  const long long m = (bits & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
+  const int sh = e - 1075 + s;
+  long long r = sh >= 0 ? (m << sh) : (sh > -63 ? (m >> -sh) : 0LL);
+  r = e == 0 ? 0LL : r;
+  return bits < 0 ? -r : r;
+}
+
+// an int64 as a pair of floats hi + lo holding its top 48 bits
+__device__ __forceinline__ void fixed_pair(long long t, float& hi, float& lo) {
+  const unsigned sign = t < 0 ? 0x80000000u : 0u;
+  unsigned long long a = t < 0 ? 0ull - (unsigned long long)t : (unsigned long long)t;
+  if (a == 0ull) {
+    hi = lo = 0.f;
+    return;
+  }
+  const int lz = __clzll((long long)a);
+  const int E = 63 - lz;  // exponent of the leading one
+  a <<= lz;
+  hi = __uint_as_float(sign | ((unsigned)(E + 127) << 23) | ((unsigned)(a >> 40) & 0x7FFFFFu));
+  const float l24 = __uint2float_rn((unsigned)(a >> 16) & 0xFFFFFFu);  // exact (< 2^24)
+  lo = (sign ? -l24 : l24) * __uint_as_float((unsigned)(E - 47 + 127) << 23);
+}
+
+__device__ __forceinline__ double pair_to_double(float h, float l) {
+  auto f2d = [](float x) {
+    const unsigned u = __float_as_uint(x);
+    const unsigned long long s = (unsigned long long)(u & 0x80000000u) << 32;
+    const unsigned ef = (u >> 23) & 0xFFu;
+    const unsigned long long bits =
+        ef == 0u ? s
+                 : (ef == 0xFFu ? 0x7FF8000000000000ull
+                                : s | ((unsigned long long)(ef + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29));
+    return __longlong_as_double((long long)bits);
+  };
+  return f2d(h) + f2d(l);
+}
+
+// (sh, sl) += d * (rh + rl) with d = dh + dl: exact product error by fma,
+// error-free two-sum into sh, errors and cross terms into sl
+__device__ __forceinline__ void df_fma(float dh, float dl, float rh, float rl, float& sh, float& sl) {
+  const float prod = __fmul_rn(dh, rh);
+  const float err = fmaf(dh, rh, -prod);
+  const float low = fmaf(dh, rl, fmaf(dl, rh, err));
+  const float t = __fadd_rn(sh, prod);
+  const float bb = __fsub_rn(t, sh);
+  const float e2 = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bb)), __fsub_rn(prod, bb));
+  sh = t;
+  sl = __fadd_rn(sl, __fadd_rn(e2, low));
+}
+
+// (sh, sl) += (xh + xl)
+__device__ __forceinline__ void df_add(float xh, float xl, float& sh, float& sl) {
+  const float t = __fadd_rn(sh, xh);
+  const float bb = __fsub_rn(t, sh);
+  const float e2 = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bb)), __fsub_rn(xh, bb));
+  sh = t;
+  sl = __fadd_rn(sl, __fadd_rn(e2, xl));
+}
+
+__global__ void __launch_bounds__(kSymThreads, 3) k_patch_sym(int n, PatchFamily fam, const uint32_t* __restrict__ blob,
+                                                              int blob_words, double eta, const double* __restrict__ r,
+                                                              double* __restrict__ z) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  constexpr int H = kSymPB / 2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nl = fam.nloc;
+  uint32_t* W = reinterpret_cast<uint32_t*>(smem_raw);                        // the blob
+  long long* I64 = reinterpret_cast<long long*>(smem_raw + ((blob_words * 4 + 15) / 16) * 16);  // nl x PB
+  float* Oh = reinterpret_cast<float*>(I64);                                   // over I64 once T is applied
+  float* Ol = Oh + nl * kSymPB;
+  float* Th = reinterpret_cast<float*>(I64 + nl * kSymPB);                     // nl x PB
+  float* Tl = Th + nl * kSymPB;
+  unsigned* loff = reinterpret_cast<unsigned*>(Tl + nl * kSymPB);
+  long long* pbase = reinterpret_cast<long long*>(loff + ((nl + 1) & ~1));
+  unsigned* amax = reinterpret_cast<unsigned*>(pbase + 3 * kSymPB);
+  const int tid = threadIdx.x;
+  // set-up, independent of the previous kernel: the blob and the local offsets
+  for (int q = tid; q < blob_words; q += blockDim.x) W[q] = __ldg(blob + q);
+  const int bx = fam.b[0], by = fam.b[1], bz = fam.b[2];
+  const int cx = bx * (by - 1) * (bz - 1), cy = (bx - 1) * by * (bz - 1);
+  for (int l = tid; l < nl; l += blockDim.x) {
+    int d, i, j, k, e = l;
+    if (e < cx) {
+      d = 0; i = e % bx; j = (e / bx) % (by - 1) + 1; k = e / (bx * (by - 1)) + 1;
+    } else if ((e -= cx) < cy) {
+      d = 1; i = e % (bx - 1) + 1; j = (e / (bx - 1)) % by; k = e / ((bx - 1) * by) + 1;
+    } else {
+      e -= cy;
+      d = 2; i = e % (bx - 1) + 1; j = (e / (bx - 1)) % (by - 1) + 1; k = e / ((bx - 1) * (by - 1));
+    }
+    loff[l] = (unsigned)sym_edge_lin(n, d, i, j, k) | ((unsigned)d << 30);
+  }
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  const int64_t N3 = (int64_t)n * (n - 1) * (n - 1);
+  r += (int64_t)blockIdx.y * 3 * N3;
+  z += (int64_t)blockIdx.y * 3 * N3;
+  __syncthreads();
+  const int half = tid / 128, row = tid % 128;
+  const bool active = row < nl;
+  const int my_off = active ? (int)(loff[row] & 0x3FFFFFFFu) : 0, my_d = active ? (int)(loff[row] >> 30) : 0;
+  // this thread's row of T, its block of M, and its edge's rows of T^t
+  uint32_t rw0 = 0, rw1 = 0, rw2 = 0, ew0 = 0, ew1 = 0, ew2 = 0;
+  int b0 = 0, bs = 0, mo = 0;
+  if (active) {
+    rw0 = W[rows_at() + 3 * row];
+    rw1 = W[rows_at() + 3 * row + 1];
+    rw2 = W[rows_at() + 3 * row + 2];
+    ew0 = W[edges_at(nl) + 3 * row];
+    ew1 = W[edges_at(nl) + 3 * row + 1];
+    ew2 = W[edges_at(nl) + 3 * row + 2];
+    const int q = (int)(rw2 >> 16);
+    b0 = (int)W[3 + 3 * q];
+    bs = (int)W[4 + 3 * q];
+    mo = (int)W[5 + 3 * q] + (row - b0);
+  }
+  const float* Mh = reinterpret_cast<const float*>(W + m_at(nl));
+  const float* Ml = Mh + W[2];
+  const int64_t NP = (int64_t)fam.np[0] * fam.np[1] * fam.np[2];
+  for (int64_t base = (int64_t)blockIdx.x * kSymPB; base < NP; base += (int64_t)gridDim.x * kSymPB) {
+    if (tid < kSymPB * 3) {
+      const int pp = tid / 3, d = tid % 3;
+      const int64_t P = base + pp < NP ? base + pp : NP - 1;
+      const int pa = (int)(P % fam.np[0]) + fam.p0[0];
+      const int pb = (int)((P / fam.np[0]) % fam.np[1]) + fam.p0[1];
+      const int pc = (int)(P / ((int64_t)fam.np[0] * fam.np[1])) + fam.p0[2];
+      pbase[tid] = sym_edge_gidx(n, d, fam.stride * pa - fam.shift[0], fam.stride * pb - fam.shift[1],
+                                 fam.stride * pc - fam.shift[2]);
+    }
+    if (tid == 0) *amax = 0u;
+    __syncthreads();
+    // gather (thread (half, row): local edge `row` of the half's 8 patches)
+    double rv[H];
+    unsigned m = 0;
+#pragma unroll
+    for (int p = 0; p < H; ++p) {
+      const int pp = half * H + p;
+      rv[p] = active && base + pp < NP ? __ldg(r + pbase[3 * pp + my_d] + my_off) : 0.0;
+      m = max(m, (unsigned)((unsigned long long)__double_as_longlong(rv[p]) >> 32) & 0x7FFFFFFFu);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((tid & 31) == 0) atomicMax(amax, m);
+    __syncthreads();
+    // fixed point: the pass maximum lies in [2^52, 2^53); Inf or NaN make
+    // the whole pass NaN
+    const unsigned mw = *amax;
+    const bool bad = mw >= 0x7FF00000u;
+    const int ex = mw == 0 ? 0 : (int)(mw >> 20) - 1023;
+    if (active) {
+#pragma unroll
+      for (int p = 0; p < H; ++p) I64[row * kSymPB + half * H + p] = scaled_fixed(rv[p], 52 - ex);
+    }
+    __syncthreads();
+    // t = T r (exact), as float pairs
+    if (active) {
+      const int cnt = (int)(rw2 & 0xFFu);
+      const uint32_t sg = (rw2 >> 8) & 0xFFu;
+      long long t[H];
+#pragma unroll
+      for (int p = 0; p < H; ++p) t[p] = 0;
+      for (int q = 0; q < cnt; ++q) {
+        const int mem = (int)(((q < 4 ? rw0 : rw1) >> (8 * (q & 3))) & 0xFFu);
+        const long long* src = I64 + mem * kSymPB + half * H;
+        const bool neg = (sg >> q) & 1u;
+#pragma unroll
+        for (int p = 0; p < H; ++p) t[p] += neg ? -src[p] : src[p];
+      }
+#pragma unroll
+      for (int p = 0; p < H; ++p) fixed_pair(t[p], Th[row * kSymPB + half * H + p], Tl[row * kSymPB + half * H + p]);
+    }
+    __syncthreads();
+    // o = M t on this row's block (double-float), over I64
+    if (active) {
+      float sh[H], sl[H];
+#pragma unroll
+      for (int p = 0; p < H; ++p) sh[p] = sl[p] = 0.f;
+      for (int c = 0; c < bs; ++c) {
+        const float dh = Mh[mo + c * bs], dl = Ml[mo + c * bs];
+        const float4* th4 = reinterpret_cast<const float4*>(Th + (b0 + c) * kSymPB + half * H);
+        const float4* tl4 = reinterpret_cast<const float4*>(Tl + (b0 + c) * kSymPB + half * H);
+        const float4 h0 = th4[0], h1 = th4[1], l0 = tl4[0], l1 = tl4[1];
+        const float rh[H] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+        const float rl[H] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
+#pragma unroll
+        for (int p = 0; p < H; ++p) df_fma(dh, dl, rh[p], rl[p], sh[p], sl[p]);
+      }
+#pragma unroll
+      for (int p = 0; p < H; ++p) {
+        Oh[row * kSymPB + half * H + p] = sh[p];
+        Ol[row * kSymPB + half * H + p] = sl[p];
+      }
+    }
+    __syncthreads();
+    // y = T^t o for this thread's edge, back to FP64 and into z
+    if (active) {
+      const int cnt = (int)(ew2 & 0xFFu);
+      const uint32_t sg = (ew2 >> 8) & 0xFFu;
+      float yh[H], yl[H];
+#pragma unroll
+      for (int p = 0; p < H; ++p) yh[p] = yl[p] = 0.f;
+      for (int q = 0; q < cnt; ++q) {
+        const int rr = (int)(((q < 4 ? ew0 : ew1) >> (8 * (q & 3))) & 0xFFu);
+        const float sgn = ((sg >> q) & 1u) ? -1.f : 1.f;
+#pragma unroll
+        for (int p = 0; p < H; ++p)
+          df_add(sgn * Oh[rr * kSymPB + half * H + p], sgn * Ol[rr * kSymPB + half * H + p], yh[p], yl[p]);
+      }
+      const double back = ldexp(eta, ex - 52);
+#pragma unroll
+      for (int p = 0; p < H; ++p) {
+        const int pp = half * H + p;
+        if (base + pp < NP)
+          atomicAdd(z + pbase[3 * pp + my_d] + my_off, bad ? (double)NAN : back * pair_to_double(yh[p], yl[p]));
+      }
+    }
+    __syncthreads();  // pbase, I64 / Oh / Ol and Th / Tl are rewritten by the next pass
+  }
+}
+
+}  // namespace
+
+size_t patch_sym_smem(int nloc, int blob_words) {
+  return (size_t)((blob_words * 4 + 15) / 16) * 16 + sizeof(long long) * nloc * kSymPB +
+         sizeof(float) * 2 * nloc * kSymPB + sizeof(int) * ((nloc + 1) & ~1) + sizeof(long long) * 3 * kSymPB + 16;
+}
+
+cudaError_t prepare_patch_sym() {
+  return cudaFuncSetAttribute(k_patch_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+}
+
+void launch_patch_sym(cudaStream_t s, int sm, int n, const PatchFamily& fam, const uint32_t* blob, int blob_words,
+                      double eta, const double* r, double* z, int R) {
+  const int64_t NP = (int64_t)fam.np[0] * fam.np[1] * fam.np[2];
+  if (NP <= 0) return;
+  int64_t blocks = (NP + kSymPB - 1) / kSymPB;
+  const int64_t cap = (int64_t)sm * 3;
+  if (blocks > cap) blocks = cap;
+  launch_pdl(k_patch_sym, dim3((int)blocks, R), kSymThreads, patch_sym_smem(fam.nloc, blob_words), s, n, fam, blob,
+             blob_words, eta, r, z);
+}
+
+}  // namespace ndmg

@@ -128,3 +128,30 @@ def test_batched_maxwell_steps_128():
         res = torch.empty_like(ur)
         S64.residual(T(F[r * Nn:(r + 1) * Nn]), ur, res)
         assert np.linalg.norm(N_(res)) / np.linalg.norm(F[r * Nn:(r + 1) * Nn]) <= 1.01e-8
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2])
+@pytest.mark.parametrize("prec", [ndmg.PREC_MIXED_BF16, ndmg.PREC_MIXED_FP16] if torch.cuda.is_available() else [0])
+@pytest.mark.parametrize("n,n0,R", [(16, 4, 3), (40, 5, 2)])
+def test_batched_smoothing_step_per_rhs_matches_oracle(kind, prec, n, n0, R):
+    # one smoothing step z <- z + M_V^{-1}(g - A z) on a batch: every
+    # right-hand side against the FP64 oracle, with the smoother kernel forced
+    # (0 FP32 CUDA cores, 1 tensor-core bricks, 2 tensor-core cell rows); the
+    # tensor-core kernels to 16 units of the operand rounding, the FP32 one to
+    # 1e-5
+    S = ndmg.Solver(n, n_coarsest=n0, nrhs=R, precision=prec)
+    S.select_smoother(kind)
+    A = hcurl.assemble(n, 1.0, 1.0, 1.0)
+    Sm = mg.Smoother(A, n, "vertex")
+    Nn = A.shape[0]
+    rng = np.random.default_rng(n + R)
+    G = rng.standard_normal((R, Nn)).astype(np.float32).astype(np.float64)
+    Z = rng.standard_normal((R, Nn)).astype(np.float32).astype(np.float64)
+    zt = T(Z.ravel(), torch.float32)
+    S.smooth(T(G.ravel(), torch.float32), zt, steps=1, level=-1)
+    got = N_(zt).reshape(R, Nn) - Z
+    u = {ndmg.PREC_MIXED_BF16: 2.0 ** -8, ndmg.PREC_MIXED_FP16: 2.0 ** -11}[prec]
+    tol = 1e-5 if kind == 0 else 16 * u
+    for r in range(R):
+        corr = Sm.apply(G[r] - A @ Z[r])
+        assert rel(got[r], corr) < tol, (r, rel(got[r], corr))

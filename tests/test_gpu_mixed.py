@@ -74,6 +74,31 @@ def test_tc_smoothing_step(kernel, prec, n, n0, alpha):
     assert rel(got, corr) < 16 * U[prec]
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+@pytest.mark.parametrize("n,n0,alpha", [(4, 2, 1.0), (8, 4, 1.0), (12, 6, 0.01), (20, 10, 100.0), (32, 4, 1.0),
+                                        (36, 9, 1.0), (40, 5, 1.0)])
+def test_cuda_core_smoothing_step(prec, n, n0, alpha):
+    # the FP32 CUDA-core smoother (one launch on levels with at most 4096
+    # vertex patches, n <= 32 here; the staged pair above) against the FP64
+    # oracle; FP32 arithmetic: sums of 108 products (relative 1e-5), and the
+    # FP32-rounded patch operator, whose error grows with the patch matrix's
+    # condition number (8 cond 2^-24, as the FP64 tests' bound with FP64 eps)
+    code = ndmg.PREC_FP32 if prec == "fp32" else ndmg.PREC_MIXED_FP16
+    S = ndmg.Solver(n, n_coarsest=n0, alpha=alpha, precision=code)
+    S.select_smoother(0)
+    A = hcurl.assemble(n, 1.0, alpha, 1.0)
+    Sm = mg.Smoother(A, n, "vertex")
+    rng = np.random.default_rng(n + 1)
+    g = rng.standard_normal(A.shape[0]).astype(np.float32).astype(np.float64)
+    z = rng.standard_normal(A.shape[0]).astype(np.float32).astype(np.float64)
+    corr = Sm.apply(g - A @ z)
+    zt = T(z)
+    S.smooth(T(g), zt, steps=1, level=-1)
+    got = N(zt) - z
+    kappa = np.linalg.cond(hcurl.assemble(4, 4.0 / n, alpha, 1.0).toarray())
+    assert rel(got, corr) < max(1e-5, 8 * kappa * 2.0 ** -24)
+
+
 @pytest.mark.parametrize("kernel", ["brick", "cell"])
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
 @pytest.mark.parametrize("n", [64, 128])
