@@ -237,6 +237,15 @@ __device__ __forceinline__ int sym_edge_lin(int n, int d, int i, int j, int k) {
 
 constexpr int kSymThreads = 256;
 constexpr int kSymPB = 16;  // patches per pass, 8 per thread half
+// row strides of the per-pass arrays: an odd number of 16-byte slots, so the
+// 16-byte accesses of 8 consecutive rows (one shared-memory wavefront) fall
+// into distinct slots
+constexpr int kRS64 = kSymPB + 2;  // int64 entries per row of I64
+constexpr int kRS32 = kSymPB + 4;  // floats per row of Th, Tl, Oh, Ol
+
+__host__ __device__ constexpr size_t sym_region_a(int nl) {  // I64, then Oh / Ol over it
+  return (size_t)nl * kRS64 * 8 > (size_t)nl * kRS32 * 8 ? (size_t)nl * kRS64 * 8 : (size_t)nl * kRS32 * 8;
+}
 
 // v 2^s truncated to int64 on the integer pipe (|v| 2^s < 2^62)
 __device__ __forceinline__ long long scaled_fixed(double v, int s) {
@@ -309,12 +318,13 @@ __global__ void __launch_bounds__(kSymThreads, 3) k_patch_sym(int n, PatchFamily
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nl = fam.nloc;
   uint32_t* W = reinterpret_cast<uint32_t*>(smem_raw);                        // the blob
-  long long* I64 = reinterpret_cast<long long*>(smem_raw + ((blob_words * 4 + 15) / 16) * 16);  // nl x PB
-  float* Oh = reinterpret_cast<float*>(I64);                                   // over I64 once T is applied
-  float* Ol = Oh + nl * kSymPB;
-  float* Th = reinterpret_cast<float*>(I64 + nl * kSymPB);                     // nl x PB
-  float* Tl = Th + nl * kSymPB;
-  unsigned* loff = reinterpret_cast<unsigned*>(Tl + nl * kSymPB);
+  unsigned char* regA = smem_raw + ((blob_words * 4 + 15) / 16) * 16;
+  long long* I64 = reinterpret_cast<long long*>(regA);  // nl rows of kRS64
+  float* Oh = reinterpret_cast<float*>(regA);            // over I64 once T is applied: nl rows of kRS32
+  float* Ol = Oh + nl * kRS32;
+  float* Th = reinterpret_cast<float*>(regA + sym_region_a(nl));  // nl rows of kRS32
+  float* Tl = Th + nl * kRS32;
+  unsigned* loff = reinterpret_cast<unsigned*>(Tl + nl * kRS32);
   long long* pbase = reinterpret_cast<long long*>(loff + ((nl + 1) & ~1));
   unsigned* amax = reinterpret_cast<unsigned*>(pbase + 3 * kSymPB);
   const int tid = threadIdx.x;
@@ -392,7 +402,12 @@ __global__ void __launch_bounds__(kSymThreads, 3) k_patch_sym(int n, PatchFamily
     const int ex = mw == 0 ? 0 : (int)(mw >> 20) - 1023;
     if (active) {
 #pragma unroll
-      for (int p = 0; p < H; ++p) I64[row * kSymPB + half * H + p] = scaled_fixed(rv[p], 52 - ex);
+      for (int p = 0; p < H; p += 2) {
+        longlong2 v2;
+        v2.x = scaled_fixed(rv[p], 52 - ex);
+        v2.y = scaled_fixed(rv[p + 1], 52 - ex);
+        *reinterpret_cast<longlong2*>(I64 + row * kRS64 + half * H + p) = v2;
+      }
     }
     __syncthreads();
     // t = T r (exact), as float pairs
@@ -404,13 +419,24 @@ __global__ void __launch_bounds__(kSymThreads, 3) k_patch_sym(int n, PatchFamily
       for (int p = 0; p < H; ++p) t[p] = 0;
       for (int q = 0; q < cnt; ++q) {
         const int mem = (int)(((q < 4 ? rw0 : rw1) >> (8 * (q & 3))) & 0xFFu);
-        const long long* src = I64 + mem * kSymPB + half * H;
+        const longlong2* src = reinterpret_cast<const longlong2*>(I64 + mem * kRS64 + half * H);
         const bool neg = (sg >> q) & 1u;
 #pragma unroll
-        for (int p = 0; p < H; ++p) t[p] += neg ? -src[p] : src[p];
+        for (int p = 0; p < H / 2; ++p) {
+          const longlong2 v2 = src[p];
+          t[2 * p] += neg ? -v2.x : v2.x;
+          t[2 * p + 1] += neg ? -v2.y : v2.y;
+        }
       }
+      float th[H], tl[H];
 #pragma unroll
-      for (int p = 0; p < H; ++p) fixed_pair(t[p], Th[row * kSymPB + half * H + p], Tl[row * kSymPB + half * H + p]);
+      for (int p = 0; p < H; ++p) fixed_pair(t[p], th[p], tl[p]);
+      float4* dh = reinterpret_cast<float4*>(Th + row * kRS32 + half * H);
+      float4* dl = reinterpret_cast<float4*>(Tl + row * kRS32 + half * H);
+      dh[0] = make_float4(th[0], th[1], th[2], th[3]);
+      dh[1] = make_float4(th[4], th[5], th[6], th[7]);
+      dl[0] = make_float4(tl[0], tl[1], tl[2], tl[3]);
+      dl[1] = make_float4(tl[4], tl[5], tl[6], tl[7]);
     }
     __syncthreads();
     // o = M t on this row's block (double-float), over I64
@@ -420,19 +446,20 @@ __global__ void __launch_bounds__(kSymThreads, 3) k_patch_sym(int n, PatchFamily
       for (int p = 0; p < H; ++p) sh[p] = sl[p] = 0.f;
       for (int c = 0; c < bs; ++c) {
         const float dh = Mh[mo + c * bs], dl = Ml[mo + c * bs];
-        const float4* th4 = reinterpret_cast<const float4*>(Th + (b0 + c) * kSymPB + half * H);
-        const float4* tl4 = reinterpret_cast<const float4*>(Tl + (b0 + c) * kSymPB + half * H);
+        const float4* th4 = reinterpret_cast<const float4*>(Th + (b0 + c) * kRS32 + half * H);
+        const float4* tl4 = reinterpret_cast<const float4*>(Tl + (b0 + c) * kRS32 + half * H);
         const float4 h0 = th4[0], h1 = th4[1], l0 = tl4[0], l1 = tl4[1];
         const float rh[H] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
         const float rl[H] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
 #pragma unroll
         for (int p = 0; p < H; ++p) df_fma(dh, dl, rh[p], rl[p], sh[p], sl[p]);
       }
-#pragma unroll
-      for (int p = 0; p < H; ++p) {
-        Oh[row * kSymPB + half * H + p] = sh[p];
-        Ol[row * kSymPB + half * H + p] = sl[p];
-      }
+      float4* oh = reinterpret_cast<float4*>(Oh + row * kRS32 + half * H);
+      float4* ol = reinterpret_cast<float4*>(Ol + row * kRS32 + half * H);
+      oh[0] = make_float4(sh[0], sh[1], sh[2], sh[3]);
+      oh[1] = make_float4(sh[4], sh[5], sh[6], sh[7]);
+      ol[0] = make_float4(sl[0], sl[1], sl[2], sl[3]);
+      ol[1] = make_float4(sl[4], sl[5], sl[6], sl[7]);
     }
     __syncthreads();
     // y = T^t o for this thread's edge, back to FP64 and into z
@@ -445,9 +472,13 @@ __global__ void __launch_bounds__(kSymThreads, 3) k_patch_sym(int n, PatchFamily
       for (int q = 0; q < cnt; ++q) {
         const int rr = (int)(((q < 4 ? ew0 : ew1) >> (8 * (q & 3))) & 0xFFu);
         const float sgn = ((sg >> q) & 1u) ? -1.f : 1.f;
+        const float4* oh = reinterpret_cast<const float4*>(Oh + rr * kRS32 + half * H);
+        const float4* ol = reinterpret_cast<const float4*>(Ol + rr * kRS32 + half * H);
+        const float4 h0 = oh[0], h1 = oh[1], l0 = ol[0], l1 = ol[1];
+        const float xh[H] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+        const float xl[H] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
 #pragma unroll
-        for (int p = 0; p < H; ++p)
-          df_add(sgn * Oh[rr * kSymPB + half * H + p], sgn * Ol[rr * kSymPB + half * H + p], yh[p], yl[p]);
+        for (int p = 0; p < H; ++p) df_add(sgn * xh[p], sgn * xl[p], yh[p], yl[p]);
       }
       const double back = ldexp(eta, ex - 52);
 #pragma unroll
@@ -464,8 +495,8 @@ __global__ void __launch_bounds__(kSymThreads, 3) k_patch_sym(int n, PatchFamily
 }  // namespace
 
 size_t patch_sym_smem(int nloc, int blob_words) {
-  return (size_t)((blob_words * 4 + 15) / 16) * 16 + sizeof(long long) * nloc * kSymPB +
-         sizeof(float) * 2 * nloc * kSymPB + sizeof(int) * ((nloc + 1) & ~1) + sizeof(long long) * 3 * kSymPB + 16;
+  return (size_t)((blob_words * 4 + 15) / 16) * 16 + sym_region_a(nloc) + sizeof(float) * 2 * nloc * kRS32 +
+         sizeof(int) * ((nloc + 1) & ~1) + sizeof(long long) * 3 * kSymPB + 16;
 }
 
 cudaError_t prepare_patch_sym() {
