@@ -148,11 +148,12 @@ cudaError_t upload_sym(uint32_t** dst, int* words, const PatchFamily& fam, const
     cudaFree(*dst);
     *dst = nullptr;
   }
+  *words = (int)blob.size();
+  blob.resize((blob.size() + 3) & ~(size_t)3, 0u);  // padded to 16 bytes for whole-chunk copies
   if (!*dst) {
     cudaError_t e = cudaMalloc((void**)dst, sizeof(uint32_t) * blob.size());
     if (e != cudaSuccess) return e;
   }
-  *words = (int)blob.size();
   return cudaMemcpy(*dst, blob.data(), sizeof(uint32_t) * blob.size(), cudaMemcpyHostToDevice);
 }
 
@@ -405,9 +406,16 @@ void op_smoother<float>(ndmg_t* h, int k, const float* r, float* z) {
                        h->o.eta, r, z, h->status, R);
     return;
   }
+  if (L.sym_v_words > 0) {
+    // interior and patch solves in one launch, the patch operator in the
+    // basis of the patch's mirror symmetries (FP32 block products)
+    Span sp(h, NDMG_K_PATCH, mixed(h) ? 12.0 * L.N * R : num_patches(L.n) * 2.0 * 108 * 108 * R);
+    launch_smooth_sym32(h->stream, L.n, L.sym_v, L.sym_v_words, L.AinvT32, h->o.eta, r, z, R);
+    return;
+  }
   if (smooth_direct_fits(L.n)) {
     // a small level: interior and patch solves in one launch, the operator
-    // read from L2
+    // staged in shared memory
     Span sp(h, NDMG_K_PATCH, mixed(h) ? 12.0 * L.N * R : num_patches(L.n) * 2.0 * 108 * 108 * R);
     launch_smooth_direct(h->stream, L.n, L.Dv32, L.AinvT32, h->o.eta, r, z, R);
     return;
@@ -1370,6 +1378,7 @@ int ndmg_create(const ndmg_opts* o, ndmg_t** out) {
   if (ae == cudaSuccess) ae = prepare_vertex_dense<double>();
   if (ae == cudaSuccess) ae = prepare_patch_sym();
   if (ae == cudaSuccess) ae = prepare_smooth_direct();
+  if (ae == cudaSuccess) ae = prepare_smooth_sym32();
   if (ae == cudaSuccess) ae = prepare_vertex_dense<float>();
   if (ae == cudaSuccess && h->o.subdomain == 4) ae = prepare_patch_gram<double>();
   if (ae == cudaSuccess && h->o.subdomain == 4) ae = prepare_patch_gram<float>();

@@ -73,6 +73,12 @@ bool build_patch_sym(const PatchFamily& fam, const double* D, std::vector<uint32
 cudaError_t prepare_patch_sym();
 void launch_patch_sym(cudaStream_t s, int sm, int n, const PatchFamily& fam, const uint32_t* blob, int blob_words,
                       double eta, const double* r, double* z, int R);
+// the FP32 smoother (vertex patches in the same basis, FP32 block products,
+// and the 6 x 6 interior solves Ainv) in one launch: z += eta * M^{-1} r;
+// blob: the vertex operator's tables (stored padded to 16 bytes)
+cudaError_t prepare_smooth_sym32();
+void launch_smooth_sym32(cudaStream_t s, int n, const uint32_t* blob, int blob_words, const float* Ainv, double eta,
+                         const float* r, float* z, int R);
 // z += eta * D r_p for every patch p of the family; D: one operator in the
 // dense_stride<T> layout (FP64: the double-float kernel)
 template <typename T>

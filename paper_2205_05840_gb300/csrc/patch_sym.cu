@@ -492,7 +492,207 @@ __global__ void __launch_bounds__(kSymThreads, 3) k_patch_sym(int n, PatchFamily
   }
 }
 
+// The FP32 smoother correction of eq. (Preconditioner P) in the same basis,
+// with the interior solves in the same launch: CTAs [0, npb) take PB vertex
+// patches each (gather, T, the FP32 block products, T^t, atomic additions
+// into z), the other CTAs take the 6 x 6 interior solves of 128 coarse
+// elements each.  The tables and the float blocks of M are copied into
+// shared memory before the kernel waits for its predecessor (they are
+// constant); a CTA's critical path is then one gather and a seventh of the
+// dense product's multiply-adds.
+constexpr int kSym32PB = 8;
+constexpr int kRS8 = kSym32PB + 4;  // floats per row: an odd number of 16-byte slots
+
+template <int PB>
+__global__ void __launch_bounds__(128) k_smooth_sym32(int n, PatchFamily fam, const uint32_t* __restrict__ blob,
+                                                      int blob_words, const float* __restrict__ Ainv, float eta,
+                                                      int npb, const float* __restrict__ r, float* __restrict__ z) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  static_assert(PB == 8, "the 16-byte accesses below take 8 patches per row");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ unsigned loff[128];
+  __shared__ long long pbase[3 * PB];
+  __shared__ float As[36];
+  const int tid = threadIdx.x;
+  const int64_t N3 = (int64_t)n * (n - 1) * (n - 1);
+  if ((int)blockIdx.x < npb) {
+    const int nl = fam.nloc;
+    uint32_t* W = reinterpret_cast<uint32_t*>(smem_raw);
+    const int wpad = (blob_words + 3) & ~3;  // the blob is stored padded to 16 bytes
+    float* Rr = reinterpret_cast<float*>(W + wpad);  // nl rows of kRS8
+    float* Tt = Rr + nl * kRS8;
+    float* Oo = Tt + nl * kRS8;
+    {
+      const uint32_t dst = static_cast<uint32_t>(__cvta_generic_to_shared(W));
+      const uint4* src = reinterpret_cast<const uint4*>(blob);
+      for (int q = tid; q < wpad / 4; q += blockDim.x)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + 16u * q), "l"(src + q) : "memory");
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    const int bx = fam.b[0], by = fam.b[1], bz = fam.b[2];
+    const int cx = bx * (by - 1) * (bz - 1), cy = (bx - 1) * by * (bz - 1);
+    if (tid < nl) {
+      int d, i, j, k, e = tid;
+      if (e < cx) {
+        d = 0; i = e % bx; j = (e / bx) % (by - 1) + 1; k = e / (bx * (by - 1)) + 1;
+      } else if ((e -= cx) < cy) {
+        d = 1; i = e % (bx - 1) + 1; j = (e / (bx - 1)) % by; k = e / ((bx - 1) * by) + 1;
+      } else {
+        e -= cy;
+        d = 2; i = e % (bx - 1) + 1; j = (e / (bx - 1)) % (by - 1) + 1; k = e / ((bx - 1) * (by - 1));
+      }
+      loff[tid] = (unsigned)sym_edge_lin(n, d, i, j, k) | ((unsigned)d << 30);
+    }
+    const int64_t NP = (int64_t)fam.np[0] * fam.np[1] * fam.np[2];
+    const int64_t base = (int64_t)blockIdx.x * PB;
+    if (tid < 3 * PB) {
+      const int pp = tid / 3, d = tid % 3;
+      const int64_t P = base + pp < NP ? base + pp : NP - 1;
+      const int pa = (int)(P % fam.np[0]) + fam.p0[0];
+      const int pb = (int)((P / fam.np[0]) % fam.np[1]) + fam.p0[1];
+      const int pc = (int)(P / ((int64_t)fam.np[0] * fam.np[1])) + fam.p0[2];
+      pbase[tid] = sym_edge_gidx(n, d, fam.stride * pa - fam.shift[0], fam.stride * pb - fam.shift[1],
+                                 fam.stride * pc - fam.shift[2]);
+    }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    r += (int64_t)blockIdx.y * 3 * N3;
+    z += (int64_t)blockIdx.y * 3 * N3;
+    __syncthreads();
+    const bool active = tid < nl;
+    const int row = tid;
+    const int my_off = active ? (int)(loff[row] & 0x3FFFFFFFu) : 0, my_d = active ? (int)(loff[row] >> 30) : 0;
+    if (active) {
+      float v[PB];
+#pragma unroll
+      for (int p = 0; p < PB; ++p) v[p] = base + p < NP ? __ldg(r + pbase[3 * p + my_d] + my_off) : 0.f;
+      float4* d4 = reinterpret_cast<float4*>(Rr + row * kRS8);
+      d4[0] = make_float4(v[0], v[1], v[2], v[3]);
+      d4[1] = make_float4(v[4], v[5], v[6], v[7]);
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    uint32_t rw0 = 0, rw1 = 0, rw2 = 0;
+    int b0 = 0, bs = 0, mo = 0;
+    if (active) {
+      rw0 = W[rows_at() + 3 * row];
+      rw1 = W[rows_at() + 3 * row + 1];
+      rw2 = W[rows_at() + 3 * row + 2];
+      const int q = (int)(rw2 >> 16);
+      b0 = (int)W[3 + 3 * q];
+      bs = (int)W[4 + 3 * q];
+      mo = (int)W[5 + 3 * q] + (row - b0);
+      // t = T r
+      const int cnt = (int)(rw2 & 0xFFu);
+      const uint32_t sg = (rw2 >> 8) & 0xFFu;
+      float t[PB];
+#pragma unroll
+      for (int p = 0; p < PB; ++p) t[p] = 0.f;
+      for (int q2 = 0; q2 < cnt; ++q2) {
+        const int mem = (int)(((q2 < 4 ? rw0 : rw1) >> (8 * (q2 & 3))) & 0xFFu);
+        const float sgn = ((sg >> q2) & 1u) ? -1.f : 1.f;
+        const float4* s4 = reinterpret_cast<const float4*>(Rr + mem * kRS8);
+        const float4 a0 = s4[0], a1 = s4[1];
+        t[0] = fmaf(sgn, a0.x, t[0]); t[1] = fmaf(sgn, a0.y, t[1]); t[2] = fmaf(sgn, a0.z, t[2]); t[3] = fmaf(sgn, a0.w, t[3]);
+        t[4] = fmaf(sgn, a1.x, t[4]); t[5] = fmaf(sgn, a1.y, t[5]); t[6] = fmaf(sgn, a1.z, t[6]); t[7] = fmaf(sgn, a1.w, t[7]);
+      }
+      float4* d4 = reinterpret_cast<float4*>(Tt + row * kRS8);
+      d4[0] = make_float4(t[0], t[1], t[2], t[3]);
+      d4[1] = make_float4(t[4], t[5], t[6], t[7]);
+    }
+    __syncthreads();
+    if (active) {
+      // o = M t on this row's block
+      const float* Mh = reinterpret_cast<const float*>(W + m_at(nl));
+      float o[PB];
+#pragma unroll
+      for (int p = 0; p < PB; ++p) o[p] = 0.f;
+      for (int c = 0; c < bs; ++c) {
+        const float m = Mh[mo + c * bs];
+        const float4* s4 = reinterpret_cast<const float4*>(Tt + (b0 + c) * kRS8);
+        const float4 a0 = s4[0], a1 = s4[1];
+        o[0] = fmaf(m, a0.x, o[0]); o[1] = fmaf(m, a0.y, o[1]); o[2] = fmaf(m, a0.z, o[2]); o[3] = fmaf(m, a0.w, o[3]);
+        o[4] = fmaf(m, a1.x, o[4]); o[5] = fmaf(m, a1.y, o[5]); o[6] = fmaf(m, a1.z, o[6]); o[7] = fmaf(m, a1.w, o[7]);
+      }
+      float4* d4 = reinterpret_cast<float4*>(Oo + row * kRS8);
+      d4[0] = make_float4(o[0], o[1], o[2], o[3]);
+      d4[1] = make_float4(o[4], o[5], o[6], o[7]);
+    }
+    __syncthreads();
+    if (active) {
+      // y = T^t o for this thread's edge, into z
+      const uint32_t ew0 = W[edges_at(nl) + 3 * row], ew1 = W[edges_at(nl) + 3 * row + 1];
+      const uint32_t ew2 = W[edges_at(nl) + 3 * row + 2];
+      const int cnt = (int)(ew2 & 0xFFu);
+      const uint32_t sg = (ew2 >> 8) & 0xFFu;
+      float y[PB];
+#pragma unroll
+      for (int p = 0; p < PB; ++p) y[p] = 0.f;
+      for (int q2 = 0; q2 < cnt; ++q2) {
+        const int rr = (int)(((q2 < 4 ? ew0 : ew1) >> (8 * (q2 & 3))) & 0xFFu);
+        const float sgn = ((sg >> q2) & 1u) ? -1.f : 1.f;
+        const float4* s4 = reinterpret_cast<const float4*>(Oo + rr * kRS8);
+        const float4 a0 = s4[0], a1 = s4[1];
+        y[0] = fmaf(sgn, a0.x, y[0]); y[1] = fmaf(sgn, a0.y, y[1]); y[2] = fmaf(sgn, a0.z, y[2]); y[3] = fmaf(sgn, a0.w, y[3]);
+        y[4] = fmaf(sgn, a1.x, y[4]); y[5] = fmaf(sgn, a1.y, y[5]); y[6] = fmaf(sgn, a1.z, y[6]); y[7] = fmaf(sgn, a1.w, y[7]);
+      }
+#pragma unroll
+      for (int p = 0; p < PB; ++p)
+        if (base + p < NP) atomicAdd(z + pbase[3 * p + my_d] + my_off, eta * y[p]);
+    }
+    return;
+  }
+  // interior spaces: one coarse element per thread
+  if (tid < 36) As[tid] = __ldg(Ainv + tid);
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  r += (int64_t)blockIdx.y * 3 * N3;
+  z += (int64_t)blockIdx.y * 3 * N3;
+  __syncthreads();
+  const int nc = n / 2;
+  const int64_t NT = (int64_t)nc * nc * nc;
+  const int64_t t = (int64_t)(blockIdx.x - npb) * blockDim.x + tid;
+  if (t >= NT) return;
+  const int I = (int)(t % nc), J = (int)((t / nc) % nc), K = (int)(t / ((int64_t)nc * nc));
+  int64_t g[6];
+  int q = 0;
+  for (int d = 0; d < 3; ++d)
+    for (int s2 = 0; s2 < 2; ++s2) {
+      int pq[3] = {2 * I + 1, 2 * J + 1, 2 * K + 1};
+      pq[d] = (d == 0 ? 2 * I : d == 1 ? 2 * J : 2 * K) + s2;
+      g[q++] = sym_edge_gidx(n, d, pq[0], pq[1], pq[2]);
+    }
+  float rv[6];
+#pragma unroll
+  for (int a = 0; a < 6; ++a) rv[a] = __ldg(r + g[a]);
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    float sum = 0.f;
+#pragma unroll
+    for (int b = 0; b < 6; ++b) sum = fmaf(As[a * 6 + b], rv[b], sum);
+    atomicAdd(z + g[a], eta * sum);
+  }
+}
+
 }  // namespace
+
+size_t smooth_sym32_smem(int nloc, int blob_words) {
+  return sizeof(uint32_t) * ((blob_words + 3) & ~3) + sizeof(float) * 3 * nloc * kRS8;
+}
+
+cudaError_t prepare_smooth_sym32() {
+  return cudaFuncSetAttribute(k_smooth_sym32<kSym32PB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+}
+
+void launch_smooth_sym32(cudaStream_t s, int n, const uint32_t* blob, int blob_words, const float* Ainv, double eta,
+                         const float* r, float* z, int R) {
+  const PatchFamily fam = vertex_family(n);
+  const int64_t NP = (int64_t)fam.np[0] * fam.np[1] * fam.np[2];
+  if (NP <= 0) return;
+  const int64_t nc = n / 2;
+  const int npb = (int)((NP + kSym32PB - 1) / kSym32PB);
+  const int nbb = (int)((nc * nc * nc + 127) / 128);
+  launch_pdl(k_smooth_sym32<kSym32PB>, dim3(npb + nbb, R), 128, smooth_sym32_smem(fam.nloc, blob_words), s, n, fam,
+             blob, blob_words, Ainv, (float)eta, npb, r, z);
+}
 
 size_t patch_sym_smem(int nloc, int blob_words) {
   return (size_t)((blob_words * 4 + 15) / 16) * 16 + sym_region_a(nloc) + sizeof(float) * 2 * nloc * kRS32 +
