@@ -350,6 +350,15 @@ void op_smoother(ndmg_t* h, int k, const T* r, T* z) {
     op_smoother_s4<T>(h, k, r, z);
     return;
   }
+  if constexpr (std::is_same<T, double>::value)
+    if (L.sym_v_words > 0 && !edge_smoother(h)) {
+      // the vertex patches in the mirror-symmetry basis and the interior
+      // solves of the coarse elements in one launch
+      Span sp(h, NDMG_K_PATCH, num_patches(L.n) * 2.0 * 108 * 108 * R);  // dense-equivalent 108x108 per patch
+      launch_patch_sym(h->stream, h->sm_count, L.n, vertex_family(L.n), L.sym_v, L.sym_v_words, h->o.eta, r, z, R,
+                       L.AinvT64);
+      return;
+    }
   {
     Span sp(h, NDMG_K_BUBBLE, bubble_bytes(L.n, sizeof(T)) * R);
     launch_bubble<T>(h->stream, h->sm_count, L.n, lv_Ainv(L, (T*)nullptr), h->o.eta, r, z, R);
@@ -359,11 +368,6 @@ void op_smoother(ndmg_t* h, int k, const T* r, T* z) {
     return;
   }
   Span sp(h, NDMG_K_PATCH, num_patches(L.n) * 2.0 * 108 * 108 * R);  // dense 108x108 per patch
-  if constexpr (std::is_same<T, double>::value)
-    if (L.sym_v_words > 0) {
-      launch_patch_sym(h->stream, h->sm_count, L.n, vertex_family(L.n), L.sym_v, L.sym_v_words, h->o.eta, r, z, R);
-      return;
-    }
   launch_vertex_dense<T>(h->stream, h->sm_count, L.n, lv_D(L, (T*)nullptr), h->o.eta, r, z, R);
 }
 

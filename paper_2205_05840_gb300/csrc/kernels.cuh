@@ -68,11 +68,13 @@ constexpr size_t dense_stride(int nl) {
 // family's box into the kernel's tables and block-diagonal factor (false:
 // the box has no such structure; dropped: the largest off-block entry, which
 // is rounding noise, relative to the largest entry); launch_patch_sym adds
-// eta * D r_p into z for every patch p
+// eta * D r_p into z for every patch p, and with Ainv (the 6 x 6 interior
+// inverse) also the interior-space solves of every coarse element, in the
+// same launch
 bool build_patch_sym(const PatchFamily& fam, const double* D, std::vector<uint32_t>* blob, double* dropped);
 cudaError_t prepare_patch_sym();
 void launch_patch_sym(cudaStream_t s, int sm, int n, const PatchFamily& fam, const uint32_t* blob, int blob_words,
-                      double eta, const double* r, double* z, int R);
+                      double eta, const double* r, double* z, int R, const double* Ainv = nullptr);
 // the FP32 smoother (vertex patches in the same basis, FP32 block products,
 // and the 6 x 6 interior solves Ainv) in one launch: z += eta * M^{-1} r;
 // blob: the vertex operator's tables (stored padded to 16 bytes)

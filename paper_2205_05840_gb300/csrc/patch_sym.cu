@@ -310,10 +310,52 @@ __device__ __forceinline__ void df_add(float xh, float xl, float& sh, float& sl)
   sl = __fadd_rn(sl, __fadd_rn(e2, xl));
 }
 
+// CTAs [gp, gridDim.x) (gp < gridDim.x only when Ainv is given) take the
+// 6 x 6 interior-space solves of the coarse elements instead, kSymThreads
+// elements per CTA, with atomic additions (vertex patches contain
+// element-interior edges)
+__device__ __forceinline__ void interior_solves64(int n, int blk, const double* __restrict__ Ainv, double eta,
+                                                  const double* __restrict__ r, double* __restrict__ z) {
+  __shared__ double As[36];
+  if (threadIdx.x < 36) As[threadIdx.x] = __ldg(Ainv + threadIdx.x);
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  __syncthreads();
+  const int nc = n / 2;
+  const int64_t NT = (int64_t)nc * nc * nc;
+  const int64_t t = (int64_t)blk * blockDim.x + threadIdx.x;
+  if (t >= NT) return;
+  const int I = (int)(t % nc), J = (int)((t / nc) % nc), K = (int)(t / ((int64_t)nc * nc));
+  int64_t g[6];
+  int q = 0;
+  for (int d = 0; d < 3; ++d)
+    for (int s2 = 0; s2 < 2; ++s2) {
+      int pq[3] = {2 * I + 1, 2 * J + 1, 2 * K + 1};
+      pq[d] = (d == 0 ? 2 * I : d == 1 ? 2 * J : 2 * K) + s2;
+      g[q++] = sym_edge_gidx(n, d, pq[0], pq[1], pq[2]);
+    }
+  double rv[6];
+#pragma unroll
+  for (int a = 0; a < 6; ++a) rv[a] = __ldg(r + g[a]);
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    double sum = 0.0;
+#pragma unroll
+    for (int b = 0; b < 6; ++b) sum = fma(As[a * 6 + b], rv[b], sum);
+    atomicAdd(z + g[a], eta * sum);
+  }
+}
+
 __global__ void __launch_bounds__(kSymThreads, 3) k_patch_sym(int n, PatchFamily fam, const uint32_t* __restrict__ blob,
                                                               int blob_words, double eta, const double* __restrict__ r,
-                                                              double* __restrict__ z) {
+                                                              double* __restrict__ z, const double* __restrict__ Ainv,
+                                                              int gp) {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  if ((int)blockIdx.x >= gp) {
+    const int64_t N3b = (int64_t)n * (n - 1) * (n - 1);
+    interior_solves64(n, (int)blockIdx.x - gp, Ainv, eta, r + (int64_t)blockIdx.y * 3 * N3b,
+                      z + (int64_t)blockIdx.y * 3 * N3b);
+    return;
+  }
   constexpr int H = kSymPB / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nl = fam.nloc;
@@ -370,7 +412,7 @@ __global__ void __launch_bounds__(kSymThreads, 3) k_patch_sym(int n, PatchFamily
   const float* Mh = reinterpret_cast<const float*>(W + m_at(nl));
   const float* Ml = Mh + W[2];
   const int64_t NP = (int64_t)fam.np[0] * fam.np[1] * fam.np[2];
-  for (int64_t base = (int64_t)blockIdx.x * kSymPB; base < NP; base += (int64_t)gridDim.x * kSymPB) {
+  for (int64_t base = (int64_t)blockIdx.x * kSymPB; base < NP; base += (int64_t)gp * kSymPB) {
     if (tid < kSymPB * 3) {
       const int pp = tid / 3, d = tid % 3;
       const int64_t P = base + pp < NP ? base + pp : NP - 1;
@@ -704,14 +746,16 @@ cudaError_t prepare_patch_sym() {
 }
 
 void launch_patch_sym(cudaStream_t s, int sm, int n, const PatchFamily& fam, const uint32_t* blob, int blob_words,
-                      double eta, const double* r, double* z, int R) {
+                      double eta, const double* r, double* z, int R, const double* Ainv) {
   const int64_t NP = (int64_t)fam.np[0] * fam.np[1] * fam.np[2];
-  if (NP <= 0) return;
+  if (NP <= 0 && !Ainv) return;
   int64_t blocks = (NP + kSymPB - 1) / kSymPB;
   const int64_t cap = (int64_t)sm * 3;
   if (blocks > cap) blocks = cap;
-  launch_pdl(k_patch_sym, dim3((int)blocks, R), kSymThreads, patch_sym_smem(fam.nloc, blob_words), s, n, fam, blob,
-             blob_words, eta, r, z);
+  const int64_t nc = n / 2;
+  const int64_t nbb = Ainv ? (nc * nc * nc + kSymThreads - 1) / kSymThreads : 0;
+  launch_pdl(k_patch_sym, dim3((int)(blocks + nbb), R), kSymThreads, patch_sym_smem(fam.nloc, blob_words), s, n, fam,
+             blob, blob_words, eta, r, z, Ainv, (int)blocks);
 }
 
 }  // namespace ndmg
