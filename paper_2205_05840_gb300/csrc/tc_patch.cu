@@ -161,6 +161,8 @@ static_assert(2 * (kSmemF + 1024) <= 228 * 1024, "two CTAs per SM (228 KB, 1 KB 
 
 constexpr int kImgBytes = (kN1 * kK1 + kN2 * kK2) * 2;  // both W images
 constexpr int kImgStride = kImgBytes + 16;               // one image and its scale
+constexpr int kLoBytes = kN2 * kK2 * 2;                   // low-order part of the second W image
+static_assert(kLoBytes <= ((kRegionAll * 4 + 15) / 16) * 16, "the low-order image fits the region buffer");
 static_assert(OFF_B2 - OFF_B1 == kN1 * kK1 * 2 && OFF_R - OFF_B1 == kImgBytes, "W images are one block");
 constexpr int kTimeout = 1;                              // status code
 
@@ -345,6 +347,22 @@ __device__ __forceinline__ void issue_mma2(uint32_t tmem, uint32_t a0, uint32_t 
   mma_commit(bar);
 }
 
+// D' = A' (W_hi + W_lo)^t: the product above, then the same with the
+// low-order image at b0lo into the same accumulator (one elected thread)
+template <bool FP16>
+__device__ __forceinline__ void issue_mma2_split(uint32_t tmem, uint32_t a0, uint32_t b0, uint32_t b0lo, uint32_t bar) {
+  const uint32_t idesc = instr_desc(kM, kN2, FP16);
+#pragma unroll
+  for (int kk = 0; kk < kK2 / 16; ++kk)
+    mma_f16(tmem, smem_desc(a0 + kk * 256, 128, (kK2 / 8) * 128), smem_desc(b0 + kk * 256, 128, (kK2 / 8) * 128),
+            idesc, kk > 0);
+#pragma unroll
+  for (int kk = 0; kk < kK2 / 16; ++kk)
+    mma_f16(tmem, smem_desc(a0 + kk * 256, 128, (kK2 / 8) * 128), smem_desc(b0lo + kk * 256, 128, (kK2 / 8) * 128),
+            idesc, true);
+  mma_commit(bar);
+}
+
 // A' = low-precision copy of D (8 warps: lane quadrant x column half)
 template <bool FP16>
 __device__ __forceinline__ void convert_d(uint32_t tmem, uint8_t* A2, int warp, int lane) {
@@ -487,19 +505,60 @@ __global__ void __launch_bounds__(kThreads, 3)
       else
         gather_chunks<7, FP16>(R_, A, p, a, b, c, live, rscale);
     }
+    // interior spaces of the coarse elements the brick owns: E in [V0-1, V1-1]
+    // per axis, plus element nv on the last brick of an axis (its last vertex
+    // is nv); the 6 interior edges of E are row t = 2d + (segment parity).
+    // Solved now, while r is staged, and added into the accumulator later.
+    constexpr int kBubMax = ((kBX + 1) * (kBY + 1) * (kBZ + 1) * 6 + kThreads - 1) / kThreads;
+    int bub_at[kBubMax];
+    float bub_v[kBubMax];
+    {
+      const int ex1 = VX + kBX - 1 >= nv ? nv : VX + kBX - 2;
+      const int ey1 = VY + kBY - 1 >= nv ? nv : VY + kBY - 2;
+      const int ez1 = VZ + kBZ - 1 >= nv ? nv : VZ + kBZ - 2;
+      const int mx = ex1 - VX + 2, my = ey1 - VY + 2, mz = ez1 - VZ + 2;
+#pragma unroll
+      for (int w = 0; w < kBubMax; ++w) {
+        const int q = tid + w * kThreads;
+        bub_at[w] = -1;
+        bub_v[w] = 0.f;
+        if (q < mx * my * mz * 6) {
+          const int t = q % 6, e = q / 6;
+          const int ei = e % mx, ej = (e / mx) % my, ek = e / (mx * my);  // E - (V0 - 1)
+          float sum = 0.f;
+          int it = 0;
+#pragma unroll
+          for (int u = 0; u < 6; ++u) {
+            const int ix = bubble_elem(u, ei, ej, ek);
+            sum += At[t * 6 + u] * R_[ix];
+            if (u == t) it = ix;
+          }
+          bub_at[w] = it;
+          bub_v[w] = sum;
+        }
+      }
+    }
     fence_async_smem();
-    __syncthreads();
+    __syncthreads();  // A is complete and r is no longer read
 
-    // ---- 3. D = A W -------------------------------------------------------------
+    // ---- 3. D = A W; the low-order image of W^t into the region buffer ------------
     if (tid == 0) {
       fence_after();
       issue_mma1<FP16>(tmem, smem_u32(smem + OFF_A), smem_u32(smem + OFF_B1), bar0);
+    }
+    {
+      const uint4* src = reinterpret_cast<const uint4*>(img + kImgStride);
+      const uint32_t lbase = smem_u32(smem + OFF_R);
+      for (int q = tid; q < kLoBytes / 16; q += kThreads)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(lbase + 16u * q), "l"(src + q) : "memory");
+      asm volatile("cp.async.commit_group;" ::: "memory");
     }
     bool ok = mbar_wait(bar0, parity);
     fence_after();
 
     // ---- 4. A' = low-precision copy of D (8 warps: lane quadrant x column half)
     if (ok) convert_d<FP16>(tmem, smem + OFF_A, warp, lane);
+    asm volatile("cp.async.wait_group 0;" ::: "memory");  // the low-order image landed
     fence_async_smem();
     fence_before();
     __syncthreads();
@@ -511,7 +570,7 @@ __global__ void __launch_bounds__(kThreads, 3)
       red[8] = ok ? 1.f : 0.f;
       if (ok) {
         fence_after();
-        issue_mma2<FP16>(tmem, smem_u32(smem + OFF_A), smem_u32(smem + OFF_B2), bar1);
+        issue_mma2_split<FP16>(tmem, smem_u32(smem + OFF_A), smem_u32(smem + OFF_B2), smem_u32(smem + OFF_R), bar1);
       }
     }
     if (ok) ok = mbar_wait(bar1, parity);
@@ -544,30 +603,10 @@ __global__ void __launch_bounds__(kThreads, 3)
       const bool live = VX + a <= nv && VY + b <= nv && VZ + c <= nv;
       scatter_rows(tmem, ACC, warp, lane, live ? wscale / rscale : 0.f);  // live rows add
     }
-    // interior spaces of the coarse elements the brick owns: E in [V0-1, V1-1]
-    // per axis, plus element nv on the last brick of an axis (its last vertex
-    // is nv); the 6 interior edges of E are row t = 2d + (segment parity)
-    {
-      const int ex1 = VX + kBX - 1 >= nv ? nv : VX + kBX - 2;
-      const int ey1 = VY + kBY - 1 >= nv ? nv : VY + kBY - 2;
-      const int ez1 = VZ + kBZ - 1 >= nv ? nv : VZ + kBZ - 2;
-      const int mx = ex1 - VX + 2, my = ey1 - VY + 2, mz = ez1 - VZ + 2;
-      for (int q = tid; q < mx * my * mz * 6; q += kThreads) {
-        const int t = q % 6, e = q / 6;
-        const int ei = e % mx, ej = (e / mx) % my, ek = e / (mx * my);  // E - (V0 - 1)
-        int idx[6];
+    // the interior-space solves formed before the products
 #pragma unroll
-        for (int u = 0; u < 6; ++u) idx[u] = bubble_elem(u, ei, ej, ek);
-        float sum = 0.f;
-        int it = idx[0];
-#pragma unroll
-        for (int u = 0; u < 6; ++u) {
-          sum += At[t * 6 + u] * R_[idx[u]];
-          if (u == t) it = idx[u];
-        }
-        atomicAdd(ACC + it, sum);
-      }
-    }
+    for (int w = 0; w < kBubMax; ++w)
+      if (bub_at[w] >= 0) atomicAdd(ACC + bub_at[w], bub_v[w]);
     fence_before();
     __syncthreads();
 
@@ -792,11 +831,23 @@ __global__ void __launch_bounds__(kThreads, 2)
 // image of one Gram factor W (108 x 60 row-major) at img (kImgStride bytes):
 // both operand layouts, scaled by a power of two so that max |W| <= 1, then
 // the float 1 / scale^2
-static void tc_image(const double* Wp, bool fp16, uint8_t* img) {
+// The operand images of W: B1 for D = A W (W scaled by sw, max |W sw| in
+// (1/2, 1]) and B2 for D' = A' W^t (scaled by sw2 = 2^12 sw, so that the
+// low-order part below stays clear of the subnormal range); the float after
+// both is 1 / (sw sw2).  lo (optional): B2's low-order part, W sw2 minus its
+// rounding, in the same format and layout.  Rounding W in the second product
+// moves the smoother's output out of the vertex space and costs V-cycles;
+// the first product's rounding only perturbs coefficients inside it, so only
+// the second product gets the low-order part.
+static void tc_image(const double* Wp, bool fp16, uint8_t* img, uint8_t* lo = nullptr) {
   const std::vector<double> W(Wp, Wp + 108 * 60);
   double mx = 0.0;
   for (double v : W) mx = std::fmax(mx, std::fabs(v));
   const double sw = mx > 0 ? std::exp2(-std::ceil(std::log2(mx))) : 1.0;
+  const double sw2 = sw * 4096.0;
+  auto round_to = [&](double v) {
+    return fp16 ? (double)__half2float(__double2half(v)) : (double)__bfloat162float(__double2bfloat16(v));
+  };
   auto put = [&](uint8_t* base, int row, int k, int K, double v) {
     uint16_t bits;
     if (fp16) {
@@ -809,15 +860,17 @@ static void tc_image(const double* Wp, bool fp16, uint8_t* img) {
     std::memcpy(base + core_off(row, k, K), &bits, 2);
   };
   std::memset(img, 0, kImgStride);
+  if (lo) std::memset(lo, 0, kLoBytes);
   uint8_t* b1 = img;                           // B1[n][k] = W[k][n]: N = 64, K = 112
   uint8_t* b2 = img + kN1 * kK1 * 2;           // B2[n][k] = W[n][k]: N = 112, K = 64
   for (int l = 0; l < 108; ++l)
     for (int c = 0; c < 60; ++c) {
-      const double v = W[(size_t)l * 60 + c] * sw;
-      put(b1, c, l, kK1, v);
-      put(b2, l, c, kK2, v);
+      const double w = W[(size_t)l * 60 + c];
+      put(b1, c, l, kK1, w * sw);
+      put(b2, l, c, kK2, w * sw2);
+      if (lo) put(lo, l, c, kK2, w * sw2 - round_to(w * sw2));
     }
-  const float inv = (float)(1.0 / (sw * sw));
+  const float inv = (float)(1.0 / (sw * sw2));
   std::memcpy(img + kImgBytes, &inv, sizeof(float));
 }
 
@@ -831,7 +884,10 @@ double tc_operand_spectral_max(const double* Wp, const std::vector<double>& Ap, 
   float inv = 0.f;
   std::memcpy(&inv, img.data() + kImgBytes, sizeof(float));
   std::vector<double> Wr((size_t)108 * 60);
-  const uint8_t* b2 = img.data() + kN1 * kK1 * 2;  // B2[l][c] = W[l][c] (scaled)
+  // B2[l][c] = W[l][c] sw2 rounded, with sw2 = 4096 sw and inv = 1 / (sw sw2):
+  // the rounding of the first product's operand, the one the kernel keeps
+  const double unscale = std::sqrt((double)inv / 4096.0);  // 1 / sw2
+  const uint8_t* b2 = img.data() + kN1 * kK1 * 2;
   for (int l = 0; l < 108; ++l)
     for (int c = 0; c < 60; ++c) {
       uint16_t bits;
@@ -846,7 +902,7 @@ double tc_operand_spectral_max(const double* Wp, const std::vector<double>& Ap, 
         std::memcpy(&bv, &bits, 2);
         v = (double)__bfloat162float(bv);
       }
-      Wr[(size_t)l * 60 + c] = v * std::sqrt((double)inv);
+      Wr[(size_t)l * 60 + c] = v * unscale;
     }
   std::vector<double> x(108, 1.0), ax(108), t(60), y(108);
   for (int l = 0; l < 108; ++l) x[l] = 1.0 + 0.01 * l;  // not orthogonal to the top eigenvector
@@ -881,8 +937,8 @@ double tc_operand_spectral_max(const double* Wp, const std::vector<double>& Ap, 
 }
 
 cudaError_t upload_tc_operand(void** dst, const std::vector<double>& W, bool fp16) {
-  std::vector<uint8_t> img(kImgStride, 0);
-  tc_image(W.data(), fp16, img.data());
+  std::vector<uint8_t> img(kImgStride + kLoBytes, 0);  // the image, then B2's low-order part
+  tc_image(W.data(), fp16, img.data(), img.data() + kImgStride);
   if (!*dst) {
     cudaError_t e = cudaMalloc(dst, img.size());
     if (e != cudaSuccess) return e;
