@@ -377,8 +377,8 @@ def whole_job_value(world: int, dofs: int, vcycles_per_step: float, steps: int, 
 # dram__bytes_write.sum, one ncu capture at 128^3, profiles/), valid only for
 # the kernel source it was measured on (sha256 prefix of the file)
 PROFILED_TRAFFIC = {
-    "patch": {"bytes": 49.651712e6 + 0.000256e6, "algorithmic": 12.0 * 6193536,
-              "source": "paper_2205_05840_gb300/csrc/tc_patch.cu", "sha256": "b2cd7820d0165401"},
+    "patch": {"bytes": 49.67808e6, "algorithmic": 12.0 * 6193536,
+              "source": "paper_2205_05840_gb300/csrc/tc_patch.cu", "sha256": "be9e3835445de476"},
     "stencil": {"bytes": 49.56288e6 + 1.243648e6, "algorithmic": 12.0 * 6193536,
                 "source": "paper_2205_05840_gb300/csrc/kernels.cu", "sha256": "220b325b85590e47"},
 }

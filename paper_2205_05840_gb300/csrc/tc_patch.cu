@@ -162,6 +162,7 @@ static_assert(2 * (kSmemF + 1024) <= 228 * 1024, "two CTAs per SM (228 KB, 1 KB 
 constexpr int kImgBytes = (kN1 * kK1 + kN2 * kK2) * 2;  // both W images
 constexpr int kImgStride = kImgBytes + 16;               // one image and its scale
 constexpr int kLoBytes = kN2 * kK2 * 2;                   // low-order part of the second W image
+constexpr int kFieldImgStride = kImgStride + kLoBytes;    // one group's image and its low-order part
 static_assert(kLoBytes <= ((kRegionAll * 4 + 15) / 16) * 16, "the low-order image fits the region buffer");
 static_assert(OFF_B2 - OFF_B1 == kN1 * kK1 * 2 && OFF_R - OFF_B1 == kImgBytes, "W images are one block");
 constexpr int kTimeout = 1;                              // status code
@@ -719,6 +720,36 @@ __global__ void __launch_bounds__(kThreads, 2)
       gather_chunks<7, FP16>(R, A, p, a, b, c, live, rscale);
   }
 
+  // interior spaces of the coarse elements the brick owns (see k_tc_smoother),
+  // solved while r is staged; the region buffer then takes each group's
+  // low-order W image
+  {
+    const int ex1 = VX + kBX - 1 >= nv ? nv : VX + kBX - 2;
+    const int ey1 = VY + kBY - 1 >= nv ? nv : VY + kBY - 2;
+    const int ez1 = VZ + kBZ - 1 >= nv ? nv : VZ + kBZ - 2;
+    const int mx = ex1 - VX + 2, my = ey1 - VY + 2, mz = ez1 - VZ + 2;
+    auto item = [&](int t, int ei, int ej, int ek) {
+      const int EI = VX - 1 + ei, EJ = VY - 1 + ej, EK = VZ - 1 + ek;  // coarse element
+      const float* At = Atab + 36 * (size_t)__ldg(bub_gid + ((size_t)EK * nc + EJ) * nc + EI);
+      int idx[6];
+#pragma unroll
+      for (int w = 0; w < 6; ++w) idx[w] = bubble_elem(w, ei, ej, ek);
+      float s = 0.f;
+      int it = idx[0];
+#pragma unroll
+      for (int w = 0; w < 6; ++w) {
+        s += __ldg(At + t * 6 + w) * R[idx[w]];
+        if (w == t) it = idx[w];
+      }
+      atomicAdd(ACC + it, s);
+    };
+    for (int q = tid; q < mx * my * mz * 6; q += kThreads) {
+      const int e = q / 6;
+      item(q % 6, e % mx, (e / mx) % my, e / (mx * my));
+    }
+  }
+  __syncthreads();  // r is no longer read
+
   // ---- one pass per group of patches in the brick ---------------------------
   const int e0 = __ldg(goff + brick), e1 = __ldg(goff + brick + 1);
   const int prow = (warp & 3) * 32 + lane;
@@ -730,7 +761,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   for (int e = e0; e < e1 && ok; ++e) {
     const uint32_t parity = (uint32_t)(e - e0) & 1u;
     last_parity = parity;
-    const uint8_t* img = imgs + (size_t)__ldg(ggrp + e) * kImgStride;
+    const uint8_t* img = imgs + (size_t)__ldg(ggrp + e) * kFieldImgStride;
     const uint4 mk = __ldg(gmask + e);
     const uint32_t word = prow < 32 ? mk.x : prow < 64 ? mk.y : prow < 96 ? mk.z : mk.w;
     const bool mine = live && ((word >> (prow & 31)) & 1u);
@@ -738,6 +769,12 @@ __global__ void __launch_bounds__(kThreads, 2)
     const uint4* src = reinterpret_cast<const uint4*>(img);
     for (int q = tid; q < kImgBytes / 16; q += kThreads)
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(wbase + 16u * q), "l"(src + q) : "memory");
+    {
+      const uint4* lsrc = reinterpret_cast<const uint4*>(img + kImgStride);
+      const uint32_t lbase = smem_u32(smem + OFF_R);
+      for (int q = tid; q < kLoBytes / 16; q += kThreads)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(lbase + 16u * q), "l"(lsrc + q) : "memory");
+    }
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
     const float wscale = __ldg(reinterpret_cast<const float*>(img + kImgBytes));
     fence_async_smem();
@@ -757,7 +794,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       red[8] = okg ? 1.f : 0.f;  // whether the second product of this group was issued
       if (okg) {
         fence_after();
-        issue_mma2<FP16>(tmem, smem_u32(A2), smem_u32(smem + OFF_B2), bar1);
+        issue_mma2_split<FP16>(tmem, smem_u32(A2), smem_u32(smem + OFF_B2), smem_u32(smem + OFF_R), bar1);
       }
     }
     if (okg) okg = mbar_wait(bar1, parity);
@@ -783,32 +820,6 @@ __global__ void __launch_bounds__(kThreads, 2)
     return;
   }
 
-  // interior spaces of the coarse elements the brick owns (see k_tc_smoother)
-  if (ok) {
-    const int ex1 = VX + kBX - 1 >= nv ? nv : VX + kBX - 2;
-    const int ey1 = VY + kBY - 1 >= nv ? nv : VY + kBY - 2;
-    const int ez1 = VZ + kBZ - 1 >= nv ? nv : VZ + kBZ - 2;
-    const int mx = ex1 - VX + 2, my = ey1 - VY + 2, mz = ez1 - VZ + 2;
-    auto item = [&](int t, int ei, int ej, int ek) {
-      const int EI = VX - 1 + ei, EJ = VY - 1 + ej, EK = VZ - 1 + ek;  // coarse element
-      const float* At = Atab + 36 * (size_t)__ldg(bub_gid + ((size_t)EK * nc + EJ) * nc + EI);
-      int idx[6];
-#pragma unroll
-      for (int w = 0; w < 6; ++w) idx[w] = bubble_elem(w, ei, ej, ek);
-      float s = 0.f;
-      int it = idx[0];
-#pragma unroll
-      for (int w = 0; w < 6; ++w) {
-        s += __ldg(At + t * 6 + w) * R[idx[w]];
-        if (w == t) it = idx[w];
-      }
-      atomicAdd(ACC + it, s);
-    };
-    for (int q = tid; q < mx * my * mz * 6; q += kThreads) {
-      const int e = q / 6;
-      item(q % 6, e % mx, (e / mx) % my, e / (mx * my));
-    }
-  }
   fence_before();
   __syncthreads();
 
@@ -958,8 +969,11 @@ cudaError_t prepare_tc_patch() {
 }
 
 std::vector<uint8_t> tc_images(const std::vector<double>& W, int ngroups, bool fp16) {
-  std::vector<uint8_t> out((size_t)ngroups * kImgStride);
-  for (int q = 0; q < ngroups; ++q) tc_image(W.data() + (size_t)q * 108 * 60, fp16, out.data() + (size_t)q * kImgStride);
+  std::vector<uint8_t> out((size_t)ngroups * kFieldImgStride);
+  for (int q = 0; q < ngroups; ++q) {
+    uint8_t* img = out.data() + (size_t)q * kFieldImgStride;
+    tc_image(W.data() + (size_t)q * 108 * 60, fp16, img, img + kImgStride);
+  }
   return out;
 }
 
