@@ -66,8 +66,10 @@ typedef enum ndmg_smoother {
 /* Arithmetic of the V-cycle.  FP64: everything in double.  MIXED_BF16 /
  * MIXED_FP16: the inner V-cycle runs on float vectors (stencil, transfers,
  * interior solves in FP32) with the vertex-patch solves on tensor cores in
- * bf16 / fp16 with FP32 accumulation; residuals of the outer refinement loop,
- * PCG inner products and the coarsest solve stay in double. */
+ * bf16 / fp16 with FP32 accumulation (the product that forms the patch
+ * output, W t, with W's high and low-order bf16 / fp16 parts; t = W^t r with
+ * single-rounded operands); residuals of the outer refinement loop, PCG
+ * inner products and the coarsest solve stay in double. */
 typedef enum ndmg_precision {
   NDMG_PREC_FP64 = 0,
   NDMG_PREC_MIXED_BF16 = 1,
@@ -198,8 +200,9 @@ int ndmg_set_launch_shapes(ndmg_t* h, const int32_t* choices);
 /* Chooses the smoother kernel of a level by hand (what ndmg_autotune decides
  * by timing): kind 0 FP32 CUDA cores, 1 tensor cores per brick of 128 vertex
  * patches, 2 tensor cores on cell-owned rows (both tensor-core kernels compute
- * eq. (Preconditioner P) with the same operand precision; they differ in how
- * the overlapping patch outputs are summed).  level: 1 .. K, or -1 for every
+ * eq. (Preconditioner P); the brick kernel forms the patch outputs with W's
+ * high and low-order parts, the cell-owned kernel with its single rounding,
+ * and they differ in how the overlapping patch outputs are summed).  level: 1 .. K, or -1 for every
  * level.  Kinds 1 and 2 need a MIXED handle with the vertex smoother and
  * subdomain size 2.  level 0 instead selects how float V-cycles run the
  * levels n <= 16 (when the handle has them): kind 1 in one launch of a
