@@ -401,3 +401,22 @@ def test_set_launch_shapes_reproduces_autotuned_handle():
     S64 = ndmg.Solver(16, n_coarsest=4)
     with pytest.raises(ndmg.NdmgError):          # tensor-core smoothers need a MIXED handle
         S64.set_launch_shapes({0: (1, 1, 0), 1: (1, 1, 1), 2: (1, 1, 0)})
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_mixed_solve_takes_the_fp64_vcycle_count(prec):
+    # the tensor-core smoother forms its patch outputs with W's high and
+    # low-order parts: a single rounding of W there costs V-cycles (fp16:
+    # 17 against 15 at 128^3, bf16: 22), the other roundings do not, so the
+    # mixed solve needs (about) the FP64 V-cycle's iterations
+    n = 64
+    f = T(inputs.random_load(n, 0), torch.float64)
+    S64 = ndmg.Solver(n, n_coarsest=4)
+    u = torch.zeros_like(f)
+    _, it64, _ = S64.solve(f, u, tol=1e-8)
+    S = ndmg.Solver(n, n_coarsest=4, precision=prec_code(prec))
+    S.select_smoother(1)
+    u.zero_()
+    _, it, rr = S.solve(f, u, tol=1e-8)
+    assert rr <= 1e-8 and it <= it64 + 1, (it, it64)
