@@ -433,13 +433,71 @@ __global__ void __launch_bounds__(256) k_restrict(int nf, const T* __restrict__ 
   }
 }
 
-// One thread per coarse cell (I, J, K) updates the 24 fine edges of its
-// 2 x 2 x 2 block of fine lattice points, (2I + di, 2J + dj, 2K + dk): along
-// a coarse edge both fine halves take its value; across it the coarse hat is
-// linear (fine node 2P: weight 1 at coarse node P; fine node 2P + 1: weight
-// 1/2 at P and P + 1).  The 12 coarse values it needs (4 per direction, 0 on
-// coarse boundary nodes) are loaded once; the fine x-edge pair (2I, 2I+1) is
-// one 2-element access.
+// Prolongation z_f += P z_c, one thread per fine lattice point (i, j, k)
+// adding into its x-, y- and z-edge (each a plain coalesced read-modify-write
+// of the thread's own entry, so no atomics).  Along a coarse edge both fine
+// halves take its value; across it the coarse hat is linear (fine node 2P:
+// weight 1 at coarse node P; fine node 2P + 1: weight 1/2 at P and P + 1),
+// coarse boundary nodes carrying 0.  Neighbouring threads read the same few
+// coarse values, which the L1 serves.
+template <typename T>
+__global__ void __launch_bounds__(256) k_prolong_add(int nf, const T* __restrict__ zc, T* __restrict__ zf) {
+  pdl_start();
+  const int rhs = blockIdx.z / nf;
+  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z - rhs * nf;
+  if (i >= nf || j >= nf) return;
+  const int nc = nf >> 1, n1 = nf - 1, c1 = nc - 1;
+  const int64_t N3c = (int64_t)nc * c1 * c1, N3f = (int64_t)nf * n1 * n1;
+  const T* cx = zc + rhs * 3 * N3c;
+  const T* cy = cx + N3c;
+  const T* cz = cy + N3c;
+  T* fx = zf + rhs * 3 * N3f;
+  T* fy = fx + N3f;
+  T* fz = fy + N3f;
+  const int I = i >> 1, J = j >> 1, K = k >> 1, di = i & 1, dj = j & 1, dk = k & 1;
+  // x-edge: segment i, nodes (j, k); y-edge: segment j, nodes (i, k); z-edge:
+  // segment k, nodes (i, j).  Offsets within one direction fit 32 bits
+  // (n <= 1024); the coarse neighbours are constant strides from one base.
+  const bool vx = in_node(j, nf) && in_node(k, nf);
+  const bool vy = in_node(i, nf) && in_node(k, nf);
+  const bool vz = in_node(i, nf) && in_node(j, nf);
+  const int ofx = ((k - 1) * n1 + (j - 1)) * nf + i;
+  const int ofy = ((k - 1) * nf + j) * n1 + (i - 1);
+  const int ofz = (k * n1 + (j - 1)) * n1 + (i - 1);
+  // all loads (3 fine, up to 12 coarse) are issued before the first store
+  const T ax = vx ? fx[ofx] : T(0), ay = vy ? fy[ofy] : T(0), az = vz ? fz[ofz] : T(0);
+  // interior coarse nodes P (and P + 1 where the fine node is odd)
+  const bool I0 = in_node(I, nc), J0 = in_node(J, nc), K0 = in_node(K, nc);
+  const bool I1 = di && in_node(I + 1, nc), J1 = dj && in_node(J + 1, nc), K1 = dk && in_node(K + 1, nc);
+  const int ocx = ((K - 1) * c1 + (J - 1)) * nc + I;  // +nc: J + 1; +c1 nc: K + 1
+  const int ocy = ((K - 1) * nc + J) * c1 + (I - 1);  // +1: I + 1; +nc c1: K + 1
+  const int ocz = (K * c1 + (J - 1)) * c1 + (I - 1);  // +1: I + 1; +c1: J + 1
+  auto ld = [](bool ok, const T* p) { return ok ? __ldg(p) : T(0); };
+  const T x00 = ld(vx && J0 && K0, cx + ocx), x10 = ld(vx && J1 && K0, cx + ocx + nc),
+          x01 = ld(vx && J0 && K1, cx + ocx + c1 * nc), x11 = ld(vx && J1 && K1, cx + ocx + nc + c1 * nc);
+  const T y00 = ld(vy && I0 && K0, cy + ocy), y10 = ld(vy && I1 && K0, cy + ocy + 1),
+          y01 = ld(vy && I0 && K1, cy + ocy + nc * c1), y11 = ld(vy && I1 && K1, cy + ocy + 1 + nc * c1);
+  const T z00 = ld(vz && I0 && J0, cz + ocz), z10 = ld(vz && I1 && J0, cz + ocz + 1),
+          z01 = ld(vz && I0 && J1, cz + ocz + c1), z11 = ld(vz && I1 && J1, cz + ocz + 1 + c1);
+  // value at fine across-nodes (2P + d1, 2Q + d2) from the coarse values at
+  // (P + a, Q + b); entries with a > d1 or b > d2 are 0 and unused
+  auto lerp = [](T v00, T v10, T v01, T v11, int d1, int d2) -> T {
+    const T v0 = d1 ? T(0.5) * (v00 + v10) : v00;
+    const T v1 = d1 ? T(0.5) * (v01 + v11) : v01;
+    return d2 ? T(0.5) * (v0 + v1) : v0;
+  };
+  if (vx) fx[ofx] = ax + lerp(x00, x10, x01, x11, dj, dk);
+  if (vy) fy[ofy] = ay + lerp(y00, y10, y01, y11, di, dk);
+  if (vz) fz[ofz] = az + lerp(z00, z10, z01, z11, di, dj);
+}
+
+// The same prolongation, one thread per coarse cell (I, J, K) updating the
+// 24 fine edges of its
+// 2 x 2 x 2 block of fine lattice points (2I + di, 2J + dj, 2K + dk) from 12
+// coarse values loaded once; the fine x-edge pair (2I, 2I+1) is one
+// 2-element access.  Eight times fewer threads than the per-fine-point form,
+// whose index arithmetic it shares among 24 edges: the faster form on the
+// largest grids, the per-fine-point one on the smaller.
 template <typename T>
 struct Vec2;
 template <>
@@ -448,7 +506,7 @@ template <>
 struct Vec2<double> { using type = double2; };
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_prolong_add(int nf, const T* __restrict__ zc, T* __restrict__ zf) {
+__global__ void __launch_bounds__(256) k_prolong_add_cell(int nf, const T* __restrict__ zc, T* __restrict__ zf) {
   pdl_start();
   const int nc = nf / 2;
   const int rhs = blockIdx.z / nc;
@@ -502,6 +560,7 @@ __global__ void __launch_bounds__(256) k_prolong_add(int nf, const T* __restrict
       }
     }
 }
+
 
 // ---------------------------------------------------------------------------
 // Smoother, eq. (Preconditioner P): z += eta (sum_T J_T A_T^{-1} J_T^t r +
@@ -1575,6 +1634,8 @@ void launch_stencil_field(cudaStream_t s, int sm, int n, double cK, double cM, c
 // product would pass the 65,535 limit of grid z go in groups of right-hand
 // sides (contiguous vectors, so a group is a pointer offset)
 constexpr int kMaxGridZ = 65535;
+// fine grids from this size on take the per-coarse-cell prolongation kernel
+constexpr int kProlongCellMinN = 128;
 
 template <typename T>
 void launch_restrict(cudaStream_t s, int, int nf, const T* rf, T* gc, int R, T* zc) {
@@ -1594,10 +1655,19 @@ void launch_prolong_add(cudaStream_t s, int, int nf, const T* zc, T* zf, int R) 
   const int nc = nf / 2;
   if (nc < 1) return;
   const int64_t Nf = 3LL * nf * (nf - 1) * (nf - 1), Nc = 3LL * nc * (nc - 1) * (nc - 1);
-  const int group = kMaxGridZ / nc;
+  if (nf >= kProlongCellMinN) {
+    const int group = kMaxGridZ / nc;
+    for (int r0 = 0; r0 < R; r0 += group) {
+      const int rg = R - r0 < group ? R - r0 : group;
+      launch_pdl(k_prolong_add_cell<T>, dim3((nc + 31) / 32, (nc + 7) / 8, nc * rg), dim3(32, 8), 0, s, nf,
+                 zc + r0 * Nc, zf + r0 * Nf);
+    }
+    return;
+  }
+  const int group = kMaxGridZ / nf;
   for (int r0 = 0; r0 < R; r0 += group) {
     const int rg = R - r0 < group ? R - r0 : group;
-    launch_pdl(k_prolong_add<T>, dim3((nc + 31) / 32, (nc + 7) / 8, nc * rg), dim3(32, 8), 0, s, nf, zc + r0 * Nc,
+    launch_pdl(k_prolong_add<T>, dim3((nf + 31) / 32, (nf + 7) / 8, nf * rg), dim3(32, 8), 0, s, nf, zc + r0 * Nc,
                                                                                           zf + r0 * Nf);
   }
 }
