@@ -262,8 +262,10 @@ int ndmg_vcycle(ndmg_t* h, int32_t dtype, const void* g, void* z);
  * preconditioned by one V-cycle MG(K, ., 0, m) (symmetric: Remark 6).  FP64
  * handles run FP64 PCG.  MIXED / FP32 handles run the same FP64 PCG (FP64
  * vectors, residuals and inner products, flexible beta) with the float
- * V-cycle as preconditioner: r / ||r|| is handed to the V-cycle in float and
- * its result scaled back in double.  f, u: double device vectors, u in/out
+ * V-cycle as preconditioner: 2^-e r with 2^(e-1) <= ||r|| < 2^e is handed
+ * to the V-cycle in float and its result scaled back by 2^e in double (power
+ * of two scales: both are exact exponent shifts; float results below the
+ * smallest normal float flush to zero).  f, u: double device vectors, u in/out
  * (warm start).  *iters: PCG iterations (= V-cycles), *relres: final relative
  * residual in FP64 (either may be NULL).  Returns NOT_CONVERGED after maxit
  * iterations, BREAKDOWN on a non-finite residual or non-positive curvature. */

@@ -1,6 +1,7 @@
 // C ABI of libndmg (include/ndmg.h): handle, level hierarchy, V-cycle driver
 // (Fig. 1), PCG and the FP64 iterative-refinement loop.  All vector work runs
 // in the kernels of kernels.cu / tc_patch.cu on the handle's stream.
+#include <algorithm>
 #include <cstdlib>
 #include <cmath>
 #include <cstdio>
@@ -236,6 +237,37 @@ void op_apply(ndmg_t* h, int k, const T* x, T* y, bool umax_ready = false) {
   DevLevel& L = h->lv[k];
   Span sp(h, NDMG_K_STENCIL, 2.0 * sizeof(T) * L.N * nrhs(h));  // read x; write y
   stencil<T>(h, k, L.cK, L.cM, x, (const T*)nullptr, y, umax_ready);
+}
+
+// q = A p on the finest level for PCG, with the block partial sums of the
+// curvature p.q formed in the same launch (fixed-point stencil) and left in
+// h->pq_red; returns their number per right-hand side, 0 when the launch
+// formed none (coefficient field, or more blocks than the buffer holds)
+int op_apply_curvature(ndmg_t* h, const double* p, double* q, bool umax_ready) {
+  const int K = h->K;
+  DevLevel& L = h->lv[K];
+  Span sp(h, NDMG_K_STENCIL, 2.0 * sizeof(double) * L.N * nrhs(h));  // read p; write q
+  if (h->field) {
+    stencil<double>(h, K, L.cK, L.cM, p, (const double*)nullptr, q, umax_ready);
+    return 0;
+  }
+  return launch_stencil<double>(h->stream, h->sm_count, L.n, L.cK, L.cM, p, (const double*)nullptr, q, nrhs(h),
+                                h->umax, L.kz[1], umax_ready, h->pq_red, h->pq_cap);
+}
+
+// alpha = rz / p.q on the device from the stencil's partial sums (nbq > 0)
+// or from a separate reduction over p and q
+void cg_alpha_device(ndmg_t* h, int nbq, const double* p, const double* q, const CgScalars& C, bool flex) {
+  const int R = nrhs(h);
+  const int64_t N = h->lv[h->K].N;
+  if (nbq > 0) {
+    Span sp(h, NDMG_K_BLAS, 0.0);
+    launch_cg_scalars(h->stream, CG_ALPHA, nbq, h->pq_red, C, flex, h->status, R);
+    return;
+  }
+  Span sp(h, NDMG_K_BLAS, 2.0 * 8 * N * R, 2);
+  launch_dot2_partial<double>(h->stream, h->sm_count, N, p, q, nullptr, nullptr, h->red, R);
+  launch_cg_scalars(h->stream, CG_ALPHA, reduction_blocks(h->sm_count), h->red, C, flex, h->status, R);
 }
 
 // y = g + (a K + b M) x (or (a K + b M) x when g is null): the stencil in
@@ -742,12 +774,8 @@ int pcg64(ndmg_t* h, const double* f, double* u, double tol, int maxit, int* ite
   // field's FP64 stencil runs in plain FP64 and needs none
   const bool fuse_max = !h->field;
   for (int it = 1; it <= maxit; ++it) {
-    op_apply<double>(h, K, p, q, fuse_max && it > 1);
-    {
-      Span sp(h, NDMG_K_BLAS, 2.0 * 8 * N * R, 2);
-      launch_dot2_partial<double>(h->stream, sm, N, p, q, nullptr, nullptr, h->red, R);
-      launch_cg_scalars(h->stream, CG_ALPHA, nb, h->red, C, false, h->status, R);
-    }
+    const int nbq = op_apply_curvature(h, p, q, fuse_max && it > 1);
+    cg_alpha_device(h, nbq, p, q, C, false);
     {
       Span sp(h, NDMG_K_BLAS, 6.0 * 8 * N * R);
       launch_cg_update<double>(h->stream, sm, N, C.alpha, p, q, u, r, R);
@@ -865,8 +893,19 @@ int precondition_mixed(ndmg_t* h, const double* r, double* z, const std::vector<
   const int64_t N = h->lv[K].N;
   const int sm = h->sm_count;
   float *r32 = h->w32[4], *z32 = h->w32[5];
-  std::vector<double> inv(R);
-  for (int i = 0; i < R; ++i) inv[i] = rnorm[i] > 0 ? 1.0 / rnorm[i] : 0.0;
+  // power-of-two scales 2^-e, 2^e with 2^(e-1) <= ||r|| < 2^e (as the
+  // device forms them for the later iterations, k_cg_scalars)
+  std::vector<double> inv(R), fwd(R);
+  for (int i = 0; i < R; ++i) {
+    if (rnorm[i] > 0 && std::isfinite(rnorm[i])) {
+      const int e = std::min(1022, std::max(-1022, std::ilogb(rnorm[i]) + 1));
+      inv[i] = std::ldexp(1.0, -e);
+      fwd[i] = std::ldexp(1.0, e);
+    } else {
+      inv[i] = 0.0;
+      fwd[i] = rnorm[i];
+    }
+  }
   {
     const double* d = push_coef(h, SLOT_TO, inv);
     Span sp(h, NDMG_K_BLAS, 12.0 * N * R);
@@ -874,7 +913,7 @@ int precondition_mixed(ndmg_t* h, const double* r, double* z, const std::vector<
   }
   if (int st = vcycle_f32_graph(h)) return st;
   {
-    const double* d = push_coef(h, SLOT_FROM, rnorm);
+    const double* d = push_coef(h, SLOT_FROM, fwd);
     Span sp(h, NDMG_K_BLAS, 12.0 * N * R);
     launch_from_f32(h->stream, sm, N, d, z32, z, R);
   }
@@ -883,7 +922,9 @@ int precondition_mixed(ndmg_t* h, const double* r, double* z, const std::vector<
 
 // FP64 flexible PCG preconditioned by the float V-cycle (mixed handles):
 // r, p, q, u and every inner product stay in double; the preconditioner sees
-// r / ||r|| in float (keeps fp16 operands in range) and returns z in double.
+// 2^-e r in float with 2^(e-1) <= ||r|| < 2^e (keeps fp16 operands in range;
+// a power of two, so both scalings are exact exponent shifts) and returns z
+// in double.
 // beta = -a (q . z_new) / (r . z)_old (flexible form: the low-precision
 // V-cycle is symmetric only up to rounding).  The scalars live on the device
 // (k_cg_scalars); each iteration reads back only ||r||^2 and the status word.
@@ -920,12 +961,8 @@ int pcg_mixed(ndmg_t* h, const double* f, double* u, double tol, int maxit, int*
   // field's FP64 stencil runs in plain FP64 and needs none
   const bool fuse_max = !h->field;
   for (int it = 1; it <= maxit; ++it) {
-    op_apply<double>(h, K, p, q, fuse_max && it > 1);
-    {
-      Span sp(h, NDMG_K_BLAS, 2.0 * 8 * N * R, 2);
-      launch_dot2_partial<double>(h->stream, sm, N, p, q, nullptr, nullptr, h->red, R);
-      launch_cg_scalars(h->stream, CG_ALPHA, nb, h->red, C, true, h->status, R);
-    }
+    const int nbq = op_apply_curvature(h, p, q, fuse_max && it > 1);
+    cg_alpha_device(h, nbq, p, q, C, true);
     {
       Span sp(h, NDMG_K_BLAS, (6.0 * 8 + 4) * N * R, 2);
       launch_cg_update_rr_partial(h->stream, sm, N, C.alpha, p, q, u, r, C.sto, h->w32[4], h->red, R);
@@ -1094,6 +1131,7 @@ void free_handle(ndmg_t* h) {
   cudaFree(h->Ainv0);
   for (int i = 0; i < 6; ++i) { cudaFree(h->w64[i]); cudaFree(h->w32[i]); }
   cudaFree(h->red);
+  cudaFree(h->pq_red);
   cudaFree(h->umax);
   cudaFree(h->coef);
   cudaFree(h->cg);
@@ -1368,6 +1406,11 @@ int ndmg_create(const ndmg_opts* o, ndmg_t** out) {
     h->w32[i] = dev_alloc<float>(NF, &ae, pz);
   }
   h->red = dev_alloc<double>(2 * (int64_t)reduction_blocks(h->sm_count) * R + 2 * R + 8, &ae, pz);
+  {  // the finest stencil's blocks per right-hand side at its shortest z chunk (one plane), capped
+    const int64_t nF = h->lv[K].n;
+    h->pq_cap = std::min<int64_t>(16384, ((nF + 31) / 32) * ((nF + 7) / 8) * nF);
+    h->pq_red = dev_alloc<double>(2 * h->pq_cap * R, &ae, pz);
+  }
   h->umax = dev_alloc<unsigned long long>(R, &ae, pz);
   h->coef = dev_alloc<double>(4 * 2 * R, &ae, pz);
   h->cg = dev_alloc<double>(8 * R, &ae, pz);

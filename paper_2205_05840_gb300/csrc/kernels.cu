@@ -4,6 +4,7 @@
 // (double for the FP64 path, float for the mixed path's inner V-cycle).
 #include <type_traits>
 
+#include "fpbits.cuh"
 #include "kernels.cuh"
 #include "pdl.cuh"
 
@@ -48,6 +49,7 @@ __device__ __forceinline__ bool in_node(int p, int n) { return (unsigned)(p - 1)
 constexpr int kTX = 32, kTY = 8;
 constexpr int kPX = kTX + 2, kPY = kTY + 2, kP = kPX * kPY;  // one staged plane
 constexpr int kTP = kTX * kTY;                               // outputs per plane
+static_assert(kTX == 32, "one warp per row of a stencil block");
 
 // asynchronous copy of one element global -> shared; zero fill when !valid
 template <typename T>
@@ -91,34 +93,13 @@ __device__ __forceinline__ PlanePos plane_pos(int n, int i, int j) {
 // whose FP64 rate is 1/64 of its FP32 rate.  The scale comes from max |u| of
 // each right-hand side (k_absmax); the truncation error is below
 // 2^-54 max |u| per entry.
-__device__ __forceinline__ long long to_fixed(double v, int s) {
-  const long long b = __double_as_longlong(v);
-  const int e = (int)((b >> 52) & 0x7FF);
-  const long long m = (b & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
-  const int sh = e - 1075 + s;  // v 2^s = m 2^sh, sh <= 2 by the choice of s
-  long long r = sh >= 0 ? (m << sh) : (sh > -63 ? (m >> -sh) : 0LL);
-  r = e == 0 ? 0LL : r;         // zero and subnormals
-  return b < 0 ? -r : r;
-}
+// (to_fixed and fixed_to_double: fpbits.cuh)
 
-// int64 -> double rounded to nearest (ties to even) on the integer pipe:
-// normalise |x| so that its leading one is bit 63, keep 53 bits, round on the
-// 11 bits below, assemble sign / exponent / fraction
-__device__ __forceinline__ double fixed_to_double(long long x) {
-  if (x == 0) return 0.0;
-  const unsigned long long sgn = (unsigned long long)x & 0x8000000000000000ull;
-  unsigned long long a = x < 0 ? 0ull - (unsigned long long)x : (unsigned long long)x;
-  const int lz = __clzll((long long)a);
-  a <<= lz;                                     // leading one at bit 63
-  unsigned long long m = a >> 11;               // 53 significant bits
-  const unsigned long long rest = a & 0x7FFull;  // the 11 bits rounded away
-  m += (rest > 0x400ull || (rest == 0x400ull && (m & 1ull))) ? 1ull : 0ull;
-  unsigned long long e = (unsigned long long)(1086 - lz);  // 1023 + 63 - lz
-  if (m >> 53) {                                // rounding carried into bit 53
-    m >>= 1;
-    ++e;
-  }
-  return __longlong_as_double((long long)(sgn | (e << 52) | (m & 0xFFFFFFFFFFFFFull)));
+// sum over the 32 lanes of a warp (the same in every lane)
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
 }
 
 // max |x_r| of every right-hand side, as the bit pattern of |x| (monotonic as
@@ -148,11 +129,16 @@ __global__ void __launch_bounds__(256) k_absmax(int64_t N, const double* __restr
 // mass along the normal then weighs each of the two cells beside a face by its
 // own coefficient, alpha_lo (c_lo + 2 c) + alpha_hi (2 c + c_hi) over 6, which
 // is alpha (c_lo + 4 c + c_hi) / 6 for a constant one.
+// pq (fixed-point FP64 apply only, optional): the CTA's sum of u_e y_e over
+// its outputs, the block partial sums of u.(A u) for the PCG's curvature
+// p.q, at pq[2 (rhs nb + b)] (second slot 0; b the CTA's index within its
+// right-hand side, nb = gridDim.x gridDim.y z chunks), the layout of k_dot2
 template <typename T, typename S, bool FLD = false>
 __global__ void __launch_bounds__(kTX * kTY) k_stencil_stream(int n, int KZ, T cK, T cM, const T* __restrict__ u,
                                                               const T* __restrict__ g, T* __restrict__ y,
                                                               const unsigned long long* __restrict__ umax,
-                                                              const T* __restrict__ acell = nullptr) {
+                                                              const T* __restrict__ acell = nullptr,
+                                                              double* __restrict__ pq = nullptr) {
   pdl_start();
   static_assert(sizeof(S) == sizeof(T), "staged planes hold T and are read as S");
   constexpr bool FX = !std::is_same<S, T>::value;
@@ -285,6 +271,7 @@ __global__ void __launch_bounds__(kTX * kTY) k_stencil_stream(int n, int KZ, T c
   // rows of x- and y-edges, for planes k-1 (0) and k (1); Xf, Yf of plane k-1
   S cz0[3] = {S(0), S(0), S(0)}, cz1[3] = {S(0), S(0), S(0)};
   S rx0 = S(0), rx1 = S(0), ry0 = S(0), ry1 = S(0), yf_prev = S(0), xf_prev = S(0);
+  double pqv = 0.0;  // pq: this thread's sum of u_e y_e
   // the circulation positions of this thread (fixed): neighbours staged?
   const bool ha_a = qa % kPX + 1 < kPX, hb_a = qa / kPX + 1 < kPY;
   const bool ha_b = qb % kPX + 1 < kPX, hb_b = qb / kPX + 1 < kPY;
@@ -344,14 +331,21 @@ __global__ void __launch_bounds__(kTX * kTY) k_stencil_stream(int n, int KZ, T c
         const S zf = Zf(q, cz0[0], cz1[0], cz2[0]);          // Zf(a, b, k)
         const S zf_b = Zf(q - kPX, cz0[1], cz1[1], cz2[1]);  // Zf(a, b-1, k)
         const S zf_a = Zf(q - 1, cz0[2], cz1[2], cz2[2]);    // Zf(a-1, b, k)
-        if (pg.vx && kn) y[px(k) + pg.ox] = combine((yf_prev - yf) + (zf - zf_b), f3(rx0, rx1, rx2), G + tid);
-        if (pg.vy && kn) y[py(k) + pg.oy] = combine((zf_a - zf) + (xf - xf_prev), f3(ry0, ry1, ry2), G + kTP + tid);
+        // store one output; with pq also add u_e y_e (u_e read back in
+        // FP64: the staged copy is in fixed point)
+        auto put = [&](uint32_t o, T v) {
+          y[o] = v;
+          if constexpr (FX)
+            if (pq) pqv = fma((double)u[o], (double)v, pqv);
+        };
+        if (pg.vx && kn) put(px(k) + pg.ox, combine((yf_prev - yf) + (zf - zf_b), f3(rx0, rx1, rx2), G + tid));
+        if (pg.vy && kn) put(py(k) + pg.oy, combine((zf_a - zf) + (xf - xf_prev), f3(ry0, ry1, ry2), G + kTP + tid));
         if (pg.vz && ks) {
           const S* Uz = Uc + 2 * kP;
           const S kv = (Xf(q - kPX) - xf) + (yf - Yf(q - 1));
           const S mz = f3(f3(Uz[q - kPX - 1], Uz[q - 1], Uz[q + kPX - 1]), f3(Uz[q - kPX], Uz[q], Uz[q + kPX]),
                           f3(Uz[q - kPX + 1], Uz[q + 1], Uz[q + kPX + 1]));
-          y[pz(k) + pg.oz] = combine(kv, mz, G + 2 * kTP + tid);
+          put(pz(k) + pg.oz, combine(kv, mz, G + 2 * kTP + tid));
         }
       }
       yf_prev = yf;
@@ -366,6 +360,23 @@ __global__ void __launch_bounds__(kTX * kTY) k_stencil_stream(int n, int KZ, T c
     ry0 = ry1; ry1 = ry2;
   }
   asm volatile("cp.async.wait_group 0;" ::: "memory");
+  if constexpr (FX) {
+    if (pq) {  // one warp per row of the block (kTX = 32)
+      __shared__ double pq_rows[kTY];
+      const double w = warp_sum(pqv);
+      if (threadIdx.x == 0) pq_rows[threadIdx.y] = w;
+      __syncthreads();
+      if (tid == 0) {
+        double sum = 0.0;
+#pragma unroll
+        for (int r = 0; r < kTY; ++r) sum += pq_rows[r];
+        const int64_t nb = (int64_t)gridDim.x * gridDim.y * nzc;
+        const int64_t b = ((int64_t)(blockIdx.z - rhs * nzc) * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        pq[2 * (rhs * nb + b)] = sum;
+        pq[2 * (rhs * nb + b) + 1] = 0.0;
+      }
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1247,12 +1258,6 @@ __global__ void __launch_bounds__(256) k_grad_cells(int n, double h, const doubl
 // inverse (symmetric, so row i is column i): one warp per row, lanes along
 // the row (coalesced), g staged in shared memory; 8 rows per CTA.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
 template <typename T>
 __global__ void __launch_bounds__(256) k_coarse(int N0, const double* __restrict__ Ainv, const T* __restrict__ g,
                                                 T* __restrict__ z) {
@@ -1362,7 +1367,8 @@ __global__ void __launch_bounds__(256) k_grad_alpha_sum(int n, double h, const d
 // three inner products.
 //   CG_ALPHA: p.q -> alpha = rz / p.q (0 for a converged right-hand side;
 //             a non-positive or non-finite curvature sets kStatusBreakdown);
-//             also sto = 1 / ||r||, sfrom = ||r|| from the last rr
+//             also the scales sto = 2^-e, sfrom = 2^e of the last rr
+//             (2^(e-1) <= ||r|| < 2^e)
 //   CG_RR:    rr = r.r
 //   CG_BETA:  r.z -> beta = rz_new / rz (textbook CG), rz = rz_new
 //   CG_BETA_FLEX: r.z32, q.z32 with z = sfrom z32 -> beta = -alpha q.z / rz
@@ -1391,9 +1397,19 @@ __global__ void k_cg_scalars(int mode, int nb, const double* __restrict__ partia
       else atomicOr(status, kStatusBreakdown);
     }
     S.alpha[i] = a;
+    // the float V-cycle's input scale: sto = 2^-e, sfrom = 2^e with
+    // 2^(e-1) <= ||r|| < 2^e, so that ||sto r|| lies in [1/2, 1) and both
+    // scalings are exact exponent shifts (k_cg_update_rr, k_axpby_zf)
     const double rn = sqrt(S.rr[i]);
-    S.sto[i] = rn > 0.0 ? 1.0 / rn : 0.0;
-    S.sfrom[i] = rn;
+    if (rn > 0.0 && isfinite(rn)) {
+      int e = ilogb(rn) + 1;
+      e = e < -1022 ? -1022 : (e > 1022 ? 1022 : e);  // both scales stay normal doubles
+      S.sto[i] = ldexp(1.0, -e);
+      S.sfrom[i] = ldexp(1.0, e);
+    } else {
+      S.sto[i] = 0.0;
+      S.sfrom[i] = rn;
+    }
   } else if (mode == CG_RR) {
     S.rr[i] = s0;
   } else if (mode == CG_BETA || mode == CG_BETA_FLEX) {
@@ -1442,23 +1458,12 @@ __global__ void __launch_bounds__(256) k_cg_update(int64_t N, const double* __re
   }
 }
 
-// float -> double on the integer pipe: exact for normal floats, subnormals
-// flush to signed zero.  The FP64 vector kernels of the mixed PCG are bound
-// by the FP64 pipe (about 2 FMA per clock per SM on this part), which
-// conversions share.
-__device__ __forceinline__ double f2d_bits(float f) {
-  const uint32_t b = __float_as_uint(f);
-  const uint32_t e = (b >> 23) & 0xFFu;
-  const unsigned long long sgn = (unsigned long long)(b >> 31) << 63;
-  const unsigned long long ed = e == 0xFFu ? 0x7FFull : (unsigned long long)(e + 896u);  // 1023 - 127
-  const unsigned long long bits =
-      e == 0u ? sgn : (sgn | (ed << 52) | ((unsigned long long)(b & 0x7FFFFFu) << 29));
-  return __longlong_as_double((long long)bits);
-}
-
 // Fused steps of the mixed flexible PCG (FP64 vectors, float preconditioner):
 // u += a p ; r -= a q ; g32 = sto * r (the float right-hand side of the next
-// V-cycle) and block sums of r.r (partials in the layout of k_dot2)
+// V-cycle) and block sums of r.r (partials in the layout of k_dot2).  sto is
+// a power of two (k_cg_scalars), so g32 is the rounded r with its exponent
+// shifted, formed on the integer pipe (d2f_pow2): three FP64 operations per
+// entry instead of five
 __global__ void __launch_bounds__(256) k_cg_update_rr(int64_t N, const double* __restrict__ alpha,
                                                       const double* __restrict__ p, const double* __restrict__ q,
                                                       double* __restrict__ u, double* __restrict__ r,
@@ -1466,13 +1471,14 @@ __global__ void __launch_bounds__(256) k_cg_update_rr(int64_t N, const double* _
                                                       double* __restrict__ partial) {
   pdl_start();
   const int64_t off = (int64_t)blockIdx.y * N;
-  const double a = alpha[blockIdx.y], s = sto[blockIdx.y];
+  const double a = alpha[blockIdx.y];
+  const int ks = pow2_exponent(sto[blockIdx.y]);
   double v[2] = {0.0, 0.0};
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
     u[off + e] += a * p[off + e];
     const double rn = r[off + e] - a * q[off + e];
     r[off + e] = rn;
-    g32[off + e] = (float)(s * rn);
+    g32[off + e] = d2f_pow2(rn, ks);
     v[0] += rn * rn;
   }
   block_sum_store<2>(v, partial + 2 * ((int64_t)blockIdx.y * gridDim.x + blockIdx.x));
@@ -1498,7 +1504,9 @@ __global__ void __launch_bounds__(256) k_dot2_zf(int64_t N, const double* __rest
   block_sum_store<2>(v, partial + 2 * ((int64_t)blockIdx.y * gridDim.x + blockIdx.x));
 }
 
-// p = sc * z32 + b p with b = ab[2 rhs + 1]; umax (optional, 0 on entry):
+// p = sc * z32 + b p with b = ab[2 rhs + 1]; sc is a power of two
+// (k_cg_scalars), so sc * z32 is exact and formed on the integer pipe
+// (f2d_pow2), one FP64 operation per entry; umax (optional, 0 on entry):
 // max |p| of each right-hand side as k_absmax forms it, for the fixed-point
 // stencil that applies A to p next
 __global__ void __launch_bounds__(256) k_axpby_zf(int64_t N, const double* __restrict__ sc, const float* __restrict__ z32,
@@ -1506,10 +1514,11 @@ __global__ void __launch_bounds__(256) k_axpby_zf(int64_t N, const double* __res
                                                   unsigned long long* __restrict__ umax) {
   pdl_start();
   const int64_t off = (int64_t)blockIdx.y * N;
-  const double s = sc[blockIdx.y], b = ab[2 * blockIdx.y + 1];
+  const int ks = pow2_exponent(sc[blockIdx.y]);
+  const double b = ab[2 * blockIdx.y + 1];
   unsigned long long m = 0;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
-    const double v = s * f2d_bits(z32[off + e]) + b * p[off + e];
+    const double v = fma(b, p[off + e], f2d_pow2(z32[off + e], ks));
     p[off + e] = v;
     const unsigned long long bits = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
     m = bits > m ? bits : m;
@@ -1597,18 +1606,23 @@ static inline dim3 stencil_grid(int n, int sm, int R, int* KZ, int kz_choice) {
 }
 
 template <typename T>
-void launch_stencil(cudaStream_t s, int sm, int n, double cK, double cM, const T* u, const T* g, T* y, int R,
-                    unsigned long long* umax, int kz, bool umax_ready) {
+int launch_stencil(cudaStream_t s, int sm, int n, double cK, double cM, const T* u, const T* g, T* y, int R,
+                   unsigned long long* umax, int kz, bool umax_ready, double* pq, int64_t pq_cap) {
   const int64_t N = 3LL * n * (n - 1) * (n - 1);
-  if (N == 0) return;
+  if (N == 0) return 0;
   if constexpr (std::is_same<T, double>::value) if (!umax_ready) {
     cudaMemsetAsync(umax, 0, sizeof(unsigned long long) * R, s);
     launch_pdl(k_absmax, dim3(grid_for(N, sm, 4), R), 256, 0, s, N, u, umax);
   }
   int KZ = 0;
   const dim3 grid = stencil_grid(n, sm, R, &KZ, kz);
+  // the fused curvature sums: the fixed-point apply only, and only when the
+  // blocks of one right-hand side fit the caller's buffer
+  const int64_t nb = (int64_t)grid.x * grid.y * (grid.z / R);
+  const bool fuse = std::is_same<T, double>::value && g == nullptr && pq != nullptr && nb <= pq_cap;
   launch_pdl(k_stencil_stream<T, StencilArith<T>>, grid, dim3(kTX, kTY), stencil_smem<T>(), s, n, KZ, (T)cK, (T)cM, u, g,
-             y, (const unsigned long long*)umax, (const T*)nullptr);
+             y, (const unsigned long long*)umax, (const T*)nullptr, fuse ? pq : (double*)nullptr);
+  return fuse ? (int)nb : 0;
 }
 
 // coefficient field: three more staged planes (the cell coefficients)
@@ -1627,7 +1641,8 @@ void launch_stencil_field(cudaStream_t s, int sm, int n, double cK, double cM, c
   if (n < 2) return;
   int KZ = 0;
   const dim3 grid = stencil_grid(n, sm, R, &KZ, kz);
-  launch_pdl(k_stencil_stream<T, T, true>, grid, dim3(kTX, kTY), stencil_field_smem<T>(), s, n, KZ, (T)cK, (T)cM, u, g, y, nullptr, acell);
+  launch_pdl(k_stencil_stream<T, T, true>, grid, dim3(kTX, kTY), stencil_field_smem<T>(), s, n, KZ, (T)cK, (T)cM, u, g, y, nullptr, acell,
+             (double*)nullptr);
 }
 
 // grid z of the transfers = coarse planes x right-hand sides; batches whose
@@ -1943,8 +1958,8 @@ void launch_grad_cells(cudaStream_t s, int sm, int n, double h, const double* la
 }
 
 #define NDMG_INST(T)                                                                                   \
-  template void launch_stencil<T>(cudaStream_t, int, int, double, double, const T*, const T*, T*, int,    \
-                                  unsigned long long*, int, bool);                                    \
+  template int launch_stencil<T>(cudaStream_t, int, int, double, double, const T*, const T*, T*, int,     \
+                                 unsigned long long*, int, bool, double*, int64_t);                   \
   template cudaError_t prepare_stencil<T>();                                                          \
   template cudaError_t prepare_stencil_field<T>();                                                    \
   template void launch_stencil_field<T>(cudaStream_t, int, int, double, double, const T*, const T*, T*, int, \

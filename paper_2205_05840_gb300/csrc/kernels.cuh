@@ -10,10 +10,15 @@ namespace ndmg {
 // fixed point; umax is R words of device scratch for its scale, which the
 // launch forms from u first unless umax_ready (then they hold max |u| bits
 // already).  kz: planes per CTA along z (0 = the built-in choice; any value
-// gives the same result).
+// gives the same result).  pq (double apply only): room for pq_cap block
+// partial sums per right-hand side; when the launch's blocks per right-hand
+// side fit, it also leaves the partial sums of u.y there (layout of
+// k_dot2) and returns their number per right-hand side, else it returns 0
+// and writes none.
 template <typename T>
-void launch_stencil(cudaStream_t s, int sm, int n, double cK, double cM, const T* u, const T* g, T* y, int R,
-                    unsigned long long* umax, int kz = 0, bool umax_ready = false);
+int launch_stencil(cudaStream_t s, int sm, int n, double cK, double cM, const T* u, const T* g, T* y, int R,
+                   unsigned long long* umax, int kz = 0, bool umax_ready = false, double* pq = nullptr,
+                   int64_t pq_cap = 0);
 template <typename T>
 cudaError_t prepare_stencil();
 // g_c = P^t r_f; with zc, also z_c = 0

@@ -169,6 +169,8 @@ struct ndmg_handle {
   double *w64[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   float *w32[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   double* red = nullptr;                  // reduction scratch (partials + results)
+  double* pq_red = nullptr;               // the finest-level FP64 stencil's block partial sums of p.q
+  int64_t pq_cap = 0;                     // ... room per right-hand side (blocks)
   double* red_host = nullptr;             // pinned mirror of the results (2 per right-hand side)
   double* coef = nullptr;                 // per-right-hand-side BLAS scalars (4 slots x 2R)
   double* coef_host = nullptr;            // pinned staging of those scalars
