@@ -1620,12 +1620,18 @@ int ndmg_autotune(ndmg_t* h, int32_t* choices) {
   // the small levels: one cluster launch or the separate launches
   if (st == NDMG_OK && h->Kc > 0 && !h->field) {
     const int kc = h->Kc;
+    // the cycle's right-hand side and solution on level kc: that level's
+    // own vectors, or, when kc is the finest level (every level n <= 16),
+    // which has no float solution vector of its own, the float work vectors
+    // (finest-level size, zeroed above)
+    const float* gc = kc < h->K ? h->lv[kc].r32 : h->w32[0];
+    float* zc = kc < h->K ? h->lv[kc].z32 : h->w32[1];
     float t_on = 0.f, t_off = 0.f;
     for (int v = 0; v < 2 && st == NDMG_OK; ++v) {
       h->coarse_on = v == 0;
       auto cycle = [&] {
-        cudaMemsetAsync(h->lv[kc].z32, 0, sizeof(float) * h->lv[kc].N * R, h->stream);
-        op_vcycle<float>(h, kc, h->lv[kc].r32, h->lv[kc].z32, true);
+        cudaMemsetAsync(zc, 0, sizeof(float) * h->lv[kc].N * R, h->stream);
+        op_vcycle<float>(h, kc, gc, zc, true);
       };
       cycle();
       cudaEventRecord(e0, h->stream);
