@@ -58,9 +58,13 @@ def parse():
                         "whose slowed launches would distort the timings)")
     p.add_argument("--grad-sweep", action="store_true",
                    help="forward + adjoint solve throughput for 32^3 .. 256^3 (one JSON line per size)")
-    p.add_argument("--oracle-job", choices=["none", "solve", "vcycles"], default="none",
+    p.add_argument("--oracle-job", choices=["none", "solve", "vcycles", "configs"], default="none",
                    help="(internal) run the FP64 CPU oracle in this process: 'solve' = one PCG solve at --n "
-                        "(solution written to --out), 'vcycles' = V-cycles at --n; prints one JSON line")
+                        "(solution written to --out), 'vcycles' = V-cycles at --n, 'configs' = the standalone "
+                        "8^3 V-cycle iteration, the --n^3 manufactured PCG solves and the gradient at "
+                        "min(32, --n)^3; prints one JSON line")
+    p.add_argument("--oracle-configs-n", type=int, default=64,
+                   help="--impl reference: grid of the oracle's manufactured PCG solves (0 = skip those timings)")
     p.add_argument("--out", default="")
     p.add_argument("--oracle-tol", type=float, default=1e-10)
     p.add_argument("--cycles", type=int, default=2)
@@ -263,11 +267,59 @@ def cpu_model():
     return {"model": name, "logical_cpus": os.cpu_count(), "machine": platform.machine()}
 
 
+def oracle_configs(n2: int):
+    """The oracle's time-to-tolerance on the smaller workload configurations,
+    in this process (thread count fixed by the environment the parent set):
+    the standalone V-cycle iteration on 8^3 (coarsest 2^3, seed-0 load) to
+    1e-8; PCG preconditioned by the V-cycle on n2^3 (coarsest 4^3) with the
+    manufactured sine load for alpha = 0.01, 1, 100 to 1e-8; and the
+    differentiable solve's forward and adjoint solves with dL/dalpha on
+    min(32, n2)^3 (seed-0 load, seed-1 target) to 1e-8."""
+    import numpy as np
+    from oracle import mg
+    from paper_2205_05840_gb300 import inputs
+    out = {"threads": cores_used()}
+    t0 = time.perf_counter()
+    H = mg.Hierarchy(8, 1.0, 1.0, 1.0, n0=2, kind="vertex", m=M_SMOOTH)
+    f = inputs.random_load(8, 0)
+    t1 = time.perf_counter()
+    _, it, hist = mg.vcycle_iteration(H, f, tol=TOL)
+    t2 = time.perf_counter()
+    out["standalone_8"] = {"n": 8, "dofs": num_edges(8), "setup_s": t1 - t0, "time_to_1e-8_s": t2 - t1,
+                           "vcycles": it, "s_per_vcycle": (t2 - t1) / max(it, 1), "relres": hist[-1]}
+    out["manufactured_pcg"] = []
+    for a in (0.01, 1.0, 100.0):
+        t0 = time.perf_counter()
+        H = mg.Hierarchy(n2, 1.0, a, 1.0, n0=N_COARSEST, kind="vertex", m=M_SMOOTH)
+        f = inputs.manufactured_load(n2, 1.0, a, 1.0)
+        t1 = time.perf_counter()
+        _, it, rr, _ = mg.pcg(H, f, tol=TOL)
+        t2 = time.perf_counter()
+        out["manufactured_pcg"].append({"n": n2, "dofs": num_edges(n2), "alpha": a, "setup_s": t1 - t0,
+                                        "time_to_1e-8_s": t2 - t1, "iters": it,
+                                        "s_per_iter": (t2 - t1) / max(it, 1), "relres": rr})
+    ng = min(32, n2)
+    t0 = time.perf_counter()
+    H = mg.Hierarchy(ng, 1.0, 1.0, 1.0, n0=N_COARSEST, kind="vertex", m=M_SMOOTH)
+    f = inputs.random_load(ng, 0)
+    ut = inputs.random_target(ng, 1)
+    t1 = time.perf_counter()
+    loss, _, dalpha, _ = mg.loss_and_grad(H, f, ut, tol=TOL)
+    t2 = time.perf_counter()
+    out["gradient"] = {"n": ng, "dofs": num_edges(ng), "setup_s": t1 - t0, "fwd_bwd_s": t2 - t1,
+                       "loss": loss, "dL_dalpha": dalpha}
+    return out
+
+
 def oracle_job(args):
     """The oracle in a process of its own (thread count fixed by the
     environment the parent set): 'solve' = FP64 PCG with the oracle's V-cycle
     at --n to --oracle-tol from u = 0 (seed-0 load), solution saved to --out;
-    'vcycles' = --cycles V-cycles at --n.  One JSON line with the timings."""
+    'vcycles' = --cycles V-cycles at --n; 'configs' = oracle_configs(--n).
+    One JSON line with the timings."""
+    if args.oracle_job == "configs":
+        print(json.dumps(oracle_configs(args.n)), flush=True)
+        return
     import numpy as np
     from oracle import mg
     from paper_2205_05840_gb300 import inputs
@@ -341,6 +393,14 @@ def run_reference(args):
         secs.append(dt)
     value = num_edges(ORACLE_SAMPLE_N) * len(rates) / sum(secs)
     sample = f"one FP64 oracle V-cycle per step on the {ORACLE_SAMPLE_N}^3 grid (same alpha, m, coarsest 4^3)"
+    # after the timed steps: the oracle's time-to-tolerance on the smaller
+    # workload configurations, one thread (the oracle's sparse and small
+    # dense work runs no faster on more)
+    configs = None
+    if args.oracle_configs_n > 0:
+        configs = oracle_result(spawn_oracle("configs", args.oracle_configs_n, 1), timeout=900)
+        if configs is not None:
+            configs["cpu"] = cpu_model()
     out = {"impl": "reference", "metric": "V-cycle DoF*cycles/s (solve to 1e-8 at 128^3)", "value": value,
            "unit": "DoF*cycles/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * sum(secs) / len(secs), "higher_is_better": True, "scaling": "weak",
@@ -348,7 +408,8 @@ def run_reference(args):
            "config": {"workload": f"{ORACLE_SAMPLE_N}^3 sample of the 128^3 alpha=1 seeded-uniform-load solve"},
            "cpu_baseline": {"value": value, "unit": "DoF*cycles/s", "cores": cores_used(), "kind": "oracle",
                             "sample": sample},
-           "e2e": {"value": value, "unit": "DoF*cycles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+           "e2e": {"value": value, "unit": "DoF*cycles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "oracle_configs": configs}
     print(json.dumps(out), flush=True)
 
 
@@ -505,6 +566,60 @@ def time_solves(ndmg, inputs, torch, dev, prec, alpha, nrhs, rank, reps=2, field
     if roof:
         out["roofline_patch"] = roof
     del S, f, u
+    torch.cuda.empty_cache()
+    return out
+
+
+def config_legs(torch, ndmg, inputs, dev, reps=3):
+    """The smaller workload configurations on the GPU with FP64 handles (the
+    paper's setting): the standalone V-cycle iteration on 8^3 (coarsest 2^3,
+    seed-0 load) to 1e-8, and PCG preconditioned by the V-cycle on 64^3
+    (coarsest 4^3) with the manufactured sine load for alpha = 0.01, 1, 100
+    to 1e-8, with the largest deviation from the closed-form discrete
+    solution c Pi u relative to its largest entry.  Best of `reps` runs after
+    an untimed one, CUDA events on the handle's stream."""
+    import numpy as np
+
+    def best_of(S, stream, f, u, call):
+        call(f, u)
+        best, res = None, None
+        for _ in range(reps):
+            with torch.cuda.stream(stream):
+                u.zero_()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+            res = call(f, u)
+            with torch.cuda.stream(stream):
+                b.record(stream)
+            b.synchronize()
+            t = a.elapsed_time(b)
+            best = t if best is None else min(best, t)
+        return best, res
+
+    out = {"precision": "fp64", "launch_shapes": "built-in (not autotuned)"}
+    stream = torch.cuda.Stream(device=dev)
+    S = ndmg.Solver(8, n_coarsest=2, m=M_SMOOTH, stream=stream)
+    f = torch.tensor(inputs.random_load(8, 0), dtype=torch.float64, device=dev)
+    u = torch.zeros_like(f)
+    ms, (_, cyc, rr) = best_of(S, stream, f, u, lambda f_, u_: S.vcycle_iterate(f_, u_, tol=TOL, maxit=500))
+    out["standalone_8"] = {"n": 8, "dofs": S.num_dofs(), "time_to_1e-8_ms": ms, "vcycles": cyc, "relres": rr}
+    del S, f, u
+    n, h = 64, 1.0 / 64
+    mu = (2.0 + np.cos(np.pi * h)) / 3.0
+    sig = (np.sin(np.pi * h / 2) / (np.pi * h / 2)) ** 2
+    ref = inputs.sine_interpolant(n)
+    out["manufactured_pcg"] = []
+    for alpha in (0.01, 1.0, 100.0):
+        S = ndmg.Solver(n, n_coarsest=N_COARSEST, alpha=alpha, m=M_SMOOTH, stream=stream)
+        f = torch.tensor(inputs.manufactured_load(n, 1.0, alpha, 1.0), dtype=torch.float64, device=dev)
+        u = torch.zeros_like(f)
+        ms, (_, it, rr) = best_of(S, stream, f, u, lambda f_, u_: S.solve(f_, u_, tol=TOL, maxit=500))
+        c = (2 * np.pi ** 2 * alpha + 1) * sig ** 2 / (8 * alpha * np.sin(np.pi * h / 2) ** 2 * mu / h ** 2 + mu ** 2)
+        err = float(np.abs(u.cpu().numpy() - c * ref).max() / np.abs(c * ref).max())
+        out["manufactured_pcg"].append({"n": n, "dofs": S.num_dofs(), "alpha": alpha, "time_to_1e-8_ms": ms,
+                                        "iters": it, "relres": rr, "max_rel_err_vs_closed_form": err})
+        del S, f, u
     torch.cuda.empty_cache()
     return out
 
@@ -712,6 +827,10 @@ def run_ours(args):
                                      field=inputs.inclusion_field(N_GRID, 1.0, 10.0))
         extra["field"]["field"] = "inclusion: alpha = 10 on cells [n/4, 3n/4)^3, 1 elsewhere"
         extra["grad"] = grad_legs(torch, ndmg, inputs, dev, (96, 256), prec)
+        try:   # the 8^3 and 64^3 configurations (FP64); a failure here leaves the line intact
+            extra["configs"] = config_legs(torch, ndmg, inputs, dev)
+        except Exception as e:  # noqa: BLE001
+            extra["configs"] = {"error": repr(e)}
     del S
     torch.cuda.empty_cache()
 
