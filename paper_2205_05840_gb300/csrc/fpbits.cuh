@@ -7,12 +7,12 @@
 // check each function bit for bit against the IEEE conversions.
 #pragma once
 #include <stdint.h>
+#include <string.h>
 
 #if defined(__CUDACC__)
 #define NDMG_HD __host__ __device__ __forceinline__
 #else
 #define NDMG_HD inline
-#include <string.h>
 #endif
 
 namespace ndmg {
