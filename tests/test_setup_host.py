@@ -58,8 +58,17 @@ int main(int argc, char** argv) {
   const std::string dir = argv[1];
   const int n = atoi(argv[2]), n0 = atoi(argv[3]);
   const double L = atof(argv[4]), alpha = atof(argv[5]), beta = atof(argv[6]);
+  const int s = argc > 7 ? atoi(argv[7]) : 2;
   LocalOps ops;
-  build_local_ops(n, L, alpha, beta, &ops, 2);
+  build_local_ops(n, L, alpha, beta, &ops, s);
+  if (s != 2) {  // subdomains of s^3 cells: interior inverses and the Gram factor only
+    wr(dir + "/AinvT.bin", ops.AinvT);
+    wr(dir + "/Wv.bin", ops.Wv);
+    wr(dir + "/map_T.bin", box_map(Box{{s, s, s}}));
+    wr(dir + "/map_V.bin", box_map(Box{{2 * s, 2 * s, 2 * s}}));
+    printf("%d %d %d\n", ops.mT, ops.mV, ops.nG);
+    return 0;
+  }
   wr(dir + "/AinvT.bin", ops.AinvT);
   wr(dir + "/Dv.bin", ops.Dv);
   wr(dir + "/Wv.bin", ops.Wv);
@@ -107,6 +116,18 @@ def _run(driver, n, n0, L, alpha, beta):
            "map_T": rd("map_T").reshape(-1, 4).astype(int), "map_V": rd("map_V").reshape(-1, 4).astype(int),
            "map_E": [rd(f"map_E{k}").reshape(-1, 4).astype(int) for k in range(3)]}
     return ops
+
+
+def _run_s(driver, n, L, alpha, beta, s):
+    exe, d = driver
+    out = os.path.join(d, f"run_s{s}_{n}_{alpha}")
+    os.makedirs(out, exist_ok=True)
+    res = subprocess.run([exe, out, str(n), "2", repr(L), repr(alpha), repr(beta), str(s)], check=True,
+                         capture_output=True, text=True)
+    mT, mV, nG = map(int, res.stdout.split())
+    rd = lambda name: np.fromfile(os.path.join(out, name + ".bin"), dtype=np.float64)  # noqa: E731
+    return {"mT": mT, "mV": mV, "nG": nG, "AinvT": rd("AinvT").reshape(mT, mT), "Wv": rd("Wv").reshape(mV, nG),
+            "map_T": rd("map_T").reshape(-1, 4).astype(int), "map_V": rd("map_V").reshape(-1, 4).astype(int)}
 
 
 def _global(n, box_map, origin):
@@ -182,3 +203,29 @@ def test_setup_box_numbering_is_the_canonical_layout(driver):
     ops = _run(driver, 4, 2, 1.0, 1.0, 1.0)
     m = ops["map_V"]            # a 4 x 4 x 4 box
     assert (_global(4, m, np.zeros(3, dtype=int)) == np.arange(hcurl.num_edges(4))).all()
+
+
+@pytest.mark.parametrize("alpha", [1.0, 30.0])
+def test_setup_subdomain4_operators_reproduce_the_oracle_smoother(driver, alpha):
+    # subdomains of 4^3 cells: 108 x 108 interior-space inverses and the
+    # Gram factor W (1176 x 312) of the 8^3-cell vertex patches, applied as
+    # W (W^t r) patch by patch (the dense 1176^2 operator is never formed)
+    n, s, L, beta = 16, 4, 1.0, 1.0
+    ops = _run_s(driver, n, L, alpha, beta, s)
+    assert (ops["mT"], ops["mV"], ops["nG"]) == (108, 1176, 312)
+    A = hcurl.assemble(n, L, alpha, beta)
+    R = np.random.default_rng(12).standard_normal((A.shape[0], 4))
+    got = np.zeros_like(R)
+    nc = n // s
+    for c in np.ndindex(nc, nc, nc):                 # subdomains: cells [4c, 4c + 4)
+        idx = _global(n, ops["map_T"], s * np.array(c[::-1]))
+        assert (idx >= 0).all()
+        got[idx] += ops["AinvT"] @ R[idx]
+    for v in np.ndindex(nc - 1, nc - 1, nc - 1):     # interior subdomain vertices: cells [4v - 4, 4v + 4)
+        idx = _global(n, ops["map_V"], s * (np.array(v[::-1]) + 1) - s)
+        assert (idx >= 0).all()
+        got[idx] += ops["Wv"] @ (ops["Wv"].T @ R[idx])
+    S = mg.Smoother(A, n, "vertex", s=s)
+    want = np.stack([S.apply(R[:, c]) for c in range(R.shape[1])], axis=1) / S.eta
+    err = np.abs(got - want).max() / np.abs(want).max()
+    assert err < 1e-10, err
