@@ -108,9 +108,11 @@ int ndmg_opts_default(ndmg_opts* o);
  * device workspaces.  *out receives the handle (NULL on failure).  Errors:
  * INVALID_ARG (bad sizes, alpha/beta/L <= 0, nrhs < 1, unsupported smoother;
  * MIXED precision whose rounded Gram factor W~ cannot carry the vertex-patch
- * operator: largest eigenvalue of A_p W~W~^t above 16, which bf16 operands reach
- * near alpha / (beta h^2) = 2.8e5 and fp16 ones near 2.5e7 -- the smoother would
- * diverge; the message names the level), OUT_OF_MEMORY, CUDA_ERROR.
+ * operator: largest eigenvalue of A_p W~W~^t above 16, which bf16 operands can
+ * reach from alpha / (beta h^2) ~ 3e5 on (23 at 4.1e5 on a 64^3 level; the value
+ * also depends on the rounded factor's bit patterns, 7.3 there on 32^3 and
+ * 128^3) and fp16 ones only beyond ~2.5e7 -- the smoother would diverge; the
+ * message names the level), OUT_OF_MEMORY, CUDA_ERROR.
  * Debugging aid: with the environment variable NDMG_POISON_WORKSPACES=1 set
  * when the handle is created, every device workspace starts as all-one bytes
  * (NaN in float and double), so a read of an entry nothing has written shows

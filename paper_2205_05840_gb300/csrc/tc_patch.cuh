@@ -10,9 +10,12 @@ cudaError_t upload_tc_operand(void** dst, const std::vector<double>& W, bool fp1
 // Largest eigenvalue of A_p W~ W~^t for the rounded operand W~ of W (1 for
 // the exact factor); the smoother loses its stability as it grows.
 double tc_operand_spectral_max(const double* W, const std::vector<double>& Ap, bool fp16);
-// Most the library accepts (measured: bf16 operands reach it near
-// alpha / (beta h^2) = 2.8e5 on a vertex patch, fp16 operands near 2.5e7; a
-// bf16 solve with 22 at 4e5 diverged, one with 13 at 2.3e5 converged).
+// Most the library accepts.  The value grows with the patch's conditioning,
+// ~ alpha / (beta h^2), and depends on the bit patterns of the rounded factor
+// as well: bf16 operands give 13 at alpha / (beta h^2) = 2.3e5 and 23 at
+// 4.1e5 on 64^3 vertex patches, 4.8 and 7.3 at the same ratios on 32^3 and
+// 128^3 (14 at 9.2e5 on 128^3); fp16 operands stay below 15 up to 2.5e7.  A
+// bf16 solve with 23 at 4.1e5 diverged, one with 13 at 2.3e5 converged.
 constexpr double kTcSpectralMax = 16.0;
 // Opt in to the kernel's dynamic shared memory.
 cudaError_t prepare_tc_patch();

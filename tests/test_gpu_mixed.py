@@ -307,7 +307,7 @@ def test_graph_replay_matches_direct_launches(prec):
 
 def test_bf16_rejects_operator_it_cannot_represent():
     # alpha / (beta h^2) = 4.1e5 (alpha = 100 at 64^3): the bf16-rounded Gram
-    # factor gives A_p W~W~^t an eigenvalue of 22 instead of 1 and the solve
+    # factor gives A_p W~W~^t an eigenvalue of 23 instead of 1 and the solve
     # diverged; the library refuses it at set-up and fp16 handles the case
     with pytest.raises(ndmg.NdmgError) as e:
         ndmg.Solver(64, n_coarsest=4, alpha=100.0, precision=ndmg.PREC_MIXED_BF16)
