@@ -64,6 +64,11 @@ static std::vector<double> fam(const PatchFamily& f) {
 static void group(const std::string& p, const GroupedFamily& g) {
   wr(p + "_gid.bin", std::vector<double>(g.gid.begin(), g.gid.end()));
   wr(p + "_op.bin", g.op);
+  // the kernels' work list: members group by group, chunks of at most 8
+  std::vector<int> plist, chunks;
+  group_chunks(g, 8, &plist, &chunks);
+  wr(p + "_plist.bin", std::vector<double>(plist.begin(), plist.end()));
+  wr(p + "_chunks.bin", std::vector<double>(chunks.begin(), chunks.end()));
 }
 int main(int argc, char** argv) {
   const std::string dir = argv[1];
@@ -228,3 +233,24 @@ def test_field_groups_follow_the_cell_coefficients(driver):
         o = 2 * np.array([c % nc, (c // nc) % nc, c // (nc * nc)])
         covers = all(o[ax] <= (5, 4, 3)[ax] < o[ax] + 2 for ax in range(3))
         assert (gid_b[c] != 0) == covers
+
+
+@pytest.mark.parametrize("field", sorted(FIELDS))
+def test_field_work_lists_cover_every_member_once(driver, field):
+    # the grouped kernels walk chunks {group, first, count} of the member list
+    # (members listed group by group): every member exactly once, a chunk
+    # holds at most 8 members of one group
+    n = 8
+    rd = _run(driver, f"chunks_{field}", FIELDS[field](n), n, 2, 1.0, 1.0)
+    for name in ("bub", "vtx", "edge0", "edge1", "edge2"):
+        gid = rd(name + "_gid").astype(int)
+        plist = rd(name + "_plist").astype(int)
+        chunks = rd(name + "_chunks").astype(int).reshape(-1, 4)
+        assert sorted(plist) == list(range(gid.size))
+        covered = []
+        for q, first, count, pad in chunks:
+            assert 1 <= count <= 8 and pad == 0
+            members = plist[first:first + count]
+            assert (gid[members] == q).all()
+            covered.extend(members)
+        assert sorted(covered) == list(range(gid.size))
