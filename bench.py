@@ -48,7 +48,9 @@ def parse():
     p.add_argument("--precision", choices=["auto", "fp64", "fp32", "bf16", "fp16"], default="auto")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
-    p.add_argument("--no-extra", action="store_true", help="skip the FP64 and batched comparison solves")
+    p.add_argument("--no-extra", action="store_true",
+                   help="skip the comparison solves (FP64, batched, coefficient field, gradient, 8^3 and 64^3 "
+                        "configurations)")
     p.add_argument("--profile-case", choices=["none", "smooth", "residual", "vcycle"], default="none",
                    help="run only a few launches of one kernel class on an --n grid (for ncu captures)")
     p.add_argument("--n", type=int, default=N_GRID)
