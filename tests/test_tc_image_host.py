@@ -1,0 +1,128 @@
+"""The operand image of the tensor-core smoother (tc_image in
+paper_2205_05840_gb300/csrc/tc_patch.cu), built by a host program and checked
+on the CPU.
+
+The brick kernel multiplies the gathered patch residuals by W (108 x 60, the
+Gram factor of the vertex-patch operator, eq. vertex space) and the result by
+W^t on the tensor cores, with operands in the K-major layout of 8 x 8-element
+core matrices (16-byte rows).  The set-up writes, per level, one image: B1 =
+W^t scaled by sw (N = 64, K = 112), B2 = W scaled by sw2 = 4096 sw (N = 112,
+K = 64), each rounded to fp16 or bf16 and zero-padded, the float 1 / (sw sw2)
+after them, and B2's low-order part (W sw2 minus its rounding, rounded again)
+for the second product.  The test compiles the kernel's translation unit into
+a host program (nothing is launched), reads every element back through the
+kernel's own layout function, and compares with W rounded by NumPy (IEEE
+round-to-nearest-even)."""
+from __future__ import annotations
+
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2205_05840_gb300", "csrc")
+
+DRIVER = r"""
+#include <cstdio>
+#include <cstdlib>
+#include <string>
+#include <vector>
+#include "tc_patch.cu"   // this translation unit: its file-local image builder and layout function
+using namespace ndmg;
+static void wr(const std::string& p, const void* v, size_t bytes) {
+  FILE* f = fopen(p.c_str(), "wb"); fwrite(v, 1, bytes, f); fclose(f);
+}
+int main(int argc, char** argv) {
+  const std::string dir = argv[1];
+  const int n = atoi(argv[2]);
+  const double alpha = atof(argv[3]);
+  const bool fp16 = atoi(argv[4]) != 0;
+  LocalOps ops;
+  build_local_ops(n, 1.0, alpha, 1.0, &ops, 2);
+  std::vector<uint8_t> img(kImgStride + kLoBytes, 0xAB);
+  tc_image(ops.Wv.data(), fp16, img.data(), img.data() + kImgStride);
+  // every element read back through the layout function: B1 [64][112],
+  // B2 [112][64], lo [112][64] (16-bit words), then the scale
+  std::vector<uint16_t> b1(kN1 * kK1), b2(kN2 * kK2), lo(kN2 * kK2);
+  for (int r = 0; r < kN1; ++r)
+    for (int k = 0; k < kK1; ++k) std::memcpy(&b1[r * kK1 + k], img.data() + core_off(r, k, kK1), 2);
+  for (int r = 0; r < kN2; ++r)
+    for (int k = 0; k < kK2; ++k) {
+      std::memcpy(&b2[r * kK2 + k], img.data() + kN1 * kK1 * 2 + core_off(r, k, kK2), 2);
+      std::memcpy(&lo[r * kK2 + k], img.data() + kImgStride + core_off(r, k, kK2), 2);
+    }
+  float inv;
+  std::memcpy(&inv, img.data() + kImgBytes, sizeof(float));
+  wr(dir + "/W.bin", ops.Wv.data(), ops.Wv.size() * sizeof(double));
+  wr(dir + "/b1.bin", b1.data(), b1.size() * 2);
+  wr(dir + "/b2.bin", b2.data(), b2.size() * 2);
+  wr(dir + "/lo.bin", lo.data(), lo.size() * 2);
+  printf("%d %d %d %.9g\n", kImgBytes, kImgStride, kLoBytes, (double)inv);
+  return 0;
+}
+"""
+
+SOURCES = ["setup.cpp", "kernels.cu"]
+
+
+@pytest.fixture(scope="module")
+def driver(tmp_path_factory):
+    nvcc = os.environ.get("NVCC") or shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not found")
+    d = str(tmp_path_factory.mktemp("tc_image_host"))
+    src = os.path.join(d, "drv.cu")
+    with open(src, "w") as fh:
+        fh.write(DRIVER)
+    exe = os.path.join(d, "drv")
+    subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O2", "-std=c++17",
+                    "--expt-relaxed-constexpr", "-w", "-I", os.path.join(ROOT, "include"), "-I", CSRC, src,
+                    *[os.path.join(CSRC, s) for s in SOURCES], "-o", exe], check=True, capture_output=True)
+    return exe, d
+
+
+def _round_bf16(x: np.ndarray) -> np.ndarray:
+    m, e = np.frexp(x)
+    return np.ldexp(np.rint(m * 256.0), e - 8)
+
+
+def _decode(bits: np.ndarray, fp16: bool) -> np.ndarray:
+    if fp16:
+        return bits.view(np.float16).astype(np.float64)
+    return (bits.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+@pytest.mark.parametrize("n,alpha", [(16, 1.0), (128, 1.0), (64, 100.0)])
+def test_operand_image_holds_the_rounded_gram_factor(driver, prec, n, alpha):
+    exe, d = driver
+    fp16 = prec == "fp16"
+    out = os.path.join(d, f"run_{n}_{alpha}_{prec}")
+    os.makedirs(out, exist_ok=True)
+    res = subprocess.run([exe, out, str(n), repr(alpha), "1" if fp16 else "0"], check=True, capture_output=True,
+                         text=True)
+    img_bytes, stride, lo_bytes, inv = res.stdout.split()
+    assert (int(img_bytes), int(stride), int(lo_bytes)) == ((64 * 112 + 112 * 64) * 2, (64 * 112 + 112 * 64) * 2 + 16,
+                                                            112 * 64 * 2)
+    W = np.fromfile(os.path.join(out, "W.bin")).reshape(108, 60)
+    b1 = _decode(np.fromfile(os.path.join(out, "b1.bin"), dtype=np.uint16), fp16).reshape(64, 112)
+    b2 = _decode(np.fromfile(os.path.join(out, "b2.bin"), dtype=np.uint16), fp16).reshape(112, 64)
+    lo = _decode(np.fromfile(os.path.join(out, "lo.bin"), dtype=np.uint16), fp16).reshape(112, 64)
+    rnd = (lambda x: x.astype(np.float16).astype(np.float64)) if fp16 else _round_bf16
+    sw = 2.0 ** -np.ceil(np.log2(np.abs(W).max()))
+    sw2 = 4096.0 * sw
+    # B1 = W^t sw and B2 = W sw2, rounded; the padding rows and columns are 0
+    assert np.array_equal(b1[:60, :108], rnd(W.T * sw)) and not b1[60:].any() and not b1[:, 108:].any()
+    assert np.array_equal(b2[:108, :60], rnd(W * sw2)) and not b2[108:].any() and not b2[:, 60:].any()
+    # the low-order part of B2, and what the two parts carry together
+    assert np.array_equal(lo[:108, :60], rnd(W * sw2 - rnd(W * sw2))) and not lo[108:].any() and not lo[:, 60:].any()
+    bits = 11 if fp16 else 8
+    two = b2[:108, :60] + lo[:108, :60]
+    assert np.abs(two - W * sw2).max() <= 2.0 ** (-2 * bits + 1) * np.abs(W * sw2).max()
+    # the scale after both images undoes sw sw2
+    assert float(inv) == float(np.float32(1.0 / (sw * sw2)))
+    # max |W sw| in (1/2, 1]
+    assert 0.5 < np.abs(W * sw).max() <= 1.0
