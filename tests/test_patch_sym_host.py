@@ -18,7 +18,6 @@ oracle in test_setup_host.py).  No kernel is launched, so no GPU is needed."""
 from __future__ import annotations
 
 import os
-import shutil
 import subprocess
 
 import numpy as np
@@ -65,19 +64,8 @@ K_HDR = 3 + 3 * 8
 
 
 @pytest.fixture(scope="module")
-def driver(tmp_path_factory):
-    nvcc = os.environ.get("NVCC") or shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
-    if not os.path.exists(nvcc):
-        pytest.skip("nvcc not found")
-    d = str(tmp_path_factory.mktemp("patch_sym_host"))
-    src = os.path.join(d, "drv.cpp")
-    with open(src, "w") as fh:
-        fh.write(DRIVER)
-    exe = os.path.join(d, "drv")
-    subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O2", "-std=c++17",
-                    "--expt-relaxed-constexpr", "-w", "-I", os.path.join(ROOT, "include"), "-I", CSRC, src,
-                    *[os.path.join(CSRC, s) for s in SOURCES], "-o", exe], check=True, capture_output=True)
-    return exe, d
+def driver(host_build, tmp_path_factory):
+    return host_build(DRIVER, SOURCES), str(tmp_path_factory.mktemp("patch_sym_host"))
 
 
 def _decode(blob: np.ndarray):

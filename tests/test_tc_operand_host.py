@@ -15,7 +15,6 @@ property of the exact factor.  No kernel is launched, so no GPU is needed."""
 from __future__ import annotations
 
 import os
-import shutil
 import subprocess
 
 import numpy as np
@@ -53,19 +52,8 @@ SOURCES = ["setup.cpp", "kernels.cu", "tc_patch.cu"]
 
 
 @pytest.fixture(scope="module")
-def driver(tmp_path_factory):
-    nvcc = os.environ.get("NVCC") or shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
-    if not os.path.exists(nvcc):
-        pytest.skip("nvcc not found")
-    d = str(tmp_path_factory.mktemp("tc_operand_host"))
-    src = os.path.join(d, "drv.cpp")
-    with open(src, "w") as fh:
-        fh.write(DRIVER)
-    exe = os.path.join(d, "drv")
-    subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O2", "-std=c++17",
-                    "--expt-relaxed-constexpr", "-w", "-I", os.path.join(ROOT, "include"), "-I", CSRC, src,
-                    *[os.path.join(CSRC, s) for s in SOURCES], "-o", exe], check=True, capture_output=True)
-    return exe, d
+def driver(host_build, tmp_path_factory):
+    return host_build(DRIVER, SOURCES), str(tmp_path_factory.mktemp("tc_operand_host"))
 
 
 def _round_bf16(x: np.ndarray) -> np.ndarray:
