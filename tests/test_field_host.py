@@ -1,6 +1,6 @@
 """The library's host-side set-up for a curl-curl coefficient per hexahedron
-(paper_2205_05840_gb300/csrc/field.cpp, row f4), built as a host program and
-checked on the CPU against the oracle.
+(paper_2205_05840_gb300/csrc/field.cpp), built as a host program and checked
+on the CPU against the oracle.
 
 With a coefficient per cell the local problems of the smoother differ between
 subdomains and patches; the set-up groups the members of each family (coarse

@@ -1,5 +1,5 @@
-"""The library's host-side level set-up (paper_2205_05840_gb300/csrc/setup.cpp,
-row a1), compiled as host C++ and checked on the CPU against the oracle.
+"""The library's host-side level set-up (paper_2205_05840_gb300/csrc/setup.cpp),
+compiled as host C++ and checked on the CPU against the oracle.
 
 The set-up forms the local operators every smoother kernel applies: the 6 x 6
 inverse of the interior-space matrix A_T of a coarse element, the 108 x 108
